@@ -1,0 +1,131 @@
+"""Planted mistakes in the oracle (on the CPU) must be caught by its pins.
+
+Each test patches one plausible error into the oracle - a dropped term, a
+wrong sign, a wrong order or index - and checks that the pin covering that
+part fails.  This shows the pins are not vacuous.
+"""
+import math
+
+import numpy as np
+import scipy.sparse.linalg as spla
+import scipy.special as ss
+
+import oracle.decomposition as odec
+import oracle.discretization as odis
+import oracle.sweeping as oswp
+import workloads as W
+from oracle import Decomposition, Sweeper, assemble_operator
+
+
+def _exact_interface_error():
+    w = W.workload("custom", n=30, N1=3, N2=2, medium="layered", seed=2,
+                   xcuts=[0, 11, 19, 30], ycuts=[0, 13, 30])
+    A = assemble_operator(w.n, w.h, w.omega, w.m2)
+    dec = Decomposition(w.n, w.h, w.omega, w.m2, w.xcuts, w.ycuts)
+    r = W.random_complex(w.N, 11)
+    z = Sweeper(dec).precondition(r, "exact")
+    u = spla.spsolve(A.tocsc(), r)
+    return np.linalg.norm(z - u) / np.linalg.norm(u)
+
+
+def test_pin_holds_unpatched():
+    assert _exact_interface_error() < 1e-12
+
+
+def test_dropped_incoming_term_in_transmission_is_caught(monkeypatch):
+    def bad(self, i, j, u_local, G_in):
+        p_local, beta_e = self._edges[(i, j)]
+        return -(4.0 * beta_e * u_local[p_local]) / (1.0 - beta_e)
+    monkeypatch.setattr(odec.Decomposition, "outgoing", bad)
+    assert _exact_interface_error() > 1e-3
+
+
+def test_wrong_sign_in_transmission_is_caught(monkeypatch):
+    def bad(self, i, j, u_local, G_in):
+        p_local, beta_e = self._edges[(i, j)]
+        return -((1.0 + beta_e) * G_in - 4.0 * beta_e * u_local[p_local]) / (1.0 - beta_e)
+    monkeypatch.setattr(odec.Decomposition, "outgoing", bad)
+    assert _exact_interface_error() > 1e-3
+
+
+def test_unscaled_incoming_data_in_local_rhs_is_caught(monkeypatch):
+    orig = odec.Decomposition.local_solve
+
+    def bad(self, i, source, incoming):
+        # forgets the 1/(1 - beta_e) factor of the incoming data
+        x0, x1, y0, y1 = self.box(i)
+        M = (x1 - x0) * (y1 - y0)
+        rhs = np.zeros(M, dtype=np.complex128) if source is None else np.array(source, dtype=np.complex128)
+        for j, G in incoming.items():
+            p_local, beta_e = self._edges[(i, j)]
+            np.add.at(rhs, p_local, G)
+        return self.local_solver(i).solve(rhs)
+    monkeypatch.setattr(odec.Decomposition, "local_solve", bad)
+    assert _exact_interface_error() > 1e-3
+    monkeypatch.setattr(odec.Decomposition, "local_solve", orig)
+
+
+def test_reversed_sweep_order_is_caught(monkeypatch):
+    """Applying the elementary factors of S_L^{-1} in the reverse order is no
+    longer a forward substitution: the dense Proposition-1 pin fails."""
+    w = W.workload("custom", n=23, N1=3, N2=3, medium="layered", seed=6)
+    dec = Decomposition(w.n, w.h, w.omega, w.m2, w.xcuts, w.ycuts)
+    sw = Sweeper(dec)
+    S = sw.dense_S()
+    d = np.concatenate([[dec.diagonal(ij[0])] * dec.side_length(*ij) for ij in dec.slots])
+    SL = np.eye(len(d)) - np.where(d[:, None] == d[None, :] + 1, S, 0)
+    b = dec.unflatten(W.random_complex(len(d), 7))
+    ref = np.linalg.solve(SL, dec.flatten(b))
+    good = dec.flatten(sw.inv_SL(b))
+    bad = dec.flatten(sw.inv_SL(b, diags=range(dec.Ng + 1, 2, -1)))
+    assert np.linalg.norm(good - ref) / np.linalg.norm(ref) < 1e-12
+    assert np.linalg.norm(bad - ref) / np.linalg.norm(ref) > 1e-3
+
+
+def test_incoming_radiation_sign_is_caught(monkeypatch):
+    """Flipping the sign of beta in the outer ABC turns the outgoing condition
+    into an incoming one: the Hankel pin fails."""
+    orig = odis.ghost_factor
+    monkeypatch.setattr(odis, "ghost_factor", lambda beta: orig(-beta))
+    n = 255
+    h = 1.0 / (n + 1)
+    kap = 2 * math.pi / (25 * h)
+    A = odis.assemble_operator(n, h, kap, np.ones(n * n)).tocsc()
+    c = n // 2
+    f = np.zeros(n * n, complex)
+    f[c * n + c] = 1.0
+    U = spla.spsolve(A, f).reshape(n, n)
+    errs = [abs(U[c, c + k] - 0.25j * ss.hankel1(0, kap * k * h)) / abs(0.25j * ss.hankel1(0, kap * k * h))
+            for k in (6, 12, 25, 40)]
+    assert max(errs) > 0.1
+
+
+def test_row_major_numbering_is_caught(monkeypatch):
+    """Ordering subdomains by (i2, i1) instead of the paper's (|i|_1, i1) breaks
+    the paper's example m((1,1),(2,1)) = 2."""
+    monkeypatch.setattr(odec, "multi_index_key", lambda i: (i[1], i[0]))
+    w = W.workload("custom", n=15, N1=3, N2=3)
+    dec = odec.Decomposition(w.n, w.h, w.omega, w.m2, w.xcuts, w.ycuts)
+    assert dec.m[((1, 1), (2, 1))] != 2 or dec.m[((1, 2), (1, 1))] != 3
+
+
+def test_double_counted_shared_diagonal_is_caught():
+    """The literal additive combination (shared diagonal counted by both bands)
+    differs from the restricted-additive reading, which the single-band
+    identity BSP == SGS pins."""
+    w = W.workload("custom", n=24, N1=2, N2=2, medium="layered", seed=1)
+    dec = Decomposition(w.n, w.h, w.omega, w.m2, w.xcuts, w.ycuts)
+    sw = Sweeper(dec)
+    b = dec.unflatten(W.random_complex(sum(dec.side_length(*ij) for ij in dec.slots), 3))
+    ref = dec.flatten(sw.sgs(b))
+    assert np.linalg.norm(dec.flatten(sw.bsp(b)) - ref) <= 1e-13 * np.linalg.norm(ref)
+    # an additive x' that adds b once more on the start diagonal breaks it
+    xh = sw.block_jacobi_L(b)
+    for ij in dec.slots:
+        if dec.diagonal(ij[0]) == 2:
+            xh[ij] = xh[ij] + b[ij]
+    Sx = sw.apply_S(xh)
+    rho = {ij: b[ij] - xh[ij] + Sx[ij] for ij in dec.slots}
+    y = sw.block_jacobi_U(rho)
+    bad = dec.flatten({ij: xh[ij] + y[ij] for ij in dec.slots})
+    assert np.linalg.norm(bad - ref) > 1e-3 * np.linalg.norm(ref)
