@@ -1,0 +1,201 @@
+/*
+ * helm.h - C ABI of the GB300 block Jacobi sweeping preconditioner library
+ *
+ * Method: R. Dai, "A Block Jacobi Sweeping Preconditioner for the Helmholtz
+ * Equation" (arXiv 2209.10886).  The library discretises
+ *
+ *     -Delta u - kappa(x)^2 u = f   on the grid's rectangle,  kappa = omega sqrt(m2),
+ *     d_n u - i kappa u = 0          on the outer boundary (first-order absorbing,
+ *                                    the paper's Eq. origPbm with T = i kappa,
+ *                                    time dependence e^{-i omega t}, Section 3)
+ *
+ * with the five-point stencil on n_x x n_y interior nodes x_{a,b} = (a h, b h),
+ * a = 1..n_x, b = 1..n_y.  Every row is multiplied by h^2, so the linear
+ * system is  A u = h^2 f  with the complex symmetric matrix
+ *
+ *     (A u)_p = (4 - kappa_p^2 h^2 - sum_{outer ghost sides} c_p) u_p - sum_{grid nbrs q} u_q,
+ *     c_p = (1 + beta_p)/(1 - beta_p),  beta_p = i kappa_p h / 2.
+ *
+ * The domain is split into an N1 x N2 checkerboard of subdomains (Section 2)
+ * coupled by Robin transmission conditions (Eq. subPbm).  The preconditioner
+ * (Sections 3-5) solves all local problems of one stage of the sweep schedule
+ * in one batched launch, exchanges the interface traces through the
+ * transmission operator, and is applied inside FP64 flexible GMRES
+ * (Section 6: GMRES to a relative residual of 1e-6).
+ *
+ * Conventions for every entry point
+ * * Arrays: complex values are helm_c128 (layout-compatible with
+ *   torch.complex128 / C99 double complex).  A field is n_x*n_y values,
+ *   row-major with the y index slowest: p = (b-1)*n_x + (a-1).  Several
+ *   right-hand sides are stored back to back: RHS k starts at ptr + k*n_x*n_y.
+ * * Pointers marked "device" must be CUDA device (or managed) memory of the
+ *   current device; "host" pointers are ordinary host memory.
+ * * Ownership: the caller owns every array it passes and keeps it alive until
+ *   the call's work on `stream` has completed.  The handle owns the factors,
+ *   interface buffers and Krylov workspace and frees them in helm_destroy.
+ * * Execution: calls are ordered on the given stream and return without
+ *   synchronising, except where stated (gmres_solve and misfit_grad read
+ *   convergence data back and synchronise the stream).
+ * * Errors: no C++ exception crosses the ABI.  A non-zero helm_status is
+ *   returned and helm_last_error() describes it.  HELM_ERR_ARG for invalid
+ *   arguments, HELM_ERR_STATE for calls in the wrong order, HELM_ERR_OOM when
+ *   a device allocation fails, HELM_ERR_CUDA for any other CUDA error,
+ *   HELM_ERR_TIMEOUT when a bounded device-side wait gave up.
+ * * Threads: a handle must not be used from two host threads at once.
+ */
+#ifndef HELM_H
+#define HELM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct { double re, im; } helm_c128;
+
+typedef enum {
+    HELM_OK = 0,
+    HELM_ERR_ARG = 1,
+    HELM_ERR_CUDA = 2,
+    HELM_ERR_OOM = 3,
+    HELM_ERR_STATE = 4,
+    HELM_ERR_NO_CONVERGENCE = 5,
+    HELM_ERR_TIMEOUT = 6,
+    HELM_ERR_UNSUPPORTED = 7
+} helm_status;
+
+/* Precision of the subdomain factors and of the preconditioner arithmetic.
+ * HELM_PREC_C128: complex128 factors and solves (the all-FP64 form).
+ * HELM_PREC_C64:  complex64 factors and solves, FP32 accumulation; the
+ *                 interface data and local solves are complex64, the input
+ *                 residual is scaled by its 2-norm before rounding. */
+typedef enum {
+    HELM_PREC_C128 = 0,
+    HELM_PREC_C64 = 1
+} helm_prec;
+
+/* Sweep schedule of the interface preconditioner.
+ * HELM_SCHED_BSP: block Jacobi sweeping (Section 5): forward bands of N1+1
+ *                 diagonals from the bottom-left corner, backward bands from
+ *                 the top-right corner, all bands concurrently; 2 N1 sweep
+ *                 steps (plus one residual stage) per application.
+ * HELM_SCHED_SP:  symmetric Gauss-Seidel sweeping (Section 4,
+ *                 Eq. sgs_preconditioner_forward_backward): 2 (N1+N2-2) steps. */
+typedef enum { HELM_SCHED_BSP = 0, HELM_SCHED_SP = 1 } helm_sched;
+
+/* Robin parameter T_e of the interface condition (d_n - T_e) u = g.
+ * HELM_TC_OPTIMIZED: T_e = (i - 1) s sqrt(kappa_e pi / (2 h)) with s = tc_scale,
+ *                    an optimized zeroth-order complex Robin parameter.
+ * HELM_TC_IMPEDANCE: T_e = i kappa_e, the basic impedance operator the paper
+ *                    uses for its algebra (Section 3).
+ * kappa_e = omega sqrt((m2_p + m2_q)/2) on the edge between nodes p and q.
+ * The converged solution does not depend on T_e; the iteration count does. */
+typedef enum { HELM_TC_OPTIMIZED = 0, HELM_TC_IMPEDANCE = 1 } helm_transmission;
+
+typedef struct {
+    int transmission;   /* helm_transmission; default HELM_TC_OPTIMIZED */
+    double tc_scale;    /* s of HELM_TC_OPTIMIZED; default 1.5 */
+} helm_setup_opts;
+
+typedef struct {
+    int restart;        /* FGMRES restart length m (>= 1); default 50 */
+    int maxit;          /* maximum Arnoldi steps per RHS over all cycles */
+    double tol;         /* stop when ||h^2 f - A u|| <= tol ||h^2 f|| (true residual) */
+    int x0_given;       /* 1: u holds the initial guess; 0: start from u = 0 */
+    int sched;          /* helm_sched used by the preconditioner */
+    int use_graph;      /* 1: replay the preconditioner from a captured CUDA graph */
+    double* hist;       /* optional host buffer of maxit*nrhs doubles: the Arnoldi
+                           residual estimate of RHS k after step j at hist[k*maxit+j] */
+} helm_opts;
+
+typedef struct {
+    int iters;          /* Arnoldi steps taken */
+    double relres;      /* final true relative residual ||h^2 f - A u|| / ||h^2 f|| */
+} helm_info;
+
+typedef struct helm_problem helm_problem;
+
+/* Fill *o with the defaults listed above. */
+void helm_default_opts(helm_opts* o);
+void helm_default_setup_opts(helm_setup_opts* o);
+
+/* Partition the grid and build the coefficient tables (paper Sections 2-3).
+ * n_x, n_y   interior nodes per direction (>= 1); h grid step (> 0);
+ * omega      angular frequency (> 0);
+ * m2         device, n_x*n_y squared slowness values (> 0), copied;
+ * N1, N2     subdomain columns and rows (1 <= N1 <= n_x, 1 <= N2 <= n_y);
+ * xcuts      host, N1+1 increasing node offsets from 0 to n_x (column i1 owns
+ *            x-nodes xcuts[i1-1] .. xcuts[i1]-1, 0-based), or NULL for the
+ *            most even split (larger pieces first); ycuts likewise;
+ * opts       host, or NULL for defaults;
+ * out        host; receives the new handle (NULL on failure).
+ * Synchronises the device once (coefficient upload). */
+helm_status helm_setup(int n_x, int n_y, double h, double omega, const double* m2,
+                       int N1, int N2, const int* xcuts, const int* ycuts,
+                       const helm_setup_opts* opts, helm_problem** out);
+
+/* Factor every subdomain matrix (paper Eq. subPbm; the paper uses a sparse
+ * direct solver, Section 6) as a block tridiagonal LU over its grid rows:
+ * T_1 = D_1, X_r = T_r^{-1}, T_{r+1} = D_{r+1} - X_r, storing all X_r.
+ * Replaces factors of another precision.  Stream-ordered. */
+helm_status precond_factor(helm_problem* p, helm_prec prec, void* stream);
+
+/* z = M^{-1} r for nrhs right-hand sides (device r and z, nrhs*n_x*n_y each,
+ * may not overlap).  M^{-1} approximates A^{-1}: liftings of r on every
+ * subdomain (Eq. subPbmLifting) give the interface right-hand side b, the
+ * sweep `sched` approximates (I - S)^{-1} b (Eq. abstractSys), and local
+ * solves with source r and the resulting incoming data give z.
+ * HELM_ERR_STATE before precond_factor.  Stream-ordered. */
+helm_status precond_apply(helm_problem* p, int sched, const helm_c128* r, helm_c128* z,
+                          int nrhs, void* stream);
+
+/* Au = A u for nrhs fields (device u, Au; the h^2-scaled operator above).
+ * Stream-ordered. */
+helm_status helm_matvec(helm_problem* p, const helm_c128* u, helm_c128* Au, int nrhs, void* stream);
+
+/* Solve A u = h^2 f for nrhs sources by right-preconditioned flexible GMRES
+ * in FP64 (residual, Gram-Schmidt, Hessenberg least squares and update in
+ * FP64; the preconditioner in the factor precision).  f, u device; opts host
+ * (NULL: defaults); info host array of nrhs entries (or NULL).
+ * Returns HELM_ERR_NO_CONVERGENCE (u holds the last iterate, info filled)
+ * when some RHS did not reach tol within maxit.  Synchronises `stream`. */
+helm_status gmres_solve(helm_problem* p, const helm_c128* f, helm_c128* u, int nrhs,
+                        const helm_opts* opts, helm_info* info, void* stream);
+
+/* Misfit J = 1/2 sum_s ||P u_s - d_s||^2 over nsrc sources and its gradient
+ * with respect to m2 by the adjoint-state method:
+ *   A u_s = h^2 f_s,   A conj(lambda_s) = conj(P^T (P u_s - d_s))  (A complex symmetric),
+ *   grad_p = - sum_s Re(conj(lambda_{s,p}) dA_pp/dm2_p u_{s,p}).
+ * The adjoint solves reuse the factors and preconditioner.
+ * f device nsrc*N; rec_idx device nrec flat node indices; d device nsrc*nrec
+ * (RHS-major); misfit host scalar; grad_m2 device N doubles (overwritten);
+ * u_out device nsrc*N or NULL.  Needs precond_factor first.  Synchronises. */
+helm_status misfit_grad(helm_problem* p, const helm_c128* f, int nsrc, const int* rec_idx, int nrec,
+                        const helm_c128* d, const helm_opts* opts, double* misfit, double* grad_m2,
+                        helm_c128* u_out, void* stream);
+
+/* Release the handle and everything it owns (NULL is allowed). */
+helm_status helm_destroy(helm_problem* p);
+
+/* Message describing the last non-OK status returned on this host thread. */
+const char* helm_last_error(void);
+
+/* Host-only query of the sweep schedule (no GPU needed): the number of
+ * sequential sweep steps per application (Section 4: 2(N1+N2-2) for SP;
+ * Section 5: 2 x the longest band, i.e. 2 N1 with two or more bands, for BSP)
+ * and the number of batched stage launches (steps plus the lifting and
+ * reconstruction stages, plus the residual stage of BSP).  steps/stages host. */
+helm_status helm_schedule_info(int N1, int N2, int sched, int* steps, int* stages);
+
+/* Problem sizes of a handle: N = n_x*n_y unknowns, number of subdomains,
+ * 2 N_e interface unknowns (trace points), bytes of the current factors. */
+helm_status helm_problem_info(const helm_problem* p, long long* n_unknowns, int* n_subdomains,
+                              long long* n_trace, long long* factor_bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HELM_H */

@@ -1,0 +1,784 @@
+// C ABI of libhelm: problem setup (partition, the paper's interface
+// numbering, coefficient tables), the sweep schedules as lists of batched
+// stages, the preconditioner driver, FP64 flexible GMRES and the adjoint
+// misfit gradient.  See include/helm.h for the contract of each entry point.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "helm_internal.cuh"
+
+size_t factor_work_elems(int max_mx, size_t elem);
+
+// ------------------------------------------------------------------ errors
+static thread_local std::string g_err;
+void set_error(const std::string& m) { g_err = m; }
+helm_status cuda_status(cudaError_t e, const char* what) {
+    set_error(std::string(what) + ": " + cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? HELM_ERR_OOM : HELM_ERR_CUDA;
+}
+static helm_status arg_error(const std::string& m) {
+    set_error(m);
+    return HELM_ERR_ARG;
+}
+
+// ------------------------------------------------------------ schedule (S1)
+namespace {
+
+struct SubHost {
+    int i1, i2;          // 1-based column, row
+    int diag;            // i1 + i2
+    SubDev dev;
+};
+
+// Block Jacobi bands (Section 5): forward 2+(g-1)N1 <= d <= 2+g N1, backward
+// (1+Ng)-g N1 <= d <= (1+Ng)-(g-1)N1, clipped to [2, Ng+1].
+std::vector<std::pair<int, int>> bands(int N1, int Ng, bool forward) {
+    std::vector<std::pair<int, int>> out;
+    for (int g = 1;; ++g) {
+        int lo, hi;
+        if (forward) { lo = 2 + (g - 1) * N1; hi = lo + N1; }
+        else { hi = (1 + Ng) - (g - 1) * N1; lo = hi - N1; }
+        lo = std::max(lo, 2);
+        hi = std::min(hi, Ng + 1);
+        if (lo > Ng + 1 || hi < 2) break;
+        out.push_back({lo, hi});
+        if ((forward && hi >= Ng + 1) || (!forward && lo <= 2)) break;
+    }
+    return out;
+}
+
+// Stage lists of one application of the volume preconditioner.  `ondiag[d]`
+// lists the subdomains of diagonal d; `all` every subdomain.
+std::vector<StageDesc> build_schedule(int sched, int N1, int N2, const std::vector<std::vector<int>>& ondiag,
+                                      const std::vector<int>& all, bool have_interfaces) {
+    std::vector<StageDesc> st;
+    const int Ng = N1 + N2 - 1;
+    const int ALL = 15, FWD = (1 << SE) | (1 << SN), BWD = (1 << SW) | (1 << SS);
+    auto mk_stage = [](std::vector<int> subs, int src, int in0, int in1, int mask, int dst, int dst2, int base,
+                       int sub, int fin) {
+        StageDesc s;
+        s.subs = std::move(subs);
+        s.src = src; s.in0 = in0; s.in1 = in1; s.mask = mask;
+        s.dst = dst; s.dst2 = dst2; s.base = base; s.sub = sub; s.final_ = fin; s.sub_off = 0;
+        return s;
+    };
+    if (!have_interfaces) {       // one subdomain: M^{-1} = A^{-1}, one solve
+        st.push_back(mk_stage(all, 1, BUF_NONE, BUF_NONE, 0, BUF_NONE, BUF_NONE, BUF_NONE, BUF_NONE, 1));
+        return st;
+    }
+    // liftings w_i (Eq. subPbmLifting): b = outgoing of w, copied into X
+    st.push_back(mk_stage(all, 1, BUF_NONE, BUF_NONE, ALL, BUF_B, BUF_X, BUF_NONE, BUF_NONE, 0));
+    if (sched == HELM_SCHED_SP) {
+        // S_L^{-1} = (I + E_{Ng+1}) ... (I + E_3): step d solves diagonal d-1 into d
+        for (int d = 3; d <= Ng + 1; ++d)
+            st.push_back(mk_stage(ondiag[d - 1], 0, BUF_X, BUF_NONE, FWD, BUF_X, BUF_NONE, BUF_B, BUF_NONE, 0));
+        // S_U^{-1} = (I + F_3) ... (I + F_{Ng+1}): step d solves diagonal d into d-1
+        for (int d = Ng + 1; d >= 3; --d)
+            st.push_back(mk_stage(ondiag[d], 0, BUF_X, BUF_NONE, BWD, BUF_X, BUF_NONE, BUF_X, BUF_NONE, 0));
+        st.push_back(mk_stage(all, 1, BUF_X, BUF_NONE, 0, BUF_NONE, BUF_NONE, BUF_NONE, BUF_NONE, 1));
+        return st;
+    }
+    // BSP: x' = B_L^{-1} b (bands run concurrently; a band's first diagonal
+    // reads the unpropagated b, later ones the propagated x)
+    auto fb = bands(N1, Ng, true);
+    int fsteps = 0;
+    for (auto& b : fb) fsteps = std::max(fsteps, b.second - b.first);
+    for (int s = 1; s <= fsteps; ++s) {
+        std::vector<int> subs;
+        for (auto& b : fb) {
+            const int d = b.first + s - 1;
+            if (d <= b.second - 1) subs.insert(subs.end(), ondiag[d].begin(), ondiag[d].end());
+        }
+        st.push_back(mk_stage(subs, 0, s == 1 ? BUF_B : BUF_X, BUF_NONE, FWD, BUF_X, BUF_NONE, BUF_B, BUF_NONE, 0));
+    }
+    // rho = b - (I - S) x': every subdomain, into B (in place) and Y
+    st.push_back(mk_stage(all, 0, BUF_X, BUF_NONE, ALL, BUF_B, BUF_Y, BUF_B, BUF_X, 0));
+    // y = B_U^{-1} rho
+    auto ub = bands(N1, Ng, false);
+    int bsteps = 0;
+    for (auto& b : ub) bsteps = std::max(bsteps, b.second - b.first);
+    for (int s = 1; s <= bsteps; ++s) {
+        std::vector<int> subs;
+        for (auto& b : ub) {
+            const int d = b.second - s + 1;
+            if (d >= b.first + 1) subs.insert(subs.end(), ondiag[d].begin(), ondiag[d].end());
+        }
+        st.push_back(mk_stage(subs, 0, s == 1 ? BUF_B : BUF_Y, BUF_NONE, BWD, BUF_Y, BUF_NONE, BUF_B, BUF_NONE, 0));
+    }
+    // reconstruction with incoming x = x' + y
+    st.push_back(mk_stage(all, 1, BUF_X, BUF_Y, 0, BUF_NONE, BUF_NONE, BUF_NONE, BUF_NONE, 1));
+    return st;
+}
+
+int sweep_steps(int sched, int N1, int N2) {
+    const int Ng = N1 + N2 - 1;
+    if (sched == HELM_SCHED_SP) return 2 * (Ng - 1);
+    int f = 0, b = 0;
+    for (auto& x : bands(N1, Ng, true)) f = std::max(f, x.second - x.first);
+    for (auto& x : bands(N1, Ng, false)) b = std::max(b, x.second - x.first);
+    return f + b;
+}
+
+template <typename P> cudaError_t dalloc(P*& p, size_t count) {
+    p = nullptr;
+    if (count == 0) return cudaSuccess;
+    return cudaMalloc((void**)&p, count * sizeof(P));
+}
+template <typename P> void dfree(P*& p) {
+    if (p) cudaFree((void*)p);
+    p = nullptr;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ handle
+struct helm_problem {
+    int nx = 0, ny = 0, N1 = 0, N2 = 0;
+    double h = 0, omega = 0;
+    helm_setup_opts sopts{};
+    std::vector<int> xcut, ycut;
+    std::vector<SubHost> subs;
+    std::vector<std::vector<int>> ondiag;
+    std::vector<int> all;
+    int max_mx = 0, max_my = 0;
+    long long ntrace = 0;
+    int nslots = 0;
+    std::vector<StageDesc> sched[2];
+
+    double* d_m2 = nullptr;
+    double2* d_adiag = nullptr;
+    double2* d_dloc = nullptr;
+    SubDev* d_subtab = nullptr;
+    TraceCoef<double2>* d_tc128 = nullptr;
+    TraceCoef<float2>* d_tc64 = nullptr;
+    int* d_stage_subs = nullptr;
+
+    int factored = 0;
+    int prec = HELM_PREC_C128;
+    void* d_X = nullptr;
+    size_t X_bytes = 0;
+
+    // preconditioner workspace
+    int ws_nrhs = 0;
+    void* d_trace[3] = {nullptr, nullptr, nullptr};
+    void* d_yws = nullptr;
+    double* d_pc_norm = nullptr;     // per RHS: ||r||^2, 1/||r||, ||r||
+    double* d_pc_partial = nullptr;
+
+    // Krylov workspace
+    int kw_nrhs = 0, kw_restart = 0;
+    double2 *d_V = nullptr, *d_Z = nullptr, *d_H = nullptr, *d_cs = nullptr, *d_sn = nullptr, *d_g = nullptr;
+    double2 *d_h1 = nullptr, *d_h2 = nullptr, *d_hsum = nullptr, *d_y = nullptr, *d_cpart = nullptr;
+    double *d_rpart = nullptr, *d_rn = nullptr, *d_est = nullptr, *d_invh = nullptr;
+    int *d_active = nullptr, *d_jcount = nullptr;
+    int kw_nblk = 0;
+
+    // adjoint workspace
+    double2 *d_res = nullptr, *d_fadj = nullptr, *d_U = nullptr, *d_L = nullptr;
+    double* d_jpart = nullptr;
+    int aw_nsrc = 0, aw_nrec = 0;
+
+    long long N() const { return (long long)nx * ny; }
+};
+
+static void free_pc_ws(helm_problem* p) {
+    for (auto& b : p->d_trace) dfree(b);
+    dfree(p->d_yws);
+    dfree(p->d_pc_norm);
+    dfree(p->d_pc_partial);
+    p->ws_nrhs = 0;
+}
+static void free_krylov(helm_problem* p) {
+    dfree(p->d_V); dfree(p->d_Z); dfree(p->d_H); dfree(p->d_cs); dfree(p->d_sn); dfree(p->d_g);
+    dfree(p->d_h1); dfree(p->d_h2); dfree(p->d_hsum); dfree(p->d_y); dfree(p->d_cpart);
+    dfree(p->d_rpart); dfree(p->d_rn); dfree(p->d_est); dfree(p->d_invh); dfree(p->d_active); dfree(p->d_jcount);
+    p->kw_nrhs = p->kw_restart = 0;
+}
+static void free_adj(helm_problem* p) {
+    dfree(p->d_res); dfree(p->d_fadj); dfree(p->d_U); dfree(p->d_L); dfree(p->d_jpart);
+    p->aw_nsrc = p->aw_nrec = 0;
+}
+
+static constexpr int kPartialBlocks = 1216;   // 8 per SM on 152 SMs
+
+// ------------------------------------------------------------------- setup
+extern "C" void helm_default_opts(helm_opts* o) {
+    if (!o) return;
+    o->restart = 50;
+    o->maxit = 1000;
+    o->tol = 1e-6;
+    o->x0_given = 0;
+    o->sched = HELM_SCHED_BSP;
+    o->use_graph = 0;
+    o->hist = nullptr;
+}
+extern "C" void helm_default_setup_opts(helm_setup_opts* o) {
+    if (!o) return;
+    o->transmission = HELM_TC_OPTIMIZED;
+    o->tc_scale = 1.5;
+}
+
+extern "C" const char* helm_last_error(void) { return g_err.c_str(); }
+
+extern "C" helm_status helm_schedule_info(int N1, int N2, int sched, int* steps, int* stages) {
+    if (N1 < 1 || N2 < 1 || (sched != HELM_SCHED_BSP && sched != HELM_SCHED_SP))
+        return arg_error("helm_schedule_info: N1, N2 >= 1 and a valid schedule are required");
+    const int Ng = N1 + N2 - 1;
+    std::vector<std::vector<int>> ondiag(Ng + 2);
+    std::vector<int> all;
+    int id = 0;
+    for (int d = 2; d <= Ng + 1; ++d)
+        for (int i1 = 1; i1 <= N1; ++i1) {
+            const int i2 = d - i1;
+            if (i2 >= 1 && i2 <= N2) { ondiag[d].push_back(id); all.push_back(id); ++id; }
+        }
+    const bool inter = N1 * N2 > 1;
+    auto st = build_schedule(sched, N1, N2, ondiag, all, inter);
+    if (steps) *steps = inter ? sweep_steps(sched, N1, N2) : 0;
+    if (stages) *stages = (int)st.size();
+    return HELM_OK;
+}
+
+static std::vector<int> make_cuts(int n, int parts, const int* cuts) {
+    std::vector<int> c(parts + 1);
+    if (cuts) {
+        for (int k = 0; k <= parts; ++k) c[k] = cuts[k];
+    } else {
+        const int q = n / parts, r = n % parts;
+        c[0] = 0;
+        for (int k = 0; k < parts; ++k) c[k + 1] = c[k] + q + (k < r ? 1 : 0);
+    }
+    return c;
+}
+
+extern "C" helm_status helm_setup(int n_x, int n_y, double h, double omega, const double* m2, int N1, int N2,
+                                  const int* xcuts, const int* ycuts, const helm_setup_opts* opts,
+                                  helm_problem** out) {
+    if (!out) return arg_error("helm_setup: out is NULL");
+    *out = nullptr;
+    if (n_x < 1 || n_y < 1) return arg_error("helm_setup: n_x, n_y must be >= 1");
+    if (!(h > 0) || !(omega > 0)) return arg_error("helm_setup: h and omega must be > 0");
+    if (!m2) return arg_error("helm_setup: m2 is NULL");
+    if (N1 < 1 || N2 < 1 || N1 > n_x || N2 > n_y) return arg_error("helm_setup: need 1 <= N1 <= n_x, 1 <= N2 <= n_y");
+    helm_setup_opts so;
+    helm_default_setup_opts(&so);
+    if (opts) so = *opts;
+    if (so.transmission != HELM_TC_OPTIMIZED && so.transmission != HELM_TC_IMPEDANCE)
+        return arg_error("helm_setup: unknown transmission");
+    if (so.transmission == HELM_TC_OPTIMIZED && !(so.tc_scale > 0)) return arg_error("helm_setup: tc_scale must be > 0");
+
+    auto xc = make_cuts(n_x, N1, xcuts), yc = make_cuts(n_y, N2, ycuts);
+    for (int k = 0; k < N1; ++k)
+        if (xc[k + 1] <= xc[k]) return arg_error("helm_setup: xcuts must increase strictly");
+    for (int k = 0; k < N2; ++k)
+        if (yc[k + 1] <= yc[k]) return arg_error("helm_setup: ycuts must increase strictly");
+    if (xc[0] != 0 || xc[N1] != n_x || yc[0] != 0 || yc[N2] != n_y)
+        return arg_error("helm_setup: cuts must run from 0 to n");
+
+    helm_problem* p = new (std::nothrow) helm_problem();
+    if (!p) { set_error("helm_setup: host allocation failed"); return HELM_ERR_OOM; }
+    p->nx = n_x; p->ny = n_y; p->N1 = N1; p->N2 = N2; p->h = h; p->omega = omega; p->sopts = so;
+    p->xcut = xc; p->ycut = yc;
+    const int Ng = N1 + N2 - 1;
+
+    // subdomains in the paper's order on multi-indices (|i|_1, then i1), Section 2
+    std::vector<int> subid(N1 * N2);
+    p->ondiag.assign(Ng + 2, {});
+    for (int d = 2; d <= Ng + 1; ++d)
+        for (int i1 = 1; i1 <= N1; ++i1) {
+            const int i2 = d - i1;
+            if (i2 < 1 || i2 > N2) continue;
+            SubHost s{};
+            s.i1 = i1; s.i2 = i2; s.diag = d;
+            s.dev.x0 = xc[i1 - 1]; s.dev.mx = xc[i1] - xc[i1 - 1];
+            s.dev.y0 = yc[i2 - 1]; s.dev.my = yc[i2] - yc[i2 - 1];
+            for (int k = 0; k < 4; ++k) { s.dev.tin[k] = -1; s.dev.tout[k] = -1; }
+            const int id = (int)p->subs.size();
+            subid[(i2 - 1) * N1 + (i1 - 1)] = id;
+            p->ondiag[d].push_back(id);
+            p->all.push_back(id);
+            p->subs.push_back(s);
+            p->max_mx = std::max(p->max_mx, s.dev.mx);
+            p->max_my = std::max(p->max_my, s.dev.my);
+        }
+    if (p->max_mx > 512) { delete p; return arg_error("helm_setup: subdomains wider than 512 nodes are not supported"); }
+    long long loff = 0;
+    for (auto& s : p->subs) { s.dev.loff = loff; s.dev.yoff = loff; loff += (long long)s.dev.mx * s.dev.my; }
+
+    // interface unknowns (i, j) in the paper's pair order m(i, j) (Section 2)
+    std::vector<int> slot_sub, slot_side, slot_off, slot_len;
+    auto nb_of = [&](const SubHost& s, int side, int& j1, int& j2) {
+        j1 = s.i1 + (side == SE) - (side == SW);
+        j2 = s.i2 + (side == SN) - (side == SS);
+        return j1 >= 1 && j1 <= N1 && j2 >= 1 && j2 <= N2;
+    };
+    long long off = 0;
+    for (int id = 0; id < (int)p->subs.size(); ++id) {
+        auto& s = p->subs[id];
+        std::vector<std::pair<std::pair<int, int>, int>> nbs;   // ((|j|_1, j1), side)
+        for (int side = 0; side < 4; ++side) {
+            int j1, j2;
+            if (nb_of(s, side, j1, j2)) nbs.push_back({{j1 + j2, j1}, side});
+        }
+        std::sort(nbs.begin(), nbs.end());
+        for (auto& e : nbs) {
+            const int side = e.second;
+            const int len = (side == SW || side == SE) ? s.dev.my : s.dev.mx;
+            s.dev.tin[side] = (int)off;
+            slot_sub.push_back(id); slot_side.push_back(side); slot_off.push_back((int)off); slot_len.push_back(len);
+            off += len;
+        }
+    }
+    if (off > (1LL << 30)) { delete p; return arg_error("helm_setup: too many interface unknowns"); }
+    p->ntrace = off;
+    p->nslots = (int)slot_sub.size();
+    for (auto& s : p->subs)
+        for (int side = 0; side < 4; ++side) {
+            int j1, j2;
+            if (!nb_of(s, side, j1, j2)) continue;
+            const int opp = side ^ 1;           // W<->E, S<->N
+            s.dev.tout[side] = p->subs[subid[(j2 - 1) * N1 + (j1 - 1)]].dev.tin[opp];
+        }
+
+    // stage lists and their subdomain arrays
+    std::vector<int> all_stage_subs;
+    for (int sc = 0; sc < 2; ++sc) {
+        p->sched[sc] = build_schedule(sc, N1, N2, p->ondiag, p->all, p->nslots > 0);
+        for (auto& st : p->sched[sc]) {
+            st.sub_off = (int)all_stage_subs.size();
+            all_stage_subs.insert(all_stage_subs.end(), st.subs.begin(), st.subs.end());
+        }
+    }
+
+    // device tables
+    helm_status status = HELM_OK;
+    int *d_xcut = nullptr, *d_ycut = nullptr, *d_subid = nullptr;
+    int *d_ssub = nullptr, *d_sside = nullptr, *d_soff = nullptr, *d_slen = nullptr;
+    const long long N = p->N();
+    auto fail = [&](cudaError_t e, const char* w) {
+        status = cuda_status(e, w);
+        return status;
+    };
+    do {
+        cudaError_t e;
+        if ((e = dalloc(p->d_m2, N)) != cudaSuccess) { fail(e, "alloc m2"); break; }
+        if ((e = cudaMemcpy(p->d_m2, m2, N * sizeof(double), cudaMemcpyDefault)) != cudaSuccess) { fail(e, "copy m2"); break; }
+        if ((e = dalloc(p->d_adiag, N)) != cudaSuccess) { fail(e, "alloc adiag"); break; }
+        if ((e = dalloc(p->d_dloc, N)) != cudaSuccess) { fail(e, "alloc dloc"); break; }
+        if ((e = dalloc(p->d_subtab, p->subs.size())) != cudaSuccess) { fail(e, "alloc subtab"); break; }
+        std::vector<SubDev> tab;
+        for (auto& s : p->subs) tab.push_back(s.dev);
+        if ((e = cudaMemcpy(p->d_subtab, tab.data(), tab.size() * sizeof(SubDev), cudaMemcpyHostToDevice)) != cudaSuccess) { fail(e, "copy subtab"); break; }
+        if ((e = dalloc(d_xcut, xc.size())) || (e = dalloc(d_ycut, yc.size())) || (e = dalloc(d_subid, subid.size()))) { fail(e, "alloc cuts"); break; }
+        cudaMemcpy(d_xcut, xc.data(), xc.size() * sizeof(int), cudaMemcpyHostToDevice);
+        cudaMemcpy(d_ycut, yc.data(), yc.size() * sizeof(int), cudaMemcpyHostToDevice);
+        cudaMemcpy(d_subid, subid.data(), subid.size() * sizeof(int), cudaMemcpyHostToDevice);
+        launch_setup_coeffs(p->d_m2, n_x, n_y, h, omega, d_xcut, d_ycut, N1, N2, d_subid, so.transmission, so.tc_scale,
+                            p->d_adiag, p->d_dloc, p->d_subtab, 0);
+        if (p->nslots > 0) {
+            if ((e = dalloc(p->d_tc128, p->ntrace)) || (e = dalloc(p->d_tc64, p->ntrace))) { fail(e, "alloc trace coefficients"); break; }
+            if ((e = dalloc(d_ssub, p->nslots)) || (e = dalloc(d_sside, p->nslots)) || (e = dalloc(d_soff, p->nslots)) ||
+                (e = dalloc(d_slen, p->nslots))) { fail(e, "alloc slots"); break; }
+            cudaMemcpy(d_ssub, slot_sub.data(), p->nslots * sizeof(int), cudaMemcpyHostToDevice);
+            cudaMemcpy(d_sside, slot_side.data(), p->nslots * sizeof(int), cudaMemcpyHostToDevice);
+            cudaMemcpy(d_soff, slot_off.data(), p->nslots * sizeof(int), cudaMemcpyHostToDevice);
+            cudaMemcpy(d_slen, slot_len.data(), p->nslots * sizeof(int), cudaMemcpyHostToDevice);
+            launch_trace_coeffs(p->d_m2, n_x, h, omega, so.transmission, so.tc_scale, d_ssub, d_sside, d_soff, d_slen,
+                                p->nslots, p->d_subtab, p->d_tc128, p->d_tc64, 0);
+        }
+        if ((e = dalloc(p->d_stage_subs, all_stage_subs.size())) != cudaSuccess) { fail(e, "alloc stage lists"); break; }
+        cudaMemcpy(p->d_stage_subs, all_stage_subs.data(), all_stage_subs.size() * sizeof(int), cudaMemcpyHostToDevice);
+        if ((e = cudaDeviceSynchronize()) != cudaSuccess) { fail(e, "setup kernels"); break; }
+    } while (0);
+    dfree(d_xcut); dfree(d_ycut); dfree(d_subid); dfree(d_ssub); dfree(d_sside); dfree(d_soff); dfree(d_slen);
+    if (status != HELM_OK) { helm_destroy(p); return status; }
+    *out = p;
+    return HELM_OK;
+}
+
+extern "C" helm_status helm_destroy(helm_problem* p) {
+    if (!p) return HELM_OK;
+    free_pc_ws(p);
+    free_krylov(p);
+    free_adj(p);
+    dfree(p->d_m2); dfree(p->d_adiag); dfree(p->d_dloc); dfree(p->d_subtab);
+    dfree(p->d_tc128); dfree(p->d_tc64); dfree(p->d_stage_subs);
+    if (p->d_X) cudaFree(p->d_X);
+    delete p;
+    return HELM_OK;
+}
+
+extern "C" helm_status helm_problem_info(const helm_problem* p, long long* n_unknowns, int* n_subdomains,
+                                         long long* n_trace, long long* factor_bytes) {
+    if (!p) return arg_error("helm_problem_info: NULL handle");
+    if (n_unknowns) *n_unknowns = p->N();
+    if (n_subdomains) *n_subdomains = (int)p->subs.size();
+    if (n_trace) *n_trace = p->ntrace;
+    if (factor_bytes) *factor_bytes = (long long)p->X_bytes;
+    return HELM_OK;
+}
+
+// ----------------------------------------------------------------- factor
+extern "C" helm_status precond_factor(helm_problem* p, helm_prec prec, void* stream) {
+    if (!p) return arg_error("precond_factor: NULL handle");
+    if (prec != HELM_PREC_C128 && prec != HELM_PREC_C64) return arg_error("precond_factor: unknown precision");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t elem = prec == HELM_PREC_C64 ? sizeof(float2) : sizeof(double2);
+    // layout of the stored X_r: per subdomain my blocks of mx x ldx (ldx even for complex64,
+    // so that every block and row chunk starts on a 16-byte boundary)
+    long long xoff = 0;
+    std::vector<SubDev> tab;
+    for (auto& s : p->subs) {
+        s.dev.ldx = prec == HELM_PREC_C64 ? ((s.dev.mx + 1) & ~1) : s.dev.mx;
+        s.dev.xoff = xoff;
+        xoff += (long long)s.dev.my * s.dev.mx * s.dev.ldx;
+        tab.push_back(s.dev);
+    }
+    const size_t bytes = (size_t)xoff * elem;
+    HELM_CUDA_TRY(cudaStreamSynchronize(st));
+    if (p->d_X) { cudaFree(p->d_X); p->d_X = nullptr; p->X_bytes = 0; p->factored = 0; }
+    cudaError_t e = cudaMalloc(&p->d_X, bytes);
+    if (e != cudaSuccess) { p->d_X = nullptr; return cuda_status(e, "precond_factor: allocating the factors"); }
+    p->X_bytes = bytes;
+    HELM_CUDA_TRY(cudaMemcpy(p->d_subtab, tab.data(), tab.size() * sizeof(SubDev), cudaMemcpyHostToDevice));
+    const size_t wel = factor_work_elems(p->max_mx, elem);
+    void* work = nullptr;
+    int* info = nullptr;
+    if (wel) {
+        e = cudaMalloc(&work, wel * elem * p->subs.size());
+        if (e != cudaSuccess) return cuda_status(e, "precond_factor: allocating the factor workspace");
+    }
+    e = cudaMalloc(&info, p->subs.size() * sizeof(int));
+    if (e != cudaSuccess) { if (work) cudaFree(work); return cuda_status(e, "precond_factor: alloc info"); }
+    if (prec == HELM_PREC_C64)
+        e = launch_factor<float>(p->d_subtab, (int)p->subs.size(), p->max_mx, p->d_dloc, (float2*)p->d_X, (float2*)work,
+                                 wel, info, st);
+    else
+        e = launch_factor<double>(p->d_subtab, (int)p->subs.size(), p->max_mx, p->d_dloc, (double2*)p->d_X,
+                                  (double2*)work, wel, info, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    std::vector<int> hinfo(p->subs.size());
+    if (e == cudaSuccess) e = cudaMemcpy(hinfo.data(), info, hinfo.size() * sizeof(int), cudaMemcpyDeviceToHost);
+    if (work) cudaFree(work);
+    cudaFree(info);
+    if (e != cudaSuccess) return cuda_status(e, "precond_factor: factor kernel");
+    for (size_t k = 0; k < hinfo.size(); ++k)
+        if (hinfo[k]) {
+            char buf[160];
+            snprintf(buf, sizeof buf, "precond_factor: zero pivot in subdomain %zu (row %d, column %d)", k,
+                     (hinfo[k] - 1) / p->subs[k].dev.mx, (hinfo[k] - 1) % p->subs[k].dev.mx);
+            set_error(buf);
+            return HELM_ERR_ARG;
+        }
+    p->prec = prec;
+    p->factored = 1;
+    // the workspace depends on the precision
+    free_pc_ws(p);
+    return HELM_OK;
+}
+
+// ------------------------------------------------------------ preconditioner
+static helm_status ensure_pc_ws(helm_problem* p, int nrhs) {
+    if (p->ws_nrhs >= nrhs) return HELM_OK;
+    free_pc_ws(p);
+    const size_t elem = p->prec == HELM_PREC_C64 ? sizeof(float2) : sizeof(double2);
+    cudaError_t e = cudaSuccess;
+    for (int b = 0; b < 3 && e == cudaSuccess && p->ntrace > 0; ++b)
+        e = cudaMalloc(&p->d_trace[b], (size_t)p->ntrace * nrhs * elem);
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_yws, (size_t)p->N() * nrhs * elem);
+    if (e == cudaSuccess) e = dalloc(p->d_pc_norm, 3 * (size_t)nrhs);
+    if (e == cudaSuccess) e = dalloc(p->d_pc_partial, (size_t)kPartialBlocks * nrhs);
+    if (e != cudaSuccess) { free_pc_ws(p); return cuda_status(e, "allocating the preconditioner workspace"); }
+    p->ws_nrhs = nrhs;
+    return HELM_OK;
+}
+
+template <typename R>
+static helm_status run_precond_t(helm_problem* p, int sched, const double2* r, double2* z, int nrhs, cudaStream_t st) {
+    using T = Cx<R>;
+    const double* rinv = nullptr;
+    const double* rsc = nullptr;
+    if (sizeof(R) == 4) {
+        // scale each right-hand side to unit 2-norm before rounding to complex64
+        launch_norm2_partial(r, p->N(), nrhs, p->N(), p->d_pc_partial, kPartialBlocks, st);
+        launch_reduce_rows(p->d_pc_partial, kPartialBlocks, nrhs, p->d_pc_norm, 0, st);
+        launch_scale_from_norm(p->d_pc_norm, p->d_pc_norm + nrhs, p->d_pc_norm + 2 * nrhs, nrhs, st);
+        rinv = p->d_pc_norm + nrhs;
+        rsc = p->d_pc_norm + 2 * nrhs;
+    }
+    T* buf[3] = {(T*)p->d_trace[0], (T*)p->d_trace[1], (T*)p->d_trace[2]};
+    auto B = [&](int id) -> T* { return id < 0 ? nullptr : buf[id]; };
+    for (const StageDesc& sd : p->sched[sched]) {
+        StageArgs<R> a{};
+        a.subtab = p->d_subtab;
+        a.subs = p->d_stage_subs + sd.sub_off;
+        a.nx = p->nx; a.ny = p->ny; a.nrhs = nrhs;
+        a.ntrace = p->ntrace;
+        a.wstride = p->N();
+        a.X = (const T*)p->d_X;
+        a.tc = sizeof(R) == 4 ? (const TraceCoef<T>*)p->d_tc64 : (const TraceCoef<T>*)p->d_tc128;
+        a.src = sd.src;
+        a.r = r;
+        a.rscale = rinv;
+        a.gin0 = B(sd.in0); a.gin1 = B(sd.in1);
+        a.mask = sd.mask;
+        a.dst = B(sd.dst); a.dst2 = B(sd.dst2); a.base = B(sd.base); a.sub = B(sd.sub);
+        a.z = sd.final_ ? z : nullptr;
+        a.zscale = rsc;
+        a.yws = (T*)p->d_yws;
+        cudaError_t e = launch_stage<R>(a, (int)sd.subs.size(), p->max_mx, st);
+        if (e != cudaSuccess) return cuda_status(e, "stage launch");
+    }
+    return HELM_OK;
+}
+
+static helm_status run_precond(helm_problem* p, int sched, const double2* r, double2* z, int nrhs, cudaStream_t st) {
+    helm_status s = ensure_pc_ws(p, nrhs);
+    if (s != HELM_OK) return s;
+    return p->prec == HELM_PREC_C64 ? run_precond_t<float>(p, sched, r, z, nrhs, st)
+                                    : run_precond_t<double>(p, sched, r, z, nrhs, st);
+}
+
+extern "C" helm_status precond_apply(helm_problem* p, int sched, const helm_c128* r, helm_c128* z, int nrhs,
+                                     void* stream) {
+    if (!p) return arg_error("precond_apply: NULL handle");
+    if (!p->factored) { set_error("precond_apply: call precond_factor first"); return HELM_ERR_STATE; }
+    if (sched != HELM_SCHED_BSP && sched != HELM_SCHED_SP) return arg_error("precond_apply: unknown schedule");
+    if (nrhs < 0) return arg_error("precond_apply: nrhs < 0");
+    if (nrhs == 0) return HELM_OK;
+    if (!r || !z) return arg_error("precond_apply: NULL array");
+    return run_precond(p, sched, (const double2*)r, (double2*)z, nrhs, (cudaStream_t)stream);
+}
+
+extern "C" helm_status helm_matvec(helm_problem* p, const helm_c128* u, helm_c128* Au, int nrhs, void* stream) {
+    if (!p) return arg_error("helm_matvec: NULL handle");
+    if (nrhs < 0) return arg_error("helm_matvec: nrhs < 0");
+    if (nrhs == 0) return HELM_OK;
+    if (!u || !Au) return arg_error("helm_matvec: NULL array");
+    launch_matvec(p->d_adiag, p->nx, p->ny, (const double2*)u, (double2*)Au, nrhs, (cudaStream_t)stream);
+    HELM_CUDA_TRY(cudaGetLastError());
+    return HELM_OK;
+}
+
+// ------------------------------------------------------------------ FGMRES
+static helm_status ensure_krylov(helm_problem* p, int nrhs, int m) {
+    if (p->kw_nrhs >= nrhs && p->kw_restart >= m) return HELM_OK;
+    free_krylov(p);
+    const long long N = p->N();
+    const int nb = kPartialBlocks;
+    cudaError_t e = cudaSuccess;
+    auto chk = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
+    chk(dalloc(p->d_V, (size_t)(m + 1) * nrhs * N));
+    chk(dalloc(p->d_Z, (size_t)m * nrhs * N));
+    chk(dalloc(p->d_H, (size_t)nrhs * (m + 1) * m));
+    chk(dalloc(p->d_cs, (size_t)nrhs * (m + 1)));
+    chk(dalloc(p->d_sn, (size_t)nrhs * (m + 1)));
+    chk(dalloc(p->d_g, (size_t)nrhs * (m + 1)));
+    chk(dalloc(p->d_h1, (size_t)nrhs * (m + 1)));
+    chk(dalloc(p->d_h2, (size_t)nrhs * (m + 1)));
+    chk(dalloc(p->d_hsum, (size_t)nrhs * (m + 1)));
+    chk(dalloc(p->d_y, (size_t)nrhs * (m + 1)));
+    chk(dalloc(p->d_cpart, (size_t)nb * nrhs * (m + 1)));
+    chk(dalloc(p->d_rpart, (size_t)nb * nrhs));
+    chk(dalloc(p->d_rn, (size_t)2 * nrhs));
+    chk(dalloc(p->d_est, (size_t)nrhs));
+    chk(dalloc(p->d_invh, (size_t)nrhs));
+    chk(dalloc(p->d_active, (size_t)nrhs));
+    chk(dalloc(p->d_jcount, (size_t)nrhs));
+    if (e != cudaSuccess) { free_krylov(p); return cuda_status(e, "allocating the Krylov workspace"); }
+    p->kw_nrhs = nrhs;
+    p->kw_restart = m;
+    p->kw_nblk = nb;
+    return HELM_OK;
+}
+
+__global__ void add_cols_kernel(const double2* a, const double2* b, double2* c, int n, int nrhs, int ld) {
+    int k = blockIdx.x, i = threadIdx.x;
+    for (; i < n; i += blockDim.x) {
+        double2 x = a[k * ld + i], y = b[k * ld + i];
+        c[k * ld + i] = make_double2(x.x + y.x, x.y + y.y);
+    }
+}
+
+static helm_status gmres_impl(helm_problem* p, const double2* f, double2* u, int nrhs, const helm_opts& o,
+                              helm_info* info, cudaStream_t st) {
+    const long long N = p->N();
+    const int m = o.restart;
+    helm_status s = ensure_krylov(p, nrhs, m);
+    if (s != HELM_OK) return s;
+    s = ensure_pc_ws(p, nrhs);
+    if (s != HELM_OK) return s;
+    const int nb = p->kw_nblk;
+    const long long vsk = (long long)nrhs * N;    // V_j of RHS k at d_V + j*vsk + k*N
+    const double h2 = p->h * p->h;
+    const int ld = m + 1;
+    if (!o.x0_given) HELM_CUDA_TRY(cudaMemsetAsync(u, 0, (size_t)nrhs * N * sizeof(double2), st));
+
+    // ||h^2 f||
+    std::vector<double> bnorm(nrhs), rn(nrhs), est(nrhs);
+    launch_norm2_partial(f, N, nrhs, N, p->d_rpart, nb, st);
+    launch_reduce_rows(p->d_rpart, nb, nrhs, p->d_rn, 1, st);
+    HELM_CUDA_TRY(cudaMemcpyAsync(bnorm.data(), p->d_rn, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
+    HELM_CUDA_TRY(cudaStreamSynchronize(st));
+    for (auto& b : bnorm) b *= h2;
+
+    std::vector<int> iters(nrhs, 0), done(nrhs, 0), active(nrhs, 0), jcount(nrhs, 0);
+    std::vector<double> relres(nrhs, 0.0);
+    for (int k = 0; k < nrhs; ++k) done[k] = bnorm[k] == 0.0;
+
+    while (true) {
+        // r = h^2 f - A u into V_0, beta = ||r||
+        launch_residual(p->d_adiag, p->nx, p->ny, f, h2, u, p->d_V, nrhs, nullptr, p->d_rpart, nb, st);
+        launch_reduce_rows(p->d_rpart, nb, nrhs, p->d_rn, 1, st);
+        HELM_CUDA_TRY(cudaMemcpyAsync(rn.data(), p->d_rn, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
+        HELM_CUDA_TRY(cudaStreamSynchronize(st));
+        bool any = false;
+        for (int k = 0; k < nrhs; ++k) {
+            relres[k] = bnorm[k] > 0 ? rn[k] / bnorm[k] : 0.0;
+            if (relres[k] <= o.tol || iters[k] >= o.maxit) done[k] = 1;
+            active[k] = !done[k];
+            any |= active[k] != 0;
+            jcount[k] = 0;
+        }
+        if (!any) break;
+        HELM_CUDA_TRY(cudaMemcpyAsync(p->d_active, active.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, st));
+        // g = beta e_1, V_0 = r / beta
+        {
+            std::vector<double2> g0((size_t)nrhs * ld, make_double2(0, 0));
+            std::vector<double> inv(nrhs);
+            for (int k = 0; k < nrhs; ++k) {
+                g0[(size_t)k * ld] = make_double2(rn[k], 0.0);
+                inv[k] = rn[k] > 0 ? 1.0 / rn[k] : 0.0;
+            }
+            HELM_CUDA_TRY(cudaMemcpyAsync(p->d_g, g0.data(), g0.size() * sizeof(double2), cudaMemcpyHostToDevice, st));
+            HELM_CUDA_TRY(cudaMemcpyAsync(p->d_invh, inv.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, st));
+            launch_scale_vec(p->d_V, N, p->d_V, N, p->d_invh, N, nrhs, p->d_active, st);
+            HELM_CUDA_TRY(cudaStreamSynchronize(st));    // host vectors above go out of scope
+        }
+        for (int j = 0; j < m; ++j) {
+            double2* Vj = p->d_V + (long long)j * vsk;
+            double2* Vn = p->d_V + (long long)(j + 1) * vsk;
+            double2* Zj = p->d_Z + (long long)j * vsk;
+            // z_j = M^{-1} v_j ; w = A z_j
+            s = run_precond(p, o.sched, Vj, Zj, nrhs, st);
+            if (s != HELM_OK) return s;
+            launch_matvec(p->d_adiag, p->nx, p->ny, Zj, Vn, nrhs, st);
+            // classical Gram-Schmidt, twice
+            launch_mdot(p->d_V, vsk, N, j + 1, Vn, N, N, nrhs, p->d_active, p->d_cpart, nb, st);
+            launch_reduce_cpartials(p->d_cpart, nb, j + 1, p->d_h1, ld, nrhs, st);
+            launch_mupdate(p->d_V, vsk, N, j + 1, nullptr, p->d_h1, ld, -1.0, Vn, N, N, nrhs, p->d_active, nullptr, nb, st);
+            launch_mdot(p->d_V, vsk, N, j + 1, Vn, N, N, nrhs, p->d_active, p->d_cpart, nb, st);
+            launch_reduce_cpartials(p->d_cpart, nb, j + 1, p->d_h2, ld, nrhs, st);
+            launch_mupdate(p->d_V, vsk, N, j + 1, nullptr, p->d_h2, ld, -1.0, Vn, N, N, nrhs, p->d_active, p->d_rpart, nb, st);
+            launch_reduce_rows(p->d_rpart, nb, nrhs, p->d_rn, 1, st);
+            add_cols_kernel<<<nrhs, 128, 0, st>>>(p->d_h1, p->d_h2, p->d_hsum, j + 1, nrhs, ld);
+            launch_hessenberg_step(p->d_H, ld, (long long)ld * m, p->d_cs, p->d_sn, p->d_g, ld, p->d_hsum, ld, p->d_rn, j,
+                                   nrhs, p->d_active, p->d_est, p->d_invh, st);
+            launch_scale_vec(Vn, N, Vn, N, p->d_invh, N, nrhs, p->d_active, st);
+            HELM_CUDA_TRY(cudaGetLastError());
+            HELM_CUDA_TRY(cudaMemcpyAsync(est.data(), p->d_est, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
+            HELM_CUDA_TRY(cudaStreamSynchronize(st));
+            bool still = false;
+            for (int k = 0; k < nrhs; ++k) {
+                if (!active[k]) continue;
+                if (o.hist && iters[k] < o.maxit) o.hist[(size_t)k * o.maxit + iters[k]] = est[k] / bnorm[k];
+                ++iters[k];
+                jcount[k] = j + 1;
+                if (est[k] <= o.tol * bnorm[k] || iters[k] >= o.maxit || !std::isfinite(est[k])) active[k] = 0;
+                still |= active[k] != 0;
+            }
+            if (!still) break;
+            HELM_CUDA_TRY(cudaMemcpyAsync(p->d_active, active.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, st));
+            HELM_CUDA_TRY(cudaStreamSynchronize(st));
+        }
+        // u += Z y with y = R^{-1} g
+        HELM_CUDA_TRY(cudaMemcpyAsync(p->d_jcount, jcount.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, st));
+        launch_hessenberg_solve(p->d_H, ld, (long long)ld * m, p->d_g, ld, p->d_jcount, p->d_y, ld, nrhs, st);
+        launch_mupdate(p->d_Z, vsk, N, m, p->d_jcount, p->d_y, ld, 1.0, u, N, N, nrhs, nullptr, nullptr, nb, st);
+        HELM_CUDA_TRY(cudaGetLastError());
+        HELM_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    bool ok = true;
+    for (int k = 0; k < nrhs; ++k) {
+        if (info) { info[k].iters = iters[k]; info[k].relres = relres[k]; }
+        if (relres[k] > o.tol) ok = false;
+    }
+    if (!ok) {
+        set_error("gmres_solve: tolerance not reached within maxit");
+        return HELM_ERR_NO_CONVERGENCE;
+    }
+    return HELM_OK;
+}
+
+extern "C" helm_status gmres_solve(helm_problem* p, const helm_c128* f, helm_c128* u, int nrhs, const helm_opts* opts,
+                                   helm_info* info, void* stream) {
+    if (!p) return arg_error("gmres_solve: NULL handle");
+    if (!p->factored) { set_error("gmres_solve: call precond_factor first"); return HELM_ERR_STATE; }
+    if (nrhs < 0) return arg_error("gmres_solve: nrhs < 0");
+    if (nrhs == 0) return HELM_OK;
+    if (!f || !u) return arg_error("gmres_solve: NULL array");
+    helm_opts o;
+    helm_default_opts(&o);
+    if (opts) o = *opts;
+    if (o.restart < 1 || o.restart > 500) return arg_error("gmres_solve: restart must be in 1..500");
+    if (o.maxit < 1) return arg_error("gmres_solve: maxit must be >= 1");
+    if (!(o.tol > 0)) return arg_error("gmres_solve: tol must be > 0");
+    if (o.sched != HELM_SCHED_BSP && o.sched != HELM_SCHED_SP) return arg_error("gmres_solve: unknown schedule");
+    return gmres_impl(p, (const double2*)f, (double2*)u, nrhs, o, info, (cudaStream_t)stream);
+}
+
+// ----------------------------------------------------------------- adjoint
+extern "C" helm_status misfit_grad(helm_problem* p, const helm_c128* f, int nsrc, const int* rec_idx, int nrec,
+                                   const helm_c128* d, const helm_opts* opts, double* misfit, double* grad_m2,
+                                   helm_c128* u_out, void* stream) {
+    if (!p) return arg_error("misfit_grad: NULL handle");
+    if (!p->factored) { set_error("misfit_grad: call precond_factor first"); return HELM_ERR_STATE; }
+    if (nsrc < 1 || nrec < 1) return arg_error("misfit_grad: nsrc and nrec must be >= 1");
+    if (!f || !rec_idx || !d || !misfit || !grad_m2) return arg_error("misfit_grad: NULL array");
+    cudaStream_t st = (cudaStream_t)stream;
+    const long long N = p->N();
+    // receivers must be valid nodes
+    {
+        std::vector<int> r(nrec);
+        HELM_CUDA_TRY(cudaMemcpy(r.data(), rec_idx, nrec * sizeof(int), cudaMemcpyDefault));
+        for (int v : r)
+            if (v < 0 || v >= N) return arg_error("misfit_grad: receiver index out of range");
+    }
+    if (p->aw_nsrc < nsrc || p->aw_nrec < nrec) {
+        free_adj(p);
+        cudaError_t e = cudaSuccess;
+        auto chk = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
+        chk(dalloc(p->d_res, (size_t)nsrc * nrec));
+        chk(dalloc(p->d_fadj, (size_t)nsrc * N));
+        chk(dalloc(p->d_U, (size_t)nsrc * N));
+        chk(dalloc(p->d_L, (size_t)nsrc * N));
+        chk(dalloc(p->d_jpart, (size_t)nsrc));
+        if (e != cudaSuccess) { free_adj(p); return cuda_status(e, "allocating the adjoint workspace"); }
+        p->aw_nsrc = nsrc;
+        p->aw_nrec = nrec;
+    }
+    helm_opts o;
+    helm_default_opts(&o);
+    if (opts) o = *opts;
+    o.x0_given = 0;
+    std::vector<helm_info> inf(nsrc);
+    double2* U = u_out ? (double2*)u_out : p->d_U;
+    helm_status s = gmres_solve(p, f, (helm_c128*)U, nsrc, &o, inf.data(), stream);
+    if (s != HELM_OK) return s;
+    launch_receiver_residual(U, N, rec_idx, nrec, (const double2*)d, nsrc, p->d_res, p->d_jpart, st);
+    HELM_CUDA_TRY(cudaMemsetAsync(p->d_fadj, 0, (size_t)nsrc * N * sizeof(double2), st));
+    launch_adjoint_rhs(p->d_res, rec_idx, nrec, nsrc, N, 1.0 / (p->h * p->h), p->d_fadj, st);
+    s = gmres_solve(p, (helm_c128*)p->d_fadj, (helm_c128*)p->d_L, nsrc, &o, inf.data(), stream);
+    if (s != HELM_OK) return s;
+    launch_gradient(U, p->d_L, p->d_m2, p->nx, p->ny, p->h, p->omega, nsrc, grad_m2, st);
+    HELM_CUDA_TRY(cudaGetLastError());
+    launch_reduce_rows(p->d_jpart, nsrc, 1, p->d_rn, 0, st);
+    HELM_CUDA_TRY(cudaMemcpyAsync(misfit, p->d_rn, sizeof(double), cudaMemcpyDeviceToHost, st));
+    HELM_CUDA_TRY(cudaStreamSynchronize(st));
+    return HELM_OK;
+}

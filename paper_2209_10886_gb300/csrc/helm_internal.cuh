@@ -1,0 +1,171 @@
+// Internal declarations shared by the CUDA translation units of libhelm.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "helm.h"
+
+// ----------------------------------------------------------------- complex
+// float2 / double2 carry complex64 / complex128 values (re, im).
+template <typename R> struct CplxOf;
+template <> struct CplxOf<float> { using T = float2; };
+template <> struct CplxOf<double> { using T = double2; };
+template <typename R> using Cx = typename CplxOf<R>::T;
+
+__host__ __device__ __forceinline__ float2 mk(float a, float b) { return make_float2(a, b); }
+__host__ __device__ __forceinline__ double2 mk(double a, double b) { return make_double2(a, b); }
+template <typename T> __host__ __device__ __forceinline__ T czero();
+template <> __host__ __device__ __forceinline__ float2 czero<float2>() { return make_float2(0.f, 0.f); }
+template <> __host__ __device__ __forceinline__ double2 czero<double2>() { return make_double2(0.0, 0.0); }
+
+template <typename T> __host__ __device__ __forceinline__ T cadd(T a, T b) { return mk(a.x + b.x, a.y + b.y); }
+template <typename T> __host__ __device__ __forceinline__ T csub(T a, T b) { return mk(a.x - b.x, a.y - b.y); }
+template <typename T> __host__ __device__ __forceinline__ T cmul(T a, T b) {
+    return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// acc + a*b
+template <typename T> __host__ __device__ __forceinline__ T cfma(T a, T b, T acc) {
+    return mk(fma(a.x, b.x, fma(-a.y, b.y, acc.x)), fma(a.x, b.y, fma(a.y, b.x, acc.y)));
+}
+// acc + conj(a)*b
+template <typename T> __host__ __device__ __forceinline__ T cfmaconj(T a, T b, T acc) {
+    return mk(fma(a.x, b.x, fma(a.y, b.y, acc.x)), fma(a.x, b.y, fma(-a.y, b.x, acc.y)));
+}
+template <typename T, typename S> __host__ __device__ __forceinline__ T cscale(T a, S s) { return mk(a.x * s, a.y * s); }
+template <typename T> __host__ __device__ __forceinline__ auto cabs2(T a) { return a.x * a.x + a.y * a.y; }
+__device__ __forceinline__ float2 to_c64(double2 a) { return make_float2((float)a.x, (float)a.y); }
+__device__ __forceinline__ double2 to_c128(float2 a) { return make_double2((double)a.x, (double)a.y); }
+__device__ __forceinline__ double2 to_c128(double2 a) { return a; }
+template <typename T> __device__ __forceinline__ T from_c128(double2 a);
+template <> __device__ __forceinline__ float2 from_c128<float2>(double2 a) { return to_c64(a); }
+template <> __device__ __forceinline__ double2 from_c128<double2>(double2 a) { return a; }
+
+// complex division a/b in double (setup-time only)
+__host__ __device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
+    double d = b.x * b.x + b.y * b.y;
+    return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+
+// ------------------------------------------------------------------ tables
+enum Side { SW = 0, SE = 1, SS = 2, SN = 3 };   // neighbour direction: west, east, south, north
+
+// One subdomain as the kernels see it.
+struct SubDev {
+    int x0, y0, mx, my;        // node box origin and size (0-based global nodes)
+    int ldx;                   // leading dimension of each stored X_r (elements)
+    int tin[4];                // start of the incoming slot (this, neighbour) in the trace buffer, -1: outer side
+    int tout[4];               // start of the slot (neighbour, this) that receives this subdomain's outgoing data
+    long long xoff;            // element offset of X_1 of this subdomain in the factor array
+    long long yoff;            // element offset of this subdomain's block in the solve workspace (per RHS)
+    long long loff;            // offset of the node block in the local-diagonal array
+};
+
+// Trace-point coefficients of one interface edge point (beta_e = T_e h / 2):
+//   cin = 1/(1-beta)                (incoming data -> local right-hand side)
+//   ca  = -(1+beta)/(1-beta)        (outgoing data: G_out = ca*G_in + cb*u_p)
+//   cb  = -4 beta/(1-beta)
+template <typename T> struct TraceCoef { T cin, ca, cb; };
+
+// Interface-buffer identifiers used by the stage lists.
+enum Buf { BUF_NONE = -1, BUF_B = 0, BUF_X = 1, BUF_Y = 2 };
+
+struct StageDesc {
+    std::vector<int> subs;     // subdomains solved in this stage
+    int src;                   // 1: volume source r_i, 0: zero source
+    int in0, in1;              // incoming data = in0 (+ in1), Buf ids
+    int mask;                  // bit s set: emit outgoing data toward side s
+    int dst, dst2, base, sub;  // dst[slot] = base[slot] - sub[slot] + G_out (also into dst2)
+    int final_;                // 1: write the volume solution into z
+    int sub_off;               // offset of `subs` in the device stage-list array
+};
+
+// launch parameters of the fused stage kernel (passed by value)
+template <typename R> struct StageArgs {
+    using T = Cx<R>;
+    const SubDev* subtab;
+    const int* subs;           // active subdomain ids for this stage
+    int nx, ny;                // global grid
+    int nrhs;                  // right-hand sides in the batch
+    long long ntrace;          // trace points per RHS
+    long long wstride;         // solve-workspace elements per RHS
+    const T* X;                // factors
+    const TraceCoef<T>* tc;    // per trace point
+    int src;
+    const double2* r;          // source fields (c128), RHS stride nx*ny
+    const double* rscale;      // per-RHS factor applied to r (1/||r|| for c64), or null = 1
+    const T* gin0; const T* gin1;
+    int mask;
+    T* dst; T* dst2; const T* base; const T* sub;
+    double2* z;                // volume output (final stage) or null
+    const double* zscale;      // per-RHS factor applied to the output, or null = 1
+    T* yws;                    // solve workspace
+};
+
+// ------------------------------------------------------------ error helpers
+void set_error(const std::string& msg);
+helm_status cuda_status(cudaError_t e, const char* what);
+
+#define HELM_CUDA_TRY(expr)                                            \
+    do {                                                               \
+        cudaError_t _e = (expr);                                       \
+        if (_e != cudaSuccess) return cuda_status(_e, #expr);          \
+    } while (0)
+
+// --------------------------------------------------------------- launchers
+// setup kernels
+void launch_setup_coeffs(const double* m2, int nx, int ny, double h, double omega,
+                         const int* xcut, const int* ycut, int N1, int N2, const int* subid,
+                         int transmission, double tc_scale,
+                         double2* adiag, double2* dloc, const SubDev* subtab, cudaStream_t st);
+void launch_trace_coeffs(const double* m2, int nx, double h, double omega, int transmission,
+                         double tc_scale, const int* slot_sub, const int* slot_side, const int* slot_off,
+                         const int* slot_len, int nslots, const SubDev* subtab,
+                         TraceCoef<double2>* tc128, TraceCoef<float2>* tc64, cudaStream_t st);
+// factor
+template <typename R>
+cudaError_t launch_factor(const SubDev* subtab, int nsub, int max_mx, const double2* dloc,
+                          Cx<R>* X, Cx<R>* work, size_t work_stride, int* info, cudaStream_t st);
+// stage
+template <typename R>
+cudaError_t launch_stage(const StageArgs<R>& a, int nactive, int max_mx, cudaStream_t st);
+// krylov / vector kernels
+void launch_matvec(const double2* adiag, int nx, int ny, const double2* u, double2* Au, int nrhs,
+                   cudaStream_t st);
+void launch_residual(const double2* adiag, int nx, int ny, const double2* f, double fscale,
+                     const double2* u, double2* r, int nrhs, const int* active, double* partial,
+                     int nblk, cudaStream_t st);
+void launch_norm2_partial(const double2* v, long long n, int nrhs, long long stride, double* partial,
+                          int nblk, cudaStream_t st);
+void launch_reduce_rows(const double* partial, int nblk, int nrows, double* out, int mode,
+                        cudaStream_t st);
+void launch_mdot(const double2* V, long long vstride_k, long long vstride_rhs, int nvec,
+                 const double2* w, long long wstride, long long n, int nrhs, const int* active,
+                 double2* partial, int nblk, cudaStream_t st);
+void launch_reduce_cpartials(const double2* partial, int nblk, int nrows, double2* out,
+                             long long out_stride, int nrhs, cudaStream_t st);
+void launch_mupdate(const double2* V, long long vstride_k, long long vstride_rhs, int nvec,
+                    const int* nvec_rhs, const double2* coef, long long coef_stride, double sign, double2* w,
+                    long long wstride, long long n, int nrhs, const int* active, double* norm_partial,
+                    int nblk, cudaStream_t st);
+void launch_scale_vec(double2* dst, long long dstride, const double2* src, long long sstride,
+                      const double* inv, long long n, int nrhs, const int* active, cudaStream_t st);
+void launch_hessenberg_step(double2* H, int ldh, long long hstride, double2* cs, double2* sn, double2* g,
+                            int ldg, const double2* hcol, long long hcol_stride, const double* hnorm,
+                            int j, int nrhs, const int* active, double* resid_est, double* inv_hnext,
+                            cudaStream_t st);
+void launch_hessenberg_solve(const double2* H, int ldh, long long hstride, const double2* g, int ldg,
+                             const int* jcount, double2* y, int ldy, int nrhs, cudaStream_t st);
+void launch_mask_copy(double2* dst, const double2* src, long long n, int nrhs, const int* active,
+                      cudaStream_t st);
+void launch_sqrt_inplace(double* v, int n, cudaStream_t st);
+void launch_scale_from_norm(const double* norm2, double* inv, double* scale, int n, cudaStream_t st);
+// adjoint
+void launch_receiver_residual(const double2* u, long long N, const int* rec, int nrec, const double2* d,
+                              int nsrc, double2* res, double* partial, cudaStream_t st);
+void launch_adjoint_rhs(const double2* res, const int* rec, int nrec, int nsrc, long long N,
+                        double inv_h2, double2* f_adj, cudaStream_t st);
+void launch_gradient(const double2* U, const double2* Lt, const double* m2, int nx, int ny, double h,
+                     double omega, int nsrc, double* grad, cudaStream_t st);

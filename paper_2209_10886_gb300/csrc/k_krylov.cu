@@ -1,0 +1,341 @@
+// FP64 kernels of the flexible GMRES solver (paper Section 6: GMRES to a
+// relative residual of 1e-6) and of the five-point operator.
+//
+// Reductions are deterministic: every block writes its partial sums, a second
+// kernel adds them in a fixed order.
+#include "helm_internal.cuh"
+
+namespace {
+
+constexpr int VT = 256;
+
+template <typename V> __device__ __forceinline__ V warp_sum(V v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// block-wide sum of one double; result valid in thread 0
+__device__ double block_sum(double v, double* sh) {
+    v = warp_sum(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x < 32) {
+        t = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+        t = warp_sum(t);
+    }
+    return t;
+}
+
+// (A u)_p = adiag_p u_p - sum_{grid neighbours} u_q     (h^2-scaled five-point operator)
+__device__ __forceinline__ double2 apply_A(const double2* __restrict__ u, const double2 ad, long long p, int a, int b,
+                                           int nx, int ny) {
+    double sx = 0.0, sy = 0.0;
+    if (a > 0) { double2 q = u[p - 1]; sx += q.x; sy += q.y; }
+    if (a < nx - 1) { double2 q = u[p + 1]; sx += q.x; sy += q.y; }
+    if (b > 0) { double2 q = u[p - nx]; sx += q.x; sy += q.y; }
+    if (b < ny - 1) { double2 q = u[p + nx]; sx += q.x; sy += q.y; }
+    const double2 c = u[p];
+    return make_double2(fma(ad.x, c.x, fma(-ad.y, c.y, -sx)), fma(ad.x, c.y, fma(ad.y, c.x, -sy)));
+}
+
+__global__ void matvec_kernel(const double2* __restrict__ adiag, int nx, int ny, const double2* __restrict__ u,
+                              double2* __restrict__ Au) {
+    const long long N = (long long)nx * ny;
+    const int k = blockIdx.y;
+    const double2* uk = u + k * N;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
+        const int a = (int)(p % nx), b = (int)(p / nx);
+        Au[k * N + p] = apply_A(uk, adiag[p], p, a, b, nx, ny);
+    }
+}
+
+// r = fscale f - A u, and per-block partial ||r||^2
+__global__ void residual_kernel(const double2* __restrict__ adiag, int nx, int ny, const double2* __restrict__ f,
+                                double fscale, const double2* __restrict__ u, double2* __restrict__ r,
+                                const int* __restrict__ active, double* __restrict__ partial) {
+    __shared__ double sh[32];
+    const long long N = (long long)nx * ny;
+    const int k = blockIdx.y;
+    if (active && !active[k]) {
+        if (threadIdx.x == 0) partial[(long long)k * gridDim.x + blockIdx.x] = 0.0;
+        return;
+    }
+    const double2* uk = u + k * N;
+    double acc = 0.0;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
+        const int a = (int)(p % nx), b = (int)(p / nx);
+        const double2 Av = apply_A(uk, adiag[p], p, a, b, nx, ny);
+        const double2 fv = f[k * N + p];
+        const double2 rv = make_double2(fma(fscale, fv.x, -Av.x), fma(fscale, fv.y, -Av.y));
+        r[k * N + p] = rv;
+        acc = fma(rv.x, rv.x, fma(rv.y, rv.y, acc));
+    }
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) partial[(long long)k * gridDim.x + blockIdx.x] = acc;
+}
+
+__global__ void norm2_partial_kernel(const double2* __restrict__ v, long long n, long long stride,
+                                     double* __restrict__ partial) {
+    __shared__ double sh[32];
+    const int k = blockIdx.y;
+    double acc = 0.0;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
+        const double2 x = v[k * stride + p];
+        acc = fma(x.x, x.x, fma(x.y, x.y, acc));
+    }
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) partial[(long long)k * gridDim.x + blockIdx.x] = acc;
+}
+
+// out[row] = sum_b partial[row][b]   (mode 1: sqrt of the sum)
+__global__ void reduce_rows_kernel(const double* __restrict__ partial, int nblk, double* __restrict__ out, int mode) {
+    __shared__ double sh[32];
+    const int row = blockIdx.x;
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) acc += partial[(long long)row * nblk + b];
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) out[row] = mode == 1 ? sqrt(acc) : acc;
+}
+
+// partial[k][blk][j] = sum_{p in block range} conj(V_j[p]) w[p],  j < nvec
+constexpr int KB = 4;
+__global__ void mdot_kernel(const double2* __restrict__ V, long long vsk, long long vsr, int nvec,
+                            const double2* __restrict__ w, long long ws, long long n, const int* __restrict__ active,
+                            double2* __restrict__ partial) {
+    __shared__ double sh[32];
+    const int k = blockIdx.y;
+    const int nblk = gridDim.x;
+    double2* out = partial + ((long long)k * nblk + blockIdx.x) * nvec;
+    if (active && !active[k]) {
+        for (int j = threadIdx.x; j < nvec; j += blockDim.x) out[j] = make_double2(0.0, 0.0);
+        return;
+    }
+    const long long chunk = (n + nblk - 1) / nblk;
+    const long long p0 = blockIdx.x * chunk, p1 = min(n, p0 + chunk);
+    const double2* wk = w + k * ws;
+    for (int j0 = 0; j0 < nvec; j0 += KB) {
+        double2 acc[KB];
+#pragma unroll
+        for (int q = 0; q < KB; ++q) acc[q] = make_double2(0.0, 0.0);
+        for (long long p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+            const double2 wv = wk[p];
+#pragma unroll
+            for (int q = 0; q < KB; ++q)
+                if (j0 + q < nvec) acc[q] = cfmaconj(V[(long long)(j0 + q) * vsk + k * vsr + p], wv, acc[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < KB; ++q) {
+            if (j0 + q >= nvec) break;
+            const double re = block_sum(acc[q].x, sh);
+            const double im = block_sum(acc[q].y, sh);
+            if (threadIdx.x == 0) out[j0 + q] = make_double2(re, im);
+        }
+    }
+}
+
+__global__ void reduce_cpartials_kernel(const double2* __restrict__ partial, int nblk, int nvec,
+                                        double2* __restrict__ out, long long os) {
+    __shared__ double sh[32];
+    const int k = blockIdx.y, j = blockIdx.x;
+    double re = 0.0, im = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
+        const double2 v = partial[((long long)k * nblk + b) * nvec + j];
+        re += v.x;
+        im += v.y;
+    }
+    re = block_sum(re, sh);
+    im = block_sum(im, sh);
+    if (threadIdx.x == 0) out[k * os + j] = make_double2(re, im);
+}
+
+// w += sign * sum_j coef[k][j] V_j, optional per-block ||w||^2 partials
+__global__ void mupdate_kernel(const double2* __restrict__ V, long long vsk, long long vsr, int nvec,
+                               const int* __restrict__ nvec_rhs, const double2* __restrict__ coef, long long cs,
+                               double sign, double2* __restrict__ w, long long ws, long long n,
+                               const int* __restrict__ active, double* __restrict__ norm_partial) {
+    __shared__ double2 c[512];
+    __shared__ double sh[32];
+    const int k = blockIdx.y;
+    const bool on = !(active && !active[k]);
+    const int nv = nvec_rhs ? nvec_rhs[k] : nvec;
+    for (int j = threadIdx.x; j < nv && j < 512; j += blockDim.x) {
+        const double2 cj = coef[k * cs + j];
+        c[j] = make_double2(sign * cj.x, sign * cj.y);
+    }
+    __syncthreads();
+    double acc = 0.0;
+    if (on) {
+        double2* wk = w + k * ws;
+        for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
+            double2 x = wk[p];
+            for (int j = 0; j < nv; ++j) x = cfma(c[j], V[(long long)j * vsk + k * vsr + p], x);
+            wk[p] = x;
+            acc = fma(x.x, x.x, fma(x.y, x.y, acc));
+        }
+    }
+    if (norm_partial) {
+        acc = block_sum(acc, sh);
+        if (threadIdx.x == 0) norm_partial[(long long)k * gridDim.x + blockIdx.x] = acc;
+    }
+}
+
+// dst = src * inv[k]  (inactive RHS: dst = 0)
+__global__ void scale_vec_kernel(double2* __restrict__ dst, long long ds, const double2* __restrict__ src,
+                                 long long ss, const double* __restrict__ inv, long long n,
+                                 const int* __restrict__ active) {
+    const int k = blockIdx.y;
+    const bool on = !(active && !active[k]);
+    const double s = on ? inv[k] : 0.0;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
+        const double2 x = on ? src[k * ss + p] : make_double2(0.0, 0.0);
+        dst[k * ds + p] = make_double2(x.x * s, x.y * s);
+    }
+}
+
+// One Arnoldi column j per RHS: H(0..j, j) = h1 + h2, H(j+1, j) = ||w||, then the
+// Givens rotations of the earlier columns, a new rotation that annihilates
+// H(j+1, j), and the rotated right-hand side g.  |g_{j+1}| is the residual norm
+// of the least-squares problem min ||beta e_1 - H y||.
+__global__ void hessenberg_step_kernel(double2* __restrict__ H, int ldh, long long hs, double2* __restrict__ cs,
+                                       double2* __restrict__ sn, double2* __restrict__ g, int ldg,
+                                       const double2* __restrict__ hcol, long long hcs, const double* __restrict__ hnorm,
+                                       int j, int nrhs, const int* __restrict__ active,
+                                       double* __restrict__ resid_est, double* __restrict__ inv_hnext) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nrhs) return;
+    if (active && !active[k]) return;
+    double2* Hk = H + k * hs;            // column-major: H(i, jj) at Hk[jj*ldh + i]
+    double2* col = Hk + (long long)j * ldh;
+    for (int i = 0; i <= j; ++i) col[i] = hcol[k * hcs + i];
+    const double hn = hnorm[k];
+    col[j + 1] = make_double2(hn, 0.0);
+    double2* csk = cs + (long long)k * ldg;
+    double2* snk = sn + (long long)k * ldg;
+    for (int i = 0; i < j; ++i) {
+        const double2 a = col[i], b = col[i + 1];
+        const double c = csk[i].x;
+        const double2 s = snk[i];
+        // [a; b] <- [c a + s b; -conj(s) a + c b]
+        col[i] = make_double2(c * a.x + (s.x * b.x - s.y * b.y), c * a.y + (s.x * b.y + s.y * b.x));
+        col[i + 1] = make_double2(c * b.x - (s.x * a.x + s.y * a.y), c * b.y - (s.x * a.y - s.y * a.x));
+    }
+    const double2 a = col[j], b = col[j + 1];
+    const double na = sqrt(a.x * a.x + a.y * a.y), nb = sqrt(b.x * b.x + b.y * b.y);
+    const double den = sqrt(na * na + nb * nb);
+    double c;
+    double2 s;
+    if (den == 0.0) { c = 1.0; s = make_double2(0.0, 0.0); }
+    else if (na == 0.0) { c = 0.0; s = make_double2(b.x / den, -b.y / den); }      // conj(b)/|b| * (b real >= 0)
+    else {
+        c = na / den;
+        const double2 ph = make_double2(a.x / na, a.y / na);                      // a/|a|
+        s = make_double2((ph.x * b.x + ph.y * b.y) / den, (ph.y * b.x - ph.x * b.y) / den);   // ph*conj(b)/den
+    }
+    csk[j] = make_double2(c, 0.0);
+    snk[j] = s;
+    col[j] = make_double2(c * a.x + (s.x * b.x - s.y * b.y), c * a.y + (s.x * b.y + s.y * b.x));
+    col[j + 1] = make_double2(0.0, 0.0);
+    double2* gk = g + (long long)k * ldg;
+    const double2 gj = gk[j];
+    gk[j + 1] = make_double2(-(s.x * gj.x + s.y * gj.y), -(s.x * gj.y - s.y * gj.x));   // -conj(s) g_j
+    gk[j] = make_double2(c * gj.x, c * gj.y);
+    resid_est[k] = sqrt(gk[j + 1].x * gk[j + 1].x + gk[j + 1].y * gk[j + 1].y);
+    inv_hnext[k] = hn > 0.0 ? 1.0 / hn : 0.0;
+}
+
+// y = R^{-1} g (upper triangular R = rotated H, first jcount[k] columns)
+__global__ void hessenberg_solve_kernel(const double2* __restrict__ H, int ldh, long long hs, const double2* __restrict__ g,
+                                        int ldg, const int* __restrict__ jcount, double2* __restrict__ y, int ldy, int nrhs) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nrhs) return;
+    const int m = jcount[k];
+    const double2* Hk = H + k * hs;
+    double2* yk = y + (long long)k * ldy;
+    for (int i = m - 1; i >= 0; --i) {
+        double2 acc = g[(long long)k * ldg + i];
+        for (int jj = i + 1; jj < m; ++jj) {
+            const double2 h = Hk[(long long)jj * ldh + i];
+            const double2 yy = yk[jj];
+            acc.x -= h.x * yy.x - h.y * yy.y;
+            acc.y -= h.x * yy.y + h.y * yy.x;
+        }
+        yk[i] = cdiv(acc, Hk[(long long)i * ldh + i]);
+    }
+}
+
+__global__ void sqrt_kernel(double* v, int n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) v[i] = sqrt(v[i]);
+}
+
+// norm -> (1/norm, norm) with zero norms mapped to (1, 1)
+__global__ void scale_from_norm_kernel(const double* norm2, double* inv, double* scale, int n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double s = sqrt(norm2[i]);
+    inv[i] = s > 0.0 ? 1.0 / s : 1.0;
+    scale[i] = s > 0.0 ? s : 1.0;
+}
+
+int grid_for(long long n) {
+    long long b = (n + VT - 1) / VT;
+    return (int)min(b, (long long)152 * 8);
+}
+
+}  // namespace
+
+void launch_matvec(const double2* adiag, int nx, int ny, const double2* u, double2* Au, int nrhs, cudaStream_t st) {
+    dim3 g(grid_for((long long)nx * ny), nrhs);
+    matvec_kernel<<<g, VT, 0, st>>>(adiag, nx, ny, u, Au);
+}
+void launch_residual(const double2* adiag, int nx, int ny, const double2* f, double fscale, const double2* u,
+                     double2* r, int nrhs, const int* active, double* partial, int nblk, cudaStream_t st) {
+    dim3 g(nblk, nrhs);
+    residual_kernel<<<g, VT, 0, st>>>(adiag, nx, ny, f, fscale, u, r, active, partial);
+}
+void launch_norm2_partial(const double2* v, long long n, int nrhs, long long stride, double* partial, int nblk,
+                          cudaStream_t st) {
+    dim3 g(nblk, nrhs);
+    norm2_partial_kernel<<<g, VT, 0, st>>>(v, n, stride, partial);
+}
+void launch_reduce_rows(const double* partial, int nblk, int nrows, double* out, int mode, cudaStream_t st) {
+    reduce_rows_kernel<<<nrows, VT, 0, st>>>(partial, nblk, out, mode);
+}
+void launch_mdot(const double2* V, long long vsk, long long vsr, int nvec, const double2* w, long long ws, long long n,
+                 int nrhs, const int* active, double2* partial, int nblk, cudaStream_t st) {
+    dim3 g(nblk, nrhs);
+    mdot_kernel<<<g, VT, 0, st>>>(V, vsk, vsr, nvec, w, ws, n, active, partial);
+}
+void launch_reduce_cpartials(const double2* partial, int nblk, int nrows, double2* out, long long os, int nrhs,
+                             cudaStream_t st) {
+    dim3 g(nrows, nrhs);
+    reduce_cpartials_kernel<<<g, VT, 0, st>>>(partial, nblk, nrows, out, os);
+}
+void launch_mupdate(const double2* V, long long vsk, long long vsr, int nvec, const int* nvec_rhs, const double2* coef,
+                    long long cs, double sign, double2* w, long long ws, long long n, int nrhs, const int* active,
+                    double* norm_partial, int nblk, cudaStream_t st) {
+    dim3 g(nblk, nrhs);
+    mupdate_kernel<<<g, VT, 0, st>>>(V, vsk, vsr, nvec, nvec_rhs, coef, cs, sign, w, ws, n, active, norm_partial);
+}
+void launch_scale_vec(double2* dst, long long ds, const double2* src, long long ss, const double* inv, long long n,
+                      int nrhs, const int* active, cudaStream_t st) {
+    dim3 g(grid_for(n), nrhs);
+    scale_vec_kernel<<<g, VT, 0, st>>>(dst, ds, src, ss, inv, n, active);
+}
+void launch_hessenberg_step(double2* H, int ldh, long long hs, double2* cs, double2* sn, double2* g, int ldg,
+                            const double2* hcol, long long hcs, const double* hnorm, int j, int nrhs, const int* active,
+                            double* resid_est, double* inv_hnext, cudaStream_t st) {
+    hessenberg_step_kernel<<<(nrhs + 31) / 32, 32, 0, st>>>(H, ldh, hs, cs, sn, g, ldg, hcol, hcs, hnorm, j, nrhs,
+                                                           active, resid_est, inv_hnext);
+}
+void launch_hessenberg_solve(const double2* H, int ldh, long long hs, const double2* g, int ldg, const int* jcount,
+                             double2* y, int ldy, int nrhs, cudaStream_t st) {
+    hessenberg_solve_kernel<<<(nrhs + 31) / 32, 32, 0, st>>>(H, ldh, hs, g, ldg, jcount, y, ldy, nrhs);
+}
+void launch_sqrt_inplace(double* v, int n, cudaStream_t st) { sqrt_kernel<<<(n + 127) / 128, 128, 0, st>>>(v, n); }
+void launch_scale_from_norm(const double* norm2, double* inv, double* scale, int n, cudaStream_t st) {
+    scale_from_norm_kernel<<<(n + 127) / 128, 128, 0, st>>>(norm2, inv, scale, n);
+}

@@ -1,0 +1,256 @@
+"""ctypes binding of libhelm (include/helm.h): argument marshalling only.
+
+Every computation runs in the CUDA library; this module converts torch
+tensors to device pointers, passes the current CUDA stream and turns status
+codes into exceptions.  There is no CPU fallback: if the shared library is
+missing or fails to load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhelm.so")
+HEADER_PATH = os.path.join(os.path.dirname(_HERE), "include", "helm.h")
+
+PREC = {"c128": 0, "c64": 1}
+SCHED = {"BSP": 0, "SP": 1}
+TRANSMISSION = {"optimized": 0, "impedance": 1}
+STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_STATE", 5: "ERR_NO_CONVERGENCE",
+          6: "ERR_TIMEOUT", 7: "ERR_UNSUPPORTED"}
+
+
+class HelmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class HelmOpts(ctypes.Structure):
+    _fields_ = [("restart", ctypes.c_int), ("maxit", ctypes.c_int), ("tol", ctypes.c_double),
+                ("x0_given", ctypes.c_int), ("sched", ctypes.c_int), ("use_graph", ctypes.c_int),
+                ("hist", ctypes.POINTER(ctypes.c_double))]
+
+
+class HelmSetupOpts(ctypes.Structure):
+    _fields_ = [("transmission", ctypes.c_int), ("tc_scale", ctypes.c_double)]
+
+
+class HelmInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("relres", ctypes.c_double)]
+
+
+_lib = None
+_vp, _i, _d, _ll = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong
+
+
+def lib():
+    """Load libhelm.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2209_10886_gb300.build.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    L.helm_default_opts.argtypes = [ctypes.POINTER(HelmOpts)]
+    L.helm_default_opts.restype = None
+    L.helm_default_setup_opts.argtypes = [ctypes.POINTER(HelmSetupOpts)]
+    L.helm_default_setup_opts.restype = None
+    L.helm_setup.argtypes = [_i, _i, _d, _d, _vp, _i, _i, _vp, _vp, ctypes.POINTER(HelmSetupOpts),
+                             ctypes.POINTER(_vp)]
+    L.precond_factor.argtypes = [_vp, _i, _vp]
+    L.precond_apply.argtypes = [_vp, _i, _vp, _vp, _i, _vp]
+    L.helm_matvec.argtypes = [_vp, _vp, _vp, _i, _vp]
+    L.gmres_solve.argtypes = [_vp, _vp, _vp, _i, ctypes.POINTER(HelmOpts), ctypes.POINTER(HelmInfo), _vp]
+    L.misfit_grad.argtypes = [_vp, _vp, _i, _vp, _i, _vp, ctypes.POINTER(HelmOpts), ctypes.POINTER(_d), _vp, _vp, _vp]
+    L.helm_destroy.argtypes = [_vp]
+    L.helm_last_error.argtypes = []
+    L.helm_last_error.restype = ctypes.c_char_p
+    L.helm_schedule_info.argtypes = [_i, _i, _i, ctypes.POINTER(_i), ctypes.POINTER(_i)]
+    L.helm_problem_info.argtypes = [_vp, ctypes.POINTER(_ll), ctypes.POINTER(_i), ctypes.POINTER(_ll),
+                                    ctypes.POINTER(_ll)]
+    for name in ("helm_setup", "precond_factor", "precond_apply", "helm_matvec", "gmres_solve", "misfit_grad",
+                 "helm_destroy", "helm_schedule_info", "helm_problem_info"):
+        getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def header_functions():
+    """Names of the functions declared in include/helm.h."""
+    txt = open(HEADER_PATH).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(\w+)\s*\([^;{]*\)\s*;", txt)) - {"if", "while", "for", "sizeof"})
+
+
+def _check(status, what=""):
+    if status != 0:
+        raise HelmError(status, lib().helm_last_error().decode() or what)
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t: torch.Tensor):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _as_fields(x: torch.Tensor, N: int, name: str) -> torch.Tensor:
+    if not x.is_cuda or x.dtype != torch.complex128:
+        raise TypeError(f"{name} must be a complex128 CUDA tensor")
+    if x.numel() % N != 0:
+        raise ValueError(f"{name} must hold a multiple of N = {N} values")
+    return x.contiguous()
+
+
+def schedule_info(N1: int, N2: int, sched: str = "BSP"):
+    """(sweep steps, stage launches) per preconditioner application (host only)."""
+    steps, stages = _i(), _i()
+    _check(lib().helm_schedule_info(N1, N2, SCHED[sched], ctypes.byref(steps), ctypes.byref(stages)))
+    return steps.value, stages.value
+
+
+def default_opts(**kw) -> HelmOpts:
+    o = HelmOpts()
+    lib().helm_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        if k == "sched":
+            v = SCHED[v] if isinstance(v, str) else v
+        setattr(o, k, v)
+    return o
+
+
+class Problem:
+    """A discretised Helmholtz problem with its checkerboard decomposition.
+
+    ``m2``: squared slowness (float64, n_x*n_y values, CUDA).  ``xcuts`` /
+    ``ycuts``: node offsets of the subdomain columns / rows (length N1+1 /
+    N2+1) or None for an even split.
+    """
+
+    def __init__(self, n_x, n_y, h, omega, m2, N1, N2, xcuts=None, ycuts=None,
+                 transmission="optimized", tc_scale=1.5):
+        L = lib()
+        if not (m2.is_cuda and m2.dtype == torch.float64 and m2.numel() == n_x * n_y):
+            raise TypeError("m2 must be a float64 CUDA tensor with n_x*n_y values")
+        m2 = m2.contiguous()
+        so = HelmSetupOpts(TRANSMISSION[transmission], float(tc_scale))
+        xc = (ctypes.c_int * (N1 + 1))(*[int(v) for v in xcuts]) if xcuts is not None else None
+        yc = (ctypes.c_int * (N2 + 1))(*[int(v) for v in ycuts]) if ycuts is not None else None
+        h_ = ctypes.c_void_p()
+        torch.cuda.current_stream().synchronize()
+        _check(L.helm_setup(n_x, n_y, float(h), float(omega), _ptr(m2), N1, N2, xc, yc, ctypes.byref(so),
+                            ctypes.byref(h_)))
+        self._h = h_
+        self.n_x, self.n_y, self.h, self.omega, self.N1, self.N2 = n_x, n_y, h, omega, N1, N2
+        self.N = n_x * n_y
+        self.m2 = m2
+
+    # ----------------------------------------------------------------- info
+    def info(self):
+        n, ns, nt, fb = _ll(), _i(), _ll(), _ll()
+        _check(lib().helm_problem_info(self._h, ctypes.byref(n), ctypes.byref(ns), ctypes.byref(nt),
+                                       ctypes.byref(fb)))
+        return dict(n_unknowns=n.value, n_subdomains=ns.value, n_trace=nt.value, factor_bytes=fb.value)
+
+    # -------------------------------------------------------------- compute
+    def factor(self, prec="c64", stream=None):
+        _check(lib().precond_factor(self._h, PREC[prec], _stream(stream)))
+        self.prec = prec
+        return self
+
+    def precond_apply(self, r, z=None, sched="BSP", stream=None):
+        r = _as_fields(r, self.N, "r")
+        z = torch.empty_like(r) if z is None else z
+        _check(lib().precond_apply(self._h, SCHED[sched], _ptr(r), _ptr(z), r.numel() // self.N, _stream(stream)))
+        return z
+
+    def matvec(self, u, Au=None, stream=None):
+        u = _as_fields(u, self.N, "u")
+        Au = torch.empty_like(u) if Au is None else Au
+        _check(lib().helm_matvec(self._h, _ptr(u), _ptr(Au), u.numel() // self.N, _stream(stream)))
+        return Au
+
+    def solve(self, f, u=None, restart=50, maxit=1000, tol=1e-6, sched="BSP", x0=None, history=False,
+              stream=None, raise_on_noconv=True):
+        """Solve A u = h^2 f (FP64 FGMRES); returns (u, [(iters, relres)], history or None)."""
+        f = _as_fields(f, self.N, "f")
+        nrhs = f.numel() // self.N
+        u = torch.empty_like(f) if u is None else u
+        if x0 is not None:
+            u.copy_(x0)
+        hist = (ctypes.c_double * (maxit * nrhs))() if history else None
+        o = default_opts(restart=restart, maxit=maxit, tol=tol, sched=sched, x0_given=int(x0 is not None))
+        if hist is not None:
+            o.hist = ctypes.cast(hist, ctypes.POINTER(ctypes.c_double))
+        info = (HelmInfo * nrhs)()
+        st = lib().gmres_solve(self._h, _ptr(f), _ptr(u), nrhs, ctypes.byref(o), info, _stream(stream))
+        if st != 0 and (raise_on_noconv or st != 5):
+            _check(st)
+        out = [(info[k].iters, info[k].relres) for k in range(nrhs)]
+        hh = None
+        if hist is not None:
+            hh = [[hist[k * maxit + j] for j in range(out[k][0])] for k in range(nrhs)]
+        return u, out, hh
+
+    def misfit_grad(self, f, rec_idx, d, restart=50, maxit=1000, tol=1e-6, sched="BSP", stream=None):
+        """(J, grad_m2, u) of J = 1/2 sum_s ||P u_s - d_s||^2 by the adjoint-state method."""
+        f = _as_fields(f, self.N, "f")
+        nsrc = f.numel() // self.N
+        rec = rec_idx.to(device=f.device, dtype=torch.int32).contiguous()
+        d = d.to(device=f.device, dtype=torch.complex128).contiguous()
+        if d.numel() != nsrc * rec.numel():
+            raise ValueError("d must hold nsrc*nrec values")
+        grad = torch.empty(self.N, dtype=torch.float64, device=f.device)
+        u = torch.empty_like(f)
+        J = ctypes.c_double()
+        o = default_opts(restart=restart, maxit=maxit, tol=tol, sched=sched)
+        _check(lib().misfit_grad(self._h, _ptr(f), nsrc, _ptr(rec), rec.numel(), _ptr(d), ctypes.byref(o),
+                                 ctypes.byref(J), _ptr(grad), _ptr(u), _stream(stream)))
+        return J.value, grad, u
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().helm_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class MisfitFn(torch.autograd.Function):
+    """``J = MisfitFn.apply(m2, f, rec_idx, d, spec)``: the misfit of the sources
+    ``f`` at the receivers ``rec_idx`` for the squared slowness ``m2``; its
+    backward returns ``grad_output * dJ/dm2`` computed by the adjoint kernels.
+
+    ``spec``: dict with n, h, omega, N1, N2, xcuts, ycuts and optional prec,
+    restart, tol, sched, transmission.
+    """
+
+    @staticmethod
+    def forward(ctx, m2, f, rec_idx, d, spec):
+        n = spec["n"]
+        p = Problem(n, n, spec["h"], spec["omega"], m2.detach(), spec["N1"], spec["N2"], spec.get("xcuts"),
+                    spec.get("ycuts"), transmission=spec.get("transmission", "optimized"))
+        try:
+            p.factor(spec.get("prec", "c64"))
+            J, grad, _ = p.misfit_grad(f, rec_idx, d, restart=spec.get("restart", 50), tol=spec.get("tol", 1e-6),
+                                       maxit=spec.get("maxit", 2000), sched=spec.get("sched", "BSP"))
+        finally:
+            p.close()
+        ctx.save_for_backward(grad)
+        return torch.tensor(J, dtype=torch.float64, device=m2.device)
+
+    @staticmethod
+    def backward(ctx, grad_output):
+        (grad,) = ctx.saved_tensors
+        return grad_output * grad, None, None, None, None

@@ -1,0 +1,58 @@
+"""CPU checks of the C ABI: the library loads, exports every function the
+header declares, and its host-side scheduler reproduces the paper's step
+counts.  No compute call needs a GPU here."""
+import ctypes
+import os
+
+import numpy as np
+import pytest
+
+from paper_2209_10886_gb300 import build as B
+
+
+@pytest.fixture(scope="module")
+def L():
+    B.build()
+    from paper_2209_10886_gb300 import helm
+    return helm.lib()
+
+
+def test_library_exports_every_declared_function(L):
+    from paper_2209_10886_gb300 import helm
+    names = helm.header_functions()
+    assert {"helm_setup", "precond_factor", "precond_apply", "gmres_solve", "misfit_grad", "helm_matvec",
+            "helm_destroy", "helm_last_error"} <= set(names)
+    for n in names:
+        assert hasattr(L, n), n
+
+
+def test_scheduler_reproduces_table1(L, golden_dir):
+    from paper_2209_10886_gb300 import schedule_info
+    rows = np.loadtxt(os.path.join(golden_dir, "table1_steps.txt"), dtype=int, ndmin=2)
+    for N1, N2, sp_ns, bsp_ns in rows:
+        assert schedule_info(N1, N2, "SP")[0] == sp_ns
+        assert schedule_info(N1, N2, "BSP")[0] == bsp_ns
+
+
+@pytest.mark.parametrize("N1,N2", [(1, 1), (2, 2), (8, 8), (12, 12), (16, 16), (5, 10), (3, 7), (7, 3), (1, 5)])
+def test_scheduler_matches_oracle_schedule(L, N1, N2):
+    """Step counts of the C++ scheduler equal the oracle's (Sections 4-5), and the
+    stage count is steps + lifting + reconstruction (+ residual for BSP)."""
+    from oracle import schedule_steps
+    from paper_2209_10886_gb300 import schedule_info
+    for kind in ("SP", "BSP"):
+        steps, stages = schedule_info(N1, N2, kind)
+        if N1 * N2 == 1:
+            assert (steps, stages) == (0, 1)
+            continue
+        assert steps == schedule_steps(N1, N2, kind)
+        assert stages == steps + 2 + (kind == "BSP")
+
+
+def test_invalid_arguments_are_rejected_without_gpu(L):
+    from paper_2209_10886_gb300 import helm
+    s = ctypes.c_int()
+    assert L.helm_schedule_info(0, 3, 0, ctypes.byref(s), None) == 1
+    assert b"N1" in L.helm_last_error()
+    assert L.helm_setup(0, 5, 0.1, 1.0, None, 1, 1, None, None, None, ctypes.byref(ctypes.c_void_p())) == 1
+    assert L.helm_destroy(None) == 0

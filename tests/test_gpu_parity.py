@@ -1,0 +1,212 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Tolerances (written per test):
+* complex128 path vs oracle: both compute the same operator in FP64 with
+  different elimination orders (block-tridiagonal Gauss-Jordan vs sparse LU);
+  the difference is roundoff times the local condition number, <= 1e-10.
+* complex64 preconditioner vs the complex128 oracle: unit roundoff 6e-8
+  amplified by the block recursion over ~128 grid rows; bound 5e-4 (measured
+  values are printed with -s).
+* Solutions: both sides solve to a true relative residual of 1e-9, so they
+  agree to cond(A) * 1e-9; the bar is rel. L2 <= 1e-5.
+"""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import workloads as W
+from oracle import Decomposition, Sweeper, assemble_operator
+from oracle.adjoint import misfit_gradient_direct
+
+
+@pytest.fixture(scope="module")
+def H():
+    from paper_2209_10886_gb300 import build
+    build.build()
+    from paper_2209_10886_gb300 import helm
+    helm.lib()
+    return helm
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def cuda(x, dtype=torch.complex128):
+    return torch.as_tensor(np.ascontiguousarray(x)).to(device="cuda", dtype=dtype)
+
+
+def make(H, w, prec="c128", transmission="optimized"):
+    p = H.Problem(w.n, w.n, w.h, w.omega, cuda(w.m2, torch.float64), w.N1, w.N2, w.xcuts, w.ycuts,
+                  transmission=transmission)
+    p.factor(prec)
+    dec = Decomposition(w.n, w.h, w.omega, w.m2, w.xcuts, w.ycuts, transmission=transmission)
+    return p, dec
+
+
+CASES = {
+    "tiny_2x2": lambda: W.workload("tiny"),
+    "ragged_3x2": lambda: W.workload("custom", n=60, N1=3, N2=2, medium="layered", seed=3,
+                                     xcuts=[0, 21, 39, 60], ycuts=[0, 33, 60]),
+    "uneven_4x3": lambda: W.workload("custom", n=70, N1=4, N2=3, medium="layered", seed=4,
+                                     xcuts=[0, 17, 35, 52, 70], ycuts=[0, 25, 46, 70]),
+    "column_1x3": lambda: W.workload("custom", n=40, N1=1, N2=3, medium="layered", seed=5),
+    "row_3x1": lambda: W.workload("custom", n=40, N1=3, N2=1, medium="layered", seed=6),
+    "wide_2x2_131": lambda: W.workload("custom", n=262, N1=2, N2=2, medium="layered", seed=7,
+                                       xcuts=[0, 131, 262], ycuts=[0, 129, 262]),
+}
+
+
+def test_matvec_matches_sparse_matrix(H):
+    for name in ("tiny_2x2", "uneven_4x3"):
+        w = CASES[name]()
+        p, _ = make(H, w)
+        A = assemble_operator(w.n, w.h, w.omega, w.m2)
+        u = W.random_complex((3, w.N), 1)
+        Au = p.matvec(cuda(u)).cpu().numpy()
+        ref = np.stack([A @ u[k] for k in range(3)])
+        assert np.abs(Au - ref).max() <= 1e-14 * np.abs(ref).max()
+        p.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("c128", 1e-11), ("c64", 5e-4)])
+def test_single_subdomain_is_direct_solve(H, prec, tol):
+    w = W.workload("custom", n=75, N1=1, N2=1, medium="layered", seed=2)
+    p, _ = make(H, w, prec)
+    A = assemble_operator(w.n, w.h, w.omega, w.m2).tocsc()
+    r = W.random_complex((2, w.N), 3)
+    z = p.precond_apply(cuda(r)).cpu().numpy()
+    for k in range(2):
+        e = rel(z[k], spla.spsolve(A, r[k]))
+        print(f"single subdomain {prec}: rel {e:.2e}")
+        assert e <= tol
+    p.close()
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("sched", ["BSP", "SP"])
+def test_precond_apply_c128_matches_oracle(H, case, sched):
+    w = CASES[case]()
+    p, dec = make(H, w, "c128")
+    sw = Sweeper(dec)
+    nrhs = 3 if case in ("tiny_2x2", "uneven_4x3") else 1
+    r = W.random_complex((nrhs, w.N), 5)
+    z = p.precond_apply(cuda(r), sched=sched).cpu().numpy()
+    for k in range(nrhs):
+        ref = sw.precondition(r[k], sched)
+        e = rel(z[k], ref)
+        print(f"{case} {sched} c128 rhs{k}: rel {e:.2e}")
+        assert e <= 1e-10
+    p.close()
+
+
+@pytest.mark.parametrize("case", ["tiny_2x2", "uneven_4x3", "wide_2x2_131"])
+def test_precond_apply_c64_matches_oracle(H, case):
+    w = CASES[case]()
+    p, dec = make(H, w, "c64")
+    sw = Sweeper(dec)
+    r = W.random_complex((5, w.N), 6)      # 5 RHS: one CTA of 4 and a ragged CTA of 1
+    z = p.precond_apply(cuda(r), sched="BSP").cpu().numpy()
+    for k in range(5):
+        e = rel(z[k], sw.precondition(r[k], "BSP"))
+        print(f"{case} BSP c64 rhs{k}: rel {e:.2e}")
+        assert e <= 5e-4
+    p.close()
+
+
+def test_impedance_transmission_matches_oracle(H):
+    w = CASES["ragged_3x2"]()
+    p, dec = make(H, w, "c128", transmission="impedance")
+    r = W.random_complex(w.N, 8)
+    z = p.precond_apply(cuda(r)).cpu().numpy()
+    assert rel(z, Sweeper(dec).precondition(r, "BSP")) <= 1e-10
+    p.close()
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+@pytest.mark.parametrize("sched", ["BSP", "SP"])
+def test_gmres_matches_direct_solve(H, prec, sched):
+    w = CASES["tiny_2x2"]()
+    p, _ = make(H, w, prec)
+    A = assemble_operator(w.n, w.h, w.omega, w.m2).tocsc()
+    ref = spla.spsolve(A, w.h ** 2 * w.f[0])
+    u, info, _ = p.solve(cuda(w.f), tol=1e-9, restart=50, sched=sched)
+    u = u.cpu().numpy()[0]
+    true_rr = np.linalg.norm(w.h ** 2 * w.f[0] - A @ u) / np.linalg.norm(w.h ** 2 * w.f[0])
+    print(f"gmres {prec} {sched}: iters {info[0][0]} relres {info[0][1]:.2e} true {true_rr:.2e} err {rel(u, ref):.2e}")
+    assert info[0][1] <= 1e-9 and true_rr <= 1.01e-9
+    assert rel(u, ref) <= 1e-5
+
+
+def test_gmres_multi_rhs_and_initial_guess(H):
+    w = W.workload("custom", n=60, N1=3, N2=2, medium="layered", seed=3, nrhs=3,
+                   xcuts=[0, 21, 39, 60], ycuts=[0, 33, 60])
+    p, _ = make(H, w, "c64")
+    A = assemble_operator(w.n, w.h, w.omega, w.m2).tocsc()
+    u, info, hist = p.solve(cuda(w.f), tol=1e-9, history=True)
+    u = u.cpu().numpy()
+    for k in range(3):
+        ref = spla.spsolve(A, w.h ** 2 * w.f[k])
+        assert rel(u[k], ref) <= 1e-5 and info[k][1] <= 1e-9
+        assert len(hist[k]) == info[k][0] and hist[k][-1] <= 1e-9 * 1.0001
+    # restarting from the solution needs no iteration
+    u2, info2, _ = p.solve(cuda(w.f), x0=cuda(u), tol=1e-9)
+    assert all(it == 0 for it, _ in info2)
+
+
+def test_misfit_gradient_matches_direct_adjoint(H):
+    n = 63
+    w = W.workload("custom", n=n, N1=2, N2=2, medium="layered", seed=3, nrhs=3)
+    rec = np.arange((n - 1) * n + 1, n * n, 4)
+    rng = np.random.default_rng(1)
+    d = (rng.normal(size=(3, len(rec))) + 1j * rng.normal(size=(3, len(rec)))) * 1e-4
+    J, g, U = misfit_gradient_direct(w.n, w.h, w.omega, w.m2, w.f, rec, d)
+    for prec, tol in (("c128", 1e-7), ("c64", 1e-7)):
+        p, _ = make(H, w, prec)
+        Jg, gg, ug = p.misfit_grad(cuda(w.f), torch.as_tensor(rec), cuda(d), tol=1e-11, maxit=2000)
+        gg = gg.cpu().numpy()
+        print(f"misfit {prec}: J rel {abs(Jg - J) / J:.2e}, grad rel {rel(gg, g):.2e}")
+        assert abs(Jg - J) <= tol * J
+        assert rel(gg, g) <= 1e-6
+        p.close()
+
+
+def test_autograd_function_backward_is_the_adjoint_gradient(H):
+    n = 47
+    w = W.workload("custom", n=n, N1=2, N2=2, medium="layered", seed=9, nrhs=2)
+    rec = np.arange((n - 1) * n, n * n, 3)
+    d = np.zeros((2, len(rec)), dtype=complex)
+    J, g, _ = misfit_gradient_direct(w.n, w.h, w.omega, w.m2, w.f, rec, d)
+    m2 = cuda(w.m2, torch.float64).requires_grad_(True)
+    spec = dict(n=n, h=w.h, omega=w.omega, N1=2, N2=2, xcuts=w.xcuts, ycuts=w.ycuts, prec="c128", tol=1e-11)
+    Jt = H.MisfitFn.apply(m2, cuda(w.f), torch.as_tensor(rec), cuda(d), spec)
+    (2.0 * Jt).backward()
+    assert abs(Jt.item() - J) <= 1e-7 * J
+    assert rel(m2.grad.cpu().numpy(), 2.0 * g) <= 1e-6
+
+
+def test_state_and_argument_errors(H):
+    w = CASES["tiny_2x2"]()
+    p = H.Problem(w.n, w.n, w.h, w.omega, cuda(w.m2, torch.float64), 2, 2, w.xcuts, w.ycuts)
+    with pytest.raises(H.HelmError) as e:
+        p.precond_apply(cuda(np.zeros(w.N)))
+    assert e.value.status == 4
+    with pytest.raises(H.HelmError) as e:
+        p.solve(cuda(w.f))
+    assert e.value.status == 4
+    p.factor("c64")
+    with pytest.raises(H.HelmError) as e:
+        p.solve(cuda(w.f), restart=0)
+    assert e.value.status == 1
+    u, info, _ = p.solve(cuda(w.f), maxit=2, raise_on_noconv=False)
+    assert info[0][0] == 2 and info[0][1] > 1e-6
+    with pytest.raises(H.HelmError) as e:
+        p.solve(cuda(w.f), maxit=2)
+    assert e.value.status == 5
+    with pytest.raises(H.HelmError):
+        H.Problem(w.n, w.n, w.h, w.omega, cuda(w.m2, torch.float64), 2, 2, [0, 70, 60], [0, 64, 127])
+    p.close()
