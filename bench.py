@@ -1,0 +1,375 @@
+#!/usr/bin/env python
+"""Throughput of the sweeping-preconditioned FGMRES solve on one GB300.
+
+Metric: unknowns x RHS solved per second to a true relative residual of 1e-6
+(the paper times only the GMRES phase, Section 6; the subdomain factors are
+built once, outside the timed region, and their time is reported beside it).
+
+Workload (the configuration the metric is quoted on): 1023 x 1023 grid,
+8 x 8 checkerboard (128-node subdomains, the last row/column 127), three-layer
+medium with a smooth +-10% random perturbation at 8 points per wavelength,
+one Gaussian source; complex64 subdomain factors and preconditioner inside
+FP64 flexible GMRES.  One step = one complete solve of that system.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+N > 1 (torchrun) runs independent replicas, one per GPU (the path does not
+exchange data between solves): weak scaling, value = all ranks' work / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "unknowns×RHS solved/s to rel. residual 1e-6 (mixed vs FP64, 1 GB300); % of roofline"
+UNIT = "unknowns*RHS/s"
+WORKLOAD = "plain_mixed"
+# DRAM traffic of one stage-kernel launch measured by ncu, keyed by the sha256 of
+# the kernel source it was measured on (None once the source changes).
+NCU_TRAFFIC = {}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--prec", default="c64", choices=["c64", "c128"])
+    ap.add_argument("--sched", default="BSP", choices=["BSP", "SP"])
+    ap.add_argument("--restart", type=int, default=200)
+    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--no-fp64-form", action="store_true", help="skip the all-FP64 comparison solve")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-iters", type=int, default=2, help="oracle FGMRES iterations per CPU sample")
+    return ap.parse_args()
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_hash():
+    src = os.path.join(ROOT, "paper_2209_10886_gb300", "csrc", "k_stage.cu")
+    return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- CPU oracle
+ORACLE_SAMPLE = r"""
+import json, os, sys, time
+sys.path.insert(0, {root!r})
+import numpy as np
+import workloads as W
+from oracle import Decomposition, Sweeper, assemble_operator, fgmres
+w = W.workload({workload!r})
+A = assemble_operator(w.n, w.h, w.omega, w.m2)
+dec = Decomposition(w.n, w.h, w.omega, w.m2, w.xcuts, w.ycuts)
+sw = Sweeper(dec)
+t0 = time.perf_counter()
+for i in dec.subdomains:
+    dec.local_solver(i)
+t_factor = time.perf_counter() - t0
+b = w.h ** 2 * w.f[0]
+times = []
+for rep in range({reps}):
+    t0 = time.perf_counter()
+    x, it, rr = fgmres(lambda v: A @ v, lambda v: sw.precondition(v, {sched!r}), b, tol=1e-300,
+                       restart={restart}, maxit={iters})
+    times.append((time.perf_counter() - t0) / it)
+print(json.dumps(dict(t_factor=t_factor, t_iter=times, iters=it)))
+"""
+
+
+def oracle_iterations(sched, restart):
+    """The oracle's own FGMRES iteration count on the workload, if recorded."""
+    p = os.path.join(ROOT, "oracle", "reference_counts.json")
+    try:
+        d = json.load(open(p))
+        e = d[WORKLOAD][f"{sched}_restart{restart}"]
+        return int(e["iterations"]), "oracle FGMRES to 1e-6 (oracle/reference_counts.json)"
+    except Exception:
+        return None, None
+
+
+def run_oracle_sample(sched, restart, iters, reps):
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = "1"
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    code = ORACLE_SAMPLE.format(root=ROOT, workload=WORKLOAD, sched=sched, restart=max(restart, iters),
+                                iters=iters, reps=reps)
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=1800)
+    if r.returncode != 0:
+        raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+# ------------------------------------------------------------------- arms
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import workloads as W
+    w = W.workload(WORKLOAD)
+    ni, src = oracle_iterations(args.sched, args.restart)
+    res = run_oracle_sample(args.sched, args.restart, args.cpu_iters, args.warmup + args.steps)
+    t_iter = statistics.median(res["t_iter"][args.warmup:] or res["t_iter"])
+    if ni is None:
+        ni, src = 1, "no recorded oracle iteration count: value is per FGMRES iteration"
+    t_solve = t_iter * ni
+    value = w.N * w.nrhs / t_solve
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_iter * args.cpu_iters * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+        "config": {"workload": w.description, "n": w.n, "N1": w.N1, "N2": w.N2, "nrhs": w.nrhs,
+                   "sched": args.sched, "restart": args.restart, "tol": args.tol,
+                   "oracle_iterations": ni, "iterations_source": src},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{args.cpu_iters} oracle FGMRES iterations per step (scipy splu local solves, "
+                                   f"one thread; {len(os.sched_getaffinity(0))} host cores available), "
+                                   f"t/iteration {t_iter:.3f} s x {ni} iterations; factorisation "
+                                   f"{res['t_factor']:.1f} s excluded like on the GPU"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def gpu_arm(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import workloads as W
+    from paper_2209_10886_gb300 import Problem, helm
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    w = W.workload(WORKLOAD)
+    m2 = torch.as_tensor(w.m2, dtype=torch.float64, device=dev)
+    f = torch.as_tensor(w.f, dtype=torch.complex128, device=dev)
+    p = Problem(w.n, w.n, w.h, w.omega, m2, w.N1, w.N2, w.xcuts, w.ycuts)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    p.factor(args.prec)
+    torch.cuda.synchronize()
+    factor_ms = (time.perf_counter() - t0) * 1e3
+    st = torch.cuda.current_stream()
+    u = torch.empty_like(f)
+
+    def solve():
+        _, info, _ = p.solve(f, u=u, restart=args.restart, maxit=3000, tol=args.tol, sched=args.sched)
+        return info[0]
+
+    for _ in range(args.warmup):
+        info = solve()
+    clocks = ClockSampler(local)
+    clocks.start()
+    helm.profile(p, True)
+    l0 = helm.launch_count()
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    iters = []
+    for _ in range(args.steps):
+        info = solve()
+        iters.append(info)
+    e1.record(st)
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    launches = helm.launch_count() - l0
+    stage = helm.profile_read(p, "stage")
+    trace = helm.profile_read(p, "trace")
+    matv = helm.profile_read(p, "matvec")
+    orth = helm.profile_read(p, "ortho")
+    helm.profile(p, False)
+    clk = clocks.stop()
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    relres = info[1]
+
+    # true residual on the host with the oracle's sparse matrix (property check at full size)
+    check = None
+    if rank == 0:
+        from oracle import assemble_operator
+        A = assemble_operator(w.n, w.h, w.omega, w.m2)
+        uh = u.cpu().numpy()[0]
+        bh = w.h ** 2 * w.f[0]
+        check = float(np.linalg.norm(bh - A @ uh) / np.linalg.norm(bh))
+
+    # end to end through the public API with host buffers
+    fh = torch.empty(f.shape, dtype=f.dtype, pin_memory=True)
+    fh.copy_(torch.as_tensor(w.f))
+    uh_pinned = torch.empty_like(fh, pin_memory=True)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        fd = fh.to(dev, non_blocking=True)
+        ud, info2, _ = p.solve(fd, restart=args.restart, maxit=3000, tol=args.tol, sched=args.sched)
+        uh_pinned.copy_(ud, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    # the all-FP64 form on the same GPU (one solve), for the mixed-vs-FP64 speedup
+    fp64 = None
+    if not args.no_fp64_form and args.prec == "c64":
+        q = Problem(w.n, w.n, w.h, w.omega, m2, w.N1, w.N2, w.xcuts, w.ycuts)
+        q.factor("c128")
+        _, i64, _ = q.solve(f, restart=args.restart, maxit=3000, tol=args.tol, sched=args.sched)  # warm
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(st)
+        _, i64, _ = q.solve(f, restart=args.restart, maxit=3000, tol=args.tol, sched=args.sched)
+        a1.record(st)
+        torch.cuda.synchronize()
+        ms64 = a0.elapsed_time(a1)
+        fp64 = {"value": w.N * w.nrhs / (ms64 / 1e3), "ms_per_step": ms64, "iterations": i64[0][0],
+                "relres": i64[0][1], "speedup_mixed_over_fp64": ms64 / ms}
+        q.close()
+
+    if rank != 0:
+        return
+    total_units = w.N * w.nrhs * world
+    value = total_units / (ms / 1e3)
+    peak, peak_src = peaks()
+    achieved = stage[2] / (stage[1] / 1e3) / 1e9 if stage[1] > 0 else 0.0
+    traffic = NCU_TRAFFIC.get(kernel_hash())
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        try:
+            res = run_oracle_sample(args.sched, args.restart, args.cpu_iters, 1)
+            t_iter = res["t_iter"][-1]
+            ni, src = oracle_iterations(args.sched, args.restart)
+            if ni is None:
+                ni = iters[-1][0]
+                src = "GPU mixed-form iteration count (no recorded oracle count)"
+            cpu = {"value": w.N * w.nrhs / (t_iter * ni), "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": f"{args.cpu_iters} oracle FGMRES iterations after the local splu factorisations "
+                             f"(one thread; {len(os.sched_getaffinity(0))} host cores available): "
+                             f"{t_iter:.3f} s per iteration x {ni} iterations ({src})"}
+        except Exception as e:  # the baseline must not hide the GPU line
+            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {e}"[:300]}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "c64+f64" if args.prec == "c64" else "c128", "data": "synthetic",
+        "config": {
+            "workload": w.description, "n": w.n, "N1": w.N1, "N2": w.N2, "nrhs": w.nrhs, "unknowns": w.N,
+            "prec": args.prec, "sched": args.sched, "restart": args.restart, "tol": args.tol,
+            "transmission": "optimized, scale 1.0", "iterations": iters[-1][0], "relres": relres,
+            "relres_host_check": check, "factor_ms": factor_ms, "factor_bytes": p.info()["factor_bytes"],
+            "l2": "inputs larger than L2: every preconditioner application streams the 1.07 GB of factors",
+            "parallelism": f"replicas x{world}",
+            "kernel_time_ms_per_step": {"stage": stage[1] / args.steps, "trace": trace[1] / args.steps,
+                                        "matvec": matv[1] / args.steps, "ortho": orth[1] / args.steps},
+            "launches_per_step": {"stage": stage[0] / args.steps, "trace": trace[0] / args.steps},
+            "fp64_form": fp64,
+        },
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "stage_kernel (fused subdomain solve + transmission)",
+                     "launches": stage[0], "peak_source": f"hbm_gbs of {peak_src}"},
+        "clocks": clk,
+        "e2e": {"value": total_units / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(f.numel() * 16),
+                "d2h_bytes_per_step": int(f.numel() * 16)},
+        "gpu_launches": launches,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    p.close()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -96,7 +96,7 @@ typedef enum { HELM_TC_OPTIMIZED = 0, HELM_TC_IMPEDANCE = 1 } helm_transmission;
 
 typedef struct {
     int transmission;   /* helm_transmission; default HELM_TC_OPTIMIZED */
-    double tc_scale;    /* s of HELM_TC_OPTIMIZED; default 1.5 */
+    double tc_scale;    /* s of HELM_TC_OPTIMIZED; default 1.0 */
 } helm_setup_opts;
 
 typedef struct {
@@ -193,6 +193,33 @@ helm_status helm_schedule_info(int N1, int N2, int sched, int* steps, int* stage
  * 2 N_e interface unknowns (trace points), bytes of the current factors. */
 helm_status helm_problem_info(const helm_problem* p, long long* n_unknowns, int* n_subdomains,
                               long long* n_trace, long long* factor_bytes);
+
+/* Kernel classes of the library's own launches, for helm_profile_read. */
+typedef enum {
+    HELM_K_STAGE = 0,      /* fused block-tridiagonal subdomain solve + transmission */
+    HELM_K_MATVEC = 1,     /* five-point operator (matvec and true residual) */
+    HELM_K_ORTHO = 2,      /* Gram-Schmidt dot products and updates, solution update */
+    HELM_K_OTHER = 3,      /* norms, reductions, Hessenberg, scaling, adjoint */
+    HELM_K_TRACE = 4       /* interface stages: boundary-operator GEMV + transmission */
+} helm_kernel_class;
+
+typedef struct {
+    long long launches;    /* launches recorded since profiling was enabled */
+    double ms;             /* summed device time between CUDA events recorded on the
+                              launch stream immediately before and after each launch */
+    double bytes;          /* algorithmic bytes those launches must move (HBM reads +
+                              writes of the data they touch, counted once) */
+} helm_kstat;
+
+/* Number of CUDA kernel launches issued by the library in this process. */
+long long helm_launch_count(void);
+
+/* Enable (on != 0) or disable per-launch event timing on handle p; enabling
+ * resets the statistics.  Timing adds two event records per launch. */
+helm_status helm_profile(helm_problem* p, int on);
+
+/* Statistics of one kernel class (synchronises the device to read the events). */
+helm_status helm_profile_read(helm_problem* p, int kernel_class, helm_kstat* out);
 
 #ifdef __cplusplus
 }

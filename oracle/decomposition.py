@@ -69,7 +69,7 @@ class Decomposition:
     owns 0-based x-nodes ``xcuts[i1-1] .. xcuts[i1]-1``.
     """
 
-    def __init__(self, n, h, omega, m2, xcuts, ycuts, transmission="optimized", tc_scale=1.5):
+    def __init__(self, n, h, omega, m2, xcuts, ycuts, transmission="optimized", tc_scale=1.0):
         self.n, self.h, self.omega = n, h, omega
         self.transmission, self.tc_scale = transmission, tc_scale
         self.m2 = np.asarray(m2, dtype=np.float64).reshape(n, n)   # [b, a]

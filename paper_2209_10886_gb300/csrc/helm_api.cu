@@ -14,6 +14,12 @@
 
 size_t factor_work_elems(int max_mx, size_t elem);
 
+// ------------------------------------------------------------ launch count
+#include <atomic>
+static std::atomic<long long> g_launches{0};
+void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+extern "C" long long helm_launch_count(void) { return g_launches.load(); }
+
 // ------------------------------------------------------------------ errors
 static thread_local std::string g_err;
 void set_error(const std::string& m) { g_err = m; }
@@ -62,6 +68,7 @@ std::vector<StageDesc> build_schedule(int sched, int N1, int N2, const std::vect
     auto mk_stage = [](std::vector<int> subs, int src, int in0, int in1, int mask, int dst, int dst2, int base,
                        int sub, int fin) {
         StageDesc s;
+        s.iface = (src == 0 && !fin) ? 1 : 0;     // zero source, traces only: boundary-operator GEMV
         s.subs = std::move(subs);
         s.src = src; s.in0 = in0; s.in1 = in1; s.mask = mask;
         s.dst = dst; s.dst2 = dst2; s.base = base; s.sub = sub; s.final_ = fin; s.sub_off = 0;
@@ -145,7 +152,7 @@ struct helm_problem {
     std::vector<SubHost> subs;
     std::vector<std::vector<int>> ondiag;
     std::vector<int> all;
-    int max_mx = 0, max_my = 0;
+    int max_mx = 0, max_my = 0, max_Lb = 0;
     long long ntrace = 0;
     int nslots = 0;
     std::vector<StageDesc> sched[2];
@@ -161,6 +168,8 @@ struct helm_problem {
     int factored = 0;
     int prec = HELM_PREC_C128;
     void* d_X = nullptr;
+    void* d_K = nullptr;             // boundary operators of all subdomains
+    size_t K_bytes = 0;
     size_t X_bytes = 0;
 
     // preconditioner workspace
@@ -183,8 +192,62 @@ struct helm_problem {
     double* d_jpart = nullptr;
     int aw_nsrc = 0, aw_nrec = 0;
 
+    // per-kernel-class event timing (helm_profile)
+    struct KProf {
+        std::vector<cudaEvent_t> a, b;
+        size_t used = 0;
+        double bytes = 0;
+    };
+    KProf prof[5];
+    int prof_on = 0;
+
     long long N() const { return (long long)nx * ny; }
 };
+
+// event pair around one launch of class k (no-op when profiling is off)
+static void prof_begin(helm_problem* p, int k, cudaStream_t st) {
+    if (!p->prof_on) return;
+    auto& q = p->prof[k];
+    if (q.used == q.a.size()) {
+        cudaEvent_t e1, e2;
+        cudaEventCreate(&e1);
+        cudaEventCreate(&e2);
+        q.a.push_back(e1);
+        q.b.push_back(e2);
+    }
+    cudaEventRecord(q.a[q.used], st);
+}
+static void prof_end(helm_problem* p, int k, double bytes, cudaStream_t st) {
+    if (!p->prof_on) return;
+    auto& q = p->prof[k];
+    cudaEventRecord(q.b[q.used], st);
+    ++q.used;
+    q.bytes += bytes;
+}
+
+extern "C" helm_status helm_profile(helm_problem* p, int on) {
+    if (!p) { set_error("helm_profile: NULL handle"); return HELM_ERR_ARG; }
+    for (auto& q : p->prof) { q.used = 0; q.bytes = 0; }
+    p->prof_on = on != 0;
+    return HELM_OK;
+}
+
+extern "C" helm_status helm_profile_read(helm_problem* p, int k, helm_kstat* out) {
+    if (!p || !out || k < 0 || k > 4) { set_error("helm_profile_read: bad argument"); return HELM_ERR_ARG; }
+    auto& q = p->prof[k];
+    double ms = 0;
+    for (size_t i = 0; i < q.used; ++i) {
+        cudaError_t e = cudaEventSynchronize(q.b[i]);
+        if (e != cudaSuccess) return cuda_status(e, "helm_profile_read");
+        float t = 0;
+        cudaEventElapsedTime(&t, q.a[i], q.b[i]);
+        ms += t;
+    }
+    out->launches = (long long)q.used;
+    out->ms = ms;
+    out->bytes = q.bytes;
+    return HELM_OK;
+}
 
 static void free_pc_ws(helm_problem* p) {
     for (auto& b : p->d_trace) dfree(b);
@@ -220,7 +283,7 @@ extern "C" void helm_default_opts(helm_opts* o) {
 extern "C" void helm_default_setup_opts(helm_setup_opts* o) {
     if (!o) return;
     o->transmission = HELM_TC_OPTIMIZED;
-    o->tc_scale = 1.5;
+    o->tc_scale = 1.0;
 }
 
 extern "C" const char* helm_last_error(void) { return g_err.c_str(); }
@@ -344,6 +407,21 @@ extern "C" helm_status helm_setup(int n_x, int n_y, double h, double omega, cons
             const int opp = side ^ 1;           // W<->E, S<->N
             s.dev.tout[side] = p->subs[subid[(j2 - 1) * N1 + (j1 - 1)]].dev.tin[opp];
         }
+    // interface boundary vector (W, E, S, N interface sides) and boundary-operator offsets
+    long long koff = 0;
+    for (auto& s : p->subs) {
+        int lb = 0;
+        for (int side = 0; side < 4; ++side) {
+            s.dev.bo[side] = -1;
+            if (s.dev.tin[side] < 0) continue;
+            s.dev.bo[side] = lb;
+            lb += (side == SW || side == SE) ? s.dev.my : s.dev.mx;
+        }
+        s.dev.Lb = lb;
+        s.dev.koff = koff;
+        koff += (long long)lb * lb;
+        p->max_Lb = std::max(p->max_Lb, lb);
+    }
 
     // stage lists and their subdomain arrays
     std::vector<int> all_stage_subs;
@@ -408,7 +486,12 @@ extern "C" helm_status helm_destroy(helm_problem* p) {
     free_adj(p);
     dfree(p->d_m2); dfree(p->d_adiag); dfree(p->d_dloc); dfree(p->d_subtab);
     dfree(p->d_tc128); dfree(p->d_tc64); dfree(p->d_stage_subs);
+    for (auto& q : p->prof) {
+        for (auto e : q.a) cudaEventDestroy(e);
+        for (auto e : q.b) cudaEventDestroy(e);
+    }
     if (p->d_X) cudaFree(p->d_X);
+    if (p->d_K) cudaFree(p->d_K);
     delete p;
     return HELM_OK;
 }
@@ -421,6 +504,46 @@ extern "C" helm_status helm_problem_info(const helm_problem* p, long long* n_unk
     if (n_trace) *n_trace = p->ntrace;
     if (factor_bytes) *factor_bytes = (long long)p->X_bytes;
     return HELM_OK;
+}
+
+// ------------------------------------------------------ boundary operators
+// K_i = interface-boundary block of A_loc^{-1} for every subdomain: one batched
+// multi-RHS block solve per group of `NB` unit data (basis mode of the stage kernel).
+template <typename R>
+static helm_status build_boundary_operators_t(helm_problem* p, cudaStream_t st) {
+    using T = Cx<R>;
+    if (p->max_Lb == 0) return HELM_OK;
+    long long kel = 0;
+    for (auto& s : p->subs) kel += (long long)s.dev.Lb * s.dev.Lb;
+    cudaError_t e = cudaMalloc(&p->d_K, (size_t)kel * sizeof(T));
+    if (e != cudaSuccess) { p->d_K = nullptr; return cuda_status(e, "precond_factor: allocating boundary operators"); }
+    p->K_bytes = (size_t)kel * sizeof(T);
+    const int NB = 64;
+    void* yws = nullptr;
+    e = cudaMalloc(&yws, (size_t)p->N() * NB * sizeof(T));
+    if (e != cudaSuccess) return cuda_status(e, "precond_factor: allocating the basis workspace");
+    StageArgs<R> a{};
+    a.subtab = p->d_subtab;
+    a.nx = p->nx; a.ny = p->ny;
+    a.nrhs = NB;
+    a.wstride = p->N();
+    a.X = (const T*)p->d_X;
+    a.tc = sizeof(R) == 4 ? (const TraceCoef<T>*)p->d_tc64 : (const TraceCoef<T>*)p->d_tc128;
+    a.yws = (T*)yws;
+    a.K = (T*)p->d_K;
+    for (int c0 = 0; c0 < p->max_Lb && e == cudaSuccess; c0 += NB) {
+        a.col0 = c0;
+        e = launch_basis<R>(a, (int)p->subs.size(), NB, p->max_mx, p->max_my, st);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(yws);
+    if (e != cudaSuccess) return cuda_status(e, "precond_factor: boundary operators");
+    return HELM_OK;
+}
+
+static helm_status build_boundary_operators(helm_problem* p, cudaStream_t st) {
+    return p->prec == HELM_PREC_C64 ? build_boundary_operators_t<float>(p, st)
+                                    : build_boundary_operators_t<double>(p, st);
 }
 
 // ----------------------------------------------------------------- factor
@@ -442,6 +565,7 @@ extern "C" helm_status precond_factor(helm_problem* p, helm_prec prec, void* str
     const size_t bytes = (size_t)xoff * elem;
     HELM_CUDA_TRY(cudaStreamSynchronize(st));
     if (p->d_X) { cudaFree(p->d_X); p->d_X = nullptr; p->X_bytes = 0; p->factored = 0; }
+    if (p->d_K) { cudaFree(p->d_K); p->d_K = nullptr; p->K_bytes = 0; }
     cudaError_t e = cudaMalloc(&p->d_X, bytes);
     if (e != cudaSuccess) { p->d_X = nullptr; return cuda_status(e, "precond_factor: allocating the factors"); }
     p->X_bytes = bytes;
@@ -476,6 +600,10 @@ extern "C" helm_status precond_factor(helm_problem* p, helm_prec prec, void* str
             return HELM_ERR_ARG;
         }
     p->prec = prec;
+    {
+        const helm_status ks = build_boundary_operators(p, st);
+        if (ks != HELM_OK) return ks;
+    }
     p->factored = 1;
     // the workspace depends on the precision
     free_pc_ws(p);
@@ -514,6 +642,36 @@ static helm_status run_precond_t(helm_problem* p, int sched, const double2* r, d
     T* buf[3] = {(T*)p->d_trace[0], (T*)p->d_trace[1], (T*)p->d_trace[2]};
     auto B = [&](int id) -> T* { return id < 0 ? nullptr : buf[id]; };
     for (const StageDesc& sd : p->sched[sched]) {
+        if (sd.iface) {
+            IfaceArgs<R> ia{};
+            ia.subtab = p->d_subtab;
+            ia.subs = p->d_stage_subs + sd.sub_off;
+            ia.nrhs = nrhs;
+            ia.ntrace = p->ntrace;
+            ia.K = (const T*)p->d_K;
+            ia.tc = sizeof(R) == 4 ? (const TraceCoef<T>*)p->d_tc64 : (const TraceCoef<T>*)p->d_tc128;
+            ia.gin0 = B(sd.in0); ia.gin1 = B(sd.in1);
+            ia.mask = sd.mask;
+            ia.dst = B(sd.dst); ia.dst2 = B(sd.dst2); ia.base = B(sd.base); ia.sub = B(sd.sub);
+            double bytes = 0;
+            if (p->prof_on) {
+                const double sT = sizeof(T);
+                for (int id : sd.subs) {
+                    const SubDev& d = p->subs[id].dev;
+                    double rows = 0;
+                    for (int sde = 0; sde < 4; ++sde)
+                        if ((sd.mask & (1 << sde)) && d.bo[sde] >= 0) rows += (sde == SW || sde == SE) ? d.my : d.mx;
+                    const double io = d.Lb * sT * ((sd.in0 >= 0) + (sd.in1 >= 0)) +
+                                      rows * sT * (1 + (sd.dst2 >= 0) + (sd.base >= 0) + (sd.sub >= 0));
+                    bytes += rows * d.Lb * sT + io * nrhs;
+                }
+            }
+            prof_begin(p, HELM_K_TRACE, st);
+            cudaError_t e = launch_iface<R>(ia, (int)sd.subs.size(), 2 * (p->max_mx + p->max_my), p->max_Lb, st);
+            prof_end(p, HELM_K_TRACE, bytes, st);
+            if (e != cudaSuccess) return cuda_status(e, "interface stage launch");
+            continue;
+        }
         StageArgs<R> a{};
         a.subtab = p->d_subtab;
         a.subs = p->d_stage_subs + sd.sub_off;
@@ -531,7 +689,31 @@ static helm_status run_precond_t(helm_problem* p, int sched, const double2* r, d
         a.z = sd.final_ ? z : nullptr;
         a.zscale = rsc;
         a.yws = (T*)p->d_yws;
-        cudaError_t e = launch_stage<R>(a, (int)sd.subs.size(), p->max_mx, st);
+        double bytes = 0;
+        if (p->prof_on) {
+            // algorithmic bytes: each X_r once per stage (shared by all RHS), the
+            // solve workspace y written and read once, source read, volume output
+            // written, incoming traces read, outgoing traces (and their base/sub) moved
+            const double sT = sizeof(T);
+            for (int id : sd.subs) {
+                const SubDev& d = p->subs[id].dev;
+                double per_rhs = 2.0 * (d.my - 1) * d.mx * sT;
+                if (sd.src) per_rhs += 16.0 * d.mx * d.my;
+                if (sd.final_) per_rhs += 16.0 * d.mx * d.my;
+                for (int sde = 0; sde < 4; ++sde) {
+                    if (d.tin[sde] < 0) continue;
+                    const double len = (sde == SW || sde == SE) ? d.my : d.mx;
+                    if (sd.in0 >= 0) per_rhs += len * sT;
+                    if (sd.in1 >= 0) per_rhs += len * sT;
+                    if (sd.mask & (1 << sde))
+                        per_rhs += len * sT * (1 + (sd.dst2 >= 0) + (sd.base >= 0) + (sd.sub >= 0));
+                }
+                bytes += (2.0 * d.my - 1) * d.mx * (double)d.mx * sT + per_rhs * nrhs;
+            }
+        }
+        prof_begin(p, HELM_K_STAGE, st);
+        cudaError_t e = launch_stage<R>(a, (int)sd.subs.size(), p->max_mx, p->max_my, st);
+        prof_end(p, HELM_K_STAGE, bytes, st);
         if (e != cudaSuccess) return cuda_status(e, "stage launch");
     }
     return HELM_OK;
@@ -633,8 +815,8 @@ static helm_status gmres_impl(helm_problem* p, const double2* f, double2* u, int
 
     while (true) {
         // r = h^2 f - A u into V_0, beta = ||r||
-        launch_residual(p->d_adiag, p->nx, p->ny, f, h2, u, p->d_V, nrhs, nullptr, p->d_rpart, nb, st);
-        launch_reduce_rows(p->d_rpart, nb, nrhs, p->d_rn, 1, st);
+        const int nrp = launch_residual(p->d_adiag, p->nx, p->ny, f, h2, u, p->d_V, nrhs, nullptr, p->d_rpart, nb, st);
+        launch_reduce_rows(p->d_rpart, nrp, nrhs, p->d_rn, 1, st);
         HELM_CUDA_TRY(cudaMemcpyAsync(rn.data(), p->d_rn, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
         HELM_CUDA_TRY(cudaStreamSynchronize(st));
         bool any = false;
@@ -667,15 +849,27 @@ static helm_status gmres_impl(helm_problem* p, const double2* f, double2* u, int
             // z_j = M^{-1} v_j ; w = A z_j
             s = run_precond(p, o.sched, Vj, Zj, nrhs, st);
             if (s != HELM_OK) return s;
+            const double vb = 16.0 * N * nrhs;   // bytes of one field for all RHS
+            prof_begin(p, HELM_K_MATVEC, st);
             launch_matvec(p->d_adiag, p->nx, p->ny, Zj, Vn, nrhs, st);
+            prof_end(p, HELM_K_MATVEC, 2 * vb + 16.0 * N, st);
             // classical Gram-Schmidt, twice
+            prof_begin(p, HELM_K_ORTHO, st);
             launch_mdot(p->d_V, vsk, N, j + 1, Vn, N, N, nrhs, p->d_active, p->d_cpart, nb, st);
+            prof_end(p, HELM_K_ORTHO, (j + 2) * vb, st);
             launch_reduce_cpartials(p->d_cpart, nb, j + 1, p->d_h1, ld, nrhs, st);
+            prof_begin(p, HELM_K_ORTHO, st);
             launch_mupdate(p->d_V, vsk, N, j + 1, nullptr, p->d_h1, ld, -1.0, Vn, N, N, nrhs, p->d_active, nullptr, nb, st);
+            prof_end(p, HELM_K_ORTHO, (j + 3) * vb, st);
+            prof_begin(p, HELM_K_ORTHO, st);
             launch_mdot(p->d_V, vsk, N, j + 1, Vn, N, N, nrhs, p->d_active, p->d_cpart, nb, st);
+            prof_end(p, HELM_K_ORTHO, (j + 2) * vb, st);
             launch_reduce_cpartials(p->d_cpart, nb, j + 1, p->d_h2, ld, nrhs, st);
+            prof_begin(p, HELM_K_ORTHO, st);
             launch_mupdate(p->d_V, vsk, N, j + 1, nullptr, p->d_h2, ld, -1.0, Vn, N, N, nrhs, p->d_active, p->d_rpart, nb, st);
+            prof_end(p, HELM_K_ORTHO, (j + 3) * vb, st);
             launch_reduce_rows(p->d_rpart, nb, nrhs, p->d_rn, 1, st);
+            count_launch();
             add_cols_kernel<<<nrhs, 128, 0, st>>>(p->d_h1, p->d_h2, p->d_hsum, j + 1, nrhs, ld);
             launch_hessenberg_step(p->d_H, ld, (long long)ld * m, p->d_cs, p->d_sn, p->d_g, ld, p->d_hsum, ld, p->d_rn, j,
                                    nrhs, p->d_active, p->d_est, p->d_invh, st);

@@ -61,6 +61,12 @@ struct SubDev {
     long long xoff;            // element offset of X_1 of this subdomain in the factor array
     long long yoff;            // element offset of this subdomain's block in the solve workspace (per RHS)
     long long loff;            // offset of the node block in the local-diagonal array
+    // interface boundary vector of this subdomain: the points of its interface
+    // sides in the order W, E, S, N (outer sides skipped); bo[s] = offset of
+    // side s in it (-1: outer side), Lb = its length
+    int bo[4];
+    int Lb;
+    long long koff;            // element offset of the Lb x Lb boundary operator K in its array
 };
 
 // Trace-point coefficients of one interface edge point (beta_e = T_e h / 2):
@@ -73,6 +79,7 @@ template <typename T> struct TraceCoef { T cin, ca, cb; };
 enum Buf { BUF_NONE = -1, BUF_B = 0, BUF_X = 1, BUF_Y = 2 };
 
 struct StageDesc {
+    int iface;                 // 1: zero volume source and no volume output: boundary-operator GEMV
     std::vector<int> subs;     // subdomains solved in this stage
     int src;                   // 1: volume source r_i, 0: zero source
     int in0, in1;              // incoming data = in0 (+ in1), Buf ids
@@ -102,7 +109,29 @@ template <typename R> struct StageArgs {
     double2* z;                // volume output (final stage) or null
     const double* zscale;      // per-RHS factor applied to the output, or null = 1
     T* yws;                    // solve workspace
+    // basis mode (boundary operator construction): RHS k of CTA column block y is
+    // the unit datum at interface boundary point col0 + y*NR + k; the boundary
+    // values of the solution are stored as that row of K
+    T* K;
+    int col0;
 };
+
+// launch parameters of the interface (boundary-operator) stage kernel
+template <typename R> struct IfaceArgs {
+    using T = Cx<R>;
+    const SubDev* subtab;
+    const int* subs;
+    int nrhs;
+    long long ntrace;
+    const T* K;
+    const TraceCoef<T>* tc;
+    const T* gin0; const T* gin1;
+    int mask;
+    T* dst; T* dst2; const T* base; const T* sub;
+};
+
+// ------------------------------------------------------------ launch count
+void count_launch(int n = 1);
 
 // ------------------------------------------------------------ error helpers
 void set_error(const std::string& msg);
@@ -130,11 +159,16 @@ cudaError_t launch_factor(const SubDev* subtab, int nsub, int max_mx, const doub
                           Cx<R>* X, Cx<R>* work, size_t work_stride, int* info, cudaStream_t st);
 // stage
 template <typename R>
-cudaError_t launch_stage(const StageArgs<R>& a, int nactive, int max_mx, cudaStream_t st);
+cudaError_t launch_stage(const StageArgs<R>& a, int nactive, int max_mx, int max_my, cudaStream_t st);
+// boundary operators K of all subdomains, columns [col0, col0 + ncols) per launch
+template <typename R>
+cudaError_t launch_basis(const StageArgs<R>& a, int nsub, int ncols, int max_mx, int max_my, cudaStream_t st);
+template <typename R>
+cudaError_t launch_iface(const IfaceArgs<R>& a, int nactive, int max_rows, int max_Lb, cudaStream_t st);
 // krylov / vector kernels
 void launch_matvec(const double2* adiag, int nx, int ny, const double2* u, double2* Au, int nrhs,
                    cudaStream_t st);
-void launch_residual(const double2* adiag, int nx, int ny, const double2* f, double fscale,
+int launch_residual(const double2* adiag, int nx, int ny, const double2* f, double fscale,
                      const double2* u, double2* r, int nrhs, const int* active, double* partial,
                      int nblk, cudaStream_t st);
 void launch_norm2_partial(const double2* v, long long n, int nrhs, long long stride, double* partial,

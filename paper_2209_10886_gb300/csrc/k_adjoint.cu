@@ -75,15 +75,18 @@ __global__ void gradient_kernel(const double2* __restrict__ U, const double2* __
 
 void launch_receiver_residual(const double2* u, long long N, const int* rec, int nrec, const double2* d, int nsrc,
                               double2* res, double* partial, cudaStream_t st) {
+    count_launch();
     receiver_residual_kernel<<<nsrc, 256, 0, st>>>(u, N, rec, nrec, d, res, partial);
 }
 void launch_adjoint_rhs(const double2* res, const int* rec, int nrec, int nsrc, long long N, double inv_h2,
                         double2* f_adj, cudaStream_t st) {
+    count_launch();
     adjoint_rhs_kernel<<<nsrc, 32, 0, st>>>(res, rec, nrec, N, inv_h2, f_adj);
 }
 void launch_gradient(const double2* U, const double2* Lt, const double* m2, int nx, int ny, double h, double omega,
                      int nsrc, double* grad, cudaStream_t st) {
     long long N = (long long)nx * ny;
     int nb = (int)min((N + 255) / 256, (long long)152 * 8);
+    count_launch();
     gradient_kernel<<<nb, 256, 0, st>>>(U, Lt, m2, nx, ny, h, omega, nsrc, grad);
 }

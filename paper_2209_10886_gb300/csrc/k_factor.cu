@@ -141,6 +141,7 @@ cudaError_t launch_factor(const SubDev* subtab, int nsub, int max_mx, const doub
     if (!use_smem && work == nullptr) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(factor_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    count_launch();
     factor_kernel<R><<<nsub, FT, smem, st>>>(subtab, dloc, X, work, work_stride, use_smem, info);
     return cudaGetLastError();
 }

@@ -41,40 +41,47 @@ __device__ __forceinline__ double2 apply_A(const double2* __restrict__ u, const 
     return make_double2(fma(ad.x, c.x, fma(-ad.y, c.y, -sx)), fma(ad.x, c.y, fma(ad.y, c.x, -sy)));
 }
 
+// grid: x covers a row of the grid in VT-wide segments, y strides over rows, z = RHS
 __global__ void matvec_kernel(const double2* __restrict__ adiag, int nx, int ny, const double2* __restrict__ u,
                               double2* __restrict__ Au) {
     const long long N = (long long)nx * ny;
-    const int k = blockIdx.y;
+    const int k = blockIdx.z;
+    const int a = blockIdx.x * VT + threadIdx.x;
+    if (a >= nx) return;
     const double2* uk = u + k * N;
-    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
-        const int a = (int)(p % nx), b = (int)(p / nx);
+    for (int b = blockIdx.y; b < ny; b += gridDim.y) {
+        const long long p = (long long)b * nx + a;
         Au[k * N + p] = apply_A(uk, adiag[p], p, a, b, nx, ny);
     }
 }
 
-// r = fscale f - A u, and per-block partial ||r||^2
+// r = fscale f - A u, and per-block partial ||r||^2 (partial index: y * gridDim.x + x)
 __global__ void residual_kernel(const double2* __restrict__ adiag, int nx, int ny, const double2* __restrict__ f,
                                 double fscale, const double2* __restrict__ u, double2* __restrict__ r,
                                 const int* __restrict__ active, double* __restrict__ partial) {
     __shared__ double sh[32];
     const long long N = (long long)nx * ny;
-    const int k = blockIdx.y;
+    const int k = blockIdx.z;
+    const int nb = gridDim.x * gridDim.y, bid = blockIdx.y * gridDim.x + blockIdx.x;
     if (active && !active[k]) {
-        if (threadIdx.x == 0) partial[(long long)k * gridDim.x + blockIdx.x] = 0.0;
+        if (threadIdx.x == 0) partial[(long long)k * nb + bid] = 0.0;
         return;
     }
+    const int a = blockIdx.x * VT + threadIdx.x;
     const double2* uk = u + k * N;
     double acc = 0.0;
-    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
-        const int a = (int)(p % nx), b = (int)(p / nx);
-        const double2 Av = apply_A(uk, adiag[p], p, a, b, nx, ny);
-        const double2 fv = f[k * N + p];
-        const double2 rv = make_double2(fma(fscale, fv.x, -Av.x), fma(fscale, fv.y, -Av.y));
-        r[k * N + p] = rv;
-        acc = fma(rv.x, rv.x, fma(rv.y, rv.y, acc));
+    if (a < nx) {
+        for (int b = blockIdx.y; b < ny; b += gridDim.y) {
+            const long long p = (long long)b * nx + a;
+            const double2 Av = apply_A(uk, adiag[p], p, a, b, nx, ny);
+            const double2 fv = f[k * N + p];
+            const double2 rv = make_double2(fma(fscale, fv.x, -Av.x), fma(fscale, fv.y, -Av.y));
+            r[k * N + p] = rv;
+            acc = fma(rv.x, rv.x, fma(rv.y, rv.y, acc));
+        }
     }
     acc = block_sum(acc, sh);
-    if (threadIdx.x == 0) partial[(long long)k * gridDim.x + blockIdx.x] = acc;
+    if (threadIdx.x == 0) partial[(long long)k * nb + bid] = acc;
 }
 
 __global__ void norm2_partial_kernel(const double2* __restrict__ v, long long n, long long stride,
@@ -287,55 +294,75 @@ int grid_for(long long n) {
 
 }  // namespace
 
-void launch_matvec(const double2* adiag, int nx, int ny, const double2* u, double2* Au, int nrhs, cudaStream_t st) {
-    dim3 g(grid_for((long long)nx * ny), nrhs);
-    matvec_kernel<<<g, VT, 0, st>>>(adiag, nx, ny, u, Au);
+static dim3 rows_grid(int nx, int ny, int nblk, int nrhs) {
+    const int gx = (nx + VT - 1) / VT;
+    const int gy = max(1, min(ny, nblk / gx));
+    return dim3(gx, gy, nrhs);
 }
-void launch_residual(const double2* adiag, int nx, int ny, const double2* f, double fscale, const double2* u,
-                     double2* r, int nrhs, const int* active, double* partial, int nblk, cudaStream_t st) {
-    dim3 g(nblk, nrhs);
+void launch_matvec(const double2* adiag, int nx, int ny, const double2* u, double2* Au, int nrhs, cudaStream_t st) {
+    count_launch();
+    matvec_kernel<<<rows_grid(nx, ny, 152 * 16, nrhs), VT, 0, st>>>(adiag, nx, ny, u, Au);
+}
+// returns the number of partials per RHS written into `partial` (<= nblk)
+int launch_residual(const double2* adiag, int nx, int ny, const double2* f, double fscale, const double2* u,
+                    double2* r, int nrhs, const int* active, double* partial, int nblk, cudaStream_t st) {
+    const dim3 g = rows_grid(nx, ny, nblk, nrhs);
+    count_launch();
     residual_kernel<<<g, VT, 0, st>>>(adiag, nx, ny, f, fscale, u, r, active, partial);
+    return (int)(g.x * g.y);
 }
 void launch_norm2_partial(const double2* v, long long n, int nrhs, long long stride, double* partial, int nblk,
                           cudaStream_t st) {
     dim3 g(nblk, nrhs);
+    count_launch();
     norm2_partial_kernel<<<g, VT, 0, st>>>(v, n, stride, partial);
 }
 void launch_reduce_rows(const double* partial, int nblk, int nrows, double* out, int mode, cudaStream_t st) {
+    count_launch();
     reduce_rows_kernel<<<nrows, VT, 0, st>>>(partial, nblk, out, mode);
 }
 void launch_mdot(const double2* V, long long vsk, long long vsr, int nvec, const double2* w, long long ws, long long n,
                  int nrhs, const int* active, double2* partial, int nblk, cudaStream_t st) {
     dim3 g(nblk, nrhs);
+    count_launch();
     mdot_kernel<<<g, VT, 0, st>>>(V, vsk, vsr, nvec, w, ws, n, active, partial);
 }
 void launch_reduce_cpartials(const double2* partial, int nblk, int nrows, double2* out, long long os, int nrhs,
                              cudaStream_t st) {
     dim3 g(nrows, nrhs);
+    count_launch();
     reduce_cpartials_kernel<<<g, VT, 0, st>>>(partial, nblk, nrows, out, os);
 }
 void launch_mupdate(const double2* V, long long vsk, long long vsr, int nvec, const int* nvec_rhs, const double2* coef,
                     long long cs, double sign, double2* w, long long ws, long long n, int nrhs, const int* active,
                     double* norm_partial, int nblk, cudaStream_t st) {
     dim3 g(nblk, nrhs);
+    count_launch();
     mupdate_kernel<<<g, VT, 0, st>>>(V, vsk, vsr, nvec, nvec_rhs, coef, cs, sign, w, ws, n, active, norm_partial);
 }
 void launch_scale_vec(double2* dst, long long ds, const double2* src, long long ss, const double* inv, long long n,
                       int nrhs, const int* active, cudaStream_t st) {
     dim3 g(grid_for(n), nrhs);
+    count_launch();
     scale_vec_kernel<<<g, VT, 0, st>>>(dst, ds, src, ss, inv, n, active);
 }
 void launch_hessenberg_step(double2* H, int ldh, long long hs, double2* cs, double2* sn, double2* g, int ldg,
                             const double2* hcol, long long hcs, const double* hnorm, int j, int nrhs, const int* active,
                             double* resid_est, double* inv_hnext, cudaStream_t st) {
+    count_launch();
     hessenberg_step_kernel<<<(nrhs + 31) / 32, 32, 0, st>>>(H, ldh, hs, cs, sn, g, ldg, hcol, hcs, hnorm, j, nrhs,
                                                            active, resid_est, inv_hnext);
 }
 void launch_hessenberg_solve(const double2* H, int ldh, long long hs, const double2* g, int ldg, const int* jcount,
                              double2* y, int ldy, int nrhs, cudaStream_t st) {
+    count_launch();
     hessenberg_solve_kernel<<<(nrhs + 31) / 32, 32, 0, st>>>(H, ldh, hs, g, ldg, jcount, y, ldy, nrhs);
 }
-void launch_sqrt_inplace(double* v, int n, cudaStream_t st) { sqrt_kernel<<<(n + 127) / 128, 128, 0, st>>>(v, n); }
+void launch_sqrt_inplace(double* v, int n, cudaStream_t st) {
+    count_launch();
+    sqrt_kernel<<<(n + 127) / 128, 128, 0, st>>>(v, n);
+}
 void launch_scale_from_norm(const double* norm2, double* inv, double* scale, int n, cudaStream_t st) {
+    count_launch();
     scale_from_norm_kernel<<<(n + 127) / 128, 128, 0, st>>>(norm2, inv, scale, n);
 }

@@ -102,6 +102,7 @@ void launch_setup_coeffs(const double* m2, int nx, int ny, double h, double omeg
                          double2* adiag, double2* dloc, const SubDev* subtab, cudaStream_t st) {
     long long N = (long long)nx * ny;
     int nb = (int)((N + 255) / 256);
+    count_launch();
     setup_coeffs_kernel<<<nb, 256, 0, st>>>(m2, nx, ny, h, omega, xcut, ycut, N1, N2, subid, transmission,
                                              tc_scale, adiag, dloc, subtab);
 }
@@ -111,6 +112,7 @@ void launch_trace_coeffs(const double* m2, int nx, double h, double omega, int t
                          int nslots, const SubDev* subtab, TraceCoef<double2>* tc128, TraceCoef<float2>* tc64,
                          cudaStream_t st) {
     if (nslots == 0) return;
+    count_launch();
     trace_coeffs_kernel<<<nslots, 128, 0, st>>>(m2, nx, h, omega, transmission, tc_scale, slot_sub, slot_side,
                                                 slot_off, slot_len, subtab, tc128, tc64);
 }

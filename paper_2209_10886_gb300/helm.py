@@ -135,7 +135,7 @@ class Problem:
     """
 
     def __init__(self, n_x, n_y, h, omega, m2, N1, N2, xcuts=None, ycuts=None,
-                 transmission="optimized", tc_scale=1.5):
+                 transmission="optimized", tc_scale=1.0):
         L = lib()
         if not (m2.is_cuda and m2.dtype == torch.float64 and m2.numel() == n_x * n_y):
             raise TypeError("m2 must be a float64 CUDA tensor with n_x*n_y values")
@@ -254,3 +254,31 @@ class MisfitFn(torch.autograd.Function):
     def backward(ctx, grad_output):
         (grad,) = ctx.saved_tensors
         return grad_output * grad, None, None, None, None
+
+
+# ------------------------------------------------------------------ profiling
+class HelmKStat(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_longlong), ("ms", ctypes.c_double), ("bytes", ctypes.c_double)]
+
+
+KERNEL_CLASS = {"stage": 0, "matvec": 1, "ortho": 2, "other": 3, "trace": 4}
+
+
+def launch_count() -> int:
+    """CUDA kernel launches issued by the library in this process."""
+    L = lib()
+    L.helm_launch_count.restype = ctypes.c_longlong
+    return int(L.helm_launch_count())
+
+
+def profile(problem: "Problem", on: bool = True):
+    _check(lib().helm_profile(problem._h, int(on)))
+
+
+def profile_read(problem: "Problem", kind: str):
+    """(launches, summed event ms, algorithmic bytes) of one kernel class."""
+    L = lib()
+    L.helm_profile_read.argtypes = [_vp, _i, ctypes.POINTER(HelmKStat)]
+    st = HelmKStat()
+    _check(L.helm_profile_read(problem._h, KERNEL_CLASS[kind], ctypes.byref(st)))
+    return st.launches, st.ms, st.bytes
