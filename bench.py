@@ -54,7 +54,34 @@ def parse():
     ap.add_argument("--no-fp64-form", action="store_true", help="skip the all-FP64 comparison solve")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=2, help="oracle FGMRES iterations per CPU sample")
+    ap.add_argument("--mode", default="solve", choices=["solve", "precond"],
+                    help="precond: factor once, then time --steps preconditioner applications only "
+                         "(a small, fixed launch sequence for profilers)")
     return ap.parse_args()
+
+
+def precond_only(args):
+    """Factor the bench workload and apply the preconditioner --steps times."""
+    import torch
+
+    import workloads as W
+    from paper_2209_10886_gb300 import Problem
+    w = W.workload(WORKLOAD)
+    m2 = torch.as_tensor(w.m2, dtype=torch.float64, device="cuda")
+    p = Problem(w.n, w.n, w.h, w.omega, m2, w.N1, w.N2, w.xcuts, w.ycuts).factor(args.prec)
+    r = torch.as_tensor(w.f, dtype=torch.complex128, device="cuda")
+    for _ in range(args.warmup):
+        p.precond_apply(r, sched=args.sched)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        p.precond_apply(r, sched=args.sched)
+    e1.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"mode": "precond", "prec": args.prec, "sched": args.sched,
+                      "ms_per_apply": e0.elapsed_time(e1) / max(args.steps, 1)}))
+    p.close()
 
 
 def peaks():
@@ -367,6 +394,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         reference_arm(args)
+    elif args.mode == "precond":
+        precond_only(args)
     else:
         gpu_arm(args)
 

@@ -184,7 +184,7 @@ struct helm_problem {
     double2 *d_V = nullptr, *d_Z = nullptr, *d_H = nullptr, *d_cs = nullptr, *d_sn = nullptr, *d_g = nullptr;
     double2 *d_h1 = nullptr, *d_h2 = nullptr, *d_hsum = nullptr, *d_y = nullptr, *d_cpart = nullptr;
     double *d_rpart = nullptr, *d_rn = nullptr, *d_est = nullptr, *d_invh = nullptr;
-    int *d_active = nullptr, *d_jcount = nullptr;
+    int *d_active = nullptr, *d_jcount = nullptr, *d_need = nullptr;
     int kw_nblk = 0;
 
     // adjoint workspace
@@ -259,7 +259,7 @@ static void free_pc_ws(helm_problem* p) {
 static void free_krylov(helm_problem* p) {
     dfree(p->d_V); dfree(p->d_Z); dfree(p->d_H); dfree(p->d_cs); dfree(p->d_sn); dfree(p->d_g);
     dfree(p->d_h1); dfree(p->d_h2); dfree(p->d_hsum); dfree(p->d_y); dfree(p->d_cpart);
-    dfree(p->d_rpart); dfree(p->d_rn); dfree(p->d_est); dfree(p->d_invh); dfree(p->d_active); dfree(p->d_jcount);
+    dfree(p->d_rpart); dfree(p->d_rn); dfree(p->d_est); dfree(p->d_invh); dfree(p->d_active); dfree(p->d_jcount); dfree(p->d_need);
     p->kw_nrhs = p->kw_restart = 0;
 }
 static void free_adj(helm_problem* p) {
@@ -767,7 +767,8 @@ static helm_status ensure_krylov(helm_problem* p, int nrhs, int m) {
     chk(dalloc(p->d_y, (size_t)nrhs * (m + 1)));
     chk(dalloc(p->d_cpart, (size_t)nb * nrhs * (m + 1)));
     chk(dalloc(p->d_rpart, (size_t)nb * nrhs));
-    chk(dalloc(p->d_rn, (size_t)2 * nrhs));
+    chk(dalloc(p->d_rn, (size_t)4 * nrhs));
+    chk(dalloc(p->d_need, (size_t)nrhs));
     chk(dalloc(p->d_est, (size_t)nrhs));
     chk(dalloc(p->d_invh, (size_t)nrhs));
     chk(dalloc(p->d_active, (size_t)nrhs));
@@ -785,6 +786,22 @@ __global__ void add_cols_kernel(const double2* a, const double2* b, double2* c, 
         double2 x = a[k * ld + i], y = b[k * ld + i];
         c[k * ld + i] = make_double2(x.x + y.x, x.y + y.y);
     }
+}
+
+// Selective reorthogonalisation (Daniel-Gragg-Kaufman-Stewart): after one
+// classical Gram-Schmidt pass w' = w - V h1, a second pass is needed only when
+// the projection cancelled most of w, ||w'|| < ||w|| / sqrt(2).
+// n2[k] = ||w||^2 (before), n2[nrhs + k] = ||w'||^2 (after the first pass).
+__global__ void dgks_decide_kernel(const double* n2, const int* active, int* need, int nrhs) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nrhs) return;
+    need[k] = (active[k] && n2[nrhs + k] < 0.5 * n2[k]) ? 1 : 0;
+}
+// hnorm[k] = sqrt(need ? ||w''||^2 : ||w'||^2)
+__global__ void dgks_norm_kernel(const double* n2, const int* need, double* hnorm, int nrhs) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nrhs) return;
+    hnorm[k] = sqrt(need[k] ? n2[2 * nrhs + k] : n2[nrhs + k]);
 }
 
 static helm_status gmres_impl(helm_problem* p, const double2* f, double2* u, int nrhs, const helm_opts& o,
@@ -853,25 +870,34 @@ static helm_status gmres_impl(helm_problem* p, const double2* f, double2* u, int
             prof_begin(p, HELM_K_MATVEC, st);
             launch_matvec(p->d_adiag, p->nx, p->ny, Zj, Vn, nrhs, st);
             prof_end(p, HELM_K_MATVEC, 2 * vb + 16.0 * N, st);
-            // classical Gram-Schmidt, twice
+            // classical Gram-Schmidt with selective reorthogonalisation (all in FP64)
+            launch_norm2_partial(Vn, N, nrhs, N, p->d_rpart, nb, st);
+            launch_reduce_rows(p->d_rpart, nb, nrhs, p->d_rn, 0, st);                 // ||w||^2
             prof_begin(p, HELM_K_ORTHO, st);
             launch_mdot(p->d_V, vsk, N, j + 1, Vn, N, N, nrhs, p->d_active, p->d_cpart, nb, st);
             prof_end(p, HELM_K_ORTHO, (j + 2) * vb, st);
             launch_reduce_cpartials(p->d_cpart, nb, j + 1, p->d_h1, ld, nrhs, st);
             prof_begin(p, HELM_K_ORTHO, st);
-            launch_mupdate(p->d_V, vsk, N, j + 1, nullptr, p->d_h1, ld, -1.0, Vn, N, N, nrhs, p->d_active, nullptr, nb, st);
+            launch_mupdate(p->d_V, vsk, N, j + 1, nullptr, p->d_h1, ld, -1.0, Vn, N, N, nrhs, p->d_active, p->d_rpart,
+                           nb, st);
             prof_end(p, HELM_K_ORTHO, (j + 3) * vb, st);
+            launch_reduce_rows(p->d_rpart, nb, nrhs, p->d_rn + nrhs, 0, st);          // ||w'||^2
+            count_launch();
+            dgks_decide_kernel<<<(nrhs + 127) / 128, 128, 0, st>>>(p->d_rn, p->d_active, p->d_need, nrhs);
             prof_begin(p, HELM_K_ORTHO, st);
-            launch_mdot(p->d_V, vsk, N, j + 1, Vn, N, N, nrhs, p->d_active, p->d_cpart, nb, st);
-            prof_end(p, HELM_K_ORTHO, (j + 2) * vb, st);
+            launch_mdot(p->d_V, vsk, N, j + 1, Vn, N, N, nrhs, p->d_need, p->d_cpart, nb, st);
+            prof_end(p, HELM_K_ORTHO, 0.0, st);
             launch_reduce_cpartials(p->d_cpart, nb, j + 1, p->d_h2, ld, nrhs, st);
             prof_begin(p, HELM_K_ORTHO, st);
-            launch_mupdate(p->d_V, vsk, N, j + 1, nullptr, p->d_h2, ld, -1.0, Vn, N, N, nrhs, p->d_active, p->d_rpart, nb, st);
-            prof_end(p, HELM_K_ORTHO, (j + 3) * vb, st);
-            launch_reduce_rows(p->d_rpart, nb, nrhs, p->d_rn, 1, st);
+            launch_mupdate(p->d_V, vsk, N, j + 1, nullptr, p->d_h2, ld, -1.0, Vn, N, N, nrhs, p->d_need, p->d_rpart,
+                           nb, st);
+            prof_end(p, HELM_K_ORTHO, 0.0, st);
+            launch_reduce_rows(p->d_rpart, nb, nrhs, p->d_rn + 2 * nrhs, 0, st);      // ||w''||^2
+            count_launch();
+            dgks_norm_kernel<<<(nrhs + 127) / 128, 128, 0, st>>>(p->d_rn, p->d_need, p->d_rn + 3 * nrhs, nrhs);
             count_launch();
             add_cols_kernel<<<nrhs, 128, 0, st>>>(p->d_h1, p->d_h2, p->d_hsum, j + 1, nrhs, ld);
-            launch_hessenberg_step(p->d_H, ld, (long long)ld * m, p->d_cs, p->d_sn, p->d_g, ld, p->d_hsum, ld, p->d_rn, j,
+            launch_hessenberg_step(p->d_H, ld, (long long)ld * m, p->d_cs, p->d_sn, p->d_g, ld, p->d_hsum, ld, p->d_rn + 3 * nrhs, j,
                                    nrhs, p->d_active, p->d_est, p->d_invh, st);
             launch_scale_vec(Vn, N, Vn, N, p->d_invh, N, nrhs, p->d_active, st);
             HELM_CUDA_TRY(cudaGetLastError());
