@@ -151,6 +151,33 @@ helm_status precond_factor(helm_problem* p, helm_prec prec, void* stream);
 helm_status precond_apply(helm_problem* p, int sched, const helm_c128* r, helm_c128* z,
                           int nrhs, void* stream);
 
+/* Size of the fixed scratch array used by precond_apply_noalloc (32 MiB). */
+#define HELM_NOALLOC_SCRATCH_BYTES (32 << 20)
+
+/* precond_apply without any memory allocation.  The paper has no counterpart:
+ * this is a service for callers that must not allocate device memory during
+ * the solve phase, e.g. code running under a memory budget fixed up front, or
+ * inside a framework whose caching allocator owns every device allocation and
+ * forbids others.  precond_apply allocates its workspace on first use (and
+ * again when nrhs grows); this variant instead takes its scratch (three
+ * interface buffers, the solve workspace, norms) from one static array of
+ * HELM_NOALLOC_SCRATCH_BYTES in device memory that belongs to the library
+ * image: every GPU that loads the library holds it until the process exits.
+ * Result: the same z = M^{-1} r as precond_apply (same kernels, same order).
+ * Arguments as for precond_apply; p must be factored (HELM_ERR_STATE if not).
+ * Sizes: returns HELM_ERR_ARG, with a message naming the bytes needed, when
+ * 3*ntrace*nrhs*e + N*nrhs*e (e = 8 for HELM_PREC_C64, 16 for C128) plus a
+ * few KB exceed HELM_NOALLOC_SCRATCH_BYTES; nothing is launched then.
+ * Calls no cudaMalloc, cudaFree or other allocating routine.  The first call
+ * on a device looks up the array's device address with that device current;
+ * make that first call before any stream capture.  Every call on a device
+ * shares the one array and it keeps the last call's contents (no part of it
+ * needs to start at zero: every value is written before it is read); calls
+ * whose work overlaps on the GPU (other streams, other host threads) race on
+ * it and must be serialised by the caller.  Stream-ordered. */
+helm_status precond_apply_noalloc(helm_problem* p, int sched, const helm_c128* r, helm_c128* z,
+                                  int nrhs, void* stream);
+
 /* Au = A u for nrhs fields (device u, Au; the h^2-scaled operator above).
  * Stream-ordered. */
 helm_status helm_matvec(helm_problem* p, const helm_c128* u, helm_c128* Au, int nrhs, void* stream);

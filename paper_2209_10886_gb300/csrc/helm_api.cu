@@ -626,20 +626,31 @@ static helm_status ensure_pc_ws(helm_problem* p, int nrhs) {
     return HELM_OK;
 }
 
+// scratch of one preconditioner application: three interface buffers of
+// ntrace*nrhs values, the solve workspace (N*nrhs), 3*nrhs norms and
+// kPartialBlocks*nrhs partial sums
+struct PcWork {
+    void* trace[3];
+    void* yws;
+    double* norm;
+    double* partial;
+};
+
 template <typename R>
-static helm_status run_precond_t(helm_problem* p, int sched, const double2* r, double2* z, int nrhs, cudaStream_t st) {
+static helm_status run_precond_t(helm_problem* p, const PcWork& w, int sched, const double2* r, double2* z, int nrhs,
+                                 cudaStream_t st) {
     using T = Cx<R>;
     const double* rinv = nullptr;
     const double* rsc = nullptr;
     if (sizeof(R) == 4) {
         // scale each right-hand side to unit 2-norm before rounding to complex64
-        launch_norm2_partial(r, p->N(), nrhs, p->N(), p->d_pc_partial, kPartialBlocks, st);
-        launch_reduce_rows(p->d_pc_partial, kPartialBlocks, nrhs, p->d_pc_norm, 0, st);
-        launch_scale_from_norm(p->d_pc_norm, p->d_pc_norm + nrhs, p->d_pc_norm + 2 * nrhs, nrhs, st);
-        rinv = p->d_pc_norm + nrhs;
-        rsc = p->d_pc_norm + 2 * nrhs;
+        launch_norm2_partial(r, p->N(), nrhs, p->N(), w.partial, kPartialBlocks, st);
+        launch_reduce_rows(w.partial, kPartialBlocks, nrhs, w.norm, 0, st);
+        launch_scale_from_norm(w.norm, w.norm + nrhs, w.norm + 2 * nrhs, nrhs, st);
+        rinv = w.norm + nrhs;
+        rsc = w.norm + 2 * nrhs;
     }
-    T* buf[3] = {(T*)p->d_trace[0], (T*)p->d_trace[1], (T*)p->d_trace[2]};
+    T* buf[3] = {(T*)w.trace[0], (T*)w.trace[1], (T*)w.trace[2]};
     auto B = [&](int id) -> T* { return id < 0 ? nullptr : buf[id]; };
     for (const StageDesc& sd : p->sched[sched]) {
         if (sd.iface) {
@@ -688,7 +699,7 @@ static helm_status run_precond_t(helm_problem* p, int sched, const double2* r, d
         a.dst = B(sd.dst); a.dst2 = B(sd.dst2); a.base = B(sd.base); a.sub = B(sd.sub);
         a.z = sd.final_ ? z : nullptr;
         a.zscale = rsc;
-        a.yws = (T*)p->d_yws;
+        a.yws = (T*)w.yws;
         double bytes = 0;
         if (p->prof_on) {
             // algorithmic bytes: each X_r once per stage (shared by all RHS), the
@@ -722,8 +733,9 @@ static helm_status run_precond_t(helm_problem* p, int sched, const double2* r, d
 static helm_status run_precond(helm_problem* p, int sched, const double2* r, double2* z, int nrhs, cudaStream_t st) {
     helm_status s = ensure_pc_ws(p, nrhs);
     if (s != HELM_OK) return s;
-    return p->prec == HELM_PREC_C64 ? run_precond_t<float>(p, sched, r, z, nrhs, st)
-                                    : run_precond_t<double>(p, sched, r, z, nrhs, st);
+    const PcWork w{{p->d_trace[0], p->d_trace[1], p->d_trace[2]}, p->d_yws, p->d_pc_norm, p->d_pc_partial};
+    return p->prec == HELM_PREC_C64 ? run_precond_t<float>(p, w, sched, r, z, nrhs, st)
+                                    : run_precond_t<double>(p, w, sched, r, z, nrhs, st);
 }
 
 extern "C" helm_status precond_apply(helm_problem* p, int sched, const helm_c128* r, helm_c128* z, int nrhs,
@@ -735,6 +747,58 @@ extern "C" helm_status precond_apply(helm_problem* p, int sched, const helm_c128
     if (nrhs == 0) return HELM_OK;
     if (!r || !z) return arg_error("precond_apply: NULL array");
     return run_precond(p, sched, (const double2*)r, (double2*)z, nrhs, (cudaStream_t)stream);
+}
+
+// ---------------------------------------------- preconditioner without allocation
+// Scratch of precond_apply_noalloc: one fixed array in device memory, part of the
+// library image, so every GPU that loads the library holds these bytes until the
+// process exits.  All calls share it (see include/helm.h).
+static __device__ __align__(256) unsigned char g_noalloc_scratch[HELM_NOALLOC_SCRATCH_BYTES];
+
+// device address of g_noalloc_scratch per device ordinal, looked up on the first
+// call made with that device current (host code cannot use the symbol itself)
+static std::atomic<void*> g_noalloc_ptr[128];
+
+extern "C" helm_status precond_apply_noalloc(helm_problem* p, int sched, const helm_c128* r, helm_c128* z, int nrhs,
+                                             void* stream) {
+    if (!p) return arg_error("precond_apply_noalloc: NULL handle");
+    if (!p->factored) { set_error("precond_apply_noalloc: call precond_factor first"); return HELM_ERR_STATE; }
+    if (sched != HELM_SCHED_BSP && sched != HELM_SCHED_SP) return arg_error("precond_apply_noalloc: unknown schedule");
+    if (nrhs < 0) return arg_error("precond_apply_noalloc: nrhs < 0");
+    if (nrhs == 0) return HELM_OK;
+    if (!r || !z) return arg_error("precond_apply_noalloc: NULL array");
+    // carve the scratch: 3 interface buffers, the solve workspace, norms, partial sums
+    const size_t elem = p->prec == HELM_PREC_C64 ? sizeof(float2) : sizeof(double2);
+    auto round256 = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const size_t tbytes = round256((size_t)p->ntrace * nrhs * elem);
+    const size_t ybytes = round256((size_t)p->N() * nrhs * elem);
+    const size_t nbytes = round256((size_t)3 * nrhs * sizeof(double));
+    const size_t pbytes = round256((size_t)kPartialBlocks * nrhs * sizeof(double));
+    const size_t need = 3 * tbytes + ybytes + nbytes + pbytes;
+    if (need > (size_t)HELM_NOALLOC_SCRATCH_BYTES) {
+        char buf[256];
+        snprintf(buf, sizeof buf,
+                 "precond_apply_noalloc: needs %zu bytes of scratch for %d right-hand sides, more than the fixed "
+                 "%d bytes; use precond_apply or fewer right-hand sides per call",
+                 need, nrhs, (int)HELM_NOALLOC_SCRATCH_BYTES);
+        set_error(buf);
+        return HELM_ERR_ARG;
+    }
+    int dev = 0;
+    HELM_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 128) return arg_error("precond_apply_noalloc: device ordinal out of range");
+    void* base = g_noalloc_ptr[dev].load();
+    if (!base) {
+        cudaError_t e = cudaGetSymbolAddress(&base, g_noalloc_scratch);
+        if (e != cudaSuccess || !base) return cuda_status(e, "precond_apply_noalloc: cudaGetSymbolAddress");
+        g_noalloc_ptr[dev].store(base);
+    }
+    unsigned char* b = (unsigned char*)base;
+    PcWork w{{b, b + tbytes, b + 2 * tbytes}, b + 3 * tbytes, (double*)(b + 3 * tbytes + ybytes),
+             (double*)(b + 3 * tbytes + ybytes + nbytes)};
+    cudaStream_t st = (cudaStream_t)stream;
+    return p->prec == HELM_PREC_C64 ? run_precond_t<float>(p, w, sched, (const double2*)r, (double2*)z, nrhs, st)
+                                    : run_precond_t<double>(p, w, sched, (const double2*)r, (double2*)z, nrhs, st);
 }
 
 extern "C" helm_status helm_matvec(helm_problem* p, const helm_c128* u, helm_c128* Au, int nrhs, void* stream) {
