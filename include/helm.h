@@ -108,7 +108,17 @@ typedef struct {
     int use_graph;      /* 1: replay the preconditioner from a captured CUDA graph */
     double* hist;       /* optional host buffer of maxit*nrhs doubles: the Arnoldi
                            residual estimate of RHS k after step j at hist[k*maxit+j] */
+    int ortho;          /* Arnoldi orthogonalisation, all FP64: HELM_ORTHO_MGS (default;
+                           used when n_x*n_y fits the persistent kernel, else CGS2) or
+                           HELM_ORTHO_CGS2 */
 } helm_opts;
+
+/* Orthogonalisation of the Arnoldi vectors.
+ * HELM_ORTHO_MGS:  modified Gram-Schmidt in one persistent kernel per step
+ *                  (8 FP64 FMA per element per basis vector).
+ * HELM_ORTHO_CGS2: classical Gram-Schmidt, a second pass when the first
+ *                  cancelled more than half of the norm (16 FMA per element). */
+enum { HELM_ORTHO_MGS = 0, HELM_ORTHO_CGS2 = 1 };
 
 typedef struct {
     int iters;          /* Arnoldi steps taken */
@@ -234,6 +244,8 @@ typedef struct {
     long long launches;    /* launches recorded since profiling was enabled */
     double ms;             /* summed device time between CUDA events recorded on the
                               launch stream immediately before and after each launch */
+    double flops;          /* algorithmic real floating-point operations of those launches
+                              (a complex multiply-add counts 8) */
     double bytes;          /* algorithmic bytes those launches must move (HBM reads +
                               writes of the data they touch, counted once) */
 } helm_kstat;

@@ -13,6 +13,11 @@
 #include "helm_internal.cuh"
 
 size_t factor_work_elems(int max_mx, size_t elem);
+int mgs_grid();
+long long mgs_max_n(int grid);
+cudaError_t launch_mgs(const double2* V, long long vsk, long long vsr, double2* w, int nvec, long long n, int nrhs,
+                       const int* active, double2* hcol, int ldh, double* hnorm, double2* partial, unsigned* bar,
+                       int* err, int grid, cudaStream_t st);
 
 // ------------------------------------------------------------ launch count
 #include <atomic>
@@ -164,6 +169,7 @@ struct helm_problem {
     TraceCoef<double2>* d_tc128 = nullptr;
     TraceCoef<float2>* d_tc64 = nullptr;
     int* d_stage_subs = nullptr;
+    int* d_err = nullptr;            // device status word written by kernels whose bounded waits expired
 
     int factored = 0;
     int prec = HELM_PREC_C128;
@@ -185,6 +191,8 @@ struct helm_problem {
     double2 *d_h1 = nullptr, *d_h2 = nullptr, *d_hsum = nullptr, *d_y = nullptr, *d_cpart = nullptr;
     double *d_rpart = nullptr, *d_rn = nullptr, *d_est = nullptr, *d_invh = nullptr;
     int *d_active = nullptr, *d_jcount = nullptr, *d_need = nullptr;
+    double2* d_mgs_part = nullptr;   // partial sums of the persistent Gram-Schmidt kernel
+    unsigned* d_mgs_bar = nullptr;   // its grid-barrier state
     int kw_nblk = 0;
 
     // adjoint workspace
@@ -197,6 +205,7 @@ struct helm_problem {
         std::vector<cudaEvent_t> a, b;
         size_t used = 0;
         double bytes = 0;
+        double flops = 0;
     };
     KProf prof[5];
     int prof_on = 0;
@@ -217,17 +226,24 @@ static void prof_begin(helm_problem* p, int k, cudaStream_t st) {
     }
     cudaEventRecord(q.a[q.used], st);
 }
-static void prof_end(helm_problem* p, int k, double bytes, cudaStream_t st) {
+static void prof_end(helm_problem* p, int k, double bytes, cudaStream_t st, double flops = 0.0) {
     if (!p->prof_on) return;
     auto& q = p->prof[k];
     cudaEventRecord(q.b[q.used], st);
     ++q.used;
     q.bytes += bytes;
+    q.flops += flops;
+}
+// work known only after the launch (e.g. a pass the device decided to run)
+static void prof_add(helm_problem* p, int k, double bytes, double flops) {
+    if (!p->prof_on) return;
+    p->prof[k].bytes += bytes;
+    p->prof[k].flops += flops;
 }
 
 extern "C" helm_status helm_profile(helm_problem* p, int on) {
     if (!p) { set_error("helm_profile: NULL handle"); return HELM_ERR_ARG; }
-    for (auto& q : p->prof) { q.used = 0; q.bytes = 0; }
+    for (auto& q : p->prof) { q.used = 0; q.bytes = 0; q.flops = 0; }
     p->prof_on = on != 0;
     return HELM_OK;
 }
@@ -246,6 +262,7 @@ extern "C" helm_status helm_profile_read(helm_problem* p, int k, helm_kstat* out
     out->launches = (long long)q.used;
     out->ms = ms;
     out->bytes = q.bytes;
+    out->flops = q.flops;
     return HELM_OK;
 }
 
@@ -260,6 +277,7 @@ static void free_krylov(helm_problem* p) {
     dfree(p->d_V); dfree(p->d_Z); dfree(p->d_H); dfree(p->d_cs); dfree(p->d_sn); dfree(p->d_g);
     dfree(p->d_h1); dfree(p->d_h2); dfree(p->d_hsum); dfree(p->d_y); dfree(p->d_cpart);
     dfree(p->d_rpart); dfree(p->d_rn); dfree(p->d_est); dfree(p->d_invh); dfree(p->d_active); dfree(p->d_jcount); dfree(p->d_need);
+    dfree(p->d_mgs_part); dfree(p->d_mgs_bar);
     p->kw_nrhs = p->kw_restart = 0;
 }
 static void free_adj(helm_problem* p) {
@@ -279,6 +297,7 @@ extern "C" void helm_default_opts(helm_opts* o) {
     o->sched = HELM_SCHED_BSP;
     o->use_graph = 0;
     o->hist = nullptr;
+    o->ortho = HELM_ORTHO_MGS;
 }
 extern "C" void helm_default_setup_opts(helm_setup_opts* o) {
     if (!o) return;
@@ -369,7 +388,7 @@ extern "C" helm_status helm_setup(int n_x, int n_y, double h, double omega, cons
             p->max_mx = std::max(p->max_mx, s.dev.mx);
             p->max_my = std::max(p->max_my, s.dev.my);
         }
-    if (p->max_mx > 512) { delete p; return arg_error("helm_setup: subdomains wider than 512 nodes are not supported"); }
+    if (p->max_mx > 256) { delete p; return arg_error("helm_setup: subdomains wider than 256 nodes are not supported"); }
     long long loff = 0;
     for (auto& s : p->subs) { s.dev.loff = loff; s.dev.yoff = loff; loff += (long long)s.dev.mx * s.dev.my; }
 
@@ -470,6 +489,8 @@ extern "C" helm_status helm_setup(int n_x, int n_y, double h, double omega, cons
                                 p->nslots, p->d_subtab, p->d_tc128, p->d_tc64, 0);
         }
         if ((e = dalloc(p->d_stage_subs, all_stage_subs.size())) != cudaSuccess) { fail(e, "alloc stage lists"); break; }
+        if ((e = dalloc(p->d_err, 1)) != cudaSuccess) { fail(e, "alloc status word"); break; }
+        if ((e = cudaMemset(p->d_err, 0, sizeof(int))) != cudaSuccess) { fail(e, "clear status word"); break; }
         cudaMemcpy(p->d_stage_subs, all_stage_subs.data(), all_stage_subs.size() * sizeof(int), cudaMemcpyHostToDevice);
         if ((e = cudaDeviceSynchronize()) != cudaSuccess) { fail(e, "setup kernels"); break; }
     } while (0);
@@ -485,7 +506,7 @@ extern "C" helm_status helm_destroy(helm_problem* p) {
     free_krylov(p);
     free_adj(p);
     dfree(p->d_m2); dfree(p->d_adiag); dfree(p->d_dloc); dfree(p->d_subtab);
-    dfree(p->d_tc128); dfree(p->d_tc64); dfree(p->d_stage_subs);
+    dfree(p->d_tc128); dfree(p->d_tc64); dfree(p->d_stage_subs); dfree(p->d_err);
     for (auto& q : p->prof) {
         for (auto e : q.a) cudaEventDestroy(e);
         for (auto e : q.b) cudaEventDestroy(e);
@@ -504,6 +525,17 @@ extern "C" helm_status helm_problem_info(const helm_problem* p, long long* n_unk
     if (n_trace) *n_trace = p->ntrace;
     if (factor_bytes) *factor_bytes = (long long)p->X_bytes;
     return HELM_OK;
+}
+
+// Read and clear the device status word (synchronous).  A kernel sets it when
+// one of its bounded waits expired; the work of that launch is then invalid.
+static helm_status take_device_status(helm_problem* p, const char* who) {
+    int v = 0;
+    HELM_CUDA_TRY(cudaMemcpy(&v, p->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (v == 0) return HELM_OK;
+    HELM_CUDA_TRY(cudaMemset(p->d_err, 0, sizeof(int)));
+    set_error(std::string(who) + ": a device wait timed out; results of this call are invalid");
+    return HELM_ERR_TIMEOUT;
 }
 
 // ------------------------------------------------------ boundary operators
@@ -531,6 +563,7 @@ static helm_status build_boundary_operators_t(helm_problem* p, cudaStream_t st) 
     a.tc = sizeof(R) == 4 ? (const TraceCoef<T>*)p->d_tc64 : (const TraceCoef<T>*)p->d_tc128;
     a.yws = (T*)yws;
     a.K = (T*)p->d_K;
+    a.err = p->d_err;
     for (int c0 = 0; c0 < p->max_Lb && e == cudaSuccess; c0 += NB) {
         a.col0 = c0;
         e = launch_basis<R>(a, (int)p->subs.size(), NB, p->max_mx, p->max_my, st);
@@ -538,6 +571,8 @@ static helm_status build_boundary_operators_t(helm_problem* p, cudaStream_t st) 
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     cudaFree(yws);
     if (e != cudaSuccess) return cuda_status(e, "precond_factor: boundary operators");
+    const helm_status ds = take_device_status(p, "precond_factor");
+    if (ds != HELM_OK) return ds;
     return HELM_OK;
 }
 
@@ -664,7 +699,7 @@ static helm_status run_precond_t(helm_problem* p, const PcWork& w, int sched, co
             ia.gin0 = B(sd.in0); ia.gin1 = B(sd.in1);
             ia.mask = sd.mask;
             ia.dst = B(sd.dst); ia.dst2 = B(sd.dst2); ia.base = B(sd.base); ia.sub = B(sd.sub);
-            double bytes = 0;
+            double bytes = 0, flops = 0;
             if (p->prof_on) {
                 const double sT = sizeof(T);
                 for (int id : sd.subs) {
@@ -675,11 +710,12 @@ static helm_status run_precond_t(helm_problem* p, const PcWork& w, int sched, co
                     const double io = d.Lb * sT * ((sd.in0 >= 0) + (sd.in1 >= 0)) +
                                       rows * sT * (1 + (sd.dst2 >= 0) + (sd.base >= 0) + (sd.sub >= 0));
                     bytes += rows * d.Lb * sT + io * nrhs;
+                    flops += 8.0 * rows * d.Lb * nrhs;
                 }
             }
             prof_begin(p, HELM_K_TRACE, st);
             cudaError_t e = launch_iface<R>(ia, (int)sd.subs.size(), 2 * (p->max_mx + p->max_my), p->max_Lb, st);
-            prof_end(p, HELM_K_TRACE, bytes, st);
+            prof_end(p, HELM_K_TRACE, bytes, st, flops);
             if (e != cudaSuccess) return cuda_status(e, "interface stage launch");
             continue;
         }
@@ -700,7 +736,8 @@ static helm_status run_precond_t(helm_problem* p, const PcWork& w, int sched, co
         a.z = sd.final_ ? z : nullptr;
         a.zscale = rsc;
         a.yws = (T*)w.yws;
-        double bytes = 0;
+        a.err = p->d_err;
+        double bytes = 0, flops = 0;
         if (p->prof_on) {
             // algorithmic bytes: each X_r once per stage (shared by all RHS), the
             // solve workspace y written and read once, source read, volume output
@@ -720,11 +757,12 @@ static helm_status run_precond_t(helm_problem* p, const PcWork& w, int sched, co
                         per_rhs += len * sT * (1 + (sd.dst2 >= 0) + (sd.base >= 0) + (sd.sub >= 0));
                 }
                 bytes += (2.0 * d.my - 1) * d.mx * (double)d.mx * sT + per_rhs * nrhs;
+                flops += 8.0 * (2.0 * d.my - 1) * d.mx * (double)d.mx * nrhs;
             }
         }
         prof_begin(p, HELM_K_STAGE, st);
         cudaError_t e = launch_stage<R>(a, (int)sd.subs.size(), p->max_mx, p->max_my, st);
-        prof_end(p, HELM_K_STAGE, bytes, st);
+        prof_end(p, HELM_K_STAGE, bytes, st, flops);
         if (e != cudaSuccess) return cuda_status(e, "stage launch");
     }
     return HELM_OK;
@@ -833,6 +871,14 @@ static helm_status ensure_krylov(helm_problem* p, int nrhs, int m) {
     chk(dalloc(p->d_rpart, (size_t)nb * nrhs));
     chk(dalloc(p->d_rn, (size_t)4 * nrhs));
     chk(dalloc(p->d_need, (size_t)nrhs));
+    {
+        const int g = mgs_grid();
+        if (g > 0) {
+            chk(dalloc(p->d_mgs_part, (size_t)2 * g));
+            chk(dalloc(p->d_mgs_bar, (size_t)2));
+            if (e == cudaSuccess) e = cudaMemset(p->d_mgs_bar, 0, 2 * sizeof(unsigned));
+        }
+    }
     chk(dalloc(p->d_est, (size_t)nrhs));
     chk(dalloc(p->d_invh, (size_t)nrhs));
     chk(dalloc(p->d_active, (size_t)nrhs));
@@ -880,10 +926,14 @@ static helm_status gmres_impl(helm_problem* p, const double2* f, double2* u, int
     const long long vsk = (long long)nrhs * N;    // V_j of RHS k at d_V + j*vsk + k*N
     const double h2 = p->h * p->h;
     const int ld = m + 1;
+    // modified Gram-Schmidt needs the vector to fit the persistent kernel's registers
+    const int mgs_grid_n = (o.ortho == HELM_ORTHO_MGS) ? mgs_grid() : 0;
+    const bool use_mgs = mgs_grid_n > 0 && N <= mgs_max_n(mgs_grid_n) && p->d_mgs_part != nullptr;
     if (!o.x0_given) HELM_CUDA_TRY(cudaMemsetAsync(u, 0, (size_t)nrhs * N * sizeof(double2), st));
 
     // ||h^2 f||
     std::vector<double> bnorm(nrhs), rn(nrhs), est(nrhs);
+    std::vector<int> need(nrhs, 0);
     launch_norm2_partial(f, N, nrhs, N, p->d_rpart, nb, st);
     launch_reduce_rows(p->d_rpart, nb, nrhs, p->d_rn, 1, st);
     HELM_CUDA_TRY(cudaMemcpyAsync(bnorm.data(), p->d_rn, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -933,18 +983,31 @@ static helm_status gmres_impl(helm_problem* p, const double2* f, double2* u, int
             const double vb = 16.0 * N * nrhs;   // bytes of one field for all RHS
             prof_begin(p, HELM_K_MATVEC, st);
             launch_matvec(p->d_adiag, p->nx, p->ny, Zj, Vn, nrhs, st);
-            prof_end(p, HELM_K_MATVEC, 2 * vb + 16.0 * N, st);
+            prof_end(p, HELM_K_MATVEC, 2 * vb + 16.0 * N, st, 16.0 * N * nrhs);
+            if (use_mgs) {
+                // modified Gram-Schmidt, persistent kernel: h = column j of H, ||w||, v_{j+1}
+                int nact = 0;
+                for (int k = 0; k < nrhs; ++k) nact += active[k];
+                prof_begin(p, HELM_K_ORTHO, st);
+                cudaError_t e = launch_mgs(p->d_V, vsk, N, Vn, j + 1, N, nrhs, p->d_active, p->d_hsum, ld,
+                                           p->d_rn + 3 * nrhs, p->d_mgs_part, p->d_mgs_bar, p->d_err, mgs_grid_n, st);
+                prof_end(p, HELM_K_ORTHO, (j + 3) * 16.0 * N * nact, st, (16.0 * (j + 1) + 4.0) * N * nact);
+                if (e != cudaSuccess) return cuda_status(e, "modified Gram-Schmidt launch");
+                launch_hessenberg_step(p->d_H, ld, (long long)ld * m, p->d_cs, p->d_sn, p->d_g, ld, p->d_hsum, ld,
+                                       p->d_rn + 3 * nrhs, j, nrhs, p->d_active, p->d_est, p->d_invh, st);
+                goto step_done;
+            }
             // classical Gram-Schmidt with selective reorthogonalisation (all in FP64)
             launch_norm2_partial(Vn, N, nrhs, N, p->d_rpart, nb, st);
             launch_reduce_rows(p->d_rpart, nb, nrhs, p->d_rn, 0, st);                 // ||w||^2
             prof_begin(p, HELM_K_ORTHO, st);
             launch_mdot(p->d_V, vsk, N, j + 1, Vn, N, N, nrhs, p->d_active, p->d_cpart, nb, st);
-            prof_end(p, HELM_K_ORTHO, (j + 2) * vb, st);
+            prof_end(p, HELM_K_ORTHO, (j + 2) * vb, st, 8.0 * (j + 1) * N * nrhs);
             launch_reduce_cpartials(p->d_cpart, nb, j + 1, p->d_h1, ld, nrhs, st);
             prof_begin(p, HELM_K_ORTHO, st);
             launch_mupdate(p->d_V, vsk, N, j + 1, nullptr, p->d_h1, ld, -1.0, Vn, N, N, nrhs, p->d_active, p->d_rpart,
                            nb, st);
-            prof_end(p, HELM_K_ORTHO, (j + 3) * vb, st);
+            prof_end(p, HELM_K_ORTHO, (j + 3) * vb, st, 8.0 * (j + 1) * N * nrhs + 4.0 * N * nrhs);
             launch_reduce_rows(p->d_rpart, nb, nrhs, p->d_rn + nrhs, 0, st);          // ||w'||^2
             count_launch();
             dgks_decide_kernel<<<(nrhs + 127) / 128, 128, 0, st>>>(p->d_rn, p->d_active, p->d_need, nrhs);
@@ -964,9 +1027,18 @@ static helm_status gmres_impl(helm_problem* p, const double2* f, double2* u, int
             launch_hessenberg_step(p->d_H, ld, (long long)ld * m, p->d_cs, p->d_sn, p->d_g, ld, p->d_hsum, ld, p->d_rn + 3 * nrhs, j,
                                    nrhs, p->d_active, p->d_est, p->d_invh, st);
             launch_scale_vec(Vn, N, Vn, N, p->d_invh, N, nrhs, p->d_active, st);
+            if (p->prof_on)
+                HELM_CUDA_TRY(cudaMemcpyAsync(need.data(), p->d_need, nrhs * sizeof(int), cudaMemcpyDeviceToHost, st));
+        step_done:
             HELM_CUDA_TRY(cudaGetLastError());
             HELM_CUDA_TRY(cudaMemcpyAsync(est.data(), p->d_est, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
             HELM_CUDA_TRY(cudaStreamSynchronize(st));
+            if (p->prof_on && !use_mgs) {
+                // the second Gram-Schmidt pass ran for the RHS that needed it
+                int nre = 0;
+                for (int k = 0; k < nrhs; ++k) nre += need[k];
+                prof_add(p, HELM_K_ORTHO, (2.0 * j + 5) * 16.0 * N * nre, (16.0 * (j + 1) + 4.0) * N * nre);
+            }
             bool still = false;
             for (int k = 0; k < nrhs; ++k) {
                 if (!active[k]) continue;
@@ -986,6 +1058,10 @@ static helm_status gmres_impl(helm_problem* p, const double2* f, double2* u, int
         launch_mupdate(p->d_Z, vsk, N, m, p->d_jcount, p->d_y, ld, 1.0, u, N, N, nrhs, nullptr, nullptr, nb, st);
         HELM_CUDA_TRY(cudaGetLastError());
         HELM_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    {
+        const helm_status ds = take_device_status(p, "gmres_solve");
+        if (ds != HELM_OK) return ds;
     }
     bool ok = true;
     for (int k = 0; k < nrhs; ++k) {
@@ -1013,6 +1089,7 @@ extern "C" helm_status gmres_solve(helm_problem* p, const helm_c128* f, helm_c12
     if (o.maxit < 1) return arg_error("gmres_solve: maxit must be >= 1");
     if (!(o.tol > 0)) return arg_error("gmres_solve: tol must be > 0");
     if (o.sched != HELM_SCHED_BSP && o.sched != HELM_SCHED_SP) return arg_error("gmres_solve: unknown schedule");
+    if (o.ortho != HELM_ORTHO_MGS && o.ortho != HELM_ORTHO_CGS2) return arg_error("gmres_solve: unknown ortho");
     return gmres_impl(p, (const double2*)f, (double2*)u, nrhs, o, info, (cudaStream_t)stream);
 }
 

@@ -114,6 +114,7 @@ template <typename R> struct StageArgs {
     // values of the solution are stored as that row of K
     T* K;
     int col0;
+    int* err;                  // device status word: set to HELM_ERR_TIMEOUT when a bounded wait expires
 };
 
 // launch parameters of the interface (boundary-operator) stage kernel

@@ -1,17 +1,21 @@
-// One stage of the sweep schedule: all subdomain solves that the schedule
-// makes independent run in this single launch (paper Sections 4-5), with the
-// assembly of the local right-hand sides from the volume source and the
-// incoming interface data (Eq. subPbm, subPbmLifting) in the prologue and the
+// One stage of the sweep schedule that needs full subdomain solves (the
+// liftings of Eq. subPbmLifting and the reconstruction with the final
+// interface data): all subdomains of the stage run in this single launch
+// (paper Sections 4-5), with the assembly of the local right-hand sides from
+// the volume source and the incoming data (Eq. subPbm) in the prologue and the
 // transmission of the outgoing traces to the neighbours in the epilogue.
 //
 // Local solve with the stored factors X_r (k_factor.cu):
 //     forward   y_1 = X_1 b_1,        y_r = X_r (b_r + y_{r-1})
 //     backward  u_my = y_my,          u_r = y_r + X_r u_{r+1}
 // X_r is complex symmetric, so y = X v is computed column-wise from the
-// row-major storage (thread = output column, coalesced rows).  X is streamed
-// from HBM through a multi-stage shared-memory ring filled with cp.async;
-// the first X of the backward pass follows the last forward one in the same
-// stream of chunks, so the copy engine never idles between the two passes.
+// row-major storage: one consumer thread per output column, coalesced rows in
+// shared memory, four independent partial sums.  X is streamed from HBM by
+// bulk (TMA) copies that one producer thread issues into a ring of shared
+// memory slots guarded by full/empty mbarriers; the first X of the backward
+// pass follows the last forward one in the same stream of chunks.  Every
+// mbarrier wait is bounded in time; on expiry the kernel records HELM_ERR_TIMEOUT
+// in a device flag, drains its own copies and returns.
 //
 // Outgoing data toward the neighbour across side s (scaled form of
 // (-d_{n_{i,j}} - T) u_i):  G_out = ca * G_in + cb * u_p  with the edge's
@@ -20,24 +24,58 @@
 
 namespace {
 
-constexpr int ST = 512;       // threads per CTA
-constexpr int NSTAGE = 4;     // pipeline depth
+constexpr int MAXNS = 8;                        // ring slots (upper bound)
+constexpr long long WAIT_LIMIT = 2000000000LL;  // cycles (~1 s) before a wait gives up
 
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* b, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(b)), "r"(count) : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N> __device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+__device__ __forceinline__ void mbar_arrive(unsigned long long* b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_addr(b)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* b, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(b)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try(unsigned long long* b, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// wait for the phase with this parity, at most WAIT_LIMIT cycles
+__device__ __forceinline__ bool mbar_wait(unsigned long long* b, unsigned parity) {
+    if (mbar_try(b, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try(b, parity))
+        if (clock64() - t0 > WAIT_LIMIT) return false;
+    return true;
+}
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+__device__ __forceinline__ void consumer_sync(int nthreads) {
+    asm volatile("bar.sync 1, %0;\n" ::"r"(nthreads) : "memory");
 }
 
 // BASIS = true: the NR right-hand sides of a CTA are unit data at consecutive
 // interface boundary points (columns of the boundary operator K, see StageArgs).
 template <typename R, int NR, bool BASIS>
-__global__ void __launch_bounds__(ST) stage_kernel(StageArgs<R> a, int rows_per_chunk) {
+__global__ void __launch_bounds__(288) stage_kernel(StageArgs<R> a, int rows_per_chunk, int nslots, int cwarps) {
     using T = Cx<R>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) unsigned long long full_bar[MAXNS], empty_bar[MAXNS];
+    __shared__ int abort_flag;
+
     const int s = BASIS ? blockIdx.x : a.subs[blockIdx.x];
     const SubDev sd = a.subtab[s];
     const int mx = sd.mx, my = sd.my, ldx = sd.ldx;
@@ -45,58 +83,41 @@ __global__ void __launch_bounds__(ST) stage_kernel(StageArgs<R> a, int rows_per_
     const int e0 = BASIS ? a.col0 + rhs0 : 0;            // first boundary point (basis mode)
     if (BASIS && e0 >= sd.Lb) return;
     const int nr = BASIS ? min(NR, sd.Lb - e0) : min(NR, a.nrhs - rhs0);
-    const int tid = threadIdx.x;
-    const int NC = (mx + 31) & ~31;
-    const int G = ST / NC;
-    const int col = tid % NC, grp = tid / NC;
-    const bool worker = grp < G && col < mx;
-    const bool lead = grp == 0 && col < mx;       // owns column `col` of the solution
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int ncons = 32 * cwarps;                       // consumer threads (warps 0 .. cwarps-1)
+    const bool producer = warp == cwarps;
+    const int col = tid;                                 // consumer thread = output column
+    const bool owner = !producer && col < mx;
     const int Rch = rows_per_chunk;
     const int nq = (mx + Rch - 1) / Rch;
     const int Q = (2 * my - 1) * nq;
+    const int mxp = ncons;
     // boundary arrays per RHS: W[my] | E[my] | S[mx] | N[mx]
     const int L = 2 * (mx + my);
-    const int boff[4] = {0, my, 2 * my, 2 * my + mx};
+    auto boff = [&](int side) { return side < 2 ? side * my : 2 * my + (side - 2) * mx; };
 
-    // shared memory: NSTAGE chunks | v[NR][NC] | part[NR*ST] | binc[NR][L] | ub[NR][L]
-    T* stg = reinterpret_cast<T*>(smem_raw);
-    const size_t chunk_elems = (size_t)Rch * ldx;
-    T* v = stg + (size_t)NSTAGE * chunk_elems;
-    T* part = v + (size_t)NR * NC;
-    T* binc = part + (size_t)NR * ST;
+    // dynamic shared memory: ring[nslots][Rch*ldx] | v[2][NR][mxp] | binc[NR][L] | ub[NR][L]
+    T* ring = reinterpret_cast<T*>(smem_raw);
+    const size_t slot_elems = (size_t)Rch * ldx;
+    T* vbuf = ring + (size_t)nslots * slot_elems;
+    T* binc = vbuf + 2 * (size_t)NR * mxp;
     T* ub = binc + (size_t)NR * L;
 
     const long long N = (long long)a.nx * a.ny;
     const T* Xs = a.X + sd.xoff;
 
-    auto issue = [&](int t) {
-        if (t < Q) {
-            int r, q;
-            if (t < my * nq) { r = t / nq; q = t - r * nq; }
-            else { int tb = t - my * nq; r = my - 2 - tb / nq; q = tb % nq; }
-            const int rows = min(Rch, mx - q * Rch);
-            const T* src = Xs + (long long)r * mx * ldx + (long long)q * Rch * ldx;
-            T* dst = stg + (size_t)(t % NSTAGE) * chunk_elems;
-            const int pieces = (int)((size_t)rows * ldx * sizeof(T) / 16);
-            const char* sg = reinterpret_cast<const char*>(src);
-            char* dg = reinterpret_cast<char*>(dst);
-            for (int pc = tid; pc < pieces; pc += ST) cp_async16(dg + 16 * (size_t)pc, sg + 16 * (size_t)pc);
-        }
-        cp_async_commit();
-    };
     auto gin = [&](int k, long long idx) -> T {
         T g = a.gin0 ? a.gin0[(long long)(rhs0 + k) * a.ntrace + idx] : czero<T>();
         if (a.gin1) g = cadd(g, a.gin1[(long long)(rhs0 + k) * a.ntrace + idx]);
         return g;
     };
-    // incoming-data part of the local right-hand side at node (r, c) (from shared memory)
     auto bterm = [&](int r, int c, int k) -> T {
         const T* bk = binc + (size_t)k * L;
         T b = czero<T>();
-        if (c == 0) b = cadd(b, bk[boff[SW] + r]);
-        if (c == mx - 1) b = cadd(b, bk[boff[SE] + r]);
-        if (r == 0) b = cadd(b, bk[boff[SS] + c]);
-        if (r == my - 1) b = cadd(b, bk[boff[SN] + c]);
+        if (c == 0) b = cadd(b, bk[boff(SW) + r]);
+        if (c == mx - 1) b = cadd(b, bk[boff(SE) + r]);
+        if (r == 0) b = cadd(b, bk[boff(SS) + c]);
+        if (r == my - 1) b = cadd(b, bk[boff(SN) + c]);
         return b;
     };
     auto src_row = [&](int r, int c, int k) -> double2 {
@@ -108,34 +129,35 @@ __global__ void __launch_bounds__(ST) stage_kernel(StageArgs<R> a, int rows_per_
         rsc[k] = (a.rscale && k < nr) ? a.rscale[rhs0 + k] : 1.0;
         zsc[k] = (a.zscale && k < nr) ? a.zscale[rhs0 + k] : 1.0;
     }
-    auto scaled = [&](double2 rv, int k) -> T {
-        const double sc = rsc[k];
-        return from_c128<T>(make_double2(rv.x * sc, rv.y * sc));
-    };
-    // row r of the solution is final: keep the boundary values, write the volume output
+    auto scaled = [&](double2 rv, int k) -> T { return from_c128<T>(make_double2(rv.x * rsc[k], rv.y * rsc[k])); };
     auto finish_row = [&](int r, int c, int k, T u) {
         T* uk = ub + (size_t)k * L;
-        if (c == 0) uk[boff[SW] + r] = u;
-        if (c == mx - 1) uk[boff[SE] + r] = u;
-        if (r == 0) uk[boff[SS] + c] = u;
-        if (r == my - 1) uk[boff[SN] + c] = u;
+        if (c == 0) uk[boff(SW) + r] = u;
+        if (c == mx - 1) uk[boff(SE) + r] = u;
+        if (r == 0) uk[boff(SS) + c] = u;
+        if (r == my - 1) uk[boff(SN) + c] = u;
         if (!BASIS && a.z) {
-            const double sc = zsc[k];
             const double2 zu = to_c128(u);
             a.z[(long long)(rhs0 + k) * N + (long long)(sd.y0 + r) * a.nx + sd.x0 + c] =
-                make_double2(zu.x * sc, zu.y * sc);
+                make_double2(zu.x * zsc[k], zu.y * zsc[k]);
         }
     };
 
-    // ---- prologue: start the copies; incoming terms G_in/(1-beta) into shared memory
-    for (int t = 0; t < NSTAGE - 1; ++t) issue(t);
-    for (int idx = tid; idx < NR * L; idx += ST) {
+    // ---- prologue: barriers, incoming terms G_in/(1-beta) into shared memory, v = b_1
+    if (tid == 0) {
+        for (int i = 0; i < nslots; ++i) {
+            mbar_init(&full_bar[i], 1);
+            mbar_init(&empty_bar[i], cwarps);
+        }
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    for (int idx = tid; idx < NR * L; idx += blockDim.x) {
         const int k = idx / L, e = idx - k * L;
         const int side = e < my ? SW : e < 2 * my ? SE : e < 2 * my + mx ? SS : SN;
-        const int pt = e - boff[side];
+        const int pt = e - boff(side);
         T b = czero<T>();
         if (BASIS) {
-            // unit datum at boundary point e0 + k (an interface side's point)
             if (k < nr && sd.bo[side] >= 0 && sd.bo[side] + pt == e0 + k) b = mk((R)1, (R)0);
         } else if (k < nr && sd.tin[side] >= 0 && (a.gin0 || a.gin1)) {
             const long long ti = sd.tin[side] + pt;
@@ -144,65 +166,113 @@ __global__ void __launch_bounds__(ST) stage_kernel(StageArgs<R> a, int rows_per_
         binc[idx] = b;
     }
     __syncthreads();
-    for (int idx = tid; idx < NR * mx; idx += ST) {
-        const int k = idx / mx, c = idx - k * mx;
+    for (int idx = tid; idx < NR * mxp; idx += blockDim.x) {
+        const int k = idx / mxp, c = idx - k * mxp;
         T b = czero<T>();
-        if (k < nr) {
+        if (k < nr && c < mx) {
             b = bterm(0, c, k);
             if (!BASIS && a.src) b = cadd(b, scaled(src_row(0, c, k), k));
         }
-        v[k * NC + c] = b;
+        vbuf[idx] = b;
     }
-    // one-row-ahead register prefetch (raw loads; consumed at the end of the next row)
-    double2 rnext[NR];
-    T ynext[NR];
-#pragma unroll
-    for (int k = 0; k < NR; ++k) { rnext[k] = make_double2(0.0, 0.0); ynext[k] = czero<T>(); }
-    if (!BASIS && lead && a.src && my > 1) {
-#pragma unroll
-        for (int k = 0; k < NR; ++k)
-            if (k < nr) rnext[k] = src_row(1, col, k);
-    }
+    __syncthreads();
 
-    T acc[NR];
-#pragma unroll
-    for (int k = 0; k < NR; ++k) acc[k] = czero<T>();
-    T* yw = a.yws + sd.yoff;
-
-    for (int t = 0; t < Q; ++t) {
-        cp_async_wait<NSTAGE - 2>();
-        __syncthreads();
-        issue(t + NSTAGE - 1);
-        int r, q;
-        bool fwd;
-        if (t < my * nq) { r = t / nq; q = t - r * nq; fwd = true; }
-        else { int tb = t - my * nq; r = my - 2 - tb / nq; q = tb % nq; fwd = false; }
-        const int rows = min(Rch, mx - q * Rch);
-        const T* S = stg + (size_t)(t % NSTAGE) * chunk_elems;
-        if (worker) {
-            const T* vq = v + q * Rch;
-#pragma unroll 4
-            for (int jj = grp; jj < rows; jj += G) {
-                const T xv = S[(size_t)jj * ldx + col];
-#pragma unroll
-                for (int k = 0; k < NR; ++k) acc[k] = cfma(xv, vq[k * NC + jj], acc[k]);
-            }
-        }
-        if (q == nq - 1) {
-            if (worker) {
-#pragma unroll
-                for (int k = 0; k < NR; ++k) {
-                    part[(size_t)(grp * NR + k) * NC + col] = acc[k];
-                    acc[k] = czero<T>();
+    if (producer) {
+        // ---- producer: one thread streams every chunk of X_1..X_my, X_{my-1}..X_1
+        if (lane == 0) {
+            int r = 0, q = 0, slot = 0;
+            unsigned ph = 0;
+            bool fwd = true;
+            int issued = 0;
+            for (int t = 0; t < Q; ++t) {
+                if (t >= nslots && !mbar_wait(&empty_bar[slot], ph ^ 1u)) {
+                    abort_flag = 1;
+                    if (a.err) atomicExch(a.err, (int)HELM_ERR_TIMEOUT);
+                    break;
+                }
+                if (*((volatile int*)&abort_flag)) break;
+                const int rows = min(Rch, mx - q * Rch);
+                const unsigned bytes = (unsigned)((size_t)rows * ldx * sizeof(T));
+                mbar_expect_tx(&full_bar[slot], bytes);
+                bulk_copy(ring + (size_t)slot * slot_elems, Xs + (long long)r * mx * ldx + (long long)q * Rch * ldx,
+                          bytes, &full_bar[slot]);
+                ++issued;
+                if (++slot == nslots) { slot = 0; ph ^= 1u; }
+                if (++q == nq) {
+                    q = 0;
+                    if (fwd) { if (++r == my) { fwd = false; r = my - 2; } }
+                    else --r;
                 }
             }
-            __syncthreads();
-            if (lead) {
+            if (*((volatile int*)&abort_flag)) {
+                // drain: wait (bounded) for every copy this CTA issued before leaving
+                for (int t = max(0, issued - nslots); t < issued; ++t)
+                    mbar_wait(&full_bar[t % nslots], (unsigned)((t / nslots) & 1));
+            }
+        }
+    } else {
+        // ---- consumers: y = X v column-wise, one thread per column
+        double2 rnext[NR];
+        T ynext[NR];
+#pragma unroll
+        for (int k = 0; k < NR; ++k) { rnext[k] = make_double2(0.0, 0.0); ynext[k] = czero<T>(); }
+        if (!BASIS && owner && a.src && my > 1) {
+#pragma unroll
+            for (int k = 0; k < NR; ++k)
+                if (k < nr) rnext[k] = src_row(1, col, k);
+        }
+        T* yw = a.yws + sd.yoff;
+        int slot = 0;
+        unsigned ph = 0;
+        int cur = 0;                                      // v buffer holding the current step's input
+        const int nsteps = 2 * my - 1;
+        for (int step = 0; step < nsteps; ++step) {
+            const bool fwd = step < my;
+            const int r = fwd ? step : 2 * my - 2 - step;
+            const T* v = vbuf + (size_t)cur * NR * mxp;
+            T acc[NR][4];
+#pragma unroll
+            for (int k = 0; k < NR; ++k)
+#pragma unroll
+                for (int u = 0; u < 4; ++u) acc[k][u] = czero<T>();
+            for (int q = 0; q < nq; ++q) {
+                if (!mbar_wait(&full_bar[slot], ph)) {
+                    abort_flag = 1;
+                    if (a.err) atomicExch(a.err, (int)HELM_ERR_TIMEOUT);
+                }
+                if (owner && !*((volatile int*)&abort_flag)) {
+                    const T* S = ring + (size_t)slot * slot_elems + col;
+                    const T* vq = v + q * Rch;
+                    const int rows = min(Rch, mx - q * Rch);
+                    int jj = 0;
+                    for (; jj + 4 <= rows; jj += 4) {
+                        const T x0 = S[(size_t)(jj + 0) * ldx], x1 = S[(size_t)(jj + 1) * ldx];
+                        const T x2 = S[(size_t)(jj + 2) * ldx], x3 = S[(size_t)(jj + 3) * ldx];
+#pragma unroll
+                        for (int k = 0; k < NR; ++k) {
+                            const T* vk = vq + k * mxp + jj;
+                            acc[k][0] = cfma(x0, vk[0], acc[k][0]);
+                            acc[k][1] = cfma(x1, vk[1], acc[k][1]);
+                            acc[k][2] = cfma(x2, vk[2], acc[k][2]);
+                            acc[k][3] = cfma(x3, vk[3], acc[k][3]);
+                        }
+                    }
+                    for (; jj < rows; ++jj) {
+                        const T x0 = S[(size_t)jj * ldx];
+#pragma unroll
+                        for (int k = 0; k < NR; ++k) acc[k][0] = cfma(x0, vq[k * mxp + jj], acc[k][0]);
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty_bar[slot]);
+                if (++slot == nslots) { slot = 0; ph ^= 1u; }
+            }
+            T* vn = vbuf + (size_t)(cur ^ 1) * NR * mxp;
+            if (owner) {
 #pragma unroll
                 for (int k = 0; k < NR; ++k) {
                     if (k >= nr) break;
-                    T sum = part[(size_t)k * NC + col];
-                    for (int g2 = 1; g2 < G; ++g2) sum = cadd(sum, part[(size_t)(g2 * NR + k) * NC + col]);
+                    const T sum = cadd(cadd(acc[k][0], acc[k][1]), cadd(acc[k][2], acc[k][3]));
                     T* ywk = yw + (long long)(rhs0 + k) * a.wstride;
                     T nv;
                     if (fwd) {
@@ -212,7 +282,7 @@ __global__ void __launch_bounds__(ST) stage_kernel(StageArgs<R> a, int rows_per_
                             if (!BASIS && a.src) b = cadd(b, scaled(rnext[k], k));
                             nv = cadd(b, sum);                                     // b_{r+1} + y_r
                             if (!BASIS && a.src && r + 2 < my) rnext[k] = src_row(r + 2, col, k);
-                            if (r + 2 == my) ynext[k] = sum;                       // y_{my-1} for the first backward row
+                            if (r + 2 == my) ynext[k] = sum;                       // y_{my-1}
                         } else {
                             finish_row(r, col, k, sum);                            // u_my = y_my
                             nv = sum;
@@ -223,36 +293,37 @@ __global__ void __launch_bounds__(ST) stage_kernel(StageArgs<R> a, int rows_per_
                         nv = u;
                         if (r >= 1) ynext[k] = ywk[(long long)(r - 1) * mx + col];
                     }
-                    v[k * NC + col] = nv;
+                    vn[k * mxp + col] = nv;
                 }
             }
-            // the next iteration's barrier orders these writes of v before any read
+            consumer_sync(ncons);
+            cur ^= 1;
+            if (*((volatile int*)&abort_flag)) break;
         }
     }
-    cp_async_wait<0>();
     __syncthreads();
+    if (abort_flag) return;
 
     if (BASIS) {
         // row e0 + k of K = boundary values of the response to the unit datum
-        // (K is symmetric: K = the interface-boundary block of the local inverse)
-        for (int idx = tid; idx < NR * L; idx += ST) {
+        for (int idx = tid; idx < NR * L; idx += blockDim.x) {
             const int k = idx / L, e = idx - k * L;
             if (k >= nr) continue;
             const int side = e < my ? SW : e < 2 * my ? SE : e < 2 * my + mx ? SS : SN;
             if (sd.bo[side] < 0) continue;
-            const int pt = e - boff[side];
+            const int pt = e - boff(side);
             a.K[sd.koff + (long long)(e0 + k) * sd.Lb + sd.bo[side] + pt] = ub[idx];
         }
         return;
     }
     // ---- epilogue: outgoing data G_out = ca G_in + cb u_p toward the masked sides
     if (a.mask) {
-        for (int idx = tid; idx < NR * L; idx += ST) {
+        for (int idx = tid; idx < NR * L; idx += blockDim.x) {
             const int k = idx / L, e = idx - k * L;
             if (k >= nr) continue;
             const int side = e < my ? SW : e < 2 * my ? SE : e < 2 * my + mx ? SS : SN;
             if (!(a.mask & (1 << side)) || sd.tin[side] < 0) continue;
-            const int pt = e - boff[side];
+            const int pt = e - boff(side);
             const long long in = sd.tin[side] + pt, out = sd.tout[side] + pt;
             const TraceCoef<T> c = a.tc[in];
             T g = cfma(c.cb, ub[idx], cmul(c.ca, gin(k, in)));
@@ -268,27 +339,26 @@ __global__ void __launch_bounds__(ST) stage_kernel(StageArgs<R> a, int rows_per_
 template <typename R, int NR, bool BASIS>
 cudaError_t launch_nr(const StageArgs<R>& a, int nactive, int ny_blocks, int max_mx, int max_my, cudaStream_t st) {
     using T = Cx<R>;
+    const int cwarps = (max_mx + 31) / 32;
+    const int mxp = 32 * cwarps;
     const int maxldx = sizeof(T) == 8 ? ((max_mx + 1) & ~1) : max_mx;
-    const int NC = (max_mx + 31) & ~31;
-    const int G = ST / NC;
-    // v[NR][NC] plus part[G][NR][NC]; a narrower subdomain in the same launch
-    // has more row groups, but G*NC <= ST always
-    const size_t fixed = (size_t)NR * NC * sizeof(T) + (size_t)NR * ST * sizeof(T) +
-                         2 * (size_t)NR * 2 * (max_mx + max_my) * sizeof(T);
-    const size_t budget = 227 * 1024 - 2048;
+    const size_t fixed = 2 * (size_t)NR * mxp * sizeof(T) + 2 * (size_t)NR * 2 * (max_mx + max_my) * sizeof(T);
+    const size_t budget = 227 * 1024 - 1024;
     if (fixed >= budget) return cudaErrorInvalidValue;
-    size_t per_chunk_max = (budget - fixed) / NSTAGE;
-    int rows = (int)(per_chunk_max / ((size_t)maxldx * sizeof(T)));
-    rows = min(rows, max_mx);
-    if (rows >= G) rows -= rows % G;
-    if (rows < 1) return cudaErrorInvalidValue;
-    const size_t smem = fixed + (size_t)NSTAGE * rows * maxldx * sizeof(T);
+    // chunk of ~32 KB, a multiple of 4 rows
+    int rows = (int)(32768 / ((size_t)maxldx * sizeof(T)));
+    rows = std::max(4, rows & ~3);
+    rows = std::min(rows, max_mx);
+    int nslots = (int)((budget - fixed) / ((size_t)rows * maxldx * sizeof(T)));
+    nslots = std::min(nslots, MAXNS);
+    if (nslots < 2) return cudaErrorInvalidValue;
+    const size_t smem = fixed + (size_t)nslots * rows * maxldx * sizeof(T);
     cudaError_t e = cudaFuncSetAttribute(stage_kernel<R, NR, BASIS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid(nactive, ny_blocks);
     count_launch();
-    stage_kernel<R, NR, BASIS><<<grid, ST, smem, st>>>(a, rows);
+    stage_kernel<R, NR, BASIS><<<grid, 32 * (cwarps + 1), smem, st>>>(a, rows, nslots, cwarps);
     return cudaGetLastError();
 }
 
@@ -297,7 +367,7 @@ cudaError_t launch_nr(const StageArgs<R>& a, int nactive, int ny_blocks, int max
 template <typename R>
 cudaError_t launch_stage(const StageArgs<R>& a, int nactive, int max_mx, int max_my, cudaStream_t st) {
     if (nactive == 0) return cudaSuccess;
-    if (max_mx > ST) return cudaErrorInvalidValue;
+    if (max_mx > 256) return cudaErrorInvalidValue;
     if (a.nrhs >= 4) return launch_nr<R, 4, false>(a, nactive, (a.nrhs + 3) / 4, max_mx, max_my, st);
     if (a.nrhs >= 2) return launch_nr<R, 2, false>(a, nactive, (a.nrhs + 1) / 2, max_mx, max_my, st);
     return launch_nr<R, 1, false>(a, nactive, a.nrhs, max_mx, max_my, st);
@@ -305,11 +375,11 @@ cudaError_t launch_stage(const StageArgs<R>& a, int nactive, int max_mx, int max
 
 template <typename R>
 cudaError_t launch_basis(const StageArgs<R>& a, int nsub, int ncols, int max_mx, int max_my, cudaStream_t st) {
-    if (max_mx > ST) return cudaErrorInvalidValue;
+    if (max_mx > 256) return cudaErrorInvalidValue;
     return launch_nr<R, 4, true>(a, nsub, (ncols + 3) / 4, max_mx, max_my, st);
 }
-template cudaError_t launch_basis<float>(const StageArgs<float>&, int, int, int, int, cudaStream_t);
-template cudaError_t launch_basis<double>(const StageArgs<double>&, int, int, int, int, cudaStream_t);
 
 template cudaError_t launch_stage<float>(const StageArgs<float>&, int, int, int, cudaStream_t);
 template cudaError_t launch_stage<double>(const StageArgs<double>&, int, int, int, cudaStream_t);
+template cudaError_t launch_basis<float>(const StageArgs<float>&, int, int, int, int, cudaStream_t);
+template cudaError_t launch_basis<double>(const StageArgs<double>&, int, int, int, int, cudaStream_t);

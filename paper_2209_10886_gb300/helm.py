@@ -33,7 +33,7 @@ class HelmError(RuntimeError):
 class HelmOpts(ctypes.Structure):
     _fields_ = [("restart", ctypes.c_int), ("maxit", ctypes.c_int), ("tol", ctypes.c_double),
                 ("x0_given", ctypes.c_int), ("sched", ctypes.c_int), ("use_graph", ctypes.c_int),
-                ("hist", ctypes.POINTER(ctypes.c_double))]
+                ("hist", ctypes.POINTER(ctypes.c_double)), ("ortho", ctypes.c_int)]
 
 
 class HelmSetupOpts(ctypes.Structure):
@@ -259,7 +259,8 @@ class MisfitFn(torch.autograd.Function):
 
 # ------------------------------------------------------------------ profiling
 class HelmKStat(ctypes.Structure):
-    _fields_ = [("launches", ctypes.c_longlong), ("ms", ctypes.c_double), ("bytes", ctypes.c_double)]
+    _fields_ = [("launches", ctypes.c_longlong), ("ms", ctypes.c_double), ("flops", ctypes.c_double),
+                ("bytes", ctypes.c_double)]
 
 
 KERNEL_CLASS = {"stage": 0, "matvec": 1, "ortho": 2, "other": 3, "trace": 4}
@@ -277,9 +278,9 @@ def profile(problem: "Problem", on: bool = True):
 
 
 def profile_read(problem: "Problem", kind: str):
-    """(launches, summed event ms, algorithmic bytes) of one kernel class."""
+    """(launches, summed event ms, algorithmic bytes, algorithmic flops) of one kernel class."""
     L = lib()
     L.helm_profile_read.argtypes = [_vp, _i, ctypes.POINTER(HelmKStat)]
     st = HelmKStat()
     _check(L.helm_profile_read(problem._h, KERNEL_CLASS[kind], ctypes.byref(st)))
-    return st.launches, st.ms, st.bytes
+    return st.launches, st.ms, st.bytes, st.flops
