@@ -97,6 +97,13 @@ typedef enum { HELM_TC_OPTIMIZED = 0, HELM_TC_IMPEDANCE = 1 } helm_transmission;
 typedef struct {
     int transmission;   /* helm_transmission; default HELM_TC_OPTIMIZED */
     double tc_scale;    /* s of HELM_TC_OPTIMIZED; default 1.0 */
+    int boundary_operators;  /* 1 (default): precond_factor also builds, per subdomain, the
+                                interface-boundary block K of the local inverse, and the
+                                zero-source stages of the sweeps (all sweep steps and the
+                                block Jacobi residual) apply it as one GEMV per subdomain;
+                                0: those stages run full block-tridiagonal solves instead
+                                (the same operator; no K memory, no K construction time,
+                                which grows like (boundary points) x (subdomain solve)) */
 } helm_setup_opts;
 
 typedef struct {

@@ -303,6 +303,7 @@ extern "C" void helm_default_setup_opts(helm_setup_opts* o) {
     if (!o) return;
     o->transmission = HELM_TC_OPTIMIZED;
     o->tc_scale = 1.0;
+    o->boundary_operators = 1;
 }
 
 extern "C" const char* helm_last_error(void) { return g_err.c_str(); }
@@ -636,7 +637,7 @@ extern "C" helm_status precond_factor(helm_problem* p, helm_prec prec, void* str
         }
     p->prec = prec;
     {
-        const helm_status ks = build_boundary_operators(p, st);
+        const helm_status ks = p->sopts.boundary_operators ? build_boundary_operators(p, st) : HELM_OK;
         if (ks != HELM_OK) return ks;
     }
     p->factored = 1;
@@ -688,7 +689,7 @@ static helm_status run_precond_t(helm_problem* p, const PcWork& w, int sched, co
     T* buf[3] = {(T*)w.trace[0], (T*)w.trace[1], (T*)w.trace[2]};
     auto B = [&](int id) -> T* { return id < 0 ? nullptr : buf[id]; };
     for (const StageDesc& sd : p->sched[sched]) {
-        if (sd.iface) {
+        if (sd.iface && p->d_K) {
             IfaceArgs<R> ia{};
             ia.subtab = p->d_subtab;
             ia.subs = p->d_stage_subs + sd.sub_off;
@@ -1090,7 +1091,32 @@ extern "C" helm_status gmres_solve(helm_problem* p, const helm_c128* f, helm_c12
     if (!(o.tol > 0)) return arg_error("gmres_solve: tol must be > 0");
     if (o.sched != HELM_SCHED_BSP && o.sched != HELM_SCHED_SP) return arg_error("gmres_solve: unknown schedule");
     if (o.ortho != HELM_ORTHO_MGS && o.ortho != HELM_ORTHO_CGS2) return arg_error("gmres_solve: unknown ortho");
-    return gmres_impl(p, (const double2*)f, (double2*)u, nrhs, o, info, (cudaStream_t)stream);
+    // Right-hand sides are solved in chunks whose Krylov workspace, (2 restart + 1)
+    // complex128 fields per RHS plus the preconditioner workspace, fits in 60% of
+    // the device memory that is free now (already-allocated workspace counts as free).
+    const long long N = p->N();
+    size_t freeb = 0, totalb = 0;
+    HELM_CUDA_TRY(cudaMemGetInfo(&freeb, &totalb));
+    const size_t held = (size_t)p->kw_nrhs * ((size_t)2 * p->kw_restart + 1) * N * sizeof(double2);
+    const size_t per_rhs = ((size_t)2 * o.restart + 1) * N * sizeof(double2) + (size_t)N * 2 * sizeof(double2);
+    long long fit = (long long)((0.6 * (double)(freeb + held)) / (double)per_rhs);
+    if (fit < 1) {
+        set_error("gmres_solve: the Krylov workspace of one right-hand side does not fit in device memory; "
+                  "lower the restart length");
+        return HELM_ERR_OOM;
+    }
+    const int chunk = (int)std::min<long long>(fit, nrhs);
+    helm_status worst = HELM_OK;
+    for (int k0 = 0; k0 < nrhs; k0 += chunk) {
+        const int nk = std::min(chunk, nrhs - k0);
+        if (chunk < nrhs && p->kw_nrhs > nk) free_krylov(p);        // never hold more than one chunk
+        const helm_status s = gmres_impl(p, (const double2*)f + (size_t)k0 * N, (double2*)u + (size_t)k0 * N, nk, o,
+                                         info ? info + k0 : nullptr, (cudaStream_t)stream);
+        if (s == HELM_ERR_NO_CONVERGENCE) worst = s;
+        else if (s != HELM_OK) return s;
+    }
+    if (worst != HELM_OK) set_error("gmres_solve: tolerance not reached within maxit");
+    return worst;
 }
 
 // ----------------------------------------------------------------- adjoint

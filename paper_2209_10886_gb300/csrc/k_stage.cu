@@ -230,11 +230,13 @@ __global__ void __launch_bounds__(288) stage_kernel(StageArgs<R> a, int rows_per
             const bool fwd = step < my;
             const int r = fwd ? step : 2 * my - 2 - step;
             const T* v = vbuf + (size_t)cur * NR * mxp;
-            T acc[NR][4];
+            // independent partial sums: 4 per RHS for few RHS, else the RHS themselves
+            constexpr int U = NR >= 8 ? 1 : 4;
+            T acc[NR][U];
 #pragma unroll
             for (int k = 0; k < NR; ++k)
 #pragma unroll
-                for (int u = 0; u < 4; ++u) acc[k][u] = czero<T>();
+                for (int u = 0; u < U; ++u) acc[k][u] = czero<T>();
             for (int q = 0; q < nq; ++q) {
                 if (!mbar_wait(&full_bar[slot], ph)) {
                     abort_flag = 1;
@@ -251,10 +253,10 @@ __global__ void __launch_bounds__(288) stage_kernel(StageArgs<R> a, int rows_per
 #pragma unroll
                         for (int k = 0; k < NR; ++k) {
                             const T* vk = vq + k * mxp + jj;
-                            acc[k][0] = cfma(x0, vk[0], acc[k][0]);
-                            acc[k][1] = cfma(x1, vk[1], acc[k][1]);
-                            acc[k][2] = cfma(x2, vk[2], acc[k][2]);
-                            acc[k][3] = cfma(x3, vk[3], acc[k][3]);
+                            acc[k][0 % U] = cfma(x0, vk[0], acc[k][0 % U]);
+                            acc[k][1 % U] = cfma(x1, vk[1], acc[k][1 % U]);
+                            acc[k][2 % U] = cfma(x2, vk[2], acc[k][2 % U]);
+                            acc[k][3 % U] = cfma(x3, vk[3], acc[k][3 % U]);
                         }
                     }
                     for (; jj < rows; ++jj) {
@@ -272,7 +274,9 @@ __global__ void __launch_bounds__(288) stage_kernel(StageArgs<R> a, int rows_per
 #pragma unroll
                 for (int k = 0; k < NR; ++k) {
                     if (k >= nr) break;
-                    const T sum = cadd(cadd(acc[k][0], acc[k][1]), cadd(acc[k][2], acc[k][3]));
+                    T sum = acc[k][0];
+#pragma unroll
+                    for (int u = 1; u < U; ++u) sum = cadd(sum, acc[k][u]);
                     T* ywk = yw + (long long)(rhs0 + k) * a.wstride;
                     T nv;
                     if (fwd) {
@@ -364,18 +368,39 @@ cudaError_t launch_nr(const StageArgs<R>& a, int nactive, int ny_blocks, int max
 
 }  // namespace
 
+// Fixed shared memory of a CTA with NR right-hand sides (the ring needs at least two more slots).
+template <typename R, int NR>
+static bool stage_fits(int max_mx, int max_my) {
+    using T = Cx<R>;
+    const int mxp = 32 * ((max_mx + 31) / 32);
+    const int maxldx = sizeof(T) == 8 ? ((max_mx + 1) & ~1) : max_mx;
+    const size_t fixed = 2 * (size_t)NR * mxp * sizeof(T) + 2 * (size_t)NR * 2 * (max_mx + max_my) * sizeof(T);
+    int rows = (int)(32768 / ((size_t)maxldx * sizeof(T)));
+    rows = std::min(std::max(4, rows & ~3), max_mx);
+    return fixed + 2 * (size_t)rows * maxldx * sizeof(T) <= 227 * 1024 - 1024;
+}
+
 template <typename R>
 cudaError_t launch_stage(const StageArgs<R>& a, int nactive, int max_mx, int max_my, cudaStream_t st) {
     if (nactive == 0) return cudaSuccess;
     if (max_mx > 256) return cudaErrorInvalidValue;
-    if (a.nrhs >= 4) return launch_nr<R, 4, false>(a, nactive, (a.nrhs + 3) / 4, max_mx, max_my, st);
-    if (a.nrhs >= 2) return launch_nr<R, 2, false>(a, nactive, (a.nrhs + 1) / 2, max_mx, max_my, st);
+    // as many right-hand sides per CTA as the RHS count and shared memory allow
+    if (a.nrhs >= 16 && stage_fits<R, 16>(max_mx, max_my))
+        return launch_nr<R, 16, false>(a, nactive, (a.nrhs + 15) / 16, max_mx, max_my, st);
+    if (a.nrhs >= 8 && stage_fits<R, 8>(max_mx, max_my))
+        return launch_nr<R, 8, false>(a, nactive, (a.nrhs + 7) / 8, max_mx, max_my, st);
+    if (a.nrhs >= 4 && stage_fits<R, 4>(max_mx, max_my))
+        return launch_nr<R, 4, false>(a, nactive, (a.nrhs + 3) / 4, max_mx, max_my, st);
+    if (a.nrhs >= 2 && stage_fits<R, 2>(max_mx, max_my))
+        return launch_nr<R, 2, false>(a, nactive, (a.nrhs + 1) / 2, max_mx, max_my, st);
     return launch_nr<R, 1, false>(a, nactive, a.nrhs, max_mx, max_my, st);
 }
 
 template <typename R>
 cudaError_t launch_basis(const StageArgs<R>& a, int nsub, int ncols, int max_mx, int max_my, cudaStream_t st) {
     if (max_mx > 256) return cudaErrorInvalidValue;
+    if (stage_fits<R, 16>(max_mx, max_my)) return launch_nr<R, 16, true>(a, nsub, (ncols + 15) / 16, max_mx, max_my, st);
+    if (stage_fits<R, 8>(max_mx, max_my)) return launch_nr<R, 8, true>(a, nsub, (ncols + 7) / 8, max_mx, max_my, st);
     return launch_nr<R, 4, true>(a, nsub, (ncols + 3) / 4, max_mx, max_my, st);
 }
 

@@ -118,6 +118,41 @@ def test_precond_apply_c64_matches_oracle(H, case):
     p.close()
 
 
+@pytest.mark.parametrize("prec,tol", [("c128", 1e-10), ("c64", 5e-4)])
+def test_without_boundary_operators_matches_oracle(H, prec, tol):
+    """Sweep steps as full block-tridiagonal solves (no K): the same operator."""
+    w = CASES["uneven_4x3"]()
+    p = H.Problem(w.n, w.n, w.h, w.omega, cuda(w.m2, torch.float64), w.N1, w.N2, w.xcuts, w.ycuts,
+                  boundary_operators=False).factor(prec)
+    dec = Decomposition(w.n, w.h, w.omega, w.m2, w.xcuts, w.ycuts)
+    r = W.random_complex((2, w.N), 9)
+    for sched in ("BSP", "SP"):
+        z = p.precond_apply(cuda(r), sched=sched).cpu().numpy()
+        for k in range(2):
+            assert rel(z[k], Sweeper(dec).precondition(r[k], sched)) <= tol
+    p.close()
+
+
+@pytest.mark.parametrize("ortho", [0, 1])
+def test_gram_schmidt_variants_agree(H, ortho):
+    """Modified (persistent kernel) and reorthogonalised classical Gram-Schmidt
+    both reach the direct solution."""
+    import ctypes
+    w = CASES["tiny_2x2"]()
+    p, _ = make(H, w, "c64")
+    A = assemble_operator(w.n, w.h, w.omega, w.m2).tocsc()
+    ref = spla.spsolve(A, w.h ** 2 * w.f[0])
+    f = cuda(w.f)
+    u = torch.empty_like(f)
+    o = H.default_opts(restart=40, maxit=500, tol=1e-9, ortho=ortho)
+    info = (H.HelmInfo * 1)()
+    st = H.lib().gmres_solve(p._h, ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(u.data_ptr()), 1, ctypes.byref(o),
+                             info, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == 0 and info[0].relres <= 1e-9
+    assert rel(u.cpu().numpy()[0], ref) <= 1e-5
+    p.close()
+
+
 def test_impedance_transmission_matches_oracle(H):
     w = CASES["ragged_3x2"]()
     p, dec = make(H, w, "c128", transmission="impedance")

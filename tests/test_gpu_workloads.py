@@ -1,0 +1,114 @@
+"""GPU checks at the sizes of the named workloads (slow: minutes).
+
+* differentiation (511^2, 4x4, 16 sources, 128 receivers): the adjoint gradient
+  against the oracle's direct-solve adjoint and against central differences
+  on 20 seeded smooth directions (||dm||_inf = 1e-3 max m2, eps = 1).
+* batching (1535^2, 12x12 with uneven subdomains, 64 sources): the
+  preconditioner against the oracle at full size for sampled sources, and the
+  FGMRES residual reported by the library against the residual recomputed on
+  the host with the oracle's sparse matrix.
+"""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+import workloads as W
+from oracle import Decomposition, Sweeper, assemble_operator
+from oracle.adjoint import misfit_gradient_direct
+
+
+@pytest.fixture(scope="module")
+def H():
+    from paper_2209_10886_gb300 import build
+    build.build()
+    from paper_2209_10886_gb300 import helm
+    helm.lib()
+    return helm
+
+
+def cuda(x, dtype=torch.complex128):
+    return torch.as_tensor(np.ascontiguousarray(x)).to(device="cuda", dtype=dtype)
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+@pytest.fixture(scope="module")
+def diff_case():
+    w = W.workload("differentiation")
+    # observed data from the true medium, by a direct solve (oracle)
+    A_true = assemble_operator(w.n, w.h, w.omega, w.m2_true).tocsc()
+    lu = spla.splu(A_true)
+    d = np.stack([lu.solve(w.h ** 2 * w.f[s])[w.rec_idx] for s in range(w.nrhs)])
+    J, g, _ = misfit_gradient_direct(w.n, w.h, w.omega, w.m2, w.f, w.rec_idx, d)
+    return w, d, J, g
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_differentiation_gradient_matches_direct_adjoint(H, diff_case, prec):
+    w, d, J, g = diff_case
+    p = H.Problem(w.n, w.n, w.h, w.omega, cuda(w.m2, torch.float64), w.N1, w.N2, w.xcuts, w.ycuts).factor(prec)
+    Jg, gg, _ = p.misfit_grad(cuda(w.f), torch.as_tensor(w.rec_idx), cuda(d), tol=1e-10, maxit=3000, restart=200)
+    gg = gg.cpu().numpy()
+    print(f"differentiation {prec}: J rel {abs(Jg - J) / J:.2e}, gradient rel {rel(gg, g):.2e}")
+    assert abs(Jg - J) <= 1e-6 * J
+    assert rel(gg, g) <= 1e-5
+    p.close()
+
+
+def test_differentiation_gradient_matches_central_differences(H, diff_case):
+    w, d, J, g = diff_case
+    p = H.Problem(w.n, w.n, w.h, w.omega, cuda(w.m2, torch.float64), w.N1, w.N2, w.xcuts, w.ycuts).factor("c64")
+    _, gg, _ = p.misfit_grad(cuda(w.f), torch.as_tensor(w.rec_idx), cuda(d), tol=1e-10, maxit=3000, restart=200)
+    gg = gg.cpu().numpy()
+    p.close()
+
+    def misfit(m2):
+        q = H.Problem(w.n, w.n, w.h, w.omega, cuda(m2, torch.float64), w.N1, w.N2, w.xcuts, w.ycuts).factor("c64")
+        u, info, _ = q.solve(cuda(w.f), tol=1e-10, maxit=3000, restart=200)
+        q.close()
+        uh = u.cpu().numpy()
+        return 0.5 * float(np.sum(np.abs(uh[:, w.rec_idx] - d) ** 2))
+
+    worst = 0.0
+    for k in range(20):
+        dm = W.smooth_random_field(w.n, 200 + k, 0.1, w.h).reshape(-1)     # seeded smooth directions
+        dm *= 1e-3 * w.m2.max() / np.abs(dm).max()
+        fd = (misfit(w.m2 + dm) - misfit(w.m2 - dm)) / 2.0                  # eps = 1
+        e = abs(fd - gg @ dm) / abs(fd)
+        worst = max(worst, e)
+    print(f"central differences, 20 directions: worst rel {worst:.2e}")
+    assert worst <= 1e-4
+
+
+def test_batching_preconditioner_matches_oracle_at_full_size(H):
+    w = W.workload("batching", nrhs=64)
+    p = H.Problem(w.n, w.n, w.h, w.omega, cuda(w.m2, torch.float64), w.N1, w.N2, w.xcuts, w.ycuts).factor("c64")
+    z = p.precond_apply(cuda(w.f)).cpu().numpy()                # all 64 sources in one application
+    dec = Decomposition(w.n, w.h, w.omega, w.m2, w.xcuts, w.ycuts)
+    sw = Sweeper(dec)
+    for s in (0, 37, 63):
+        e = rel(z[s], sw.precondition(w.f[s], "BSP"))
+        print(f"batching source {s}: c64 preconditioner rel {e:.2e}")
+        assert e <= 5e-4
+    p.close()
+
+
+def test_batching_fgmres_residuals_are_true_residuals(H):
+    w = W.workload("batching", nrhs=8)
+    p = H.Problem(w.n, w.n, w.h, w.omega, cuda(w.m2, torch.float64), w.N1, w.N2, w.xcuts, w.ycuts).factor("c64")
+    u, info, hist = p.solve(cuda(w.f), tol=1e-6, maxit=60, restart=30, history=True, raise_on_noconv=False)
+    A = assemble_operator(w.n, w.h, w.omega, w.m2)
+    u = u.cpu().numpy()
+    for s in range(8):
+        b = w.h ** 2 * w.f[s]
+        rr = np.linalg.norm(b - A @ u[s]) / np.linalg.norm(b)
+        assert abs(rr - info[s][1]) <= 1e-6 * max(rr, 1e-30) + 1e-12
+        assert info[s][0] == 60 or info[s][1] <= 1e-6
+        h = np.array(hist[s])
+        assert np.all(np.diff(h[:30]) <= 1e-12)                  # GMRES residual is monotone in a cycle
+    p.close()
