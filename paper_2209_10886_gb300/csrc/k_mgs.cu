@@ -129,27 +129,34 @@ __global__ void __launch_bounds__(MT) mgs_kernel(MgsArgs a) {
             const long long p = base + e * stride;
             wr[e] = p < a.n ? w[p] : make_double2(0.0, 0.0);
         }
+        // step k: finish the update with v_{k-1} (h_{k-1} known) and, in the same
+        // pass over the elements, the dot product with v_k against the updated w
+        double2 mh = make_double2(0.0, 0.0);
+        const double2* vprev = nullptr;
         for (int k = 0; k < a.nvec; ++k) {
             const double2* v = a.V + k * a.vsk + r * a.vsr;
             double2 acc = make_double2(0.0, 0.0);
 #pragma unroll
             for (int e = 0; e < EPT; ++e) {
                 const long long p = base + e * stride;
-                if (p < a.n) acc = cfmaconj(v[p], wr[e], acc);
+                if (p < a.n) {
+                    if (vprev) wr[e] = cfma(mh, vprev[p], wr[e]);
+                    acc = cfmaconj(v[p], wr[e], acc);
+                }
             }
             double2 h;
             if (!reduce(acc, h)) return;
             if (blockIdx.x == 0 && threadIdx.x == 0) a.hcol[(long long)r * a.ldh + k] = h;
-            const double2 mh = make_double2(-h.x, -h.y);
-#pragma unroll
-            for (int e = 0; e < EPT; ++e) {
-                const long long p = base + e * stride;
-                if (p < a.n) wr[e] = cfma(mh, v[p], wr[e]);
-            }
+            mh = make_double2(-h.x, -h.y);
+            vprev = v;
         }
         double nrm = 0.0;
 #pragma unroll
-        for (int e = 0; e < EPT; ++e) nrm = fma(wr[e].x, wr[e].x, fma(wr[e].y, wr[e].y, nrm));
+        for (int e = 0; e < EPT; ++e) {
+            const long long p = base + e * stride;
+            if (vprev && p < a.n) wr[e] = cfma(mh, vprev[p], wr[e]);
+            nrm = fma(wr[e].x, wr[e].x, fma(wr[e].y, wr[e].y, nrm));
+        }
         double2 tot;
         if (!reduce(make_double2(nrm, 0.0), tot)) return;
         const double hn = sqrt(tot.x);

@@ -70,7 +70,8 @@ __device__ __forceinline__ void consumer_sync(int nthreads) {
 // BASIS = true: the NR right-hand sides of a CTA are unit data at consecutive
 // interface boundary points (columns of the boundary operator K, see StageArgs).
 template <typename R, int NR, bool BASIS>
-__global__ void __launch_bounds__(288) stage_kernel(StageArgs<R> a, int rows_per_chunk, int nslots, int cwarps) {
+__global__ void __launch_bounds__(NR <= 4 ? 544 : 288) stage_kernel(StageArgs<R> a, int rows_per_chunk, int nslots,
+                                                                  int cwarps, int ngroups) {
     using T = Cx<R>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) unsigned long long full_bar[MAXNS], empty_bar[MAXNS];
@@ -84,14 +85,18 @@ __global__ void __launch_bounds__(288) stage_kernel(StageArgs<R> a, int rows_per
     if (BASIS && e0 >= sd.Lb) return;
     const int nr = BASIS ? min(NR, sd.Lb - e0) : min(NR, a.nrhs - rhs0);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int ncons = 32 * cwarps;                       // consumer threads (warps 0 .. cwarps-1)
-    const bool producer = warp == cwarps;
-    const int col = tid;                                 // consumer thread = output column
-    const bool owner = !producer && col < mx;
+    // consumers: ngroups groups of cwarps warps; thread (grp, col) sums the rows
+    // grp, grp + ngroups, ... of every chunk for output column col
+    const int ncons = 32 * cwarps * ngroups;
+    const bool producer = warp == cwarps * ngroups;
+    const int col = tid % (32 * cwarps);
+    const int grp = tid / (32 * cwarps);
+    const bool worker = !producer && col < mx;
+    const bool owner = worker && grp == 0;               // finishes column col of every row
     const int Rch = rows_per_chunk;
     const int nq = (mx + Rch - 1) / Rch;
     const int Q = (2 * my - 1) * nq;
-    const int mxp = ncons;
+    const int mxp = 32 * cwarps;
     // boundary arrays per RHS: W[my] | E[my] | S[mx] | N[mx]
     const int L = 2 * (mx + my);
     auto boff = [&](int side) { return side < 2 ? side * my : 2 * my + (side - 2) * mx; };
@@ -102,6 +107,7 @@ __global__ void __launch_bounds__(288) stage_kernel(StageArgs<R> a, int rows_per
     T* vbuf = ring + (size_t)nslots * slot_elems;
     T* binc = vbuf + 2 * (size_t)NR * mxp;
     T* ub = binc + (size_t)NR * L;
+    T* part = ub + (size_t)NR * L;                       // [ngroups-1][NR][mxp] row-group partial sums
 
     const long long N = (long long)a.nx * a.ny;
     const T* Xs = a.X + sd.xoff;
@@ -147,7 +153,7 @@ __global__ void __launch_bounds__(288) stage_kernel(StageArgs<R> a, int rows_per
     if (tid == 0) {
         for (int i = 0; i < nslots; ++i) {
             mbar_init(&full_bar[i], 1);
-            mbar_init(&empty_bar[i], cwarps);
+            mbar_init(&empty_bar[i], cwarps * ngroups);
         }
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
@@ -242,24 +248,25 @@ __global__ void __launch_bounds__(288) stage_kernel(StageArgs<R> a, int rows_per
                     abort_flag = 1;
                     if (a.err) atomicExch(a.err, (int)HELM_ERR_TIMEOUT);
                 }
-                if (owner && !*((volatile int*)&abort_flag)) {
+                if (worker && !*((volatile int*)&abort_flag)) {
                     const T* S = ring + (size_t)slot * slot_elems + col;
                     const T* vq = v + q * Rch;
                     const int rows = min(Rch, mx - q * Rch);
-                    int jj = 0;
-                    for (; jj + 4 <= rows; jj += 4) {
-                        const T x0 = S[(size_t)(jj + 0) * ldx], x1 = S[(size_t)(jj + 1) * ldx];
-                        const T x2 = S[(size_t)(jj + 2) * ldx], x3 = S[(size_t)(jj + 3) * ldx];
+                    const int G = ngroups;
+                    int jj = grp;
+                    for (; jj + 3 * G < rows; jj += 4 * G) {
+                        const T x0 = S[(size_t)(jj + 0 * G) * ldx], x1 = S[(size_t)(jj + 1 * G) * ldx];
+                        const T x2 = S[(size_t)(jj + 2 * G) * ldx], x3 = S[(size_t)(jj + 3 * G) * ldx];
 #pragma unroll
                         for (int k = 0; k < NR; ++k) {
                             const T* vk = vq + k * mxp + jj;
-                            acc[k][0 % U] = cfma(x0, vk[0], acc[k][0 % U]);
-                            acc[k][1 % U] = cfma(x1, vk[1], acc[k][1 % U]);
-                            acc[k][2 % U] = cfma(x2, vk[2], acc[k][2 % U]);
-                            acc[k][3 % U] = cfma(x3, vk[3], acc[k][3 % U]);
+                            acc[k][0 % U] = cfma(x0, vk[0 * G], acc[k][0 % U]);
+                            acc[k][1 % U] = cfma(x1, vk[1 * G], acc[k][1 % U]);
+                            acc[k][2 % U] = cfma(x2, vk[2 * G], acc[k][2 % U]);
+                            acc[k][3 % U] = cfma(x3, vk[3 * G], acc[k][3 % U]);
                         }
                     }
-                    for (; jj < rows; ++jj) {
+                    for (; jj < rows; jj += G) {
                         const T x0 = S[(size_t)jj * ldx];
 #pragma unroll
                         for (int k = 0; k < NR; ++k) acc[k][0] = cfma(x0, vq[k * mxp + jj], acc[k][0]);
@@ -268,6 +275,25 @@ __global__ void __launch_bounds__(288) stage_kernel(StageArgs<R> a, int rows_per
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&empty_bar[slot]);
                 if (++slot == nslots) { slot = 0; ph ^= 1u; }
+            }
+            if (ngroups > 1) {
+                // row groups 1.. hand their partial sums to group 0
+                if (worker && grp > 0) {
+#pragma unroll
+                    for (int k = 0; k < NR; ++k) {
+                        T sum = acc[k][0];
+#pragma unroll
+                        for (int u = 1; u < U; ++u) sum = cadd(sum, acc[k][u]);
+                        part[((size_t)(grp - 1) * NR + k) * mxp + col] = sum;
+                    }
+                }
+                consumer_sync(ncons);
+                if (owner) {
+#pragma unroll
+                    for (int k = 0; k < NR; ++k)
+                        for (int g2 = 1; g2 < ngroups; ++g2)
+                            acc[k][0] = cadd(acc[k][0], part[((size_t)(g2 - 1) * NR + k) * mxp + col]);
+                }
             }
             T* vn = vbuf + (size_t)(cur ^ 1) * NR * mxp;
             if (owner) {
@@ -345,8 +371,11 @@ cudaError_t launch_nr(const StageArgs<R>& a, int nactive, int ny_blocks, int max
     using T = Cx<R>;
     const int cwarps = (max_mx + 31) / 32;
     const int mxp = 32 * cwarps;
+    // row groups raise the number of consumer warps (latency hiding) for few RHS
+    const int ngroups = NR <= 4 ? std::max(1, std::min(4, 16 / cwarps)) : 1;
     const int maxldx = sizeof(T) == 8 ? ((max_mx + 1) & ~1) : max_mx;
-    const size_t fixed = 2 * (size_t)NR * mxp * sizeof(T) + 2 * (size_t)NR * 2 * (max_mx + max_my) * sizeof(T);
+    const size_t fixed = 2 * (size_t)NR * mxp * sizeof(T) + 2 * (size_t)NR * 2 * (max_mx + max_my) * sizeof(T) +
+                         (size_t)(ngroups - 1) * NR * mxp * sizeof(T);
     const size_t budget = 227 * 1024 - 1024;
     if (fixed >= budget) return cudaErrorInvalidValue;
     // chunk of ~32 KB, a multiple of 4 rows
@@ -362,7 +391,7 @@ cudaError_t launch_nr(const StageArgs<R>& a, int nactive, int ny_blocks, int max
     if (e != cudaSuccess) return e;
     dim3 grid(nactive, ny_blocks);
     count_launch();
-    stage_kernel<R, NR, BASIS><<<grid, 32 * (cwarps + 1), smem, st>>>(a, rows, nslots, cwarps);
+    stage_kernel<R, NR, BASIS><<<grid, 32 * (cwarps * ngroups + 1), smem, st>>>(a, rows, nslots, cwarps, ngroups);
     return cudaGetLastError();
 }
 
@@ -374,7 +403,9 @@ static bool stage_fits(int max_mx, int max_my) {
     using T = Cx<R>;
     const int mxp = 32 * ((max_mx + 31) / 32);
     const int maxldx = sizeof(T) == 8 ? ((max_mx + 1) & ~1) : max_mx;
-    const size_t fixed = 2 * (size_t)NR * mxp * sizeof(T) + 2 * (size_t)NR * 2 * (max_mx + max_my) * sizeof(T);
+    const int ngroups = NR <= 4 ? std::max(1, std::min(4, 16 / ((max_mx + 31) / 32))) : 1;
+    const size_t fixed = 2 * (size_t)NR * mxp * sizeof(T) + 2 * (size_t)NR * 2 * (max_mx + max_my) * sizeof(T) +
+                         (size_t)(ngroups - 1) * NR * mxp * sizeof(T);
     int rows = (int)(32768 / ((size_t)maxldx * sizeof(T)));
     rows = std::min(std::max(4, rows & ~3), max_mx);
     return fixed + 2 * (size_t)rows * maxldx * sizeof(T) <= 227 * 1024 - 1024;
