@@ -158,6 +158,8 @@ struct helm_problem {
     std::vector<std::vector<int>> ondiag;
     std::vector<int> all;
     int max_mx = 0, max_my = 0, max_Lb = 0;
+    int max_w = 0, max_ld = 0;       // widest column half and largest half leading dimension of the factors
+    int num_sms = 0;
     long long ntrace = 0;
     int nslots = 0;
     std::vector<StageDesc> sched[2];
@@ -367,6 +369,12 @@ extern "C" helm_status helm_setup(int n_x, int n_y, double h, double omega, cons
     if (!p) { set_error("helm_setup: host allocation failed"); return HELM_ERR_OOM; }
     p->nx = n_x; p->ny = n_y; p->N1 = N1; p->N2 = N2; p->h = h; p->omega = omega; p->sopts = so;
     p->xcut = xc; p->ycut = yc;
+    {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            p->num_sms = 1;                     // a later CUDA call reports the failure
+    }
     const int Ng = N1 + N2 - 1;
 
     // subdomains in the paper's order on multi-indices (|i|_1, then i1), Section 2
@@ -567,7 +575,7 @@ static helm_status build_boundary_operators_t(helm_problem* p, cudaStream_t st) 
     a.err = p->d_err;
     for (int c0 = 0; c0 < p->max_Lb && e == cudaSuccess; c0 += NB) {
         a.col0 = c0;
-        e = launch_basis<R>(a, (int)p->subs.size(), NB, p->max_mx, p->max_my, st);
+        e = launch_basis<R>(a, (int)p->subs.size(), NB, p->max_mx, p->max_my, p->max_w, p->max_ld, st);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     cudaFree(yws);
@@ -588,14 +596,24 @@ extern "C" helm_status precond_factor(helm_problem* p, helm_prec prec, void* str
     if (prec != HELM_PREC_C128 && prec != HELM_PREC_C64) return arg_error("precond_factor: unknown precision");
     cudaStream_t st = (cudaStream_t)stream;
     const size_t elem = prec == HELM_PREC_C64 ? sizeof(float2) : sizeof(double2);
-    // layout of the stored X_r: per subdomain my blocks of mx x ldx (ldx even for complex64,
-    // so that every block and row chunk starts on a 16-byte boundary)
+    // layout of the stored X_r: per subdomain my blocks, each two column halves of
+    // widths w0 = mx/2 rounded up to even and mx - w0, leading dimensions even for
+    // complex64 so that every half, block and row chunk starts on a 16-byte boundary
     long long xoff = 0;
     std::vector<SubDev> tab;
+    p->max_w = p->max_ld = 0;
     for (auto& s : p->subs) {
-        s.dev.ldx = prec == HELM_PREC_C64 ? ((s.dev.mx + 1) & ~1) : s.dev.mx;
+        const int mx = s.dev.mx;
+        const int w0 = std::min(mx, ((mx + 1) / 2 + 1) & ~1);
+        const int w1 = mx - w0;
+        s.dev.w0 = w0;
+        s.dev.ld0 = w0;                                                   // even (or mx itself when mx <= 2)
+        s.dev.ld1 = prec == HELM_PREC_C64 ? ((w1 + 1) & ~1) : w1;
+        if (prec == HELM_PREC_C64 && (s.dev.ld0 & 1)) s.dev.ld0 += 1;
         s.dev.xoff = xoff;
-        xoff += (long long)s.dev.my * s.dev.mx * s.dev.ldx;
+        xoff += (long long)s.dev.my * mx * (s.dev.ld0 + s.dev.ld1);
+        p->max_w = std::max(p->max_w, std::max(w0, w1));
+        p->max_ld = std::max(p->max_ld, std::max(s.dev.ld0, s.dev.ld1));
         tab.push_back(s.dev);
     }
     const size_t bytes = (size_t)xoff * elem;
@@ -762,7 +780,8 @@ static helm_status run_precond_t(helm_problem* p, const PcWork& w, int sched, co
             }
         }
         prof_begin(p, HELM_K_STAGE, st);
-        cudaError_t e = launch_stage<R>(a, (int)sd.subs.size(), p->max_mx, p->max_my, st);
+        cudaError_t e = launch_stage<R>(a, (int)sd.subs.size(), p->max_mx, p->max_my, p->max_w, p->max_ld,
+                                        p->num_sms, st);
         prof_end(p, HELM_K_STAGE, bytes, st, flops);
         if (e != cudaSuccess) return cuda_status(e, "stage launch");
     }

@@ -55,7 +55,10 @@ enum Side { SW = 0, SE = 1, SS = 2, SN = 3 };   // neighbour direction: west, ea
 // One subdomain as the kernels see it.
 struct SubDev {
     int x0, y0, mx, my;        // node box origin and size (0-based global nodes)
-    int ldx;                   // leading dimension of each stored X_r (elements)
+    // each stored X_r is two column halves, each row-major: columns [0, w0) with
+    // leading dimension ld0, then columns [w0, mx) with leading dimension ld1
+    // (element (i, j) at i*ld0 + j, or mx*ld0 + i*ld1 + (j - w0))
+    int w0, ld0, ld1;
     int tin[4];                // start of the incoming slot (this, neighbour) in the trace buffer, -1: outer side
     int tout[4];               // start of the slot (neighbour, this) that receives this subdomain's outgoing data
     long long xoff;            // element offset of X_1 of this subdomain in the factor array
@@ -159,11 +162,14 @@ template <typename R>
 cudaError_t launch_factor(const SubDev* subtab, int nsub, int max_mx, const double2* dloc,
                           Cx<R>* X, Cx<R>* work, size_t work_stride, int* info, cudaStream_t st);
 // stage
+// max_w: widest column half, max_ld: largest half leading dimension, num_sms: SMs of the device
 template <typename R>
-cudaError_t launch_stage(const StageArgs<R>& a, int nactive, int max_mx, int max_my, cudaStream_t st);
+cudaError_t launch_stage(const StageArgs<R>& a, int nactive, int max_mx, int max_my, int max_w, int max_ld,
+                         int num_sms, cudaStream_t st);
 // boundary operators K of all subdomains, columns [col0, col0 + ncols) per launch
 template <typename R>
-cudaError_t launch_basis(const StageArgs<R>& a, int nsub, int ncols, int max_mx, int max_my, cudaStream_t st);
+cudaError_t launch_basis(const StageArgs<R>& a, int nsub, int ncols, int max_mx, int max_my, int max_w, int max_ld,
+                         cudaStream_t st);
 template <typename R>
 cudaError_t launch_iface(const IfaceArgs<R>& a, int nactive, int max_rows, int max_Lb, cudaStream_t st);
 // krylov / vector kernels

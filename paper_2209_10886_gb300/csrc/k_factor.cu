@@ -30,7 +30,13 @@ __global__ void __launch_bounds__(FT) factor_kernel(const SubDev* __restrict__ s
     using T = Cx<R>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const SubDev sd = subtab[blockIdx.x];
-    const int m = sd.mx, my = sd.my, ldx = sd.ldx;
+    const int m = sd.mx, my = sd.my;
+    const int w0 = sd.w0, ld0 = sd.ld0, ld1 = sd.ld1;
+    const long long xr_elems = (long long)m * (ld0 + ld1);
+    // element (i, j) of a stored X_r (two column halves)
+    auto xidx = [&](int i, int j) -> long long {
+        return j < w0 ? (long long)i * ld0 + j : (long long)m * ld0 + (long long)i * ld1 + (j - w0);
+    };
     const int tid = threadIdx.x;
     T* W = use_smem ? reinterpret_cast<T*>(smem_raw) : work + blockIdx.x * work_stride;
     unsigned char* tail = smem_raw + (use_smem ? (size_t)m * m * sizeof(T) : 0);
@@ -43,10 +49,14 @@ __global__ void __launch_bounds__(FT) factor_kernel(const SubDev* __restrict__ s
     for (int r = 0; r < my; ++r) {
         // T_r = D_r - X_{r-1}
         const double2* d = dloc + sd.loff + (long long)r * m;
-        const T* Xp = X + sd.xoff + (long long)(r - 1) * m * ldx;
+        const T* Xp = X + sd.xoff + (long long)(r - 1) * xr_elems;
         for (int idx = tid; idx < m * m; idx += FT) {
             const int i = idx / m, j = idx - i * m;
-            T v = r > 0 ? mk(-Xp[(long long)i * ldx + j].x, -Xp[(long long)i * ldx + j].y) : czero<T>();
+            T v = czero<T>();
+            if (r > 0) {
+                const T xp = Xp[xidx(i, j)];
+                v = mk(-xp.x, -xp.y);
+            }
             if (i == j) v = cadd(v, from_c128<T>(d[i]));
             else if (i - j == 1 || j - i == 1) v.x -= (R)1;
             W[idx] = v;
@@ -114,12 +124,25 @@ __global__ void __launch_bounds__(FT) factor_kernel(const SubDev* __restrict__ s
             }
             __syncthreads();
         }
-        // X_r = (W + W^T)/2, padded columns zeroed
-        T* Xr = X + sd.xoff + (long long)r * m * ldx;
-        for (int idx = tid; idx < m * ldx; idx += FT) {
-            const int i = idx / ldx, j = idx - i * ldx;
+        // X_r = (W + W^T)/2 in the two-half layout, padding columns zeroed
+        T* Xr = X + sd.xoff + (long long)r * xr_elems;
+        for (long long idx = tid; idx < xr_elems; idx += FT) {
+            int i, j;
+            bool pad;
+            if (idx < (long long)m * ld0) {
+                i = (int)(idx / ld0);
+                const int jj = (int)(idx - (long long)i * ld0);
+                j = jj;
+                pad = jj >= w0;
+            } else {
+                const long long t2 = idx - (long long)m * ld0;
+                i = (int)(t2 / ld1);
+                const int jj = (int)(t2 - (long long)i * ld1);
+                j = w0 + jj;
+                pad = j >= m;
+            }
             T v = czero<T>();
-            if (j < m) v = cscale(cadd(W[(long long)i * m + j], W[(long long)j * m + i]), (R)0.5);
+            if (!pad) v = cscale(cadd(W[(long long)i * m + j], W[(long long)j * m + i]), (R)0.5);
             Xr[idx] = v;
         }
         __syncthreads();

@@ -9,13 +9,19 @@
 //     forward   y_1 = X_1 b_1,        y_r = X_r (b_r + y_{r-1})
 //     backward  u_my = y_my,          u_r = y_r + X_r u_{r+1}
 // X_r is complex symmetric, so y = X v is computed column-wise from the
-// row-major storage: one consumer thread per output column, coalesced rows in
-// shared memory, four independent partial sums.  X is streamed from HBM by
+// row-major storage: consumer threads own output columns (row groups split
+// the rows of each chunk), coalesced rows in shared memory.  X is stored as
+// two column halves (each half row-major, see SubDev), streamed from HBM by
 // bulk (TMA) copies that one producer thread issues into a ring of shared
-// memory slots guarded by full/empty mbarriers; the first X of the backward
-// pass follows the last forward one in the same stream of chunks.  Every
-// mbarrier wait is bounded in time; on expiry the kernel records HELM_ERR_TIMEOUT
-// in a device flag, drains its own copies and returns.
+// memory slots guarded by full/empty mbarriers.
+//
+// A subdomain is solved either by one CTA (both halves) or by a cluster of
+// two CTAs, one per half: each computes its half of y, and after every grid
+// row the two exchange their halves of the next input vector through
+// distributed shared memory, signalled by a remote mbarrier arrival.  Every
+// wait is bounded in time; on expiry the kernel records HELM_ERR_TIMEOUT in a
+// device flag, finishes its (now meaningless) steps without waiting, drains
+// its own copies and skips the epilogue.
 //
 // Outgoing data toward the neighbour across side s (scaled form of
 // (-d_{n_{i,j}} - T) u_i):  G_out = ca * G_in + cb * u_p  with the edge's
@@ -48,12 +54,25 @@ __device__ __forceinline__ bool mbar_try(unsigned long long* b, unsigned parity)
         : "memory");
     return ok != 0;
 }
-// wait for the phase with this parity, at most WAIT_LIMIT cycles
-__device__ __forceinline__ bool mbar_wait(unsigned long long* b, unsigned parity) {
-    if (mbar_try(b, parity)) return true;
+// the same with acquire semantics at cluster scope (data written by the peer CTA)
+__device__ __forceinline__ bool mbar_try_cluster(unsigned long long* b, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// wait for the phase with this parity, at most `limit` cycles
+template <bool CLUSTER>
+__device__ __forceinline__ bool mbar_wait(unsigned long long* b, unsigned parity, long long limit) {
+    auto t = [&]() { return CLUSTER ? mbar_try_cluster(b, parity) : mbar_try(b, parity); };
+    if (t()) return true;
     const long long t0 = clock64();
-    while (!mbar_try(b, parity))
-        if (clock64() - t0 > WAIT_LIMIT) return false;
+    while (!t())
+        if (clock64() - t0 > limit) return false;
     return true;
 }
 __device__ __forceinline__ void bulk_copy(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
@@ -66,48 +85,83 @@ __device__ __forceinline__ void bulk_copy(void* dst, const void* src, unsigned b
 __device__ __forceinline__ void consumer_sync(int nthreads) {
     asm volatile("bar.sync 1, %0;\n" ::"r"(nthreads) : "memory");
 }
+// address of the same shared-memory location in CTA `rank` of the cluster
+__device__ __forceinline__ unsigned peer_addr(const void* p, unsigned rank) {
+    unsigned r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;\n" : "=r"(r) : "r"(smem_addr(p)), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void st_peer(unsigned addr, float2 v) {
+    asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};\n" ::"r"(addr), "f"(v.x), "f"(v.y) : "memory");
+}
+__device__ __forceinline__ void st_peer(unsigned addr, double2 v) {
+    asm volatile("st.shared::cluster.v2.f64 [%0], {%1, %2};\n" ::"r"(addr), "d"(v.x), "d"(v.y) : "memory");
+}
+__device__ __forceinline__ void arrive_peer(unsigned addr) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];\n" ::"r"(addr) : "memory");
+}
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.aligned;\nbarrier.cluster.wait.aligned;\n" ::: "memory");
+}
 
 // BASIS = true: the NR right-hand sides of a CTA are unit data at consecutive
 // interface boundary points (columns of the boundary operator K, see StageArgs).
+// csize = 1: one CTA per subdomain; csize = 2: a cluster of two, one per column half.
 template <typename R, int NR, bool BASIS>
 __global__ void __launch_bounds__(NR <= 4 ? 544 : 288) stage_kernel(StageArgs<R> a, int rows_per_chunk, int nslots,
-                                                                  int cwarps, int ngroups) {
+                                                                  int cwarps, int ngroups, int csize) {
     using T = Cx<R>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ __align__(8) unsigned long long full_bar[MAXNS], empty_bar[MAXNS];
+    __shared__ __align__(8) unsigned long long full_bar[MAXNS], empty_bar[MAXNS], xbar;
     __shared__ int abort_flag;
 
-    const int s = BASIS ? blockIdx.x : a.subs[blockIdx.x];
+    const int rank = csize == 2 ? (int)(blockIdx.x & 1) : 0;
+    const int s = BASIS ? blockIdx.x / csize : a.subs[blockIdx.x / csize];
     const SubDev sd = a.subtab[s];
-    const int mx = sd.mx, my = sd.my, ldx = sd.ldx;
+    const int mx = sd.mx, my = sd.my;
     const int rhs0 = blockIdx.y * NR;                    // first RHS (workspace slot) of this CTA
     const int e0 = BASIS ? a.col0 + rhs0 : 0;            // first boundary point (basis mode)
+    // uniform across the cluster: both CTAs share blockIdx.y and the subdomain
     if (BASIS && e0 >= sd.Lb) return;
     const int nr = BASIS ? min(NR, sd.Lb - e0) : min(NR, a.nrhs - rhs0);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    // consumers: ngroups groups of cwarps warps; thread (grp, col) sums the rows
-    // grp, grp + ngroups, ... of every chunk for output column col
+    // columns of this CTA: the half `rank` (cluster) or all of them
+    const int w0 = sd.w0;
+    const int c_lo = csize == 2 ? (rank ? w0 : 0) : 0;
+    const int c_hi = csize == 2 ? (rank ? mx : w0) : mx;
+    // consumers: ngroups groups of cwarps warps; thread (grp, c) sums the rows
+    // grp, grp + ngroups, ... of every chunk for output column c_lo + c
     const int ncons = 32 * cwarps * ngroups;
     const bool producer = warp == cwarps * ngroups;
-    const int col = tid % (32 * cwarps);
+    const int col = c_lo + tid % (32 * cwarps);
     const int grp = tid / (32 * cwarps);
-    const bool worker = !producer && col < mx;
+    const bool worker = !producer && col < c_hi;
     const bool owner = worker && grp == 0;               // finishes column col of every row
+    const int myhalf = col < w0 ? 0 : 1;
     const int Rch = rows_per_chunk;
-    const int nq = (mx + Rch - 1) / Rch;
-    const int Q = (2 * my - 1) * nq;
-    const int mxp = 32 * cwarps;
+    const int nq = (mx + Rch - 1) / Rch;                 // chunks per half per step
+    const int h_first = csize == 2 ? rank : 0;           // halves streamed by this CTA
+    const int nhalves = csize == 2 ? 1 : (w0 < mx ? 2 : 1);   // a one-node-wide subdomain has one half
+    const int cps = nq * nhalves;                        // chunks per step
+    const int nsteps = 2 * my - 1;
+    const int Q = nsteps * cps;
+    const int mxp = 32 * ((mx + 31) / 32 > 0 ? (mx + 31) / 32 : 1);   // v rows (full length)
+    const int cw = 32 * cwarps;                                        // part rows (this CTA's columns)
     // boundary arrays per RHS: W[my] | E[my] | S[mx] | N[mx]
     const int L = 2 * (mx + my);
     auto boff = [&](int side) { return side < 2 ? side * my : 2 * my + (side - 2) * mx; };
+    const int ldh[2] = {sd.ld0, sd.ld1};
+    const long long hoff1 = (long long)mx * sd.ld0;     // element offset of half 1 in X_r
+    const long long xr_elems = (long long)mx * (sd.ld0 + sd.ld1);
+    const int ldmax = max(sd.ld0, sd.ld1);
 
-    // dynamic shared memory: ring[nslots][Rch*ldx] | v[2][NR][mxp] | binc[NR][L] | ub[NR][L]
+    // dynamic shared memory: ring[nslots][Rch*ldmax] | v[2][NR][mxp_max] | binc[NR][L] | ub[NR][L] | part
     T* ring = reinterpret_cast<T*>(smem_raw);
-    const size_t slot_elems = (size_t)Rch * ldx;
+    const size_t slot_elems = (size_t)Rch * ldmax;
     T* vbuf = ring + (size_t)nslots * slot_elems;
     T* binc = vbuf + 2 * (size_t)NR * mxp;
     T* ub = binc + (size_t)NR * L;
-    T* part = ub + (size_t)NR * L;                       // [ngroups-1][NR][mxp] row-group partial sums
+    T* part = ub + (size_t)NR * L;                       // [ngroups-1][NR][cw] row-group partial sums
 
     const long long N = (long long)a.nx * a.ny;
     const T* Xs = a.X + sd.xoff;
@@ -148,6 +202,11 @@ __global__ void __launch_bounds__(NR <= 4 ? 544 : 288) stage_kernel(StageArgs<R>
                 make_double2(zu.x * zsc[k], zu.y * zsc[k]);
         }
     };
+    // is boundary point e (of side `side`, index pt along it) in this CTA's columns?
+    auto owns_point = [&](int side, int pt) {
+        const int c = side == SW ? 0 : side == SE ? mx - 1 : pt;
+        return c >= c_lo && c < c_hi;
+    };
 
     // ---- prologue: barriers, incoming terms G_in/(1-beta) into shared memory, v = b_1
     if (tid == 0) {
@@ -155,6 +214,7 @@ __global__ void __launch_bounds__(NR <= 4 ? 544 : 288) stage_kernel(StageArgs<R>
             mbar_init(&full_bar[i], 1);
             mbar_init(&empty_bar[i], cwarps * ngroups);
         }
+        mbar_init(&xbar, 1);
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
@@ -182,42 +242,48 @@ __global__ void __launch_bounds__(NR <= 4 ? 544 : 288) stage_kernel(StageArgs<R>
         vbuf[idx] = b;
     }
     __syncthreads();
+    // both CTAs of a cluster have initialised their barriers before any remote arrival
+    if (csize == 2) cluster_sync_all();
 
     if (producer) {
-        // ---- producer: one thread streams every chunk of X_1..X_my, X_{my-1}..X_1
+        // ---- producer: one thread streams the chunks of X_1..X_my, X_{my-1}..X_1
         if (lane == 0) {
-            int r = 0, q = 0, slot = 0;
+            int r = 0, q = 0, hh = 0, slot = 0, step = 0;
             unsigned ph = 0;
-            bool fwd = true;
             int issued = 0;
             for (int t = 0; t < Q; ++t) {
-                if (t >= nslots && !mbar_wait(&empty_bar[slot], ph ^ 1u)) {
+                if (*((volatile int*)&abort_flag)) break;
+                if (t >= nslots && !mbar_wait<false>(&empty_bar[slot], ph ^ 1u, WAIT_LIMIT)) {
                     abort_flag = 1;
                     if (a.err) atomicExch(a.err, (int)HELM_ERR_TIMEOUT);
                     break;
                 }
-                if (*((volatile int*)&abort_flag)) break;
+                const int half = h_first + hh;
+                const int ld = ldh[half];
                 const int rows = min(Rch, mx - q * Rch);
-                const unsigned bytes = (unsigned)((size_t)rows * ldx * sizeof(T));
+                const unsigned bytes = (unsigned)((size_t)rows * ld * sizeof(T));
+                const T* src = Xs + (long long)r * xr_elems + (half ? hoff1 : 0) + (long long)q * Rch * ld;
                 mbar_expect_tx(&full_bar[slot], bytes);
-                bulk_copy(ring + (size_t)slot * slot_elems, Xs + (long long)r * mx * ldx + (long long)q * Rch * ldx,
-                          bytes, &full_bar[slot]);
+                bulk_copy(ring + (size_t)slot * slot_elems, src, bytes, &full_bar[slot]);
                 ++issued;
                 if (++slot == nslots) { slot = 0; ph ^= 1u; }
                 if (++q == nq) {
                     q = 0;
-                    if (fwd) { if (++r == my) { fwd = false; r = my - 2; } }
-                    else --r;
+                    if (++hh == nhalves) {
+                        hh = 0;
+                        ++step;
+                        r = step < my ? step : 2 * my - 2 - step;
+                    }
                 }
             }
             if (*((volatile int*)&abort_flag)) {
                 // drain: wait (bounded) for every copy this CTA issued before leaving
                 for (int t = max(0, issued - nslots); t < issued; ++t)
-                    mbar_wait(&full_bar[t % nslots], (unsigned)((t / nslots) & 1));
+                    mbar_wait<false>(&full_bar[t % nslots], (unsigned)((t / nslots) & 1), WAIT_LIMIT);
             }
         }
     } else {
-        // ---- consumers: y = X v column-wise, one thread per column
+        // ---- consumers: y = X v column-wise
         double2 rnext[NR];
         T ynext[NR];
 #pragma unroll
@@ -231,7 +297,6 @@ __global__ void __launch_bounds__(NR <= 4 ? 544 : 288) stage_kernel(StageArgs<R>
         int slot = 0;
         unsigned ph = 0;
         int cur = 0;                                      // v buffer holding the current step's input
-        const int nsteps = 2 * my - 1;
         for (int step = 0; step < nsteps; ++step) {
             const bool fwd = step < my;
             const int r = fwd ? step : 2 * my - 2 - step;
@@ -243,20 +308,23 @@ __global__ void __launch_bounds__(NR <= 4 ? 544 : 288) stage_kernel(StageArgs<R>
             for (int k = 0; k < NR; ++k)
 #pragma unroll
                 for (int u = 0; u < U; ++u) acc[k][u] = czero<T>();
-            for (int q = 0; q < nq; ++q) {
-                if (!mbar_wait(&full_bar[slot], ph)) {
+            for (int c = 0; c < cps; ++c) {
+                const int half = h_first + c / nq, q = c % nq;
+                const bool ab = *((volatile int*)&abort_flag) != 0;
+                if (!mbar_wait<false>(&full_bar[slot], ph, ab ? 0 : WAIT_LIMIT)) {
                     abort_flag = 1;
                     if (a.err) atomicExch(a.err, (int)HELM_ERR_TIMEOUT);
                 }
-                if (worker && !*((volatile int*)&abort_flag)) {
-                    const T* S = ring + (size_t)slot * slot_elems + col;
+                if (worker && half == myhalf && !*((volatile int*)&abort_flag)) {
+                    const int ld = ldh[half];
+                    const T* S = ring + (size_t)slot * slot_elems + (col - (half ? w0 : 0));
                     const T* vq = v + q * Rch;
                     const int rows = min(Rch, mx - q * Rch);
                     const int G = ngroups;
                     int jj = grp;
                     for (; jj + 3 * G < rows; jj += 4 * G) {
-                        const T x0 = S[(size_t)(jj + 0 * G) * ldx], x1 = S[(size_t)(jj + 1 * G) * ldx];
-                        const T x2 = S[(size_t)(jj + 2 * G) * ldx], x3 = S[(size_t)(jj + 3 * G) * ldx];
+                        const T x0 = S[(size_t)(jj + 0 * G) * ld], x1 = S[(size_t)(jj + 1 * G) * ld];
+                        const T x2 = S[(size_t)(jj + 2 * G) * ld], x3 = S[(size_t)(jj + 3 * G) * ld];
 #pragma unroll
                         for (int k = 0; k < NR; ++k) {
                             const T* vk = vq + k * mxp + jj;
@@ -267,7 +335,7 @@ __global__ void __launch_bounds__(NR <= 4 ? 544 : 288) stage_kernel(StageArgs<R>
                         }
                     }
                     for (; jj < rows; jj += G) {
-                        const T x0 = S[(size_t)jj * ldx];
+                        const T x0 = S[(size_t)jj * ld];
 #pragma unroll
                         for (int k = 0; k < NR; ++k) acc[k][0] = cfma(x0, vq[k * mxp + jj], acc[k][0]);
                     }
@@ -284,7 +352,7 @@ __global__ void __launch_bounds__(NR <= 4 ? 544 : 288) stage_kernel(StageArgs<R>
                         T sum = acc[k][0];
 #pragma unroll
                         for (int u = 1; u < U; ++u) sum = cadd(sum, acc[k][u]);
-                        part[((size_t)(grp - 1) * NR + k) * mxp + col] = sum;
+                        part[((size_t)(grp - 1) * NR + k) * cw + (col - c_lo)] = sum;
                     }
                 }
                 consumer_sync(ncons);
@@ -292,9 +360,10 @@ __global__ void __launch_bounds__(NR <= 4 ? 544 : 288) stage_kernel(StageArgs<R>
 #pragma unroll
                     for (int k = 0; k < NR; ++k)
                         for (int g2 = 1; g2 < ngroups; ++g2)
-                            acc[k][0] = cadd(acc[k][0], part[((size_t)(g2 - 1) * NR + k) * mxp + col]);
+                            acc[k][0] = cadd(acc[k][0], part[((size_t)(g2 - 1) * NR + k) * cw + (col - c_lo)]);
                 }
             }
+            const bool last = step == nsteps - 1;
             T* vn = vbuf + (size_t)(cur ^ 1) * NR * mxp;
             if (owner) {
 #pragma unroll
@@ -324,13 +393,27 @@ __global__ void __launch_bounds__(NR <= 4 ? 544 : 288) stage_kernel(StageArgs<R>
                         if (r >= 1) ynext[k] = ywk[(long long)(r - 1) * mx + col];
                     }
                     vn[k * mxp + col] = nv;
+                    if (csize == 2 && !last) st_peer(peer_addr(&vn[k * mxp + col], rank ^ 1), nv);
                 }
             }
             consumer_sync(ncons);
+            if (csize == 2 && !last) {
+                // exchange: my half of the next v is in the peer; wait for the peer's half
+                if (tid == 0) {
+                    asm volatile("fence.acq_rel.cluster;\n" ::: "memory");
+                    arrive_peer(peer_addr(&xbar, rank ^ 1));
+                }
+                const bool ab = *((volatile int*)&abort_flag) != 0;
+                if (!mbar_wait<true>(&xbar, (unsigned)(step & 1), ab ? 1000 : WAIT_LIMIT)) {
+                    abort_flag = 1;
+                    if (a.err) atomicExch(a.err, (int)HELM_ERR_TIMEOUT);
+                }
+            }
             cur ^= 1;
-            if (*((volatile int*)&abort_flag)) break;
         }
     }
+    // no CTA of a cluster leaves while its peer may still write into its shared memory
+    if (csize == 2) cluster_sync_all();
     __syncthreads();
     if (abort_flag) return;
 
@@ -342,6 +425,7 @@ __global__ void __launch_bounds__(NR <= 4 ? 544 : 288) stage_kernel(StageArgs<R>
             const int side = e < my ? SW : e < 2 * my ? SE : e < 2 * my + mx ? SS : SN;
             if (sd.bo[side] < 0) continue;
             const int pt = e - boff(side);
+            if (!owns_point(side, pt)) continue;
             a.K[sd.koff + (long long)(e0 + k) * sd.Lb + sd.bo[side] + pt] = ub[idx];
         }
         return;
@@ -354,6 +438,7 @@ __global__ void __launch_bounds__(NR <= 4 ? 544 : 288) stage_kernel(StageArgs<R>
             const int side = e < my ? SW : e < 2 * my ? SE : e < 2 * my + mx ? SS : SN;
             if (!(a.mask & (1 << side)) || sd.tin[side] < 0) continue;
             const int pt = e - boff(side);
+            if (!owns_point(side, pt)) continue;
             const long long in = sd.tin[side] + pt, out = sd.tout[side] + pt;
             const TraceCoef<T> c = a.tc[in];
             T g = cfma(c.cb, ub[idx], cmul(c.ca, gin(k, in)));
@@ -366,76 +451,99 @@ __global__ void __launch_bounds__(NR <= 4 ? 544 : 288) stage_kernel(StageArgs<R>
     }
 }
 
-template <typename R, int NR, bool BASIS>
-cudaError_t launch_nr(const StageArgs<R>& a, int nactive, int ny_blocks, int max_mx, int max_my, cudaStream_t st) {
+// Launch geometry of one stage launch.
+struct Geo {
+    int csize, cwarps, ngroups, rows, nslots;
+    size_t smem;
+};
+
+template <typename R, int NR>
+static bool geometry(int max_mx, int max_my, int max_w, int max_ld, int csize, Geo& g) {
     using T = Cx<R>;
-    const int cwarps = (max_mx + 31) / 32;
-    const int mxp = 32 * cwarps;
-    // row groups raise the number of consumer warps (latency hiding) for few RHS
-    const int ngroups = NR <= 4 ? std::max(1, std::min(4, 16 / cwarps)) : 1;
-    const int maxldx = sizeof(T) == 8 ? ((max_mx + 1) & ~1) : max_mx;
+    g.csize = csize;
+    const int width = csize == 2 ? max_w : max_mx;       // columns of one CTA
+    g.cwarps = (width + 31) / 32;
+    g.ngroups = NR <= 4 ? std::max(1, std::min(8, 16 / g.cwarps)) : 1;
+    const int mxp = 32 * ((max_mx + 31) / 32);
     const size_t fixed = 2 * (size_t)NR * mxp * sizeof(T) + 2 * (size_t)NR * 2 * (max_mx + max_my) * sizeof(T) +
-                         (size_t)(ngroups - 1) * NR * mxp * sizeof(T);
+                         (size_t)(g.ngroups - 1) * NR * 32 * g.cwarps * sizeof(T);
     const size_t budget = 227 * 1024 - 1024;
-    if (fixed >= budget) return cudaErrorInvalidValue;
-    // chunk of ~32 KB, a multiple of 4 rows
-    int rows = (int)(32768 / ((size_t)maxldx * sizeof(T)));
-    rows = std::max(4, rows & ~3);
-    rows = std::min(rows, max_mx);
-    int nslots = (int)((budget - fixed) / ((size_t)rows * maxldx * sizeof(T)));
-    nslots = std::min(nslots, MAXNS);
-    if (nslots < 2) return cudaErrorInvalidValue;
-    const size_t smem = fixed + (size_t)nslots * rows * maxldx * sizeof(T);
+    if (fixed >= budget) return false;
+    // the largest chunk (64, 48 or 32 KB, a multiple of 4 rows) that leaves three ring
+    // slots: the copy engine streams few large copies faster than many small ones
+    int rows = 0, nslots = 0;
+    for (int kb : {64, 48, 32}) {
+        rows = (int)((size_t)kb * 1024 / ((size_t)max_ld * sizeof(T)));
+        rows = std::min(std::max(4, rows & ~3), max_mx);
+        nslots = std::min((int)((budget - fixed) / ((size_t)rows * max_ld * sizeof(T))), MAXNS);
+        if (nslots >= 3) break;
+    }
+    if (nslots < 2) return false;
+    g.rows = rows;
+    g.nslots = nslots;
+    g.smem = fixed + (size_t)nslots * rows * max_ld * sizeof(T);
+    return true;
+}
+
+template <typename R, int NR, bool BASIS>
+cudaError_t launch_nr(const StageArgs<R>& a, int nunits, int ny_blocks, const Geo& g, cudaStream_t st) {
     cudaError_t e = cudaFuncSetAttribute(stage_kernel<R, NR, BASIS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+                                         (int)g.smem);
     if (e != cudaSuccess) return e;
-    dim3 grid(nactive, ny_blocks);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nunits * g.csize, ny_blocks);
+    cfg.blockDim = dim3(32 * (g.cwarps * g.ngroups + 1));
+    cfg.dynamicSmemBytes = g.smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = g.csize;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
     count_launch();
-    stage_kernel<R, NR, BASIS><<<grid, 32 * (cwarps * ngroups + 1), smem, st>>>(a, rows, nslots, cwarps, ngroups);
-    return cudaGetLastError();
+    return cudaLaunchKernelEx(&cfg, stage_kernel<R, NR, BASIS>, a, g.rows, g.nslots, g.cwarps, g.ngroups, g.csize);
 }
 
 }  // namespace
 
-// Fixed shared memory of a CTA with NR right-hand sides (the ring needs at least two more slots).
-template <typename R, int NR>
-static bool stage_fits(int max_mx, int max_my) {
-    using T = Cx<R>;
-    const int mxp = 32 * ((max_mx + 31) / 32);
-    const int maxldx = sizeof(T) == 8 ? ((max_mx + 1) & ~1) : max_mx;
-    const int ngroups = NR <= 4 ? std::max(1, std::min(4, 16 / ((max_mx + 31) / 32))) : 1;
-    const size_t fixed = 2 * (size_t)NR * mxp * sizeof(T) + 2 * (size_t)NR * 2 * (max_mx + max_my) * sizeof(T) +
-                         (size_t)(ngroups - 1) * NR * mxp * sizeof(T);
-    int rows = (int)(32768 / ((size_t)maxldx * sizeof(T)));
-    rows = std::min(std::max(4, rows & ~3), max_mx);
-    return fixed + 2 * (size_t)rows * maxldx * sizeof(T) <= 227 * 1024 - 1024;
-}
-
 template <typename R>
-cudaError_t launch_stage(const StageArgs<R>& a, int nactive, int max_mx, int max_my, cudaStream_t st) {
+cudaError_t launch_stage(const StageArgs<R>& a, int nactive, int max_mx, int max_my, int max_w, int max_ld,
+                         int num_sms, cudaStream_t st) {
     if (nactive == 0) return cudaSuccess;
     if (max_mx > 256) return cudaErrorInvalidValue;
-    // as many right-hand sides per CTA as the RHS count and shared memory allow
-    if (a.nrhs >= 16 && stage_fits<R, 16>(max_mx, max_my))
-        return launch_nr<R, 16, false>(a, nactive, (a.nrhs + 15) / 16, max_mx, max_my, st);
-    if (a.nrhs >= 8 && stage_fits<R, 8>(max_mx, max_my))
-        return launch_nr<R, 8, false>(a, nactive, (a.nrhs + 7) / 8, max_mx, max_my, st);
-    if (a.nrhs >= 4 && stage_fits<R, 4>(max_mx, max_my))
-        return launch_nr<R, 4, false>(a, nactive, (a.nrhs + 3) / 4, max_mx, max_my, st);
-    if (a.nrhs >= 2 && stage_fits<R, 2>(max_mx, max_my))
-        return launch_nr<R, 2, false>(a, nactive, (a.nrhs + 1) / 2, max_mx, max_my, st);
-    return launch_nr<R, 1, false>(a, nactive, a.nrhs, max_mx, max_my, st);
+    // two CTAs per subdomain when the stage leaves enough SMs idle
+    // two CTAs per subdomain when the stage leaves enough SMs idle and the arithmetic is
+    // FP64 (complex128 solves are bound by the FP64 units of one SM; complex64 ones by the
+    // per-row exchange latency the split adds)
+    const int csize =
+        (sizeof(R) == 8 && 2 * nactive * std::max(1, (a.nrhs + 15) / 16) <= num_sms && max_mx >= 64) ? 2 : 1;
+    Geo g;
+#define HELM_TRY_NR(NRV)                                                                                    \
+    if (a.nrhs >= NRV && geometry<R, NRV>(max_mx, max_my, max_w, max_ld, csize, g))                        \
+        return launch_nr<R, NRV, false>(a, nactive, (a.nrhs + NRV - 1) / NRV, g, st);
+    HELM_TRY_NR(16)
+    HELM_TRY_NR(8)
+    HELM_TRY_NR(4)
+    HELM_TRY_NR(2)
+#undef HELM_TRY_NR
+    if (!geometry<R, 1>(max_mx, max_my, max_w, max_ld, csize, g)) return cudaErrorInvalidValue;
+    return launch_nr<R, 1, false>(a, nactive, a.nrhs, g, st);
 }
 
 template <typename R>
-cudaError_t launch_basis(const StageArgs<R>& a, int nsub, int ncols, int max_mx, int max_my, cudaStream_t st) {
+cudaError_t launch_basis(const StageArgs<R>& a, int nsub, int ncols, int max_mx, int max_my, int max_w, int max_ld,
+                         cudaStream_t st) {
     if (max_mx > 256) return cudaErrorInvalidValue;
-    if (stage_fits<R, 16>(max_mx, max_my)) return launch_nr<R, 16, true>(a, nsub, (ncols + 15) / 16, max_mx, max_my, st);
-    if (stage_fits<R, 8>(max_mx, max_my)) return launch_nr<R, 8, true>(a, nsub, (ncols + 7) / 8, max_mx, max_my, st);
-    return launch_nr<R, 4, true>(a, nsub, (ncols + 3) / 4, max_mx, max_my, st);
+    Geo g;
+    if (geometry<R, 16>(max_mx, max_my, max_w, max_ld, 1, g)) return launch_nr<R, 16, true>(a, nsub, (ncols + 15) / 16, g, st);
+    if (geometry<R, 8>(max_mx, max_my, max_w, max_ld, 1, g)) return launch_nr<R, 8, true>(a, nsub, (ncols + 7) / 8, g, st);
+    if (geometry<R, 4>(max_mx, max_my, max_w, max_ld, 1, g)) return launch_nr<R, 4, true>(a, nsub, (ncols + 3) / 4, g, st);
+    return cudaErrorInvalidValue;
 }
 
-template cudaError_t launch_stage<float>(const StageArgs<float>&, int, int, int, cudaStream_t);
-template cudaError_t launch_stage<double>(const StageArgs<double>&, int, int, int, cudaStream_t);
-template cudaError_t launch_basis<float>(const StageArgs<float>&, int, int, int, int, cudaStream_t);
-template cudaError_t launch_basis<double>(const StageArgs<double>&, int, int, int, int, cudaStream_t);
+template cudaError_t launch_stage<float>(const StageArgs<float>&, int, int, int, int, int, int, cudaStream_t);
+template cudaError_t launch_stage<double>(const StageArgs<double>&, int, int, int, int, int, int, cudaStream_t);
+template cudaError_t launch_basis<float>(const StageArgs<float>&, int, int, int, int, int, int, cudaStream_t);
+template cudaError_t launch_basis<double>(const StageArgs<double>&, int, int, int, int, int, int, cudaStream_t);
