@@ -370,10 +370,10 @@ def gpu_arm(args):
         tf = orth[3] / (orth[1] / 1e3) / 1e12
         roofline = {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                     "frac": tf / FP64_PEAK_TFLOPS, "traffic": None,
-                    "kernel": "mdot_kernel + mupdate_kernel (FP64 classical Gram-Schmidt, reorthogonalised)",
+                    "kernel": "mgs_kernel (FP64 modified Gram-Schmidt, one persistent launch per Arnoldi step)",
                     "launches": orth[0],
                     "peak_source": "FP64 1.25 TFLOP/s nominal (152 SMs x 2 FP64 FMA/clk x 2.07 GHz); "
-                                   "cuBLAS DGEMM measured 1.10 TFLOP/s on the box"}
+                                   "cuBLAS DGEMM measured 1.10 TFLOP/s on GB300"}
     elif dom == "stage":
         roofline = stage_roof
     else:
