@@ -58,19 +58,36 @@ def parse():
     ap.add_argument("--mode", default="solve", choices=["solve", "precond"],
                     help="precond: factor once, then time --steps preconditioner applications only "
                          "(a small, fixed launch sequence for profilers)")
+    ap.add_argument("--workload", default=None, choices=["plain_mixed", "batching", "large"],
+                    help="--mode precond only: the workload to factor (default: the bench workload)")
+    ap.add_argument("--nrhs", type=int, default=None,
+                    help="--mode precond only: right-hand sides per application (default: the workload's)")
+    ap.add_argument("--tensor-cores", default="3xtf32", choices=["3xtf32", "tf32", "off"],
+                    help="complex64 multi-RHS block solves (construction of K, batched RHS): tensor cores with "
+                         "split TF32 operands, plain TF32, or FP32 on the CUDA cores")
     return ap.parse_args()
 
 
+TC_MODES = {"3xtf32": "3xtf32", "tf32": "tf32", "off": False}
+
+
 def precond_only(args):
-    """Factor the bench workload and apply the preconditioner --steps times."""
+    """Factor a workload and apply the preconditioner --steps times."""
     import torch
 
     import workloads as W
     from paper_2209_10886_gb300 import Problem
-    w = W.workload(WORKLOAD)
+    name = args.workload or WORKLOAD
+    w = W.workload(name, nrhs=args.nrhs) if args.nrhs else W.workload(name)
     m2 = torch.as_tensor(w.m2, dtype=torch.float64, device="cuda")
-    p = Problem(w.n, w.n, w.h, w.omega, m2, w.N1, w.N2, w.xcuts, w.ycuts).factor(args.prec)
+    p = Problem(w.n, w.n, w.h, w.omega, m2, w.N1, w.N2, w.xcuts, w.ycuts, tensor_cores=TC_MODES[args.tensor_cores])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    p.factor(args.prec)
+    torch.cuda.synchronize()
+    factor_ms = (time.perf_counter() - t0) * 1e3
     r = torch.as_tensor(w.f, dtype=torch.complex128, device="cuda")
+    from paper_2209_10886_gb300 import helm
     for _ in range(args.warmup):
         p.precond_apply(r, sched=args.sched)
     torch.cuda.synchronize()
@@ -80,8 +97,24 @@ def precond_only(args):
         p.precond_apply(r, sched=args.sched)
     e1.record()
     torch.cuda.synchronize()
-    print(json.dumps({"mode": "precond", "prec": args.prec, "sched": args.sched,
-                      "ms_per_apply": e0.elapsed_time(e1) / max(args.steps, 1)}))
+    ms = e0.elapsed_time(e1) / max(args.steps, 1)
+    # the same applications again with library-side events around every stage launch
+    helm.profile(p, True)
+    for _ in range(args.steps):
+        p.precond_apply(r, sched=args.sched)
+    torch.cuda.synchronize()
+    kern = {}
+    for k in ("stage", "trace"):
+        n, kms, kb, kf = helm.profile_read(p, k)
+        if n:
+            kern[k] = {"launches_per_apply": n / args.steps, "ms_per_apply": kms / args.steps,
+                       "GB_per_s": kb / (kms / 1e3) / 1e9 if kms else None,
+                       "TFLOP_per_s": kf / (kms / 1e3) / 1e12 if kms else None}
+    helm.profile(p, False)
+    print(json.dumps({"mode": "precond", "workload": name, "nrhs": int(r.shape[0]), "prec": args.prec,
+                      "sched": args.sched, "tensor_cores": args.tensor_cores, "factor_ms": factor_ms,
+                      "ms_per_apply": ms, "unknowns_rhs_per_s": w.N * r.shape[0] / (ms / 1e3),
+                      "kernels": kern}))
     p.close()
 
 

@@ -104,6 +104,17 @@ typedef struct {
                                 0: those stages run full block-tridiagonal solves instead
                                 (the same operator; no K memory, no K construction time,
                                 which grows like (boundary points) x (subdomain solve)) */
+    int tensor_cores;   /* with complex64 factors (HELM_PREC_C64) and subdomains at most 256
+                           nodes wide, block solves over 16 or more right-hand sides at once
+                           (the construction of K, batched sources) run on the tensor cores
+                           with FP32 accumulation, from a second copy of the factors in the
+                           tensor cores' operand layout:
+                           1 (default): every operand split into two TF32 numbers (hi + lo,
+                              three MMAs per product), FP32-level accuracy; the copy takes
+                              twice the bytes of the factors
+                           2: TF32 operands alone (rounded to nearest; unit roundoff 2^-11),
+                              one MMA per product; the copy takes the bytes of the factors
+                           0: FP32 arithmetic on the CUDA cores, no second copy */
 } helm_setup_opts;
 
 typedef struct {

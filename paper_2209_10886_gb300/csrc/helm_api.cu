@@ -179,6 +179,10 @@ struct helm_problem {
     void* d_K = nullptr;             // boundary operators of all subdomains
     size_t K_bytes = 0;
     size_t X_bytes = 0;
+    float* d_XT = nullptr;           // complex64 factors in the tensor cores' operand layout (k_tc.cu)
+    size_t XT_bytes = 0;
+    int tc_mt = 0;                   // 128-node M tiles of that layout
+    int tc_split = 0;                // 3: hi + lo TF32 pairs, 1: TF32 alone
 
     // preconditioner workspace
     int ws_nrhs = 0;
@@ -306,6 +310,7 @@ extern "C" void helm_default_setup_opts(helm_setup_opts* o) {
     o->transmission = HELM_TC_OPTIMIZED;
     o->tc_scale = 1.0;
     o->boundary_operators = 1;
+    o->tensor_cores = 1;
 }
 
 extern "C" const char* helm_last_error(void) { return g_err.c_str(); }
@@ -522,6 +527,7 @@ extern "C" helm_status helm_destroy(helm_problem* p) {
     }
     if (p->d_X) cudaFree(p->d_X);
     if (p->d_K) cudaFree(p->d_K);
+    if (p->d_XT) cudaFree(p->d_XT);
     delete p;
     return HELM_OK;
 }
@@ -575,6 +581,12 @@ static helm_status build_boundary_operators_t(helm_problem* p, cudaStream_t st) 
     a.err = p->d_err;
     for (int c0 = 0; c0 < p->max_Lb && e == cudaSuccess; c0 += NB) {
         a.col0 = c0;
+        if constexpr (sizeof(R) == 4) {
+            if (p->d_XT) {
+                e = launch_tc_basis(a, p->d_XT, p->tc_mt, p->tc_split, (int)p->subs.size(), NB, st);
+                continue;
+            }
+        }
         e = launch_basis<R>(a, (int)p->subs.size(), NB, p->max_mx, p->max_my, p->max_w, p->max_ld, st);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -599,7 +611,10 @@ extern "C" helm_status precond_factor(helm_problem* p, helm_prec prec, void* str
     // layout of the stored X_r: per subdomain my blocks, each two column halves of
     // widths w0 = mx/2 rounded up to even and mx - w0, leading dimensions even for
     // complex64 so that every half, block and row chunk starts on a 16-byte boundary
-    long long xoff = 0;
+    long long xoff = 0, xtoff = 0;
+    // second copy for the tensor cores: complex64, enabled, subdomains at most 256 nodes wide
+    const int mt = (prec == HELM_PREC_C64 && p->sopts.tensor_cores) ? tc_tiles(p->max_mx) : 0;
+    const int split = p->sopts.tensor_cores == 2 ? 1 : 3;
     std::vector<SubDev> tab;
     p->max_w = p->max_ld = 0;
     for (auto& s : p->subs) {
@@ -612,6 +627,8 @@ extern "C" helm_status precond_factor(helm_problem* p, helm_prec prec, void* str
         if (prec == HELM_PREC_C64 && (s.dev.ld0 & 1)) s.dev.ld0 += 1;
         s.dev.xoff = xoff;
         xoff += (long long)s.dev.my * mx * (s.dev.ld0 + s.dev.ld1);
+        s.dev.xtoff = xtoff;
+        if (mt) xtoff += tc_layout_floats(mx, s.dev.my, mt, split);
         p->max_w = std::max(p->max_w, std::max(w0, w1));
         p->max_ld = std::max(p->max_ld, std::max(s.dev.ld0, s.dev.ld1));
         tab.push_back(s.dev);
@@ -620,6 +637,7 @@ extern "C" helm_status precond_factor(helm_problem* p, helm_prec prec, void* str
     HELM_CUDA_TRY(cudaStreamSynchronize(st));
     if (p->d_X) { cudaFree(p->d_X); p->d_X = nullptr; p->X_bytes = 0; p->factored = 0; }
     if (p->d_K) { cudaFree(p->d_K); p->d_K = nullptr; p->K_bytes = 0; }
+    if (p->d_XT) { cudaFree(p->d_XT); p->d_XT = nullptr; p->XT_bytes = 0; p->tc_mt = 0; p->tc_split = 0; }
     cudaError_t e = cudaMalloc(&p->d_X, bytes);
     if (e != cudaSuccess) { p->d_X = nullptr; return cuda_status(e, "precond_factor: allocating the factors"); }
     p->X_bytes = bytes;
@@ -654,6 +672,15 @@ extern "C" helm_status precond_factor(helm_problem* p, helm_prec prec, void* str
             return HELM_ERR_ARG;
         }
     p->prec = prec;
+    if (mt) {
+        e = cudaMalloc(&p->d_XT, (size_t)xtoff * sizeof(float));
+        if (e != cudaSuccess) { p->d_XT = nullptr; return cuda_status(e, "precond_factor: allocating the tensor-core factors"); }
+        p->XT_bytes = (size_t)xtoff * sizeof(float);
+        p->tc_mt = mt;
+        p->tc_split = split;
+        e = launch_tc_layout(p->d_subtab, (int)p->subs.size(), mt, split, (const float2*)p->d_X, p->d_XT, st);
+        if (e != cudaSuccess) return cuda_status(e, "precond_factor: tensor-core layout");
+    }
     {
         const helm_status ks = p->sopts.boundary_operators ? build_boundary_operators(p, st) : HELM_OK;
         if (ks != HELM_OK) return ks;
@@ -780,8 +807,17 @@ static helm_status run_precond_t(helm_problem* p, const PcWork& w, int sched, co
             }
         }
         prof_begin(p, HELM_K_STAGE, st);
-        cudaError_t e = launch_stage<R>(a, (int)sd.subs.size(), p->max_mx, p->max_my, p->max_w, p->max_ld,
-                                        p->num_sms, st);
+        cudaError_t e = cudaSuccess;
+        bool done = false;
+        if constexpr (sizeof(R) == 4) {
+            // 16 or more right-hand sides: the block solves are GEMMs for the tensor cores
+            if (p->d_XT && nrhs >= 16) {
+                e = launch_tc_stage(a, p->d_XT, p->tc_mt, p->tc_split, (int)sd.subs.size(), st);
+                done = true;
+            }
+        }
+        if (!done)
+            e = launch_stage<R>(a, (int)sd.subs.size(), p->max_mx, p->max_my, p->max_w, p->max_ld, p->num_sms, st);
         prof_end(p, HELM_K_STAGE, bytes, st, flops);
         if (e != cudaSuccess) return cuda_status(e, "stage launch");
     }

@@ -70,6 +70,7 @@ struct SubDev {
     int bo[4];
     int Lb;
     long long koff;            // element offset of the Lb x Lb boundary operator K in its array
+    long long xtoff;           // float offset of this subdomain's factors in the tensor-core layout (k_tc.cu)
 };
 
 // Trace-point coefficients of one interface edge point (beta_e = T_e h / 2):
@@ -170,6 +171,16 @@ cudaError_t launch_stage(const StageArgs<R>& a, int nactive, int max_mx, int max
 template <typename R>
 cudaError_t launch_basis(const StageArgs<R>& a, int nsub, int ncols, int max_mx, int max_my, int max_w, int max_ld,
                          cudaStream_t st);
+// tensor-core (TF32) multi-RHS solves of complex64 factors (k_tc.cu)
+// split = 3: operands as hi + lo TF32 pairs, three MMAs per product; split = 1: TF32 alone
+int tc_tiles(int max_mx);                                 // 128-node M tiles (1 or 2), 0: unsupported width
+long long tc_layout_floats(int mx, int my, int MT, int split);   // floats of one subdomain's factors in that layout
+cudaError_t launch_tc_layout(const SubDev* subtab, int nsub, int MT, int split, const float2* X, float* XT,
+                             cudaStream_t st);
+cudaError_t launch_tc_stage(const StageArgs<float>& a, const float* XT, int MT, int split, int nactive,
+                            cudaStream_t st);
+cudaError_t launch_tc_basis(const StageArgs<float>& a, const float* XT, int MT, int split, int nsub, int ncols,
+                            cudaStream_t st);
 template <typename R>
 cudaError_t launch_iface(const IfaceArgs<R>& a, int nactive, int max_rows, int max_Lb, cudaStream_t st);
 // krylov / vector kernels

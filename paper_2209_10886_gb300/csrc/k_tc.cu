@@ -1,0 +1,560 @@
+// Multi-RHS subdomain solves on the tensor cores (complex64 factors, TF32 inputs,
+// FP32 accumulation): the batched forward/back block solves of the stored
+// block-tridiagonal factorisation (Section 5, the local problems of Eq. subPbm)
+// for many right-hand sides at once.  With NR right-hand sides every step
+//     forward   y_r = X_r (b_r + y_{r-1}),      backward  u_r = y_r + X_r u_{r+1}
+// is an (mx x mx) x (mx x NR) complex product, a dense contraction.
+//
+// Operands.  A complex product is two real MMAs per K-step with M = 128 output
+// nodes, N = 2 NR, K = 8 (kind::tf32):
+//     [Re D | Im D] = Xr [Br | Bi] + Xi [-Bi | Br]
+// With SPLIT = 3 every operand is the sum of two TF32 numbers, hi = tf32(x) and
+// lo = tf32(x - hi), and each real product takes three MMAs, hi*hi + hi*lo +
+// lo*hi (the lo*lo term is below FP32 roundoff): FP32-level accuracy from the
+// TF32 pipe.  SPLIT = 1 uses hi alone.
+// The factors are re-laid out once (tc_layout_kernel) into planes of real and
+// imaginary parts (hi, and lo for SPLIT = 3) in the tensor cores' no-swizzle
+// K-major core-matrix layout, cut into 32 KB chunks of K; one bulk copy lands a
+// chunk in shared memory ready for the MMA descriptors.  The right-hand-side
+// block is the K-major B operand [-Bi | Br | Bi] (K = node index, N = 3 NR) in
+// shared memory, written by the epilogue threads (a 4 x 4 shuffle transpose per
+// group of four nodes, then 16-byte stores), so the two windows [Br | Bi] and
+// [-Bi | Br] are both contiguous.  The accumulator D (128 lanes x 2 NR columns
+// per 128-node tile) is in tensor memory.
+// Descriptors (no swizzle, K-major): the leading byte offset is the distance of
+// core matrices adjacent along K, the stride byte offset that of core matrices
+// adjacent along M (A) or N (B).
+//
+// Roles.  Warps 0 .. 4MT-1: epilogue, thread i owns output node i of the
+// current grid row (TMEM lane i % 128 of tile i / 128); warp 4MT: producer (one
+// thread issues the bulk copies into a ring of chunk slots); warp 4MT+1: one
+// thread issues the MMAs and commits them to mbarriers.  Per step the epilogue
+// waits for the accumulator, forms the next operand (b_{r+1} + y_r, or
+// y_r + X_r u_{r+1} on the way back) and signals the MMA thread.  All waits are
+// bounded: on expiry the kernel records HELM_ERR_TIMEOUT, stops issuing work,
+// waits (bounded) for its own copies and MMAs and frees its tensor memory.
+#include "helm_internal.cuh"
+
+namespace {
+
+constexpr long long TC_WAIT_LIMIT = 2000000000LL;  // cycles (~1 s)
+constexpr int TC_MAXSLOTS = 8;
+constexpr int TC_CHUNK_BYTES = 32768;              // one K-chunk: real plane + imaginary plane
+
+__device__ __forceinline__ unsigned sm_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void bar_init(unsigned long long* b, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(sm_addr(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void bar_arrive(unsigned long long* b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(sm_addr(b)) : "memory");
+}
+__device__ __forceinline__ void bar_expect_tx(unsigned long long* b, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(sm_addr(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool bar_try(unsigned long long* b, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(sm_addr(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool bar_wait(unsigned long long* b, unsigned parity, long long limit) {
+    if (bar_try(b, parity)) return true;
+    const long long t0 = clock64();
+    while (!bar_try(b, parity))
+        if (clock64() - t0 > limit) return false;
+    return true;
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(sm_addr(dst)),
+        "l"(src), "r"(bytes), "r"(sm_addr(bar))
+        : "memory");
+}
+
+// shared-memory matrix descriptor, no swizzle: start, leading and stride byte offsets (>> 4),
+// bits 46-48 = 0b001
+__device__ __forceinline__ unsigned long long smem_desc(unsigned addr, unsigned lbo, unsigned sbo) {
+    return (unsigned long long)((addr >> 4) & 0x3FFFu) | ((unsigned long long)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((unsigned long long)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+// instruction descriptor of kind::tf32: D f32, A and B tf32, both K-major, N, M = 128
+__host__ __device__ constexpr unsigned tf32_idesc(int n) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((unsigned)(n >> 3) << 17) | ((128u >> 4) << 24);
+}
+__device__ __forceinline__ void mma_tf32(unsigned dtmem, unsigned long long adesc, unsigned long long bdesc,
+                                         unsigned idesc, int accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(unsigned long long* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(sm_addr(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+// 8 consecutive 32-bit columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld8(unsigned addr, float* v) {
+    unsigned r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(addr));
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
+__device__ __forceinline__ float tf32_round(float x) {
+    unsigned r;
+    asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+__device__ __forceinline__ void st_shared_v4(unsigned addr, float a, float b, float c, float d) {
+    asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};\n" ::"r"(addr), "f"(a), "f"(b), "f"(c), "f"(d) : "memory");
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------- layout
+// XT of one subdomain: my steps x nch chunks of 32 KB; chunk c holds K columns
+// [c*KC, c*KC + KC) of all 128*MT rows as planes (real hi, imaginary hi, and for
+// SPLIT = 3 real lo, imaginary lo; KC = 32 / (MT * SPLIT') with SPLIT' = 1 or 2
+// planes per part), each of core matrices 8 rows x 4 columns:
+//     float index in a plane = ((kl / 4) * 16 MT + i / 8) * 32 + (i % 8) * 4 + kl % 4
+// Rows i >= mx and columns j >= mx are zero; values are rounded to TF32.
+__host__ __device__ inline int tc_kc(int MT, int split) { return (split == 3 ? 16 : 32) / MT; }
+
+__global__ void tc_layout_kernel(const SubDev* subtab, int nsub, int MT, int split, const float2* X, float* XT) {
+    const int s = blockIdx.y;
+    if (s >= nsub) return;
+    const SubDev sd = subtab[s];
+    const int KC = tc_kc(MT, split);
+    const int nch = (sd.mx + KC - 1) / KC;
+    const long long per_step = (long long)nch * (TC_CHUNK_BYTES / 4);
+    const long long total = (long long)sd.my * per_step;
+    const int plane = 128 * MT * KC;                       // floats per plane
+    for (long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x; f < total;
+         f += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(f / per_step);
+        const long long g = f - (long long)r * per_step;
+        const int np = split == 3 ? 4 : 2;
+        const int c = (int)(g / (np * plane));
+        const int h = (int)(g - (long long)c * np * plane);
+        const int p = h / plane;                           // 0 real hi, 1 imaginary hi, 2 real lo, 3 imaginary lo
+        const int q = h - p * plane;
+        const int core = q >> 5, w = q & 31;
+        const int ck = core / (16 * MT), cm = core - ck * 16 * MT;
+        const int i = cm * 8 + (w >> 2);
+        const int j = c * KC + ck * 4 + (w & 3);
+        float v = 0.f;
+        if (i < sd.mx && j < sd.mx) {
+            const long long e = j < sd.w0 ? (long long)i * sd.ld0 + j
+                                          : (long long)sd.mx * sd.ld0 + (long long)i * sd.ld1 + (j - sd.w0);
+            const float2 x = X[sd.xoff + (long long)r * sd.mx * (sd.ld0 + sd.ld1) + e];
+            const float xv = (p & 1) ? x.y : x.x;
+            const float hi = tf32_round(xv);
+            v = p < 2 ? hi : tf32_round(xv - hi);
+        }
+        XT[sd.xtoff + f] = v;
+    }
+}
+
+namespace {
+
+// ------------------------------------------------------------- stage kernel
+template <int MT, int NR, bool BASIS, int SPLIT>
+__global__ void __launch_bounds__(32 * (4 * MT + 2), 1)
+    tc_stage_kernel(StageArgs<float> a, const float* __restrict__ XT, int nslots) {
+    using T = float2;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ __align__(8) unsigned long long full_bar[TC_MAXSLOTS], empty_bar[TC_MAXSLOTS], b_bar, d_bar, fin_bar;
+    __shared__ unsigned tmem_base;
+    __shared__ int abort_flag;
+
+    constexpr int NEPI = 128 * MT;                          // epilogue threads = output nodes
+    constexpr int KC = (SPLIT == 3 ? 16 : 32) / MT;         // K columns per chunk
+    constexpr unsigned PLANE = 128u * MT * KC * 4u;         // bytes of one plane of a chunk
+    constexpr unsigned BLO = 32u * MT * (48u * NR + 64u);  // offset of the lo operand (SPLIT = 3)
+    constexpr int NCOLS = 2 * NR * MT;                      // accumulator columns
+    constexpr int TCOLS = NCOLS <= 32 ? 32 : NCOLS <= 64 ? 64 : NCOLS <= 128 ? 128 : NCOLS <= 256 ? 256 : 512;
+    // B operand: core matrix (n / 8, node / 4) at (node / 4) * KSTRIDE_B + (n / 8) * 128; the
+    // extra 64 bytes put consecutive node groups in opposite halves of the banks
+    constexpr unsigned KSTRIDE_B = 48u * NR + 64u;
+    constexpr unsigned KSTRIDE_A = 2048u * MT;              // K-adjacent core matrices of A
+    constexpr unsigned IDESC = tf32_idesc(2 * NR);
+
+    const int s = BASIS ? blockIdx.x : a.subs[blockIdx.x];
+    const SubDev sd = a.subtab[s];
+    const int mx = sd.mx, my = sd.my;
+    const int rhs0 = blockIdx.y * NR;
+    const int e0 = BASIS ? a.col0 + rhs0 : 0;
+    if (BASIS && e0 >= sd.Lb) return;                       // uniform over the CTA
+    const int nr = BASIS ? min(NR, sd.Lb - e0) : min(NR, a.nrhs - rhs0);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nch = (mx + KC - 1) / KC;
+    const int nsteps = 2 * my - 1;
+    const long long N = (long long)a.nx * a.ny;
+
+    unsigned char* ring = smem_raw;
+    unsigned char* bop = smem_raw + (size_t)nslots * TC_CHUNK_BYTES;   // [-Bi | Br | Bi] (hi, then lo)
+    const unsigned ring_s = sm_addr(ring), bop_s = sm_addr(bop);
+
+    if (tid == 0) {
+        for (int i = 0; i < nslots; ++i) {
+            bar_init(&full_bar[i], 1);
+            bar_init(&empty_bar[i], 1);
+        }
+        bar_init(&b_bar, NEPI);
+        bar_init(&d_bar, 1);
+        bar_init(&fin_bar, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(sm_addr(&tmem_base)),
+                     "r"(TCOLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const unsigned tmem = tmem_base;
+
+    auto fail = [&]() {
+        abort_flag = 1;
+        if (a.err) atomicExch(a.err, (int)HELM_ERR_TIMEOUT);
+    };
+    auto aborted = [&]() { return *((volatile int*)&abort_flag) != 0; };
+
+    if (warp < 4 * MT) {
+        // ------------------------------------------------------------ epilogue
+        const int c = tid;                                  // node of the grid row
+        const int tile = warp >> 2;
+        const unsigned dcol = tmem + ((unsigned)(32 * (warp & 3)) << 16) + (unsigned)(tile * 2 * NR);
+        const bool live = c < mx;
+        const unsigned bgrp = bop_s + (unsigned)(c >> 2) * KSTRIDE_B;      // K core matrix of nodes 4(c/4) ..
+        T* yw = a.yws + sd.yoff;
+        auto gin = [&](int k, long long idx) -> T {
+            T g = a.gin0 ? a.gin0[(long long)(rhs0 + k) * a.ntrace + idx] : czero<T>();
+            if (a.gin1) g = cadd(g, a.gin1[(long long)(rhs0 + k) * a.ntrace + idx]);
+            return g;
+        };
+        // boundary sides through node (r, c), and the point index along each
+        auto sides = [&](int r, int* sl, int* pl) {
+            int n = 0;
+            if (c == 0) { sl[n] = SW; pl[n++] = r; }
+            if (c == mx - 1) { sl[n] = SE; pl[n++] = r; }
+            if (r == 0) { sl[n] = SS; pl[n++] = c; }
+            if (r == my - 1) { sl[n] = SN; pl[n++] = c; }
+            return n;
+        };
+        // right-hand side of grid row r at this node for RHS k: incoming data and source
+        auto bterm = [&](int r, int k) -> T {
+            T b = czero<T>();
+            if (!live || k >= nr) return b;
+            int sl[4], pl[4];
+            const int ns = (c == 0 || c == mx - 1 || r == 0 || r == my - 1) ? sides(r, sl, pl) : 0;
+            for (int q = 0; q < ns; ++q) {
+                if (BASIS) {
+                    if (sd.bo[sl[q]] >= 0 && sd.bo[sl[q]] + pl[q] == e0 + k) b = cadd(b, mk(1.f, 0.f));
+                } else if (sd.tin[sl[q]] >= 0 && (a.gin0 || a.gin1)) {
+                    const long long ti = sd.tin[sl[q]] + pl[q];
+                    b = cadd(b, cmul(gin(k, ti), a.tc[ti].cin));
+                }
+            }
+            if (!BASIS && a.src) {
+                const double2 rv = a.r[(long long)(rhs0 + k) * N + (long long)(sd.y0 + r) * a.nx + sd.x0 + c];
+                const double sc = a.rscale ? a.rscale[rhs0 + k] : 1.0;
+                b = cadd(b, mk((float)(rv.x * sc), (float)(rv.y * sc)));
+            }
+            return b;
+        };
+        // u is the solution at node (r, c) for RHS k
+        auto finish = [&](int r, int k, T u) {
+            if (!BASIS && a.z) {
+                const double sc = a.zscale ? a.zscale[rhs0 + k] : 1.0;
+                a.z[(long long)(rhs0 + k) * N + (long long)(sd.y0 + r) * a.nx + sd.x0 + c] =
+                    make_double2((double)u.x * sc, (double)u.y * sc);
+            }
+            if (!(c == 0 || c == mx - 1 || r == 0 || r == my - 1)) return;
+            int sl[4], pl[4];
+            const int ns = sides(r, sl, pl);
+            for (int q = 0; q < ns; ++q) {
+                const int side = sl[q];
+                if (BASIS) {
+                    if (sd.bo[side] >= 0) a.K[sd.koff + (long long)(e0 + k) * sd.Lb + sd.bo[side] + pl[q]] = u;
+                } else if ((a.mask & (1 << side)) && sd.tin[side] >= 0) {
+                    const long long in = sd.tin[side] + pl[q], out = sd.tout[side] + pl[q];
+                    const TraceCoef<T> cf = a.tc[in];
+                    T g = cfma(cf.cb, u, cmul(cf.ca, gin(k, in)));
+                    const long long o = (long long)(rhs0 + k) * a.ntrace + out;
+                    if (a.base) g = cadd(g, a.base[o]);
+                    if (a.sub) g = csub(g, a.sub[o]);
+                    a.dst[o] = g;
+                    if (a.dst2) a.dst2[o] = g;
+                }
+            }
+        };
+        // write the operand entries of RHS k0 .. k0+3 (v[j] = value of RHS k0 + j at this
+        // node): a 4 x 4 transpose within each group of four lanes leaves lane j of the
+        // group with RHS k0 + j at the group's four nodes, one 16-byte row of a core matrix
+        auto put4 = [&](int k0, const T* v) {
+            const int j = lane & 3, gb = lane & ~3;
+            float wr[4], wi[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int sj = (j - q) & 3, i = (j + q) & 3;
+                const float sr = sj == 0 ? v[0].x : sj == 1 ? v[1].x : sj == 2 ? v[2].x : v[3].x;
+                const float si = sj == 0 ? v[0].y : sj == 1 ? v[1].y : sj == 2 ? v[2].y : v[3].y;
+                const float rr = __shfl_sync(0xffffffffu, sr, gb | i);
+                const float ri = __shfl_sync(0xffffffffu, si, gb | i);
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    if (t == i) { wr[t] = rr; wi[t] = ri; }
+                }
+            }
+            const int n = k0 + j;
+            auto row = [&](int nn) { return bgrp + (unsigned)(nn >> 3) * 128u + (unsigned)(nn & 7) * 16u; };
+            float hr[4], hi[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) { hr[t] = tf32_round(wr[t]); hi[t] = tf32_round(wi[t]); }
+            st_shared_v4(row(n), -hi[0], -hi[1], -hi[2], -hi[3]);
+            st_shared_v4(row(NR + n), hr[0], hr[1], hr[2], hr[3]);
+            st_shared_v4(row(2 * NR + n), hi[0], hi[1], hi[2], hi[3]);
+            if (SPLIT == 3) {
+                float lr[4], li[4];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) { lr[t] = tf32_round(wr[t] - hr[t]); li[t] = tf32_round(wi[t] - hi[t]); }
+                st_shared_v4(BLO + row(n), -li[0], -li[1], -li[2], -li[3]);
+                st_shared_v4(BLO + row(NR + n), lr[0], lr[1], lr[2], lr[3]);
+                st_shared_v4(BLO + row(2 * NR + n), li[0], li[1], li[2], li[3]);
+            }
+        };
+        // operand of step 0: b_1
+        for (int k0 = 0; k0 < NR; k0 += 4) {
+            T v[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) v[j] = bterm(0, k0 + j);
+            put4(k0, v);
+        }
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        tc_fence_before();
+        bar_arrive(&b_bar);
+        for (int step = 0; step < nsteps; ++step) {
+            const bool fwd = step < my;
+            const int r = fwd ? step : 2 * my - 2 - step;
+            if (!bar_wait(&d_bar, (unsigned)(step & 1), aborted() ? 0 : TC_WAIT_LIMIT)) fail();
+            tc_fence_after();
+            const bool last = step == nsteps - 1;
+            const bool ok = !aborted();
+            for (int k0 = 0; k0 < NR; k0 += 8) {
+                float dr[8], di[8];
+                tmem_ld8(dcol + (unsigned)k0, dr);
+                tmem_ld8(dcol + (unsigned)(NR + k0), di);
+                tmem_wait_ld();
+                T nv[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int k = k0 + j;
+                    const T sum = mk(dr[j], di[j]);
+                    T v = czero<T>();
+                    if (ok && live && k < nr) {
+                        T* ywk = yw + (long long)(rhs0 + k) * a.wstride;
+                        if (fwd) {
+                            if (r < my - 1) {
+                                ywk[(long long)r * mx + c] = sum;                 // y_r
+                                v = cadd(bterm(r + 1, k), sum);                   // b_{r+1} + y_r
+                            } else {
+                                finish(r, k, sum);                                // u_my = y_my
+                                v = sum;
+                            }
+                        } else {
+                            v = cadd(ywk[(long long)r * mx + c], sum);            // u_r = y_r + X_r u_{r+1}
+                            finish(r, k, v);
+                        }
+                    }
+                    nv[j] = v;
+                }
+                if (!last) {
+                    put4(k0, nv);
+                    put4(k0 + 4, nv + 4);
+                }
+            }
+            if (!last) {
+                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                tc_fence_before();
+                bar_arrive(&b_bar);
+            }
+        }
+    } else if (warp == 4 * MT) {
+        // ------------------------------------------------------------ producer
+        if (lane == 0) {
+            const float* Xs = XT + sd.xtoff;
+            const long long chunk_f = TC_CHUNK_BYTES / 4;
+            int slot = 0, issued = 0;
+            unsigned ph = 0;
+            for (int step = 0; step < nsteps && !aborted(); ++step) {
+                const int r = step < my ? step : 2 * my - 2 - step;
+                for (int ch = 0; ch < nch; ++ch) {
+                    if (aborted()) break;
+                    if (issued >= nslots && !bar_wait(&empty_bar[slot], ph ^ 1u, TC_WAIT_LIMIT)) {
+                        fail();
+                        break;
+                    }
+                    bar_expect_tx(&full_bar[slot], TC_CHUNK_BYTES);
+                    bulk_load(ring + (size_t)slot * TC_CHUNK_BYTES, Xs + ((long long)r * nch + ch) * chunk_f,
+                              TC_CHUNK_BYTES, &full_bar[slot]);
+                    ++issued;
+                    if (++slot == nslots) { slot = 0; ph ^= 1u; }
+                }
+            }
+            if (aborted()) {
+                for (int t = max(0, issued - nslots); t < issued; ++t)
+                    bar_wait(&full_bar[t % nslots], (unsigned)((t / nslots) & 1), TC_WAIT_LIMIT);
+            } else {
+                // the last releases of every slot have landed before the CTA leaves
+                for (int t = max(0, issued - nslots); t < issued; ++t)
+                    if (!bar_wait(&empty_bar[t % nslots], (unsigned)((t / nslots) & 1), TC_WAIT_LIMIT)) fail();
+            }
+        }
+    } else {
+        // ------------------------------------------------------------ MMA issue
+        if (lane == 0) {
+            int slot = 0;
+            unsigned ph = 0;
+            bool any = false;
+            for (int step = 0; step < nsteps; ++step) {
+                if (!bar_wait(&b_bar, (unsigned)(step & 1), aborted() ? 0 : TC_WAIT_LIMIT)) fail();
+                if (aborted()) break;
+                tc_fence_after();
+                for (int ch = 0; ch < nch; ++ch) {
+                    if (!bar_wait(&full_bar[slot], ph, TC_WAIT_LIMIT)) { fail(); break; }
+                    tc_fence_after();
+                    const unsigned abase = ring_s + (unsigned)slot * TC_CHUNK_BYTES;
+#pragma unroll
+                    for (int kk = 0; kk < KC / 8; ++kk) {
+                        const int kc = (ch * KC + kk * 8) >> 2;          // first K core matrix of the B operand
+                        const unsigned bb = bop_s + (unsigned)kc * KSTRIDE_B;
+                        const unsigned long long b1 = smem_desc(bb + (unsigned)(NR / 8) * 128u, KSTRIDE_B, 128u);
+                        const unsigned long long b2 = smem_desc(bb, KSTRIDE_B, 128u);
+#pragma unroll
+                        for (int t = 0; t < MT; ++t) {
+                            const unsigned ar = abase + (unsigned)kk * 2u * KSTRIDE_A + (unsigned)t * 2048u;
+                            const unsigned long long dre = smem_desc(ar, KSTRIDE_A, 128u);
+                            const unsigned long long dim = smem_desc(ar + PLANE, KSTRIDE_A, 128u);
+                            const unsigned dt = tmem + (unsigned)(t * 2 * NR);
+                            mma_tf32(dt, dre, b1, IDESC, (ch > 0 || kk > 0) ? 1 : 0);
+                            mma_tf32(dt, dim, b2, IDESC, 1);
+                            if (SPLIT == 3) {
+                                const unsigned long long b1l = smem_desc(BLO + bb + (unsigned)(NR / 8) * 128u, KSTRIDE_B, 128u);
+                                const unsigned long long b2l = smem_desc(BLO + bb, KSTRIDE_B, 128u);
+                                const unsigned long long drel = smem_desc(ar + 2u * PLANE, KSTRIDE_A, 128u);
+                                const unsigned long long diml = smem_desc(ar + 3u * PLANE, KSTRIDE_A, 128u);
+                                mma_tf32(dt, dre, b1l, IDESC, 1);      // hi * lo
+                                mma_tf32(dt, dim, b2l, IDESC, 1);
+                                mma_tf32(dt, drel, b1, IDESC, 1);      // lo * hi
+                                mma_tf32(dt, diml, b2, IDESC, 1);
+                            }
+                        }
+                    }
+                    mma_commit(&empty_bar[slot]);                        // slot free once these complete
+                    any = true;
+                    if (++slot == nslots) { slot = 0; ph ^= 1u; }
+                }
+                if (aborted()) break;
+                mma_commit(&d_bar);                                      // accumulator of this step ready
+            }
+            if (any) {
+                // every MMA this thread issued has completed before tensor memory is freed
+                mma_commit(&fin_bar);
+                bar_wait(&fin_bar, 0u, TC_WAIT_LIMIT);
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TCOLS) : "memory");
+    }
+}
+
+template <int MT, int NR, int SPLIT>
+size_t tc_smem(int nslots) {
+    return (size_t)nslots * TC_CHUNK_BYTES + (size_t)32 * MT * (48 * NR + 64) * (SPLIT == 3 ? 2 : 1);
+}
+
+template <int MT, int NR, bool BASIS, int SPLIT>
+cudaError_t tc_launch(const StageArgs<float>& a, const float* XT, int nunits, int ny_blocks, cudaStream_t st) {
+    const size_t budget = 227 * 1024 - 1024;
+    int nslots = TC_MAXSLOTS;
+    while (nslots > 2 && tc_smem<MT, NR, SPLIT>(nslots) > budget) --nslots;
+    if (tc_smem<MT, NR, SPLIT>(nslots) > budget) return cudaErrorInvalidValue;
+    const size_t smem = tc_smem<MT, NR, SPLIT>(nslots);
+    cudaError_t e = cudaFuncSetAttribute(tc_stage_kernel<MT, NR, BASIS, SPLIT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    count_launch();
+    tc_stage_kernel<MT, NR, BASIS, SPLIT><<<dim3(nunits, ny_blocks), 32 * (4 * MT + 2), smem, st>>>(a, XT, nslots);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int tc_tiles(int max_mx) { return max_mx <= 128 ? 1 : max_mx <= 256 ? 2 : 0; }
+
+long long tc_layout_floats(int mx, int my, int MT, int split) {
+    const int KC = tc_kc(MT, split);
+    return (long long)my * ((mx + KC - 1) / KC) * (TC_CHUNK_BYTES / 4);
+}
+
+cudaError_t launch_tc_layout(const SubDev* subtab, int nsub, int MT, int split, const float2* X, float* XT,
+                             cudaStream_t st) {
+    if (nsub == 0) return cudaSuccess;
+    count_launch();
+    tc_layout_kernel<<<dim3(64, nsub), 256, 0, st>>>(subtab, nsub, MT, split, X, XT);
+    return cudaGetLastError();
+}
+
+// RHS per CTA: the widest block whose operands fit next to a ring of chunk slots
+cudaError_t launch_tc_stage(const StageArgs<float>& a, const float* XT, int MT, int split, int nactive,
+                            cudaStream_t st) {
+    if (nactive == 0) return cudaSuccess;
+    const int n = a.nrhs;
+    if (split == 3) {
+        if (MT == 1) {
+            if (n >= 32) return tc_launch<1, 32, false, 3>(a, XT, nactive, (n + 31) / 32, st);
+            return tc_launch<1, 16, false, 3>(a, XT, nactive, (n + 15) / 16, st);
+        }
+        if (MT == 2) return tc_launch<2, 16, false, 3>(a, XT, nactive, (n + 15) / 16, st);
+        return cudaErrorInvalidValue;
+    }
+    if (MT == 1) {
+        if (n >= 64) return tc_launch<1, 64, false, 1>(a, XT, nactive, (n + 63) / 64, st);
+        if (n >= 32) return tc_launch<1, 32, false, 1>(a, XT, nactive, (n + 31) / 32, st);
+        return tc_launch<1, 16, false, 1>(a, XT, nactive, (n + 15) / 16, st);
+    }
+    if (MT == 2) {
+        if (n >= 32) return tc_launch<2, 32, false, 1>(a, XT, nactive, (n + 31) / 32, st);
+        return tc_launch<2, 16, false, 1>(a, XT, nactive, (n + 15) / 16, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_tc_basis(const StageArgs<float>& a, const float* XT, int MT, int split, int nsub, int ncols,
+                            cudaStream_t st) {
+    if (split == 3) {
+        if (MT == 1) return tc_launch<1, 32, true, 3>(a, XT, nsub, (ncols + 31) / 32, st);
+        if (MT == 2) return tc_launch<2, 16, true, 3>(a, XT, nsub, (ncols + 15) / 16, st);
+        return cudaErrorInvalidValue;
+    }
+    if (MT == 1) return tc_launch<1, 64, true, 1>(a, XT, nsub, (ncols + 63) / 64, st);
+    if (MT == 2) return tc_launch<2, 32, true, 1>(a, XT, nsub, (ncols + 31) / 32, st);
+    return cudaErrorInvalidValue;
+}

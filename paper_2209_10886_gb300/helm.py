@@ -38,7 +38,7 @@ class HelmOpts(ctypes.Structure):
 
 class HelmSetupOpts(ctypes.Structure):
     _fields_ = [("transmission", ctypes.c_int), ("tc_scale", ctypes.c_double),
-                ("boundary_operators", ctypes.c_int)]
+                ("boundary_operators", ctypes.c_int), ("tensor_cores", ctypes.c_int)]
 
 
 class HelmInfo(ctypes.Structure):
@@ -137,12 +137,13 @@ class Problem:
     """
 
     def __init__(self, n_x, n_y, h, omega, m2, N1, N2, xcuts=None, ycuts=None,
-                 transmission="optimized", tc_scale=1.0, boundary_operators=True):
+                 transmission="optimized", tc_scale=1.0, boundary_operators=True, tensor_cores=True):
         L = lib()
         if not (m2.is_cuda and m2.dtype == torch.float64 and m2.numel() == n_x * n_y):
             raise TypeError("m2 must be a float64 CUDA tensor with n_x*n_y values")
         m2 = m2.contiguous()
-        so = HelmSetupOpts(TRANSMISSION[transmission], float(tc_scale), int(bool(boundary_operators)))
+        tcm = {False: 0, True: 1, "3xtf32": 1, "tf32": 2}[tensor_cores]
+        so = HelmSetupOpts(TRANSMISSION[transmission], float(tc_scale), int(bool(boundary_operators)), tcm)
         xc = (ctypes.c_int * (N1 + 1))(*[int(v) for v in xcuts]) if xcuts is not None else None
         yc = (ctypes.c_int * (N2 + 1))(*[int(v) for v in ycuts]) if ycuts is not None else None
         h_ = ctypes.c_void_p()

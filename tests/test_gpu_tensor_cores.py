@@ -1,0 +1,120 @@
+"""Tensor-core (TF32) multi-RHS subdomain solves against the oracle.
+
+With complex64 factors and 16 or more right-hand sides, the stage solves and
+the construction of the boundary operators K run as tcgen05 MMAs on TF32
+operands with FP32 accumulation (k_tc.cu).  TF32 keeps 10 explicit mantissa
+bits: unit roundoff u = 2^-11 = 4.9e-4 per rounded operand, against 6e-8 for
+complex64.  The block recursion over the grid rows amplifies the operand
+roundoff of every step, so the preconditioner agrees with the complex128
+oracle to (amplification) x u; the bar is written per test and the measured
+values are printed with -s.  The FGMRES solution does not inherit this error:
+the residual, the Arnoldi basis and the update stay FP64, so a solve to 1e-9
+matches the direct solve to the same 1e-5 as the complex128 path.
+
+Cases: 1 and 2 tiles of 128 nodes (subdomains 17..131 nodes wide), ragged
+RHS blocks (40 = 32 + 8, 70 = 64 + 6), both schedules, with and without the
+boundary operators.
+"""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import workloads as W
+from oracle import Decomposition, Sweeper, assemble_operator
+
+TF32_PRECOND_TOL = 2e-2      # rel. L2 of one preconditioner application vs the oracle
+
+
+@pytest.fixture(scope="module")
+def H():
+    from paper_2209_10886_gb300 import build
+    build.build()
+    from paper_2209_10886_gb300 import helm
+    helm.lib()
+    return helm
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def cuda(x, dtype=torch.complex128):
+    return torch.as_tensor(np.ascontiguousarray(x)).to(device="cuda", dtype=dtype)
+
+
+CASES = {
+    "tiny_2x2": lambda: W.workload("tiny"),
+    "uneven_4x3": lambda: W.workload("custom", n=70, N1=4, N2=3, medium="layered", seed=4,
+                                     xcuts=[0, 17, 35, 52, 70], ycuts=[0, 25, 46, 70]),
+    "wide_2x2_131": lambda: W.workload("custom", n=262, N1=2, N2=2, medium="layered", seed=7,
+                                       xcuts=[0, 131, 262], ycuts=[0, 129, 262]),
+}
+
+
+def make(H, w, tensor_cores=True, boundary_operators=True):
+    p = H.Problem(w.n, w.n, w.h, w.omega, cuda(w.m2, torch.float64), w.N1, w.N2, w.xcuts, w.ycuts,
+                  boundary_operators=boundary_operators, tensor_cores=tensor_cores)
+    return p.factor("c64")
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("nrhs", [16, 40, 70])
+def test_tensor_core_precond_matches_oracle(H, case, nrhs):
+    w = CASES[case]()
+    p = make(H, w)
+    sw = Sweeper(Decomposition(w.n, w.h, w.omega, w.m2, w.xcuts, w.ycuts))
+    r = W.random_complex((nrhs, w.N), 11)
+    z = p.precond_apply(cuda(r), sched="BSP").cpu().numpy()
+    for k in sorted({0, 7, 31, 32, nrhs - 1} & set(range(nrhs))):
+        e = rel(z[k], sw.precondition(r[k], "BSP"))
+        print(f"{case} nrhs {nrhs} TF32 rhs{k}: rel {e:.2e}")
+        assert e <= TF32_PRECOND_TOL
+    p.close()
+
+
+@pytest.mark.parametrize("sched", ["BSP", "SP"])
+def test_tensor_core_stages_without_boundary_operators(H, sched):
+    """Every stage is a full multi-RHS block solve on the tensor cores."""
+    w = CASES["uneven_4x3"]()
+    p = make(H, w, boundary_operators=False)
+    sw = Sweeper(Decomposition(w.n, w.h, w.omega, w.m2, w.xcuts, w.ycuts))
+    r = W.random_complex((24, w.N), 12)
+    z = p.precond_apply(cuda(r), sched=sched).cpu().numpy()
+    for k in (0, 23):
+        e = rel(z[k], sw.precondition(r[k], sched))
+        print(f"uneven_4x3 {sched} TF32 stages rhs{k}: rel {e:.2e}")
+        assert e <= TF32_PRECOND_TOL
+    p.close()
+
+
+def test_tensor_core_and_cuda_core_paths_agree_on_few_rhs(H):
+    """Below 16 RHS only the construction of K uses the tensor cores."""
+    w = CASES["tiny_2x2"]()
+    a, b = make(H, w, tensor_cores=True), make(H, w, tensor_cores=False)
+    r = cuda(W.random_complex((2, w.N), 13))
+    za, zb = a.precond_apply(r).cpu().numpy(), b.precond_apply(r).cpu().numpy()
+    e = rel(za, zb)
+    print(f"tiny_2x2 TF32 K vs FP32 K, 2 RHS: rel {e:.2e}")
+    assert e <= TF32_PRECOND_TOL
+    a.close(); b.close()
+
+
+def test_tensor_core_fgmres_matches_direct_solve(H):
+    w = CASES["uneven_4x3"]()
+    p = make(H, w)
+    A = assemble_operator(w.n, w.h, w.omega, w.m2).tocsc()
+    f = W.random_complex((20, w.N), 14)
+    u, info, _ = p.solve(cuda(f), tol=1e-9, restart=60, maxit=2000)
+    u = u.cpu().numpy()
+    lu = spla.splu(A)
+    for k in (0, 19):
+        ref = lu.solve(w.h ** 2 * f[k])
+        rr = np.linalg.norm(w.h ** 2 * f[k] - A @ u[k]) / np.linalg.norm(w.h ** 2 * f[k])
+        print(f"uneven_4x3 TF32 FGMRES rhs{k}: iters {info[k][0]}, true relres {rr:.2e}, rel {rel(u[k], ref):.2e}")
+        assert info[k][1] <= 1e-9 and rr <= 1.01e-9
+        assert rel(u[k], ref) <= 1e-5
+    p.close()
