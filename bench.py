@@ -55,9 +55,10 @@ def parse():
     ap.add_argument("--no-fp64-form", action="store_true", help="skip the all-FP64 comparison solve")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=2, help="oracle FGMRES iterations per CPU sample")
-    ap.add_argument("--mode", default="solve", choices=["solve", "precond"],
+    ap.add_argument("--mode", default="solve", choices=["solve", "precond", "schedules"],
                     help="precond: factor once, then time --steps preconditioner applications only "
-                         "(a small, fixed launch sequence for profilers)")
+                         "(a small, fixed launch sequence for profilers); schedules: SP vs BSP on 5 x N2 "
+                         "checkerboards, N2 = 5, 10, 15, 20 (the shape of Table 1)")
     ap.add_argument("--workload", default=None, choices=["plain_mixed", "batching", "large"],
                     help="--mode precond only: the workload to factor (default: the bench workload)")
     ap.add_argument("--nrhs", type=int, default=None,
@@ -65,6 +66,10 @@ def parse():
     ap.add_argument("--tensor-cores", default="3xtf32", choices=["3xtf32", "tf32", "off"],
                     help="complex64 multi-RHS block solves (construction of K, batched RHS): tensor cores with "
                          "split TF32 operands, plain TF32, or FP32 on the CUDA cores")
+    ap.add_argument("--graph", action="store_true",
+                    help="replay every preconditioner application from a captured CUDA graph")
+    ap.add_argument("--tc-min-rhs", type=int, default=16,
+                    help="stages with at least this many RHS run on the tensor cores (1: all)")
     return ap.parse_args()
 
 
@@ -80,7 +85,8 @@ def precond_only(args):
     name = args.workload or WORKLOAD
     w = W.workload(name, nrhs=args.nrhs) if args.nrhs else W.workload(name)
     m2 = torch.as_tensor(w.m2, dtype=torch.float64, device="cuda")
-    p = Problem(w.n, w.n, w.h, w.omega, m2, w.N1, w.N2, w.xcuts, w.ycuts, tensor_cores=TC_MODES[args.tensor_cores])
+    p = Problem(w.n, w.n, w.h, w.omega, m2, w.N1, w.N2, w.xcuts, w.ycuts, tensor_cores=TC_MODES[args.tensor_cores],
+                tc_min_rhs=args.tc_min_rhs)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     p.factor(args.prec)
@@ -116,6 +122,52 @@ def precond_only(args):
                       "ms_per_apply": ms, "unknowns_rhs_per_s": w.N * r.shape[0] / (ms / 1e3),
                       "kernels": kern}))
     p.close()
+
+
+def schedules(args):
+    """SP against BSP on 5 x N2 checkerboards (the shape of the paper's Table 1).
+
+    The 639^2 domain (layered + random medium, 10 points per wavelength, one source
+    at (0.5, 0.2)) is cut into 5 columns of 128 nodes (the last 127) and N2 = 5, 10,
+    15, 20 rows.  Per schedule: FGMRES iterations to 1e-6 (ni), sweep steps per
+    preconditioner application (ns: SP 2(N1+N2-2), BSP 2 N1, as in Table 1) and the
+    solve time (t), with t / (ni ns).
+    """
+    import torch
+
+    import workloads as W
+    from paper_2209_10886_gb300 import Problem
+    n = 639
+    rows = []
+    for N2 in (5, 10, 15, 20):
+        w = W.workload("custom", n=n, N1=5, N2=N2, medium="layered", seed=0, ppw=10.0,
+                       xcuts=W.even_cuts(n, 5, 128))
+        h = w.h
+        f = torch.as_tensor(W.gaussian_source(n, h, (0.5, 0.2), 2 * h)[None, :], dtype=torch.complex128,
+                            device="cuda")
+        m2 = torch.as_tensor(w.m2, dtype=torch.float64, device="cuda")
+        p = Problem(w.n, w.n, w.h, w.omega, m2, w.N1, w.N2, w.xcuts, w.ycuts,
+                    tensor_cores=TC_MODES[args.tensor_cores]).factor(args.prec)
+        row = {"N1xN2": f"5x{N2}"}
+        for sched in ("SP", "BSP"):
+            kw = dict(restart=args.restart, maxit=2000, tol=args.tol, sched=sched, use_graph=args.graph,
+                      raise_on_noconv=False)
+            p.solve(f, **kw)                                                    # warm-up
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            _, info, _ = p.solve(f, **kw)
+            e1.record()
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) / 1e3
+            ni = info[0][0]
+            ns = 2 * (5 + N2 - 2) if sched == "SP" else 2 * 5
+            row[sched] = {"ni": ni, "ns": ns, "t_s": t, "relres": info[0][1], "converged": info[0][1] <= args.tol,
+                          "t_per_ni_ns_ms": 1e3 * t / (ni * ns)}
+        p.close()
+        rows.append(row)
+    print(json.dumps({"mode": "schedules", "workload": f"{n}^2 layered+random 10 ppw, 5 x N2, 1 source",
+                      "prec": args.prec, "restart": args.restart, "tol": args.tol, "rows": rows}))
 
 
 def peaks():
@@ -284,7 +336,8 @@ def gpu_arm(args):
     w = W.workload(WORKLOAD)
     m2 = torch.as_tensor(w.m2, dtype=torch.float64, device=dev)
     f = torch.as_tensor(w.f, dtype=torch.complex128, device=dev)
-    p = Problem(w.n, w.n, w.h, w.omega, m2, w.N1, w.N2, w.xcuts, w.ycuts)
+    p = Problem(w.n, w.n, w.h, w.omega, m2, w.N1, w.N2, w.xcuts, w.ycuts, tensor_cores=TC_MODES[args.tensor_cores],
+                tc_min_rhs=args.tc_min_rhs)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     p.factor(args.prec)
@@ -294,7 +347,7 @@ def gpu_arm(args):
     u = torch.empty_like(f)
 
     def solve():
-        _, info, _ = p.solve(f, u=u, restart=args.restart, maxit=3000, tol=args.tol, sched=args.sched)
+        _, info, _ = p.solve(f, u=u, restart=args.restart, maxit=3000, tol=args.tol, sched=args.sched, use_graph=args.graph)
         return info[0]
 
     for _ in range(args.warmup):
@@ -346,7 +399,7 @@ def gpu_arm(args):
     t0 = time.perf_counter()
     for _ in range(args.steps):
         fd = fh.to(dev, non_blocking=True)
-        ud, info2, _ = p.solve(fd, restart=args.restart, maxit=3000, tol=args.tol, sched=args.sched)
+        ud, info2, _ = p.solve(fd, restart=args.restart, maxit=3000, tol=args.tol, sched=args.sched, use_graph=args.graph)
         uh_pinned.copy_(ud, non_blocking=True)
         torch.cuda.synchronize()
     e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
@@ -358,11 +411,11 @@ def gpu_arm(args):
     # the paper's other schedule (symmetric Gauss-Seidel sweeps, Section 4) on the same factors
     sp_form = None
     if args.sched == "BSP" and not args.no_fp64_form:
-        _, isp, _ = p.solve(f, restart=args.restart, maxit=3000, tol=args.tol, sched="SP")    # warm
+        _, isp, _ = p.solve(f, restart=args.restart, maxit=3000, tol=args.tol, sched="SP", use_graph=args.graph)    # warm
         torch.cuda.synchronize()
         b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         b0.record(st)
-        _, isp, _ = p.solve(f, restart=args.restart, maxit=3000, tol=args.tol, sched="SP")
+        _, isp, _ = p.solve(f, restart=args.restart, maxit=3000, tol=args.tol, sched="SP", use_graph=args.graph)
         b1.record(st)
         torch.cuda.synchronize()
         mssp = b0.elapsed_time(b1)
@@ -374,11 +427,11 @@ def gpu_arm(args):
     if not args.no_fp64_form and args.prec == "c64":
         q = Problem(w.n, w.n, w.h, w.omega, m2, w.N1, w.N2, w.xcuts, w.ycuts)
         q.factor("c128")
-        _, i64, _ = q.solve(f, restart=args.restart, maxit=3000, tol=args.tol, sched=args.sched)  # warm
+        _, i64, _ = q.solve(f, restart=args.restart, maxit=3000, tol=args.tol, sched=args.sched, use_graph=args.graph)  # warm
         torch.cuda.synchronize()
         a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a0.record(st)
-        _, i64, _ = q.solve(f, restart=args.restart, maxit=3000, tol=args.tol, sched=args.sched)
+        _, i64, _ = q.solve(f, restart=args.restart, maxit=3000, tol=args.tol, sched=args.sched, use_graph=args.graph)
         a1.record(st)
         torch.cuda.synchronize()
         ms64 = a0.elapsed_time(a1)
@@ -437,6 +490,7 @@ def gpu_arm(args):
             "workload": w.description, "n": w.n, "N1": w.N1, "N2": w.N2, "nrhs": w.nrhs, "unknowns": w.N,
             "prec": args.prec, "sched": args.sched, "restart": args.restart, "tol": args.tol,
             "transmission": "optimized, scale 1.0", "iterations": iters[-1][0], "relres": relres,
+            "tensor_cores": args.tensor_cores, "tc_min_rhs": args.tc_min_rhs, "cuda_graph": args.graph,
             "relres_host_check": check, "factor_ms": factor_ms, "factor_bytes": p.info()["factor_bytes"],
             "l2": "inputs larger than L2: every preconditioner application streams the 1.07 GB of factors",
             "parallelism": f"replicas x{world}",
@@ -464,6 +518,8 @@ def main():
         reference_arm(args)
     elif args.mode == "precond":
         precond_only(args)
+    elif args.mode == "schedules":
+        schedules(args)
     else:
         gpu_arm(args)
 

@@ -115,6 +115,9 @@ typedef struct {
                            2: TF32 operands alone (rounded to nearest; unit roundoff 2^-11),
                               one MMA per product; the copy takes the bytes of the factors
                            0: FP32 arithmetic on the CUDA cores, no second copy */
+    int tc_min_rhs;     /* stages with at least this many right-hand sides use the tensor
+                           cores (when tensor_cores != 0); default 16, minimum 1.  Below
+                           16 the MMA columns are padded (N = 32 per 16 RHS) */
 } helm_setup_opts;
 
 typedef struct {
@@ -123,7 +126,10 @@ typedef struct {
     double tol;         /* stop when ||h^2 f - A u|| <= tol ||h^2 f|| (true residual) */
     int x0_given;       /* 1: u holds the initial guess; 0: start from u = 0 */
     int sched;          /* helm_sched used by the preconditioner */
-    int use_graph;      /* 1: replay the preconditioner from a captured CUDA graph */
+    int use_graph;      /* 1: every preconditioner application is replayed from a CUDA graph
+                           captured on first use for its (schedule, nrhs, input, output)
+                           (one graph per Arnoldi slot; dropped when the factors or the
+                           workspace change); ignored while helm_profile is on */
     double* hist;       /* optional host buffer of maxit*nrhs doubles: the Arnoldi
                            residual estimate of RHS k after step j at hist[k*maxit+j] */
     int ortho;          /* Arnoldi orthogonalisation, all FP64: HELM_ORTHO_MGS (default;

@@ -23,6 +23,7 @@ cudaError_t launch_mgs(const double2* V, long long vsk, long long vsr, double2* 
 #include <atomic>
 static std::atomic<long long> g_launches{0};
 void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+static void uncount_launch(long long n) { g_launches.fetch_sub(n, std::memory_order_relaxed); }
 extern "C" long long helm_launch_count(void) { return g_launches.load(); }
 
 // ------------------------------------------------------------------ errors
@@ -181,13 +182,17 @@ struct helm_problem {
     size_t X_bytes = 0;
     float* d_XT = nullptr;           // complex64 factors in the tensor cores' operand layout (k_tc.cu)
     size_t XT_bytes = 0;
-    int tc_mt = 0;                   // 128-node M tiles of that layout
+    int tc_mt = 0;                   // largest tile count (128 nodes each) of that layout
     int tc_split = 0;                // 3: hi + lo TF32 pairs, 1: TF32 alone
+    int tc_all_off[2] = {0, 0}, tc_all_n[2] = {0, 0};   // all subdomains by tile count, in d_stage_subs
+    long long etot = 0;              // boundary slots 2 (mx + my) summed over the subdomains
 
     // preconditioner workspace
     int ws_nrhs = 0;
     void* d_trace[3] = {nullptr, nullptr, nullptr};
     void* d_yws = nullptr;
+    void* d_escr = nullptr;          // tensor-core path: 2 nrhs etot complex64 (interface data, boundary values)
+    void* d_r64 = nullptr;           // tensor-core path: the scaled source in complex64 (nrhs N)
     double* d_pc_norm = nullptr;     // per RHS: ||r||^2, 1/||r||, ||r||
     double* d_pc_partial = nullptr;
 
@@ -215,6 +220,19 @@ struct helm_problem {
     };
     KProf prof[5];
     int prof_on = 0;
+
+    // preconditioner applications captured as CUDA graphs (gmres_solve with use_graph):
+    // one executable graph per (schedule, nrhs, r, z), replayed on the caller's stream
+    struct PcGraph {
+        int sched, nrhs;
+        const void* r;
+        void* z;
+        cudaGraphExec_t exec;
+        long long kernels;           // kernel launches one replay performs
+    };
+    std::vector<PcGraph> graphs;
+    cudaStream_t cap_stream = nullptr;
+    cudaEvent_t cap_ev = nullptr;
 
     long long N() const { return (long long)nx * ny; }
 };
@@ -272,9 +290,17 @@ extern "C" helm_status helm_profile_read(helm_problem* p, int k, helm_kstat* out
     return HELM_OK;
 }
 
+// the captured graphs refer to the factors and the workspace: drop them whenever either changes
+static void drop_graphs(helm_problem* p) {
+    for (auto& g : p->graphs) cudaGraphExecDestroy(g.exec);
+    p->graphs.clear();
+}
 static void free_pc_ws(helm_problem* p) {
+    drop_graphs(p);
     for (auto& b : p->d_trace) dfree(b);
     dfree(p->d_yws);
+    dfree(p->d_escr);
+    dfree(p->d_r64);
     dfree(p->d_pc_norm);
     dfree(p->d_pc_partial);
     p->ws_nrhs = 0;
@@ -311,6 +337,7 @@ extern "C" void helm_default_setup_opts(helm_setup_opts* o) {
     o->tc_scale = 1.0;
     o->boundary_operators = 1;
     o->tensor_cores = 1;
+    o->tc_min_rhs = 16;
 }
 
 extern "C" const char* helm_last_error(void) { return g_err.c_str(); }
@@ -361,6 +388,8 @@ extern "C" helm_status helm_setup(int n_x, int n_y, double h, double omega, cons
     if (so.transmission != HELM_TC_OPTIMIZED && so.transmission != HELM_TC_IMPEDANCE)
         return arg_error("helm_setup: unknown transmission");
     if (so.transmission == HELM_TC_OPTIMIZED && !(so.tc_scale > 0)) return arg_error("helm_setup: tc_scale must be > 0");
+    if (so.tensor_cores < 0 || so.tensor_cores > 2) return arg_error("helm_setup: tensor_cores must be 0, 1 or 2");
+    if (so.tc_min_rhs < 1) return arg_error("helm_setup: tc_min_rhs must be >= 1");
 
     auto xc = make_cuts(n_x, N1, xcuts), yc = make_cuts(n_y, N2, ycuts);
     for (int k = 0; k < N1; ++k)
@@ -404,7 +433,12 @@ extern "C" helm_status helm_setup(int n_x, int n_y, double h, double omega, cons
         }
     if (p->max_mx > 256) { delete p; return arg_error("helm_setup: subdomains wider than 256 nodes are not supported"); }
     long long loff = 0;
-    for (auto& s : p->subs) { s.dev.loff = loff; s.dev.yoff = loff; loff += (long long)s.dev.mx * s.dev.my; }
+    for (auto& s : p->subs) {
+        s.dev.loff = loff; s.dev.yoff = loff; loff += (long long)s.dev.mx * s.dev.my;
+        s.dev.tcmt = tc_tiles(s.dev.mx);
+        s.dev.eoff = p->etot;
+        p->etot += 2LL * (s.dev.mx + s.dev.my);
+    }
 
     // interface unknowns (i, j) in the paper's pair order m(i, j) (Section 2)
     std::vector<int> slot_sub, slot_side, slot_off, slot_len;
@@ -458,12 +492,27 @@ extern "C" helm_status helm_setup(int n_x, int n_y, double h, double omega, cons
 
     // stage lists and their subdomain arrays
     std::vector<int> all_stage_subs;
+    // a list of subdomains split by tensor-core tile count (1: mx <= 128, 2: mx <= 256)
+    auto tc_classes = [&](const std::vector<int>& v, int* off, int* n) {
+        for (int c = 0; c < 2; ++c) {
+            off[c] = (int)all_stage_subs.size();
+            for (int id : v)
+                if (p->subs[id].dev.tcmt == c + 1) all_stage_subs.push_back(id);
+            n[c] = (int)all_stage_subs.size() - off[c];
+        }
+    };
     for (int sc = 0; sc < 2; ++sc) {
         p->sched[sc] = build_schedule(sc, N1, N2, p->ondiag, p->all, p->nslots > 0);
         for (auto& st : p->sched[sc]) {
             st.sub_off = (int)all_stage_subs.size();
             all_stage_subs.insert(all_stage_subs.end(), st.subs.begin(), st.subs.end());
+            tc_classes(st.subs, st.tc_off, st.tc_n);
         }
+    }
+    {
+        std::vector<int> ids(p->subs.size());
+        for (size_t k = 0; k < ids.size(); ++k) ids[k] = (int)k;
+        tc_classes(ids, p->tc_all_off, p->tc_all_n);
     }
 
     // device tables
@@ -517,6 +566,8 @@ extern "C" helm_status helm_setup(int n_x, int n_y, double h, double omega, cons
 extern "C" helm_status helm_destroy(helm_problem* p) {
     if (!p) return HELM_OK;
     free_pc_ws(p);
+    if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+    if (p->cap_ev) cudaEventDestroy(p->cap_ev);
     free_krylov(p);
     free_adj(p);
     dfree(p->d_m2); dfree(p->d_adiag); dfree(p->d_dloc); dfree(p->d_subtab);
@@ -583,7 +634,10 @@ static helm_status build_boundary_operators_t(helm_problem* p, cudaStream_t st) 
         a.col0 = c0;
         if constexpr (sizeof(R) == 4) {
             if (p->d_XT) {
-                e = launch_tc_basis(a, p->d_XT, p->tc_mt, p->tc_split, (int)p->subs.size(), NB, st);
+                for (int c = 0; c < 2 && e == cudaSuccess; ++c) {
+                    a.subs = p->d_stage_subs + p->tc_all_off[c];
+                    e = launch_tc_basis(a, p->d_XT, c + 1, p->tc_split, p->tc_all_n[c], NB, st);
+                }
                 continue;
             }
         }
@@ -628,13 +682,14 @@ extern "C" helm_status precond_factor(helm_problem* p, helm_prec prec, void* str
         s.dev.xoff = xoff;
         xoff += (long long)s.dev.my * mx * (s.dev.ld0 + s.dev.ld1);
         s.dev.xtoff = xtoff;
-        if (mt) xtoff += tc_layout_floats(mx, s.dev.my, mt, split);
+        if (mt) xtoff += tc_layout_floats(mx, s.dev.my, s.dev.tcmt, split);
         p->max_w = std::max(p->max_w, std::max(w0, w1));
         p->max_ld = std::max(p->max_ld, std::max(s.dev.ld0, s.dev.ld1));
         tab.push_back(s.dev);
     }
     const size_t bytes = (size_t)xoff * elem;
     HELM_CUDA_TRY(cudaStreamSynchronize(st));
+    drop_graphs(p);
     if (p->d_X) { cudaFree(p->d_X); p->d_X = nullptr; p->X_bytes = 0; p->factored = 0; }
     if (p->d_K) { cudaFree(p->d_K); p->d_K = nullptr; p->K_bytes = 0; }
     if (p->d_XT) { cudaFree(p->d_XT); p->d_XT = nullptr; p->XT_bytes = 0; p->tc_mt = 0; p->tc_split = 0; }
@@ -678,7 +733,7 @@ extern "C" helm_status precond_factor(helm_problem* p, helm_prec prec, void* str
         p->XT_bytes = (size_t)xtoff * sizeof(float);
         p->tc_mt = mt;
         p->tc_split = split;
-        e = launch_tc_layout(p->d_subtab, (int)p->subs.size(), mt, split, (const float2*)p->d_X, p->d_XT, st);
+        e = launch_tc_layout(p->d_subtab, (int)p->subs.size(), split, (const float2*)p->d_X, p->d_XT, st);
         if (e != cudaSuccess) return cuda_status(e, "precond_factor: tensor-core layout");
     }
     {
@@ -692,6 +747,11 @@ extern "C" helm_status precond_factor(helm_problem* p, helm_prec prec, void* str
 }
 
 // ------------------------------------------------------------ preconditioner
+// stages over nrhs right-hand sides run on the tensor cores
+static bool tc_used(const helm_problem* p, int nrhs) {
+    return p->d_XT != nullptr && nrhs >= std::max(1, p->sopts.tc_min_rhs);
+}
+
 static helm_status ensure_pc_ws(helm_problem* p, int nrhs) {
     if (p->ws_nrhs >= nrhs) return HELM_OK;
     free_pc_ws(p);
@@ -700,6 +760,10 @@ static helm_status ensure_pc_ws(helm_problem* p, int nrhs) {
     for (int b = 0; b < 3 && e == cudaSuccess && p->ntrace > 0; ++b)
         e = cudaMalloc(&p->d_trace[b], (size_t)p->ntrace * nrhs * elem);
     if (e == cudaSuccess) e = cudaMalloc(&p->d_yws, (size_t)p->N() * nrhs * elem);
+    if (e == cudaSuccess && tc_used(p, nrhs)) {
+        e = cudaMalloc(&p->d_escr, (size_t)2 * p->etot * nrhs * sizeof(float2));
+        if (e == cudaSuccess) e = cudaMalloc(&p->d_r64, (size_t)p->N() * nrhs * sizeof(float2));
+    }
     if (e == cudaSuccess) e = dalloc(p->d_pc_norm, 3 * (size_t)nrhs);
     if (e == cudaSuccess) e = dalloc(p->d_pc_partial, (size_t)kPartialBlocks * nrhs);
     if (e != cudaSuccess) { free_pc_ws(p); return cuda_status(e, "allocating the preconditioner workspace"); }
@@ -715,6 +779,8 @@ struct PcWork {
     void* yws;
     double* norm;
     double* partial;
+    void* escr;                      // tensor-core path only (else null)
+    void* r64;
 };
 
 template <typename R>
@@ -731,6 +797,9 @@ static helm_status run_precond_t(helm_problem* p, const PcWork& w, int sched, co
         rinv = w.norm + nrhs;
         rsc = w.norm + 2 * nrhs;
     }
+    // the tensor-core stages read the scaled source in complex64
+    const bool tc = sizeof(R) == 4 && tc_used(p, nrhs) && w.escr && w.r64;
+    if (tc) launch_to_c64_scaled(r, rinv, (float2*)w.r64, p->N(), nrhs, st);
     T* buf[3] = {(T*)w.trace[0], (T*)w.trace[1], (T*)w.trace[2]};
     auto B = [&](int id) -> T* { return id < 0 ? nullptr : buf[id]; };
     for (const StageDesc& sd : p->sched[sched]) {
@@ -811,8 +880,16 @@ static helm_status run_precond_t(helm_problem* p, const PcWork& w, int sched, co
         bool done = false;
         if constexpr (sizeof(R) == 4) {
             // 16 or more right-hand sides: the block solves are GEMMs for the tensor cores
-            if (p->d_XT && nrhs >= 16) {
-                e = launch_tc_stage(a, p->d_XT, p->tc_mt, p->tc_split, (int)sd.subs.size(), st);
+            if (tc) {
+                for (int c = 0; c < 2 && e == cudaSuccess; ++c) {
+                    StageArgs<R> ac = a;
+                    ac.escr = (T*)w.escr;
+                    ac.uscr = (T*)w.escr + (long long)nrhs * p->etot;
+                    ac.estride = p->etot;
+                    ac.r64 = (const T*)w.r64;
+                    ac.subs = p->d_stage_subs + sd.tc_off[c];
+                    e = launch_tc_stage(ac, p->d_XT, c + 1, p->tc_split, sd.tc_n[c], st);
+                }
                 done = true;
             }
         }
@@ -827,9 +904,49 @@ static helm_status run_precond_t(helm_problem* p, const PcWork& w, int sched, co
 static helm_status run_precond(helm_problem* p, int sched, const double2* r, double2* z, int nrhs, cudaStream_t st) {
     helm_status s = ensure_pc_ws(p, nrhs);
     if (s != HELM_OK) return s;
-    const PcWork w{{p->d_trace[0], p->d_trace[1], p->d_trace[2]}, p->d_yws, p->d_pc_norm, p->d_pc_partial};
+    const PcWork w{{p->d_trace[0], p->d_trace[1], p->d_trace[2]}, p->d_yws, p->d_pc_norm, p->d_pc_partial,
+                   p->d_escr, p->d_r64};
     return p->prec == HELM_PREC_C64 ? run_precond_t<float>(p, w, sched, r, z, nrhs, st)
                                     : run_precond_t<double>(p, w, sched, r, z, nrhs, st);
+}
+
+// The same application replayed from a captured CUDA graph: the first call for a
+// (schedule, nrhs, r, z) captures the launch sequence on an internal stream (the
+// caller's stream may be the legacy default stream, which cannot be captured);
+// every call launches the executable graph on the caller's stream.
+static helm_status run_precond_graph(helm_problem* p, int sched, const double2* r, double2* z, int nrhs,
+                                     cudaStream_t st) {
+    if (p->prof_on) return run_precond(p, sched, r, z, nrhs, st);   // per-launch events need plain launches
+    helm_status s = ensure_pc_ws(p, nrhs);
+    if (s != HELM_OK) return s;
+    for (const auto& g : p->graphs)
+        if (g.sched == sched && g.nrhs == nrhs && g.r == r && g.z == z) {
+            HELM_CUDA_TRY(cudaGraphLaunch(g.exec, st));
+            count_launch((int)g.kernels);
+            return HELM_OK;
+        }
+    if (p->graphs.size() >= 1024) drop_graphs(p);
+    if (!p->cap_stream) {
+        HELM_CUDA_TRY(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
+        HELM_CUDA_TRY(cudaEventCreateWithFlags(&p->cap_ev, cudaEventDisableTiming));
+    }
+    const long long before = helm_launch_count();
+    HELM_CUDA_TRY(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeRelaxed));
+    s = run_precond(p, sched, r, z, nrhs, p->cap_stream);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(p->cap_stream, &graph);
+    const long long kernels = helm_launch_count() - before;
+    uncount_launch(kernels);                                          // captured, not launched
+    if (s != HELM_OK) { if (graph) cudaGraphDestroy(graph); return s; }
+    if (ec != cudaSuccess) return cuda_status(ec, "capturing the preconditioner");
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) return cuda_status(ei, "instantiating the preconditioner graph");
+    p->graphs.push_back({sched, nrhs, r, z, exec, kernels});
+    HELM_CUDA_TRY(cudaGraphLaunch(exec, st));
+    count_launch((int)kernels);
+    return HELM_OK;
 }
 
 extern "C" helm_status precond_apply(helm_problem* p, int sched, const helm_c128* r, helm_c128* z, int nrhs,
@@ -868,7 +985,10 @@ extern "C" helm_status precond_apply_noalloc(helm_problem* p, int sched, const h
     const size_t ybytes = round256((size_t)p->N() * nrhs * elem);
     const size_t nbytes = round256((size_t)3 * nrhs * sizeof(double));
     const size_t pbytes = round256((size_t)kPartialBlocks * nrhs * sizeof(double));
-    const size_t need = 3 * tbytes + ybytes + nbytes + pbytes;
+    const bool tc = p->prec == HELM_PREC_C64 && tc_used(p, nrhs);
+    const size_t ebytes = tc ? round256((size_t)2 * p->etot * nrhs * sizeof(float2)) : 0;
+    const size_t rbytes = tc ? round256((size_t)p->N() * nrhs * sizeof(float2)) : 0;
+    const size_t need = 3 * tbytes + ybytes + nbytes + pbytes + ebytes + rbytes;
     if (need > (size_t)HELM_NOALLOC_SCRATCH_BYTES) {
         char buf[256];
         snprintf(buf, sizeof buf,
@@ -888,8 +1008,9 @@ extern "C" helm_status precond_apply_noalloc(helm_problem* p, int sched, const h
         g_noalloc_ptr[dev].store(base);
     }
     unsigned char* b = (unsigned char*)base;
+    unsigned char* tail = b + 3 * tbytes + ybytes + nbytes + pbytes;
     PcWork w{{b, b + tbytes, b + 2 * tbytes}, b + 3 * tbytes, (double*)(b + 3 * tbytes + ybytes),
-             (double*)(b + 3 * tbytes + ybytes + nbytes)};
+             (double*)(b + 3 * tbytes + ybytes + nbytes), tc ? tail : nullptr, tc ? tail + ebytes : nullptr};
     cudaStream_t st = (cudaStream_t)stream;
     return p->prec == HELM_PREC_C64 ? run_precond_t<float>(p, w, sched, (const double2*)r, (double2*)z, nrhs, st)
                                     : run_precond_t<double>(p, w, sched, (const double2*)r, (double2*)z, nrhs, st);
@@ -997,6 +1118,7 @@ static helm_status gmres_impl(helm_problem* p, const double2* f, double2* u, int
     for (auto& b : bnorm) b *= h2;
 
     std::vector<int> iters(nrhs, 0), done(nrhs, 0), active(nrhs, 0), jcount(nrhs, 0);
+    int dev_status = 0;
     std::vector<double> relres(nrhs, 0.0);
     for (int k = 0; k < nrhs; ++k) done[k] = bnorm[k] == 0.0;
 
@@ -1034,7 +1156,7 @@ static helm_status gmres_impl(helm_problem* p, const double2* f, double2* u, int
             double2* Vn = p->d_V + (long long)(j + 1) * vsk;
             double2* Zj = p->d_Z + (long long)j * vsk;
             // z_j = M^{-1} v_j ; w = A z_j
-            s = run_precond(p, o.sched, Vj, Zj, nrhs, st);
+            s = o.use_graph ? run_precond_graph(p, o.sched, Vj, Zj, nrhs, st) : run_precond(p, o.sched, Vj, Zj, nrhs, st);
             if (s != HELM_OK) return s;
             const double vb = 16.0 * N * nrhs;   // bytes of one field for all RHS
             prof_begin(p, HELM_K_MATVEC, st);
@@ -1088,7 +1210,9 @@ static helm_status gmres_impl(helm_problem* p, const double2* f, double2* u, int
         step_done:
             HELM_CUDA_TRY(cudaGetLastError());
             HELM_CUDA_TRY(cudaMemcpyAsync(est.data(), p->d_est, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
+            HELM_CUDA_TRY(cudaMemcpyAsync(&dev_status, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
             HELM_CUDA_TRY(cudaStreamSynchronize(st));
+            if (dev_status != 0) return take_device_status(p, "gmres_solve");   // a bounded device wait expired
             if (p->prof_on && !use_mgs) {
                 // the second Gram-Schmidt pass ran for the RHS that needed it
                 int nre = 0;

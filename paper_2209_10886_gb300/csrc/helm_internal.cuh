@@ -71,6 +71,8 @@ struct SubDev {
     int Lb;
     long long koff;            // element offset of the Lb x Lb boundary operator K in its array
     long long xtoff;           // float offset of this subdomain's factors in the tensor-core layout (k_tc.cu)
+    int tcmt;                  // 128-node tiles of that layout: 1 (mx <= 128), 2 (mx <= 256), 0 (wider)
+    long long eoff;            // offset of this subdomain's 2 (mx + my) boundary slots in the edge scratch
 };
 
 // Trace-point coefficients of one interface edge point (beta_e = T_e h / 2):
@@ -91,6 +93,7 @@ struct StageDesc {
     int dst, dst2, base, sub;  // dst[slot] = base[slot] - sub[slot] + G_out (also into dst2)
     int final_;                // 1: write the volume solution into z
     int sub_off;               // offset of `subs` in the device stage-list array
+    int tc_off[2], tc_n[2];    // the same subdomains split by tensor-core tile count (1, 2): offsets, counts
 };
 
 // launch parameters of the fused stage kernel (passed by value)
@@ -119,6 +122,12 @@ template <typename R> struct StageArgs {
     T* K;
     int col0;
     int* err;                  // device status word: set to HELM_ERR_TIMEOUT when a bounded wait expires
+    // tensor-core path: per RHS, estride boundary slots (W[my] E[my] S[mx] N[mx] of every
+    // subdomain at SubDev::eoff): escr = interface data of the nodes, uscr = boundary values
+    T* escr;
+    T* uscr;
+    long long estride;
+    const T* r64;              // tensor-core path: the source already scaled by rscale, in complex64
 };
 
 // launch parameters of the interface (boundary-operator) stage kernel
@@ -172,11 +181,12 @@ template <typename R>
 cudaError_t launch_basis(const StageArgs<R>& a, int nsub, int ncols, int max_mx, int max_my, int max_w, int max_ld,
                          cudaStream_t st);
 // tensor-core (TF32) multi-RHS solves of complex64 factors (k_tc.cu)
-// split = 3: operands as hi + lo TF32 pairs, three MMAs per product; split = 1: TF32 alone
-int tc_tiles(int max_mx);                                 // 128-node M tiles (1 or 2), 0: unsupported width
+// split = 3: operands as hi + lo TF32 pairs, three MMAs per product; split = 1: TF32 alone.
+// Every subdomain has its own tile count (SubDev::tcmt); one launch covers the
+// subdomains a.subs[0 .. nactive) of tile count MT.
+int tc_tiles(int mx);                                     // 128-node M tiles (1 or 2), 0: unsupported width
 long long tc_layout_floats(int mx, int my, int MT, int split);   // floats of one subdomain's factors in that layout
-cudaError_t launch_tc_layout(const SubDev* subtab, int nsub, int MT, int split, const float2* X, float* XT,
-                             cudaStream_t st);
+cudaError_t launch_tc_layout(const SubDev* subtab, int nsub, int split, const float2* X, float* XT, cudaStream_t st);
 cudaError_t launch_tc_stage(const StageArgs<float>& a, const float* XT, int MT, int split, int nactive,
                             cudaStream_t st);
 cudaError_t launch_tc_basis(const StageArgs<float>& a, const float* XT, int MT, int split, int nsub, int ncols,
@@ -213,6 +223,9 @@ void launch_hessenberg_solve(const double2* H, int ldh, long long hstride, const
 void launch_mask_copy(double2* dst, const double2* src, long long n, int nrhs, const int* active,
                       cudaStream_t st);
 void launch_sqrt_inplace(double* v, int n, cudaStream_t st);
+// out[k*n + i] = complex64(src[k*n + i] * scale[k])
+void launch_to_c64_scaled(const double2* src, const double* scale, float2* out, long long n, int nrhs,
+                          cudaStream_t st);
 void launch_scale_from_norm(const double* norm2, double* inv, double* scale, int n, cudaStream_t st);
 // adjoint
 void launch_receiver_residual(const double2* u, long long N, const int* rec, int nrec, const double2* d,

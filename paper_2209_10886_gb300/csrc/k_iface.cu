@@ -116,6 +116,8 @@ cudaError_t launch_nr(const IfaceArgs<R>& a, int nactive, int max_rows, int max_
 template <typename R>
 cudaError_t launch_iface(const IfaceArgs<R>& a, int nactive, int max_rows, int max_Lb, cudaStream_t st) {
     if (nactive == 0 || a.nrhs == 0) return cudaSuccess;
+    // blocks of 4 RHS: wider blocks (8, 16) re-read K less often but leave fewer CTAs
+    // and measured slower (16 RHS: 2x the time at 64 RHS on the 1023^2 workload)
     if (a.nrhs >= 4) return launch_nr<R, 4>(a, nactive, max_rows, max_Lb, st);
     if (a.nrhs >= 2) return launch_nr<R, 2>(a, nactive, max_rows, max_Lb, st);
     return launch_nr<R, 1>(a, nactive, max_rows, max_Lb, st);

@@ -366,3 +366,21 @@ void launch_scale_from_norm(const double* norm2, double* inv, double* scale, int
     count_launch();
     scale_from_norm_kernel<<<(n + 127) / 128, 128, 0, st>>>(norm2, inv, scale, n);
 }
+
+// ------------------------------------------------------- c128 -> c64 scaling
+__global__ void to_c64_scaled_kernel(const double2* __restrict__ src, const double* __restrict__ scale,
+                                     float2* __restrict__ out, long long n, int nrhs) {
+    const long long total = n * nrhs;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double sc = scale[i / n];
+        const double2 v = src[i];
+        out[i] = make_float2((float)(v.x * sc), (float)(v.y * sc));
+    }
+}
+
+void launch_to_c64_scaled(const double2* src, const double* scale, float2* out, long long n, int nrhs,
+                          cudaStream_t st) {
+    count_launch();
+    to_c64_scaled_kernel<<<1216, 256, 0, st>>>(src, scale, out, n, nrhs);
+}

@@ -10,7 +10,9 @@
 // update re-reads it from L1).  The dot products are reduced deterministically:
 // every CTA writes its partial sum, passes a grid barrier, and adds all
 // partials in the same order.  Barrier waits are bounded in time; on expiry the
-// kernel records HELM_ERR_TIMEOUT and returns.
+// kernel records HELM_ERR_TIMEOUT and returns.  When two slices of the vector per
+// CTA fit in shared memory, mgs_smem_kernel streams the basis vectors there by
+// bulk copies issued one step ahead.
 #include "helm_internal.cuh"
 
 namespace {
@@ -135,17 +137,22 @@ __global__ void __launch_bounds__(MT) mgs_kernel(MgsArgs a) {
         const double2* vprev = nullptr;
         for (int k = 0; k < a.nvec; ++k) {
             const double2* v = a.V + k * a.vsk + r * a.vsr;
-            double2 acc = make_double2(0.0, 0.0);
+            // four independent partial sums: short FP64 dependency chains
+            double2 acc[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[q] = make_double2(0.0, 0.0);
 #pragma unroll
             for (int e = 0; e < EPT; ++e) {
                 const long long p = base + e * stride;
                 if (p < a.n) {
                     if (vprev) wr[e] = cfma(mh, vprev[p], wr[e]);
-                    acc = cfmaconj(v[p], wr[e], acc);
+                    acc[e & 3] = cfmaconj(v[p], wr[e], acc[e & 3]);
                 }
             }
+            const double2 accs = make_double2((acc[0].x + acc[1].x) + (acc[2].x + acc[3].x),
+                                              (acc[0].y + acc[1].y) + (acc[2].y + acc[3].y));
             double2 h;
-            if (!reduce(acc, h)) return;
+            if (!reduce(accs, h)) return;
             if (blockIdx.x == 0 && threadIdx.x == 0) a.hcol[(long long)r * a.ldh + k] = h;
             mh = make_double2(-h.x, -h.y);
             vprev = v;
@@ -168,6 +175,156 @@ __global__ void __launch_bounds__(MT) mgs_kernel(MgsArgs a) {
             if (p < a.n) w[p] = make_double2(wr[e].x * inv, wr[e].y * inv);
         }
     }
+}
+
+// ---------------------------------------------------------------------------
+// The same process with the basis streamed through shared memory: CTA b owns the
+// contiguous elements [b*L, b*L + L); v_{k+1} is fetched by one bulk (TMA) copy
+// while the grid reduces h_k, so no memory latency follows a barrier.  Buffer
+// k & 1 holds v_k; the pass of step k reads v_{k-1} (update) and v_k (dot), after
+// which v_{k+1} is copied into the buffer v_{k-1} occupied.
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mb_init(unsigned long long* b) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(b)) : "memory");
+}
+__device__ __forceinline__ bool mb_try(unsigned long long* b, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool mb_wait(unsigned long long* b, unsigned parity) {
+    if (mb_try(b, parity)) return true;
+    const long long t0 = clock64();
+    while (!mb_try(b, parity))
+        if (clock64() - t0 > BAR_LIMIT) return false;
+    return true;
+}
+// one thread: copy `bytes` (a multiple of 16, both addresses 16-byte aligned) into shared memory
+__device__ __forceinline__ void bulk_fetch(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+template <int EPT>
+__global__ void __launch_bounds__(MT) mgs_smem_kernel(MgsArgs a, int L) {
+    extern __shared__ __align__(16) double2 vbuf[];           // [2][L]
+    __shared__ double2 sh[1 + MT / 32];
+    __shared__ __align__(8) unsigned long long full[2];
+    __shared__ int sflag;
+    const long long c0 = (long long)blockIdx.x * L;
+    const int len = (int)max(0LL, min((long long)L, a.n - c0));   // elements of this CTA
+    if (threadIdx.x == 0) {
+        sflag = 0;
+        mb_init(&full[0]);
+        mb_init(&full[1]);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+    unsigned fills[2] = {0u, 0u};                             // completed fills per buffer (for the parity)
+    unsigned s = 0;
+    auto reduce = [&](double2 v, double2& out) -> bool {
+        double2* part = a.partial + (s & 1u) * gridDim.x;
+        block_partial(v, part, sh);
+        if (!grid_barrier(a.bar, a.err, &sflag)) return false;
+        out = sum_partials(part, sh);
+        ++s;
+        return true;
+    };
+    auto fetch = [&](const double2* v, int b) {
+        if (threadIdx.x == 0 && len > 0) bulk_fetch(vbuf + (size_t)b * L, v + c0, (unsigned)len * 16u, &full[b]);
+    };
+    auto wait_buf = [&](int b) -> bool {
+        if (len == 0) return true;
+        const bool ok = mb_wait(&full[b], fills[b] & 1u);
+        ++fills[b];
+        if (!ok) {
+            if (threadIdx.x == 0) atomicExch(a.err, (int)HELM_ERR_TIMEOUT);
+            return false;
+        }
+        return true;
+    };
+    for (int r = 0; r < a.nrhs; ++r) {
+        if (a.active && !a.active[r]) continue;
+        double2* w = a.w + r * a.vsr;
+        double2 wr[EPT];
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) {
+            const int i = e * MT + threadIdx.x;
+            wr[e] = i < len ? w[c0 + i] : make_double2(0.0, 0.0);
+        }
+        const double2* V = a.V + r * a.vsr;
+        __syncthreads();                                       // the buffers are free
+        fetch(V, 0);
+        double2 mh = make_double2(0.0, 0.0);
+        for (int k = 0; k < a.nvec; ++k) {
+            const int b = k & 1;
+            if (!wait_buf(b)) return;                          // every thread times out the same way
+            const double2* vk = vbuf + (size_t)b * L;
+            const double2* vp = vbuf + (size_t)(b ^ 1) * L;
+            double2 acc[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[q] = make_double2(0.0, 0.0);
+#pragma unroll
+            for (int e = 0; e < EPT; ++e) {
+                const int i = e * MT + threadIdx.x;
+                if (i < len) {
+                    if (k > 0) wr[e] = cfma(mh, vp[i], wr[e]);
+                    acc[e & 3] = cfmaconj(vk[i], wr[e], acc[e & 3]);
+                }
+            }
+            const double2 accs = make_double2((acc[0].x + acc[1].x) + (acc[2].x + acc[3].x),
+                                              (acc[0].y + acc[1].y) + (acc[2].y + acc[3].y));
+            __syncthreads();                                   // v_{k-1} is no longer read
+            if (k + 1 < a.nvec) fetch(V + (long long)(k + 1) * a.vsk, b ^ 1);
+            double2 h;
+            if (!reduce(accs, h)) {
+                if (k + 1 < a.nvec) wait_buf(b ^ 1);          // no copy outlives the CTA
+                return;
+            }
+            if (blockIdx.x == 0 && threadIdx.x == 0) a.hcol[(long long)r * a.ldh + k] = h;
+            mh = make_double2(-h.x, -h.y);
+        }
+        const double2* vl = vbuf + (size_t)((a.nvec - 1) & 1) * L;
+        double nrm0 = 0.0, nrm1 = 0.0;
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) {
+            const int i = e * MT + threadIdx.x;
+            if (i < len) {
+                if (a.nvec > 0) wr[e] = cfma(mh, vl[i], wr[e]);
+                if (e & 1) nrm1 = fma(wr[e].x, wr[e].x, fma(wr[e].y, wr[e].y, nrm1));
+                else nrm0 = fma(wr[e].x, wr[e].x, fma(wr[e].y, wr[e].y, nrm0));
+            }
+        }
+        double2 tot;
+        if (!reduce(make_double2(nrm0 + nrm1, 0.0), tot)) return;
+        const double hn = sqrt(tot.x);
+        if (blockIdx.x == 0 && threadIdx.x == 0) a.hnorm[r] = hn;
+        const double inv = hn > 0.0 ? 1.0 / hn : 0.0;
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) {
+            const int i = e * MT + threadIdx.x;
+            if (i < len) w[c0 + i] = make_double2(wr[e].x * inv, wr[e].y * inv);
+        }
+    }
+}
+
+template <int EPT>
+cudaError_t launch_smem_ept(MgsArgs& a, int grid, int L, cudaStream_t st) {
+    const size_t smem = 2 * (size_t)L * sizeof(double2);
+    cudaError_t e = cudaFuncSetAttribute(mgs_smem_kernel<EPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    void* args[] = {&a, &L};
+    count_launch();
+    return cudaLaunchCooperativeKernel((const void*)mgs_smem_kernel<EPT>, dim3(grid), dim3(MT), args, smem, st);
 }
 
 template <int EPT>
@@ -196,6 +353,20 @@ cudaError_t launch_mgs(const double2* V, long long vsk, long long vsr, double2* 
                        const int* active, double2* hcol, int ldh, double* hnorm, double2* partial, unsigned* bar,
                        int* err, int grid, cudaStream_t st) {
     MgsArgs a{V, vsk, vsr, w, nvec, n, nrhs, active, hcol, ldh, hnorm, partial, bar, err};
+    {
+        // basis streamed through shared memory when two slices of every CTA fit; the
+        // slice start must stay 16-byte aligned (double2 elements: always)
+        const long long L = (n + grid - 1) / grid;
+        const long long smem = 2 * L * (long long)sizeof(double2);
+        const bool aligned = ((reinterpret_cast<uintptr_t>(V) | reinterpret_cast<uintptr_t>(w)) & 15) == 0 &&
+                             ((vsk | vsr) * (long long)sizeof(double2)) % 16 == 0;
+        if (aligned && smem <= 220 * 1024 && grid * L >= n) {
+            const long long per = (L + MT - 1) / MT;
+            if (per <= 8) return launch_smem_ept<8>(a, grid, (int)L, st);
+            if (per <= 16) return launch_smem_ept<16>(a, grid, (int)L, st);
+            if (per <= 28) return launch_smem_ept<28>(a, grid, (int)L, st);
+        }
+    }
     const long long per = (n + (long long)grid * MT - 1) / ((long long)grid * MT);
     if (per <= 4) return launch_ept<4>(a, grid, st);
     if (per <= 8) return launch_ept<8>(a, grid, st);

@@ -25,14 +25,19 @@
 // core matrices adjacent along K, the stride byte offset that of core matrices
 // adjacent along M (A) or N (B).
 //
-// Roles.  Warps 0 .. 4MT-1: epilogue, thread i owns output node i of the
-// current grid row (TMEM lane i % 128 of tile i / 128); warp 4MT: producer (one
-// thread issues the bulk copies into a ring of chunk slots); warp 4MT+1: one
-// thread issues the MMAs and commits them to mbarriers.  Per step the epilogue
-// waits for the accumulator, forms the next operand (b_{r+1} + y_r, or
-// y_r + X_r u_{r+1} on the way back) and signals the MMA thread.  All waits are
-// bounded: on expiry the kernel records HELM_ERR_TIMEOUT, stops issuing work,
-// waits (bounded) for its own copies and MMAs and frees its tensor memory.
+// Roles.  Warps 0..15: epilogue; warp w owns the 32 nodes 32 (w mod 4MT) + lane
+// of the current grid row (the TMEM lanes of its quarter, tile (w mod 4MT) / 4)
+// and one of 4/MT groups of the right-hand sides.  Warp 16: producer (one thread
+// issues the bulk copies into a ring of chunk slots); warp 17: one thread issues
+// the MMAs and commits them to mbarriers.  Per step the epilogue waits for the
+// accumulator, forms the next operand (b_{r+1} + y_r, or y_r + X_r u_{r+1} on the
+// way back) and signals the MMA thread; its global operands (y_r, the source,
+// the interface data) are loaded one chunk of 4 RHS ahead, the first chunk while
+// the MMAs run.  The interface data G/(1-beta) of all boundary nodes are gathered
+// once per launch into a scratch array, and the outgoing data are formed after
+// the sweep from the boundary values kept in a second one, by all threads.  All
+// waits are bounded: on expiry the kernel records HELM_ERR_TIMEOUT, stops issuing
+// work, waits (bounded) for its own copies and MMAs and frees its tensor memory.
 #include "helm_internal.cuh"
 
 namespace {
@@ -40,6 +45,7 @@ namespace {
 constexpr long long TC_WAIT_LIMIT = 2000000000LL;  // cycles (~1 s)
 constexpr int TC_MAXSLOTS = 8;
 constexpr int TC_CHUNK_BYTES = 32768;              // one K-chunk: real plane + imaginary plane
+constexpr int TC_EPI_WARPS = 16;                   // epilogue warps (4 MT per node set x RHS groups)
 
 __device__ __forceinline__ unsigned sm_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -108,6 +114,26 @@ __device__ __forceinline__ void tmem_ld8(unsigned addr, float* v) {
 #pragma unroll
     for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
 }
+// 4 consecutive 32-bit columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld4(unsigned addr, float* v) {
+    unsigned r[4];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(addr));
+#pragma unroll
+    for (int j = 0; j < 4; ++j) v[j] = __uint_as_float(r[j]);
+}
+// binary32 -> binary64 widening of a normal number by its bit fields (sign, exponent
+// rebiased by 1023 - 127, mantissa shifted by 52 - 23): integer instructions instead of
+// a conversion on the FP64 pipe; zero, subnormals, infinities and NaN take the conversion
+__device__ __forceinline__ double widen(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = (u >> 23) & 0xFFu;
+    if (e == 0u || e == 0xFFu) return (double)f;
+    const unsigned long long d = ((unsigned long long)(u & 0x80000000u) << 32) |
+                                 ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29);
+    return __longlong_as_double((long long)d);
+}
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
 __device__ __forceinline__ float tf32_round(float x) {
     unsigned r;
@@ -129,10 +155,12 @@ __device__ __forceinline__ void st_shared_v4(unsigned addr, float a, float b, fl
 // Rows i >= mx and columns j >= mx are zero; values are rounded to TF32.
 __host__ __device__ inline int tc_kc(int MT, int split) { return (split == 3 ? 16 : 32) / MT; }
 
-__global__ void tc_layout_kernel(const SubDev* subtab, int nsub, int MT, int split, const float2* X, float* XT) {
+__global__ void tc_layout_kernel(const SubDev* subtab, int nsub, int split, const float2* X, float* XT) {
     const int s = blockIdx.y;
     if (s >= nsub) return;
     const SubDev sd = subtab[s];
+    const int MT = sd.tcmt;
+    if (MT < 1 || MT > 2) return;
     const int KC = tc_kc(MT, split);
     const int nch = (sd.mx + KC - 1) / KC;
     const long long per_step = (long long)nch * (TC_CHUNK_BYTES / 4);
@@ -168,15 +196,21 @@ namespace {
 
 // ------------------------------------------------------------- stage kernel
 template <int MT, int NR, bool BASIS, int SPLIT>
-__global__ void __launch_bounds__(32 * (4 * MT + 2), 1)
+__global__ void __launch_bounds__(32 * (TC_EPI_WARPS + 2), 1)
     tc_stage_kernel(StageArgs<float> a, const float* __restrict__ XT, int nslots) {
     using T = float2;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ __align__(8) unsigned long long full_bar[TC_MAXSLOTS], empty_bar[TC_MAXSLOTS], b_bar, d_bar, fin_bar;
     __shared__ unsigned tmem_base;
     __shared__ int abort_flag;
+    __shared__ float zsc_s[NR];                             // per-RHS output scales
 
-    constexpr int NEPI = 128 * MT;                          // epilogue threads = output nodes
+    constexpr int NEPI = 32 * TC_EPI_WARPS;                 // epilogue threads
+    constexpr int NW = 4 * MT;                              // warps per set of 128*MT nodes
+    constexpr int RG = TC_EPI_WARPS / NW;                   // RHS groups: each epilogue warp takes NR/RG RHS
+    constexpr int RPT = NR / RG;                            // RHS per epilogue thread
+    static_assert(RPT % 4 == 0, "RHS per epilogue thread must be a multiple of 4");
+    constexpr int CH = RPT >= 8 ? 8 : 4;                    // RHS per chunk of the epilogue
     constexpr int KC = (SPLIT == 3 ? 16 : 32) / MT;         // K columns per chunk
     constexpr unsigned PLANE = 128u * MT * KC * 4u;         // bytes of one plane of a chunk
     constexpr unsigned BLO = 32u * MT * (48u * NR + 64u);  // offset of the lo operand (SPLIT = 3)
@@ -188,7 +222,7 @@ __global__ void __launch_bounds__(32 * (4 * MT + 2), 1)
     constexpr unsigned KSTRIDE_A = 2048u * MT;              // K-adjacent core matrices of A
     constexpr unsigned IDESC = tf32_idesc(2 * NR);
 
-    const int s = BASIS ? blockIdx.x : a.subs[blockIdx.x];
+    const int s = a.subs[blockIdx.x];
     const SubDev sd = a.subtab[s];
     const int mx = sd.mx, my = sd.my;
     const int rhs0 = blockIdx.y * NR;
@@ -199,6 +233,8 @@ __global__ void __launch_bounds__(32 * (4 * MT + 2), 1)
     const int nch = (mx + KC - 1) / KC;
     const int nsteps = 2 * my - 1;
     const long long N = (long long)a.nx * a.ny;
+    const int L = 2 * (mx + my);                            // boundary slots W[my] E[my] S[mx] N[mx]
+    const bool has_gin = !BASIS && (a.gin0 || a.gin1);
 
     unsigned char* ring = smem_raw;
     unsigned char* bop = smem_raw + (size_t)nslots * TC_CHUNK_BYTES;   // [-Bi | Br | Bi] (hi, then lo)
@@ -215,11 +251,56 @@ __global__ void __launch_bounds__(32 * (4 * MT + 2), 1)
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
+    for (int k = tid; k < NR; k += blockDim.x) zsc_s[k] = (!BASIS && a.zscale && k < nr) ? (float)a.zscale[rhs0 + k] : 1.f;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(sm_addr(&tmem_base)),
                      "r"(TCOLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+
+    // the four sides with compile-time indices (no local-memory arrays)
+    const int tinW = sd.tin[SW], tinE = sd.tin[SE], tinS = sd.tin[SS], tinN = sd.tin[SN];
+    const int boW = sd.bo[SW], boE = sd.bo[SE], boS = sd.bo[SS], boN = sd.bo[SN];
+    auto gin = [&](int k, long long idx) -> T {
+        T g = a.gin0 ? a.gin0[(long long)(rhs0 + k) * a.ntrace + idx] : czero<T>();
+        if (a.gin1) g = cadd(g, a.gin1[(long long)(rhs0 + k) * a.ntrace + idx]);
+        return g;
+    };
+    // interface part of the right-hand side at boundary node (r, cc) for RHS k: the
+    // incoming data G/(1-beta) of every side through the node, or the unit datum (basis)
+    auto bside = [&](int tin, int bo, int pt, int k, T b) -> T {
+        if (BASIS) {
+            if (bo >= 0 && bo + pt == e0 + k) b = cadd(b, mk(1.f, 0.f));
+        } else if (tin >= 0 && has_gin) {
+            const long long ti = tin + pt;
+            b = cadd(b, cmul(gin(k, ti), a.tc[ti].cin));
+        }
+        return b;
+    };
+    auto bnode = [&](int r, int cc, int k) -> T {
+        T b = czero<T>();
+        if (cc == 0) b = bside(tinW, boW, r, k, b);
+        if (cc == mx - 1) b = bside(tinE, boE, r, k, b);
+        if (r == 0) b = bside(tinS, boS, cc, k, b);
+        if (r == my - 1) b = bside(tinN, boN, cc, k, b);
+        return b;
+    };
+    // the one boundary slot that carries node (r, cc)'s interface data (its W or E entry
+    // on the edge columns, else its S or N entry), -1 for interior nodes
+    auto node_slot = [&](int r, int cc) -> int {
+        return cc == 0 ? r : cc == mx - 1 ? my + r : r == 0 ? 2 * my + cc : r == my - 1 ? 2 * my + mx + cc : -1;
+    };
+    T* escr = has_gin ? a.escr + (long long)rhs0 * a.estride + sd.eoff : nullptr;   // [k * estride + slot]
+    if (has_gin) {
+        // incoming data of every boundary node and RHS, once per launch (all threads, loads in parallel)
+        for (int idx = tid; idx < nr * L; idx += blockDim.x) {
+            const int k = idx / L, e = idx - k * L;
+            const int r = e < my ? e : e < 2 * my ? e - my : e < 2 * my + mx ? 0 : my - 1;
+            const int cc = e < my ? 0 : e < 2 * my ? mx - 1 : e < 2 * my + mx ? e - 2 * my : e - 2 * my - mx;
+            if (node_slot(r, cc) != e) continue;            // a corner's S/N entry, or E when mx = 1
+            escr[(long long)k * a.estride + e] = bnode(r, cc, k);
+        }
     }
     tc_fence_before();
     __syncthreads();
@@ -232,74 +313,33 @@ __global__ void __launch_bounds__(32 * (4 * MT + 2), 1)
     };
     auto aborted = [&]() { return *((volatile int*)&abort_flag) != 0; };
 
-    if (warp < 4 * MT) {
+    if (warp < TC_EPI_WARPS) {
         // ------------------------------------------------------------ epilogue
-        const int c = tid;                                  // node of the grid row
-        const int tile = warp >> 2;
+        // warp w: nodes 32 (w % NW) + lane (TMEM lanes of its quarter), RHS [kb, kb + RPT)
+        const int nw = warp % NW;
+        const int c = 32 * nw + lane;
+        const int tile = nw >> 2;
+        const int kb = (warp / NW) * RPT;
         const unsigned dcol = tmem + ((unsigned)(32 * (warp & 3)) << 16) + (unsigned)(tile * 2 * NR);
         const bool live = c < mx;
         const unsigned bgrp = bop_s + (unsigned)(c >> 2) * KSTRIDE_B;      // K core matrix of nodes 4(c/4) ..
         T* yw = a.yws + sd.yoff;
-        auto gin = [&](int k, long long idx) -> T {
-            T g = a.gin0 ? a.gin0[(long long)(rhs0 + k) * a.ntrace + idx] : czero<T>();
-            if (a.gin1) g = cadd(g, a.gin1[(long long)(rhs0 + k) * a.ntrace + idx]);
-            return g;
-        };
-        // boundary sides through node (r, c), and the point index along each
-        auto sides = [&](int r, int* sl, int* pl) {
-            int n = 0;
-            if (c == 0) { sl[n] = SW; pl[n++] = r; }
-            if (c == mx - 1) { sl[n] = SE; pl[n++] = r; }
-            if (r == 0) { sl[n] = SS; pl[n++] = c; }
-            if (r == my - 1) { sl[n] = SN; pl[n++] = c; }
-            return n;
-        };
-        // right-hand side of grid row r at this node for RHS k: incoming data and source
-        auto bterm = [&](int r, int k) -> T {
-            T b = czero<T>();
-            if (!live || k >= nr) return b;
-            int sl[4], pl[4];
-            const int ns = (c == 0 || c == mx - 1 || r == 0 || r == my - 1) ? sides(r, sl, pl) : 0;
-            for (int q = 0; q < ns; ++q) {
+        T* uscr = (!BASIS && a.mask) ? a.uscr + (long long)rhs0 * a.estride + sd.eoff : nullptr;
+        const bool edge_col = c == 0 || c == mx - 1;
+        // u is the solution at boundary node (r, c) for RHS k: K entries (basis) or the
+        // value kept for the outgoing data of every interface side through the node
+        auto finish_edge = [&](int r, int k, T u) {
+            auto one = [&](int tin, int bo, int e, int pt) {
                 if (BASIS) {
-                    if (sd.bo[sl[q]] >= 0 && sd.bo[sl[q]] + pl[q] == e0 + k) b = cadd(b, mk(1.f, 0.f));
-                } else if (sd.tin[sl[q]] >= 0 && (a.gin0 || a.gin1)) {
-                    const long long ti = sd.tin[sl[q]] + pl[q];
-                    b = cadd(b, cmul(gin(k, ti), a.tc[ti].cin));
+                    if (bo >= 0) a.K[sd.koff + (long long)(e0 + k) * sd.Lb + bo + pt] = u;
+                } else if (uscr && tin >= 0) {
+                    uscr[(long long)k * a.estride + e] = u;
                 }
-            }
-            if (!BASIS && a.src) {
-                const double2 rv = a.r[(long long)(rhs0 + k) * N + (long long)(sd.y0 + r) * a.nx + sd.x0 + c];
-                const double sc = a.rscale ? a.rscale[rhs0 + k] : 1.0;
-                b = cadd(b, mk((float)(rv.x * sc), (float)(rv.y * sc)));
-            }
-            return b;
-        };
-        // u is the solution at node (r, c) for RHS k
-        auto finish = [&](int r, int k, T u) {
-            if (!BASIS && a.z) {
-                const double sc = a.zscale ? a.zscale[rhs0 + k] : 1.0;
-                a.z[(long long)(rhs0 + k) * N + (long long)(sd.y0 + r) * a.nx + sd.x0 + c] =
-                    make_double2((double)u.x * sc, (double)u.y * sc);
-            }
-            if (!(c == 0 || c == mx - 1 || r == 0 || r == my - 1)) return;
-            int sl[4], pl[4];
-            const int ns = sides(r, sl, pl);
-            for (int q = 0; q < ns; ++q) {
-                const int side = sl[q];
-                if (BASIS) {
-                    if (sd.bo[side] >= 0) a.K[sd.koff + (long long)(e0 + k) * sd.Lb + sd.bo[side] + pl[q]] = u;
-                } else if ((a.mask & (1 << side)) && sd.tin[side] >= 0) {
-                    const long long in = sd.tin[side] + pl[q], out = sd.tout[side] + pl[q];
-                    const TraceCoef<T> cf = a.tc[in];
-                    T g = cfma(cf.cb, u, cmul(cf.ca, gin(k, in)));
-                    const long long o = (long long)(rhs0 + k) * a.ntrace + out;
-                    if (a.base) g = cadd(g, a.base[o]);
-                    if (a.sub) g = csub(g, a.sub[o]);
-                    a.dst[o] = g;
-                    if (a.dst2) a.dst2[o] = g;
-                }
-            }
+            };
+            if (c == 0) one(tinW, boW, r, r);
+            if (c == mx - 1) one(tinE, boE, my + r, r);
+            if (r == 0) one(tinS, boS, 2 * my + c, c);
+            if (r == my - 1) one(tinN, boN, 2 * my + mx + c, c);
         };
         // write the operand entries of RHS k0 .. k0+3 (v[j] = value of RHS k0 + j at this
         // node): a 4 x 4 transpose within each group of four lanes leaves lane j of the
@@ -337,54 +377,114 @@ __global__ void __launch_bounds__(32 * (4 * MT + 2), 1)
             }
         };
         // operand of step 0: b_1
-        for (int k0 = 0; k0 < NR; k0 += 4) {
+        for (int k0 = kb; k0 < kb + RPT; k0 += 4) {
             T v[4];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) v[j] = bterm(0, k0 + j);
+            for (int j = 0; j < 4; ++j) {
+                const int k = k0 + j;
+                T b = czero<T>();
+                if (live && k < nr) {
+                    const int sl = node_slot(0, c);
+                    if (sl >= 0) b = has_gin ? escr[(long long)k * a.estride + sl] : bnode(0, c, k);
+                    if (!BASIS && a.src) b = cadd(b, a.r64[(long long)(rhs0 + k) * N + (long long)sd.y0 * a.nx + sd.x0 + c]);
+                }
+                v[j] = b;
+            }
             put4(k0, v);
         }
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         tc_fence_before();
         bar_arrive(&b_bar);
+        const long long ws = a.wstride;
         for (int step = 0; step < nsteps; ++step) {
             const bool fwd = step < my;
             const int r = fwd ? step : 2 * my - 2 - step;
+            // what this step does at this node, decided once per step:
+            //   mid (forward, r < my-1): store y_r, next operand b_{r+1} + y_r
+            //   otherwise the solution of row r is final: u = y_my (r = my-1) or y_r + X_r u_{r+1}
+            const bool mid = fwd && r < my - 1;
+            const bool ok = live && !aborted();
+            T* yrow = yw + (long long)rhs0 * ws + (long long)r * mx + c;          // y_r of RHS rhs0
+            const T* srow = (!BASIS && a.src && mid && ok)
+                                ? a.r64 + (long long)rhs0 * N + (long long)(sd.y0 + r + 1) * a.nx + sd.x0 + c
+                                : nullptr;
+            double2* zrow = (!BASIS && a.z && !mid && ok)
+                                ? a.z + (long long)rhs0 * N + (long long)(sd.y0 + r) * a.nx + sd.x0 + c
+                                : nullptr;
+            const int nslot = mid ? node_slot(r + 1, c) : -1;                     // interface data in row r+1
+            const T* erow = (has_gin && ok && nslot >= 0) ? escr + nslot : nullptr;
+            const bool bunit = BASIS && mid && nslot >= 0;
+            const bool fedge = !mid && (edge_col || r == 0 || r == my - 1);
+            const bool loady = !fwd && ok;
+            // global operands of one chunk of CH RHS, loaded a chunk ahead (the first one
+            // before the accumulator wait, under the MMAs): pv = y_r on the way back or the
+            // source of row r+1 on the way forward, ev = the interface data of row r+1
+            auto prefetch = [&](int k0, T* pv, T* ev) {
+#pragma unroll
+                for (int j = 0; j < CH; ++j) {
+                    const int k = k0 + j;
+                    pv[j] = czero<T>();
+                    ev[j] = czero<T>();
+                    if (k < nr) {
+                        if (loady) pv[j] = yrow[(long long)k * ws];
+                        else if (srow) pv[j] = srow[(long long)k * N];
+                        if (erow) ev[j] = erow[(long long)k * a.estride];
+                    }
+                }
+            };
+            T pv[CH], ev[CH];
+            prefetch(kb, pv, ev);
             if (!bar_wait(&d_bar, (unsigned)(step & 1), aborted() ? 0 : TC_WAIT_LIMIT)) fail();
             tc_fence_after();
             const bool last = step == nsteps - 1;
-            const bool ok = !aborted();
-            for (int k0 = 0; k0 < NR; k0 += 8) {
-                float dr[8], di[8];
-                tmem_ld8(dcol + (unsigned)k0, dr);
-                tmem_ld8(dcol + (unsigned)(NR + k0), di);
+#pragma unroll 1
+            for (int k0 = kb; k0 < kb + RPT; k0 += CH) {
+                T pn[CH], en[CH];
+                if (k0 + CH < kb + RPT) prefetch(k0 + CH, pn, en);
+                float dr[CH], di[CH];
+                if (CH == 8) {
+                    tmem_ld8(dcol + (unsigned)k0, dr);
+                    tmem_ld8(dcol + (unsigned)(NR + k0), di);
+                } else {
+                    tmem_ld4(dcol + (unsigned)k0, dr);
+                    tmem_ld4(dcol + (unsigned)(NR + k0), di);
+                }
                 tmem_wait_ld();
-                T nv[8];
+                T nv[CH];
+                if (ok) {
+                    T* yk = yrow + (long long)k0 * ws;
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const int k = k0 + j;
-                    const T sum = mk(dr[j], di[j]);
-                    T v = czero<T>();
-                    if (ok && live && k < nr) {
-                        T* ywk = yw + (long long)(rhs0 + k) * a.wstride;
-                        if (fwd) {
-                            if (r < my - 1) {
-                                ywk[(long long)r * mx + c] = sum;                 // y_r
-                                v = cadd(bterm(r + 1, k), sum);                   // b_{r+1} + y_r
+                    for (int j = 0; j < CH; ++j, yk += ws) {
+                        const int k = k0 + j;
+                        const T sum = mk(dr[j], di[j]);
+                        T v = czero<T>();
+                        if (k < nr) {
+                            if (mid) {
+                                *yk = sum;                                        // y_r
+                                v = cadd(sum, pv[j]);                             // + source of row r+1
+                                if (erow) v = cadd(v, ev[j]);                     // + interface data
+                                if (bunit) v = cadd(v, bnode(r + 1, c, k));       // + unit datum (basis)
                             } else {
-                                finish(r, k, sum);                                // u_my = y_my
-                                v = sum;
+                                v = fwd ? sum : cadd(pv[j], sum);                 // u_my = y_my, u_r = y_r + X_r u_{r+1}
+                                if (zrow) {
+                                    const float sc = zsc_s[k];
+                                    zrow[(long long)k * N] = make_double2(widen(v.x * sc), widen(v.y * sc));
+                                }
+                                if (fedge) finish_edge(r, k, v);
                             }
-                        } else {
-                            v = cadd(ywk[(long long)r * mx + c], sum);            // u_r = y_r + X_r u_{r+1}
-                            finish(r, k, v);
                         }
+                        nv[j] = v;
                     }
-                    nv[j] = v;
+                } else {
+#pragma unroll
+                    for (int j = 0; j < CH; ++j) nv[j] = czero<T>();
                 }
                 if (!last) {
-                    put4(k0, nv);
-                    put4(k0 + 4, nv + 4);
+#pragma unroll
+                    for (int j = 0; j < CH; j += 4) put4(k0 + j, nv + j);
                 }
+#pragma unroll
+                for (int j = 0; j < CH; ++j) { pv[j] = pn[j]; ev[j] = en[j]; }
             }
             if (!last) {
                 asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
@@ -392,7 +492,7 @@ __global__ void __launch_bounds__(32 * (4 * MT + 2), 1)
                 bar_arrive(&b_bar);
             }
         }
-    } else if (warp == 4 * MT) {
+    } else if (warp == TC_EPI_WARPS) {
         // ------------------------------------------------------------ producer
         if (lane == 0) {
             const float* Xs = XT + sd.xtoff;
@@ -483,6 +583,28 @@ __global__ void __launch_bounds__(32 * (4 * MT + 2), 1)
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TCOLS) : "memory");
     }
+    // outgoing data G_out = ca G_in + cb u_p toward the masked sides, all threads at once
+    // (the boundary values u_p were kept during the sweep)
+    if (!BASIS && a.mask && !abort_flag) {
+        const T* uscr = a.uscr + (long long)rhs0 * a.estride + sd.eoff;
+        const int toutW = sd.tout[SW], toutE = sd.tout[SE], toutS = sd.tout[SS], toutN = sd.tout[SN];
+        for (int idx = tid; idx < nr * L; idx += blockDim.x) {
+            const int k = idx / L, e = idx - k * L;
+            const int side = e < my ? SW : e < 2 * my ? SE : e < 2 * my + mx ? SS : SN;
+            const int pt = e < my ? e : e < 2 * my ? e - my : e < 2 * my + mx ? e - 2 * my : e - 2 * my - mx;
+            const int tin = side == SW ? tinW : side == SE ? tinE : side == SS ? tinS : tinN;
+            const int tout = side == SW ? toutW : side == SE ? toutE : side == SS ? toutS : toutN;
+            if (!(a.mask & (1 << side)) || tin < 0) continue;
+            const long long in = tin + pt, out = tout + pt;
+            const TraceCoef<T> cf = a.tc[in];
+            T g = cfma(cf.cb, uscr[(long long)k * a.estride + e], cmul(cf.ca, gin(k, in)));
+            const long long o = (long long)(rhs0 + k) * a.ntrace + out;
+            if (a.base) g = cadd(g, a.base[o]);
+            if (a.sub) g = csub(g, a.sub[o]);
+            a.dst[o] = g;
+            if (a.dst2) a.dst2[o] = g;
+        }
+    }
 }
 
 template <int MT, int NR, int SPLIT>
@@ -492,7 +614,11 @@ size_t tc_smem(int nslots) {
 
 template <int MT, int NR, bool BASIS, int SPLIT>
 cudaError_t tc_launch(const StageArgs<float>& a, const float* XT, int nunits, int ny_blocks, cudaStream_t st) {
-    const size_t budget = 227 * 1024 - 1024;
+    // dynamic shared memory: at most 227 KB per block less the kernel's static shared memory
+    cudaFuncAttributes fa{};
+    cudaError_t e0 = cudaFuncGetAttributes(&fa, tc_stage_kernel<MT, NR, BASIS, SPLIT>);
+    if (e0 != cudaSuccess) return e0;
+    const size_t budget = 227 * 1024 - fa.sharedSizeBytes - 256;
     int nslots = TC_MAXSLOTS;
     while (nslots > 2 && tc_smem<MT, NR, SPLIT>(nslots) > budget) --nslots;
     if (tc_smem<MT, NR, SPLIT>(nslots) > budget) return cudaErrorInvalidValue;
@@ -501,24 +627,23 @@ cudaError_t tc_launch(const StageArgs<float>& a, const float* XT, int nunits, in
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     count_launch();
-    tc_stage_kernel<MT, NR, BASIS, SPLIT><<<dim3(nunits, ny_blocks), 32 * (4 * MT + 2), smem, st>>>(a, XT, nslots);
+    tc_stage_kernel<MT, NR, BASIS, SPLIT><<<dim3(nunits, ny_blocks), 32 * (TC_EPI_WARPS + 2), smem, st>>>(a, XT, nslots);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-int tc_tiles(int max_mx) { return max_mx <= 128 ? 1 : max_mx <= 256 ? 2 : 0; }
+int tc_tiles(int mx) { return mx <= 128 ? 1 : mx <= 256 ? 2 : 0; }
 
 long long tc_layout_floats(int mx, int my, int MT, int split) {
     const int KC = tc_kc(MT, split);
     return (long long)my * ((mx + KC - 1) / KC) * (TC_CHUNK_BYTES / 4);
 }
 
-cudaError_t launch_tc_layout(const SubDev* subtab, int nsub, int MT, int split, const float2* X, float* XT,
-                             cudaStream_t st) {
+cudaError_t launch_tc_layout(const SubDev* subtab, int nsub, int split, const float2* X, float* XT, cudaStream_t st) {
     if (nsub == 0) return cudaSuccess;
     count_launch();
-    tc_layout_kernel<<<dim3(64, nsub), 256, 0, st>>>(subtab, nsub, MT, split, X, XT);
+    tc_layout_kernel<<<dim3(64, nsub), 256, 0, st>>>(subtab, nsub, split, X, XT);
     return cudaGetLastError();
 }
 
@@ -549,6 +674,7 @@ cudaError_t launch_tc_stage(const StageArgs<float>& a, const float* XT, int MT, 
 
 cudaError_t launch_tc_basis(const StageArgs<float>& a, const float* XT, int MT, int split, int nsub, int ncols,
                             cudaStream_t st) {
+    if (nsub == 0) return cudaSuccess;
     if (split == 3) {
         if (MT == 1) return tc_launch<1, 32, true, 3>(a, XT, nsub, (ncols + 31) / 32, st);
         if (MT == 2) return tc_launch<2, 16, true, 3>(a, XT, nsub, (ncols + 15) / 16, st);

@@ -38,7 +38,8 @@ class HelmOpts(ctypes.Structure):
 
 class HelmSetupOpts(ctypes.Structure):
     _fields_ = [("transmission", ctypes.c_int), ("tc_scale", ctypes.c_double),
-                ("boundary_operators", ctypes.c_int), ("tensor_cores", ctypes.c_int)]
+                ("boundary_operators", ctypes.c_int), ("tensor_cores", ctypes.c_int),
+                ("tc_min_rhs", ctypes.c_int)]
 
 
 class HelmInfo(ctypes.Structure):
@@ -137,13 +138,15 @@ class Problem:
     """
 
     def __init__(self, n_x, n_y, h, omega, m2, N1, N2, xcuts=None, ycuts=None,
-                 transmission="optimized", tc_scale=1.0, boundary_operators=True, tensor_cores=True):
+                 transmission="optimized", tc_scale=1.0, boundary_operators=True, tensor_cores=True,
+                 tc_min_rhs=16):
         L = lib()
         if not (m2.is_cuda and m2.dtype == torch.float64 and m2.numel() == n_x * n_y):
             raise TypeError("m2 must be a float64 CUDA tensor with n_x*n_y values")
         m2 = m2.contiguous()
         tcm = {False: 0, True: 1, "3xtf32": 1, "tf32": 2}[tensor_cores]
-        so = HelmSetupOpts(TRANSMISSION[transmission], float(tc_scale), int(bool(boundary_operators)), tcm)
+        so = HelmSetupOpts(TRANSMISSION[transmission], float(tc_scale), int(bool(boundary_operators)), tcm,
+                           int(tc_min_rhs))
         xc = (ctypes.c_int * (N1 + 1))(*[int(v) for v in xcuts]) if xcuts is not None else None
         yc = (ctypes.c_int * (N2 + 1))(*[int(v) for v in ycuts]) if ycuts is not None else None
         h_ = ctypes.c_void_p()
@@ -181,7 +184,7 @@ class Problem:
         return Au
 
     def solve(self, f, u=None, restart=50, maxit=1000, tol=1e-6, sched="BSP", x0=None, history=False,
-              stream=None, raise_on_noconv=True):
+              stream=None, raise_on_noconv=True, use_graph=False):
         """Solve A u = h^2 f (FP64 FGMRES); returns (u, [(iters, relres)], history or None)."""
         f = _as_fields(f, self.N, "f")
         nrhs = f.numel() // self.N
@@ -189,7 +192,8 @@ class Problem:
         if x0 is not None:
             u.copy_(x0)
         hist = (ctypes.c_double * (maxit * nrhs))() if history else None
-        o = default_opts(restart=restart, maxit=maxit, tol=tol, sched=sched, x0_given=int(x0 is not None))
+        o = default_opts(restart=restart, maxit=maxit, tol=tol, sched=sched, x0_given=int(x0 is not None),
+                         use_graph=int(bool(use_graph)))
         if hist is not None:
             o.hist = ctypes.cast(hist, ctypes.POINTER(ctypes.c_double))
         info = (HelmInfo * nrhs)()

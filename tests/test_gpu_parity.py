@@ -193,6 +193,25 @@ def test_gmres_multi_rhs_and_initial_guess(H):
     assert all(it == 0 for it, _ in info2)
 
 
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_graph_replay_gives_the_same_solve(H, prec):
+    """use_graph: the preconditioner replayed from captured CUDA graphs runs the same
+    kernels on the same data, so the iteration counts and residuals are identical."""
+    w = CASES["uneven_4x3"]()
+    p, _ = make(H, w, prec)
+    f = cuda(W.random_complex((2, w.N), 21))
+    u0, i0, _ = p.solve(f, tol=1e-9, restart=30, maxit=400)
+    n0 = H.launch_count()
+    u1, i1, _ = p.solve(f, tol=1e-9, restart=30, maxit=400, use_graph=True)
+    n1 = H.launch_count()
+    u2, i2, _ = p.solve(f, tol=1e-9, restart=30, maxit=400, use_graph=True)      # replays cached graphs
+    assert i0 == i1 == i2
+    assert rel(u1.cpu().numpy(), u0.cpu().numpy()) <= 1e-12
+    assert rel(u2.cpu().numpy(), u0.cpu().numpy()) <= 1e-12
+    assert H.launch_count() - n1 == n1 - n0          # replays count the kernels they run
+    p.close()
+
+
 def test_misfit_gradient_matches_direct_adjoint(H):
     n = 63
     w = W.workload("custom", n=n, N1=2, N2=2, medium="layered", seed=3, nrhs=3)

@@ -1,15 +1,20 @@
 """Tensor-core (TF32) multi-RHS subdomain solves against the oracle.
 
 With complex64 factors and 16 or more right-hand sides, the stage solves and
-the construction of the boundary operators K run as tcgen05 MMAs on TF32
-operands with FP32 accumulation (k_tc.cu).  TF32 keeps 10 explicit mantissa
-bits: unit roundoff u = 2^-11 = 4.9e-4 per rounded operand, against 6e-8 for
-complex64.  The block recursion over the grid rows amplifies the operand
-roundoff of every step, so the preconditioner agrees with the complex128
-oracle to (amplification) x u; the bar is written per test and the measured
-values are printed with -s.  The FGMRES solution does not inherit this error:
-the residual, the Arnoldi basis and the update stay FP64, so a solve to 1e-9
-matches the direct solve to the same 1e-5 as the complex128 path.
+the construction of the boundary operators K run as tcgen05 MMAs with FP32
+accumulation (k_tc.cu).  Tolerances, from the arithmetic:
+* default (3xTF32): every operand is hi + lo, two TF32 numbers, and the three
+  products above roundoff are kept, so each product carries ~2^-21 = 4.8e-7
+  relative error (8x the complex64 unit roundoff 6e-8).  The complex64 CUDA-core
+  path measures 4e-6..1e-5 against the oracle, an amplification of 60..170 by
+  the block recursion over the grid rows, so 3xTF32 should land near
+  170 x 4.8e-7 = 8e-5 (measured up to 1.6e-4: the tensor cores' FP32 accumulation
+  adds its own rounding).  Bar: 2e-3.
+* plain TF32 (tensor_cores="tf32"): u = 2^-11 = 4.9e-4 per operand, expected up
+  to 170 x 4.9e-4 = 8e-2, measured ~1.7e-3.  Bar: 2e-2.
+The FGMRES solution does not inherit this error: the residual, the Arnoldi
+basis and the update stay FP64, so a solve to 1e-9 matches the direct solve to
+the same 1e-5 as the complex128 path.
 
 Cases: 1 and 2 tiles of 128 nodes (subdomains 17..131 nodes wide), ragged
 RHS blocks (40 = 32 + 8, 70 = 64 + 6), both schedules, with and without the
@@ -25,7 +30,8 @@ pytestmark = pytest.mark.gpu
 import workloads as W
 from oracle import Decomposition, Sweeper, assemble_operator
 
-TF32_PRECOND_TOL = 2e-2      # rel. L2 of one preconditioner application vs the oracle
+TF32_PRECOND_TOL = 2e-3      # rel. L2 of one 3xTF32 preconditioner application vs the oracle
+PLAIN_TF32_TOL = 2e-2        # the same with plain TF32 operands
 
 
 @pytest.fixture(scope="module")
@@ -88,6 +94,22 @@ def test_tensor_core_stages_without_boundary_operators(H, sched):
         e = rel(z[k], sw.precondition(r[k], sched))
         print(f"uneven_4x3 {sched} TF32 stages rhs{k}: rel {e:.2e}")
         assert e <= TF32_PRECOND_TOL
+    p.close()
+
+
+@pytest.mark.parametrize("case", ["tiny_2x2", "wide_2x2_131"])
+def test_plain_tf32_mode(H, case):
+    """tensor_cores='tf32': one MMA per product on TF32-rounded operands (64 RHS per CTA
+    for 128-node subdomains)."""
+    w = CASES[case]()
+    p = make(H, w, tensor_cores="tf32")
+    sw = Sweeper(Decomposition(w.n, w.h, w.omega, w.m2, w.xcuts, w.ycuts))
+    r = W.random_complex((70, w.N), 15)
+    z = p.precond_apply(cuda(r), sched="BSP").cpu().numpy()
+    for k in (0, 63, 64, 69):
+        e = rel(z[k], sw.precondition(r[k], "BSP"))
+        print(f"{case} plain TF32 rhs{k}: rel {e:.2e}")
+        assert e <= PLAIN_TF32_TOL
     p.close()
 
 

@@ -168,9 +168,11 @@ def workload(name: str, **over) -> Workload:
         cuts = even_cuts(n, 8, 128)
         c = layered_random_medium(n, 0, h)
         omega = _omega_for_ppw(c.min(), h, 8.0)
-        f = gaussian_source(n, h, (0.3, 0.4), 2 * h)[None, :]
+        nrhs = over.get("nrhs", 1)
+        # one point source, or (nrhs > 1) a line of sources at depth 0.05 as in the batching workload
+        f = gaussian_source(n, h, (0.3, 0.4), 2 * h)[None, :] if nrhs == 1 else _line_sources(n, h, nrhs, 0.05)
         return Workload(name, n, 8, 8, cuts, cuts.copy(), omega, (1.0 / c**2).reshape(-1), f,
-                        description="1023^2, 8x8, layered+random medium 8 ppw, 1 source")
+                        description=f"1023^2, 8x8, layered+random medium 8 ppw, {nrhs} source(s)")
     if name == "batching":
         n = 1535
         h = 1.0 / (n + 1)
