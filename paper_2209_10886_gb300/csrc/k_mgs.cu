@@ -89,7 +89,7 @@ __device__ double2 sum_partials(const double2* partial, double2* sh) {
     return t;
 }
 
-// block sum of a complex value into partial[blockIdx.x]
+// block sum of a complex value into partial[blockIdx.x] (sh holds 1 + blockDim.x / 32 values)
 __device__ void block_partial(double2 v, double2* partial, double2* sh) {
     v = warp_sum2(v);
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -97,7 +97,7 @@ __device__ void block_partial(double2 v, double2* partial, double2* sh) {
     __syncthreads();
     if (threadIdx.x == 0) {
         double2 t = make_double2(0.0, 0.0);
-        for (int i = 0; i < MT / 32; ++i) { t.x += sh[1 + i].x; t.y += sh[1 + i].y; }
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) { t.x += sh[1 + i].x; t.y += sh[1 + i].y; }
         partial[blockIdx.x] = t;
     }
 }
@@ -214,10 +214,10 @@ __device__ __forceinline__ void bulk_fetch(void* dst, const void* src, unsigned 
         : "memory");
 }
 
-template <int EPT>
-__global__ void __launch_bounds__(MT) mgs_smem_kernel(MgsArgs a, int L) {
+template <int EPT, int NT>
+__global__ void __launch_bounds__(NT) mgs_smem_kernel(MgsArgs a, int L) {
     extern __shared__ __align__(16) double2 vbuf[];           // [2][L]
-    __shared__ double2 sh[1 + MT / 32];
+    __shared__ double2 sh[1 + NT / 32];
     __shared__ __align__(8) unsigned long long full[2];
     __shared__ int sflag;
     const long long c0 = (long long)blockIdx.x * L;
@@ -258,7 +258,7 @@ __global__ void __launch_bounds__(MT) mgs_smem_kernel(MgsArgs a, int L) {
         double2 wr[EPT];
 #pragma unroll
         for (int e = 0; e < EPT; ++e) {
-            const int i = e * MT + threadIdx.x;
+            const int i = e * NT + threadIdx.x;
             wr[e] = i < len ? w[c0 + i] : make_double2(0.0, 0.0);
         }
         const double2* V = a.V + r * a.vsr;
@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(MT) mgs_smem_kernel(MgsArgs a, int L) {
             for (int q = 0; q < 4; ++q) acc[q] = make_double2(0.0, 0.0);
 #pragma unroll
             for (int e = 0; e < EPT; ++e) {
-                const int i = e * MT + threadIdx.x;
+                const int i = e * NT + threadIdx.x;
                 if (i < len) {
                     if (k > 0) wr[e] = cfma(mh, vp[i], wr[e]);
                     acc[e & 3] = cfmaconj(vk[i], wr[e], acc[e & 3]);
@@ -297,7 +297,7 @@ __global__ void __launch_bounds__(MT) mgs_smem_kernel(MgsArgs a, int L) {
         double nrm0 = 0.0, nrm1 = 0.0;
 #pragma unroll
         for (int e = 0; e < EPT; ++e) {
-            const int i = e * MT + threadIdx.x;
+            const int i = e * NT + threadIdx.x;
             if (i < len) {
                 if (a.nvec > 0) wr[e] = cfma(mh, vl[i], wr[e]);
                 if (e & 1) nrm1 = fma(wr[e].x, wr[e].x, fma(wr[e].y, wr[e].y, nrm1));
@@ -311,20 +311,21 @@ __global__ void __launch_bounds__(MT) mgs_smem_kernel(MgsArgs a, int L) {
         const double inv = hn > 0.0 ? 1.0 / hn : 0.0;
 #pragma unroll
         for (int e = 0; e < EPT; ++e) {
-            const int i = e * MT + threadIdx.x;
+            const int i = e * NT + threadIdx.x;
             if (i < len) w[c0 + i] = make_double2(wr[e].x * inv, wr[e].y * inv);
         }
     }
 }
 
-template <int EPT>
+template <int EPT, int NT>
 cudaError_t launch_smem_ept(MgsArgs& a, int grid, int L, cudaStream_t st) {
     const size_t smem = 2 * (size_t)L * sizeof(double2);
-    cudaError_t e = cudaFuncSetAttribute(mgs_smem_kernel<EPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(mgs_smem_kernel<EPT, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     void* args[] = {&a, &L};
     count_launch();
-    return cudaLaunchCooperativeKernel((const void*)mgs_smem_kernel<EPT>, dim3(grid), dim3(MT), args, smem, st);
+    return cudaLaunchCooperativeKernel((const void*)mgs_smem_kernel<EPT, NT>, dim3(grid), dim3(NT), args, smem, st);
 }
 
 template <int EPT>
@@ -361,10 +362,12 @@ cudaError_t launch_mgs(const double2* V, long long vsk, long long vsr, double2* 
         const bool aligned = ((reinterpret_cast<uintptr_t>(V) | reinterpret_cast<uintptr_t>(w)) & 15) == 0 &&
                              ((vsk | vsr) * (long long)sizeof(double2)) % 16 == 0;
         if (aligned && smem <= 220 * 1024 && grid * L >= n) {
+            // 256 threads (512 measured 7% slower on the 1023^2 workload: the grid barrier
+            // and the reduction cost more than the extra warps hide)
             const long long per = (L + MT - 1) / MT;
-            if (per <= 8) return launch_smem_ept<8>(a, grid, (int)L, st);
-            if (per <= 16) return launch_smem_ept<16>(a, grid, (int)L, st);
-            if (per <= 28) return launch_smem_ept<28>(a, grid, (int)L, st);
+            if (per <= 8) return launch_smem_ept<8, MT>(a, grid, (int)L, st);
+            if (per <= 16) return launch_smem_ept<16, MT>(a, grid, (int)L, st);
+            if (per <= 28) return launch_smem_ept<28, MT>(a, grid, (int)L, st);
         }
     }
     const long long per = (n + (long long)grid * MT - 1) / ((long long)grid * MT);
