@@ -66,6 +66,11 @@ def parse():
     ap.add_argument("--tensor-cores", default="3xtf32", choices=["3xtf32", "tf32", "off"],
                     help="complex64 multi-RHS block solves (construction of K, batched RHS): tensor cores with "
                          "split TF32 operands, plain TF32, or FP32 on the CUDA cores")
+    ap.add_argument("--inner-maxit", type=int, default=0,
+                    help="> 0: each preconditioner application solves the interface problem (I - S) g = b by "
+                         "FGMRES with the sweep as preconditioner (at most this many steps)")
+    ap.add_argument("--inner-restart", type=int, default=100)
+    ap.add_argument("--inner-tol", type=float, default=1e-4)
     ap.add_argument("--graph", action="store_true",
                     help="replay every preconditioner application from a captured CUDA graph")
     ap.add_argument("--tc-min-rhs", type=int, default=16,
@@ -74,6 +79,11 @@ def parse():
 
 
 TC_MODES = {"3xtf32": "3xtf32", "tf32": "tf32", "off": False}
+
+
+def inner_kw(args):
+    """Interface-Krylov options of Problem.solve."""
+    return dict(inner_maxit=args.inner_maxit, inner_restart=args.inner_restart, inner_tol=args.inner_tol)
 
 
 def precond_only(args):
@@ -151,7 +161,7 @@ def schedules(args):
         row = {"N1xN2": f"5x{N2}"}
         for sched in ("SP", "BSP"):
             kw = dict(restart=args.restart, maxit=2000, tol=args.tol, sched=sched, use_graph=args.graph,
-                      raise_on_noconv=False)
+                      raise_on_noconv=False, **inner_kw(args))
             p.solve(f, **kw)                                                    # warm-up
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -347,7 +357,7 @@ def gpu_arm(args):
     u = torch.empty_like(f)
 
     def solve():
-        _, info, _ = p.solve(f, u=u, restart=args.restart, maxit=3000, tol=args.tol, sched=args.sched, use_graph=args.graph)
+        _, info, _ = p.solve(f, u=u, restart=args.restart, maxit=3000, tol=args.tol, sched=args.sched, use_graph=args.graph, **inner_kw(args))
         return info[0]
 
     for _ in range(args.warmup):
@@ -356,6 +366,7 @@ def gpu_arm(args):
     clocks.start()
     helm.profile(p, True)
     l0 = helm.launch_count()
+    s0 = helm.inner_steps(p)
     barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -369,6 +380,7 @@ def gpu_arm(args):
     barrier()
     ms = e0.elapsed_time(e1) / args.steps
     launches = helm.launch_count() - l0
+    inner_per_solve = (helm.inner_steps(p) - s0) / args.steps
     stage = helm.profile_read(p, "stage")
     trace = helm.profile_read(p, "trace")
     matv = helm.profile_read(p, "matvec")
@@ -399,7 +411,7 @@ def gpu_arm(args):
     t0 = time.perf_counter()
     for _ in range(args.steps):
         fd = fh.to(dev, non_blocking=True)
-        ud, info2, _ = p.solve(fd, restart=args.restart, maxit=3000, tol=args.tol, sched=args.sched, use_graph=args.graph)
+        ud, info2, _ = p.solve(fd, restart=args.restart, maxit=3000, tol=args.tol, sched=args.sched, use_graph=args.graph, **inner_kw(args))
         uh_pinned.copy_(ud, non_blocking=True)
         torch.cuda.synchronize()
     e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
@@ -411,11 +423,11 @@ def gpu_arm(args):
     # the paper's other schedule (symmetric Gauss-Seidel sweeps, Section 4) on the same factors
     sp_form = None
     if args.sched == "BSP" and not args.no_fp64_form:
-        _, isp, _ = p.solve(f, restart=args.restart, maxit=3000, tol=args.tol, sched="SP", use_graph=args.graph)    # warm
+        _, isp, _ = p.solve(f, restart=args.restart, maxit=3000, tol=args.tol, sched="SP", use_graph=args.graph, **inner_kw(args))    # warm
         torch.cuda.synchronize()
         b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         b0.record(st)
-        _, isp, _ = p.solve(f, restart=args.restart, maxit=3000, tol=args.tol, sched="SP", use_graph=args.graph)
+        _, isp, _ = p.solve(f, restart=args.restart, maxit=3000, tol=args.tol, sched="SP", use_graph=args.graph, **inner_kw(args))
         b1.record(st)
         torch.cuda.synchronize()
         mssp = b0.elapsed_time(b1)
@@ -427,11 +439,11 @@ def gpu_arm(args):
     if not args.no_fp64_form and args.prec == "c64":
         q = Problem(w.n, w.n, w.h, w.omega, m2, w.N1, w.N2, w.xcuts, w.ycuts)
         q.factor("c128")
-        _, i64, _ = q.solve(f, restart=args.restart, maxit=3000, tol=args.tol, sched=args.sched, use_graph=args.graph)  # warm
+        _, i64, _ = q.solve(f, restart=args.restart, maxit=3000, tol=args.tol, sched=args.sched, use_graph=args.graph, **inner_kw(args))  # warm
         torch.cuda.synchronize()
         a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a0.record(st)
-        _, i64, _ = q.solve(f, restart=args.restart, maxit=3000, tol=args.tol, sched=args.sched, use_graph=args.graph)
+        _, i64, _ = q.solve(f, restart=args.restart, maxit=3000, tol=args.tol, sched=args.sched, use_graph=args.graph, **inner_kw(args))
         a1.record(st)
         torch.cuda.synchronize()
         ms64 = a0.elapsed_time(a1)
@@ -465,8 +477,10 @@ def gpu_arm(args):
     else:
         st_ = classes[dom]
         bw = st_[2] / (st_[1] / 1e3) / 1e9
+        names = {"trace": "iface_kernel (boundary-operator GEMV + transmission)", "matvec": "matvec_kernel"}
         roofline = {"bound": "hbm", "achieved": bw, "peak": peak, "unit": "GB/s", "frac": bw / peak,
-                    "traffic": None, "kernel": dom, "launches": st_[0], "peak_source": f"hbm_gbs of {peak_src}"}
+                    "traffic": None, "kernel": names.get(dom, dom), "launches": st_[0],
+                    "peak_source": f"hbm_gbs of {peak_src}"}
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         try:
@@ -491,6 +505,9 @@ def gpu_arm(args):
             "prec": args.prec, "sched": args.sched, "restart": args.restart, "tol": args.tol,
             "transmission": "optimized, scale 1.0", "iterations": iters[-1][0], "relres": relres,
             "tensor_cores": args.tensor_cores, "tc_min_rhs": args.tc_min_rhs, "cuda_graph": args.graph,
+            "interface_krylov": ({"inner_maxit": args.inner_maxit, "inner_restart": args.inner_restart,
+                                  "inner_tol": args.inner_tol, "inner_steps_per_solve": inner_per_solve}
+                                 if args.inner_maxit > 0 else None),
             "relres_host_check": check, "factor_ms": factor_ms, "factor_bytes": p.info()["factor_bytes"],
             "l2": "inputs larger than L2: every preconditioner application streams the 1.07 GB of factors",
             "parallelism": f"replicas x{world}",

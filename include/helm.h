@@ -135,6 +135,16 @@ typedef struct {
     int ortho;          /* Arnoldi orthogonalisation, all FP64: HELM_ORTHO_MGS (default;
                            used when n_x*n_y fits the persistent kernel, else CGS2) or
                            HELM_ORTHO_CGS2 */
+    int inner_maxit;    /* 0 (default): each preconditioner application runs the sweep
+                           once (g = sweep(b) on the interface).  > 0: the interface
+                           problem (I - S) g = b of the paper (Sections 3-5) is solved by
+                           FP64 FGMRES preconditioned by the sweep, at most inner_maxit
+                           steps per application, inner_restart per cycle, stopping at
+                           ||b - (I - S) g|| <= inner_tol ||b|| (classical Gram-Schmidt
+                           with reorthogonalisation on the ntrace-long vectors); the
+                           outer FGMRES stays on the volume system */
+    int inner_restart;  /* default 100 */
+    double inner_tol;   /* default 1e-4 */
 } helm_opts;
 
 /* Orthogonalisation of the Arnoldi vectors.
@@ -276,6 +286,11 @@ typedef struct {
 
 /* Number of CUDA kernel launches issued by the library in this process. */
 long long helm_launch_count(void);
+
+/* Interface Krylov steps taken inside the preconditioner applications of p
+ * (gmres_solve with inner_maxit > 0), summed over all calls; per application
+ * the largest count over its right-hand sides.  0 for a NULL handle. */
+long long helm_inner_steps(const helm_problem* p);
 
 /* Enable (on != 0) or disable per-launch event timing on handle p; enabling
  * resets the statistics.  Timing adds two event records per launch. */

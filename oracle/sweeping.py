@@ -232,6 +232,27 @@ class Sweeper:
             raise ValueError(kind)
         return self.reconstruct(r, g)
 
+    def precondition_interface_krylov(self, r, kind="BSP", tol=1e-4, restart=100, maxit=100):
+        """Volume preconditioner with the interface problem solved iteratively: the
+        paper's own use of the sweeps (Sections 3-5), GMRES on ``(I - S) g = b``
+        preconditioned by one SP or BSP application, here flexible GMRES to a
+        relative residual ``tol`` (at most ``maxit`` steps, restart ``restart``)
+        between the liftings and the reconstruction.  As ``tol -> 0`` this tends
+        to the exact interface solve, i.e. ``M^{-1} = A^{-1}``."""
+        from .krylov import fgmres
+        dec = self.dec
+        b = dec.flatten(self.lifting_traces(r))
+        sweep = self.sgs if kind == "SP" else self.bsp
+
+        def interface_operator(v):
+            return v - dec.flatten(self.apply_S(dec.unflatten(v)))
+
+        def interface_precond(v):
+            return dec.flatten(sweep(dec.unflatten(v)))
+
+        g, _, _ = fgmres(interface_operator, interface_precond, b, tol=tol, restart=restart, maxit=maxit)
+        return self.reconstruct(r, dec.unflatten(g))
+
     # ------------------------------------------------------------ dense (tiny)
     def dense_S(self):
         """Dense matrix of S in the numbering m(i, j) (tiny problems only)."""

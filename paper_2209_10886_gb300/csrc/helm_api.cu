@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <new>
 #include <string>
 #include <vector>
@@ -150,6 +151,21 @@ template <typename P> void dfree(P*& p) {
 }  // namespace
 
 // ------------------------------------------------------------------ handle
+// workspace of one restarted FGMRES (V: restart+1 basis vectors, Z: restart
+// preconditioned vectors, per RHS n values each; the rest per RHS and cycle)
+struct KrylovWS {
+    int nrhs = 0, restart = 0;
+    long long n = 0;
+    double2 *V = nullptr, *Z = nullptr, *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr;
+    double2 *h1 = nullptr, *h2 = nullptr, *hsum = nullptr, *y = nullptr, *cpart = nullptr;
+    double *rpart = nullptr, *rn = nullptr, *est = nullptr, *invh = nullptr;
+    int *active = nullptr, *jcount = nullptr, *need = nullptr;
+    double2* mgs_part = nullptr;     // partial sums of the persistent Gram-Schmidt kernel
+    unsigned* mgs_bar = nullptr;     // its grid-barrier state
+    double2 *b = nullptr, *x = nullptr;   // interface solver: right-hand side and solution (nrhs x n)
+    int nblk = 0;
+};
+
 struct helm_problem {
     int nx = 0, ny = 0, N1 = 0, N2 = 0;
     double h = 0, omega = 0;
@@ -196,15 +212,9 @@ struct helm_problem {
     double* d_pc_norm = nullptr;     // per RHS: ||r||^2, 1/||r||, ||r||
     double* d_pc_partial = nullptr;
 
-    // Krylov workspace
-    int kw_nrhs = 0, kw_restart = 0;
-    double2 *d_V = nullptr, *d_Z = nullptr, *d_H = nullptr, *d_cs = nullptr, *d_sn = nullptr, *d_g = nullptr;
-    double2 *d_h1 = nullptr, *d_h2 = nullptr, *d_hsum = nullptr, *d_y = nullptr, *d_cpart = nullptr;
-    double *d_rpart = nullptr, *d_rn = nullptr, *d_est = nullptr, *d_invh = nullptr;
-    int *d_active = nullptr, *d_jcount = nullptr, *d_need = nullptr;
-    double2* d_mgs_part = nullptr;   // partial sums of the persistent Gram-Schmidt kernel
-    unsigned* d_mgs_bar = nullptr;   // its grid-barrier state
-    int kw_nblk = 0;
+    // Krylov workspaces: the volume FGMRES and the interface FGMRES nested in the preconditioner
+    KrylovWS kw, kwi;
+    long long inner_steps = 0;       // interface Krylov steps taken inside the preconditioner (all calls)
 
     // adjoint workspace
     double2 *d_res = nullptr, *d_fadj = nullptr, *d_U = nullptr, *d_L = nullptr;
@@ -305,12 +315,17 @@ static void free_pc_ws(helm_problem* p) {
     dfree(p->d_pc_partial);
     p->ws_nrhs = 0;
 }
+static void free_kw(KrylovWS& w) {
+    dfree(w.V); dfree(w.Z); dfree(w.H); dfree(w.cs); dfree(w.sn); dfree(w.g);
+    dfree(w.h1); dfree(w.h2); dfree(w.hsum); dfree(w.y); dfree(w.cpart);
+    dfree(w.rpart); dfree(w.rn); dfree(w.est); dfree(w.invh); dfree(w.active); dfree(w.jcount); dfree(w.need);
+    dfree(w.mgs_part); dfree(w.mgs_bar); dfree(w.b); dfree(w.x);
+    w.nrhs = w.restart = 0;
+    w.n = 0;
+}
 static void free_krylov(helm_problem* p) {
-    dfree(p->d_V); dfree(p->d_Z); dfree(p->d_H); dfree(p->d_cs); dfree(p->d_sn); dfree(p->d_g);
-    dfree(p->d_h1); dfree(p->d_h2); dfree(p->d_hsum); dfree(p->d_y); dfree(p->d_cpart);
-    dfree(p->d_rpart); dfree(p->d_rn); dfree(p->d_est); dfree(p->d_invh); dfree(p->d_active); dfree(p->d_jcount); dfree(p->d_need);
-    dfree(p->d_mgs_part); dfree(p->d_mgs_bar);
-    p->kw_nrhs = p->kw_restart = 0;
+    free_kw(p->kw);
+    free_kw(p->kwi);
 }
 static void free_adj(helm_problem* p) {
     dfree(p->d_res); dfree(p->d_fadj); dfree(p->d_U); dfree(p->d_L); dfree(p->d_jpart);
@@ -330,7 +345,12 @@ extern "C" void helm_default_opts(helm_opts* o) {
     o->use_graph = 0;
     o->hist = nullptr;
     o->ortho = HELM_ORTHO_MGS;
+    o->inner_maxit = 0;
+    o->inner_restart = 100;
+    o->inner_tol = 1e-4;
 }
+
+extern "C" long long helm_inner_steps(const helm_problem* p) { return p ? p->inner_steps : 0; }
 extern "C" void helm_default_setup_opts(helm_setup_opts* o) {
     if (!o) return;
     o->transmission = HELM_TC_OPTIMIZED;
@@ -783,120 +803,144 @@ struct PcWork {
     void* r64;
 };
 
+// per-application constants of the preconditioner
+struct PcCtx {
+    const double* rinv = nullptr;    // complex64: 1/||r|| per RHS (the source is scaled to unit norm)
+    const double* rsc = nullptr;     // complex64: ||r|| per RHS (applied to the output)
+    bool tc = false;                 // the stages run on the tensor cores
+};
+
 template <typename R>
-static helm_status run_precond_t(helm_problem* p, const PcWork& w, int sched, const double2* r, double2* z, int nrhs,
-                                 cudaStream_t st) {
-    using T = Cx<R>;
-    const double* rinv = nullptr;
-    const double* rsc = nullptr;
+static PcCtx precond_prologue(helm_problem* p, const PcWork& w, const double2* r, int nrhs, cudaStream_t st) {
+    PcCtx cx;
     if (sizeof(R) == 4) {
         // scale each right-hand side to unit 2-norm before rounding to complex64
         launch_norm2_partial(r, p->N(), nrhs, p->N(), w.partial, kPartialBlocks, st);
         launch_reduce_rows(w.partial, kPartialBlocks, nrhs, w.norm, 0, st);
         launch_scale_from_norm(w.norm, w.norm + nrhs, w.norm + 2 * nrhs, nrhs, st);
-        rinv = w.norm + nrhs;
-        rsc = w.norm + 2 * nrhs;
+        cx.rinv = w.norm + nrhs;
+        cx.rsc = w.norm + 2 * nrhs;
     }
     // the tensor-core stages read the scaled source in complex64
-    const bool tc = sizeof(R) == 4 && tc_used(p, nrhs) && w.escr && w.r64;
-    if (tc) launch_to_c64_scaled(r, rinv, (float2*)w.r64, p->N(), nrhs, st);
+    cx.tc = sizeof(R) == 4 && tc_used(p, nrhs) && w.escr && w.r64;
+    if (cx.tc) launch_to_c64_scaled(r, cx.rinv, (float2*)w.r64, p->N(), nrhs, st);
+    return cx;
+}
+
+// one stage of a schedule (one batched launch, two for mixed tensor-core tile counts)
+template <typename R>
+static helm_status run_stage_t(helm_problem* p, const PcWork& w, const PcCtx& cx, const StageDesc& sd,
+                               const double2* r, double2* z, int nrhs, cudaStream_t st) {
+    using T = Cx<R>;
+    const double* rinv = cx.rinv;
+    const double* rsc = cx.rsc;
+    const bool tc = cx.tc;
     T* buf[3] = {(T*)w.trace[0], (T*)w.trace[1], (T*)w.trace[2]};
     auto B = [&](int id) -> T* { return id < 0 ? nullptr : buf[id]; };
-    for (const StageDesc& sd : p->sched[sched]) {
-        if (sd.iface && p->d_K) {
-            IfaceArgs<R> ia{};
-            ia.subtab = p->d_subtab;
-            ia.subs = p->d_stage_subs + sd.sub_off;
-            ia.nrhs = nrhs;
-            ia.ntrace = p->ntrace;
-            ia.K = (const T*)p->d_K;
-            ia.tc = sizeof(R) == 4 ? (const TraceCoef<T>*)p->d_tc64 : (const TraceCoef<T>*)p->d_tc128;
-            ia.gin0 = B(sd.in0); ia.gin1 = B(sd.in1);
-            ia.mask = sd.mask;
-            ia.dst = B(sd.dst); ia.dst2 = B(sd.dst2); ia.base = B(sd.base); ia.sub = B(sd.sub);
-            double bytes = 0, flops = 0;
-            if (p->prof_on) {
-                const double sT = sizeof(T);
-                for (int id : sd.subs) {
-                    const SubDev& d = p->subs[id].dev;
-                    double rows = 0;
-                    for (int sde = 0; sde < 4; ++sde)
-                        if ((sd.mask & (1 << sde)) && d.bo[sde] >= 0) rows += (sde == SW || sde == SE) ? d.my : d.mx;
-                    const double io = d.Lb * sT * ((sd.in0 >= 0) + (sd.in1 >= 0)) +
-                                      rows * sT * (1 + (sd.dst2 >= 0) + (sd.base >= 0) + (sd.sub >= 0));
-                    bytes += rows * d.Lb * sT + io * nrhs;
-                    flops += 8.0 * rows * d.Lb * nrhs;
-                }
-            }
-            prof_begin(p, HELM_K_TRACE, st);
-            cudaError_t e = launch_iface<R>(ia, (int)sd.subs.size(), 2 * (p->max_mx + p->max_my), p->max_Lb, st);
-            prof_end(p, HELM_K_TRACE, bytes, st, flops);
-            if (e != cudaSuccess) return cuda_status(e, "interface stage launch");
-            continue;
-        }
-        StageArgs<R> a{};
-        a.subtab = p->d_subtab;
-        a.subs = p->d_stage_subs + sd.sub_off;
-        a.nx = p->nx; a.ny = p->ny; a.nrhs = nrhs;
-        a.ntrace = p->ntrace;
-        a.wstride = p->N();
-        a.X = (const T*)p->d_X;
-        a.tc = sizeof(R) == 4 ? (const TraceCoef<T>*)p->d_tc64 : (const TraceCoef<T>*)p->d_tc128;
-        a.src = sd.src;
-        a.r = r;
-        a.rscale = rinv;
-        a.gin0 = B(sd.in0); a.gin1 = B(sd.in1);
-        a.mask = sd.mask;
-        a.dst = B(sd.dst); a.dst2 = B(sd.dst2); a.base = B(sd.base); a.sub = B(sd.sub);
-        a.z = sd.final_ ? z : nullptr;
-        a.zscale = rsc;
-        a.yws = (T*)w.yws;
-        a.err = p->d_err;
+    if (sd.iface && p->d_K) {
+        IfaceArgs<R> ia{};
+        ia.subtab = p->d_subtab;
+        ia.subs = p->d_stage_subs + sd.sub_off;
+        ia.nrhs = nrhs;
+        ia.ntrace = p->ntrace;
+        ia.K = (const T*)p->d_K;
+        ia.tc = sizeof(R) == 4 ? (const TraceCoef<T>*)p->d_tc64 : (const TraceCoef<T>*)p->d_tc128;
+        ia.gin0 = B(sd.in0); ia.gin1 = B(sd.in1);
+        ia.mask = sd.mask;
+        ia.dst = B(sd.dst); ia.dst2 = B(sd.dst2); ia.base = B(sd.base); ia.sub = B(sd.sub);
         double bytes = 0, flops = 0;
         if (p->prof_on) {
-            // algorithmic bytes: each X_r once per stage (shared by all RHS), the
-            // solve workspace y written and read once, source read, volume output
-            // written, incoming traces read, outgoing traces (and their base/sub) moved
             const double sT = sizeof(T);
             for (int id : sd.subs) {
                 const SubDev& d = p->subs[id].dev;
-                double per_rhs = 2.0 * (d.my - 1) * d.mx * sT;
-                if (sd.src) per_rhs += 16.0 * d.mx * d.my;
-                if (sd.final_) per_rhs += 16.0 * d.mx * d.my;
-                for (int sde = 0; sde < 4; ++sde) {
-                    if (d.tin[sde] < 0) continue;
-                    const double len = (sde == SW || sde == SE) ? d.my : d.mx;
-                    if (sd.in0 >= 0) per_rhs += len * sT;
-                    if (sd.in1 >= 0) per_rhs += len * sT;
-                    if (sd.mask & (1 << sde))
-                        per_rhs += len * sT * (1 + (sd.dst2 >= 0) + (sd.base >= 0) + (sd.sub >= 0));
-                }
-                bytes += (2.0 * d.my - 1) * d.mx * (double)d.mx * sT + per_rhs * nrhs;
-                flops += 8.0 * (2.0 * d.my - 1) * d.mx * (double)d.mx * nrhs;
+                double rows = 0;
+                for (int sde = 0; sde < 4; ++sde)
+                    if ((sd.mask & (1 << sde)) && d.bo[sde] >= 0) rows += (sde == SW || sde == SE) ? d.my : d.mx;
+                const double io = d.Lb * sT * ((sd.in0 >= 0) + (sd.in1 >= 0)) +
+                                  rows * sT * (1 + (sd.dst2 >= 0) + (sd.base >= 0) + (sd.sub >= 0));
+                bytes += rows * d.Lb * sT + io * nrhs;
+                flops += 8.0 * rows * d.Lb * nrhs;
             }
         }
-        prof_begin(p, HELM_K_STAGE, st);
-        cudaError_t e = cudaSuccess;
-        bool done = false;
-        if constexpr (sizeof(R) == 4) {
-            // 16 or more right-hand sides: the block solves are GEMMs for the tensor cores
-            if (tc) {
-                for (int c = 0; c < 2 && e == cudaSuccess; ++c) {
-                    StageArgs<R> ac = a;
-                    ac.escr = (T*)w.escr;
-                    ac.uscr = (T*)w.escr + (long long)nrhs * p->etot;
-                    ac.estride = p->etot;
-                    ac.r64 = (const T*)w.r64;
-                    ac.subs = p->d_stage_subs + sd.tc_off[c];
-                    e = launch_tc_stage(ac, p->d_XT, c + 1, p->tc_split, sd.tc_n[c], st);
-                }
-                done = true;
+        prof_begin(p, HELM_K_TRACE, st);
+        cudaError_t e = launch_iface<R>(ia, (int)sd.subs.size(), 2 * (p->max_mx + p->max_my), p->max_Lb, st);
+        prof_end(p, HELM_K_TRACE, bytes, st, flops);
+        if (e != cudaSuccess) return cuda_status(e, "interface stage launch");
+        return HELM_OK;
+    }
+    StageArgs<R> a{};
+    a.subtab = p->d_subtab;
+    a.subs = p->d_stage_subs + sd.sub_off;
+    a.nx = p->nx; a.ny = p->ny; a.nrhs = nrhs;
+    a.ntrace = p->ntrace;
+    a.wstride = p->N();
+    a.X = (const T*)p->d_X;
+    a.tc = sizeof(R) == 4 ? (const TraceCoef<T>*)p->d_tc64 : (const TraceCoef<T>*)p->d_tc128;
+    a.src = sd.src;
+    a.r = r;
+    a.rscale = rinv;
+    a.gin0 = B(sd.in0); a.gin1 = B(sd.in1);
+    a.mask = sd.mask;
+    a.dst = B(sd.dst); a.dst2 = B(sd.dst2); a.base = B(sd.base); a.sub = B(sd.sub);
+    a.z = sd.final_ ? z : nullptr;
+    a.zscale = rsc;
+    a.yws = (T*)w.yws;
+    a.err = p->d_err;
+    double bytes = 0, flops = 0;
+    if (p->prof_on) {
+        // algorithmic bytes: each X_r once per stage (shared by all RHS), the
+        // solve workspace y written and read once, source read, volume output
+        // written, incoming traces read, outgoing traces (and their base/sub) moved
+        const double sT = sizeof(T);
+        for (int id : sd.subs) {
+            const SubDev& d = p->subs[id].dev;
+            double per_rhs = 2.0 * (d.my - 1) * d.mx * sT;
+            if (sd.src) per_rhs += 16.0 * d.mx * d.my;
+            if (sd.final_) per_rhs += 16.0 * d.mx * d.my;
+            for (int sde = 0; sde < 4; ++sde) {
+                if (d.tin[sde] < 0) continue;
+                const double len = (sde == SW || sde == SE) ? d.my : d.mx;
+                if (sd.in0 >= 0) per_rhs += len * sT;
+                if (sd.in1 >= 0) per_rhs += len * sT;
+                if (sd.mask & (1 << sde))
+                    per_rhs += len * sT * (1 + (sd.dst2 >= 0) + (sd.base >= 0) + (sd.sub >= 0));
             }
+            bytes += (2.0 * d.my - 1) * d.mx * (double)d.mx * sT + per_rhs * nrhs;
+            flops += 8.0 * (2.0 * d.my - 1) * d.mx * (double)d.mx * nrhs;
         }
-        if (!done)
-            e = launch_stage<R>(a, (int)sd.subs.size(), p->max_mx, p->max_my, p->max_w, p->max_ld, p->num_sms, st);
-        prof_end(p, HELM_K_STAGE, bytes, st, flops);
-        if (e != cudaSuccess) return cuda_status(e, "stage launch");
+    }
+    prof_begin(p, HELM_K_STAGE, st);
+    cudaError_t e = cudaSuccess;
+    bool done = false;
+    if constexpr (sizeof(R) == 4) {
+        // 16 or more right-hand sides: the block solves are GEMMs for the tensor cores
+        if (tc) {
+            for (int c = 0; c < 2 && e == cudaSuccess; ++c) {
+                StageArgs<R> ac = a;
+                ac.escr = (T*)w.escr;
+                ac.uscr = (T*)w.escr + (long long)nrhs * p->etot;
+                ac.estride = p->etot;
+                ac.r64 = (const T*)w.r64;
+                ac.subs = p->d_stage_subs + sd.tc_off[c];
+                e = launch_tc_stage(ac, p->d_XT, c + 1, p->tc_split, sd.tc_n[c], st);
+            }
+            done = true;
+        }
+    }
+    if (!done)
+        e = launch_stage<R>(a, (int)sd.subs.size(), p->max_mx, p->max_my, p->max_w, p->max_ld, p->num_sms, st);
+    prof_end(p, HELM_K_STAGE, bytes, st, flops);
+    if (e != cudaSuccess) return cuda_status(e, "stage launch");
+    return HELM_OK;
+}
+
+template <typename R>
+static helm_status run_precond_t(helm_problem* p, const PcWork& w, int sched, const double2* r, double2* z, int nrhs,
+                                 cudaStream_t st) {
+    const PcCtx cx = precond_prologue<R>(p, w, r, nrhs, st);
+    for (const StageDesc& sd : p->sched[sched]) {
+        const helm_status s = run_stage_t<R>(p, w, cx, sd, r, z, nrhs, st);
+        if (s != HELM_OK) return s;
     }
     return HELM_OK;
 }
@@ -944,6 +988,42 @@ static helm_status run_precond_graph(helm_problem* p, int sched, const double2* 
     cudaGraphDestroy(graph);
     if (ei != cudaSuccess) return cuda_status(ei, "instantiating the preconditioner graph");
     p->graphs.push_back({sched, nrhs, r, z, exec, kernels});
+    HELM_CUDA_TRY(cudaGraphLaunch(exec, st));
+    count_launch((int)kernels);
+    return HELM_OK;
+}
+
+// A launch sequence with fixed pointers replayed from a CUDA graph: captured on
+// the first call for (tag, nrhs) on the internal stream, launched on `st`.
+// Plain launches while profiling (the per-launch events need them).
+static helm_status run_captured(helm_problem* p, int tag, int nrhs, cudaStream_t st,
+                                const std::function<helm_status(cudaStream_t)>& seq) {
+    if (p->prof_on) return seq(st);
+    const void* key = reinterpret_cast<const void*>((intptr_t)(tag + 1));
+    for (const auto& g : p->graphs)
+        if (g.sched == -1 && g.nrhs == nrhs && g.r == key) {
+            HELM_CUDA_TRY(cudaGraphLaunch(g.exec, st));
+            count_launch((int)g.kernels);
+            return HELM_OK;
+        }
+    if (!p->cap_stream) {
+        HELM_CUDA_TRY(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
+        HELM_CUDA_TRY(cudaEventCreateWithFlags(&p->cap_ev, cudaEventDisableTiming));
+    }
+    const long long before = helm_launch_count();
+    HELM_CUDA_TRY(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeRelaxed));
+    helm_status s = seq(p->cap_stream);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(p->cap_stream, &graph);
+    const long long kernels = helm_launch_count() - before;
+    uncount_launch(kernels);
+    if (s != HELM_OK) { if (graph) cudaGraphDestroy(graph); return s; }
+    if (ec != cudaSuccess) return cuda_status(ec, "capturing a stage sequence");
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) return cuda_status(ei, "instantiating a stage-sequence graph");
+    p->graphs.push_back({-1, nrhs, key, nullptr, exec, kernels});
     HELM_CUDA_TRY(cudaGraphLaunch(exec, st));
     count_launch((int)kernels);
     return HELM_OK;
@@ -1027,43 +1107,50 @@ extern "C" helm_status helm_matvec(helm_problem* p, const helm_c128* u, helm_c12
 }
 
 // ------------------------------------------------------------------ FGMRES
-static helm_status ensure_krylov(helm_problem* p, int nrhs, int m) {
-    if (p->kw_nrhs >= nrhs && p->kw_restart >= m) return HELM_OK;
-    free_krylov(p);
-    const long long N = p->N();
+// with_bx: also the right-hand side and solution arrays of the interface solver
+static helm_status ensure_kw(KrylovWS& w, int nrhs, int m, long long n, bool with_bx) {
+    if (w.nrhs >= nrhs && w.restart >= m && w.n == n && (!with_bx || w.b)) return HELM_OK;
+    free_kw(w);
     const int nb = kPartialBlocks;
     cudaError_t e = cudaSuccess;
     auto chk = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
-    chk(dalloc(p->d_V, (size_t)(m + 1) * nrhs * N));
-    chk(dalloc(p->d_Z, (size_t)m * nrhs * N));
-    chk(dalloc(p->d_H, (size_t)nrhs * (m + 1) * m));
-    chk(dalloc(p->d_cs, (size_t)nrhs * (m + 1)));
-    chk(dalloc(p->d_sn, (size_t)nrhs * (m + 1)));
-    chk(dalloc(p->d_g, (size_t)nrhs * (m + 1)));
-    chk(dalloc(p->d_h1, (size_t)nrhs * (m + 1)));
-    chk(dalloc(p->d_h2, (size_t)nrhs * (m + 1)));
-    chk(dalloc(p->d_hsum, (size_t)nrhs * (m + 1)));
-    chk(dalloc(p->d_y, (size_t)nrhs * (m + 1)));
-    chk(dalloc(p->d_cpart, (size_t)nb * nrhs * (m + 1)));
-    chk(dalloc(p->d_rpart, (size_t)nb * nrhs));
-    chk(dalloc(p->d_rn, (size_t)4 * nrhs));
-    chk(dalloc(p->d_need, (size_t)nrhs));
+    chk(dalloc(w.V, (size_t)(m + 1) * nrhs * n));
+    chk(dalloc(w.Z, (size_t)m * nrhs * n));
+    chk(dalloc(w.H, (size_t)nrhs * (m + 1) * m));
+    chk(dalloc(w.cs, (size_t)nrhs * (m + 1)));
+    chk(dalloc(w.sn, (size_t)nrhs * (m + 1)));
+    chk(dalloc(w.g, (size_t)nrhs * (m + 1)));
+    chk(dalloc(w.h1, (size_t)nrhs * (m + 1)));
+    chk(dalloc(w.h2, (size_t)nrhs * (m + 1)));
+    chk(dalloc(w.hsum, (size_t)nrhs * (m + 1)));
+    chk(dalloc(w.y, (size_t)nrhs * (m + 1)));
+    chk(dalloc(w.cpart, (size_t)nb * nrhs * (m + 1)));
+    chk(dalloc(w.rpart, (size_t)nb * nrhs));
+    chk(dalloc(w.rn, (size_t)4 * nrhs));
+    chk(dalloc(w.need, (size_t)nrhs));
     {
         const int g = mgs_grid();
         if (g > 0) {
-            chk(dalloc(p->d_mgs_part, (size_t)2 * g));
-            chk(dalloc(p->d_mgs_bar, (size_t)2));
-            if (e == cudaSuccess) e = cudaMemset(p->d_mgs_bar, 0, 2 * sizeof(unsigned));
+            chk(dalloc(w.mgs_part, (size_t)2 * g));
+            chk(dalloc(w.mgs_bar, (size_t)2));
+            if (e == cudaSuccess) e = cudaMemset(w.mgs_bar, 0, 2 * sizeof(unsigned));
         }
     }
-    chk(dalloc(p->d_est, (size_t)nrhs));
-    chk(dalloc(p->d_invh, (size_t)nrhs));
-    chk(dalloc(p->d_active, (size_t)nrhs));
-    chk(dalloc(p->d_jcount, (size_t)nrhs));
-    if (e != cudaSuccess) { free_krylov(p); return cuda_status(e, "allocating the Krylov workspace"); }
-    p->kw_nrhs = nrhs;
-    p->kw_restart = m;
-    p->kw_nblk = nb;
+    chk(dalloc(w.est, (size_t)nrhs));
+    chk(dalloc(w.invh, (size_t)nrhs));
+    chk(dalloc(w.active, (size_t)nrhs));
+    chk(dalloc(w.jcount, (size_t)nrhs));
+    if (with_bx) {
+        chk(dalloc(w.b, (size_t)nrhs * n));
+        chk(dalloc(w.x, (size_t)nrhs * n));
+    }
+    if (e != cudaSuccess) { free_kw(w); return cuda_status(e, "allocating the Krylov workspace"); }
+    w.nrhs = nrhs;
+    w.restart = m;
+    w.n = n;
+    // partial-sum blocks of the reductions: ~128 elements per block for short
+    // (interface) vectors, at least one per SM, at most the allocated count
+    w.nblk = (int)std::min<long long>(nb, std::max<long long>(152, (n + 127) / 128));
     return HELM_OK;
 }
 
@@ -1091,53 +1178,62 @@ __global__ void dgks_norm_kernel(const double* n2, const int* need, double* hnor
     hnorm[k] = sqrt(need[k] ? n2[2 * nrhs + k] : n2[nrhs + k]);
 }
 
-static helm_status gmres_impl(helm_problem* p, const double2* f, double2* u, int nrhs, const helm_opts& o,
-                              helm_info* info, cudaStream_t st) {
-    const long long N = p->N();
-    const int m = o.restart;
-    helm_status s = ensure_krylov(p, nrhs, m);
-    if (s != HELM_OK) return s;
-    s = ensure_pc_ws(p, nrhs);
-    if (s != HELM_OK) return s;
-    const int nb = p->kw_nblk;
-    const long long vsk = (long long)nrhs * N;    // V_j of RHS k at d_V + j*vsk + k*N
-    const double h2 = p->h * p->h;
+// The operator, preconditioner and residual of one FGMRES: vectors of n values
+// per RHS, RHS k at offset k*n.
+struct KrylovOps {
+    std::function<helm_status(const double2* x, bool x_zero, double2* r)> residual;   // r = b - A x
+    std::function<helm_status(const double2* v, double2* z)> precond;                // z = M^{-1} v
+    std::function<helm_status(const double2* z, double2* w)> matvec;                 // w = A z
+};
+
+// Restarted right-preconditioned flexible GMRES (all arithmetic FP64): x is the
+// initial guess on entry (zero unless x0_given) and the iterate on exit; bnorm
+// holds ||b|| per RHS; iters / relres receive the Arnoldi steps and the true
+// relative residual ||b - A x|| / ||b|| at exit.  Modified Gram-Schmidt in the
+// persistent kernel when use_mgs, else classical Gram-Schmidt with selective
+// reorthogonalisation.  `who` names the caller in error messages.
+static helm_status fgmres_core(helm_problem* p, KrylovWS& kw, long long n, int nrhs, int m, int maxit, double tol,
+                               const std::vector<double>& bnorm, double2* x, bool x0_given, bool use_mgs_req,
+                               double* hist, const KrylovOps& ops, std::vector<int>& iters,
+                               std::vector<double>& relres, const char* who, cudaStream_t st) {
+    const long long N = n;
+    helm_status s = HELM_OK;
+    const int nb = kw.nblk;
+    const long long vsk = (long long)nrhs * N;    // V_j of RHS k at V + j*vsk + k*N
     const int ld = m + 1;
     // modified Gram-Schmidt needs the vector to fit the persistent kernel's registers
-    const int mgs_grid_n = (o.ortho == HELM_ORTHO_MGS) ? mgs_grid() : 0;
-    const bool use_mgs = mgs_grid_n > 0 && N <= mgs_max_n(mgs_grid_n) && p->d_mgs_part != nullptr;
-    if (!o.x0_given) HELM_CUDA_TRY(cudaMemsetAsync(u, 0, (size_t)nrhs * N * sizeof(double2), st));
+    const int mgs_grid_n = use_mgs_req ? mgs_grid() : 0;
+    const bool use_mgs = mgs_grid_n > 0 && N <= mgs_max_n(mgs_grid_n) && kw.mgs_part != nullptr;
+    if (!x0_given) HELM_CUDA_TRY(cudaMemsetAsync(x, 0, (size_t)nrhs * N * sizeof(double2), st));
 
-    // ||h^2 f||
-    std::vector<double> bnorm(nrhs), rn(nrhs), est(nrhs);
+    std::vector<double> rn(nrhs), est(nrhs);
     std::vector<int> need(nrhs, 0);
-    launch_norm2_partial(f, N, nrhs, N, p->d_rpart, nb, st);
-    launch_reduce_rows(p->d_rpart, nb, nrhs, p->d_rn, 1, st);
-    HELM_CUDA_TRY(cudaMemcpyAsync(bnorm.data(), p->d_rn, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
-    HELM_CUDA_TRY(cudaStreamSynchronize(st));
-    for (auto& b : bnorm) b *= h2;
-
-    std::vector<int> iters(nrhs, 0), done(nrhs, 0), active(nrhs, 0), jcount(nrhs, 0);
+    std::vector<int> done(nrhs, 0), active(nrhs, 0), jcount(nrhs, 0);
+    iters.assign(nrhs, 0);
+    relres.assign(nrhs, 0.0);
     int dev_status = 0;
-    std::vector<double> relres(nrhs, 0.0);
     for (int k = 0; k < nrhs; ++k) done[k] = bnorm[k] == 0.0;
 
+    bool x_zero = !x0_given;
     while (true) {
-        // r = h^2 f - A u into V_0, beta = ||r||
-        const int nrp = launch_residual(p->d_adiag, p->nx, p->ny, f, h2, u, p->d_V, nrhs, nullptr, p->d_rpart, nb, st);
-        launch_reduce_rows(p->d_rpart, nrp, nrhs, p->d_rn, 1, st);
-        HELM_CUDA_TRY(cudaMemcpyAsync(rn.data(), p->d_rn, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
+        // r = b - A x into V_0, beta = ||r||
+        s = ops.residual(x, x_zero, kw.V);
+        if (s != HELM_OK) return s;
+        x_zero = false;
+        launch_norm2_partial(kw.V, N, nrhs, N, kw.rpart, nb, st);
+        launch_reduce_rows(kw.rpart, nb, nrhs, kw.rn, 1, st);
+        HELM_CUDA_TRY(cudaMemcpyAsync(rn.data(), kw.rn, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
         HELM_CUDA_TRY(cudaStreamSynchronize(st));
         bool any = false;
         for (int k = 0; k < nrhs; ++k) {
             relres[k] = bnorm[k] > 0 ? rn[k] / bnorm[k] : 0.0;
-            if (relres[k] <= o.tol || iters[k] >= o.maxit) done[k] = 1;
+            if (relres[k] <= tol || iters[k] >= maxit) done[k] = 1;
             active[k] = !done[k];
             any |= active[k] != 0;
             jcount[k] = 0;
         }
         if (!any) break;
-        HELM_CUDA_TRY(cudaMemcpyAsync(p->d_active, active.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, st));
+        HELM_CUDA_TRY(cudaMemcpyAsync(kw.active, active.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, st));
         // g = beta e_1, V_0 = r / beta
         {
             std::vector<double2> g0((size_t)nrhs * ld, make_double2(0, 0));
@@ -1146,103 +1242,238 @@ static helm_status gmres_impl(helm_problem* p, const double2* f, double2* u, int
                 g0[(size_t)k * ld] = make_double2(rn[k], 0.0);
                 inv[k] = rn[k] > 0 ? 1.0 / rn[k] : 0.0;
             }
-            HELM_CUDA_TRY(cudaMemcpyAsync(p->d_g, g0.data(), g0.size() * sizeof(double2), cudaMemcpyHostToDevice, st));
-            HELM_CUDA_TRY(cudaMemcpyAsync(p->d_invh, inv.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, st));
-            launch_scale_vec(p->d_V, N, p->d_V, N, p->d_invh, N, nrhs, p->d_active, st);
+            HELM_CUDA_TRY(cudaMemcpyAsync(kw.g, g0.data(), g0.size() * sizeof(double2), cudaMemcpyHostToDevice, st));
+            HELM_CUDA_TRY(cudaMemcpyAsync(kw.invh, inv.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, st));
+            launch_scale_vec(kw.V, N, kw.V, N, kw.invh, N, nrhs, kw.active, st);
             HELM_CUDA_TRY(cudaStreamSynchronize(st));    // host vectors above go out of scope
         }
         for (int j = 0; j < m; ++j) {
-            double2* Vj = p->d_V + (long long)j * vsk;
-            double2* Vn = p->d_V + (long long)(j + 1) * vsk;
-            double2* Zj = p->d_Z + (long long)j * vsk;
+            double2* Vj = kw.V + (long long)j * vsk;
+            double2* Vn = kw.V + (long long)(j + 1) * vsk;
+            double2* Zj = kw.Z + (long long)j * vsk;
             // z_j = M^{-1} v_j ; w = A z_j
-            s = o.use_graph ? run_precond_graph(p, o.sched, Vj, Zj, nrhs, st) : run_precond(p, o.sched, Vj, Zj, nrhs, st);
+            s = ops.precond(Vj, Zj);
             if (s != HELM_OK) return s;
             const double vb = 16.0 * N * nrhs;   // bytes of one field for all RHS
-            prof_begin(p, HELM_K_MATVEC, st);
-            launch_matvec(p->d_adiag, p->nx, p->ny, Zj, Vn, nrhs, st);
-            prof_end(p, HELM_K_MATVEC, 2 * vb + 16.0 * N, st, 16.0 * N * nrhs);
+            s = ops.matvec(Zj, Vn);
+            if (s != HELM_OK) return s;
             if (use_mgs) {
                 // modified Gram-Schmidt, persistent kernel: h = column j of H, ||w||, v_{j+1}
                 int nact = 0;
                 for (int k = 0; k < nrhs; ++k) nact += active[k];
                 prof_begin(p, HELM_K_ORTHO, st);
-                cudaError_t e = launch_mgs(p->d_V, vsk, N, Vn, j + 1, N, nrhs, p->d_active, p->d_hsum, ld,
-                                           p->d_rn + 3 * nrhs, p->d_mgs_part, p->d_mgs_bar, p->d_err, mgs_grid_n, st);
+                cudaError_t e = launch_mgs(kw.V, vsk, N, Vn, j + 1, N, nrhs, kw.active, kw.hsum, ld,
+                                           kw.rn + 3 * nrhs, kw.mgs_part, kw.mgs_bar, p->d_err, mgs_grid_n, st);
                 prof_end(p, HELM_K_ORTHO, (j + 3) * 16.0 * N * nact, st, (16.0 * (j + 1) + 4.0) * N * nact);
                 if (e != cudaSuccess) return cuda_status(e, "modified Gram-Schmidt launch");
-                launch_hessenberg_step(p->d_H, ld, (long long)ld * m, p->d_cs, p->d_sn, p->d_g, ld, p->d_hsum, ld,
-                                       p->d_rn + 3 * nrhs, j, nrhs, p->d_active, p->d_est, p->d_invh, st);
+                launch_hessenberg_step(kw.H, ld, (long long)ld * m, kw.cs, kw.sn, kw.g, ld, kw.hsum, ld,
+                                       kw.rn + 3 * nrhs, j, nrhs, kw.active, kw.est, kw.invh, st);
                 goto step_done;
             }
             // classical Gram-Schmidt with selective reorthogonalisation (all in FP64)
-            launch_norm2_partial(Vn, N, nrhs, N, p->d_rpart, nb, st);
-            launch_reduce_rows(p->d_rpart, nb, nrhs, p->d_rn, 0, st);                 // ||w||^2
+            launch_norm2_partial(Vn, N, nrhs, N, kw.rpart, nb, st);
+            launch_reduce_rows(kw.rpart, nb, nrhs, kw.rn, 0, st);                 // ||w||^2
             prof_begin(p, HELM_K_ORTHO, st);
-            launch_mdot(p->d_V, vsk, N, j + 1, Vn, N, N, nrhs, p->d_active, p->d_cpart, nb, st);
+            launch_mdot(kw.V, vsk, N, j + 1, Vn, N, N, nrhs, kw.active, kw.cpart, nb, st);
             prof_end(p, HELM_K_ORTHO, (j + 2) * vb, st, 8.0 * (j + 1) * N * nrhs);
-            launch_reduce_cpartials(p->d_cpart, nb, j + 1, p->d_h1, ld, nrhs, st);
+            launch_reduce_cpartials(kw.cpart, nb, j + 1, kw.h1, ld, nrhs, st);
             prof_begin(p, HELM_K_ORTHO, st);
-            launch_mupdate(p->d_V, vsk, N, j + 1, nullptr, p->d_h1, ld, -1.0, Vn, N, N, nrhs, p->d_active, p->d_rpart,
+            launch_mupdate(kw.V, vsk, N, j + 1, nullptr, kw.h1, ld, -1.0, Vn, N, N, nrhs, kw.active, kw.rpart,
                            nb, st);
             prof_end(p, HELM_K_ORTHO, (j + 3) * vb, st, 8.0 * (j + 1) * N * nrhs + 4.0 * N * nrhs);
-            launch_reduce_rows(p->d_rpart, nb, nrhs, p->d_rn + nrhs, 0, st);          // ||w'||^2
+            launch_reduce_rows(kw.rpart, nb, nrhs, kw.rn + nrhs, 0, st);          // ||w'||^2
             count_launch();
-            dgks_decide_kernel<<<(nrhs + 127) / 128, 128, 0, st>>>(p->d_rn, p->d_active, p->d_need, nrhs);
+            dgks_decide_kernel<<<(nrhs + 127) / 128, 128, 0, st>>>(kw.rn, kw.active, kw.need, nrhs);
             prof_begin(p, HELM_K_ORTHO, st);
-            launch_mdot(p->d_V, vsk, N, j + 1, Vn, N, N, nrhs, p->d_need, p->d_cpart, nb, st);
+            launch_mdot(kw.V, vsk, N, j + 1, Vn, N, N, nrhs, kw.need, kw.cpart, nb, st);
             prof_end(p, HELM_K_ORTHO, 0.0, st);
-            launch_reduce_cpartials(p->d_cpart, nb, j + 1, p->d_h2, ld, nrhs, st);
+            launch_reduce_cpartials(kw.cpart, nb, j + 1, kw.h2, ld, nrhs, st);
             prof_begin(p, HELM_K_ORTHO, st);
-            launch_mupdate(p->d_V, vsk, N, j + 1, nullptr, p->d_h2, ld, -1.0, Vn, N, N, nrhs, p->d_need, p->d_rpart,
+            launch_mupdate(kw.V, vsk, N, j + 1, nullptr, kw.h2, ld, -1.0, Vn, N, N, nrhs, kw.need, kw.rpart,
                            nb, st);
             prof_end(p, HELM_K_ORTHO, 0.0, st);
-            launch_reduce_rows(p->d_rpart, nb, nrhs, p->d_rn + 2 * nrhs, 0, st);      // ||w''||^2
+            launch_reduce_rows(kw.rpart, nb, nrhs, kw.rn + 2 * nrhs, 0, st);      // ||w''||^2
             count_launch();
-            dgks_norm_kernel<<<(nrhs + 127) / 128, 128, 0, st>>>(p->d_rn, p->d_need, p->d_rn + 3 * nrhs, nrhs);
+            dgks_norm_kernel<<<(nrhs + 127) / 128, 128, 0, st>>>(kw.rn, kw.need, kw.rn + 3 * nrhs, nrhs);
             count_launch();
-            add_cols_kernel<<<nrhs, 128, 0, st>>>(p->d_h1, p->d_h2, p->d_hsum, j + 1, nrhs, ld);
-            launch_hessenberg_step(p->d_H, ld, (long long)ld * m, p->d_cs, p->d_sn, p->d_g, ld, p->d_hsum, ld, p->d_rn + 3 * nrhs, j,
-                                   nrhs, p->d_active, p->d_est, p->d_invh, st);
-            launch_scale_vec(Vn, N, Vn, N, p->d_invh, N, nrhs, p->d_active, st);
+            add_cols_kernel<<<nrhs, 128, 0, st>>>(kw.h1, kw.h2, kw.hsum, j + 1, nrhs, ld);
+            launch_hessenberg_step(kw.H, ld, (long long)ld * m, kw.cs, kw.sn, kw.g, ld, kw.hsum, ld, kw.rn + 3 * nrhs, j,
+                                   nrhs, kw.active, kw.est, kw.invh, st);
+            launch_scale_vec(Vn, N, Vn, N, kw.invh, N, nrhs, kw.active, st);
             if (p->prof_on)
-                HELM_CUDA_TRY(cudaMemcpyAsync(need.data(), p->d_need, nrhs * sizeof(int), cudaMemcpyDeviceToHost, st));
+                HELM_CUDA_TRY(cudaMemcpyAsync(need.data(), kw.need, nrhs * sizeof(int), cudaMemcpyDeviceToHost, st));
         step_done:
             HELM_CUDA_TRY(cudaGetLastError());
-            HELM_CUDA_TRY(cudaMemcpyAsync(est.data(), p->d_est, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
+            HELM_CUDA_TRY(cudaMemcpyAsync(est.data(), kw.est, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
             HELM_CUDA_TRY(cudaMemcpyAsync(&dev_status, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
             HELM_CUDA_TRY(cudaStreamSynchronize(st));
-            if (dev_status != 0) return take_device_status(p, "gmres_solve");   // a bounded device wait expired
+            if (dev_status != 0) return take_device_status(p, who);   // a bounded device wait expired
             if (p->prof_on && !use_mgs) {
                 // the second Gram-Schmidt pass ran for the RHS that needed it
                 int nre = 0;
                 for (int k = 0; k < nrhs; ++k) nre += need[k];
                 prof_add(p, HELM_K_ORTHO, (2.0 * j + 5) * 16.0 * N * nre, (16.0 * (j + 1) + 4.0) * N * nre);
             }
-            bool still = false;
+            bool still = false, changed = false;
             for (int k = 0; k < nrhs; ++k) {
                 if (!active[k]) continue;
-                if (o.hist && iters[k] < o.maxit) o.hist[(size_t)k * o.maxit + iters[k]] = est[k] / bnorm[k];
+                if (hist && iters[k] < maxit) hist[(size_t)k * maxit + iters[k]] = est[k] / bnorm[k];
                 ++iters[k];
                 jcount[k] = j + 1;
-                if (est[k] <= o.tol * bnorm[k] || iters[k] >= o.maxit || !std::isfinite(est[k])) active[k] = 0;
+                if (est[k] <= tol * bnorm[k] || iters[k] >= maxit || !std::isfinite(est[k])) {
+                    active[k] = 0;
+                    changed = true;
+                }
                 still |= active[k] != 0;
             }
             if (!still) break;
-            HELM_CUDA_TRY(cudaMemcpyAsync(p->d_active, active.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, st));
-            HELM_CUDA_TRY(cudaStreamSynchronize(st));
+            // the host array is next written after the next step's synchronisation, which
+            // orders this copy before it
+            if (changed)
+                HELM_CUDA_TRY(cudaMemcpyAsync(kw.active, active.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, st));
         }
         // u += Z y with y = R^{-1} g
-        HELM_CUDA_TRY(cudaMemcpyAsync(p->d_jcount, jcount.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, st));
-        launch_hessenberg_solve(p->d_H, ld, (long long)ld * m, p->d_g, ld, p->d_jcount, p->d_y, ld, nrhs, st);
-        launch_mupdate(p->d_Z, vsk, N, m, p->d_jcount, p->d_y, ld, 1.0, u, N, N, nrhs, nullptr, nullptr, nb, st);
+        HELM_CUDA_TRY(cudaMemcpyAsync(kw.jcount, jcount.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, st));
+        launch_hessenberg_solve(kw.H, ld, (long long)ld * m, kw.g, ld, kw.jcount, kw.y, ld, nrhs, st);
+        launch_mupdate(kw.Z, vsk, N, m, kw.jcount, kw.y, ld, 1.0, x, N, N, nrhs, nullptr, nullptr, nb, st);
         HELM_CUDA_TRY(cudaGetLastError());
         HELM_CUDA_TRY(cudaStreamSynchronize(st));
     }
-    {
-        const helm_status ds = take_device_status(p, "gmres_solve");
-        if (ds != HELM_OK) return ds;
-    }
+    return take_device_status(p, who);
+}
+
+// ----------------------------------------------- interface Krylov preconditioner
+// z = M^{-1} r with the interface problem solved by Krylov iterations, the
+// paper's own formulation (Sections 3-5: GMRES on (I - S) g = b, preconditioned
+// by the SP or BSP sweep): liftings (source r, no incoming data) give b; g is
+// the FGMRES(inner_restart) iterate after at most inner_maxit steps or at
+// relative residual inner_tol, with the sweep of the schedule as its
+// preconditioner; the reconstruction (source r, incoming g) gives z.  The
+// interface vectors are FP64; S and the sweep run in the precision of the
+// factors.  With an exact interface solve M^{-1} = A^{-1}.
+template <typename R>
+static helm_status run_precond_iface_t(helm_problem* p, int sched, const double2* r, double2* z, int nrhs,
+                                       const helm_opts& o, cudaStream_t st) {
+    using T = Cx<R>;
+    const std::vector<StageDesc>& stg = p->sched[sched];
+    if (stg.size() < 2 || p->ntrace == 0) return run_precond(p, sched, r, z, nrhs, st);   // one subdomain
+    helm_status s = ensure_pc_ws(p, nrhs);
+    if (s != HELM_OK) return s;
+    const long long nt = p->ntrace;
+    s = ensure_kw(p->kwi, nrhs, o.inner_restart, nt, true);
+    if (s != HELM_OK) return s;
+    const PcWork w{{p->d_trace[0], p->d_trace[1], p->d_trace[2]}, p->d_yws, p->d_pc_norm, p->d_pc_partial,
+                   p->d_escr, p->d_r64};
+    T* tB = (T*)w.trace[BUF_B];
+    T* tX = (T*)w.trace[BUF_X];
+    T* tY = (T*)w.trace[BUF_Y];
+    const long long tot = nt * nrhs;
+    const PcCtx cx = precond_prologue<R>(p, w, r, nrhs, st);
+    // b: outgoing data of the liftings
+    s = run_stage_t<R>(p, w, cx, stg.front(), r, z, nrhs, st);
+    if (s != HELM_OK) return s;
+    launch_trace_to_c128<T>(tB, nullptr, 1.0, p->kwi.b, tot, st);
+    // (I - S) v: one interface stage over every subdomain writes S v - v into B
+    StageDesc sS = stg.front();
+    sS.iface = 1; sS.src = 0; sS.in0 = BUF_X; sS.in1 = BUF_NONE; sS.mask = 15;
+    sS.dst = BUF_B; sS.dst2 = BUF_NONE; sS.base = BUF_NONE; sS.sub = BUF_X; sS.final_ = 0;
+    KrylovOps ops;
+    // the interface stages read and write only the trace buffers: captured once as graphs
+    // (tags: 2 sched = the sweep, 2 sched + 1 = S)
+    ops.matvec = [&](const double2* v, double2* wv) -> helm_status {
+        launch_trace_from_c128<T>(v, tX, (T*)nullptr, tot, st);
+        helm_status q = run_captured(p, 2 * sched + 1, nrhs, st, [&](cudaStream_t cs) {
+            return run_stage_t<R>(p, w, cx, sS, r, z, nrhs, cs);
+        });
+        if (q != HELM_OK) return q;
+        launch_trace_to_c128<T>(tB, nullptr, -1.0, wv, tot, st);
+        return HELM_OK;
+    };
+    // the sweep of the schedule (its stages between lifting and reconstruction) on v:
+    // input in B (and X, where SP propagates from), result X (SP) or X + Y (BSP)
+    ops.precond = [&](const double2* v, double2* zv) -> helm_status {
+        launch_trace_from_c128<T>(v, tB, tX, tot, st);
+        helm_status q = run_captured(p, 2 * sched, nrhs, st, [&](cudaStream_t cs) {
+            for (size_t i = 1; i + 1 < stg.size(); ++i) {
+                helm_status q2 = run_stage_t<R>(p, w, cx, stg[i], r, z, nrhs, cs);
+                if (q2 != HELM_OK) return q2;
+            }
+            return HELM_OK;
+        });
+        if (q != HELM_OK) return q;
+        launch_trace_to_c128<T>(tX, sched == HELM_SCHED_BSP ? tY : (T*)nullptr, 1.0, zv, tot, st);
+        return HELM_OK;
+    };
+    ops.residual = [&](const double2* x, bool x_zero, double2* rv) -> helm_status {
+        if (x_zero) {
+            HELM_CUDA_TRY(cudaMemcpyAsync(rv, p->kwi.b, (size_t)tot * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+            return HELM_OK;
+        }
+        helm_status q = ops.matvec(x, rv);
+        if (q != HELM_OK) return q;
+        launch_sub_c128(p->kwi.b, rv, rv, tot, st);
+        return HELM_OK;
+    };
+    std::vector<double> bnorm(nrhs);
+    launch_norm2_partial(p->kwi.b, nt, nrhs, nt, p->kwi.rpart, p->kwi.nblk, st);
+    launch_reduce_rows(p->kwi.rpart, p->kwi.nblk, nrhs, p->kwi.rn, 1, st);
+    HELM_CUDA_TRY(cudaMemcpyAsync(bnorm.data(), p->kwi.rn, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
+    HELM_CUDA_TRY(cudaStreamSynchronize(st));
+    std::vector<int> it;
+    std::vector<double> rr;
+    s = fgmres_core(p, p->kwi, nt, nrhs, o.inner_restart, o.inner_maxit, o.inner_tol, bnorm, p->kwi.x, false,
+                    false, nullptr, ops, it, rr, "gmres_solve (interface iterations)", st);
+    if (s != HELM_OK) return s;
+    p->inner_steps += it.empty() ? 0 : *std::max_element(it.begin(), it.end());
+    // reconstruction with the incoming data g
+    launch_trace_from_c128<T>(p->kwi.x, tX, (T*)nullptr, tot, st);
+    StageDesc sR = stg.back();
+    sR.in0 = BUF_X; sR.in1 = BUF_NONE;
+    return run_stage_t<R>(p, w, cx, sR, r, z, nrhs, st);
+}
+
+static helm_status run_precond_iface(helm_problem* p, int sched, const double2* r, double2* z, int nrhs,
+                                     const helm_opts& o, cudaStream_t st) {
+    return p->prec == HELM_PREC_C64 ? run_precond_iface_t<float>(p, sched, r, z, nrhs, o, st)
+                                    : run_precond_iface_t<double>(p, sched, r, z, nrhs, o, st);
+}
+
+// FGMRES on A u = h^2 f for one chunk of right-hand sides
+static helm_status gmres_impl(helm_problem* p, const double2* f, double2* u, int nrhs, const helm_opts& o,
+                              helm_info* info, cudaStream_t st) {
+    const long long N = p->N();
+    helm_status s = ensure_kw(p->kw, nrhs, o.restart, N, false);
+    if (s != HELM_OK) return s;
+    s = ensure_pc_ws(p, nrhs);
+    if (s != HELM_OK) return s;
+    const double h2 = p->h * p->h;
+    // ||h^2 f||
+    std::vector<double> bnorm(nrhs);
+    launch_norm2_partial(f, N, nrhs, N, p->kw.rpart, p->kw.nblk, st);
+    launch_reduce_rows(p->kw.rpart, p->kw.nblk, nrhs, p->kw.rn, 1, st);
+    HELM_CUDA_TRY(cudaMemcpyAsync(bnorm.data(), p->kw.rn, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
+    HELM_CUDA_TRY(cudaStreamSynchronize(st));
+    for (auto& b : bnorm) b *= h2;
+    KrylovOps ops;
+    ops.residual = [&](const double2* x, bool, double2* rv) -> helm_status {
+        launch_residual(p->d_adiag, p->nx, p->ny, f, h2, x, rv, nrhs, nullptr, p->kw.rpart, p->kw.nblk, st);
+        return HELM_OK;
+    };
+    ops.matvec = [&](const double2* zv, double2* wv) -> helm_status {
+        prof_begin(p, HELM_K_MATVEC, st);
+        launch_matvec(p->d_adiag, p->nx, p->ny, zv, wv, nrhs, st);
+        prof_end(p, HELM_K_MATVEC, 48.0 * N * nrhs + 16.0 * N, st, 16.0 * N * nrhs);
+        return HELM_OK;
+    };
+    ops.precond = [&](const double2* v, double2* zv) -> helm_status {
+        if (o.inner_maxit > 0) return run_precond_iface(p, o.sched, v, zv, nrhs, o, st);
+        return o.use_graph ? run_precond_graph(p, o.sched, v, zv, nrhs, st) : run_precond(p, o.sched, v, zv, nrhs, st);
+    };
+    std::vector<int> iters;
+    std::vector<double> relres;
+    s = fgmres_core(p, p->kw, N, nrhs, o.restart, o.maxit, o.tol, bnorm, u, o.x0_given != 0, o.ortho == HELM_ORTHO_MGS,
+                    o.hist, ops, iters, relres, "gmres_solve", st);
+    if (s != HELM_OK) return s;
     bool ok = true;
     for (int k = 0; k < nrhs; ++k) {
         if (info) { info[k].iters = iters[k]; info[k].relres = relres[k]; }
@@ -1270,13 +1501,17 @@ extern "C" helm_status gmres_solve(helm_problem* p, const helm_c128* f, helm_c12
     if (!(o.tol > 0)) return arg_error("gmres_solve: tol must be > 0");
     if (o.sched != HELM_SCHED_BSP && o.sched != HELM_SCHED_SP) return arg_error("gmres_solve: unknown schedule");
     if (o.ortho != HELM_ORTHO_MGS && o.ortho != HELM_ORTHO_CGS2) return arg_error("gmres_solve: unknown ortho");
+    if (o.inner_maxit < 0) return arg_error("gmres_solve: inner_maxit must be >= 0");
+    if (o.inner_maxit > 0 && (o.inner_restart < 1 || o.inner_restart > 500))
+        return arg_error("gmres_solve: inner_restart must be in 1..500");
+    if (o.inner_maxit > 0 && !(o.inner_tol > 0)) return arg_error("gmres_solve: inner_tol must be > 0");
     // Right-hand sides are solved in chunks whose Krylov workspace, (2 restart + 1)
     // complex128 fields per RHS plus the preconditioner workspace, fits in 60% of
     // the device memory that is free now (already-allocated workspace counts as free).
     const long long N = p->N();
     size_t freeb = 0, totalb = 0;
     HELM_CUDA_TRY(cudaMemGetInfo(&freeb, &totalb));
-    const size_t held = (size_t)p->kw_nrhs * ((size_t)2 * p->kw_restart + 1) * N * sizeof(double2);
+    const size_t held = (size_t)p->kw.nrhs * ((size_t)2 * p->kw.restart + 1) * N * sizeof(double2);
     const size_t per_rhs = ((size_t)2 * o.restart + 1) * N * sizeof(double2) + (size_t)N * 2 * sizeof(double2);
     long long fit = (long long)((0.6 * (double)(freeb + held)) / (double)per_rhs);
     if (fit < 1) {
@@ -1288,7 +1523,7 @@ extern "C" helm_status gmres_solve(helm_problem* p, const helm_c128* f, helm_c12
     helm_status worst = HELM_OK;
     for (int k0 = 0; k0 < nrhs; k0 += chunk) {
         const int nk = std::min(chunk, nrhs - k0);
-        if (chunk < nrhs && p->kw_nrhs > nk) free_krylov(p);        // never hold more than one chunk
+        if (chunk < nrhs && p->kw.nrhs > nk) free_krylov(p);        // never hold more than one chunk
         const helm_status s = gmres_impl(p, (const double2*)f + (size_t)k0 * N, (double2*)u + (size_t)k0 * N, nk, o,
                                          info ? info + k0 : nullptr, (cudaStream_t)stream);
         if (s == HELM_ERR_NO_CONVERGENCE) worst = s;
@@ -1343,8 +1578,8 @@ extern "C" helm_status misfit_grad(helm_problem* p, const helm_c128* f, int nsrc
     if (s != HELM_OK) return s;
     launch_gradient(U, p->d_L, p->d_m2, p->nx, p->ny, p->h, p->omega, nsrc, grad_m2, st);
     HELM_CUDA_TRY(cudaGetLastError());
-    launch_reduce_rows(p->d_jpart, nsrc, 1, p->d_rn, 0, st);
-    HELM_CUDA_TRY(cudaMemcpyAsync(misfit, p->d_rn, sizeof(double), cudaMemcpyDeviceToHost, st));
+    launch_reduce_rows(p->d_jpart, nsrc, 1, p->kw.rn, 0, st);
+    HELM_CUDA_TRY(cudaMemcpyAsync(misfit, p->kw.rn, sizeof(double), cudaMemcpyDeviceToHost, st));
     HELM_CUDA_TRY(cudaStreamSynchronize(st));
     return HELM_OK;
 }

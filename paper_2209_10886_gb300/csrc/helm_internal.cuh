@@ -223,6 +223,13 @@ void launch_hessenberg_solve(const double2* H, int ldh, long long hstride, const
 void launch_mask_copy(double2* dst, const double2* src, long long n, int nrhs, const int* active,
                       cudaStream_t st);
 void launch_sqrt_inplace(double* v, int n, cudaStream_t st);
+// interface vectors (T = the trace buffers' complex type): out = sign (a + b) (b optional);
+// out (and out2) = in rounded to T; r = b - w
+template <typename T>
+void launch_trace_to_c128(const T* a, const T* b, double sign, double2* out, long long total, cudaStream_t st);
+template <typename T>
+void launch_trace_from_c128(const double2* in, T* out, T* out2, long long total, cudaStream_t st);
+void launch_sub_c128(const double2* b, const double2* w, double2* r, long long total, cudaStream_t st);
 // out[k*n + i] = complex64(src[k*n + i] * scale[k])
 void launch_to_c64_scaled(const double2* src, const double* scale, float2* out, long long n, int nrhs,
                           cudaStream_t st);

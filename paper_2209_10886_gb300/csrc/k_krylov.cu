@@ -5,6 +5,8 @@
 // kernel adds them in a fixed order.
 #include "helm_internal.cuh"
 
+#include <algorithm>
+
 namespace {
 
 constexpr int VT = 256;
@@ -384,3 +386,57 @@ void launch_to_c64_scaled(const double2* src, const double* scale, float2* out, 
     count_launch();
     to_c64_scaled_kernel<<<1216, 256, 0, st>>>(src, scale, out, n, nrhs);
 }
+
+// ------------------------------------------------- interface (trace) vectors
+// out128 = sign * (a + b) for n * nrhs values, b optional (T: the trace buffers' type)
+template <typename T>
+__global__ void trace_to_c128_kernel(const T* __restrict__ a, const T* __restrict__ b, double sign,
+                                     double2* __restrict__ out, long long total) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        double2 v = to_c128(a[i]);
+        if (b) { const double2 w = to_c128(b[i]); v.x += w.x; v.y += w.y; }
+        out[i] = make_double2(sign * v.x, sign * v.y);
+    }
+}
+// out (and out2, optional) = in rounded to T
+template <typename T>
+__global__ void trace_from_c128_kernel(const double2* __restrict__ in, T* __restrict__ out, T* __restrict__ out2,
+                                       long long total) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const T f = from_c128<T>(in[i]);
+        out[i] = f;
+        if (out2) out2[i] = f;
+    }
+}
+// r = b - w
+__global__ void sub_c128_kernel(const double2* __restrict__ b, const double2* __restrict__ w, double2* __restrict__ r,
+                                long long total) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double2 x = b[i], y = w[i];
+        r[i] = make_double2(x.x - y.x, x.y - y.y);
+    }
+}
+
+static int small_grid(long long total) { return (int)std::min<long long>(1216, (total + 255) / 256 + 1); }
+
+template <typename T>
+void launch_trace_to_c128(const T* a, const T* b, double sign, double2* out, long long total, cudaStream_t st) {
+    count_launch();
+    trace_to_c128_kernel<T><<<small_grid(total), 256, 0, st>>>(a, b, sign, out, total);
+}
+template <typename T>
+void launch_trace_from_c128(const double2* in, T* out, T* out2, long long total, cudaStream_t st) {
+    count_launch();
+    trace_from_c128_kernel<T><<<small_grid(total), 256, 0, st>>>(in, out, out2, total);
+}
+void launch_sub_c128(const double2* b, const double2* w, double2* r, long long total, cudaStream_t st) {
+    count_launch();
+    sub_c128_kernel<<<small_grid(total), 256, 0, st>>>(b, w, r, total);
+}
+template void launch_trace_to_c128<float2>(const float2*, const float2*, double, double2*, long long, cudaStream_t);
+template void launch_trace_to_c128<double2>(const double2*, const double2*, double, double2*, long long, cudaStream_t);
+template void launch_trace_from_c128<float2>(const double2*, float2*, float2*, long long, cudaStream_t);
+template void launch_trace_from_c128<double2>(const double2*, double2*, double2*, long long, cudaStream_t);

@@ -33,7 +33,8 @@ class HelmError(RuntimeError):
 class HelmOpts(ctypes.Structure):
     _fields_ = [("restart", ctypes.c_int), ("maxit", ctypes.c_int), ("tol", ctypes.c_double),
                 ("x0_given", ctypes.c_int), ("sched", ctypes.c_int), ("use_graph", ctypes.c_int),
-                ("hist", ctypes.POINTER(ctypes.c_double)), ("ortho", ctypes.c_int)]
+                ("hist", ctypes.POINTER(ctypes.c_double)), ("ortho", ctypes.c_int),
+                ("inner_maxit", ctypes.c_int), ("inner_restart", ctypes.c_int), ("inner_tol", ctypes.c_double)]
 
 
 class HelmSetupOpts(ctypes.Structure):
@@ -184,7 +185,7 @@ class Problem:
         return Au
 
     def solve(self, f, u=None, restart=50, maxit=1000, tol=1e-6, sched="BSP", x0=None, history=False,
-              stream=None, raise_on_noconv=True, use_graph=False):
+              stream=None, raise_on_noconv=True, use_graph=False, inner_maxit=0, inner_restart=100, inner_tol=1e-4):
         """Solve A u = h^2 f (FP64 FGMRES); returns (u, [(iters, relres)], history or None)."""
         f = _as_fields(f, self.N, "f")
         nrhs = f.numel() // self.N
@@ -193,7 +194,8 @@ class Problem:
             u.copy_(x0)
         hist = (ctypes.c_double * (maxit * nrhs))() if history else None
         o = default_opts(restart=restart, maxit=maxit, tol=tol, sched=sched, x0_given=int(x0 is not None),
-                         use_graph=int(bool(use_graph)))
+                         use_graph=int(bool(use_graph)), inner_maxit=int(inner_maxit),
+                         inner_restart=int(inner_restart), inner_tol=float(inner_tol))
         if hist is not None:
             o.hist = ctypes.cast(hist, ctypes.POINTER(ctypes.c_double))
         info = (HelmInfo * nrhs)()
@@ -277,6 +279,14 @@ def launch_count() -> int:
     L = lib()
     L.helm_launch_count.restype = ctypes.c_longlong
     return int(L.helm_launch_count())
+
+
+def inner_steps(problem: "Problem") -> int:
+    """Interface Krylov steps taken inside the preconditioner applications of a problem."""
+    L = lib()
+    L.helm_inner_steps.restype = ctypes.c_longlong
+    L.helm_inner_steps.argtypes = [_vp]
+    return int(L.helm_inner_steps(problem._h))
 
 
 def profile(problem: "Problem", on: bool = True):

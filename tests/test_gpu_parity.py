@@ -194,6 +194,45 @@ def test_gmres_multi_rhs_and_initial_guess(H):
 
 
 @pytest.mark.parametrize("prec", ["c128", "c64"])
+@pytest.mark.parametrize("sched", ["BSP", "SP"])
+def test_interface_krylov_gmres_matches_direct_solve(H, prec, sched):
+    """inner_maxit > 0: the preconditioner solves the interface problem (I - S) g = b by
+    FGMRES with the sweep as its preconditioner (the paper's formulation); the outer
+    FP64 FGMRES on the volume still reaches the true residual and the direct solution."""
+    w = CASES["uneven_4x3"]()
+    p, _ = make(H, w, prec)
+    A = assemble_operator(w.n, w.h, w.omega, w.m2).tocsc()
+    f = W.random_complex((2, w.N), 22)
+    s0 = H.inner_steps(p)
+    u, info, _ = p.solve(cuda(f), tol=1e-9, restart=30, maxit=200, sched=sched, inner_maxit=60, inner_tol=1e-3)
+    steps = H.inner_steps(p) - s0
+    u = u.cpu().numpy()
+    lu = spla.splu(A)
+    for k in range(2):
+        ref = lu.solve(w.h ** 2 * f[k])
+        rr = np.linalg.norm(w.h ** 2 * f[k] - A @ u[k]) / np.linalg.norm(w.h ** 2 * f[k])
+        print(f"uneven_4x3 {prec} {sched} interface Krylov rhs{k}: outer its {info[k][0]}, inner steps {steps}, "
+              f"true relres {rr:.2e}, rel {rel(u[k], ref):.2e}")
+        assert info[k][1] <= 1e-9 and rr <= 1.01e-9
+        assert rel(u[k], ref) <= 1e-5
+        assert info[k][0] <= 12                     # a few outer steps: the inner solve does the work
+    assert steps > 0
+    p.close()
+
+
+def test_interface_krylov_without_boundary_operators(H):
+    """The interface operator S and the sweep by full local solves (no K)."""
+    w = CASES["tiny_2x2"]()
+    p = H.Problem(w.n, w.n, w.h, w.omega, cuda(w.m2, torch.float64), w.N1, w.N2, w.xcuts, w.ycuts,
+                  boundary_operators=False).factor("c64")
+    A = assemble_operator(w.n, w.h, w.omega, w.m2).tocsc()
+    u, info, _ = p.solve(cuda(w.f), tol=1e-9, restart=30, maxit=100, inner_maxit=40, inner_tol=1e-4)
+    ref = spla.spsolve(A, w.h ** 2 * w.f[0])
+    assert info[0][1] <= 1e-9 and rel(u.cpu().numpy()[0], ref) <= 1e-5
+    p.close()
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
 def test_graph_replay_gives_the_same_solve(H, prec):
     """use_graph: the preconditioner replayed from captured CUDA graphs runs the same
     kernels on the same data, so the iteration counts and residuals are identical."""

@@ -140,3 +140,20 @@ def test_tensor_core_fgmres_matches_direct_solve(H):
         assert info[k][1] <= 1e-9 and rr <= 1.01e-9
         assert rel(u[k], ref) <= 1e-5
     p.close()
+
+
+def test_interface_krylov_with_tensor_core_stages(H):
+    """20 RHS: liftings and reconstructions on the tensor cores, the interface
+    problem solved by FGMRES inside the preconditioner."""
+    w = CASES["uneven_4x3"]()
+    p = make(H, w)
+    A = assemble_operator(w.n, w.h, w.omega, w.m2).tocsc()
+    f = W.random_complex((20, w.N), 23)
+    u, info, _ = p.solve(cuda(f), tol=1e-9, restart=30, maxit=300, inner_maxit=60, inner_tol=1e-3)
+    u = u.cpu().numpy()
+    lu = spla.splu(A)
+    for k in (0, 19):
+        ref = lu.solve(w.h ** 2 * f[k])
+        print(f"uneven_4x3 TF32 interface Krylov rhs{k}: outer its {info[k][0]}, rel {rel(u[k], ref):.2e}")
+        assert info[k][1] <= 1e-9 and rel(u[k], ref) <= 1e-5
+    p.close()

@@ -149,6 +149,20 @@ def test_exact_interface_solve_reproduces_global_solution(n, N1, N2, xc, yc, tra
     assert _rel(z, spla.spsolve(A.tocsc(), r)) < 1e-12
 
 
+@pytest.mark.parametrize("kind", ["SP", "BSP"])
+def test_interface_krylov_preconditioner_tends_to_the_inverse(kind):
+    """GMRES on (I - S) g = b (the paper's formulation) to a tight tolerance gives
+    the exact interface solution, so the nested preconditioner reproduces A^{-1} r;
+    with a loose tolerance it is a (nonlinear) approximation no better than that."""
+    w, A, dec, sw = _problem(30, 3, 2, medium="layered", xcuts=[0, 11, 19, 30], ycuts=[0, 13, 30], seed=2)
+    r = W.random_complex(w.N, 17)
+    ref = spla.spsolve(A.tocsc(), r)
+    z = sw.precondition_interface_krylov(r, kind, tol=1e-13, restart=200, maxit=400)
+    assert _rel(z, ref) < 1e-10
+    loose = sw.precondition_interface_krylov(r, kind, tol=1e-2, restart=200, maxit=400)
+    assert 1e-10 < _rel(loose, ref) < 1.0
+
+
 def test_single_subdomain_is_a_direct_solve():
     """N1 = N2 = 1: M^{-1} = A^{-1} and FGMRES converges in one iteration."""
     w, A, dec, sw = _problem(33, 1, 1, medium="layered", seed=5)
