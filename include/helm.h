@@ -293,7 +293,10 @@ long long helm_launch_count(void);
 long long helm_inner_steps(const helm_problem* p);
 
 /* Enable (on != 0) or disable per-launch event timing on handle p; enabling
- * resets the statistics.  Timing adds two event records per launch. */
+ * (or disabling) resets the statistics.  Timing adds two event records per
+ * launch; a stage sequence replayed from a CUDA graph (the sweeps and S inside
+ * the interface Krylov iterations) is bracketed as a whole and its time,
+ * launches, bytes and flops are attributed to its kernel class. */
 helm_status helm_profile(helm_problem* p, int on);
 
 /* Statistics of one kernel class (synchronises the device to read the events). */

@@ -224,12 +224,17 @@ struct helm_problem {
     // per-kernel-class event timing (helm_profile)
     struct KProf {
         std::vector<cudaEvent_t> a, b;
-        size_t used = 0;
+        size_t used = 0;             // event pairs recorded
+        long long kernels = 0;       // kernel launches inside them
         double bytes = 0;
         double flops = 0;
     };
     KProf prof[5];
     int prof_on = 0;
+    // while a launch sequence is captured into a graph: its accounting per class
+    int prof_capture = 0;
+    double cap_bytes[5] = {0, 0, 0, 0, 0}, cap_flops[5] = {0, 0, 0, 0, 0};
+    long long cap_kernels[5] = {0, 0, 0, 0, 0};
 
     // preconditioner applications captured as CUDA graphs (gmres_solve with use_graph):
     // one executable graph per (schedule, nrhs, r, z), replayed on the caller's stream
@@ -239,6 +244,9 @@ struct helm_problem {
         void* z;
         cudaGraphExec_t exec;
         long long kernels;           // kernel launches one replay performs
+        int cls = -1;                // kernel class of the sequence (profiling), -1: none
+        long long cls_kernels = 0;   // its launches, algorithmic bytes and flops per replay
+        double cls_bytes = 0, cls_flops = 0;
     };
     std::vector<PcGraph> graphs;
     cudaStream_t cap_stream = nullptr;
@@ -249,7 +257,7 @@ struct helm_problem {
 
 // event pair around one launch of class k (no-op when profiling is off)
 static void prof_begin(helm_problem* p, int k, cudaStream_t st) {
-    if (!p->prof_on) return;
+    if (!p->prof_on || p->prof_capture) return;
     auto& q = p->prof[k];
     if (q.used == q.a.size()) {
         cudaEvent_t e1, e2;
@@ -262,9 +270,16 @@ static void prof_begin(helm_problem* p, int k, cudaStream_t st) {
 }
 static void prof_end(helm_problem* p, int k, double bytes, cudaStream_t st, double flops = 0.0) {
     if (!p->prof_on) return;
+    if (p->prof_capture) {                       // accounting of a sequence being captured
+        p->cap_bytes[k] += bytes;
+        p->cap_flops[k] += flops;
+        p->cap_kernels[k] += 1;
+        return;
+    }
     auto& q = p->prof[k];
     cudaEventRecord(q.b[q.used], st);
     ++q.used;
+    ++q.kernels;
     q.bytes += bytes;
     q.flops += flops;
 }
@@ -277,7 +292,7 @@ static void prof_add(helm_problem* p, int k, double bytes, double flops) {
 
 extern "C" helm_status helm_profile(helm_problem* p, int on) {
     if (!p) { set_error("helm_profile: NULL handle"); return HELM_ERR_ARG; }
-    for (auto& q : p->prof) { q.used = 0; q.bytes = 0; q.flops = 0; }
+    for (auto& q : p->prof) { q.used = 0; q.kernels = 0; q.bytes = 0; q.flops = 0; }
     p->prof_on = on != 0;
     return HELM_OK;
 }
@@ -293,7 +308,7 @@ extern "C" helm_status helm_profile_read(helm_problem* p, int k, helm_kstat* out
         cudaEventElapsedTime(&t, q.a[i], q.b[i]);
         ms += t;
     }
-    out->launches = (long long)q.used;
+    out->launches = q.kernels;
     out->ms = ms;
     out->bytes = q.bytes;
     out->flops = q.flops;
@@ -998,23 +1013,36 @@ static helm_status run_precond_graph(helm_problem* p, int sched, const double2* 
 // Plain launches while profiling (the per-launch events need them).
 static helm_status run_captured(helm_problem* p, int tag, int nrhs, cudaStream_t st,
                                 const std::function<helm_status(cudaStream_t)>& seq) {
-    if (p->prof_on) return seq(st);
     const void* key = reinterpret_cast<const void*>((intptr_t)(tag + 1));
-    for (const auto& g : p->graphs)
-        if (g.sched == -1 && g.nrhs == nrhs && g.r == key) {
-            HELM_CUDA_TRY(cudaGraphLaunch(g.exec, st));
-            count_launch((int)g.kernels);
-            return HELM_OK;
+    auto replay = [&](const helm_problem::PcGraph& g) -> helm_status {
+        // while profiling, one event pair brackets the whole sequence of its class
+        if (g.cls >= 0) prof_begin(p, g.cls, st);
+        HELM_CUDA_TRY(cudaGraphLaunch(g.exec, st));
+        if (g.cls >= 0 && p->prof_on) {
+            prof_end(p, g.cls, g.cls_bytes, st, g.cls_flops);
+            p->prof[g.cls].kernels += g.cls_kernels - 1;
         }
+        count_launch((int)g.kernels);
+        return HELM_OK;
+    };
+    for (const auto& g : p->graphs)
+        if (g.sched == -1 && g.nrhs == nrhs && g.r == key) return replay(g);
     if (!p->cap_stream) {
         HELM_CUDA_TRY(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
         HELM_CUDA_TRY(cudaEventCreateWithFlags(&p->cap_ev, cudaEventDisableTiming));
     }
     const long long before = helm_launch_count();
+    // capture with the per-class accounting switched on (no events are recorded)
+    const int prof_was = p->prof_on;
+    p->prof_on = 1;
+    p->prof_capture = 1;
+    for (int k = 0; k < 5; ++k) { p->cap_bytes[k] = p->cap_flops[k] = 0; p->cap_kernels[k] = 0; }
     HELM_CUDA_TRY(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeRelaxed));
     helm_status s = seq(p->cap_stream);
     cudaGraph_t graph = nullptr;
     const cudaError_t ec = cudaStreamEndCapture(p->cap_stream, &graph);
+    p->prof_capture = 0;
+    p->prof_on = prof_was;
     const long long kernels = helm_launch_count() - before;
     uncount_launch(kernels);
     if (s != HELM_OK) { if (graph) cudaGraphDestroy(graph); return s; }
@@ -1023,10 +1051,12 @@ static helm_status run_captured(helm_problem* p, int tag, int nrhs, cudaStream_t
     const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
     if (ei != cudaSuccess) return cuda_status(ei, "instantiating a stage-sequence graph");
-    p->graphs.push_back({-1, nrhs, key, nullptr, exec, kernels});
-    HELM_CUDA_TRY(cudaGraphLaunch(exec, st));
-    count_launch((int)kernels);
-    return HELM_OK;
+    helm_problem::PcGraph g{-1, nrhs, key, nullptr, exec, kernels};
+    for (int k = 0; k < 5; ++k)
+        if (p->cap_kernels[k] > 0 && (g.cls < 0 || p->cap_kernels[k] > g.cls_kernels)) { g.cls = k; g.cls_kernels = p->cap_kernels[k]; }
+    for (int k = 0; k < 5; ++k) { g.cls_bytes += p->cap_bytes[k]; g.cls_flops += p->cap_flops[k]; }
+    p->graphs.push_back(g);
+    return replay(p->graphs.back());
 }
 
 extern "C" helm_status precond_apply(helm_problem* p, int sched, const helm_c128* r, helm_c128* z, int nrhs,
