@@ -202,6 +202,9 @@ struct helm_problem {
     int tc_split = 0;                // 3: hi + lo TF32 pairs, 1: TF32 alone
     int tc_all_off[2] = {0, 0}, tc_all_n[2] = {0, 0};   // all subdomains by tile count, in d_stage_subs
     long long etot = 0;              // boundary slots 2 (mx + my) summed over the subdomains
+    SweepStage* d_sweep = nullptr;   // interface stages of each schedule for the sweep kernel
+    int sweep_off[2] = {0, 0}, sweep_n[2] = {0, 0};
+    unsigned* d_sweep_bar = nullptr; // its grid-barrier words
 
     // preconditioner workspace
     int ws_nrhs = 0;
@@ -215,6 +218,7 @@ struct helm_problem {
     // Krylov workspaces: the volume FGMRES and the interface FGMRES nested in the preconditioner
     KrylovWS kw, kwi;
     long long inner_steps = 0;       // interface Krylov steps taken inside the preconditioner (all calls)
+    int persistent = 0;              // gmres_solve option: sweeps in the persistent sweep kernel
 
     // adjoint workspace
     double2 *d_res = nullptr, *d_fadj = nullptr, *d_U = nullptr, *d_L = nullptr;
@@ -363,6 +367,7 @@ extern "C" void helm_default_opts(helm_opts* o) {
     o->inner_maxit = 0;
     o->inner_restart = 100;
     o->inner_tol = 1e-4;
+    o->persistent = 0;
 }
 
 extern "C" long long helm_inner_steps(const helm_problem* p) { return p ? p->inner_steps : 0; }
@@ -549,6 +554,35 @@ extern "C" helm_status helm_setup(int n_x, int n_y, double h, double omega, cons
         for (size_t k = 0; k < ids.size(); ++k) ids[k] = (int)k;
         tc_classes(ids, p->tc_all_off, p->tc_all_n);
     }
+    // the interface stages of each schedule (between lifting and reconstruction) for the
+    // persistent sweep kernel, when they are all boundary-operator stages
+    std::vector<SweepStage> sweep_tab;
+    for (int sc = 0; sc < 2; ++sc) {
+        const auto& stg = p->sched[sc];
+        p->sweep_off[sc] = (int)sweep_tab.size();
+        p->sweep_n[sc] = 0;
+        bool all_iface = stg.size() > 2;
+        for (size_t i = 1; i + 1 < stg.size(); ++i) all_iface = all_iface && stg[i].iface;
+        if (!all_iface) continue;
+        for (size_t i = 1; i + 1 < stg.size(); ++i) {
+            const StageDesc& sd = stg[i];
+            SweepStage t{};
+            t.sub_off = sd.sub_off;
+            t.nsub = (int)sd.subs.size();
+            t.in0 = sd.in0; t.in1 = sd.in1; t.mask = sd.mask;
+            t.dst = sd.dst; t.dst2 = sd.dst2; t.base = sd.base; t.sub = sd.sub;
+            t.max_rows = 0;
+            for (int id : sd.subs) {
+                const SubDev& d = p->subs[id].dev;
+                int rows = 0;
+                for (int sde = 0; sde < 4; ++sde)
+                    if ((sd.mask & (1 << sde)) && d.bo[sde] >= 0) rows += (sde == SW || sde == SE) ? d.my : d.mx;
+                t.max_rows = std::max(t.max_rows, rows);
+            }
+            sweep_tab.push_back(t);
+        }
+        p->sweep_n[sc] = (int)(sweep_tab.size() - p->sweep_off[sc]);
+    }
 
     // device tables
     helm_status status = HELM_OK;
@@ -590,6 +624,12 @@ extern "C" helm_status helm_setup(int n_x, int n_y, double h, double omega, cons
         if ((e = dalloc(p->d_err, 1)) != cudaSuccess) { fail(e, "alloc status word"); break; }
         if ((e = cudaMemset(p->d_err, 0, sizeof(int))) != cudaSuccess) { fail(e, "clear status word"); break; }
         cudaMemcpy(p->d_stage_subs, all_stage_subs.data(), all_stage_subs.size() * sizeof(int), cudaMemcpyHostToDevice);
+        if (!sweep_tab.empty()) {
+            if ((e = dalloc(p->d_sweep, sweep_tab.size())) != cudaSuccess) { fail(e, "alloc sweep table"); break; }
+            cudaMemcpy(p->d_sweep, sweep_tab.data(), sweep_tab.size() * sizeof(SweepStage), cudaMemcpyHostToDevice);
+        }
+        if ((e = dalloc(p->d_sweep_bar, 2)) != cudaSuccess) { fail(e, "alloc sweep barrier"); break; }
+        if ((e = cudaMemset(p->d_sweep_bar, 0, 2 * sizeof(unsigned))) != cudaSuccess) { fail(e, "clear sweep barrier"); break; }
         if ((e = cudaDeviceSynchronize()) != cudaSuccess) { fail(e, "setup kernels"); break; }
     } while (0);
     dfree(d_xcut); dfree(d_ycut); dfree(d_subid); dfree(d_ssub); dfree(d_sside); dfree(d_soff); dfree(d_slen);
@@ -607,6 +647,7 @@ extern "C" helm_status helm_destroy(helm_problem* p) {
     free_adj(p);
     dfree(p->d_m2); dfree(p->d_adiag); dfree(p->d_dloc); dfree(p->d_subtab);
     dfree(p->d_tc128); dfree(p->d_tc64); dfree(p->d_stage_subs); dfree(p->d_err);
+    dfree(p->d_sweep); dfree(p->d_sweep_bar);
     for (auto& q : p->prof) {
         for (auto e : q.a) cudaEventDestroy(e);
         for (auto e : q.b) cudaEventDestroy(e);
@@ -635,6 +676,10 @@ static helm_status take_device_status(helm_problem* p, const char* who) {
     HELM_CUDA_TRY(cudaMemcpy(&v, p->d_err, sizeof(int), cudaMemcpyDeviceToHost));
     if (v == 0) return HELM_OK;
     HELM_CUDA_TRY(cudaMemset(p->d_err, 0, sizeof(int)));
+    // a grid barrier that gave up may have left its arrival count behind
+    if (p->d_sweep_bar) HELM_CUDA_TRY(cudaMemset(p->d_sweep_bar, 0, 2 * sizeof(unsigned)));
+    if (p->kw.mgs_bar) HELM_CUDA_TRY(cudaMemset(p->kw.mgs_bar, 0, 2 * sizeof(unsigned)));
+    if (p->kwi.mgs_bar) HELM_CUDA_TRY(cudaMemset(p->kwi.mgs_bar, 0, 2 * sizeof(unsigned)));
     set_error(std::string(who) + ": a device wait timed out; results of this call are invalid");
     return HELM_ERR_TIMEOUT;
 }
@@ -818,6 +863,54 @@ struct PcWork {
     void* r64;
 };
 
+// algorithmic bytes and flops of one interface stage: the rows of K it applies,
+// the incoming data it reads, the outgoing data (and base / sub) it moves
+static void iface_accounting(const helm_problem* p, const StageDesc& sd, int nrhs, double sT, double& bytes,
+                             double& flops) {
+    for (int id : sd.subs) {
+        const SubDev& d = p->subs[id].dev;
+        double rows = 0;
+        for (int sde = 0; sde < 4; ++sde)
+            if ((sd.mask & (1 << sde)) && d.bo[sde] >= 0) rows += (sde == SW || sde == SE) ? d.my : d.mx;
+        const double io = d.Lb * sT * ((sd.in0 >= 0) + (sd.in1 >= 0)) +
+                          rows * sT * (1 + (sd.dst2 >= 0) + (sd.base >= 0) + (sd.sub >= 0));
+        bytes += rows * d.Lb * sT + io * nrhs;
+        flops += 8.0 * rows * d.Lb * nrhs;
+    }
+}
+
+// The interface stages of a schedule (all but the lifting and the reconstruction)
+// in the persistent sweep kernel; false when it does not apply (no boundary
+// operators, or no cooperative launch), and the caller runs the stages one by one.
+template <typename R>
+static bool run_sweep_persistent(helm_problem* p, const PcWork& w, int sched, int nrhs, cudaStream_t st,
+                                 helm_status& status) {
+    using T = Cx<R>;
+    if (!p->persistent || !p->d_K || !p->d_sweep || p->sweep_n[sched] == 0) return false;
+    const int grid = sweep_grid<R>(nrhs, p->max_Lb);
+    if (grid <= 0) return false;
+    IfaceArgs<R> a{};
+    a.subtab = p->d_subtab;
+    a.subs = p->d_stage_subs;
+    a.nrhs = nrhs;
+    a.ntrace = p->ntrace;
+    a.K = (const T*)p->d_K;
+    a.tc = sizeof(R) == 4 ? (const TraceCoef<T>*)p->d_tc64 : (const TraceCoef<T>*)p->d_tc128;
+    for (int b = 0; b < 3; ++b) a.bufs[b] = w.trace[b];
+    double bytes = 0, flops = 0;
+    if (p->prof_on) {
+        const auto& stg = p->sched[sched];
+        for (size_t i = 1; i + 1 < stg.size(); ++i) iface_accounting(p, stg[i], nrhs, sizeof(T), bytes, flops);
+    }
+    prof_begin(p, HELM_K_TRACE, st);
+    const cudaError_t e = launch_sweep<R>(a, p->d_sweep + p->sweep_off[sched], p->sweep_n[sched], p->max_Lb, grid,
+                                          p->d_sweep_bar, p->d_err, st);
+    prof_end(p, HELM_K_TRACE, bytes, st, flops);
+    if (p->prof_on && !p->prof_capture) p->prof[HELM_K_TRACE].kernels += p->sweep_n[sched] - 1;
+    status = e == cudaSuccess ? HELM_OK : cuda_status(e, "sweep kernel launch");
+    return true;
+}
+
 // per-application constants of the preconditioner
 struct PcCtx {
     const double* rinv = nullptr;    // complex64: 1/||r|| per RHS (the source is scaled to unit norm)
@@ -864,19 +957,7 @@ static helm_status run_stage_t(helm_problem* p, const PcWork& w, const PcCtx& cx
         ia.mask = sd.mask;
         ia.dst = B(sd.dst); ia.dst2 = B(sd.dst2); ia.base = B(sd.base); ia.sub = B(sd.sub);
         double bytes = 0, flops = 0;
-        if (p->prof_on) {
-            const double sT = sizeof(T);
-            for (int id : sd.subs) {
-                const SubDev& d = p->subs[id].dev;
-                double rows = 0;
-                for (int sde = 0; sde < 4; ++sde)
-                    if ((sd.mask & (1 << sde)) && d.bo[sde] >= 0) rows += (sde == SW || sde == SE) ? d.my : d.mx;
-                const double io = d.Lb * sT * ((sd.in0 >= 0) + (sd.in1 >= 0)) +
-                                  rows * sT * (1 + (sd.dst2 >= 0) + (sd.base >= 0) + (sd.sub >= 0));
-                bytes += rows * d.Lb * sT + io * nrhs;
-                flops += 8.0 * rows * d.Lb * nrhs;
-            }
-        }
+        if (p->prof_on) iface_accounting(p, sd, nrhs, sizeof(T), bytes, flops);
         prof_begin(p, HELM_K_TRACE, st);
         cudaError_t e = launch_iface<R>(ia, (int)sd.subs.size(), 2 * (p->max_mx + p->max_my), p->max_Lb, st);
         prof_end(p, HELM_K_TRACE, bytes, st, flops);
@@ -953,8 +1034,17 @@ template <typename R>
 static helm_status run_precond_t(helm_problem* p, const PcWork& w, int sched, const double2* r, double2* z, int nrhs,
                                  cudaStream_t st) {
     const PcCtx cx = precond_prologue<R>(p, w, r, nrhs, st);
-    for (const StageDesc& sd : p->sched[sched]) {
-        const helm_status s = run_stage_t<R>(p, w, cx, sd, r, z, nrhs, st);
+    const std::vector<StageDesc>& stg = p->sched[sched];
+    for (size_t i = 0; i < stg.size(); ++i) {
+        if (i == 1 && stg.size() > 2) {
+            helm_status s = HELM_OK;
+            if (run_sweep_persistent<R>(p, w, sched, nrhs, st, s)) {
+                if (s != HELM_OK) return s;
+                i = stg.size() - 2;                  // continue with the reconstruction
+                continue;
+            }
+        }
+        const helm_status s = run_stage_t<R>(p, w, cx, stg[i], r, z, nrhs, st);
         if (s != HELM_OK) return s;
     }
     return HELM_OK;
@@ -1423,7 +1513,13 @@ static helm_status run_precond_iface_t(helm_problem* p, int sched, const double2
     // input in B (and X, where SP propagates from), result X (SP) or X + Y (BSP)
     ops.precond = [&](const double2* v, double2* zv) -> helm_status {
         launch_trace_from_c128<T>(v, tB, tX, tot, st);
-        helm_status q = run_captured(p, 2 * sched, nrhs, st, [&](cudaStream_t cs) {
+        helm_status q = HELM_OK;
+        if (run_sweep_persistent<R>(p, w, sched, nrhs, st, q)) {
+            if (q != HELM_OK) return q;
+            launch_trace_to_c128<T>(tX, sched == HELM_SCHED_BSP ? tY : (T*)nullptr, 1.0, zv, tot, st);
+            return HELM_OK;
+        }
+        q = run_captured(p, 2 * sched, nrhs, st, [&](cudaStream_t cs) {
             for (size_t i = 1; i + 1 < stg.size(); ++i) {
                 helm_status q2 = run_stage_t<R>(p, w, cx, stg[i], r, z, nrhs, cs);
                 if (q2 != HELM_OK) return q2;
@@ -1501,8 +1597,10 @@ static helm_status gmres_impl(helm_problem* p, const double2* f, double2* u, int
     };
     std::vector<int> iters;
     std::vector<double> relres;
+    p->persistent = o.persistent != 0;
     s = fgmres_core(p, p->kw, N, nrhs, o.restart, o.maxit, o.tol, bnorm, u, o.x0_given != 0, o.ortho == HELM_ORTHO_MGS,
                     o.hist, ops, iters, relres, "gmres_solve", st);
+    p->persistent = 0;
     if (s != HELM_OK) return s;
     bool ok = true;
     for (int k = 0; k < nrhs; ++k) {

@@ -142,6 +142,14 @@ template <typename R> struct IfaceArgs {
     const T* gin0; const T* gin1;
     int mask;
     T* dst; T* dst2; const T* base; const T* sub;
+    void* bufs[3];             // sweep kernel: the interface buffers B, X, Y the stages name
+};
+
+// one interface stage of a sweep run by the persistent sweep kernel (device table)
+struct SweepStage {
+    int sub_off, nsub;         // its subdomains in the stage-list array
+    int in0, in1, mask, dst, dst2, base, sub;   // Buf ids (-1: none), as in StageDesc
+    int max_rows;              // the most output rows (masked-side points) of one of its subdomains
 };
 
 // ------------------------------------------------------------ launch count
@@ -193,6 +201,12 @@ cudaError_t launch_tc_basis(const StageArgs<float>& a, const float* XT, int MT, 
                             cudaStream_t st);
 template <typename R>
 cudaError_t launch_iface(const IfaceArgs<R>& a, int nactive, int max_rows, int max_Lb, cudaStream_t st);
+// a whole sweep (nstages interface stages, in order) in one cooperative launch of `grid`
+// CTAs (sweep_grid: the co-resident count, 0 when unavailable); bar: two zeroed words
+template <typename R> int sweep_grid(int nrhs, int max_Lb);
+template <typename R>
+cudaError_t launch_sweep(const IfaceArgs<R>& a, const SweepStage* stages, int nstages, int max_Lb, int grid,
+                         unsigned* bar, int* err, cudaStream_t st);
 // krylov / vector kernels
 void launch_matvec(const double2* adiag, int nx, int ny, const double2* u, double2* Au, int nrhs,
                    cudaStream_t st);

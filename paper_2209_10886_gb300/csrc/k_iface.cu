@@ -11,30 +11,45 @@
 // (-d_{n_{i,j}} - T) u_i, Eq. subPbm), i.e. one application of the paper's
 // local scattering operators S_{m(j,i),m(i,k)} of subdomain i (Section 3).
 // K is built once per factorisation by batched multi-RHS block solves
-// (k_stage.cu, basis mode).  This kernel gathers the incoming traces, runs the
-// GEMV with a warp per output row, applies the transmission and scatters the
-// results into the neighbours' slots.
+// (k_tc.cu / k_stage.cu, basis mode).  One work item (a subdomain, a block of
+// RB output rows, a block of NR right-hand sides) gathers the incoming traces,
+// runs the GEMV with a warp per output row, applies the transmission and
+// scatters the results into the neighbours' slots.  iface_kernel runs one stage
+// with one item per CTA; sweep_kernel runs a whole sweep (its stages in order)
+// as one cooperative launch, items distributed over the CTAs and a bounded grid
+// barrier between stages, so a stage costs a barrier instead of a launch.
 #include "helm_internal.cuh"
+
+#include <algorithm>
 
 namespace {
 
 constexpr int IT = 256;      // threads per CTA
-constexpr int RB = 16;       // output rows per CTA
+constexpr int RB = 16;       // output rows per work item
+constexpr long long SWEEP_WAIT = 2000000000LL;   // cycles (~1 s) before a grid barrier gives up
 
-template <typename R, int NR>
-__global__ void __launch_bounds__(IT) iface_kernel(IfaceArgs<R> a) {
+// LDCG: read through L2 only (data another SM wrote earlier in the same launch)
+template <typename T, bool LDCG>
+__device__ __forceinline__ T ldg_(const T* p) {
+    if constexpr (LDCG) return __ldcg(p);
+    else return *p;
+}
+
+// one work item of an interface stage: subdomain a.subs[item_sub], output rows
+// [row_block*RB, +RB) of its masked sides, RHS [rhs_block*NR, +NR)
+template <typename R, int NR, bool LDCG>
+__device__ void iface_item(const IfaceArgs<R>& a, int item_sub, int row_block, int rhs_block, unsigned char* smem_raw) {
     using T = Cx<R>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const SubDev sd = a.subtab[a.subs[blockIdx.x]];
+    const SubDev sd = a.subtab[a.subs[item_sub]];
     const int Lb = sd.Lb;
-    const int rhs0 = blockIdx.z * NR;
+    const int rhs0 = rhs_block * NR;
     const int nr = min(NR, a.nrhs - rhs0);
     const int len[4] = {sd.my, sd.my, sd.mx, sd.mx};
     // output rows: points of the masked interface sides, in the order W, E, S, N
     int rcount = 0;
     for (int s = 0; s < 4; ++s)
         if ((a.mask & (1 << s)) && sd.bo[s] >= 0) rcount += len[s];
-    const int row0 = blockIdx.y * RB;
+    const int row0 = row_block * RB;
     if (row0 >= rcount) return;
 
     T* graw = reinterpret_cast<T*>(smem_raw);      // [NR][Lb] incoming data
@@ -47,8 +62,8 @@ __global__ void __launch_bounds__(IT) iface_kernel(IfaceArgs<R> a) {
         T G = czero<T>(), Gs = czero<T>();
         if (k < nr) {
             const long long o = (long long)(rhs0 + k) * a.ntrace + ti;
-            if (a.gin0) G = a.gin0[o];
-            if (a.gin1) G = cadd(G, a.gin1[o]);
+            if (a.gin0) G = ldg_<T, LDCG>(a.gin0 + o);
+            if (a.gin1) G = cadd(G, ldg_<T, LDCG>(a.gin1 + o));
             Gs = cmul(G, a.tc[ti].cin);
         }
         graw[idx] = G;
@@ -90,12 +105,78 @@ __global__ void __launch_bounds__(IT) iface_kernel(IfaceArgs<R> a) {
             for (int k = 0; k < nr; ++k) {
                 T out = cfma(c.cb, acc[k], cmul(c.ca, graw[k * Lb + krow]));
                 const long long o = (long long)(rhs0 + k) * a.ntrace + to;
-                if (a.base) out = cadd(out, a.base[o]);
-                if (a.sub) out = csub(out, a.sub[o]);
+                if (a.base) out = cadd(out, ldg_<T, LDCG>(a.base + o));
+                if (a.sub) out = csub(out, ldg_<T, LDCG>(a.sub + o));
                 a.dst[o] = out;
                 if (a.dst2) a.dst2[o] = out;
             }
         }
+    }
+    __syncthreads();                                // the shared gather is reused by the next item
+}
+
+template <typename R, int NR>
+__global__ void __launch_bounds__(IT) iface_kernel(IfaceArgs<R> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    iface_item<R, NR, false>(a, blockIdx.x, blockIdx.y, blockIdx.z, smem_raw);
+}
+
+// grid-wide barrier of a cooperative launch; false (and HELM_ERR_TIMEOUT in err) when it expired
+__device__ bool sweep_barrier(unsigned* bar, int* err, volatile int* sflag) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned* gen = bar + 1;
+        const unsigned g = *gen;
+        __threadfence();
+        if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            const long long t0 = clock64();
+            while (*gen == g) {
+                if (clock64() - t0 > SWEEP_WAIT) {
+                    atomicExch(err, (int)HELM_ERR_TIMEOUT);
+                    *sflag = 1;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return *sflag == 0;
+}
+
+template <typename R, int NR>
+__global__ void __launch_bounds__(IT) sweep_kernel(IfaceArgs<R> base, const SweepStage* stages, int nstages,
+                                                   unsigned* bar, int* err) {
+    using T = Cx<R>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int sflag;
+    if (threadIdx.x == 0) sflag = 0;
+    __syncthreads();
+    T* const* bufs = reinterpret_cast<T* const*>(base.bufs);
+    const int rblocks = (base.nrhs + NR - 1) / NR;
+    for (int s = 0; s < nstages; ++s) {
+        const SweepStage& st = stages[s];
+        IfaceArgs<R> a = base;
+        a.subs = base.subs + st.sub_off;
+        a.gin0 = st.in0 >= 0 ? bufs[st.in0] : nullptr;
+        a.gin1 = st.in1 >= 0 ? bufs[st.in1] : nullptr;
+        a.mask = st.mask;
+        a.dst = st.dst >= 0 ? bufs[st.dst] : nullptr;
+        a.dst2 = st.dst2 >= 0 ? bufs[st.dst2] : nullptr;
+        a.base = st.base >= 0 ? bufs[st.base] : nullptr;
+        a.sub = st.sub >= 0 ? bufs[st.sub] : nullptr;
+        const int rowb = (st.max_rows + RB - 1) / RB;
+        const int items = st.nsub * rowb * rblocks;
+        for (int it = blockIdx.x; it < items; it += gridDim.x) {
+            const int sub_i = it / (rowb * rblocks);
+            const int rem = it - sub_i * rowb * rblocks;
+            iface_item<R, NR, true>(a, sub_i, rem / rblocks, rem % rblocks, smem_raw);
+        }
+        if (s + 1 < nstages && !sweep_barrier(bar, err, &sflag)) return;
     }
 }
 
@@ -111,7 +192,46 @@ cudaError_t launch_nr(const IfaceArgs<R>& a, int nactive, int max_rows, int max_
     return cudaGetLastError();
 }
 
+template <typename R, int NR>
+cudaError_t launch_sweep_nr(const IfaceArgs<R>& a, const SweepStage* stages, int nstages, int max_Lb, int grid,
+                            unsigned* bar, int* err, cudaStream_t st) {
+    using T = Cx<R>;
+    size_t smem = 2 * (size_t)NR * max_Lb * sizeof(T);
+    cudaError_t e = cudaFuncSetAttribute(sweep_kernel<R, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    IfaceArgs<R> aa = a;
+    void* args[] = {&aa, (void*)&stages, &nstages, &bar, &err};
+    count_launch();
+    return cudaLaunchCooperativeKernel((const void*)sweep_kernel<R, NR>, dim3(grid), dim3(IT), args, smem, st);
+}
+
 }  // namespace
+
+// CTAs of the sweep kernel that are co-resident on the device (0: cooperative launch unavailable)
+template <typename R>
+int sweep_grid(int nrhs, int max_Lb) {
+    int dev = 0, sms = 0, coop = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    const size_t smem = 2 * (size_t)(nrhs >= 4 ? 4 : nrhs >= 2 ? 2 : 1) * max_Lb * sizeof(Cx<R>);
+    cudaError_t e;
+    if (nrhs >= 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, sweep_kernel<R, 4>, IT, smem);
+    else if (nrhs >= 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, sweep_kernel<R, 2>, IT, smem);
+    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, sweep_kernel<R, 1>, IT, smem);
+    if (e != cudaSuccess || per < 1) return 0;
+    return sms;                       // one CTA per SM: the grid barrier costs one arrival per CTA
+}
+
+template <typename R>
+cudaError_t launch_sweep(const IfaceArgs<R>& a, const SweepStage* stages, int nstages, int max_Lb, int grid,
+                         unsigned* bar, int* err, cudaStream_t st) {
+    if (nstages == 0 || a.nrhs == 0) return cudaSuccess;
+    if (grid <= 0) return cudaErrorNotSupported;
+    if (a.nrhs >= 4) return launch_sweep_nr<R, 4>(a, stages, nstages, max_Lb, grid, bar, err, st);
+    if (a.nrhs >= 2) return launch_sweep_nr<R, 2>(a, stages, nstages, max_Lb, grid, bar, err, st);
+    return launch_sweep_nr<R, 1>(a, stages, nstages, max_Lb, grid, bar, err, st);
+}
 
 template <typename R>
 cudaError_t launch_iface(const IfaceArgs<R>& a, int nactive, int max_rows, int max_Lb, cudaStream_t st) {
@@ -125,3 +245,9 @@ cudaError_t launch_iface(const IfaceArgs<R>& a, int nactive, int max_rows, int m
 
 template cudaError_t launch_iface<float>(const IfaceArgs<float>&, int, int, int, cudaStream_t);
 template cudaError_t launch_iface<double>(const IfaceArgs<double>&, int, int, int, cudaStream_t);
+template int sweep_grid<float>(int, int);
+template int sweep_grid<double>(int, int);
+template cudaError_t launch_sweep<float>(const IfaceArgs<float>&, const SweepStage*, int, int, int, unsigned*, int*,
+                                         cudaStream_t);
+template cudaError_t launch_sweep<double>(const IfaceArgs<double>&, const SweepStage*, int, int, int, unsigned*, int*,
+                                          cudaStream_t);

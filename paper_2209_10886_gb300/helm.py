@@ -34,7 +34,8 @@ class HelmOpts(ctypes.Structure):
     _fields_ = [("restart", ctypes.c_int), ("maxit", ctypes.c_int), ("tol", ctypes.c_double),
                 ("x0_given", ctypes.c_int), ("sched", ctypes.c_int), ("use_graph", ctypes.c_int),
                 ("hist", ctypes.POINTER(ctypes.c_double)), ("ortho", ctypes.c_int),
-                ("inner_maxit", ctypes.c_int), ("inner_restart", ctypes.c_int), ("inner_tol", ctypes.c_double)]
+                ("inner_maxit", ctypes.c_int), ("inner_restart", ctypes.c_int), ("inner_tol", ctypes.c_double),
+                ("persistent", ctypes.c_int)]
 
 
 class HelmSetupOpts(ctypes.Structure):
@@ -185,7 +186,8 @@ class Problem:
         return Au
 
     def solve(self, f, u=None, restart=50, maxit=1000, tol=1e-6, sched="BSP", x0=None, history=False,
-              stream=None, raise_on_noconv=True, use_graph=False, inner_maxit=0, inner_restart=100, inner_tol=1e-4):
+              stream=None, raise_on_noconv=True, use_graph=False, inner_maxit=0, inner_restart=100, inner_tol=1e-4,
+              persistent=False):
         """Solve A u = h^2 f (FP64 FGMRES); returns (u, [(iters, relres)], history or None)."""
         f = _as_fields(f, self.N, "f")
         nrhs = f.numel() // self.N
@@ -195,7 +197,7 @@ class Problem:
         hist = (ctypes.c_double * (maxit * nrhs))() if history else None
         o = default_opts(restart=restart, maxit=maxit, tol=tol, sched=sched, x0_given=int(x0 is not None),
                          use_graph=int(bool(use_graph)), inner_maxit=int(inner_maxit),
-                         inner_restart=int(inner_restart), inner_tol=float(inner_tol))
+                         inner_restart=int(inner_restart), inner_tol=float(inner_tol), persistent=int(bool(persistent)))
         if hist is not None:
             o.hist = ctypes.cast(hist, ctypes.POINTER(ctypes.c_double))
         info = (HelmInfo * nrhs)()

@@ -220,6 +220,21 @@ def test_interface_krylov_gmres_matches_direct_solve(H, prec, sched):
     p.close()
 
 
+@pytest.mark.parametrize("sched", ["BSP", "SP"])
+def test_persistent_sweep_gives_the_same_solve(H, sched):
+    """persistent: the interface stages of each sweep in one cooperative launch with grid
+    barriers; the same stages in the same order, so the same iterates."""
+    w = CASES["uneven_4x3"]()
+    p, _ = make(H, w, "c64")
+    f = cuda(W.random_complex((2, w.N), 24))
+    u0, i0, _ = p.solve(f, tol=1e-9, restart=30, maxit=200, sched=sched, inner_maxit=60, inner_tol=1e-3)
+    u1, i1, _ = p.solve(f, tol=1e-9, restart=30, maxit=200, sched=sched, inner_maxit=60, inner_tol=1e-3,
+                        persistent=True)
+    assert [i[0] for i in i0] == [i[0] for i in i1]
+    assert rel(u1.cpu().numpy(), u0.cpu().numpy()) <= 1e-9
+    p.close()
+
+
 def test_interface_krylov_without_boundary_operators(H):
     """The interface operator S and the sweep by full local solves (no K)."""
     w = CASES["tiny_2x2"]()

@@ -88,16 +88,20 @@ def test_differentiation_gradient_matches_central_differences(H, diff_case):
     assert worst <= 1e-4
 
 
-def test_batching_preconditioner_matches_oracle_at_full_size(H):
+# complex64 on the CUDA cores: bar 5e-4; 3xTF32 on the tensor cores: bar 2e-3 (the
+# derivation is in test_gpu_tensor_cores.py)
+@pytest.mark.parametrize("tensor_cores,bar", [(False, 5e-4), ("3xtf32", 2e-3)])
+def test_batching_preconditioner_matches_oracle_at_full_size(H, tensor_cores, bar):
     w = W.workload("batching", nrhs=64)
-    p = H.Problem(w.n, w.n, w.h, w.omega, cuda(w.m2, torch.float64), w.N1, w.N2, w.xcuts, w.ycuts).factor("c64")
+    p = H.Problem(w.n, w.n, w.h, w.omega, cuda(w.m2, torch.float64), w.N1, w.N2, w.xcuts, w.ycuts,
+                  tensor_cores=tensor_cores).factor("c64")
     z = p.precond_apply(cuda(w.f)).cpu().numpy()                # all 64 sources in one application
     dec = Decomposition(w.n, w.h, w.omega, w.m2, w.xcuts, w.ycuts)
     sw = Sweeper(dec)
     for s in (0, 37, 63):
         e = rel(z[s], sw.precondition(w.f[s], "BSP"))
-        print(f"batching source {s}: c64 preconditioner rel {e:.2e}")
-        assert e <= 5e-4
+        print(f"batching source {s}: c64 preconditioner ({tensor_cores or 'CUDA cores'}) rel {e:.2e}")
+        assert e <= bar
     p.close()
 
 
