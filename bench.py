@@ -71,6 +71,8 @@ def parse():
                          "FGMRES with the sweep as preconditioner (at most this many steps); 0: one sweep")
     ap.add_argument("--inner-restart", type=int, default=30)
     ap.add_argument("--inner-tol", type=float, default=1e-2)
+    ap.add_argument("--inner-fp64", action="store_true",
+                    help="FP64 interface Krylov vectors with complex64 factors (default: complex64 vectors)")
     ap.add_argument("--tc-scale", type=float, default=0.5,
                     help="scale s of the optimized Robin parameter T_e = (i - 1) s sqrt(kappa_e pi / (2 h))")
     ap.add_argument("--graph", action="store_true",
@@ -90,7 +92,8 @@ ORACLE_RESTART = 150
 
 def inner_kw(args):
     """Interface-Krylov options of Problem.solve."""
-    return dict(inner_maxit=args.inner_maxit, inner_restart=args.inner_restart, inner_tol=args.inner_tol)
+    return dict(inner_maxit=args.inner_maxit, inner_restart=args.inner_restart, inner_tol=args.inner_tol,
+                inner_fp64=args.inner_fp64)
 
 
 def precond_only(args):
@@ -527,7 +530,8 @@ def gpu_arm(args):
             "transmission": f"optimized, scale {args.tc_scale:g}", "iterations": iters[-1][0], "relres": relres,
             "tensor_cores": args.tensor_cores, "tc_min_rhs": args.tc_min_rhs, "cuda_graph": args.graph,
             "interface_krylov": ({"inner_maxit": args.inner_maxit, "inner_restart": args.inner_restart,
-                                  "inner_tol": args.inner_tol, "inner_steps_per_solve": inner_per_solve}
+                                  "inner_tol": args.inner_tol, "inner_steps_per_solve": inner_per_solve,
+                                  "vectors": "c128" if (args.inner_fp64 or args.prec == "c128") else "c64"}
                                  if args.inner_maxit > 0 else None),
             "relres_host_check": check, "factor_ms": factor_ms, "factor_bytes": p.info()["factor_bytes"],
             "l2": ("inputs larger than L2: every timed solve streams the 1.07 GB of factors in each lifting "

@@ -133,16 +133,18 @@ typedef struct {
     double* hist;       /* optional host buffer of maxit*nrhs doubles: the Arnoldi
                            residual estimate of RHS k after step j at hist[k*maxit+j] */
     int ortho;          /* Arnoldi orthogonalisation, all FP64: HELM_ORTHO_MGS (default;
-                           used when n_x*n_y fits the persistent kernel, else CGS2) or
-                           HELM_ORTHO_CGS2 */
+                           used when n_x*n_y fits the persistent kernel, else CGS2),
+                           HELM_ORTHO_CGS2 or HELM_ORTHO_CGS2_SPLIT; the interface
+                           iterations use CGS2 (CGS2_SPLIT when that is chosen) */
     int inner_maxit;    /* 0 (default): each preconditioner application runs the sweep
                            once (g = sweep(b) on the interface).  > 0: the interface
                            problem (I - S) g = b of the paper (Sections 3-5) is solved by
                            FP64 FGMRES preconditioned by the sweep, at most inner_maxit
                            steps per application, inner_restart per cycle, stopping at
                            ||b - (I - S) g|| <= inner_tol ||b|| (classical Gram-Schmidt
-                           with reorthogonalisation on the ntrace-long vectors); the
-                           outer FGMRES stays on the volume system */
+                           with reorthogonalisation on the ntrace-long vectors, their
+                           precision as inner_fp64 says); the outer FGMRES stays FP64
+                           on the volume system */
     int inner_restart;  /* default 100 */
     double inner_tol;   /* default 1e-4 */
     int persistent;     /* 1: the interface stages of every sweep run as one cooperative
@@ -150,14 +152,25 @@ typedef struct {
                            operators); 0 (default): one launch per stage, replayed from a
                            CUDA graph inside the interface iterations (measured faster on
                            GB300: 48 vs 39 ms of interface stages per 1023^2 solve) */
+    int inner_fp64;     /* interface iterations (inner_maxit > 0) with complex64 factors:
+                           0 (default) keeps the interface Krylov vectors in complex64
+                           (FP32 vector arithmetic; reductions, Gram-Schmidt coefficients
+                           and the least-squares problem stay FP64), which suits an
+                           inner_tol well above the FP32 roundoff; 1 keeps them FP64.
+                           With complex128 factors they are always FP64 */
 } helm_opts;
 
 /* Orthogonalisation of the Arnoldi vectors.
  * HELM_ORTHO_MGS:  modified Gram-Schmidt in one persistent kernel per step
  *                  (8 FP64 FMA per element per basis vector).
  * HELM_ORTHO_CGS2: classical Gram-Schmidt, a second pass when the first
- *                  cancelled more than half of the norm (16 FMA per element). */
-enum { HELM_ORTHO_MGS = 0, HELM_ORTHO_CGS2 = 1 };
+ *                  cancelled more than half of the norm (16 FMA per element).
+ *                  When a slice of the vector per SM fits in shared memory
+ *                  (up to ~6000 values per SM), the passes, the norm and the
+ *                  Givens update run as one cooperative launch per step.
+ * HELM_ORTHO_CGS2_SPLIT: the same arithmetic as separate reduction kernels
+ *                  (about 15 launches per step). */
+enum { HELM_ORTHO_MGS = 0, HELM_ORTHO_CGS2 = 1, HELM_ORTHO_CGS2_SPLIT = 2 };
 
 typedef struct {
     int iters;          /* Arnoldi steps taken */

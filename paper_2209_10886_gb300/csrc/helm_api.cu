@@ -19,6 +19,13 @@ long long mgs_max_n(int grid);
 cudaError_t launch_mgs(const double2* V, long long vsk, long long vsr, double2* w, int nvec, long long n, int nrhs,
                        const int* active, double2* hcol, int ldh, double* hnorm, double2* partial, unsigned* bar,
                        int* err, int grid, cudaStream_t st);
+template <typename VT>
+int cgs2_grid(long long n, int max_j);
+template <typename VT>
+cudaError_t launch_cgs2_step(const VT* V, long long vsk, long long vsr, int j, long long n, int nrhs,
+                             const int* active, double2* hsum, int ldh, double* hnorm, int* need, double2* H, int ldH,
+                             long long hs, double2* cs, double2* sn, double2* g, int ldg, double* est, double* invh,
+                             double2* partial, unsigned* bar, int* err, int grid, cudaStream_t st);
 
 // ------------------------------------------------------------ launch count
 #include <atomic>
@@ -368,6 +375,7 @@ extern "C" void helm_default_opts(helm_opts* o) {
     o->inner_restart = 100;
     o->inner_tol = 1e-4;
     o->persistent = 0;
+    o->inner_fp64 = 0;
 }
 
 extern "C" long long helm_inner_steps(const helm_problem* p) { return p ? p->inner_steps : 0; }
@@ -1251,7 +1259,9 @@ static helm_status ensure_kw(KrylovWS& w, int nrhs, int m, long long n, bool wit
     {
         const int g = mgs_grid();
         if (g > 0) {
-            chk(dalloc(w.mgs_part, (size_t)2 * g));
+            // two halves of per-CTA partials: one value (modified Gram-Schmidt) or j + 2
+            // values (the fused classical step) per CTA
+            chk(dalloc(w.mgs_part, (size_t)2 * g * (m + 2)));
             chk(dalloc(w.mgs_bar, (size_t)2));
             if (e == cudaSuccess) e = cudaMemset(w.mgs_bar, 0, 2 * sizeof(unsigned));
         }
@@ -1299,32 +1309,47 @@ __global__ void dgks_norm_kernel(const double* n2, const int* need, double* hnor
 }
 
 // The operator, preconditioner and residual of one FGMRES: vectors of n values
-// per RHS, RHS k at offset k*n.
+// per RHS, RHS k at offset k*n, of type VT (double2, or float2 for the interface
+// iterations with complex64 factors).
+template <typename VT>
 struct KrylovOps {
-    std::function<helm_status(const double2* x, bool x_zero, double2* r)> residual;   // r = b - A x
-    std::function<helm_status(const double2* v, double2* z)> precond;                // z = M^{-1} v
-    std::function<helm_status(const double2* z, double2* w)> matvec;                 // w = A z
+    std::function<helm_status(const VT* x, bool x_zero, VT* r)> residual;   // r = b - A x
+    std::function<helm_status(const VT* v, VT* z)> precond;                // z = M^{-1} v
+    std::function<helm_status(const VT* z, VT* w)> matvec;                 // w = A z
 };
 
-// Restarted right-preconditioned flexible GMRES (all arithmetic FP64): x is the
-// initial guess on entry (zero unless x0_given) and the iterate on exit; bnorm
-// holds ||b|| per RHS; iters / relres receive the Arnoldi steps and the true
-// relative residual ||b - A x|| / ||b|| at exit.  Modified Gram-Schmidt in the
-// persistent kernel when use_mgs, else classical Gram-Schmidt with selective
-// reorthogonalisation.  `who` names the caller in error messages.
+// Restarted right-preconditioned flexible GMRES: x is the initial guess on entry
+// (zero unless x0_given) and the iterate on exit; bnorm holds ||b|| per RHS;
+// iters / relres receive the Arnoldi steps and the true relative residual
+// ||b - A x|| / ||b|| at exit.  The vectors are VT (double2: all arithmetic FP64;
+// float2: vector arithmetic FP32, reductions, coefficients and the least-squares
+// problem FP64; the workspace arrays are allocated as double2 and hold either).
+// Modified Gram-Schmidt in the persistent kernel (ortho HELM_ORTHO_MGS, FP64
+// vectors), else classical Gram-Schmidt with selective reorthogonalisation, fused
+// into one launch per step unless HELM_ORTHO_CGS2_SPLIT.  `who` names the caller
+// in error messages.
+template <typename VT>
 static helm_status fgmres_core(helm_problem* p, KrylovWS& kw, long long n, int nrhs, int m, int maxit, double tol,
-                               const std::vector<double>& bnorm, double2* x, bool x0_given, bool use_mgs_req,
-                               double* hist, const KrylovOps& ops, std::vector<int>& iters,
+                               const std::vector<double>& bnorm, VT* x, bool x0_given, int ortho,
+                               double* hist, const KrylovOps<VT>& ops, std::vector<int>& iters,
                                std::vector<double>& relres, const char* who, cudaStream_t st) {
+    constexpr bool fp64 = std::is_same<VT, double2>::value;
+    VT* const KV = reinterpret_cast<VT*>(kw.V);
+    VT* const KZ = reinterpret_cast<VT*>(kw.Z);
     const long long N = n;
     helm_status s = HELM_OK;
     const int nb = kw.nblk;
     const long long vsk = (long long)nrhs * N;    // V_j of RHS k at V + j*vsk + k*N
     const int ld = m + 1;
     // modified Gram-Schmidt needs the vector to fit the persistent kernel's registers
-    const int mgs_grid_n = use_mgs_req ? mgs_grid() : 0;
+    const int mgs_grid_n = (fp64 && ortho == HELM_ORTHO_MGS) ? mgs_grid() : 0;
     const bool use_mgs = mgs_grid_n > 0 && N <= mgs_max_n(mgs_grid_n) && kw.mgs_part != nullptr;
-    if (!x0_given) HELM_CUDA_TRY(cudaMemsetAsync(x, 0, (size_t)nrhs * N * sizeof(double2), st));
+    // classical Gram-Schmidt: one fused launch per step when a slice of the vector per CTA
+    // fits in shared memory, else the reduction kernels one by one
+    const int cgs2_grid_n =
+        (!use_mgs && ortho != HELM_ORTHO_CGS2_SPLIT && kw.mgs_part != nullptr && kw.restart >= m) ? cgs2_grid<VT>(N, m)
+                                                                                                : 0;
+    if (!x0_given) HELM_CUDA_TRY(cudaMemsetAsync(x, 0, (size_t)nrhs * N * sizeof(VT), st));
 
     std::vector<double> rn(nrhs), est(nrhs);
     std::vector<int> need(nrhs, 0);
@@ -1337,10 +1362,10 @@ static helm_status fgmres_core(helm_problem* p, KrylovWS& kw, long long n, int n
     bool x_zero = !x0_given;
     while (true) {
         // r = b - A x into V_0, beta = ||r||
-        s = ops.residual(x, x_zero, kw.V);
+        s = ops.residual(x, x_zero, KV);
         if (s != HELM_OK) return s;
         x_zero = false;
-        launch_norm2_partial(kw.V, N, nrhs, N, kw.rpart, nb, st);
+        launch_norm2_partial(KV, N, nrhs, N, kw.rpart, nb, st);
         launch_reduce_rows(kw.rpart, nb, nrhs, kw.rn, 1, st);
         HELM_CUDA_TRY(cudaMemcpyAsync(rn.data(), kw.rn, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
         HELM_CUDA_TRY(cudaStreamSynchronize(st));
@@ -1364,17 +1389,17 @@ static helm_status fgmres_core(helm_problem* p, KrylovWS& kw, long long n, int n
             }
             HELM_CUDA_TRY(cudaMemcpyAsync(kw.g, g0.data(), g0.size() * sizeof(double2), cudaMemcpyHostToDevice, st));
             HELM_CUDA_TRY(cudaMemcpyAsync(kw.invh, inv.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, st));
-            launch_scale_vec(kw.V, N, kw.V, N, kw.invh, N, nrhs, kw.active, st);
+            launch_scale_vec(KV, N, KV, N, kw.invh, N, nrhs, kw.active, st);
             HELM_CUDA_TRY(cudaStreamSynchronize(st));    // host vectors above go out of scope
         }
         for (int j = 0; j < m; ++j) {
-            double2* Vj = kw.V + (long long)j * vsk;
-            double2* Vn = kw.V + (long long)(j + 1) * vsk;
-            double2* Zj = kw.Z + (long long)j * vsk;
+            VT* Vj = KV + (long long)j * vsk;
+            VT* Vn = KV + (long long)(j + 1) * vsk;
+            VT* Zj = KZ + (long long)j * vsk;
             // z_j = M^{-1} v_j ; w = A z_j
             s = ops.precond(Vj, Zj);
             if (s != HELM_OK) return s;
-            const double vb = 16.0 * N * nrhs;   // bytes of one field for all RHS
+            const double vb = (double)sizeof(VT) * N * nrhs;   // bytes of one field for all RHS
             s = ops.matvec(Zj, Vn);
             if (s != HELM_OK) return s;
             if (use_mgs) {
@@ -1382,7 +1407,8 @@ static helm_status fgmres_core(helm_problem* p, KrylovWS& kw, long long n, int n
                 int nact = 0;
                 for (int k = 0; k < nrhs; ++k) nact += active[k];
                 prof_begin(p, HELM_K_ORTHO, st);
-                cudaError_t e = launch_mgs(kw.V, vsk, N, Vn, j + 1, N, nrhs, kw.active, kw.hsum, ld,
+                // (FP64 vectors only: use_mgs is false for float2)
+                cudaError_t e = launch_mgs(kw.V, vsk, N, reinterpret_cast<double2*>(Vn), j + 1, N, nrhs, kw.active, kw.hsum, ld,
                                            kw.rn + 3 * nrhs, kw.mgs_part, kw.mgs_bar, p->d_err, mgs_grid_n, st);
                 prof_end(p, HELM_K_ORTHO, (j + 3) * 16.0 * N * nact, st, (16.0 * (j + 1) + 4.0) * N * nact);
                 if (e != cudaSuccess) return cuda_status(e, "modified Gram-Schmidt launch");
@@ -1390,26 +1416,42 @@ static helm_status fgmres_core(helm_problem* p, KrylovWS& kw, long long n, int n
                                        kw.rn + 3 * nrhs, j, nrhs, kw.active, kw.est, kw.invh, st);
                 goto step_done;
             }
-            // classical Gram-Schmidt with selective reorthogonalisation (all in FP64)
+            if (cgs2_grid_n > 0) {
+                // classical Gram-Schmidt with selective reorthogonalisation and the Givens
+                // update in one cooperative launch (short vectors)
+                int nact = 0;
+                for (int k = 0; k < nrhs; ++k) nact += active[k];
+                prof_begin(p, HELM_K_ORTHO, st);
+                cudaError_t e = launch_cgs2_step<VT>(KV, vsk, N, j, N, nrhs, kw.active, kw.hsum, ld, kw.rn + 3 * nrhs,
+                                                 kw.need, kw.H, ld, (long long)ld * m, kw.cs, kw.sn, kw.g, ld, kw.est,
+                                                 kw.invh, kw.mgs_part, kw.mgs_bar, p->d_err, cgs2_grid_n, st);
+                prof_end(p, HELM_K_ORTHO, (2.0 * j + 5) * (double)sizeof(VT) * N * nact, st,
+                         (16.0 * (j + 1) + 4.0) * N * nact);
+                if (e != cudaSuccess) return cuda_status(e, "Gram-Schmidt launch");
+                if (p->prof_on)
+                    HELM_CUDA_TRY(cudaMemcpyAsync(need.data(), kw.need, nrhs * sizeof(int), cudaMemcpyDeviceToHost, st));
+                goto step_done;
+            }
+            // classical Gram-Schmidt with selective reorthogonalisation (coefficients in FP64)
             launch_norm2_partial(Vn, N, nrhs, N, kw.rpart, nb, st);
             launch_reduce_rows(kw.rpart, nb, nrhs, kw.rn, 0, st);                 // ||w||^2
             prof_begin(p, HELM_K_ORTHO, st);
-            launch_mdot(kw.V, vsk, N, j + 1, Vn, N, N, nrhs, kw.active, kw.cpart, nb, st);
+            launch_mdot(KV, vsk, N, j + 1, Vn, N, N, nrhs, kw.active, kw.cpart, nb, st);
             prof_end(p, HELM_K_ORTHO, (j + 2) * vb, st, 8.0 * (j + 1) * N * nrhs);
             launch_reduce_cpartials(kw.cpart, nb, j + 1, kw.h1, ld, nrhs, st);
             prof_begin(p, HELM_K_ORTHO, st);
-            launch_mupdate(kw.V, vsk, N, j + 1, nullptr, kw.h1, ld, -1.0, Vn, N, N, nrhs, kw.active, kw.rpart,
+            launch_mupdate(KV, vsk, N, j + 1, nullptr, kw.h1, ld, -1.0, Vn, N, N, nrhs, kw.active, kw.rpart,
                            nb, st);
             prof_end(p, HELM_K_ORTHO, (j + 3) * vb, st, 8.0 * (j + 1) * N * nrhs + 4.0 * N * nrhs);
             launch_reduce_rows(kw.rpart, nb, nrhs, kw.rn + nrhs, 0, st);          // ||w'||^2
             count_launch();
             dgks_decide_kernel<<<(nrhs + 127) / 128, 128, 0, st>>>(kw.rn, kw.active, kw.need, nrhs);
             prof_begin(p, HELM_K_ORTHO, st);
-            launch_mdot(kw.V, vsk, N, j + 1, Vn, N, N, nrhs, kw.need, kw.cpart, nb, st);
+            launch_mdot(KV, vsk, N, j + 1, Vn, N, N, nrhs, kw.need, kw.cpart, nb, st);
             prof_end(p, HELM_K_ORTHO, 0.0, st);
             launch_reduce_cpartials(kw.cpart, nb, j + 1, kw.h2, ld, nrhs, st);
             prof_begin(p, HELM_K_ORTHO, st);
-            launch_mupdate(kw.V, vsk, N, j + 1, nullptr, kw.h2, ld, -1.0, Vn, N, N, nrhs, kw.need, kw.rpart,
+            launch_mupdate(KV, vsk, N, j + 1, nullptr, kw.h2, ld, -1.0, Vn, N, N, nrhs, kw.need, kw.rpart,
                            nb, st);
             prof_end(p, HELM_K_ORTHO, 0.0, st);
             launch_reduce_rows(kw.rpart, nb, nrhs, kw.rn + 2 * nrhs, 0, st);      // ||w''||^2
@@ -1455,7 +1497,7 @@ static helm_status fgmres_core(helm_problem* p, KrylovWS& kw, long long n, int n
         // u += Z y with y = R^{-1} g
         HELM_CUDA_TRY(cudaMemcpyAsync(kw.jcount, jcount.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, st));
         launch_hessenberg_solve(kw.H, ld, (long long)ld * m, kw.g, ld, kw.jcount, kw.y, ld, nrhs, st);
-        launch_mupdate(kw.Z, vsk, N, m, kw.jcount, kw.y, ld, 1.0, x, N, N, nrhs, nullptr, nullptr, nb, st);
+        launch_mupdate(KZ, vsk, N, m, kw.jcount, kw.y, ld, 1.0, x, N, N, nrhs, nullptr, nullptr, nb, st);
         HELM_CUDA_TRY(cudaGetLastError());
         HELM_CUDA_TRY(cudaStreamSynchronize(st));
     }
@@ -1471,7 +1513,7 @@ static helm_status fgmres_core(helm_problem* p, KrylovWS& kw, long long n, int n
 // preconditioner; the reconstruction (source r, incoming g) gives z.  The
 // interface vectors are FP64; S and the sweep run in the precision of the
 // factors.  With an exact interface solve M^{-1} = A^{-1}.
-template <typename R>
+template <typename R, typename VT>
 static helm_status run_precond_iface_t(helm_problem* p, int sched, const double2* r, double2* z, int nrhs,
                                        const helm_opts& o, cudaStream_t st) {
     using T = Cx<R>;
@@ -1482,6 +1524,9 @@ static helm_status run_precond_iface_t(helm_problem* p, int sched, const double2
     const long long nt = p->ntrace;
     s = ensure_kw(p->kwi, nrhs, o.inner_restart, nt, true);
     if (s != HELM_OK) return s;
+    // typed views of the interface workspace (allocated by ensure_kw just above)
+    VT* const kb = reinterpret_cast<VT*>(p->kwi.b);      // interface right-hand side
+    VT* const kx = reinterpret_cast<VT*>(p->kwi.x);      // interface iterate
     const PcWork w{{p->d_trace[0], p->d_trace[1], p->d_trace[2]}, p->d_yws, p->d_pc_norm, p->d_pc_partial,
                    p->d_escr, p->d_r64};
     T* tB = (T*)w.trace[BUF_B];
@@ -1492,31 +1537,31 @@ static helm_status run_precond_iface_t(helm_problem* p, int sched, const double2
     // b: outgoing data of the liftings
     s = run_stage_t<R>(p, w, cx, stg.front(), r, z, nrhs, st);
     if (s != HELM_OK) return s;
-    launch_trace_to_c128<T>(tB, nullptr, 1.0, p->kwi.b, tot, st);
+    launch_trace_to<T, VT>(tB, nullptr, 1, kb, tot, st);
     // (I - S) v: one interface stage over every subdomain writes S v - v into B
     StageDesc sS = stg.front();
     sS.iface = 1; sS.src = 0; sS.in0 = BUF_X; sS.in1 = BUF_NONE; sS.mask = 15;
     sS.dst = BUF_B; sS.dst2 = BUF_NONE; sS.base = BUF_NONE; sS.sub = BUF_X; sS.final_ = 0;
-    KrylovOps ops;
+    KrylovOps<VT> ops;
     // the interface stages read and write only the trace buffers: captured once as graphs
     // (tags: 2 sched = the sweep, 2 sched + 1 = S)
-    ops.matvec = [&](const double2* v, double2* wv) -> helm_status {
-        launch_trace_from_c128<T>(v, tX, (T*)nullptr, tot, st);
+    ops.matvec = [&](const VT* v, VT* wv) -> helm_status {
+        launch_trace_from<VT, T>(v, tX, (T*)nullptr, tot, st);
         helm_status q = run_captured(p, 2 * sched + 1, nrhs, st, [&](cudaStream_t cs) {
             return run_stage_t<R>(p, w, cx, sS, r, z, nrhs, cs);
         });
         if (q != HELM_OK) return q;
-        launch_trace_to_c128<T>(tB, nullptr, -1.0, wv, tot, st);
+        launch_trace_to<T, VT>(tB, nullptr, -1, wv, tot, st);
         return HELM_OK;
     };
     // the sweep of the schedule (its stages between lifting and reconstruction) on v:
     // input in B (and X, where SP propagates from), result X (SP) or X + Y (BSP)
-    ops.precond = [&](const double2* v, double2* zv) -> helm_status {
-        launch_trace_from_c128<T>(v, tB, tX, tot, st);
+    ops.precond = [&](const VT* v, VT* zv) -> helm_status {
+        launch_trace_from<VT, T>(v, tB, tX, tot, st);
         helm_status q = HELM_OK;
         if (run_sweep_persistent<R>(p, w, sched, nrhs, st, q)) {
             if (q != HELM_OK) return q;
-            launch_trace_to_c128<T>(tX, sched == HELM_SCHED_BSP ? tY : (T*)nullptr, 1.0, zv, tot, st);
+            launch_trace_to<T, VT>(tX, sched == HELM_SCHED_BSP ? tY : (T*)nullptr, 1, zv, tot, st);
             return HELM_OK;
         }
         q = run_captured(p, 2 * sched, nrhs, st, [&](cudaStream_t cs) {
@@ -1527,32 +1572,33 @@ static helm_status run_precond_iface_t(helm_problem* p, int sched, const double2
             return HELM_OK;
         });
         if (q != HELM_OK) return q;
-        launch_trace_to_c128<T>(tX, sched == HELM_SCHED_BSP ? tY : (T*)nullptr, 1.0, zv, tot, st);
+        launch_trace_to<T, VT>(tX, sched == HELM_SCHED_BSP ? tY : (T*)nullptr, 1, zv, tot, st);
         return HELM_OK;
     };
-    ops.residual = [&](const double2* x, bool x_zero, double2* rv) -> helm_status {
+    ops.residual = [&](const VT* x, bool x_zero, VT* rv) -> helm_status {
         if (x_zero) {
-            HELM_CUDA_TRY(cudaMemcpyAsync(rv, p->kwi.b, (size_t)tot * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+            HELM_CUDA_TRY(cudaMemcpyAsync(rv, kb, (size_t)tot * sizeof(VT), cudaMemcpyDeviceToDevice, st));
             return HELM_OK;
         }
         helm_status q = ops.matvec(x, rv);
         if (q != HELM_OK) return q;
-        launch_sub_c128(p->kwi.b, rv, rv, tot, st);
+        launch_sub<VT>(kb, rv, rv, tot, st);
         return HELM_OK;
     };
     std::vector<double> bnorm(nrhs);
-    launch_norm2_partial(p->kwi.b, nt, nrhs, nt, p->kwi.rpart, p->kwi.nblk, st);
+    launch_norm2_partial(kb, nt, nrhs, nt, p->kwi.rpart, p->kwi.nblk, st);
     launch_reduce_rows(p->kwi.rpart, p->kwi.nblk, nrhs, p->kwi.rn, 1, st);
     HELM_CUDA_TRY(cudaMemcpyAsync(bnorm.data(), p->kwi.rn, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
     HELM_CUDA_TRY(cudaStreamSynchronize(st));
     std::vector<int> it;
     std::vector<double> rr;
-    s = fgmres_core(p, p->kwi, nt, nrhs, o.inner_restart, o.inner_maxit, o.inner_tol, bnorm, p->kwi.x, false,
-                    false, nullptr, ops, it, rr, "gmres_solve (interface iterations)", st);
+    s = fgmres_core<VT>(p, p->kwi, nt, nrhs, o.inner_restart, o.inner_maxit, o.inner_tol, bnorm, kx, false,
+                    o.ortho == HELM_ORTHO_CGS2_SPLIT ? HELM_ORTHO_CGS2_SPLIT : HELM_ORTHO_CGS2, nullptr, ops, it, rr,
+                    "gmres_solve (interface iterations)", st);
     if (s != HELM_OK) return s;
     p->inner_steps += it.empty() ? 0 : *std::max_element(it.begin(), it.end());
     // reconstruction with the incoming data g
-    launch_trace_from_c128<T>(p->kwi.x, tX, (T*)nullptr, tot, st);
+    launch_trace_from<VT, T>(kx, tX, (T*)nullptr, tot, st);
     StageDesc sR = stg.back();
     sR.in0 = BUF_X; sR.in1 = BUF_NONE;
     return run_stage_t<R>(p, w, cx, sR, r, z, nrhs, st);
@@ -1560,8 +1606,10 @@ static helm_status run_precond_iface_t(helm_problem* p, int sched, const double2
 
 static helm_status run_precond_iface(helm_problem* p, int sched, const double2* r, double2* z, int nrhs,
                                      const helm_opts& o, cudaStream_t st) {
-    return p->prec == HELM_PREC_C64 ? run_precond_iface_t<float>(p, sched, r, z, nrhs, o, st)
-                                    : run_precond_iface_t<double>(p, sched, r, z, nrhs, o, st);
+    // interface vectors in the factors' precision unless inner_fp64
+    if (p->prec != HELM_PREC_C64) return run_precond_iface_t<double, double2>(p, sched, r, z, nrhs, o, st);
+    return o.inner_fp64 ? run_precond_iface_t<float, double2>(p, sched, r, z, nrhs, o, st)
+                        : run_precond_iface_t<float, float2>(p, sched, r, z, nrhs, o, st);
 }
 
 // FGMRES on A u = h^2 f for one chunk of right-hand sides
@@ -1580,7 +1628,7 @@ static helm_status gmres_impl(helm_problem* p, const double2* f, double2* u, int
     HELM_CUDA_TRY(cudaMemcpyAsync(bnorm.data(), p->kw.rn, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
     HELM_CUDA_TRY(cudaStreamSynchronize(st));
     for (auto& b : bnorm) b *= h2;
-    KrylovOps ops;
+    KrylovOps<double2> ops;
     ops.residual = [&](const double2* x, bool, double2* rv) -> helm_status {
         launch_residual(p->d_adiag, p->nx, p->ny, f, h2, x, rv, nrhs, nullptr, p->kw.rpart, p->kw.nblk, st);
         return HELM_OK;
@@ -1598,7 +1646,7 @@ static helm_status gmres_impl(helm_problem* p, const double2* f, double2* u, int
     std::vector<int> iters;
     std::vector<double> relres;
     p->persistent = o.persistent != 0;
-    s = fgmres_core(p, p->kw, N, nrhs, o.restart, o.maxit, o.tol, bnorm, u, o.x0_given != 0, o.ortho == HELM_ORTHO_MGS,
+    s = fgmres_core(p, p->kw, N, nrhs, o.restart, o.maxit, o.tol, bnorm, u, o.x0_given != 0, o.ortho,
                     o.hist, ops, iters, relres, "gmres_solve", st);
     p->persistent = 0;
     if (s != HELM_OK) return s;
@@ -1628,8 +1676,10 @@ extern "C" helm_status gmres_solve(helm_problem* p, const helm_c128* f, helm_c12
     if (o.maxit < 1) return arg_error("gmres_solve: maxit must be >= 1");
     if (!(o.tol > 0)) return arg_error("gmres_solve: tol must be > 0");
     if (o.sched != HELM_SCHED_BSP && o.sched != HELM_SCHED_SP) return arg_error("gmres_solve: unknown schedule");
-    if (o.ortho != HELM_ORTHO_MGS && o.ortho != HELM_ORTHO_CGS2) return arg_error("gmres_solve: unknown ortho");
+    if (o.ortho != HELM_ORTHO_MGS && o.ortho != HELM_ORTHO_CGS2 && o.ortho != HELM_ORTHO_CGS2_SPLIT)
+        return arg_error("gmres_solve: unknown ortho");
     if (o.inner_maxit < 0) return arg_error("gmres_solve: inner_maxit must be >= 0");
+    if (o.inner_fp64 != 0 && o.inner_fp64 != 1) return arg_error("gmres_solve: inner_fp64 must be 0 or 1");
     if (o.inner_maxit > 0 && (o.inner_restart < 1 || o.inner_restart > 500))
         return arg_error("gmres_solve: inner_restart must be in 1..500");
     if (o.inner_maxit > 0 && !(o.inner_tol > 0)) return arg_error("gmres_solve: inner_tol must be > 0");

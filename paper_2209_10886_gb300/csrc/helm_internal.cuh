@@ -39,6 +39,42 @@ template <typename T> __host__ __device__ __forceinline__ auto cabs2(T a) { retu
 __device__ __forceinline__ float2 to_c64(double2 a) { return make_float2((float)a.x, (float)a.y); }
 __device__ __forceinline__ double2 to_c128(float2 a) { return make_double2((double)a.x, (double)a.y); }
 __device__ __forceinline__ double2 to_c128(double2 a) { return a; }
+// Column j of the Arnoldi least-squares problem through the Givens rotations
+// (FP64).  On entry col[0..j] = h_{0..j,j}, col[j+1] = h_{j+1,j}, cs[0..j) and
+// sn[0..j) hold the earlier rotations and gj = g_j of the rotated right-hand
+// side; all in fast memory (the chain of rotations is serial).  Applies
+// rotations 0..j-1, forms rotation j so that it zeroes col[j+1], stores it in
+// cs[j], sn[j] and returns the new g_j, g_{j+1} (|g_{j+1}| is the residual
+// estimate).  A rotation acts as [a; b] <- [c a + s b; -conj(s) a + c b].
+__device__ inline void givens_column(double2* col, double2* cs, double2* sn, int j, double2& gj, double2& gj1) {
+    for (int i = 0; i < j; ++i) {
+        const double2 a = col[i], b = col[i + 1];
+        const double c = cs[i].x;
+        const double2 s = sn[i];
+        col[i] = make_double2(c * a.x + (s.x * b.x - s.y * b.y), c * a.y + (s.x * b.y + s.y * b.x));
+        col[i + 1] = make_double2(c * b.x - (s.x * a.x + s.y * a.y), c * b.y - (s.x * a.y - s.y * a.x));
+    }
+    const double2 a = col[j], b = col[j + 1];
+    const double na = sqrt(a.x * a.x + a.y * a.y), nb = sqrt(b.x * b.x + b.y * b.y);
+    const double den = sqrt(na * na + nb * nb);
+    double c;
+    double2 s;
+    if (den == 0.0) { c = 1.0; s = make_double2(0.0, 0.0); }
+    else if (na == 0.0) { c = 0.0; s = make_double2(b.x / den, -b.y / den); }      // conj(b)/|b|
+    else {
+        c = na / den;
+        const double2 ph = make_double2(a.x / na, a.y / na);                      // a/|a|
+        s = make_double2((ph.x * b.x + ph.y * b.y) / den, (ph.y * b.x - ph.x * b.y) / den);   // ph*conj(b)/den
+    }
+    cs[j] = make_double2(c, 0.0);
+    sn[j] = s;
+    col[j] = make_double2(c * a.x + (s.x * b.x - s.y * b.y), c * a.y + (s.x * b.y + s.y * b.x));
+    col[j + 1] = make_double2(0.0, 0.0);
+    const double2 g0 = gj;
+    gj1 = make_double2(-(s.x * g0.x + s.y * g0.y), -(s.x * g0.y - s.y * g0.x));   // -conj(s) g_j
+    gj = make_double2(c * g0.x, c * g0.y);
+}
+
 template <typename T> __device__ __forceinline__ T from_c128(double2 a);
 template <> __device__ __forceinline__ float2 from_c128<float2>(double2 a) { return to_c64(a); }
 template <> __device__ __forceinline__ double2 from_c128<double2>(double2 a) { return a; }
@@ -213,20 +249,25 @@ void launch_matvec(const double2* adiag, int nx, int ny, const double2* u, doubl
 int launch_residual(const double2* adiag, int nx, int ny, const double2* f, double fscale,
                      const double2* u, double2* r, int nrhs, const int* active, double* partial,
                      int nblk, cudaStream_t st);
-void launch_norm2_partial(const double2* v, long long n, int nrhs, long long stride, double* partial,
+// VT: double2 or float2 (partial sums and coefficients FP64 in both)
+template <typename VT>
+void launch_norm2_partial(const VT* v, long long n, int nrhs, long long stride, double* partial,
                           int nblk, cudaStream_t st);
 void launch_reduce_rows(const double* partial, int nblk, int nrows, double* out, int mode,
                         cudaStream_t st);
-void launch_mdot(const double2* V, long long vstride_k, long long vstride_rhs, int nvec,
-                 const double2* w, long long wstride, long long n, int nrhs, const int* active,
+template <typename VT>
+void launch_mdot(const VT* V, long long vstride_k, long long vstride_rhs, int nvec,
+                 const VT* w, long long wstride, long long n, int nrhs, const int* active,
                  double2* partial, int nblk, cudaStream_t st);
 void launch_reduce_cpartials(const double2* partial, int nblk, int nrows, double2* out,
                              long long out_stride, int nrhs, cudaStream_t st);
-void launch_mupdate(const double2* V, long long vstride_k, long long vstride_rhs, int nvec,
-                    const int* nvec_rhs, const double2* coef, long long coef_stride, double sign, double2* w,
+template <typename VT>
+void launch_mupdate(const VT* V, long long vstride_k, long long vstride_rhs, int nvec,
+                    const int* nvec_rhs, const double2* coef, long long coef_stride, double sign, VT* w,
                     long long wstride, long long n, int nrhs, const int* active, double* norm_partial,
                     int nblk, cudaStream_t st);
-void launch_scale_vec(double2* dst, long long dstride, const double2* src, long long sstride,
+template <typename VT>
+void launch_scale_vec(VT* dst, long long dstride, const VT* src, long long sstride,
                       const double* inv, long long n, int nrhs, const int* active, cudaStream_t st);
 void launch_hessenberg_step(double2* H, int ldh, long long hstride, double2* cs, double2* sn, double2* g,
                             int ldg, const double2* hcol, long long hcol_stride, const double* hnorm,
@@ -237,13 +278,14 @@ void launch_hessenberg_solve(const double2* H, int ldh, long long hstride, const
 void launch_mask_copy(double2* dst, const double2* src, long long n, int nrhs, const int* active,
                       cudaStream_t st);
 void launch_sqrt_inplace(double* v, int n, cudaStream_t st);
-// interface vectors (T = the trace buffers' complex type): out = sign (a + b) (b optional);
-// out (and out2) = in rounded to T; r = b - w
-template <typename T>
-void launch_trace_to_c128(const T* a, const T* b, double sign, double2* out, long long total, cudaStream_t st);
-template <typename T>
-void launch_trace_from_c128(const double2* in, T* out, T* out2, long long total, cudaStream_t st);
-void launch_sub_c128(const double2* b, const double2* w, double2* r, long long total, cudaStream_t st);
+// interface vectors (T = the trace buffers' complex type, VT = the Krylov vectors'):
+// out = sign (a + b) (b optional, sign +1 or -1); out (and out2) = in rounded to T; r = b - w
+template <typename T, typename VT>
+void launch_trace_to(const T* a, const T* b, int sign, VT* out, long long total, cudaStream_t st);
+template <typename VT, typename T>
+void launch_trace_from(const VT* in, T* out, T* out2, long long total, cudaStream_t st);
+template <typename VT>
+void launch_sub(const VT* b, const VT* w, VT* r, long long total, cudaStream_t st);
 // out[k*n + i] = complex64(src[k*n + i] * scale[k])
 void launch_to_c64_scaled(const double2* src, const double* scale, float2* out, long long n, int nrhs,
                           cudaStream_t st);

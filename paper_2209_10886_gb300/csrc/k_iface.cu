@@ -37,6 +37,11 @@ __device__ __forceinline__ T ldg_(const T* p) {
 
 // one work item of an interface stage: subdomain a.subs[item_sub], output rows
 // [row_block*RB, +RB) of its masked sides, RHS [rhs_block*NR, +NR)
+// v[s] for a runtime s in 0..3 without indexing the array (keeps it in registers)
+__device__ __forceinline__ int sel4(const int (&v)[4], int s) {
+    return s == 0 ? v[0] : s == 1 ? v[1] : s == 2 ? v[2] : v[3];
+}
+
 template <typename R, int NR, bool LDCG>
 __device__ void iface_item(const IfaceArgs<R>& a, int item_sub, int row_block, int rhs_block, unsigned char* smem_raw) {
     using T = Cx<R>;
@@ -44,11 +49,16 @@ __device__ void iface_item(const IfaceArgs<R>& a, int item_sub, int row_block, i
     const int Lb = sd.Lb;
     const int rhs0 = rhs_block * NR;
     const int nr = min(NR, a.nrhs - rhs0);
-    const int len[4] = {sd.my, sd.my, sd.mx, sd.mx};
+    // the per-side tables as scalars (a dynamically indexed array would live in local memory)
+    const int bo[4] = {sd.bo[0], sd.bo[1], sd.bo[2], sd.bo[3]};
+    const int tin[4] = {sd.tin[0], sd.tin[1], sd.tin[2], sd.tin[3]};
+    auto len = [&](int s) { return s < 2 ? sd.my : sd.mx; };
+    auto on = [&](int s) { return ((a.mask >> s) & 1) && sel4(bo, s) >= 0; };
     // output rows: points of the masked interface sides, in the order W, E, S, N
     int rcount = 0;
+#pragma unroll
     for (int s = 0; s < 4; ++s)
-        if ((a.mask & (1 << s)) && sd.bo[s] >= 0) rcount += len[s];
+        if (on(s)) rcount += len(s);
     const int row0 = row_block * RB;
     if (row0 >= rcount) return;
 
@@ -56,9 +66,12 @@ __device__ void iface_item(const IfaceArgs<R>& a, int item_sub, int row_block, i
     T* g = graw + (size_t)NR * Lb;                 // [NR][Lb] cin * incoming data
     for (int idx = threadIdx.x; idx < NR * Lb; idx += IT) {
         const int k = idx / Lb, e = idx - k * Lb;
+        // the side holding boundary point e: the last interface side starting at or before it
         int s = 0;
-        while (s < 3 && !(sd.bo[s] >= 0 && e >= sd.bo[s] && e < sd.bo[s] + len[s])) ++s;
-        const long long ti = sd.tin[s] + (e - sd.bo[s]);
+#pragma unroll
+        for (int q = 1; q < 4; ++q)
+            if (bo[q] >= 0 && e >= bo[q]) s = q;
+        const long long ti = sel4(tin, s) + (e - sel4(bo, s));
         T G = czero<T>(), Gs = czero<T>();
         if (k < nr) {
             const long long o = (long long)(rhs0 + k) * a.ntrace + ti;
@@ -73,37 +86,70 @@ __device__ void iface_item(const IfaceArgs<R>& a, int item_sub, int row_block, i
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const T* K = a.K + sd.koff;
-    for (int rr = warp; rr < RB; rr += IT / 32) {
-        const int row = row0 + rr;
-        if (row >= rcount) break;
-        int s = 0, pt = row;
-        for (; s < 4; ++s) {
-            if (!((a.mask & (1 << s)) && sd.bo[s] >= 0)) continue;
-            if (pt < len[s]) break;
-            pt -= len[s];
-        }
-        const int krow = sd.bo[s] + pt;
-        const T* Kr = K + (long long)krow * Lb;
-        T acc[NR];
+    // each warp takes RPW rows and keeps the loads of all of them in flight: columns in
+    // groups of CU per lane (32 CU per group), every load of a group issued before its FMAs
+    constexpr int RPW = RB / (IT / 32);
+    constexpr int CU = (sizeof(R) == 8 && NR >= 4) ? 4 : 8;   // fits the 128-register bound
+    int srow[RPW], prow[RPW], krow[RPW];
+    const T* Kr[RPW];
 #pragma unroll
-        for (int k = 0; k < NR; ++k) acc[k] = czero<T>();
-#pragma unroll 4
-        for (int c = lane; c < Lb; c += 32) {
-            const T kv = Kr[c];
+    for (int q = 0; q < RPW; ++q) {
+        const int row = row0 + warp + q * (IT / 32);
+        int s = -1, pt = row;
 #pragma unroll
-            for (int k = 0; k < NR; ++k) acc[k] = cfma(kv, g[k * Lb + c], acc[k]);
+        for (int t = 0; t < 4; ++t)
+            if (s < 0 && on(t)) {
+                if (pt < len(t)) s = t;
+                else pt -= len(t);
+            }
+        if (row >= rcount) s = -1;
+        srow[q] = s;
+        prow[q] = pt;
+        krow[q] = s >= 0 ? sel4(bo, s) + pt : 0;
+        Kr[q] = K + (long long)krow[q] * Lb;
+    }
+    T acc[RPW][NR];
+#pragma unroll
+    for (int q = 0; q < RPW; ++q)
+#pragma unroll
+        for (int k = 0; k < NR; ++k) acc[q][k] = czero<T>();
+    for (int c0 = lane; c0 < Lb; c0 += 32 * CU) {
+        T kv[RPW][CU];
+#pragma unroll
+        for (int q = 0; q < RPW; ++q)
+#pragma unroll
+            for (int u = 0; u < CU; ++u) {
+                const int c = c0 + 32 * u;
+                kv[q][u] = (srow[q] >= 0 && c < Lb) ? Kr[q][c] : czero<T>();
+            }
+#pragma unroll
+        for (int u = 0; u < CU; ++u) {
+            const int c = c0 + 32 * u;
+            if (c < Lb) {
+#pragma unroll
+                for (int k = 0; k < NR; ++k) {
+                    const T gv = g[k * Lb + c];
+#pragma unroll
+                    for (int q = 0; q < RPW; ++q) acc[q][k] = cfma(kv[q][u], gv, acc[q][k]);
+                }
+            }
         }
+    }
+#pragma unroll
+    for (int q = 0; q < RPW; ++q) {
 #pragma unroll
         for (int k = 0; k < NR; ++k)
             for (int o = 16; o > 0; o >>= 1) {
-                acc[k].x += __shfl_down_sync(0xffffffffu, acc[k].x, o);
-                acc[k].y += __shfl_down_sync(0xffffffffu, acc[k].y, o);
+                acc[q][k].x += __shfl_down_sync(0xffffffffu, acc[q][k].x, o);
+                acc[q][k].y += __shfl_down_sync(0xffffffffu, acc[q][k].y, o);
             }
-        if (lane == 0) {
-            const long long ti = sd.tin[s] + pt, to = sd.tout[s] + pt;
+        if (lane == 0 && srow[q] >= 0) {
+            const int s = srow[q], pt = prow[q];
+            const long long ti = sel4(tin, s) + pt;
+            const long long to = (long long)(s == 0 ? sd.tout[0] : s == 1 ? sd.tout[1] : s == 2 ? sd.tout[2] : sd.tout[3]) + pt;
             const TraceCoef<T> c = a.tc[ti];
             for (int k = 0; k < nr; ++k) {
-                T out = cfma(c.cb, acc[k], cmul(c.ca, graw[k * Lb + krow]));
+                T out = cfma(c.cb, acc[q][k], cmul(c.ca, graw[k * Lb + krow[q]]));
                 const long long o = (long long)(rhs0 + k) * a.ntrace + to;
                 if (a.base) out = cadd(out, ldg_<T, LDCG>(a.base + o));
                 if (a.sub) out = csub(out, ldg_<T, LDCG>(a.sub + o));

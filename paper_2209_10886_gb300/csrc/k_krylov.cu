@@ -9,7 +9,7 @@
 
 namespace {
 
-constexpr int VT = 256;
+constexpr int NTH = 256;
 
 template <typename V> __device__ __forceinline__ V warp_sum(V v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -43,12 +43,12 @@ __device__ __forceinline__ double2 apply_A(const double2* __restrict__ u, const 
     return make_double2(fma(ad.x, c.x, fma(-ad.y, c.y, -sx)), fma(ad.x, c.y, fma(ad.y, c.x, -sy)));
 }
 
-// grid: x covers a row of the grid in VT-wide segments, y strides over rows, z = RHS
+// grid: x covers a row of the grid in NTH-wide segments, y strides over rows, z = RHS
 __global__ void matvec_kernel(const double2* __restrict__ adiag, int nx, int ny, const double2* __restrict__ u,
                               double2* __restrict__ Au) {
     const long long N = (long long)nx * ny;
     const int k = blockIdx.z;
-    const int a = blockIdx.x * VT + threadIdx.x;
+    const int a = blockIdx.x * NTH + threadIdx.x;
     if (a >= nx) return;
     const double2* uk = u + k * N;
     for (int b = blockIdx.y; b < ny; b += gridDim.y) {
@@ -69,7 +69,7 @@ __global__ void residual_kernel(const double2* __restrict__ adiag, int nx, int n
         if (threadIdx.x == 0) partial[(long long)k * nb + bid] = 0.0;
         return;
     }
-    const int a = blockIdx.x * VT + threadIdx.x;
+    const int a = blockIdx.x * NTH + threadIdx.x;
     const double2* uk = u + k * N;
     double acc = 0.0;
     if (a < nx) {
@@ -86,17 +86,19 @@ __global__ void residual_kernel(const double2* __restrict__ adiag, int nx, int n
     if (threadIdx.x == 0) partial[(long long)k * nb + bid] = acc;
 }
 
-__global__ void norm2_partial_kernel(const double2* __restrict__ v, long long n, long long stride,
+template <typename VT>
+__global__ void norm2_partial_kernel(const VT* __restrict__ v, long long n, long long stride,
                                      double* __restrict__ partial) {
+    using Re = decltype(VT::x);
     __shared__ double sh[32];
     const int k = blockIdx.y;
-    double acc = 0.0;
+    Re acc = 0;
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
-        const double2 x = v[k * stride + p];
+        const VT x = v[k * stride + p];
         acc = fma(x.x, x.x, fma(x.y, x.y, acc));
     }
-    acc = block_sum(acc, sh);
-    if (threadIdx.x == 0) partial[(long long)k * gridDim.x + blockIdx.x] = acc;
+    const double t = block_sum((double)acc, sh);
+    if (threadIdx.x == 0) partial[(long long)k * gridDim.x + blockIdx.x] = t;
 }
 
 // out[row] = sum_b partial[row][b]   (mode 1: sqrt of the sum)
@@ -109,10 +111,12 @@ __global__ void reduce_rows_kernel(const double* __restrict__ partial, int nblk,
     if (threadIdx.x == 0) out[row] = mode == 1 ? sqrt(acc) : acc;
 }
 
-// partial[k][blk][j] = sum_{p in block range} conj(V_j[p]) w[p],  j < nvec
+// partial[k][blk][j] = sum_{p in block range} conj(V_j[p]) w[p],  j < nvec (summed in the
+// vectors' precision within a block, in FP64 across blocks)
 constexpr int KB = 4;
-__global__ void mdot_kernel(const double2* __restrict__ V, long long vsk, long long vsr, int nvec,
-                            const double2* __restrict__ w, long long ws, long long n, const int* __restrict__ active,
+template <typename VT>
+__global__ void mdot_kernel(const VT* __restrict__ V, long long vsk, long long vsr, int nvec,
+                            const VT* __restrict__ w, long long ws, long long n, const int* __restrict__ active,
                             double2* __restrict__ partial) {
     __shared__ double sh[32];
     const int k = blockIdx.y;
@@ -124,13 +128,13 @@ __global__ void mdot_kernel(const double2* __restrict__ V, long long vsk, long l
     }
     const long long chunk = (n + nblk - 1) / nblk;
     const long long p0 = blockIdx.x * chunk, p1 = min(n, p0 + chunk);
-    const double2* wk = w + k * ws;
+    const VT* wk = w + k * ws;
     for (int j0 = 0; j0 < nvec; j0 += KB) {
-        double2 acc[KB];
+        VT acc[KB];
 #pragma unroll
-        for (int q = 0; q < KB; ++q) acc[q] = make_double2(0.0, 0.0);
+        for (int q = 0; q < KB; ++q) acc[q] = czero<VT>();
         for (long long p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
-            const double2 wv = wk[p];
+            const VT wv = wk[p];
 #pragma unroll
             for (int q = 0; q < KB; ++q)
                 if (j0 + q < nvec) acc[q] = cfmaconj(V[(long long)(j0 + q) * vsk + k * vsr + p], wv, acc[q]);
@@ -138,8 +142,8 @@ __global__ void mdot_kernel(const double2* __restrict__ V, long long vsk, long l
 #pragma unroll
         for (int q = 0; q < KB; ++q) {
             if (j0 + q >= nvec) break;
-            const double re = block_sum(acc[q].x, sh);
-            const double im = block_sum(acc[q].y, sh);
+            const double re = block_sum((double)acc[q].x, sh);
+            const double im = block_sum((double)acc[q].y, sh);
             if (threadIdx.x == 0) out[j0 + q] = make_double2(re, im);
         }
     }
@@ -160,47 +164,52 @@ __global__ void reduce_cpartials_kernel(const double2* __restrict__ partial, int
     if (threadIdx.x == 0) out[k * os + j] = make_double2(re, im);
 }
 
-// w += sign * sum_j coef[k][j] V_j, optional per-block ||w||^2 partials
-__global__ void mupdate_kernel(const double2* __restrict__ V, long long vsk, long long vsr, int nvec,
+// w += sign * sum_j coef[k][j] V_j, optional per-block ||w||^2 partials (the update in
+// the vectors' precision with the FP64 coefficients rounded to it)
+template <typename VT>
+__global__ void mupdate_kernel(const VT* __restrict__ V, long long vsk, long long vsr, int nvec,
                                const int* __restrict__ nvec_rhs, const double2* __restrict__ coef, long long cs,
-                               double sign, double2* __restrict__ w, long long ws, long long n,
+                               double sign, VT* __restrict__ w, long long ws, long long n,
                                const int* __restrict__ active, double* __restrict__ norm_partial) {
-    __shared__ double2 c[512];
+    using Re = decltype(VT::x);
+    __shared__ VT c[512];
     __shared__ double sh[32];
     const int k = blockIdx.y;
     const bool on = !(active && !active[k]);
     const int nv = nvec_rhs ? nvec_rhs[k] : nvec;
     for (int j = threadIdx.x; j < nv && j < 512; j += blockDim.x) {
         const double2 cj = coef[k * cs + j];
-        c[j] = make_double2(sign * cj.x, sign * cj.y);
+        c[j] = mk((Re)(sign * cj.x), (Re)(sign * cj.y));
     }
     __syncthreads();
-    double acc = 0.0;
+    Re acc = 0;
     if (on) {
-        double2* wk = w + k * ws;
+        VT* wk = w + k * ws;
         for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
-            double2 x = wk[p];
+            VT x = wk[p];
             for (int j = 0; j < nv; ++j) x = cfma(c[j], V[(long long)j * vsk + k * vsr + p], x);
             wk[p] = x;
             acc = fma(x.x, x.x, fma(x.y, x.y, acc));
         }
     }
     if (norm_partial) {
-        acc = block_sum(acc, sh);
-        if (threadIdx.x == 0) norm_partial[(long long)k * gridDim.x + blockIdx.x] = acc;
+        const double t = block_sum((double)acc, sh);
+        if (threadIdx.x == 0) norm_partial[(long long)k * gridDim.x + blockIdx.x] = t;
     }
 }
 
 // dst = src * inv[k]  (inactive RHS: dst = 0)
-__global__ void scale_vec_kernel(double2* __restrict__ dst, long long ds, const double2* __restrict__ src,
+template <typename VT>
+__global__ void scale_vec_kernel(VT* __restrict__ dst, long long ds, const VT* __restrict__ src,
                                  long long ss, const double* __restrict__ inv, long long n,
                                  const int* __restrict__ active) {
+    using Re = decltype(VT::x);
     const int k = blockIdx.y;
     const bool on = !(active && !active[k]);
-    const double s = on ? inv[k] : 0.0;
+    const Re s = on ? (Re)inv[k] : (Re)0;
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
-        const double2 x = on ? src[k * ss + p] : make_double2(0.0, 0.0);
-        dst[k * ds + p] = make_double2(x.x * s, x.y * s);
+        const VT x = on ? src[k * ss + p] : czero<VT>();
+        dst[k * ds + p] = mk(x.x * s, x.y * s);
     }
 }
 
@@ -208,51 +217,42 @@ __global__ void scale_vec_kernel(double2* __restrict__ dst, long long ds, const 
 // Givens rotations of the earlier columns, a new rotation that annihilates
 // H(j+1, j), and the rotated right-hand side g.  |g_{j+1}| is the residual norm
 // of the least-squares problem min ||beta e_1 - H y||.
+// one warp per RHS: the column and the earlier rotations are gathered into shared
+// memory by all lanes, lane 0 runs the serial chain of rotations there
 __global__ void hessenberg_step_kernel(double2* __restrict__ H, int ldh, long long hs, double2* __restrict__ cs,
                                        double2* __restrict__ sn, double2* __restrict__ g, int ldg,
                                        const double2* __restrict__ hcol, long long hcs, const double* __restrict__ hnorm,
                                        int j, int nrhs, const int* __restrict__ active,
                                        double* __restrict__ resid_est, double* __restrict__ inv_hnext) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= nrhs) return;
-    if (active && !active[k]) return;
-    double2* Hk = H + k * hs;            // column-major: H(i, jj) at Hk[jj*ldh + i]
-    double2* col = Hk + (long long)j * ldh;
-    for (int i = 0; i <= j; ++i) col[i] = hcol[k * hcs + i];
-    const double hn = hnorm[k];
-    col[j + 1] = make_double2(hn, 0.0);
+    extern __shared__ double2 hsm[];                 // col[j+2], cs[j+1], sn[j+1]
+    const int k = blockIdx.x, lane = threadIdx.x;
+    if (k >= nrhs || (active && !active[k])) return;
+    double2* col = hsm;
+    double2* csv = col + (j + 2);
+    double2* snv = csv + (j + 1);
     double2* csk = cs + (long long)k * ldg;
     double2* snk = sn + (long long)k * ldg;
-    for (int i = 0; i < j; ++i) {
-        const double2 a = col[i], b = col[i + 1];
-        const double c = csk[i].x;
-        const double2 s = snk[i];
-        // [a; b] <- [c a + s b; -conj(s) a + c b]
-        col[i] = make_double2(c * a.x + (s.x * b.x - s.y * b.y), c * a.y + (s.x * b.y + s.y * b.x));
-        col[i + 1] = make_double2(c * b.x - (s.x * a.x + s.y * a.y), c * b.y - (s.x * a.y - s.y * a.x));
+    const double hn = hnorm[k];
+    for (int i = lane; i <= j; i += 32) {
+        col[i] = hcol[k * hcs + i];
+        if (i < j) { csv[i] = csk[i]; snv[i] = snk[i]; }
     }
-    const double2 a = col[j], b = col[j + 1];
-    const double na = sqrt(a.x * a.x + a.y * a.y), nb = sqrt(b.x * b.x + b.y * b.y);
-    const double den = sqrt(na * na + nb * nb);
-    double c;
-    double2 s;
-    if (den == 0.0) { c = 1.0; s = make_double2(0.0, 0.0); }
-    else if (na == 0.0) { c = 0.0; s = make_double2(b.x / den, -b.y / den); }      // conj(b)/|b| * (b real >= 0)
-    else {
-        c = na / den;
-        const double2 ph = make_double2(a.x / na, a.y / na);                      // a/|a|
-        s = make_double2((ph.x * b.x + ph.y * b.y) / den, (ph.y * b.x - ph.x * b.y) / den);   // ph*conj(b)/den
+    __syncwarp();
+    if (lane == 0) {
+        col[j + 1] = make_double2(hn, 0.0);
+        double2* gk = g + (long long)k * ldg;
+        double2 gj = gk[j], gj1;
+        givens_column(col, csv, snv, j, gj, gj1);
+        gk[j] = gj;
+        gk[j + 1] = gj1;
+        csk[j] = csv[j];
+        snk[j] = snv[j];
+        resid_est[k] = sqrt(gj1.x * gj1.x + gj1.y * gj1.y);
+        inv_hnext[k] = hn > 0.0 ? 1.0 / hn : 0.0;
     }
-    csk[j] = make_double2(c, 0.0);
-    snk[j] = s;
-    col[j] = make_double2(c * a.x + (s.x * b.x - s.y * b.y), c * a.y + (s.x * b.y + s.y * b.x));
-    col[j + 1] = make_double2(0.0, 0.0);
-    double2* gk = g + (long long)k * ldg;
-    const double2 gj = gk[j];
-    gk[j + 1] = make_double2(-(s.x * gj.x + s.y * gj.y), -(s.x * gj.y - s.y * gj.x));   // -conj(s) g_j
-    gk[j] = make_double2(c * gj.x, c * gj.y);
-    resid_est[k] = sqrt(gk[j + 1].x * gk[j + 1].x + gk[j + 1].y * gk[j + 1].y);
-    inv_hnext[k] = hn > 0.0 ? 1.0 / hn : 0.0;
+    __syncwarp();
+    double2* colg = H + k * hs + (long long)j * ldh;       // column-major: H(i, jj) at H[jj*ldh + i]
+    for (int i = lane; i <= j + 1; i += 32) colg[i] = col[i];
 }
 
 // y = R^{-1} g (upper triangular R = rotated H, first jcount[k] columns)
@@ -290,70 +290,87 @@ __global__ void scale_from_norm_kernel(const double* norm2, double* inv, double*
 }
 
 int grid_for(long long n) {
-    long long b = (n + VT - 1) / VT;
+    long long b = (n + NTH - 1) / NTH;
     return (int)min(b, (long long)152 * 8);
 }
 
 }  // namespace
 
 static dim3 rows_grid(int nx, int ny, int nblk, int nrhs) {
-    const int gx = (nx + VT - 1) / VT;
+    const int gx = (nx + NTH - 1) / NTH;
     const int gy = max(1, min(ny, nblk / gx));
     return dim3(gx, gy, nrhs);
 }
 void launch_matvec(const double2* adiag, int nx, int ny, const double2* u, double2* Au, int nrhs, cudaStream_t st) {
     count_launch();
-    matvec_kernel<<<rows_grid(nx, ny, 152 * 16, nrhs), VT, 0, st>>>(adiag, nx, ny, u, Au);
+    matvec_kernel<<<rows_grid(nx, ny, 152 * 16, nrhs), NTH, 0, st>>>(adiag, nx, ny, u, Au);
 }
 // returns the number of partials per RHS written into `partial` (<= nblk)
 int launch_residual(const double2* adiag, int nx, int ny, const double2* f, double fscale, const double2* u,
                     double2* r, int nrhs, const int* active, double* partial, int nblk, cudaStream_t st) {
     const dim3 g = rows_grid(nx, ny, nblk, nrhs);
     count_launch();
-    residual_kernel<<<g, VT, 0, st>>>(adiag, nx, ny, f, fscale, u, r, active, partial);
+    residual_kernel<<<g, NTH, 0, st>>>(adiag, nx, ny, f, fscale, u, r, active, partial);
     return (int)(g.x * g.y);
 }
-void launch_norm2_partial(const double2* v, long long n, int nrhs, long long stride, double* partial, int nblk,
+template <typename VT>
+void launch_norm2_partial(const VT* v, long long n, int nrhs, long long stride, double* partial, int nblk,
                           cudaStream_t st) {
     dim3 g(nblk, nrhs);
     count_launch();
-    norm2_partial_kernel<<<g, VT, 0, st>>>(v, n, stride, partial);
+    norm2_partial_kernel<VT><<<g, NTH, 0, st>>>(v, n, stride, partial);
 }
 void launch_reduce_rows(const double* partial, int nblk, int nrows, double* out, int mode, cudaStream_t st) {
     count_launch();
-    reduce_rows_kernel<<<nrows, VT, 0, st>>>(partial, nblk, out, mode);
+    reduce_rows_kernel<<<nrows, NTH, 0, st>>>(partial, nblk, out, mode);
 }
-void launch_mdot(const double2* V, long long vsk, long long vsr, int nvec, const double2* w, long long ws, long long n,
+template <typename VT>
+void launch_mdot(const VT* V, long long vsk, long long vsr, int nvec, const VT* w, long long ws, long long n,
                  int nrhs, const int* active, double2* partial, int nblk, cudaStream_t st) {
     dim3 g(nblk, nrhs);
     count_launch();
-    mdot_kernel<<<g, VT, 0, st>>>(V, vsk, vsr, nvec, w, ws, n, active, partial);
+    mdot_kernel<VT><<<g, NTH, 0, st>>>(V, vsk, vsr, nvec, w, ws, n, active, partial);
 }
 void launch_reduce_cpartials(const double2* partial, int nblk, int nrows, double2* out, long long os, int nrhs,
                              cudaStream_t st) {
     dim3 g(nrows, nrhs);
     count_launch();
-    reduce_cpartials_kernel<<<g, VT, 0, st>>>(partial, nblk, nrows, out, os);
+    reduce_cpartials_kernel<<<g, NTH, 0, st>>>(partial, nblk, nrows, out, os);
 }
-void launch_mupdate(const double2* V, long long vsk, long long vsr, int nvec, const int* nvec_rhs, const double2* coef,
-                    long long cs, double sign, double2* w, long long ws, long long n, int nrhs, const int* active,
+template <typename VT>
+void launch_mupdate(const VT* V, long long vsk, long long vsr, int nvec, const int* nvec_rhs, const double2* coef,
+                    long long cs, double sign, VT* w, long long ws, long long n, int nrhs, const int* active,
                     double* norm_partial, int nblk, cudaStream_t st) {
     dim3 g(nblk, nrhs);
     count_launch();
-    mupdate_kernel<<<g, VT, 0, st>>>(V, vsk, vsr, nvec, nvec_rhs, coef, cs, sign, w, ws, n, active, norm_partial);
+    mupdate_kernel<VT><<<g, NTH, 0, st>>>(V, vsk, vsr, nvec, nvec_rhs, coef, cs, sign, w, ws, n, active,
+                                                 norm_partial);
 }
-void launch_scale_vec(double2* dst, long long ds, const double2* src, long long ss, const double* inv, long long n,
+template <typename VT>
+void launch_scale_vec(VT* dst, long long ds, const VT* src, long long ss, const double* inv, long long n,
                       int nrhs, const int* active, cudaStream_t st) {
     dim3 g(grid_for(n), nrhs);
     count_launch();
-    scale_vec_kernel<<<g, VT, 0, st>>>(dst, ds, src, ss, inv, n, active);
+    scale_vec_kernel<VT><<<g, NTH, 0, st>>>(dst, ds, src, ss, inv, n, active);
 }
+#define HELM_VEC_INST(VT)                                                                                          \
+    template void launch_norm2_partial<VT>(const VT*, long long, int, long long, double*, int, cudaStream_t);       \
+    template void launch_mdot<VT>(const VT*, long long, long long, int, const VT*, long long, long long, int,       \
+                                  const int*, double2*, int, cudaStream_t);                                         \
+    template void launch_mupdate<VT>(const VT*, long long, long long, int, const int*, const double2*, long long,   \
+                                     double, VT*, long long, long long, int, const int*, double*, int,              \
+                                     cudaStream_t);                                                                 \
+    template void launch_scale_vec<VT>(VT*, long long, const VT*, long long, const double*, long long, int,        \
+                                       const int*, cudaStream_t);
+HELM_VEC_INST(double2)
+HELM_VEC_INST(float2)
+#undef HELM_VEC_INST
 void launch_hessenberg_step(double2* H, int ldh, long long hs, double2* cs, double2* sn, double2* g, int ldg,
                             const double2* hcol, long long hcs, const double* hnorm, int j, int nrhs, const int* active,
                             double* resid_est, double* inv_hnext, cudaStream_t st) {
     count_launch();
-    hessenberg_step_kernel<<<(nrhs + 31) / 32, 32, 0, st>>>(H, ldh, hs, cs, sn, g, ldg, hcol, hcs, hnorm, j, nrhs,
-                                                           active, resid_est, inv_hnext);
+    hessenberg_step_kernel<<<nrhs, 32, (size_t)(3 * j + 4) * sizeof(double2), st>>>(
+        H, ldh, hs, cs, sn, g, ldg, hcol, hcs, hnorm, j, nrhs, active, resid_est, inv_hnext);
 }
 void launch_hessenberg_solve(const double2* H, int ldh, long long hs, const double2* g, int ldg, const int* jcount,
                              double2* y, int ldy, int nrhs, cudaStream_t st) {
@@ -388,55 +405,67 @@ void launch_to_c64_scaled(const double2* src, const double* scale, float2* out, 
 }
 
 // ------------------------------------------------- interface (trace) vectors
-// out128 = sign * (a + b) for n * nrhs values, b optional (T: the trace buffers' type)
-template <typename T>
-__global__ void trace_to_c128_kernel(const T* __restrict__ a, const T* __restrict__ b, double sign,
-                                     double2* __restrict__ out, long long total) {
+// T: the trace buffers' complex type (the factors' precision); VT: the interface
+// Krylov vectors' type.  Same types: plain copies and sums in that precision.
+template <typename O, typename I> __device__ __forceinline__ O cvt(I a);
+template <> __device__ __forceinline__ float2 cvt<float2, float2>(float2 a) { return a; }
+template <> __device__ __forceinline__ double2 cvt<double2, double2>(double2 a) { return a; }
+template <> __device__ __forceinline__ double2 cvt<double2, float2>(float2 a) { return to_c128(a); }
+template <> __device__ __forceinline__ float2 cvt<float2, double2>(double2 a) { return to_c64(a); }
+
+// out = sign * (a + b) for n * nrhs values, b optional
+template <typename T, typename VT>
+__global__ void trace_to_kernel(const T* __restrict__ a, const T* __restrict__ b, int sign, VT* __restrict__ out,
+                                long long total) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x) {
-        double2 v = to_c128(a[i]);
-        if (b) { const double2 w = to_c128(b[i]); v.x += w.x; v.y += w.y; }
-        out[i] = make_double2(sign * v.x, sign * v.y);
+        VT v = cvt<VT>(a[i]);
+        if (b) v = cadd(v, cvt<VT>(b[i]));
+        out[i] = sign < 0 ? mk(-v.x, -v.y) : v;
     }
 }
 // out (and out2, optional) = in rounded to T
-template <typename T>
-__global__ void trace_from_c128_kernel(const double2* __restrict__ in, T* __restrict__ out, T* __restrict__ out2,
-                                       long long total) {
+template <typename VT, typename T>
+__global__ void trace_from_kernel(const VT* __restrict__ in, T* __restrict__ out, T* __restrict__ out2,
+                                  long long total) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x) {
-        const T f = from_c128<T>(in[i]);
+        const T f = cvt<T>(in[i]);
         out[i] = f;
         if (out2) out2[i] = f;
     }
 }
 // r = b - w
-__global__ void sub_c128_kernel(const double2* __restrict__ b, const double2* __restrict__ w, double2* __restrict__ r,
-                                long long total) {
+template <typename VT>
+__global__ void sub_kernel(const VT* __restrict__ b, const VT* __restrict__ w, VT* __restrict__ r, long long total) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-         i += (long long)gridDim.x * blockDim.x) {
-        const double2 x = b[i], y = w[i];
-        r[i] = make_double2(x.x - y.x, x.y - y.y);
-    }
+         i += (long long)gridDim.x * blockDim.x)
+        r[i] = csub(b[i], w[i]);
 }
 
 static int small_grid(long long total) { return (int)std::min<long long>(1216, (total + 255) / 256 + 1); }
 
-template <typename T>
-void launch_trace_to_c128(const T* a, const T* b, double sign, double2* out, long long total, cudaStream_t st) {
+template <typename T, typename VT>
+void launch_trace_to(const T* a, const T* b, int sign, VT* out, long long total, cudaStream_t st) {
     count_launch();
-    trace_to_c128_kernel<T><<<small_grid(total), 256, 0, st>>>(a, b, sign, out, total);
+    trace_to_kernel<T, VT><<<small_grid(total), 256, 0, st>>>(a, b, sign, out, total);
 }
-template <typename T>
-void launch_trace_from_c128(const double2* in, T* out, T* out2, long long total, cudaStream_t st) {
+template <typename VT, typename T>
+void launch_trace_from(const VT* in, T* out, T* out2, long long total, cudaStream_t st) {
     count_launch();
-    trace_from_c128_kernel<T><<<small_grid(total), 256, 0, st>>>(in, out, out2, total);
+    trace_from_kernel<VT, T><<<small_grid(total), 256, 0, st>>>(in, out, out2, total);
 }
-void launch_sub_c128(const double2* b, const double2* w, double2* r, long long total, cudaStream_t st) {
+template <typename VT>
+void launch_sub(const VT* b, const VT* w, VT* r, long long total, cudaStream_t st) {
     count_launch();
-    sub_c128_kernel<<<small_grid(total), 256, 0, st>>>(b, w, r, total);
+    sub_kernel<VT><<<small_grid(total), 256, 0, st>>>(b, w, r, total);
 }
-template void launch_trace_to_c128<float2>(const float2*, const float2*, double, double2*, long long, cudaStream_t);
-template void launch_trace_to_c128<double2>(const double2*, const double2*, double, double2*, long long, cudaStream_t);
-template void launch_trace_from_c128<float2>(const double2*, float2*, float2*, long long, cudaStream_t);
-template void launch_trace_from_c128<double2>(const double2*, double2*, double2*, long long, cudaStream_t);
+#define HELM_TRACE_INST(T, VT)                                                                      \
+    template void launch_trace_to<T, VT>(const T*, const T*, int, VT*, long long, cudaStream_t);    \
+    template void launch_trace_from<VT, T>(const VT*, T*, T*, long long, cudaStream_t);
+HELM_TRACE_INST(float2, float2)
+HELM_TRACE_INST(float2, double2)
+HELM_TRACE_INST(double2, double2)
+#undef HELM_TRACE_INST
+template void launch_sub<float2>(const float2*, const float2*, float2*, long long, cudaStream_t);
+template void launch_sub<double2>(const double2*, const double2*, double2*, long long, cudaStream_t);

@@ -13,6 +13,8 @@
 // kernel records HELM_ERR_TIMEOUT and returns.  When two slices of the vector per
 // CTA fit in shared memory, mgs_smem_kernel streams the basis vectors there by
 // bulk copies issued one step ahead.
+#include <algorithm>
+
 #include "helm_internal.cuh"
 
 namespace {
@@ -335,6 +337,246 @@ cudaError_t launch_ept(MgsArgs& a, int grid, cudaStream_t st) {
     return cudaLaunchCooperativeKernel((const void*)mgs_kernel<EPT>, dim3(grid), dim3(MT), args, 0, st);
 }
 
+// ---------------------------------------------------------------------------
+// Classical Gram-Schmidt with selective reorthogonalisation (the DGKS test: a
+// second pass when ||w'||^2 < ||w||^2 / 2) for short vectors, one cooperative
+// launch per Arnoldi step: CTA b keeps the contiguous slice [b*L, b*L + L) of w
+// in shared memory; a pass computes all j+1 dot products (warp q takes the basis
+// vectors q + 16 t and q + 8 + 16 t), reduces them over the grid (one barrier),
+// and updates its slice against the basis read from L2.  The norm, the
+// normalisation of v_{j+1} and the Givens update of the least-squares problem
+// (CTA 0) follow in the same launch.  VT = double2 or float2: products and
+// updates in the vectors' precision, sums across CTAs, coefficients and the
+// least-squares problem in FP64.  Reductions are deterministic: every CTA adds
+// the partials of all CTAs in the same order.  2 grid barriers per RHS, 4 when
+// the second pass runs, each bounded in time (HELM_ERR_TIMEOUT, then return).
+template <typename VT>
+struct Cgs2Args {
+    const VT* V;               // basis: v_k of RHS r at V + k*vsk + r*vsr; w = v_{j+1} in place
+    long long vsk, vsr;
+    int j;                     // new column j: j+1 basis vectors to project out
+    long long n;
+    int nrhs;
+    const int* active;
+    double2* hsum;             // h_{0..j,j} of RHS r at hsum[r*ldh + k] (both passes summed)
+    int ldh;
+    double* hnorm;             // h_{j+1,j} per RHS
+    int* need;                 // 1 where the second pass ran
+    // Arnoldi least-squares state (the Hessenberg step)
+    double2* H;                // column-major per RHS, H(i, jj) at H[r*hs + jj*ldH + i]
+    int ldH;
+    long long hs;
+    double2 *cs, *sn, *g;      // rotations and rotated right-hand side, ldg per RHS
+    int ldg;
+    double* est;               // |g_{j+1}| per RHS
+    double* invh;              // 1 / h_{j+1,j}
+    double2* partial;          // [2][gridDim.x][j + 2] scratch
+    unsigned* bar;
+    int* err;
+    int L;                     // slice length per CTA
+};
+
+constexpr int CT = 256;        // threads per CTA of the fused step
+
+template <typename VT> __device__ __forceinline__ VT warp_sumc(VT v) {
+    for (int o = 16; o > 0; o >>= 1) {
+        v.x += __shfl_down_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_down_sync(0xffffffffu, v.y, o);
+    }
+    return v;
+}
+
+template <typename VT>
+__global__ void __launch_bounds__(CT) cgs2_step_kernel(Cgs2Args<VT> a) {
+    using Re = decltype(VT::x);
+    extern __shared__ __align__(16) double2 csm[];
+    double2* hv = csm;                              // [j + 2] reduced values of the current pass
+    double2* h1 = hv + (a.j + 2);                   // [j + 1] coefficients, both passes
+    double2* gv = h1 + (a.j + 1);                   // [3 (j + 2)] Givens scratch (CTA 0)
+    VT* hc = reinterpret_cast<VT*>(gv + 3 * (a.j + 2));   // [j + 1] -hv in the vectors' precision
+    VT* ws = hc + (a.j + 1);                        // [L] slice of w
+    __shared__ double red[CT / 32];
+    __shared__ int sflag;
+    const int nvec = a.j + 1, PS = a.j + 2;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long c0 = (long long)blockIdx.x * a.L;
+    const int len = (int)max(0LL, min((long long)a.L, a.n - c0));
+    if (threadIdx.x == 0) sflag = 0;
+    __syncthreads();
+    unsigned s = 0;
+    // CTA sum of one value per thread (all threads see it after the call)
+    auto block_sum = [&](double v) -> double {
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        __syncthreads();
+        if (lane == 0) red[warp] = v;
+        __syncthreads();
+        double t = 0.0;
+        for (int q = 0; q < CT / 32; ++q) t += red[q];
+        return t;
+    };
+    // partials of this CTA are in part[cta*PS + 0..cnt); after the barrier every CTA
+    // sums column k over all CTAs in the same order into hv[k]
+    auto grid_reduce = [&](double2* part, int cnt) -> bool {
+        if (!grid_barrier(a.bar, a.err, &sflag)) return false;
+        for (int k = warp; k < cnt; k += CT / 32) {
+            // up to 8 partials per lane in flight, added in a fixed order
+            double2 t = make_double2(0.0, 0.0);
+            for (int cb = 0; cb < (int)gridDim.x; cb += 256) {
+                double2 pv[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int c = cb + lane + 32 * u;
+                    pv[u] = c < (int)gridDim.x ? __ldcg(part + (long long)c * PS + k) : make_double2(0.0, 0.0);
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) { t.x += pv[u].x; t.y += pv[u].y; }
+            }
+            t = warp_sum2(t);
+            if (lane == 0) hv[k] = t;
+        }
+        __syncthreads();
+        ++s;
+        return true;
+    };
+    auto cur_part = [&]() { return a.partial + (size_t)(s & 1u) * gridDim.x * PS; };
+    // dot products of the slice with all basis vectors into this CTA's partials, 8
+    // elements of two vectors per lane loaded before they are used
+    auto dots = [&](const VT* V, double2* part) {
+        for (int ka = warp; ka < nvec; ka += 2 * (CT / 32)) {
+            const int kb = ka + CT / 32;
+            const bool hb = kb < nvec;
+            const VT* va = V + ka * a.vsk + c0;
+            const VT* vb = V + (hb ? kb : ka) * a.vsk + c0;
+            VT acca = czero<VT>(), accb = acca;
+            for (int i0 = 0; i0 < len; i0 += 256) {
+                VT xa[8], xb[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int i = i0 + lane + 32 * u;
+                    const bool in = i < len;
+                    xa[u] = in ? __ldcg(va + i) : czero<VT>();
+                    xb[u] = (in && hb) ? __ldcg(vb + i) : czero<VT>();
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int i = i0 + lane + 32 * u;
+                    if (i < len) {
+                        const VT wv = ws[i];
+                        acca = cfmaconj(xa[u], wv, acca);
+                        accb = cfmaconj(xb[u], wv, accb);
+                    }
+                }
+            }
+            acca = warp_sumc(acca);
+            accb = warp_sumc(accb);
+            if (lane == 0) {
+                part[(long long)blockIdx.x * PS + ka] = make_double2((double)acca.x, (double)acca.y);
+                if (hb) part[(long long)blockIdx.x * PS + kb] = make_double2((double)accb.x, (double)accb.y);
+            }
+        }
+    };
+    // hc = -hv rounded to the vectors' precision (then a barrier before use)
+    auto set_coef = [&]() {
+        for (int k = threadIdx.x; k < nvec; k += CT) hc[k] = mk((Re)-hv[k].x, (Re)-hv[k].y);
+        __syncthreads();
+    };
+    // ws += sum_k hc[k] v_k over the slice, 16 basis values per element loaded before
+    // they are used; returns this thread's share of ||ws||^2
+    auto update = [&](const VT* V) -> double {
+        Re nrm = 0;
+        for (int i = threadIdx.x; i < len; i += CT) {
+            VT x = ws[i];
+            const VT* v = V + c0 + i;
+            for (int k0 = 0; k0 < nvec; k0 += 16) {
+                VT vv[16];
+#pragma unroll
+                for (int u = 0; u < 16; ++u) vv[u] = k0 + u < nvec ? __ldcg(v + (k0 + u) * a.vsk) : czero<VT>();
+#pragma unroll
+                for (int u = 0; u < 16; ++u)
+                    if (k0 + u < nvec) x = cfma(hc[k0 + u], vv[u], x);
+            }
+            ws[i] = x;
+            nrm = fma(x.x, x.x, fma(x.y, x.y, nrm));
+        }
+        return (double)nrm;
+    };
+
+    for (int r = 0; r < a.nrhs; ++r) {
+        if (a.active && !a.active[r]) continue;
+        const VT* V = a.V + r * a.vsr;
+        VT* w = const_cast<VT*>(V) + (long long)nvec * a.vsk;
+        Re n0 = 0;
+        for (int i = threadIdx.x; i < len; i += CT) {
+            const VT x = w[c0 + i];
+            ws[i] = x;
+            n0 = fma(x.x, x.x, fma(x.y, x.y, n0));
+        }
+        const double w2l = block_sum((double)n0);    // syncs: the slice is in place
+        // pass 1: h1 = V^H w and ||w||^2 (column j + 1 of the partials)
+        double2* part = cur_part();
+        dots(V, part);
+        if (threadIdx.x == 0) part[(long long)blockIdx.x * PS + nvec] = make_double2(w2l, 0.0);
+        if (!grid_reduce(part, nvec + 1)) return;
+        const double w2 = hv[nvec].x;
+        for (int k = threadIdx.x; k < nvec; k += CT) h1[k] = hv[k];
+        set_coef();
+        const double n1 = block_sum(update(V));
+        part = cur_part();
+        if (threadIdx.x == 0) part[(long long)blockIdx.x * PS] = make_double2(n1, 0.0);
+        if (!grid_reduce(part, 1)) return;
+        double hn2 = hv[0].x;                        // ||w'||^2
+        const bool second = hn2 < 0.5 * w2;
+        if (second) {
+            part = cur_part();
+            dots(V, part);
+            if (!grid_reduce(part, nvec)) return;
+            for (int k = threadIdx.x; k < nvec; k += CT) h1[k] = cadd(h1[k], hv[k]);
+            set_coef();
+            const double n2 = block_sum(update(V));
+            part = cur_part();
+            if (threadIdx.x == 0) part[(long long)blockIdx.x * PS] = make_double2(n2, 0.0);
+            if (!grid_reduce(part, 1)) return;
+            hn2 = hv[0].x;
+        }
+        const double hn = sqrt(hn2);
+        const double inv = hn > 0.0 ? 1.0 / hn : 0.0;
+        const Re invr = (Re)inv;
+        for (int i = threadIdx.x; i < len; i += CT) w[c0 + i] = mk(ws[i].x * invr, ws[i].y * invr);
+        if (blockIdx.x == 0) {
+            // h column, then the Givens update of the least-squares problem
+            double2* col = gv;
+            double2* csv = col + (a.j + 2);
+            double2* snv = csv + (a.j + 2);
+            double2* csr = a.cs + (long long)r * a.ldg;
+            double2* snr = a.sn + (long long)r * a.ldg;
+            for (int k = threadIdx.x; k <= a.j; k += CT) {
+                col[k] = h1[k];
+                a.hsum[(long long)r * a.ldh + k] = h1[k];
+                if (k < a.j) { csv[k] = csr[k]; snv[k] = snr[k]; }
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                a.hnorm[r] = hn;
+                a.need[r] = second ? 1 : 0;
+                col[a.j + 1] = make_double2(hn, 0.0);
+                double2* gr = a.g + (long long)r * a.ldg;
+                double2 gj = gr[a.j], gj1;
+                givens_column(col, csv, snv, a.j, gj, gj1);
+                gr[a.j] = gj;
+                gr[a.j + 1] = gj1;
+                csr[a.j] = csv[a.j];
+                snr[a.j] = snv[a.j];
+                a.est[r] = sqrt(gj1.x * gj1.x + gj1.y * gj1.y);
+                a.invh[r] = inv;
+            }
+            __syncthreads();
+            double2* colg = a.H + r * a.hs + (long long)a.j * a.ldH;
+            for (int k = threadIdx.x; k <= a.j + 1; k += CT) colg[k] = col[k];
+        }
+        __syncthreads();                              // ws, hv, hc and h1 are reused by the next RHS
+    }
+}
+
 }  // namespace
 
 // Grid size (CTAs, all co-resident) for the persistent Gram-Schmidt kernel, or 0.
@@ -377,3 +619,53 @@ cudaError_t launch_mgs(const double2* V, long long vsk, long long vsr, double2* 
     if (per <= 32) return launch_ept<32>(a, grid, st);
     return cudaErrorInvalidValue;
 }
+
+// shared memory of the fused CGS2 step for a slice of L elements and column j
+template <typename VT>
+static size_t cgs2_smem(long long L, int j) {
+    return (size_t)((j + 2) + (j + 1) + 3 * (j + 2)) * sizeof(double2) + (size_t)((j + 1) + L) * sizeof(VT);
+}
+
+// CTAs of the fused CGS2 step for vectors of n elements (~128 elements per CTA, at
+// most one CTA per SM), or 0 when a slice does not fit in shared memory
+template <typename VT>
+int cgs2_grid(long long n, int max_j) {
+    const int g = mgs_grid();
+    if (g <= 0) return 0;
+    const int grid = (int)std::min<long long>(g, std::max<long long>(1, (n + 127) / 128));
+    const long long L = (n + grid - 1) / grid;
+    return cgs2_smem<VT>(L, max_j) <= 100 * 1024 ? grid : 0;
+}
+
+// Column j of the Arnoldi process for every active RHS: CGS2-orthogonalise
+// v_{j+1} (in place in V) against v_0..v_j, normalise it, store h_{0..j+1,j}
+// and apply the Givens rotations (H, cs, sn, g, est, invh as the Hessenberg step
+// kernel leaves them).  partial holds 2 * grid * (j + 2) values.
+template <typename VT>
+cudaError_t launch_cgs2_step(const VT* V, long long vsk, long long vsr, int j, long long n, int nrhs,
+                             const int* active, double2* hsum, int ldh, double* hnorm, int* need, double2* H, int ldH,
+                             long long hs, double2* cs, double2* sn, double2* g, int ldg, double* est, double* invh,
+                             double2* partial, unsigned* bar, int* err, int grid, cudaStream_t st) {
+    if (grid <= 0) return cudaErrorInvalidValue;
+    const int L = (int)((n + grid - 1) / grid);
+    Cgs2Args<VT> a{V, vsk, vsr, j, n, nrhs, active, hsum, ldh, hnorm, need, H, ldH, hs, cs, sn, g, ldg, est, invh,
+                   partial, bar, err, L};
+    const size_t smem = cgs2_smem<VT>(L, j);
+    if (smem > 48 * 1024) {
+        cudaError_t e =
+            cudaFuncSetAttribute(cgs2_step_kernel<VT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    void* args[] = {&a};
+    count_launch();
+    return cudaLaunchCooperativeKernel((const void*)cgs2_step_kernel<VT>, dim3(grid), dim3(CT), args, smem, st);
+}
+#define HELM_CGS2_INST(VT)                                                                                        \
+    template int cgs2_grid<VT>(long long, int);                                                                   \
+    template cudaError_t launch_cgs2_step<VT>(const VT*, long long, long long, int, long long, int, const int*,   \
+                                              double2*, int, double*, int*, double2*, int, long long, double2*,   \
+                                              double2*, double2*, int, double*, double*, double2*, unsigned*, int*, \
+                                              int, cudaStream_t);
+HELM_CGS2_INST(double2)
+HELM_CGS2_INST(float2)
+#undef HELM_CGS2_INST

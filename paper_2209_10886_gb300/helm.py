@@ -35,7 +35,7 @@ class HelmOpts(ctypes.Structure):
                 ("x0_given", ctypes.c_int), ("sched", ctypes.c_int), ("use_graph", ctypes.c_int),
                 ("hist", ctypes.POINTER(ctypes.c_double)), ("ortho", ctypes.c_int),
                 ("inner_maxit", ctypes.c_int), ("inner_restart", ctypes.c_int), ("inner_tol", ctypes.c_double),
-                ("persistent", ctypes.c_int)]
+                ("persistent", ctypes.c_int), ("inner_fp64", ctypes.c_int)]
 
 
 class HelmSetupOpts(ctypes.Structure):
@@ -187,8 +187,10 @@ class Problem:
 
     def solve(self, f, u=None, restart=50, maxit=1000, tol=1e-6, sched="BSP", x0=None, history=False,
               stream=None, raise_on_noconv=True, use_graph=False, inner_maxit=0, inner_restart=100, inner_tol=1e-4,
-              persistent=False):
-        """Solve A u = h^2 f (FP64 FGMRES); returns (u, [(iters, relres)], history or None)."""
+              persistent=False, ortho="mgs", inner_fp64=False):
+        """Solve A u = h^2 f (FP64 FGMRES); returns (u, [(iters, relres)], history or None).
+        ortho: "mgs" (volume default), "cgs2" or "cgs2_split" (see helm.h); inner_fp64: FP64
+        interface Krylov vectors with complex64 factors (default: complex64 vectors)."""
         f = _as_fields(f, self.N, "f")
         nrhs = f.numel() // self.N
         u = torch.empty_like(f) if u is None else u
@@ -197,7 +199,8 @@ class Problem:
         hist = (ctypes.c_double * (maxit * nrhs))() if history else None
         o = default_opts(restart=restart, maxit=maxit, tol=tol, sched=sched, x0_given=int(x0 is not None),
                          use_graph=int(bool(use_graph)), inner_maxit=int(inner_maxit),
-                         inner_restart=int(inner_restart), inner_tol=float(inner_tol), persistent=int(bool(persistent)))
+                         inner_restart=int(inner_restart), inner_tol=float(inner_tol), persistent=int(bool(persistent)),
+                         ortho=ORTHO[ortho], inner_fp64=int(bool(inner_fp64)))
         if hist is not None:
             o.hist = ctypes.cast(hist, ctypes.POINTER(ctypes.c_double))
         info = (HelmInfo * nrhs)()
@@ -273,6 +276,7 @@ class HelmKStat(ctypes.Structure):
                 ("bytes", ctypes.c_double)]
 
 
+ORTHO = {"mgs": 0, "cgs2": 1, "cgs2_split": 2}
 KERNEL_CLASS = {"stage": 0, "matvec": 1, "ortho": 2, "other": 3, "trace": 4}
 
 

@@ -133,10 +133,11 @@ def test_without_boundary_operators_matches_oracle(H, prec, tol):
     p.close()
 
 
-@pytest.mark.parametrize("ortho", [0, 1])
+@pytest.mark.parametrize("ortho", [0, 1, 2])
 def test_gram_schmidt_variants_agree(H, ortho):
     """Modified (persistent kernel) and reorthogonalised classical Gram-Schmidt
-    both reach the direct solution."""
+    (fused into one launch per step, and split into reduction kernels) all reach
+    the direct solution."""
     import ctypes
     w = CASES["tiny_2x2"]()
     p, _ = make(H, w, "c64")
@@ -150,6 +151,39 @@ def test_gram_schmidt_variants_agree(H, ortho):
                              info, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert st == 0 and info[0].relres <= 1e-9
     assert rel(u.cpu().numpy()[0], ref) <= 1e-5
+    p.close()
+
+
+@pytest.mark.parametrize("where", ["volume", "interface", "interface_c64"])
+def test_fused_cgs2_matches_split(H, where):
+    """The fused Arnoldi step (CGS2, norm, normalisation and Givens update in one
+    cooperative launch) against the same arithmetic as separate kernels: three RHS
+    that converge at different steps (the active flags), both reach the direct
+    solution and take the same number of outer steps up to one (two with complex64
+    interface vectors, whose FP32 sums round differently in the two forms)."""
+    w = CASES["ragged_3x2"]()
+    p, _ = make(H, w, "c64" if where == "interface_c64" else "c128")
+    A = assemble_operator(w.n, w.h, w.omega, w.m2).tocsc()
+    f = W.random_complex((3, w.N), 31)
+    f[1, : w.N // 2] = 0.0            # a source in half of the domain
+    f[2] = 0.0
+    f[2, w.N // 2] = 1.0              # a point source
+    kw = dict(tol=1e-9, restart=25, maxit=600)
+    if where == "interface":
+        kw.update(inner_maxit=80, inner_restart=12, inner_tol=1e-6)
+    if where == "interface_c64":
+        kw.update(inner_maxit=80, inner_restart=12, inner_tol=1e-4)
+    res = {}
+    for ortho in ("cgs2", "cgs2_split"):
+        u, info, _ = p.solve(cuda(f), ortho=ortho, **kw)
+        res[ortho] = (u.cpu().numpy(), info)
+    lu = spla.splu(A.tocsc())
+    for k in range(3):
+        ref = lu.solve(w.h ** 2 * f[k])
+        for ortho, (u, info) in res.items():
+            print(f"{where} {ortho} rhs{k}: its {info[k][0]}, relres {info[k][1]:.2e}, rel {rel(u[k], ref):.2e}")
+            assert info[k][1] <= 1e-9 and rel(u[k], ref) <= 1e-5
+        assert abs(res["cgs2"][1][k][0] - res["cgs2_split"][1][k][0]) <= (2 if where == "interface_c64" else 1)
     p.close()
 
 
@@ -193,18 +227,20 @@ def test_gmres_multi_rhs_and_initial_guess(H):
     assert all(it == 0 for it, _ in info2)
 
 
-@pytest.mark.parametrize("prec", ["c128", "c64"])
+@pytest.mark.parametrize("prec", ["c128", "c64", "c64_fp64_interface"])
 @pytest.mark.parametrize("sched", ["BSP", "SP"])
 def test_interface_krylov_gmres_matches_direct_solve(H, prec, sched):
     """inner_maxit > 0: the preconditioner solves the interface problem (I - S) g = b by
     FGMRES with the sweep as its preconditioner (the paper's formulation); the outer
-    FP64 FGMRES on the volume still reaches the true residual and the direct solution."""
+    FP64 FGMRES on the volume still reaches the true residual and the direct solution.
+    With complex64 factors the interface vectors are complex64 unless inner_fp64."""
     w = CASES["uneven_4x3"]()
-    p, _ = make(H, w, prec)
+    p, _ = make(H, w, prec.split("_")[0])
     A = assemble_operator(w.n, w.h, w.omega, w.m2).tocsc()
     f = W.random_complex((2, w.N), 22)
     s0 = H.inner_steps(p)
-    u, info, _ = p.solve(cuda(f), tol=1e-9, restart=30, maxit=200, sched=sched, inner_maxit=60, inner_tol=1e-3)
+    u, info, _ = p.solve(cuda(f), tol=1e-9, restart=30, maxit=200, sched=sched, inner_maxit=60, inner_tol=1e-3,
+                         inner_fp64=prec.endswith("fp64_interface"))
     steps = H.inner_steps(p) - s0
     u = u.cpu().numpy()
     lu = spla.splu(A)
