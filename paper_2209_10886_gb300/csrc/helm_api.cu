@@ -701,7 +701,9 @@ static helm_status build_boundary_operators_t(helm_problem* p, cudaStream_t st) 
     if (p->max_Lb == 0) return HELM_OK;
     long long kel = 0;
     for (auto& s : p->subs) kel += (long long)s.dev.Lb * s.dev.Lb;
-    cudaError_t e = cudaMalloc(&p->d_K, (size_t)kel * sizeof(T));
+    // 16 bytes of padding: the staged interface kernel copies whole 16-byte units, up to
+    // 8 bytes past the last row of a complex64 operator
+    cudaError_t e = cudaMalloc(&p->d_K, (size_t)kel * sizeof(T) + 16);
     if (e != cudaSuccess) { p->d_K = nullptr; return cuda_status(e, "precond_factor: allocating boundary operators"); }
     p->K_bytes = (size_t)kel * sizeof(T);
     const int NB = 64;
@@ -905,6 +907,7 @@ static bool run_sweep_persistent(helm_problem* p, const PcWork& w, int sched, in
     a.K = (const T*)p->d_K;
     a.tc = sizeof(R) == 4 ? (const TraceCoef<T>*)p->d_tc64 : (const TraceCoef<T>*)p->d_tc128;
     for (int b = 0; b < 3; ++b) a.bufs[b] = w.trace[b];
+    a.err = p->d_err;
     double bytes = 0, flops = 0;
     if (p->prof_on) {
         const auto& stg = p->sched[sched];
@@ -964,10 +967,20 @@ static helm_status run_stage_t(helm_problem* p, const PcWork& w, const PcCtx& cx
         ia.gin0 = B(sd.in0); ia.gin1 = B(sd.in1);
         ia.mask = sd.mask;
         ia.dst = B(sd.dst); ia.dst2 = B(sd.dst2); ia.base = B(sd.base); ia.sub = B(sd.sub);
+        ia.err = p->d_err;
+        // grid rows: the most output rows (points of the masked sides) of a subdomain
+        int max_rows = 0;
+        for (int id : sd.subs) {
+            const SubDev& d = p->subs[id].dev;
+            int rows = 0;
+            for (int sde = 0; sde < 4; ++sde)
+                if ((sd.mask & (1 << sde)) && d.bo[sde] >= 0) rows += (sde == SW || sde == SE) ? d.my : d.mx;
+            max_rows = std::max(max_rows, rows);
+        }
         double bytes = 0, flops = 0;
         if (p->prof_on) iface_accounting(p, sd, nrhs, sizeof(T), bytes, flops);
         prof_begin(p, HELM_K_TRACE, st);
-        cudaError_t e = launch_iface<R>(ia, (int)sd.subs.size(), 2 * (p->max_mx + p->max_my), p->max_Lb, st);
+        cudaError_t e = launch_iface<R>(ia, (int)sd.subs.size(), max_rows, p->max_Lb, st);
         prof_end(p, HELM_K_TRACE, bytes, st, flops);
         if (e != cudaSuccess) return cuda_status(e, "interface stage launch");
         return HELM_OK;

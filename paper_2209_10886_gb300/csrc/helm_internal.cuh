@@ -39,42 +39,50 @@ template <typename T> __host__ __device__ __forceinline__ auto cabs2(T a) { retu
 __device__ __forceinline__ float2 to_c64(double2 a) { return make_float2((float)a.x, (float)a.y); }
 __device__ __forceinline__ double2 to_c128(float2 a) { return make_double2((double)a.x, (double)a.y); }
 __device__ __forceinline__ double2 to_c128(double2 a) { return a; }
-// Column j of the Arnoldi least-squares problem through the Givens rotations
-// (FP64).  On entry col[0..j] = h_{0..j,j}, col[j+1] = h_{j+1,j}, cs[0..j) and
-// sn[0..j) hold the earlier rotations and gj = g_j of the rotated right-hand
-// side; all in fast memory (the chain of rotations is serial).  Applies
-// rotations 0..j-1, forms rotation j so that it zeroes col[j+1], stores it in
-// cs[j], sn[j] and returns the new g_j, g_{j+1} (|g_{j+1}| is the residual
-// estimate).  A rotation acts as [a; b] <- [c a + s b; -conj(s) a + c b].
-__device__ inline void givens_column(double2* col, double2* cs, double2* sn, int j, double2& gj, double2& gj1) {
+// Column j of the Arnoldi least-squares problem through the Givens rotations, in
+// the precision of C2 (double2; float2 where the Krylov vectors are complex64 and
+// the least-squares problem needs no more).  On entry col[0..j] = h_{0..j,j},
+// col[j+1] = h_{j+1,j}, cs[0..j) (cosines, real parts) and sn[0..j) hold the
+// earlier rotations and gj = g_j of the rotated right-hand side, all in fast
+// memory: the chain of rotations is serial, so the caller converts precisions
+// beforehand (conversions run on GB300's narrow FP64 pipe).  Applies rotations
+// 0..j-1, forms rotation j so that it zeroes col[j+1], stores it in cs[j], sn[j]
+// and returns the new g_j, g_{j+1} (|g_{j+1}| is the residual estimate).  A
+// rotation acts as [a; b] <- [c a + s b; -conj(s) a + c b].
+template <typename C2>
+__device__ inline void givens_column(C2* col, C2* cs, C2* sn, int j, C2& gj, C2& gj1) {
+    using Re = decltype(C2::x);
+    Re ax = col[0].x, ay = col[0].y;                 // the running upper entry of the pair
     for (int i = 0; i < j; ++i) {
-        const double2 a = col[i], b = col[i + 1];
-        const double c = cs[i].x;
-        const double2 s = sn[i];
-        col[i] = make_double2(c * a.x + (s.x * b.x - s.y * b.y), c * a.y + (s.x * b.y + s.y * b.x));
-        col[i + 1] = make_double2(c * b.x - (s.x * a.x + s.y * a.y), c * b.y - (s.x * a.y - s.y * a.x));
+        const C2 b = col[i + 1];
+        const Re c = cs[i].x;
+        const C2 s = sn[i];
+        col[i] = mk(c * ax + (s.x * b.x - s.y * b.y), c * ay + (s.x * b.y + s.y * b.x));
+        const Re nx = c * b.x - (s.x * ax + s.y * ay);
+        const Re ny = c * b.y - (s.x * ay - s.y * ax);
+        ax = nx;
+        ay = ny;
     }
-    const double2 a = col[j], b = col[j + 1];
-    const double na = sqrt(a.x * a.x + a.y * a.y), nb = sqrt(b.x * b.x + b.y * b.y);
-    const double den = sqrt(na * na + nb * nb);
-    double c;
-    double2 s;
-    if (den == 0.0) { c = 1.0; s = make_double2(0.0, 0.0); }
-    else if (na == 0.0) { c = 0.0; s = make_double2(b.x / den, -b.y / den); }      // conj(b)/|b|
+    const C2 b = col[j + 1];
+    const Re na = sqrt(ax * ax + ay * ay), nb = sqrt(b.x * b.x + b.y * b.y);
+    const Re den = sqrt(na * na + nb * nb);
+    Re c;
+    C2 s;
+    if (den == (Re)0) { c = 1; s = mk((Re)0, (Re)0); }
+    else if (na == (Re)0) { c = 0; s = mk(b.x / den, -b.y / den); }          // conj(b)/|b|
     else {
         c = na / den;
-        const double2 ph = make_double2(a.x / na, a.y / na);                      // a/|a|
-        s = make_double2((ph.x * b.x + ph.y * b.y) / den, (ph.y * b.x - ph.x * b.y) / den);   // ph*conj(b)/den
+        const Re px = ax / na, py = ay / na;                                    // a/|a|
+        s = mk((px * b.x + py * b.y) / den, (py * b.x - px * b.y) / den);       // ph*conj(b)/den
     }
-    cs[j] = make_double2(c, 0.0);
+    cs[j] = mk(c, (Re)0);
     sn[j] = s;
-    col[j] = make_double2(c * a.x + (s.x * b.x - s.y * b.y), c * a.y + (s.x * b.y + s.y * b.x));
-    col[j + 1] = make_double2(0.0, 0.0);
-    const double2 g0 = gj;
-    gj1 = make_double2(-(s.x * g0.x + s.y * g0.y), -(s.x * g0.y - s.y * g0.x));   // -conj(s) g_j
-    gj = make_double2(c * g0.x, c * g0.y);
+    col[j] = mk(c * ax + (s.x * b.x - s.y * b.y), c * ay + (s.x * b.y + s.y * b.x));
+    col[j + 1] = mk((Re)0, (Re)0);
+    const C2 g0 = gj;
+    gj1 = mk(-(s.x * g0.x + s.y * g0.y), -(s.x * g0.y - s.y * g0.x));          // -conj(s) g_j
+    gj = mk(c * g0.x, c * g0.y);
 }
-
 template <typename T> __device__ __forceinline__ T from_c128(double2 a);
 template <> __device__ __forceinline__ float2 from_c128<float2>(double2 a) { return to_c64(a); }
 template <> __device__ __forceinline__ double2 from_c128<double2>(double2 a) { return a; }
@@ -179,6 +187,7 @@ template <typename R> struct IfaceArgs {
     int mask;
     T* dst; T* dst2; const T* base; const T* sub;
     void* bufs[3];             // sweep kernel: the interface buffers B, X, Y the stages name
+    int* err;                  // HELM_ERR_TIMEOUT when a bounded wait expired
 };
 
 // one interface stage of a sweep run by the persistent sweep kernel (device table)

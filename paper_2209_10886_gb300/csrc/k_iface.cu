@@ -37,13 +37,47 @@ __device__ __forceinline__ T ldg_(const T* p) {
 
 // one work item of an interface stage: subdomain a.subs[item_sub], output rows
 // [row_block*RB, +RB) of its masked sides, RHS [rhs_block*NR, +NR)
+// mbarrier primitives (the staged form of iface_kernel)
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ bool mb_try(unsigned long long* b, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait (~1 s); false when it expired
+__device__ __forceinline__ bool mb_wait(unsigned long long* b, unsigned parity) {
+    if (mb_try(b, parity)) return true;
+    const long long t0 = clock64();
+    while (!mb_try(b, parity))
+        if (clock64() - t0 > SWEEP_WAIT) return false;
+    return true;
+}
+
 // v[s] for a runtime s in 0..3 without indexing the array (keeps it in registers)
 __device__ __forceinline__ int sel4(const int (&v)[4], int s) {
     return s == 0 ? v[0] : s == 1 ? v[1] : s == 2 ? v[2] : v[3];
 }
 
+// Row stride (elements) of a staged K row: room for a row copied in whole 16-byte
+// units from any start, and a multiple of 16 bytes
+template <typename T> __host__ __device__ __forceinline__ int staged_ld(int Lb) {
+    return sizeof(T) == 8 ? ((Lb + 3) & ~1) : Lb;
+}
+
+// One work item.  Everything before the gather reads only data that no stage
+// writes (the subdomain table and K), so a launch that depends programmatically
+// on the previous stage does it while that stage still runs and waits
+// (griddepcontrol.wait, a no-op without such a dependency) just before the
+// gather.  Staged form (kbar != nullptr, one item per CTA): warp 0 first starts
+// one bulk copy per output row of K into shared memory (rows at smem_raw,
+// staged_ld apart; kofs[q] = where row q starts in its slot).
 template <typename R, int NR, bool LDCG>
-__device__ void iface_item(const IfaceArgs<R>& a, int item_sub, int row_block, int rhs_block, unsigned char* smem_raw) {
+__device__ void iface_item(const IfaceArgs<R>& a, int item_sub, int row_block, int rhs_block, unsigned char* smem_raw,
+                           unsigned long long* kbar = nullptr, int* kofs = nullptr) {
     using T = Cx<R>;
     const SubDev sd = a.subtab[a.subs[item_sub]];
     const int Lb = sd.Lb;
@@ -61,8 +95,64 @@ __device__ void iface_item(const IfaceArgs<R>& a, int item_sub, int row_block, i
         if (on(s)) rcount += len(s);
     const int row0 = row_block * RB;
     if (row0 >= rcount) return;
+    // side s and point pt of output row `row` (s = -1 past the last row)
+    auto locate = [&](int row, int& s, int& pt) {
+        s = -1;
+        pt = row;
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+            if (s < 0 && on(t)) {
+                if (pt < len(t)) s = t;
+                else pt -= len(t);
+            }
+        if (row >= rcount) s = -1;
+    };
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool staged = kbar != nullptr;
+    const int Lbp = staged_ld<T>(Lb);
+    T* Ks = reinterpret_cast<T*>(smem_raw);        // staged: [RB][Lbp] rows of K
+    if (staged && warp == 0) {
+        // lane q < RB copies row row0 + q: from the 16-byte unit holding its first element
+        // to the one holding its last (complex64 rows need not start on a unit)
+        long long a0 = 0;
+        unsigned nbytes = 0;
+        if (lane < RB) {
+            int s, pt;
+            locate(row0 + lane, s, pt);
+            int off = 0;
+            if (s >= 0) {
+                const long long el = sd.koff + (long long)(sel4(bo, s) + pt) * Lb;
+                if constexpr (sizeof(T) == 8) {
+                    a0 = el & ~1LL;
+                    off = (int)(el - a0);
+                    nbytes = (unsigned)((off + Lb + 1) & ~1) * 8u;
+                } else {
+                    a0 = el;
+                    nbytes = (unsigned)Lb * (unsigned)sizeof(T);
+                }
+            }
+            kofs[lane] = off;
+        }
+        unsigned tot = nbytes;
+        for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+        if (lane == 0) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(kbar)) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(kbar)), "r"(tot)
+                         : "memory");
+        }
+        __syncwarp();
+        if (nbytes > 0)
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                    smem_u32(Ks + (size_t)lane * Lbp)),
+                "l"(a.K + a0), "r"(nbytes), "r"(smem_u32(kbar))
+                : "memory");
+    }
+    // the incoming data, base and sub were written by earlier stages
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
 
-    T* graw = reinterpret_cast<T*>(smem_raw);      // [NR][Lb] incoming data
+    T* graw = staged ? Ks + (size_t)RB * Lbp : reinterpret_cast<T*>(smem_raw);   // [NR][Lb] incoming data
     T* g = graw + (size_t)NR * Lb;                 // [NR][Lb] cin * incoming data
     for (int idx = threadIdx.x; idx < NR * Lb; idx += IT) {
         const int k = idx / Lb, e = idx - k * Lb;
@@ -82,9 +172,24 @@ __device__ void iface_item(const IfaceArgs<R>& a, int item_sub, int row_block, i
         graw[idx] = G;
         g[idx] = Gs;
     }
-    __syncthreads();
+    if (staged) {
+        // every thread waits for the copies (bounded); a timeout anywhere ends the item
+        __shared__ int kfail;
+        if (threadIdx.x == 0) kfail = 0;
+        __syncthreads();
+        if (!mb_wait(kbar, 0)) kfail = 1;
+        __syncthreads();
+        if (kfail) {
+            if (threadIdx.x == 0) {
+                atomicExch(a.err, (int)HELM_ERR_TIMEOUT);
+                mb_wait(kbar, 0);                   // no copy outlives the CTA, bounded again
+            }
+            return;
+        }
+    } else {
+        __syncthreads();
+    }
 
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const T* K = a.K + sd.koff;
     // each warp takes RPW rows and keeps the loads of all of them in flight: columns in
     // groups of CU per lane (32 CU per group), every load of a group issued before its FMAs
@@ -94,19 +199,13 @@ __device__ void iface_item(const IfaceArgs<R>& a, int item_sub, int row_block, i
     const T* Kr[RPW];
 #pragma unroll
     for (int q = 0; q < RPW; ++q) {
-        const int row = row0 + warp + q * (IT / 32);
-        int s = -1, pt = row;
-#pragma unroll
-        for (int t = 0; t < 4; ++t)
-            if (s < 0 && on(t)) {
-                if (pt < len(t)) s = t;
-                else pt -= len(t);
-            }
-        if (row >= rcount) s = -1;
+        const int lr = warp + q * (IT / 32);       // row within the item
+        int s, pt;
+        locate(row0 + lr, s, pt);
         srow[q] = s;
         prow[q] = pt;
         krow[q] = s >= 0 ? sel4(bo, s) + pt : 0;
-        Kr[q] = K + (long long)krow[q] * Lb;
+        Kr[q] = staged ? Ks + (size_t)lr * Lbp + kofs[lr] : K + (long long)krow[q] * Lb;
     }
     T acc[RPW][NR];
 #pragma unroll
@@ -161,34 +260,45 @@ __device__ void iface_item(const IfaceArgs<R>& a, int item_sub, int row_block, i
     __syncthreads();                                // the shared gather is reused by the next item
 }
 
-template <typename R, int NR>
+// One stage, one item per CTA, launched with a programmatic dependency on the
+// previous kernel of the stream: each CTA lets the next stage launch at once
+// (that stage waits for this one to complete before its gather).
+template <typename R, int NR, bool STAGED>
 __global__ void __launch_bounds__(IT) iface_kernel(IfaceArgs<R> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    iface_item<R, NR, false>(a, blockIdx.x, blockIdx.y, blockIdx.z, smem_raw);
+    __shared__ __align__(8) unsigned long long kbar;
+    __shared__ int kofs[RB];
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+    if constexpr (STAGED) iface_item<R, NR, false>(a, blockIdx.x, blockIdx.y, blockIdx.z, smem_raw, &kbar, kofs);
+    else iface_item<R, NR, false>(a, blockIdx.x, blockIdx.y, blockIdx.z, smem_raw);
 }
 
 // grid-wide barrier of a cooperative launch; false (and HELM_ERR_TIMEOUT in err) when it expired
 __device__ bool sweep_barrier(unsigned* bar, int* err, volatile int* sflag) {
+    // bar[0] counts arrivals, bar[1] is the generation; the last arrival resets the count
+    // and publishes the next generation with release semantics, the others poll it with
+    // acquire loads (CTA writes before the barrier are ordered by __syncthreads and the
+    // release of thread 0's arrival)
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned* gen = bar + 1;
-        const unsigned g = *gen;
-        __threadfence();
-        if (atomicAdd(bar, 1u) == gridDim.x - 1) {
-            atomicExch(bar, 0u);
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
+        unsigned g, arrived;
+        asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(g) : "l"(bar + 1) : "memory");
+        asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(arrived) : "l"(bar) : "memory");
+        if (arrived == gridDim.x - 1) {
+            asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(bar), "r"(0u) : "memory");
+            asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(bar + 1), "r"(g + 1) : "memory");
         } else {
             const long long t0 = clock64();
-            while (*gen == g) {
-                if (clock64() - t0 > SWEEP_WAIT) {
+            unsigned cur;
+            do {
+                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(bar + 1) : "memory");
+                if (cur == g && clock64() - t0 > SWEEP_WAIT) {
                     atomicExch(err, (int)HELM_ERR_TIMEOUT);
                     *sflag = 1;
                     break;
                 }
-            }
+            } while (cur == g);
         }
-        __threadfence();
     }
     __syncthreads();
     return *sflag == 0;
@@ -226,16 +336,34 @@ __global__ void __launch_bounds__(IT) sweep_kernel(IfaceArgs<R> base, const Swee
     }
 }
 
+template <typename R, int NR, bool STAGED>
+cudaError_t launch_nr_s(const IfaceArgs<R>& a, int nactive, int max_rows, size_t smem, cudaStream_t st) {
+    cudaError_t e =
+        cudaFuncSetAttribute(iface_kernel<R, NR, STAGED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nactive, (max_rows + RB - 1) / RB, (a.nrhs + NR - 1) / NR);
+    cfg.blockDim = dim3(IT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    count_launch();
+    return cudaLaunchKernelEx(&cfg, iface_kernel<R, NR, STAGED>, a);
+}
+
+// staged when the item's K rows and gather fit two CTAs per SM (K 16-byte aligned)
 template <typename R, int NR>
 cudaError_t launch_nr(const IfaceArgs<R>& a, int nactive, int max_rows, int max_Lb, cudaStream_t st) {
     using T = Cx<R>;
-    const size_t smem = 2 * (size_t)NR * max_Lb * sizeof(T);
-    cudaError_t e = cudaFuncSetAttribute(iface_kernel<R, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    dim3 grid(nactive, (max_rows + RB - 1) / RB, (a.nrhs + NR - 1) / NR);
-    count_launch();
-    iface_kernel<R, NR><<<grid, IT, smem, st>>>(a);
-    return cudaGetLastError();
+    const size_t gather = 2 * (size_t)NR * max_Lb * sizeof(T);
+    const size_t staged = (size_t)RB * staged_ld<T>(max_Lb) * sizeof(T) + gather;
+    if (staged <= 113 * 1024 && (reinterpret_cast<uintptr_t>(a.K) & 15) == 0)
+        return launch_nr_s<R, NR, true>(a, nactive, max_rows, staged, st);
+    return launch_nr_s<R, NR, false>(a, nactive, max_rows, gather, st);
 }
 
 template <typename R, int NR>

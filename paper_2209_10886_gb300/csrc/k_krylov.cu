@@ -242,7 +242,7 @@ __global__ void hessenberg_step_kernel(double2* __restrict__ H, int ldh, long lo
         col[j + 1] = make_double2(hn, 0.0);
         double2* gk = g + (long long)k * ldg;
         double2 gj = gk[j], gj1;
-        givens_column(col, csv, snv, j, gj, gj1);
+        givens_column<double2>(col, csv, snv, j, gj, gj1);
         gk[j] = gj;
         gk[j + 1] = gj1;
         csk[j] = csv[j];

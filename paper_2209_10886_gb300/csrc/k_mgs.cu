@@ -48,26 +48,30 @@ __device__ __forceinline__ double2 warp_sum2(double2 v) {
 
 // grid-wide barrier over co-resident CTAs; returns false when the wait expired
 __device__ bool grid_barrier(unsigned* bar, int* err, int* sflag) {
+    // bar[0] counts arrivals, bar[1] is the generation; the last arrival resets the count
+    // and publishes the next generation with release semantics, the others poll it with
+    // acquire loads (CTA writes before the barrier are ordered by __syncthreads and the
+    // release of thread 0's arrival)
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned* gen = bar + 1;
-        const unsigned g = *gen;
-        __threadfence();
-        if (atomicAdd(bar, 1u) == gridDim.x - 1) {
-            atomicExch(bar, 0u);
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
+        unsigned g, arrived;
+        asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(g) : "l"(bar + 1) : "memory");
+        asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(arrived) : "l"(bar) : "memory");
+        if (arrived == gridDim.x - 1) {
+            asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(bar), "r"(0u) : "memory");
+            asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(bar + 1), "r"(g + 1) : "memory");
         } else {
             const long long t0 = clock64();
-            while (*gen == g) {
-                if (clock64() - t0 > BAR_LIMIT) {
+            unsigned cur;
+            do {
+                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(bar + 1) : "memory");
+                if (cur == g && clock64() - t0 > BAR_LIMIT) {
                     atomicExch(err, (int)HELM_ERR_TIMEOUT);
                     *sflag = 1;
                     break;
                 }
-            }
+            } while (cur == g);
         }
-        __threadfence();
     }
     __syncthreads();
     return *sflag == 0;
@@ -345,9 +349,10 @@ cudaError_t launch_ept(MgsArgs& a, int grid, cudaStream_t st) {
 // vectors q + 16 t and q + 8 + 16 t), reduces them over the grid (one barrier),
 // and updates its slice against the basis read from L2.  The norm, the
 // normalisation of v_{j+1} and the Givens update of the least-squares problem
-// (CTA 0) follow in the same launch.  VT = double2 or float2: products and
-// updates in the vectors' precision, sums across CTAs, coefficients and the
-// least-squares problem in FP64.  Reductions are deterministic: every CTA adds
+// (CTA 0) follow in the same launch.  VT = double2 or float2: products, updates
+// and the Givens arithmetic in the vectors' precision; sums across CTAs, the
+// coefficients and the stored least-squares problem in FP64 (the serial chain of
+// rotations in FP64 costs ~0.6 us per rotation on GB300's narrow FP64 pipe).  Reductions are deterministic: every CTA adds
 // the partials of all CTAs in the same order.  2 grid barriers per RHS, 4 when
 // the second pass runs, each bounded in time (HELM_ERR_TIMEOUT, then return).
 template <typename VT>
@@ -387,7 +392,7 @@ template <typename VT> __device__ __forceinline__ VT warp_sumc(VT v) {
 }
 
 template <typename VT>
-__global__ void __launch_bounds__(CT) cgs2_step_kernel(Cgs2Args<VT> a) {
+__global__ void __launch_bounds__(CT, 1) cgs2_step_kernel(Cgs2Args<VT> a) {
     using Re = decltype(VT::x);
     extern __shared__ __align__(16) double2 csm[];
     double2* hv = csm;                              // [j + 2] reduced values of the current pass
@@ -396,6 +401,7 @@ __global__ void __launch_bounds__(CT) cgs2_step_kernel(Cgs2Args<VT> a) {
     VT* hc = reinterpret_cast<VT*>(gv + 3 * (a.j + 2));   // [j + 1] -hv in the vectors' precision
     VT* ws = hc + (a.j + 1);                        // [L] slice of w
     __shared__ double red[CT / 32];
+    __shared__ double2 gsum[CT];                    // group sums of the grid reduction
     __shared__ int sflag;
     const int nvec = a.j + 1, PS = a.j + 2;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -415,26 +421,46 @@ __global__ void __launch_bounds__(CT) cgs2_step_kernel(Cgs2Args<VT> a) {
         return t;
     };
     // partials of this CTA are in part[cta*PS + 0..cnt); after the barrier every CTA
-    // sums column k over all CTAs in the same order into hv[k]
+    // sums column k over all CTAs in the same order into hv[k].  Per block of up to
+    // 32 columns: KP (a power of two >= the block's columns) lanes per column set,
+    // thread t takes column t % KP and the CTAs t / KP, t / KP + CT / KP, ... (loads
+    // coalesced along k, few per thread); a butterfly over the lanes of equal column,
+    // then the CT / 32 warp sums in order
     auto grid_reduce = [&](double2* part, int cnt) -> bool {
         if (!grid_barrier(a.bar, a.err, &sflag)) return false;
-        for (int k = warp; k < cnt; k += CT / 32) {
-            // up to 8 partials per lane in flight, added in a fixed order
+        const int G = (int)gridDim.x;
+        for (int kb = 0; kb < cnt; kb += 32) {
+            const int rem = min(32, cnt - kb);
+            int KP = 1;
+            while (KP < rem) KP <<= 1;
+            const int groups = CT / KP;
+            const int kq = threadIdx.x & (KP - 1), grp = threadIdx.x / KP;
             double2 t = make_double2(0.0, 0.0);
-            for (int cb = 0; cb < (int)gridDim.x; cb += 256) {
-                double2 pv[8];
+            if (kq < rem) {
+                for (int c0 = grp; c0 < G; c0 += groups * 8) {
+                    double2 pv[8];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int c = cb + lane + 32 * u;
-                    pv[u] = c < (int)gridDim.x ? __ldcg(part + (long long)c * PS + k) : make_double2(0.0, 0.0);
+                    for (int u = 0; u < 8; ++u) {
+                        const int c = c0 + groups * u;
+                        pv[u] = c < G ? __ldcg(part + (long long)c * PS + kb + kq) : make_double2(0.0, 0.0);
+                    }
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) { t.x += pv[u].x; t.y += pv[u].y; }
                 }
-#pragma unroll
-                for (int u = 0; u < 8; ++u) { t.x += pv[u].x; t.y += pv[u].y; }
             }
-            t = warp_sum2(t);
-            if (lane == 0) hv[k] = t;
+            for (int o = 16; o >= KP; o >>= 1) {
+                t.x += __shfl_xor_sync(0xffffffffu, t.x, o);
+                t.y += __shfl_xor_sync(0xffffffffu, t.y, o);
+            }
+            if (lane < KP) gsum[warp * KP + lane] = t;
+            __syncthreads();
+            if (threadIdx.x < rem) {
+                double2 v = gsum[threadIdx.x];
+                for (int q = 1; q < CT / 32; ++q) { v.x += gsum[q * KP + threadIdx.x].x; v.y += gsum[q * KP + threadIdx.x].y; }
+                hv[kb + threadIdx.x] = v;
+            }
+            __syncthreads();
         }
-        __syncthreads();
         ++s;
         return true;
     };
@@ -543,35 +569,50 @@ __global__ void __launch_bounds__(CT) cgs2_step_kernel(Cgs2Args<VT> a) {
         const Re invr = (Re)inv;
         for (int i = threadIdx.x; i < len; i += CT) w[c0 + i] = mk(ws[i].x * invr, ws[i].y * invr);
         if (blockIdx.x == 0) {
-            // h column, then the Givens update of the least-squares problem
-            double2* col = gv;
-            double2* csv = col + (a.j + 2);
-            double2* snv = csv + (a.j + 2);
+            // h column, then the Givens update of the least-squares problem in the
+            // vectors' precision: operands converted in parallel, the serial chain on
+            // thread 0, the results converted back in parallel
+            using C2 = VT;
+            C2* col = reinterpret_cast<C2*>(gv);
+            C2* csv = col + (a.j + 2);
+            C2* snv = csv + (a.j + 2);
             double2* csr = a.cs + (long long)r * a.ldg;
             double2* snr = a.sn + (long long)r * a.ldg;
-            for (int k = threadIdx.x; k <= a.j; k += CT) {
-                col[k] = h1[k];
-                a.hsum[(long long)r * a.ldh + k] = h1[k];
-                if (k < a.j) { csv[k] = csr[k]; snv[k] = snr[k]; }
+            double2* gr = a.g + (long long)r * a.ldg;
+            for (int k = threadIdx.x; k <= a.j + 1; k += CT) {
+                if (k <= a.j) a.hsum[(long long)r * a.ldh + k] = h1[k];
+                const double2 hk = k <= a.j ? h1[k] : make_double2(hn, 0.0);
+                col[k] = mk((Re)hk.x, (Re)hk.y);
+                if (k < a.j) {
+                    csv[k] = mk((Re)csr[k].x, (Re)0);
+                    snv[k] = mk((Re)snr[k].x, (Re)snr[k].y);
+                }
             }
+            __shared__ C2 gpair[2];
+            if (threadIdx.x == 0) gpair[0] = mk((Re)gr[a.j].x, (Re)gr[a.j].y);
             __syncthreads();
             if (threadIdx.x == 0) {
                 a.hnorm[r] = hn;
                 a.need[r] = second ? 1 : 0;
-                col[a.j + 1] = make_double2(hn, 0.0);
-                double2* gr = a.g + (long long)r * a.ldg;
-                double2 gj = gr[a.j], gj1;
-                givens_column(col, csv, snv, a.j, gj, gj1);
-                gr[a.j] = gj;
-                gr[a.j + 1] = gj1;
-                csr[a.j] = csv[a.j];
-                snr[a.j] = snv[a.j];
-                a.est[r] = sqrt(gj1.x * gj1.x + gj1.y * gj1.y);
+                C2 gj = gpair[0], gj1;
+                givens_column<C2>(col, csv, snv, a.j, gj, gj1);
+                gpair[0] = gj;
+                gpair[1] = gj1;
                 a.invh[r] = inv;
             }
             __syncthreads();
             double2* colg = a.H + r * a.hs + (long long)a.j * a.ldH;
-            for (int k = threadIdx.x; k <= a.j + 1; k += CT) colg[k] = col[k];
+            for (int k = threadIdx.x; k <= a.j + 1; k += CT) colg[k] = make_double2((double)col[k].x, (double)col[k].y);
+            if (threadIdx.x == 32) {
+                csr[a.j] = make_double2((double)csv[a.j].x, 0.0);
+                snr[a.j] = make_double2((double)snv[a.j].x, (double)snv[a.j].y);
+            }
+            if (threadIdx.x == 64) {
+                const C2 g0 = gpair[0], g1 = gpair[1];
+                gr[a.j] = make_double2((double)g0.x, (double)g0.y);
+                gr[a.j + 1] = make_double2((double)g1.x, (double)g1.y);
+                a.est[r] = sqrt((double)g1.x * (double)g1.x + (double)g1.y * (double)g1.y);
+            }
         }
         __syncthreads();                              // ws, hv, hc and h1 are reused by the next RHS
     }
