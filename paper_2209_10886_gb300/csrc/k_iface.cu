@@ -149,8 +149,43 @@ __device__ void iface_item(const IfaceArgs<R>& a, int item_sub, int row_block, i
                 "l"(a.K + a0), "r"(nbytes), "r"(smem_u32(kbar))
                 : "memory");
     }
+    // the rows of this warp and their transmission coefficients (immutable: before the wait)
+    constexpr int RPW = RB / (IT / 32);
+    constexpr int CU = (sizeof(R) == 8 && NR >= 4) ? 4 : 8;   // fits the 128-register bound
+    int srow[RPW], krow[RPW];
+    long long tofs[RPW];
+    T cca[RPW], ccb[RPW];
+#pragma unroll
+    for (int q = 0; q < RPW; ++q) {
+        int s, pt;
+        locate(row0 + warp + q * (IT / 32), s, pt);
+        srow[q] = s;
+        krow[q] = s >= 0 ? sel4(bo, s) + pt : 0;
+        tofs[q] = 0;
+        cca[q] = ccb[q] = czero<T>();
+        if (s >= 0) {
+            const TraceCoef<T> c = a.tc[sel4(tin, s) + pt];
+            cca[q] = c.ca;
+            ccb[q] = c.cb;
+            tofs[q] = (long long)(s == 0 ? sd.tout[0] : s == 1 ? sd.tout[1] : s == 2 ? sd.tout[2] : sd.tout[3]) + pt;
+        }
+    }
     // the incoming data, base and sub were written by earlier stages
     asm volatile("griddepcontrol.wait;\n" ::: "memory");
+    // base - sub of the warp's outputs (lane 0), loaded alongside the gather
+    T bsub[RPW][NR];
+#pragma unroll
+    for (int q = 0; q < RPW; ++q)
+#pragma unroll
+        for (int k = 0; k < NR; ++k) {
+            T v = czero<T>();
+            if (lane == 0 && srow[q] >= 0 && k < nr) {
+                const long long o = (long long)(rhs0 + k) * a.ntrace + tofs[q];
+                if (a.base) v = ldg_<T, LDCG>(a.base + o);
+                if (a.sub) v = csub(v, ldg_<T, LDCG>(a.sub + o));
+            }
+            bsub[q][k] = v;
+        }
 
     T* graw = staged ? Ks + (size_t)RB * Lbp : reinterpret_cast<T*>(smem_raw);   // [NR][Lb] incoming data
     T* g = graw + (size_t)NR * Lb;                 // [NR][Lb] cin * incoming data
@@ -193,18 +228,10 @@ __device__ void iface_item(const IfaceArgs<R>& a, int item_sub, int row_block, i
     const T* K = a.K + sd.koff;
     // each warp takes RPW rows and keeps the loads of all of them in flight: columns in
     // groups of CU per lane (32 CU per group), every load of a group issued before its FMAs
-    constexpr int RPW = RB / (IT / 32);
-    constexpr int CU = (sizeof(R) == 8 && NR >= 4) ? 4 : 8;   // fits the 128-register bound
-    int srow[RPW], prow[RPW], krow[RPW];
     const T* Kr[RPW];
 #pragma unroll
     for (int q = 0; q < RPW; ++q) {
         const int lr = warp + q * (IT / 32);       // row within the item
-        int s, pt;
-        locate(row0 + lr, s, pt);
-        srow[q] = s;
-        prow[q] = pt;
-        krow[q] = s >= 0 ? sel4(bo, s) + pt : 0;
         Kr[q] = staged ? Ks + (size_t)lr * Lbp + kofs[lr] : K + (long long)krow[q] * Lb;
     }
     T acc[RPW][NR];
@@ -243,15 +270,11 @@ __device__ void iface_item(const IfaceArgs<R>& a, int item_sub, int row_block, i
                 acc[q][k].y += __shfl_down_sync(0xffffffffu, acc[q][k].y, o);
             }
         if (lane == 0 && srow[q] >= 0) {
-            const int s = srow[q], pt = prow[q];
-            const long long ti = sel4(tin, s) + pt;
-            const long long to = (long long)(s == 0 ? sd.tout[0] : s == 1 ? sd.tout[1] : s == 2 ? sd.tout[2] : sd.tout[3]) + pt;
-            const TraceCoef<T> c = a.tc[ti];
-            for (int k = 0; k < nr; ++k) {
-                T out = cfma(c.cb, acc[q][k], cmul(c.ca, graw[k * Lb + krow[q]]));
-                const long long o = (long long)(rhs0 + k) * a.ntrace + to;
-                if (a.base) out = cadd(out, ldg_<T, LDCG>(a.base + o));
-                if (a.sub) out = csub(out, ldg_<T, LDCG>(a.sub + o));
+#pragma unroll
+            for (int k = 0; k < NR; ++k) {
+                if (k >= nr) break;
+                const T out = cadd(cfma(ccb[q], acc[q][k], cmul(cca[q], graw[k * Lb + krow[q]])), bsub[q][k]);
+                const long long o = (long long)(rhs0 + k) * a.ntrace + tofs[q];
                 a.dst[o] = out;
                 if (a.dst2) a.dst2[o] = out;
             }
