@@ -71,6 +71,9 @@ def parse():
                          "FGMRES with the sweep as preconditioner (at most this many steps); 0: one sweep")
     ap.add_argument("--inner-restart", type=int, default=30)
     ap.add_argument("--inner-tol", type=float, default=1e-2)
+    ap.add_argument("--persistent", action="store_true",
+                    help="run each sweep of the interface iterations as one cooperative launch (grid barriers "
+                         "between stages) instead of graph-replayed stage launches")
     ap.add_argument("--inner-fp64", action="store_true",
                     help="FP64 interface Krylov vectors with complex64 factors (default: complex64 vectors)")
     ap.add_argument("--tc-scale", type=float, default=0.5,
@@ -93,7 +96,7 @@ ORACLE_RESTART = 150
 def inner_kw(args):
     """Interface-Krylov options of Problem.solve."""
     return dict(inner_maxit=args.inner_maxit, inner_restart=args.inner_restart, inner_tol=args.inner_tol,
-                inner_fp64=args.inner_fp64)
+                inner_fp64=args.inner_fp64, persistent=args.persistent)
 
 
 def precond_only(args):
@@ -393,9 +396,10 @@ def gpu_arm(args):
 
     for _ in range(args.warmup):
         info = solve()
+    # timed region: the solves as a user runs them (no per-launch profiling events, so the
+    # interface Arnoldi steps run as device-driven graph loops)
     clocks = ClockSampler(local)
     clocks.start()
-    helm.profile(p, True)
     l0 = helm.launch_count()
     s0 = helm.inner_steps(p)
     barrier()
@@ -412,12 +416,23 @@ def gpu_arm(args):
     ms = e0.elapsed_time(e1) / args.steps
     launches = helm.launch_count() - l0
     inner_per_solve = (helm.inner_steps(p) - s0) / args.steps
+    clk = clocks.stop()
+    # second timed pass of the same solves with CUDA events around every launch (the
+    # host-driven interface loop): per-class kernel time and the live roofline
+    helm.profile(p, True)
+    torch.cuda.synchronize()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(st)
+    for _ in range(args.steps):
+        solve()
+    p1.record(st)
+    torch.cuda.synchronize()
+    ms_prof = p0.elapsed_time(p1) / args.steps
     stage = helm.profile_read(p, "stage")
     trace = helm.profile_read(p, "trace")
     matv = helm.profile_read(p, "matvec")
     orth = helm.profile_read(p, "ortho")
     helm.profile(p, False)
-    clk = clocks.stop()
     ms = max_over_ranks(ms, world, dev)
     relres = info[1]
 
@@ -531,13 +546,17 @@ def gpu_arm(args):
             "tensor_cores": args.tensor_cores, "tc_min_rhs": args.tc_min_rhs, "cuda_graph": args.graph,
             "interface_krylov": ({"inner_maxit": args.inner_maxit, "inner_restart": args.inner_restart,
                                   "inner_tol": args.inner_tol, "inner_steps_per_solve": inner_per_solve,
-                                  "vectors": "c128" if (args.inner_fp64 or args.prec == "c128") else "c64"}
+                                  "vectors": "c128" if (args.inner_fp64 or args.prec == "c128") else "c64",
+                                  "sweep": "persistent kernel" if args.persistent else "graph-replayed stage launches"}
                                  if args.inner_maxit > 0 else None),
             "relres_host_check": check, "factor_ms": factor_ms, "factor_bytes": p.info()["factor_bytes"],
             "l2": ("inputs larger than L2: every timed solve streams the 1.07 GB of factors in each lifting "
                    "and reconstruction, so no solve starts with a warm L2 (within a solve the 105 MB of "
                    "boundary operators are reused across the interface iterations)"),
             "parallelism": f"replicas x{world}",
+            "profiled_pass": {"ms_per_step": ms_prof,
+                              "note": "the same solves again with CUDA events around every launch (host-driven "
+                                      "interface loop); kernel_time_ms_per_step and the roofline come from it"},
             "kernel_time_ms_per_step": {"stage": stage[1] / args.steps, "trace": trace[1] / args.steps,
                                         "matvec": matv[1] / args.steps, "ortho": orth[1] / args.steps},
             "launches_per_step": {"stage": stage[0] / args.steps, "trace": trace[0] / args.steps},

@@ -25,7 +25,8 @@ template <typename VT>
 cudaError_t launch_cgs2_step(const VT* V, long long vsk, long long vsr, int j, long long n, int nrhs,
                              const int* active, double2* hsum, int ldh, double* hnorm, int* need, double2* H, int ldH,
                              long long hs, double2* cs, double2* sn, double2* g, int ldg, double* est, double* invh,
-                             double2* partial, unsigned* bar, int* err, int grid, cudaStream_t st);
+                             double2* partial, unsigned* bar, int* err, int grid, cudaStream_t st,
+                             const int* dj = nullptr, int jmax = 0);
 
 // ------------------------------------------------------------ launch count
 #include <atomic>
@@ -171,6 +172,10 @@ struct KrylovWS {
     unsigned* mgs_bar = nullptr;     // its grid-barrier state
     double2 *b = nullptr, *x = nullptr;   // interface solver: right-hand side and solution (nrhs x n)
     int nblk = 0;
+    // device-driven Arnoldi loop: ctl = {j, restart, maxit}, per-RHS step counts and stopping thresholds
+    int *ctl = nullptr, *iters = nullptr;
+    double* thr = nullptr;
+    long long gen = 0;               // allocation generation (keys the graphs that hold these pointers)
 };
 
 struct helm_problem {
@@ -258,7 +263,11 @@ struct helm_problem {
         int cls = -1;                // kernel class of the sequence (profiling), -1: none
         long long cls_kernels = 0;   // its launches, algorithmic bytes and flops per replay
         double cls_bytes = 0, cls_flops = 0;
+        cudaGraph_t tmpl = nullptr;  // device-loop graphs keep their template (conditional node)
+        long long gen = 0;           // Krylov workspace generation a device-loop graph was built for
+        int m = 0;                   // its restart length
     };
+    bool dev_loop_broken = false;    // a device-loop graph failed to build: host-driven loop from then on
     std::vector<PcGraph> graphs;
     cudaStream_t cap_stream = nullptr;
     cudaEvent_t cap_ev = nullptr;
@@ -328,7 +337,10 @@ extern "C" helm_status helm_profile_read(helm_problem* p, int k, helm_kstat* out
 
 // the captured graphs refer to the factors and the workspace: drop them whenever either changes
 static void drop_graphs(helm_problem* p) {
-    for (auto& g : p->graphs) cudaGraphExecDestroy(g.exec);
+    for (auto& g : p->graphs) {
+        cudaGraphExecDestroy(g.exec);
+        if (g.tmpl) cudaGraphDestroy(g.tmpl);
+    }
     p->graphs.clear();
 }
 static void free_pc_ws(helm_problem* p) {
@@ -346,6 +358,7 @@ static void free_kw(KrylovWS& w) {
     dfree(w.h1); dfree(w.h2); dfree(w.hsum); dfree(w.y); dfree(w.cpart);
     dfree(w.rpart); dfree(w.rn); dfree(w.est); dfree(w.invh); dfree(w.active); dfree(w.jcount); dfree(w.need);
     dfree(w.mgs_part); dfree(w.mgs_bar); dfree(w.b); dfree(w.x);
+    dfree(w.ctl); dfree(w.iters); dfree(w.thr);
     w.nrhs = w.restart = 0;
     w.n = 0;
 }
@@ -1281,6 +1294,9 @@ static helm_status ensure_kw(KrylovWS& w, int nrhs, int m, long long n, bool wit
     }
     chk(dalloc(w.est, (size_t)nrhs));
     chk(dalloc(w.invh, (size_t)nrhs));
+    chk(dalloc(w.ctl, (size_t)4));
+    chk(dalloc(w.iters, (size_t)nrhs));
+    chk(dalloc(w.thr, (size_t)nrhs));
     chk(dalloc(w.active, (size_t)nrhs));
     chk(dalloc(w.jcount, (size_t)nrhs));
     if (with_bx) {
@@ -1288,6 +1304,8 @@ static helm_status ensure_kw(KrylovWS& w, int nrhs, int m, long long n, bool wit
         chk(dalloc(w.x, (size_t)nrhs * n));
     }
     if (e != cudaSuccess) { free_kw(w); return cuda_status(e, "allocating the Krylov workspace"); }
+    static long long kw_generation = 0;
+    w.gen = ++kw_generation;
     w.nrhs = nrhs;
     w.restart = m;
     w.n = n;
@@ -1329,7 +1347,126 @@ struct KrylovOps {
     std::function<helm_status(const VT* x, bool x_zero, VT* r)> residual;   // r = b - A x
     std::function<helm_status(const VT* v, VT* z)> precond;                // z = M^{-1} v
     std::function<helm_status(const VT* z, VT* w)> matvec;                 // w = A z
+    // optional, for the device-driven loop: enqueue precond + matvec of Arnoldi step j = *dj
+    // (z_j = M^{-1} v_j into Z, w = A z_j into V slot j + 1) on stream cs without host work
+    // that depends on j, so that one capture serves every step
+    std::function<helm_status(cudaStream_t cs, VT* V, VT* Z, long long vsk, const int* dj)> dev_step;
 };
+
+// One restart cycle of FGMRES with the Arnoldi steps driven on the device (see
+// fgmres_core): the step (ops.dev_step, the fused Gram-Schmidt step and the loop
+// control, j read from kw.ctl) is captured once per workspace into the body of a
+// conditional while node; each cycle uploads the counters, launches the graph and
+// reads back the steps taken.  cycle_done = true when the cycle ran here; false
+// (and the host-driven loop runs instead) when the graph could not be built.
+template <typename VT>
+static helm_status device_cycle(helm_problem* p, KrylovWS& kw, long long N, int nrhs, int m, int maxit, double tol,
+                                const std::vector<double>& bnorm, const KrylovOps<VT>& ops, int grid,
+                                std::vector<int>& iters, std::vector<int>& active, std::vector<int>& jcount,
+                                bool& cycle_done, const char* who, cudaStream_t st) {
+    cycle_done = false;
+    const long long vsk = (long long)nrhs * N;
+    const int ld = m + 1;
+    VT* const KV = reinterpret_cast<VT*>(kw.V);
+    VT* const KZ = reinterpret_cast<VT*>(kw.Z);
+    const void* key = reinterpret_cast<const void*>((intptr_t)(1000 + (int)sizeof(VT)));
+    helm_problem::PcGraph* gr = nullptr;
+    for (auto& g : p->graphs)
+        if (g.sched == -2 && g.r == key && g.nrhs == nrhs && g.gen == kw.gen && g.m == m) gr = &g;
+    if (!gr) {
+        // graphs of earlier workspaces hold freed pointers: drop them
+        for (size_t i = 0; i < p->graphs.size();) {
+            auto& g = p->graphs[i];
+            if (g.sched == -2 && g.r == key) {
+                cudaGraphExecDestroy(g.exec);
+                if (g.tmpl) cudaGraphDestroy(g.tmpl);
+                p->graphs.erase(p->graphs.begin() + (long)i);
+            } else {
+                ++i;
+            }
+        }
+        if (!p->cap_stream) {
+            HELM_CUDA_TRY(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
+            HELM_CUDA_TRY(cudaEventCreateWithFlags(&p->cap_ev, cudaEventDisableTiming));
+        }
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        bool ok = cudaGraphCreate(&graph, 0) == cudaSuccess;
+        cudaGraphConditionalHandle h{};
+        cudaGraph_t body = nullptr;
+        if (ok) ok = cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+        if (ok) {
+            cudaGraphNodeParams np = {};
+            np.type = cudaGraphNodeTypeConditional;
+            np.conditional.handle = h;
+            np.conditional.type = cudaGraphCondTypeWhile;
+            np.conditional.size = 1;
+            cudaGraphNode_t node;
+            ok = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np) == cudaSuccess;
+            if (ok) body = np.conditional.phGraph_out[0];
+        }
+        long long step_kernels = 0;
+        if (ok) ok = cudaStreamBeginCaptureToGraph(p->cap_stream, body, nullptr, nullptr, 0,
+                                                   cudaStreamCaptureModeRelaxed) == cudaSuccess;
+        if (ok) {
+            const long long before = helm_launch_count();
+            helm_status q = ops.dev_step(p->cap_stream, KV, KZ, vsk, kw.ctl);
+            cudaError_t e = cudaSuccess;
+            if (q == HELM_OK)
+                e = launch_cgs2_step<VT>(KV, vsk, N, 0, N, nrhs, kw.active, kw.hsum, ld, kw.rn + 3 * nrhs, kw.need,
+                                         kw.H, ld, (long long)ld * m, kw.cs, kw.sn, kw.g, ld, kw.est, kw.invh,
+                                         kw.mgs_part, kw.mgs_bar, p->d_err, grid, p->cap_stream, kw.ctl, m - 1);
+            if (q == HELM_OK && e == cudaSuccess)
+                launch_arnoldi_ctl(kw.ctl, kw.est, kw.thr, kw.active, kw.iters, kw.jcount, maxit, nrhs, p->d_err, h,
+                                   p->cap_stream);
+            cudaGraph_t out = nullptr;
+            const cudaError_t ec = cudaStreamEndCapture(p->cap_stream, &out);
+            step_kernels = helm_launch_count() - before;
+            uncount_launch(step_kernels);
+            ok = q == HELM_OK && e == cudaSuccess && ec == cudaSuccess;
+            if (q != HELM_OK) { cudaGraphDestroy(graph); return q; }
+        }
+        if (ok) ok = cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+        if (!ok) {
+            // conditional graphs unavailable here: the host-driven loop from now on
+            (void)cudaGetLastError();
+            if (graph) cudaGraphDestroy(graph);
+            p->dev_loop_broken = true;
+            return HELM_OK;
+        }
+        helm_problem::PcGraph g{-2, nrhs, key, nullptr, exec, step_kernels};
+        g.tmpl = graph;
+        g.gen = kw.gen;
+        g.m = m;
+        p->graphs.push_back(g);
+        gr = &p->graphs.back();
+    }
+    // counters of this cycle: j = 0, the restart length, maxit; the steps taken so far
+    // and the stopping thresholds per RHS (active is already on the device)
+    {
+        const int ctl[4] = {0, m, maxit, 0};
+        std::vector<double> thr(nrhs);
+        for (int k = 0; k < nrhs; ++k) thr[k] = tol * bnorm[k];
+        HELM_CUDA_TRY(cudaMemcpyAsync(kw.ctl, ctl, sizeof(ctl), cudaMemcpyHostToDevice, st));
+        HELM_CUDA_TRY(cudaMemcpyAsync(kw.iters, iters.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, st));
+        HELM_CUDA_TRY(cudaMemcpyAsync(kw.thr, thr.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, st));
+        // zero for every RHS (the steps of the active ones are counted on the device)
+        HELM_CUDA_TRY(cudaMemcpyAsync(kw.jcount, jcount.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, st));
+        HELM_CUDA_TRY(cudaGraphLaunch(gr->exec, st));
+        int ctl_out[4] = {0, 0, 0, 0};
+        int dev_status = 0;
+        HELM_CUDA_TRY(cudaMemcpyAsync(ctl_out, kw.ctl, sizeof(ctl_out), cudaMemcpyDeviceToHost, st));
+        HELM_CUDA_TRY(cudaMemcpyAsync(iters.data(), kw.iters, nrhs * sizeof(int), cudaMemcpyDeviceToHost, st));
+        HELM_CUDA_TRY(cudaMemcpyAsync(jcount.data(), kw.jcount, nrhs * sizeof(int), cudaMemcpyDeviceToHost, st));
+        HELM_CUDA_TRY(cudaMemcpyAsync(active.data(), kw.active, nrhs * sizeof(int), cudaMemcpyDeviceToHost, st));
+        HELM_CUDA_TRY(cudaMemcpyAsync(&dev_status, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        HELM_CUDA_TRY(cudaStreamSynchronize(st));     // (thr and ctl are read before this returns)
+        if (dev_status != 0) return take_device_status(p, who);
+        count_launch((int)(gr->kernels * ctl_out[0]));
+    }
+    cycle_done = true;
+    return HELM_OK;
+}
 
 // Restarted right-preconditioned flexible GMRES: x is the initial guess on entry
 // (zero unless x0_given) and the iterate on exit; bnorm holds ||b|| per RHS;
@@ -1362,6 +1499,12 @@ static helm_status fgmres_core(helm_problem* p, KrylovWS& kw, long long n, int n
     const int cgs2_grid_n =
         (!use_mgs && ortho != HELM_ORTHO_CGS2_SPLIT && kw.mgs_part != nullptr && kw.restart >= m) ? cgs2_grid<VT>(N, m)
                                                                                                 : 0;
+    // device-driven Arnoldi loop: one graph launch per restart cycle, the steps repeated
+    // by a conditional (while) node until every RHS stopped or the cycle is full; the
+    // host synchronises once per cycle instead of once per step.  Needs the fused
+    // Gram-Schmidt step, no residual history and no per-launch profiling events.
+    const bool dev_loop = ops.dev_step && cgs2_grid_n > 0 && !hist && !p->prof_on && !p->persistent &&
+                          !p->dev_loop_broken && kw.ctl && kw.restart >= m;
     if (!x0_given) HELM_CUDA_TRY(cudaMemsetAsync(x, 0, (size_t)nrhs * N * sizeof(VT), st));
 
     std::vector<double> rn(nrhs), est(nrhs);
@@ -1405,7 +1548,13 @@ static helm_status fgmres_core(helm_problem* p, KrylovWS& kw, long long n, int n
             launch_scale_vec(KV, N, KV, N, kw.invh, N, nrhs, kw.active, st);
             HELM_CUDA_TRY(cudaStreamSynchronize(st));    // host vectors above go out of scope
         }
-        for (int j = 0; j < m; ++j) {
+        bool cycle_done = false;
+        if (dev_loop) {
+            s = device_cycle<VT>(p, kw, N, nrhs, m, maxit, tol, bnorm, ops, cgs2_grid_n, iters, active, jcount,
+                                 cycle_done, who, st);
+            if (s != HELM_OK) return s;
+        }
+        for (int j = 0; j < m && !cycle_done; ++j) {
             VT* Vj = KV + (long long)j * vsk;
             VT* Vn = KV + (long long)(j + 1) * vsk;
             VT* Zj = KZ + (long long)j * vsk;
@@ -1588,6 +1737,22 @@ static helm_status run_precond_iface_t(helm_problem* p, int sched, const double2
         launch_trace_to<T, VT>(tX, sched == HELM_SCHED_BSP ? tY : (T*)nullptr, 1, zv, tot, st);
         return HELM_OK;
     };
+    // one Arnoldi step with the slot read on the device (*dj): the same kernels as
+    // precond + matvec above, launched directly (this runs under a capture)
+    if (!p->persistent)
+        ops.dev_step = [&](cudaStream_t cs, VT* V, VT* Z, long long vsk, const int* dj) -> helm_status {
+            launch_trace_from<VT, T>(V, tB, tX, tot, cs, dj, 0, vsk);
+            for (size_t i = 1; i + 1 < stg.size(); ++i) {
+                helm_status q = run_stage_t<R>(p, w, cx, stg[i], r, z, nrhs, cs);
+                if (q != HELM_OK) return q;
+            }
+            launch_trace_to<T, VT>(tX, sched == HELM_SCHED_BSP ? tY : (T*)nullptr, 1, Z, tot, cs, dj, 0, vsk);
+            launch_trace_from<VT, T>(Z, tX, (T*)nullptr, tot, cs, dj, 0, vsk);
+            helm_status q = run_stage_t<R>(p, w, cx, sS, r, z, nrhs, cs);
+            if (q != HELM_OK) return q;
+            launch_trace_to<T, VT>(tB, nullptr, -1, V, tot, cs, dj, 1, vsk);
+            return HELM_OK;
+        };
     ops.residual = [&](const VT* x, bool x_zero, VT* rv) -> helm_status {
         if (x_zero) {
             HELM_CUDA_TRY(cudaMemcpyAsync(rv, kb, (size_t)tot * sizeof(VT), cudaMemcpyDeviceToDevice, st));

@@ -290,15 +290,20 @@ void launch_sqrt_inplace(double* v, int n, cudaStream_t st);
 // interface vectors (T = the trace buffers' complex type, VT = the Krylov vectors'):
 // out = sign (a + b) (b optional, sign +1 or -1); out (and out2) = in rounded to T; r = b - w
 template <typename T, typename VT>
-void launch_trace_to(const T* a, const T* b, int sign, VT* out, long long total, cudaStream_t st);
+void launch_trace_to(const T* a, const T* b, int sign, VT* out, long long total, cudaStream_t st,
+                     const int* dj = nullptr, int joff = 0, long long vsk = 0);
 template <typename VT, typename T>
-void launch_trace_from(const VT* in, T* out, T* out2, long long total, cudaStream_t st);
+void launch_trace_from(const VT* in, T* out, T* out2, long long total, cudaStream_t st, const int* dj = nullptr,
+                       int joff = 0, long long vsk = 0);
 template <typename VT>
 void launch_sub(const VT* b, const VT* w, VT* r, long long total, cudaStream_t st);
 // out[k*n + i] = complex64(src[k*n + i] * scale[k])
 void launch_to_c64_scaled(const double2* src, const double* scale, float2* out, long long n, int nrhs,
                           cudaStream_t st);
 void launch_scale_from_norm(const double* norm2, double* inv, double* scale, int n, cudaStream_t st);
+// device-driven Arnoldi loop: step bookkeeping and the loop condition (ctl[0] = j, ctl[1] = restart)
+void launch_arnoldi_ctl(int* ctl, const double* est, const double* thr, int* active, int* iters, int* jcount,
+                        int maxit, int nrhs, const int* err, cudaGraphConditionalHandle h, cudaStream_t st);
 // adjoint
 void launch_receiver_residual(const double2* u, long long N, const int* rec, int nrec, const double2* d,
                               int nsrc, double2* res, double* partial, cudaStream_t st);

@@ -413,10 +413,12 @@ template <> __device__ __forceinline__ double2 cvt<double2, double2>(double2 a) 
 template <> __device__ __forceinline__ double2 cvt<double2, float2>(float2 a) { return to_c128(a); }
 template <> __device__ __forceinline__ float2 cvt<float2, double2>(double2 a) { return to_c64(a); }
 
-// out = sign * (a + b) for n * nrhs values, b optional
+// out = sign * (a + b) for n * nrhs values, b optional; with dj, out is the Krylov slot
+// *dj + joff of an array of slots vsk apart (the slot index read on the device)
 template <typename T, typename VT>
 __global__ void trace_to_kernel(const T* __restrict__ a, const T* __restrict__ b, int sign, VT* __restrict__ out,
-                                long long total) {
+                                long long total, const int* dj, int joff, long long vsk) {
+    if (dj) out += (long long)(*dj + joff) * vsk;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x) {
         VT v = cvt<VT>(a[i]);
@@ -424,10 +426,11 @@ __global__ void trace_to_kernel(const T* __restrict__ a, const T* __restrict__ b
         out[i] = sign < 0 ? mk(-v.x, -v.y) : v;
     }
 }
-// out (and out2, optional) = in rounded to T
+// out (and out2, optional) = in rounded to T; with dj, in is the slot *dj + joff
 template <typename VT, typename T>
 __global__ void trace_from_kernel(const VT* __restrict__ in, T* __restrict__ out, T* __restrict__ out2,
-                                  long long total) {
+                                  long long total, const int* dj, int joff, long long vsk) {
+    if (dj) in += (long long)(*dj + joff) * vsk;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x) {
         const T f = cvt<T>(in[i]);
@@ -446,26 +449,64 @@ __global__ void sub_kernel(const VT* __restrict__ b, const VT* __restrict__ w, V
 static int small_grid(long long total) { return (int)std::min<long long>(1216, (total + 255) / 256 + 1); }
 
 template <typename T, typename VT>
-void launch_trace_to(const T* a, const T* b, int sign, VT* out, long long total, cudaStream_t st) {
+void launch_trace_to(const T* a, const T* b, int sign, VT* out, long long total, cudaStream_t st, const int* dj,
+                     int joff, long long vsk) {
     count_launch();
-    trace_to_kernel<T, VT><<<small_grid(total), 256, 0, st>>>(a, b, sign, out, total);
+    trace_to_kernel<T, VT><<<small_grid(total), 256, 0, st>>>(a, b, sign, out, total, dj, joff, vsk);
 }
 template <typename VT, typename T>
-void launch_trace_from(const VT* in, T* out, T* out2, long long total, cudaStream_t st) {
+void launch_trace_from(const VT* in, T* out, T* out2, long long total, cudaStream_t st, const int* dj, int joff,
+                       long long vsk) {
     count_launch();
-    trace_from_kernel<VT, T><<<small_grid(total), 256, 0, st>>>(in, out, out2, total);
+    trace_from_kernel<VT, T><<<small_grid(total), 256, 0, st>>>(in, out, out2, total, dj, joff, vsk);
 }
 template <typename VT>
 void launch_sub(const VT* b, const VT* w, VT* r, long long total, cudaStream_t st) {
     count_launch();
     sub_kernel<VT><<<small_grid(total), 256, 0, st>>>(b, w, r, total);
 }
-#define HELM_TRACE_INST(T, VT)                                                                      \
-    template void launch_trace_to<T, VT>(const T*, const T*, int, VT*, long long, cudaStream_t);    \
-    template void launch_trace_from<VT, T>(const VT*, T*, T*, long long, cudaStream_t);
+#define HELM_TRACE_INST(T, VT)                                                                                 \
+    template void launch_trace_to<T, VT>(const T*, const T*, int, VT*, long long, cudaStream_t, const int*, int,  \
+                                         long long);                                                           \
+    template void launch_trace_from<VT, T>(const VT*, T*, T*, long long, cudaStream_t, const int*, int, long long);
 HELM_TRACE_INST(float2, float2)
 HELM_TRACE_INST(float2, double2)
 HELM_TRACE_INST(double2, double2)
 #undef HELM_TRACE_INST
 template void launch_sub<float2>(const float2*, const float2*, float2*, long long, cudaStream_t);
 template void launch_sub<double2>(const double2*, const double2*, double2*, long long, cudaStream_t);
+
+// ------------------------------------------------ device-side Arnoldi loop control
+// After Arnoldi step ctl[0] = j of a device-driven FGMRES cycle: every active RHS
+// counts the step (iters, jcount = j + 1) and stops at est <= thr (tol ||b||), at
+// ctl[2] (maxit) steps or on a non-finite estimate; the loop goes on while some RHS
+// is active, j + 1 < ctl[1] (the restart length) and no device wait expired.
+__global__ void arnoldi_ctl_kernel(int* ctl, const double* est, const double* thr, int* active, int* iters,
+                                   int* jcount, int nrhs, const int* err, cudaGraphConditionalHandle h) {
+    __shared__ int any;
+    if (threadIdx.x == 0) any = 0;
+    __syncthreads();
+    const int j = ctl[0], maxit = ctl[2];
+    for (int k = threadIdx.x; k < nrhs; k += blockDim.x) {
+        if (!active[k]) continue;
+        const int it = iters[k] + 1;
+        iters[k] = it;
+        jcount[k] = j + 1;
+        const double e = est[k];
+        if (e <= thr[k] || it >= maxit || !isfinite(e)) active[k] = 0;
+        else atomicOr(&any, 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int jn = j + 1;
+        ctl[0] = jn;
+        const bool more = any && jn < ctl[1] && *err == 0;
+        cudaGraphSetConditional(h, more ? 1u : 0u);
+    }
+}
+void launch_arnoldi_ctl(int* ctl, const double* est, const double* thr, int* active, int* iters, int* jcount,
+                        int maxit, int nrhs, const int* err, cudaGraphConditionalHandle h, cudaStream_t st) {
+    count_launch();
+    (void)maxit;   // read on the device from ctl[2]: one graph serves every maxit
+    arnoldi_ctl_kernel<<<1, 256, 0, st>>>(ctl, est, thr, active, iters, jcount, nrhs, err, h);
+}

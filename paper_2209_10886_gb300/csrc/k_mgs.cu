@@ -379,6 +379,7 @@ struct Cgs2Args {
     unsigned* bar;
     int* err;
     int L;                     // slice length per CTA
+    const int* dj;             // when set, j is read from here (a device-driven loop)
 };
 
 constexpr int CT = 256;        // threads per CTA of the fused step
@@ -393,17 +394,18 @@ template <typename VT> __device__ __forceinline__ VT warp_sumc(VT v) {
 
 template <typename VT>
 __global__ void __launch_bounds__(CT, 1) cgs2_step_kernel(Cgs2Args<VT> a) {
+    const int J = a.dj ? *a.dj : a.j;             // the new column
     using Re = decltype(VT::x);
     extern __shared__ __align__(16) double2 csm[];
     double2* hv = csm;                              // [j + 2] reduced values of the current pass
-    double2* h1 = hv + (a.j + 2);                   // [j + 1] coefficients, both passes
-    double2* gv = h1 + (a.j + 1);                   // [3 (j + 2)] Givens scratch (CTA 0)
-    VT* hc = reinterpret_cast<VT*>(gv + 3 * (a.j + 2));   // [j + 1] -hv in the vectors' precision
-    VT* ws = hc + (a.j + 1);                        // [L] slice of w
+    double2* h1 = hv + (J + 2);                   // [j + 1] coefficients, both passes
+    double2* gv = h1 + (J + 1);                   // [3 (j + 2)] Givens scratch (CTA 0)
+    VT* hc = reinterpret_cast<VT*>(gv + 3 * (J + 2));   // [j + 1] -hv in the vectors' precision
+    VT* ws = hc + (J + 1);                        // [L] slice of w
     __shared__ double red[CT / 32];
     __shared__ double2 gsum[CT];                    // group sums of the grid reduction
     __shared__ int sflag;
-    const int nvec = a.j + 1, PS = a.j + 2;
+    const int nvec = J + 1, PS = J + 2;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long c0 = (long long)blockIdx.x * a.L;
     const int len = (int)max(0LL, min((long long)a.L, a.n - c0));
@@ -574,43 +576,43 @@ __global__ void __launch_bounds__(CT, 1) cgs2_step_kernel(Cgs2Args<VT> a) {
             // thread 0, the results converted back in parallel
             using C2 = VT;
             C2* col = reinterpret_cast<C2*>(gv);
-            C2* csv = col + (a.j + 2);
-            C2* snv = csv + (a.j + 2);
+            C2* csv = col + (J + 2);
+            C2* snv = csv + (J + 2);
             double2* csr = a.cs + (long long)r * a.ldg;
             double2* snr = a.sn + (long long)r * a.ldg;
             double2* gr = a.g + (long long)r * a.ldg;
-            for (int k = threadIdx.x; k <= a.j + 1; k += CT) {
-                if (k <= a.j) a.hsum[(long long)r * a.ldh + k] = h1[k];
-                const double2 hk = k <= a.j ? h1[k] : make_double2(hn, 0.0);
+            for (int k = threadIdx.x; k <= J + 1; k += CT) {
+                if (k <= J) a.hsum[(long long)r * a.ldh + k] = h1[k];
+                const double2 hk = k <= J ? h1[k] : make_double2(hn, 0.0);
                 col[k] = mk((Re)hk.x, (Re)hk.y);
-                if (k < a.j) {
+                if (k < J) {
                     csv[k] = mk((Re)csr[k].x, (Re)0);
                     snv[k] = mk((Re)snr[k].x, (Re)snr[k].y);
                 }
             }
             __shared__ C2 gpair[2];
-            if (threadIdx.x == 0) gpair[0] = mk((Re)gr[a.j].x, (Re)gr[a.j].y);
+            if (threadIdx.x == 0) gpair[0] = mk((Re)gr[J].x, (Re)gr[J].y);
             __syncthreads();
             if (threadIdx.x == 0) {
                 a.hnorm[r] = hn;
                 a.need[r] = second ? 1 : 0;
                 C2 gj = gpair[0], gj1;
-                givens_column<C2>(col, csv, snv, a.j, gj, gj1);
+                givens_column<C2>(col, csv, snv, J, gj, gj1);
                 gpair[0] = gj;
                 gpair[1] = gj1;
                 a.invh[r] = inv;
             }
             __syncthreads();
-            double2* colg = a.H + r * a.hs + (long long)a.j * a.ldH;
-            for (int k = threadIdx.x; k <= a.j + 1; k += CT) colg[k] = make_double2((double)col[k].x, (double)col[k].y);
+            double2* colg = a.H + r * a.hs + (long long)J * a.ldH;
+            for (int k = threadIdx.x; k <= J + 1; k += CT) colg[k] = make_double2((double)col[k].x, (double)col[k].y);
             if (threadIdx.x == 32) {
-                csr[a.j] = make_double2((double)csv[a.j].x, 0.0);
-                snr[a.j] = make_double2((double)snv[a.j].x, (double)snv[a.j].y);
+                csr[J] = make_double2((double)csv[J].x, 0.0);
+                snr[J] = make_double2((double)snv[J].x, (double)snv[J].y);
             }
             if (threadIdx.x == 64) {
                 const C2 g0 = gpair[0], g1 = gpair[1];
-                gr[a.j] = make_double2((double)g0.x, (double)g0.y);
-                gr[a.j + 1] = make_double2((double)g1.x, (double)g1.y);
+                gr[J] = make_double2((double)g0.x, (double)g0.y);
+                gr[J + 1] = make_double2((double)g1.x, (double)g1.y);
                 a.est[r] = sqrt((double)g1.x * (double)g1.x + (double)g1.y * (double)g1.y);
             }
         }
@@ -681,32 +683,45 @@ int cgs2_grid(long long n, int max_j) {
 // Column j of the Arnoldi process for every active RHS: CGS2-orthogonalise
 // v_{j+1} (in place in V) against v_0..v_j, normalise it, store h_{0..j+1,j}
 // and apply the Givens rotations (H, cs, sn, g, est, invh as the Hessenberg step
-// kernel leaves them).  partial holds 2 * grid * (j + 2) values.
+// kernel leaves them).  partial holds 2 * grid * (j + 2) values.  With dj, j is
+// read on the device (*dj, at most jmax) and shared memory is sized for jmax.
+// Launched through cudaLaunchKernelEx with the cooperative attribute, so it can
+// be captured into a graph.
 template <typename VT>
 cudaError_t launch_cgs2_step(const VT* V, long long vsk, long long vsr, int j, long long n, int nrhs,
                              const int* active, double2* hsum, int ldh, double* hnorm, int* need, double2* H, int ldH,
                              long long hs, double2* cs, double2* sn, double2* g, int ldg, double* est, double* invh,
-                             double2* partial, unsigned* bar, int* err, int grid, cudaStream_t st) {
+                             double2* partial, unsigned* bar, int* err, int grid, cudaStream_t st, const int* dj,
+                             int jmax) {
     if (grid <= 0) return cudaErrorInvalidValue;
     const int L = (int)((n + grid - 1) / grid);
     Cgs2Args<VT> a{V, vsk, vsr, j, n, nrhs, active, hsum, ldh, hnorm, need, H, ldH, hs, cs, sn, g, ldg, est, invh,
-                   partial, bar, err, L};
-    const size_t smem = cgs2_smem<VT>(L, j);
+                   partial, bar, err, L, dj};
+    const size_t smem = cgs2_smem<VT>(L, dj ? jmax : j);
     if (smem > 48 * 1024) {
         cudaError_t e =
             cudaFuncSetAttribute(cgs2_step_kernel<VT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    void* args[] = {&a};
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(CT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
     count_launch();
-    return cudaLaunchCooperativeKernel((const void*)cgs2_step_kernel<VT>, dim3(grid), dim3(CT), args, smem, st);
+    return cudaLaunchKernelEx(&cfg, cgs2_step_kernel<VT>, a);
 }
 #define HELM_CGS2_INST(VT)                                                                                        \
     template int cgs2_grid<VT>(long long, int);                                                                   \
     template cudaError_t launch_cgs2_step<VT>(const VT*, long long, long long, int, long long, int, const int*,   \
                                               double2*, int, double*, int*, double2*, int, long long, double2*,   \
                                               double2*, double2*, int, double*, double*, double2*, unsigned*, int*, \
-                                              int, cudaStream_t);
+                                              int, cudaStream_t, const int*, int);
 HELM_CGS2_INST(double2)
 HELM_CGS2_INST(float2)
 #undef HELM_CGS2_INST

@@ -256,6 +256,34 @@ def test_interface_krylov_gmres_matches_direct_solve(H, prec, sched):
     p.close()
 
 
+@pytest.mark.parametrize("prec", ["c64", "c128"])
+@pytest.mark.parametrize("sched", ["BSP", "SP"])
+def test_device_driven_interface_loop_matches_host_loop(H, prec, sched):
+    """The interface Arnoldi steps run as a conditional CUDA graph (device-side loop
+    control) unless per-launch profiling is on, which takes the host-driven loop; the
+    kernels and their order are the same, so are the iterates.  Three RHS that stop
+    at different steps (one zero RHS)."""
+    w = CASES["uneven_4x3"]()
+    p, _ = make(H, w, prec)
+    f = W.random_complex((3, w.N), 41)
+    f[1, : w.N // 3] = 0.0
+    f[2] = 0.0
+    kw = dict(tol=1e-9, restart=30, maxit=200, sched=sched, inner_maxit=60, inner_restart=12, inner_tol=1e-3)
+    s0 = H.inner_steps(p)
+    u0, i0, _ = p.solve(cuda(f), **kw)
+    n0 = H.inner_steps(p) - s0
+    H.profile(p, True)
+    s1 = H.inner_steps(p)
+    u1, i1, _ = p.solve(cuda(f), **kw)
+    n1 = H.inner_steps(p) - s1
+    H.profile(p, False)
+    print(f"{prec} {sched}: device loop its {[i[0] for i in i0]} inner {n0}, host loop its {[i[0] for i in i1]} inner {n1}")
+    assert [i[0] for i in i0] == [i[0] for i in i1] and n0 == n1
+    assert np.all(u0.cpu().numpy()[2] == 0) and i0[2][0] == 0
+    assert rel(u0.cpu().numpy()[:2], u1.cpu().numpy()[:2]) <= 1e-12
+    p.close()
+
+
 @pytest.mark.parametrize("sched", ["BSP", "SP"])
 def test_persistent_sweep_gives_the_same_solve(H, sched):
     """persistent: the interface stages of each sweep in one cooperative launch with grid
