@@ -72,10 +72,10 @@ template <typename T> __host__ __device__ __forceinline__ int staged_ld(int Lb) 
 // writes (the subdomain table and K), so a launch that depends programmatically
 // on the previous stage does it while that stage still runs and waits
 // (griddepcontrol.wait, a no-op without such a dependency) just before the
-// gather.  Staged form (kbar != nullptr, one item per CTA): warp 0 first starts
+// gather.  Staged form (STAGED, one item per CTA): warp 0 first starts
 // one bulk copy per output row of K into shared memory (rows at smem_raw,
 // staged_ld apart; kofs[q] = where row q starts in its slot).
-template <typename R, int NR, bool LDCG>
+template <typename R, int NR, bool LDCG, bool STAGED = false>
 __device__ void iface_item(const IfaceArgs<R>& a, int item_sub, int row_block, int rhs_block, unsigned char* smem_raw,
                            unsigned long long* kbar = nullptr, int* kofs = nullptr) {
     using T = Cx<R>;
@@ -108,7 +108,7 @@ __device__ void iface_item(const IfaceArgs<R>& a, int item_sub, int row_block, i
         if (row >= rcount) s = -1;
     };
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const bool staged = kbar != nullptr;
+    constexpr bool staged = STAGED;
     const int Lbp = staged_ld<T>(Lb);
     T* Ks = reinterpret_cast<T*>(smem_raw);        // staged: [RB][Lbp] rows of K
     if (staged && warp == 0) {
@@ -189,23 +189,38 @@ __device__ void iface_item(const IfaceArgs<R>& a, int item_sub, int row_block, i
 
     T* graw = staged ? Ks + (size_t)RB * Lbp : reinterpret_cast<T*>(smem_raw);   // [NR][Lb] incoming data
     T* g = graw + (size_t)NR * Lb;                 // [NR][Lb] cin * incoming data
-    for (int idx = threadIdx.x; idx < NR * Lb; idx += IT) {
-        const int k = idx / Lb, e = idx - k * Lb;
-        // the side holding boundary point e: the last interface side starting at or before it
-        int s = 0;
+    // every load of up to GU elements per thread is issued before the first is used
+    constexpr int GU = 4;
+    for (int i0 = threadIdx.x; i0 < NR * Lb; i0 += IT * GU) {
+        T G[GU], C[GU];
 #pragma unroll
-        for (int q = 1; q < 4; ++q)
-            if (bo[q] >= 0 && e >= bo[q]) s = q;
-        const long long ti = sel4(tin, s) + (e - sel4(bo, s));
-        T G = czero<T>(), Gs = czero<T>();
-        if (k < nr) {
-            const long long o = (long long)(rhs0 + k) * a.ntrace + ti;
-            if (a.gin0) G = ldg_<T, LDCG>(a.gin0 + o);
-            if (a.gin1) G = cadd(G, ldg_<T, LDCG>(a.gin1 + o));
-            Gs = cmul(G, a.tc[ti].cin);
+        for (int u = 0; u < GU; ++u) {
+            const int idx = i0 + u * IT;
+            G[u] = C[u] = czero<T>();
+            if (idx < NR * Lb) {
+                const int k = idx / Lb, e = idx - k * Lb;
+                // the side holding boundary point e: the last interface side starting at or before it
+                int s = 0;
+#pragma unroll
+                for (int q = 1; q < 4; ++q)
+                    if (bo[q] >= 0 && e >= bo[q]) s = q;
+                const long long ti = sel4(tin, s) + (e - sel4(bo, s));
+                if (k < nr) {
+                    const long long o = (long long)(rhs0 + k) * a.ntrace + ti;
+                    if (a.gin0) G[u] = ldg_<T, LDCG>(a.gin0 + o);
+                    if (a.gin1) G[u] = cadd(G[u], ldg_<T, LDCG>(a.gin1 + o));
+                    C[u] = a.tc[ti].cin;
+                }
+            }
         }
-        graw[idx] = G;
-        g[idx] = Gs;
+#pragma unroll
+        for (int u = 0; u < GU; ++u) {
+            const int idx = i0 + u * IT;
+            if (idx < NR * Lb) {
+                graw[idx] = G[u];
+                g[idx] = cmul(G[u], C[u]);
+            }
+        }
     }
     if (staged) {
         // every thread waits for the copies (bounded); a timeout anywhere ends the item
@@ -232,7 +247,8 @@ __device__ void iface_item(const IfaceArgs<R>& a, int item_sub, int row_block, i
 #pragma unroll
     for (int q = 0; q < RPW; ++q) {
         const int lr = warp + q * (IT / 32);       // row within the item
-        Kr[q] = staged ? Ks + (size_t)lr * Lbp + kofs[lr] : K + (long long)krow[q] * Lb;
+        if constexpr (STAGED) Kr[q] = Ks + (size_t)lr * Lbp + kofs[lr];
+        else Kr[q] = K + (long long)krow[q] * Lb;
     }
     T acc[RPW][NR];
 #pragma unroll
@@ -292,8 +308,7 @@ __global__ void __launch_bounds__(IT) iface_kernel(IfaceArgs<R> a) {
     __shared__ __align__(8) unsigned long long kbar;
     __shared__ int kofs[RB];
     asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
-    if constexpr (STAGED) iface_item<R, NR, false>(a, blockIdx.x, blockIdx.y, blockIdx.z, smem_raw, &kbar, kofs);
-    else iface_item<R, NR, false>(a, blockIdx.x, blockIdx.y, blockIdx.z, smem_raw);
+    iface_item<R, NR, false, STAGED>(a, blockIdx.x, blockIdx.y, blockIdx.z, smem_raw, &kbar, kofs);
 }
 
 // grid-wide barrier of a cooperative launch; false (and HELM_ERR_TIMEOUT in err) when it expired
