@@ -26,7 +26,8 @@ cudaError_t launch_cgs2_step(const VT* V, long long vsk, long long vsr, int j, l
                              const int* active, double2* hsum, int ldh, double* hnorm, int* need, double2* H, int ldH,
                              long long hs, double2* cs, double2* sn, double2* g, int ldg, double* est, double* invh,
                              double2* partial, unsigned* bar, int* err, int grid, cudaStream_t st,
-                             const int* dj = nullptr, int jmax = 0);
+                             const int* dj = nullptr, int jmax = 0, const VT* wsrc = nullptr,
+                             VT* vout1 = nullptr, VT* vout2 = nullptr);
 
 // ------------------------------------------------------------ launch count
 #include <atomic>
@@ -1351,6 +1352,15 @@ struct KrylovOps {
     // (z_j = M^{-1} v_j into Z, w = A z_j into V slot j + 1) on stream cs without host work
     // that depends on j, so that one capture serves every step
     std::function<helm_status(cudaStream_t cs, VT* V, VT* Z, long long vsk, const int* dj)> dev_step;
+    // optional refinements of dev_step: the operator's output is left negated in dev_w_src
+    // (instead of in V slot j + 1) for the Gram-Schmidt step to read, which also writes
+    // v_{j+1} into dev_v_out1/2 (the next step's input); dev_prologue(cs, V) prepares
+    // the first step's input from V slot 0
+    VT* dev_w_src = nullptr;
+    VT* dev_v_out1 = nullptr;
+    VT* dev_v_out2 = nullptr;
+    std::function<helm_status(cudaStream_t cs, VT* V)> dev_prologue;
+    int dev_tag = 0;   // identifies what dev_step enqueues (schedule, form): part of the graph key
 };
 
 // One restart cycle of FGMRES with the Arnoldi steps driven on the device (see
@@ -1369,7 +1379,7 @@ static helm_status device_cycle(helm_problem* p, KrylovWS& kw, long long N, int 
     const int ld = m + 1;
     VT* const KV = reinterpret_cast<VT*>(kw.V);
     VT* const KZ = reinterpret_cast<VT*>(kw.Z);
-    const void* key = reinterpret_cast<const void*>((intptr_t)(1000 + (int)sizeof(VT)));
+    const void* key = reinterpret_cast<const void*>((intptr_t)(1000 + (int)sizeof(VT) + 64 * ops.dev_tag));
     helm_problem::PcGraph* gr = nullptr;
     for (auto& g : p->graphs)
         if (g.sched == -2 && g.r == key && g.nrhs == nrhs && g.gen == kw.gen && g.m == m) gr = &g;
@@ -1415,7 +1425,8 @@ static helm_status device_cycle(helm_problem* p, KrylovWS& kw, long long N, int 
             if (q == HELM_OK)
                 e = launch_cgs2_step<VT>(KV, vsk, N, 0, N, nrhs, kw.active, kw.hsum, ld, kw.rn + 3 * nrhs, kw.need,
                                          kw.H, ld, (long long)ld * m, kw.cs, kw.sn, kw.g, ld, kw.est, kw.invh,
-                                         kw.mgs_part, kw.mgs_bar, p->d_err, grid, p->cap_stream, kw.ctl, m - 1);
+                                         kw.mgs_part, kw.mgs_bar, p->d_err, grid, p->cap_stream, kw.ctl, m - 1,
+                                         ops.dev_w_src, ops.dev_v_out1, ops.dev_v_out2);
             if (q == HELM_OK && e == cudaSuccess)
                 launch_arnoldi_ctl(kw.ctl, kw.est, kw.thr, kw.active, kw.iters, kw.jcount, maxit, nrhs, p->d_err, h,
                                    p->cap_stream);
@@ -1452,6 +1463,10 @@ static helm_status device_cycle(helm_problem* p, KrylovWS& kw, long long N, int 
         HELM_CUDA_TRY(cudaMemcpyAsync(kw.thr, thr.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, st));
         // zero for every RHS (the steps of the active ones are counted on the device)
         HELM_CUDA_TRY(cudaMemcpyAsync(kw.jcount, jcount.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, st));
+        if (ops.dev_prologue) {
+            helm_status q = ops.dev_prologue(st, KV);
+            if (q != HELM_OK) return q;
+        }
         HELM_CUDA_TRY(cudaGraphLaunch(gr->exec, st));
         int ctl_out[4] = {0, 0, 0, 0};
         int dev_status = 0;
@@ -1739,7 +1754,31 @@ static helm_status run_precond_iface_t(helm_problem* p, int sched, const double2
     };
     // one Arnoldi step with the slot read on the device (*dj): the same kernels as
     // precond + matvec above, launched directly (this runs under a capture)
-    if (!p->persistent)
+    if (!p->persistent && std::is_same<T, VT>::value) {
+        // vectors in the trace buffers' type: the step keeps its data in the trace
+        // buffers (the Gram-Schmidt step reads S v - v from B and writes the next input
+        // into B and X), one kernel between the sweep and S forms z_j
+        ops.dev_prologue = [&](cudaStream_t cs, VT* V) -> helm_status {
+            launch_trace_from<VT, T>(V, tB, tX, tot, cs);
+            return HELM_OK;
+        };
+        ops.dev_step = [&](cudaStream_t cs, VT* V, VT* Z, long long vsk, const int* dj) -> helm_status {
+            (void)V;
+            for (size_t i = 1; i + 1 < stg.size(); ++i) {
+                helm_status q = run_stage_t<R>(p, w, cx, stg[i], r, z, nrhs, cs);
+                if (q != HELM_OK) return q;
+            }
+            // z_j = X (+ Y) into Z slot j and into X, the input of S
+            launch_trace_to<T, VT>(tX, sched == HELM_SCHED_BSP ? tY : (T*)nullptr, 1, Z, tot, cs, dj, 0, vsk,
+                                   reinterpret_cast<VT*>(tX));
+            return run_stage_t<R>(p, w, cx, sS, r, z, nrhs, cs);
+        };
+        ops.dev_w_src = reinterpret_cast<VT*>(tB);
+        ops.dev_v_out1 = reinterpret_cast<VT*>(tB);
+        ops.dev_v_out2 = reinterpret_cast<VT*>(tX);
+        ops.dev_tag = 2 * sched + 1;
+    } else if (!p->persistent) {
+        ops.dev_tag = 2 * sched;
         ops.dev_step = [&](cudaStream_t cs, VT* V, VT* Z, long long vsk, const int* dj) -> helm_status {
             launch_trace_from<VT, T>(V, tB, tX, tot, cs, dj, 0, vsk);
             for (size_t i = 1; i + 1 < stg.size(); ++i) {
@@ -1753,6 +1792,7 @@ static helm_status run_precond_iface_t(helm_problem* p, int sched, const double2
             launch_trace_to<T, VT>(tB, nullptr, -1, V, tot, cs, dj, 1, vsk);
             return HELM_OK;
         };
+    }
     ops.residual = [&](const VT* x, bool x_zero, VT* rv) -> helm_status {
         if (x_zero) {
             HELM_CUDA_TRY(cudaMemcpyAsync(rv, kb, (size_t)tot * sizeof(VT), cudaMemcpyDeviceToDevice, st));

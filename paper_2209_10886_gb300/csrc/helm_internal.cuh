@@ -291,7 +291,7 @@ void launch_sqrt_inplace(double* v, int n, cudaStream_t st);
 // out = sign (a + b) (b optional, sign +1 or -1); out (and out2) = in rounded to T; r = b - w
 template <typename T, typename VT>
 void launch_trace_to(const T* a, const T* b, int sign, VT* out, long long total, cudaStream_t st,
-                     const int* dj = nullptr, int joff = 0, long long vsk = 0);
+                     const int* dj = nullptr, int joff = 0, long long vsk = 0, VT* out2 = nullptr);
 template <typename VT, typename T>
 void launch_trace_from(const VT* in, T* out, T* out2, long long total, cudaStream_t st, const int* dj = nullptr,
                        int joff = 0, long long vsk = 0);

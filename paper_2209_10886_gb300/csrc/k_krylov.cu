@@ -415,15 +415,18 @@ template <> __device__ __forceinline__ float2 cvt<float2, double2>(double2 a) { 
 
 // out = sign * (a + b) for n * nrhs values, b optional; with dj, out is the Krylov slot
 // *dj + joff of an array of slots vsk apart (the slot index read on the device)
+// (and into out2, optional, unshifted: may be a, each element is read before it is written)
 template <typename T, typename VT>
-__global__ void trace_to_kernel(const T* __restrict__ a, const T* __restrict__ b, int sign, VT* __restrict__ out,
-                                long long total, const int* dj, int joff, long long vsk) {
+__global__ void trace_to_kernel(const T* a, const T* __restrict__ b, int sign, VT* __restrict__ out,
+                                long long total, const int* dj, int joff, long long vsk, VT* out2) {
     if (dj) out += (long long)(*dj + joff) * vsk;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x) {
         VT v = cvt<VT>(a[i]);
         if (b) v = cadd(v, cvt<VT>(b[i]));
-        out[i] = sign < 0 ? mk(-v.x, -v.y) : v;
+        if (sign < 0) v = mk(-v.x, -v.y);
+        out[i] = v;
+        if (out2) out2[i] = v;
     }
 }
 // out (and out2, optional) = in rounded to T; with dj, in is the slot *dj + joff
@@ -450,9 +453,9 @@ static int small_grid(long long total) { return (int)std::min<long long>(1216, (
 
 template <typename T, typename VT>
 void launch_trace_to(const T* a, const T* b, int sign, VT* out, long long total, cudaStream_t st, const int* dj,
-                     int joff, long long vsk) {
+                     int joff, long long vsk, VT* out2) {
     count_launch();
-    trace_to_kernel<T, VT><<<small_grid(total), 256, 0, st>>>(a, b, sign, out, total, dj, joff, vsk);
+    trace_to_kernel<T, VT><<<small_grid(total), 256, 0, st>>>(a, b, sign, out, total, dj, joff, vsk, out2);
 }
 template <typename VT, typename T>
 void launch_trace_from(const VT* in, T* out, T* out2, long long total, cudaStream_t st, const int* dj, int joff,
@@ -467,7 +470,7 @@ void launch_sub(const VT* b, const VT* w, VT* r, long long total, cudaStream_t s
 }
 #define HELM_TRACE_INST(T, VT)                                                                                 \
     template void launch_trace_to<T, VT>(const T*, const T*, int, VT*, long long, cudaStream_t, const int*, int,  \
-                                         long long);                                                           \
+                                         long long, VT*);                                                      \
     template void launch_trace_from<VT, T>(const VT*, T*, T*, long long, cudaStream_t, const int*, int, long long);
 HELM_TRACE_INST(float2, float2)
 HELM_TRACE_INST(float2, double2)

@@ -380,6 +380,9 @@ struct Cgs2Args {
     int* err;
     int L;                     // slice length per CTA
     const int* dj;             // when set, j is read from here (a device-driven loop)
+    const VT* wsrc;            // when set, w = -wsrc (RHS r at wsrc + r*vsr) instead of the slot j + 1
+    VT* vout1;                 // when set, v_{j+1} is also written here and to vout2 (RHS r at + r*vsr)
+    VT* vout2;
 };
 
 constexpr int CT = 256;        // threads per CTA of the fused step
@@ -533,9 +536,16 @@ __global__ void __launch_bounds__(CT, 1) cgs2_step_kernel(Cgs2Args<VT> a) {
         if (a.active && !a.active[r]) continue;
         const VT* V = a.V + r * a.vsr;
         VT* w = const_cast<VT*>(V) + (long long)nvec * a.vsk;
+        const VT* wsrc = a.wsrc ? a.wsrc + r * a.vsr : nullptr;
         Re n0 = 0;
         for (int i = threadIdx.x; i < len; i += CT) {
-            const VT x = w[c0 + i];
+            VT x;
+            if (wsrc) {
+                x = wsrc[c0 + i];
+                x = mk(-x.x, -x.y);
+            } else {
+                x = w[c0 + i];
+            }
             ws[i] = x;
             n0 = fma(x.x, x.x, fma(x.y, x.y, n0));
         }
@@ -569,7 +579,12 @@ __global__ void __launch_bounds__(CT, 1) cgs2_step_kernel(Cgs2Args<VT> a) {
         const double hn = sqrt(hn2);
         const double inv = hn > 0.0 ? 1.0 / hn : 0.0;
         const Re invr = (Re)inv;
-        for (int i = threadIdx.x; i < len; i += CT) w[c0 + i] = mk(ws[i].x * invr, ws[i].y * invr);
+        for (int i = threadIdx.x; i < len; i += CT) {
+            const VT v = mk(ws[i].x * invr, ws[i].y * invr);
+            w[c0 + i] = v;
+            if (a.vout1) a.vout1[r * a.vsr + c0 + i] = v;
+            if (a.vout2) a.vout2[r * a.vsr + c0 + i] = v;
+        }
         if (blockIdx.x == 0) {
             // h column, then the Givens update of the least-squares problem in the
             // vectors' precision: operands converted in parallel, the serial chain on
@@ -685,6 +700,8 @@ int cgs2_grid(long long n, int max_j) {
 // and apply the Givens rotations (H, cs, sn, g, est, invh as the Hessenberg step
 // kernel leaves them).  partial holds 2 * grid * (j + 2) values.  With dj, j is
 // read on the device (*dj, at most jmax) and shared memory is sized for jmax.
+// With wsrc, w = -wsrc (the interface operator's output, S v - v); with vout1/2,
+// v_{j+1} is also written there (the next step's preconditioner input).
 // Launched through cudaLaunchKernelEx with the cooperative attribute, so it can
 // be captured into a graph.
 template <typename VT>
@@ -692,11 +709,11 @@ cudaError_t launch_cgs2_step(const VT* V, long long vsk, long long vsr, int j, l
                              const int* active, double2* hsum, int ldh, double* hnorm, int* need, double2* H, int ldH,
                              long long hs, double2* cs, double2* sn, double2* g, int ldg, double* est, double* invh,
                              double2* partial, unsigned* bar, int* err, int grid, cudaStream_t st, const int* dj,
-                             int jmax) {
+                             int jmax, const VT* wsrc, VT* vout1, VT* vout2) {
     if (grid <= 0) return cudaErrorInvalidValue;
     const int L = (int)((n + grid - 1) / grid);
     Cgs2Args<VT> a{V, vsk, vsr, j, n, nrhs, active, hsum, ldh, hnorm, need, H, ldH, hs, cs, sn, g, ldg, est, invh,
-                   partial, bar, err, L, dj};
+                   partial, bar, err, L, dj, wsrc, vout1, vout2};
     const size_t smem = cgs2_smem<VT>(L, dj ? jmax : j);
     if (smem > 48 * 1024) {
         cudaError_t e =
@@ -721,7 +738,7 @@ cudaError_t launch_cgs2_step(const VT* V, long long vsk, long long vsr, int j, l
     template cudaError_t launch_cgs2_step<VT>(const VT*, long long, long long, int, long long, int, const int*,   \
                                               double2*, int, double*, int*, double2*, int, long long, double2*,   \
                                               double2*, double2*, int, double*, double*, double2*, unsigned*, int*, \
-                                              int, cudaStream_t, const int*, int);
+                                              int, cudaStream_t, const int*, int, const VT*, VT*, VT*);
 HELM_CGS2_INST(double2)
 HELM_CGS2_INST(float2)
 #undef HELM_CGS2_INST

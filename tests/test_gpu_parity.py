@@ -256,31 +256,36 @@ def test_interface_krylov_gmres_matches_direct_solve(H, prec, sched):
     p.close()
 
 
-@pytest.mark.parametrize("prec", ["c64", "c128"])
-@pytest.mark.parametrize("sched", ["BSP", "SP"])
-def test_device_driven_interface_loop_matches_host_loop(H, prec, sched):
+@pytest.mark.parametrize("prec", ["c64", "c128", "c64_fp64_interface"])
+def test_device_driven_interface_loop_matches_host_loop(H, prec):
     """The interface Arnoldi steps run as a conditional CUDA graph (device-side loop
     control) unless per-launch profiling is on, which takes the host-driven loop; the
-    kernels and their order are the same, so are the iterates.  Three RHS that stop
-    at different steps (one zero RHS)."""
+    kernels and their order are the same, so are the iterates.  Both schedules on the
+    same problem, one after the other (each has its own graph); three RHS that stop at
+    different steps (one zero RHS)."""
     w = CASES["uneven_4x3"]()
-    p, _ = make(H, w, prec)
+    p, _ = make(H, w, prec.split("_")[0])
     f = W.random_complex((3, w.N), 41)
     f[1, : w.N // 3] = 0.0
     f[2] = 0.0
-    kw = dict(tol=1e-9, restart=30, maxit=200, sched=sched, inner_maxit=60, inner_restart=12, inner_tol=1e-3)
-    s0 = H.inner_steps(p)
-    u0, i0, _ = p.solve(cuda(f), **kw)
-    n0 = H.inner_steps(p) - s0
-    H.profile(p, True)
-    s1 = H.inner_steps(p)
-    u1, i1, _ = p.solve(cuda(f), **kw)
-    n1 = H.inner_steps(p) - s1
+    res = {}
+    for prof in (False, True):
+        H.profile(p, prof)
+        for sched in ("BSP", "SP"):
+            kw = dict(tol=1e-9, restart=30, maxit=200, sched=sched, inner_maxit=60, inner_restart=12,
+                      inner_tol=1e-3, inner_fp64=prec.endswith("fp64_interface"))
+            s0 = H.inner_steps(p)
+            u, info, _ = p.solve(cuda(f), **kw)
+            res[(prof, sched)] = (u.cpu().numpy(), [i[0] for i in info], H.inner_steps(p) - s0)
     H.profile(p, False)
-    print(f"{prec} {sched}: device loop its {[i[0] for i in i0]} inner {n0}, host loop its {[i[0] for i in i1]} inner {n1}")
-    assert [i[0] for i in i0] == [i[0] for i in i1] and n0 == n1
-    assert np.all(u0.cpu().numpy()[2] == 0) and i0[2][0] == 0
-    assert rel(u0.cpu().numpy()[:2], u1.cpu().numpy()[:2]) <= 1e-12
+    for sched in ("BSP", "SP"):
+        (u0, i0, n0), (u1, i1, n1) = res[(False, sched)], res[(True, sched)]
+        print(f"{prec} {sched}: device loop its {i0} inner {n0}, host loop its {i1} inner {n1}")
+        assert i0 == i1 and n0 == n1
+        assert np.all(u0[2] == 0) and i0[2] == 0
+        assert rel(u0[:2], u1[:2]) <= 1e-12
+    # the schedules differ (so each ran its own sweep)
+    assert res[(False, "BSP")][2] != res[(False, "SP")][2] or rel(res[(False, "BSP")][0][:2], res[(False, "SP")][0][:2]) > 1e-12
     p.close()
 
 
