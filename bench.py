@@ -60,9 +60,10 @@ def parse():
                          "(a small, fixed launch sequence for profilers); schedules: SP vs BSP on 5 x N2 "
                          "checkerboards, N2 = 5, 10, 15, 20 (the shape of Table 1)")
     ap.add_argument("--workload", default=None, choices=["plain_mixed", "batching", "large"],
-                    help="--mode precond only: the workload to factor (default: the bench workload)")
+                    help="the workload to factor (default: the 1023^2 one-source bench workload); solve mode "
+                         "reports the oracle baseline for the default workload only")
     ap.add_argument("--nrhs", type=int, default=None,
-                    help="--mode precond only: right-hand sides per application (default: the workload's)")
+                    help="right-hand sides (default: the workload's)")
     ap.add_argument("--tensor-cores", default="3xtf32", choices=["3xtf32", "tf32", "off"],
                     help="complex64 multi-RHS block solves (construction of K, batched RHS): tensor cores with "
                          "split TF32 operands, plain TF32, or FP32 on the CUDA cores")
@@ -377,7 +378,8 @@ def gpu_arm(args):
         if world > 1:
             dist.barrier()
 
-    w = W.workload(WORKLOAD)
+    wname = args.workload or WORKLOAD
+    w = W.workload(wname, nrhs=args.nrhs) if args.nrhs else W.workload(wname)
     m2 = torch.as_tensor(w.m2, dtype=torch.float64, device=dev)
     f = torch.as_tensor(w.f, dtype=torch.complex128, device=dev)
     p = Problem(w.n, w.n, w.h, w.omega, m2, w.N1, w.N2, w.xcuts, w.ycuts, tensor_cores=TC_MODES[args.tensor_cores],
@@ -521,7 +523,7 @@ def gpu_arm(args):
                     "traffic": None, "kernel": names.get(dom, dom), "launches": st_[0],
                     "peak_source": f"hbm_gbs of {peak_src}"}
     cpu = None
-    if not args.no_cpu_baseline and world == 1:
+    if not args.no_cpu_baseline and world == 1 and wname == WORKLOAD and not args.nrhs:
         try:
             res = run_oracle_sample(args.sched, ORACLE_RESTART, args.cpu_iters, 1)
             t_iter = res["t_iter"][-1]
@@ -550,9 +552,9 @@ def gpu_arm(args):
                                   "sweep": "persistent kernel" if args.persistent else "graph-replayed stage launches"}
                                  if args.inner_maxit > 0 else None),
             "relres_host_check": check, "factor_ms": factor_ms, "factor_bytes": p.info()["factor_bytes"],
-            "l2": ("inputs larger than L2: every timed solve streams the 1.07 GB of factors in each lifting "
-                   "and reconstruction, so no solve starts with a warm L2 (within a solve the 105 MB of "
-                   "boundary operators are reused across the interface iterations)"),
+            "l2": (f"inputs larger than L2: every timed solve streams the {p.info()['factor_bytes'] / 1e9:.2f} GB "
+                   "of factors in each lifting and reconstruction, so no solve starts with a warm L2 (within a "
+                   "solve the boundary operators are reused across the interface iterations)"),
             "parallelism": f"replicas x{world}",
             "profiled_pass": {"ms_per_step": ms_prof,
                               "note": "the same solves again with CUDA events around every launch (host-driven "

@@ -35,8 +35,6 @@ __device__ __forceinline__ T ldg_(const T* p) {
     else return *p;
 }
 
-// one work item of an interface stage: subdomain a.subs[item_sub], output rows
-// [row_block*RB, +RB) of its masked sides, RHS [rhs_block*NR, +NR)
 // mbarrier primitives (the staged form of iface_kernel)
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ bool mb_try(unsigned long long* b, unsigned parity) {
@@ -68,21 +66,23 @@ template <typename T> __host__ __device__ __forceinline__ int staged_ld(int Lb) 
     return sizeof(T) == 8 ? ((Lb + 3) & ~1) : Lb;
 }
 
-// One work item.  Everything before the gather reads only data that no stage
+// One work item of an interface stage: subdomain a.subs[item_sub], output rows
+// [row_block*RB, +RB) of its masked sides, the blocks of NR right-hand sides
+// rb_first, rb_first + rb_step, ... (the K rows are loaded once for all of them).
+// Everything before the gather reads only data that no stage
 // writes (the subdomain table and K), so a launch that depends programmatically
 // on the previous stage does it while that stage still runs and waits
 // (griddepcontrol.wait, a no-op without such a dependency) just before the
 // gather.  Staged form (STAGED, one item per CTA): warp 0 first starts
 // one bulk copy per output row of K into shared memory (rows at smem_raw,
 // staged_ld apart; kofs[q] = where row q starts in its slot).
-template <typename R, int NR, bool LDCG, bool STAGED = false>
-__device__ void iface_item(const IfaceArgs<R>& a, int item_sub, int row_block, int rhs_block, unsigned char* smem_raw,
-                           unsigned long long* kbar = nullptr, int* kofs = nullptr) {
+template <typename R, int NR, bool LDCG, bool STAGED = false, bool MULTI = false>
+__device__ void iface_item(const IfaceArgs<R>& a, int item_sub, int row_block, int rb_first, int rb_step,
+                           unsigned char* smem_raw, unsigned long long* kbar = nullptr, int* kofs = nullptr) {
     using T = Cx<R>;
     const SubDev sd = a.subtab[a.subs[item_sub]];
     const int Lb = sd.Lb;
-    const int rhs0 = rhs_block * NR;
-    const int nr = min(NR, a.nrhs - rhs0);
+    const int nrb = (a.nrhs + NR - 1) / NR;        // RHS blocks: this item takes rb_first, + rb_step, ...
     // the per-side tables as scalars (a dynamically indexed array would live in local memory)
     const int bo[4] = {sd.bo[0], sd.bo[1], sd.bo[2], sd.bo[3]};
     const int tin[4] = {sd.tin[0], sd.tin[1], sd.tin[2], sd.tin[3]};
@@ -172,6 +172,10 @@ __device__ void iface_item(const IfaceArgs<R>& a, int item_sub, int row_block, i
     }
     // the incoming data, base and sub were written by earlier stages
     asm volatile("griddepcontrol.wait;\n" ::: "memory");
+    // MULTI = false: exactly one block (straight-line code)
+    for (int rb = rb_first; MULTI ? rb < nrb : rb == rb_first; rb += rb_step) {
+    const int rhs0 = rb * NR;
+    const int nr = min(NR, a.nrhs - rhs0);
     // base - sub of the warp's outputs (lane 0), loaded alongside the gather
     T bsub[RPW][NR];
 #pragma unroll
@@ -222,7 +226,7 @@ __device__ void iface_item(const IfaceArgs<R>& a, int item_sub, int row_block, i
             }
         }
     }
-    if (staged) {
+    if (staged && rb == rb_first) {
         // every thread waits for the copies (bounded); a timeout anywhere ends the item
         __shared__ int kfail;
         if (threadIdx.x == 0) kfail = 0;
@@ -296,19 +300,20 @@ __device__ void iface_item(const IfaceArgs<R>& a, int item_sub, int row_block, i
             }
         }
     }
-    __syncthreads();                                // the shared gather is reused by the next item
+    __syncthreads();                                // the shared gather is reused by the next block
+    }
 }
 
 // One stage, one item per CTA, launched with a programmatic dependency on the
 // previous kernel of the stream: each CTA lets the next stage launch at once
 // (that stage waits for this one to complete before its gather).
-template <typename R, int NR, bool STAGED>
+template <typename R, int NR, bool STAGED, bool MULTI>
 __global__ void __launch_bounds__(IT) iface_kernel(IfaceArgs<R> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(8) unsigned long long kbar;
     __shared__ int kofs[RB];
     asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
-    iface_item<R, NR, false, STAGED>(a, blockIdx.x, blockIdx.y, blockIdx.z, smem_raw, &kbar, kofs);
+    iface_item<R, NR, false, STAGED, MULTI>(a, blockIdx.x, blockIdx.y, blockIdx.z, gridDim.z, smem_raw, &kbar, kofs);
 }
 
 // grid-wide barrier of a cooperative launch; false (and HELM_ERR_TIMEOUT in err) when it expired
@@ -368,19 +373,19 @@ __global__ void __launch_bounds__(IT) sweep_kernel(IfaceArgs<R> base, const Swee
         for (int it = blockIdx.x; it < items; it += gridDim.x) {
             const int sub_i = it / (rowb * rblocks);
             const int rem = it - sub_i * rowb * rblocks;
-            iface_item<R, NR, true>(a, sub_i, rem / rblocks, rem % rblocks, smem_raw);
+            iface_item<R, NR, true>(a, sub_i, rem / rblocks, rem % rblocks, 1 << 30, smem_raw);
         }
         if (s + 1 < nstages && !sweep_barrier(bar, err, &sflag)) return;
     }
 }
 
-template <typename R, int NR, bool STAGED>
-cudaError_t launch_nr_s(const IfaceArgs<R>& a, int nactive, int max_rows, size_t smem, cudaStream_t st) {
+template <typename R, int NR, bool STAGED, bool MULTI>
+cudaError_t launch_nr_s_m(const IfaceArgs<R>& a, int nactive, int max_rows, size_t smem, int zb, cudaStream_t st) {
     cudaError_t e =
-        cudaFuncSetAttribute(iface_kernel<R, NR, STAGED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(iface_kernel<R, NR, STAGED, MULTI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(nactive, (max_rows + RB - 1) / RB, (a.nrhs + NR - 1) / NR);
+    cfg.gridDim = dim3(nactive, (max_rows + RB - 1) / RB, zb);
     cfg.blockDim = dim3(IT);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
@@ -390,7 +395,25 @@ cudaError_t launch_nr_s(const IfaceArgs<R>& a, int nactive, int max_rows, size_t
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     count_launch();
-    return cudaLaunchKernelEx(&cfg, iface_kernel<R, NR, STAGED>, a);
+    return cudaLaunchKernelEx(&cfg, iface_kernel<R, NR, STAGED, MULTI>, a);
+}
+
+// RHS blocks: each CTA stages its K rows once and loops over the blocks z, z + gridDim.z,
+// ...; gridDim.z spreads them only as far as needed to fill the GPU about three times
+template <typename R, int NR, bool STAGED>
+cudaError_t launch_nr_s(const IfaceArgs<R>& a, int nactive, int max_rows, size_t smem, cudaStream_t st) {
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            sms = 1;
+    }
+    const long long items = (long long)nactive * ((max_rows + RB - 1) / RB);
+    const int nrb = (a.nrhs + NR - 1) / NR;
+    const int zb = (int)std::min<long long>(nrb, std::max<long long>(1, (3LL * sms + items - 1) / items));
+    if (zb == nrb) return launch_nr_s_m<R, NR, STAGED, false>(a, nactive, max_rows, smem, zb, st);
+    return launch_nr_s_m<R, NR, STAGED, true>(a, nactive, max_rows, smem, zb, st);
 }
 
 // staged when the item's K rows and gather fit two CTAs per SM (K 16-byte aligned)
