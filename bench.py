@@ -556,6 +556,7 @@ def gpu_arm(args):
                    "of factors in each lifting and reconstruction, so no solve starts with a warm L2 (within a "
                    "solve the boundary operators are reused across the interface iterations)"),
             "parallelism": f"replicas x{world}",
+            "iface_shape": helm.iface_shape(p, w.nrhs),
             "profiled_pass": {"ms_per_step": ms_prof,
                               "note": "the same solves again with CUDA events around every launch (host-driven "
                                       "interface loop); kernel_time_ms_per_step and the roofline come from it"},

@@ -118,6 +118,12 @@ typedef struct {
     int tc_min_rhs;     /* stages with at least this many right-hand sides use the tensor
                            cores (when tensor_cores != 0); default 16, minimum 1.  Below
                            16 the MMA columns are padded (N = 32 per 16 RHS) */
+    int autotune;       /* 1 (default): the first preconditioner application with a given
+                           RHS count (2 or more) times the candidate launch shapes of the
+                           interface-stage kernel (RHS per block 2/4/8/16, K rows staged in
+                           shared memory or not) on the all-subdomain stage S, on the
+                           caller's stream, and keeps the fastest for this problem;
+                           0: fixed rules (see helm_iface_shape) */
 } helm_setup_opts;
 
 typedef struct {
@@ -301,6 +307,12 @@ typedef struct {
     double bytes;          /* algorithmic bytes those launches must move (HBM reads +
                               writes of the data they touch, counted once) */
 } helm_kstat;
+
+/* Launch shape of the interface-stage kernel for nrhs right-hand sides on p: RHS per
+ * block (*nr), K rows staged in shared memory when they fit (*staged), target CTAs per SM
+ * (*waves); *tuned = 1 when the autotuner chose it, 0 for the fixed rules (4, 2 or 1 RHS
+ * per block, staged, 3).  Any output pointer may be NULL. */
+helm_status helm_iface_shape(const helm_problem* p, int nrhs, int* nr, int* staged, int* waves, int* tuned);
 
 /* Number of CUDA kernel launches issued by the library in this process. */
 long long helm_launch_count(void);

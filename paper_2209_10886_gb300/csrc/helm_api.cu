@@ -232,6 +232,8 @@ struct helm_problem {
     KrylovWS kw, kwi;
     long long inner_steps = 0;       // interface Krylov steps taken inside the preconditioner (all calls)
     int persistent = 0;              // gmres_solve option: sweeps in the persistent sweep kernel
+    struct TunedShape { int prec, nrhs; IfaceCfg cfg; };
+    std::vector<TunedShape> iface_tuned;   // autotuned interface-stage launch shapes
 
     // adjoint workspace
     double2 *d_res = nullptr, *d_fadj = nullptr, *d_U = nullptr, *d_L = nullptr;
@@ -400,6 +402,7 @@ extern "C" void helm_default_setup_opts(helm_setup_opts* o) {
     o->boundary_operators = 1;
     o->tensor_cores = 1;
     o->tc_min_rhs = 16;
+    o->autotune = 1;
 }
 
 extern "C" const char* helm_last_error(void) { return g_err.c_str(); }
@@ -452,6 +455,7 @@ extern "C" helm_status helm_setup(int n_x, int n_y, double h, double omega, cons
     if (so.transmission == HELM_TC_OPTIMIZED && !(so.tc_scale > 0)) return arg_error("helm_setup: tc_scale must be > 0");
     if (so.tensor_cores < 0 || so.tensor_cores > 2) return arg_error("helm_setup: tensor_cores must be 0, 1 or 2");
     if (so.tc_min_rhs < 1) return arg_error("helm_setup: tc_min_rhs must be >= 1");
+    if (so.autotune != 0 && so.autotune != 1) return arg_error("helm_setup: autotune must be 0 or 1");
 
     auto xc = make_cuts(n_x, N1, xcuts), yc = make_cuts(n_y, N2, ycuts);
     for (int k = 0; k < N1; ++k)
@@ -961,6 +965,101 @@ static PcCtx precond_prologue(helm_problem* p, const PcWork& w, const double2* r
 }
 
 // one stage of a schedule (one batched launch, two for mixed tensor-core tile counts)
+// autotuned launch shape of the interface stages for nrhs RHS (nullptr: the fixed rules)
+static const IfaceCfg* tuned_shape(const helm_problem* p, int nrhs) {
+    for (const auto& t : p->iface_tuned)
+        if (t.prec == p->prec && t.nrhs == nrhs) return &t.cfg;
+    return nullptr;
+}
+
+// The autotuner of the interface-stage kernel: the first application with nrhs >= 2 RHS
+// times each candidate shape (RHS per block 2/4/8/16 up to nrhs, K staged or not) on
+// the stage S (every subdomain, every side: reads X, writes B, so it may run any number
+// of times) with CUDA events on the caller's stream, after the work already queued
+// there, and keeps the fastest.  Runs before any graph capture of that RHS count.
+template <typename R>
+static helm_status tune_shape_t(helm_problem* p, int nrhs, cudaStream_t st) {
+    using T = Cx<R>;
+    const StageDesc& all = p->sched[HELM_SCHED_BSP].front();
+    IfaceArgs<R> ia{};
+    ia.subtab = p->d_subtab;
+    ia.subs = p->d_stage_subs + all.sub_off;
+    ia.nrhs = nrhs;
+    ia.ntrace = p->ntrace;
+    ia.K = (const T*)p->d_K;
+    ia.tc = sizeof(R) == 4 ? (const TraceCoef<T>*)p->d_tc64 : (const TraceCoef<T>*)p->d_tc128;
+    ia.gin0 = (const T*)p->d_trace[BUF_X];
+    ia.mask = 15;
+    ia.dst = (T*)p->d_trace[BUF_B];
+    ia.sub = (const T*)p->d_trace[BUF_X];
+    ia.err = p->d_err;
+    int max_rows = 0;
+    for (int id : all.subs) {
+        const SubDev& d = p->subs[id].dev;
+        int rows = 0;
+        for (int sde = 0; sde < 4; ++sde)
+            if (d.bo[sde] >= 0) rows += (sde == SW || sde == SE) ? d.my : d.mx;
+        max_rows = std::max(max_rows, rows);
+    }
+    HELM_CUDA_TRY(cudaMemsetAsync(p->d_trace[BUF_X], 0, (size_t)p->ntrace * nrhs * sizeof(T), st));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    HELM_CUDA_TRY(cudaEventCreate(&e0));
+    HELM_CUDA_TRY(cudaEventCreate(&e1));
+    const long long before = helm_launch_count();
+    IfaceCfg best{};
+    float best_ms = 1e30f;
+    for (int nr : {2, 4, 8, 16}) {
+        if (nr > 2 * nrhs || (nr == 16 && sizeof(R) != 4)) continue;
+        for (int staged : {1, 0}) {
+            IfaceCfg c;
+            c.nr = nr;
+            c.staged = staged;
+            c.waves = 3;
+            if (launch_iface<R>(ia, (int)all.subs.size(), max_rows, p->max_Lb, st, &c) != cudaSuccess) {
+                (void)cudaGetLastError();
+                continue;
+            }
+            cudaEventRecord(e0, st);
+            for (int rep = 0; rep < 3; ++rep) launch_iface<R>(ia, (int)all.subs.size(), max_rows, p->max_Lb, st, &c);
+            cudaEventRecord(e1, st);
+            float ms = 0;
+            if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess &&
+                ms < best_ms) {
+                best_ms = ms;
+                best = c;
+            }
+        }
+    }
+    uncount_launch(helm_launch_count() - before);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    HELM_CUDA_TRY(cudaGetLastError());
+    int dev_status = 0;
+    HELM_CUDA_TRY(cudaMemcpyAsync(&dev_status, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    HELM_CUDA_TRY(cudaStreamSynchronize(st));
+    if (dev_status != 0) return take_device_status(p, "autotuning the interface stages");
+    if (best_ms < 1e30f) p->iface_tuned.push_back({p->prec, nrhs, best});
+    return HELM_OK;
+}
+static helm_status tune_shape(helm_problem* p, int nrhs, cudaStream_t st) {
+    if (!p->sopts.autotune || nrhs < 2 || !p->d_K || p->prof_capture || tuned_shape(p, nrhs)) return HELM_OK;
+    return p->prec == HELM_PREC_C64 ? tune_shape_t<float>(p, nrhs, st) : tune_shape_t<double>(p, nrhs, st);
+}
+
+extern "C" helm_status helm_iface_shape(const helm_problem* p, int nrhs, int* nr, int* staged, int* waves,
+                                        int* tuned) {
+    if (!p) return arg_error("helm_iface_shape: NULL handle");
+    const IfaceCfg* c = tuned_shape(p, nrhs);
+    IfaceCfg d;
+    d.nr = nrhs >= 4 ? 4 : nrhs >= 2 ? 2 : 1;
+    if (!c) c = &d;
+    if (nr) *nr = c->nr;
+    if (staged) *staged = c->staged;
+    if (waves) *waves = c->waves;
+    if (tuned) *tuned = tuned_shape(p, nrhs) != nullptr;
+    return HELM_OK;
+}
+
 template <typename R>
 static helm_status run_stage_t(helm_problem* p, const PcWork& w, const PcCtx& cx, const StageDesc& sd,
                                const double2* r, double2* z, int nrhs, cudaStream_t st) {
@@ -994,7 +1093,7 @@ static helm_status run_stage_t(helm_problem* p, const PcWork& w, const PcCtx& cx
         double bytes = 0, flops = 0;
         if (p->prof_on) iface_accounting(p, sd, nrhs, sizeof(T), bytes, flops);
         prof_begin(p, HELM_K_TRACE, st);
-        cudaError_t e = launch_iface<R>(ia, (int)sd.subs.size(), max_rows, p->max_Lb, st);
+        cudaError_t e = launch_iface<R>(ia, (int)sd.subs.size(), max_rows, p->max_Lb, st, tuned_shape(p, nrhs));
         prof_end(p, HELM_K_TRACE, bytes, st, flops);
         if (e != cudaSuccess) return cuda_status(e, "interface stage launch");
         return HELM_OK;
@@ -1088,6 +1187,8 @@ static helm_status run_precond_t(helm_problem* p, const PcWork& w, int sched, co
 static helm_status run_precond(helm_problem* p, int sched, const double2* r, double2* z, int nrhs, cudaStream_t st) {
     helm_status s = ensure_pc_ws(p, nrhs);
     if (s != HELM_OK) return s;
+    s = tune_shape(p, nrhs, st);
+    if (s != HELM_OK) return s;
     const PcWork w{{p->d_trace[0], p->d_trace[1], p->d_trace[2]}, p->d_yws, p->d_pc_norm, p->d_pc_partial,
                    p->d_escr, p->d_r64};
     return p->prec == HELM_PREC_C64 ? run_precond_t<float>(p, w, sched, r, z, nrhs, st)
@@ -1102,6 +1203,8 @@ static helm_status run_precond_graph(helm_problem* p, int sched, const double2* 
                                      cudaStream_t st) {
     if (p->prof_on) return run_precond(p, sched, r, z, nrhs, st);   // per-launch events need plain launches
     helm_status s = ensure_pc_ws(p, nrhs);
+    if (s != HELM_OK) return s;
+    s = tune_shape(p, nrhs, st);
     if (s != HELM_OK) return s;
     for (const auto& g : p->graphs)
         if (g.sched == sched && g.nrhs == nrhs && g.r == r && g.z == z) {
@@ -1698,6 +1801,8 @@ static helm_status run_precond_iface_t(helm_problem* p, int sched, const double2
     if (stg.size() < 2 || p->ntrace == 0) return run_precond(p, sched, r, z, nrhs, st);   // one subdomain
     helm_status s = ensure_pc_ws(p, nrhs);
     if (s != HELM_OK) return s;
+    s = tune_shape(p, nrhs, st);
+    if (s != HELM_OK) return s;
     const long long nt = p->ntrace;
     s = ensure_kw(p->kwi, nrhs, o.inner_restart, nt, true);
     if (s != HELM_OK) return s;
@@ -1837,6 +1942,8 @@ static helm_status gmres_impl(helm_problem* p, const double2* f, double2* u, int
     helm_status s = ensure_kw(p->kw, nrhs, o.restart, N, false);
     if (s != HELM_OK) return s;
     s = ensure_pc_ws(p, nrhs);
+    if (s != HELM_OK) return s;
+    s = tune_shape(p, nrhs, st);
     if (s != HELM_OK) return s;
     const double h2 = p->h * p->h;
     // ||h^2 f||

@@ -190,6 +190,13 @@ template <typename R> struct IfaceArgs {
     int* err;                  // HELM_ERR_TIMEOUT when a bounded wait expired
 };
 
+// launch shape of the interface-stage kernel: right-hand sides per block (1, 2, 4, 8, 16),
+// K rows staged in shared memory when they fit (1) or read from global memory (0), and
+// the CTAs per SM the grid aims at when it spreads RHS blocks over CTAs
+struct IfaceCfg {
+    int nr = 4, staged = 1, waves = 3;
+};
+
 // one interface stage of a sweep run by the persistent sweep kernel (device table)
 struct SweepStage {
     int sub_off, nsub;         // its subdomains in the stage-list array
@@ -244,8 +251,11 @@ cudaError_t launch_tc_stage(const StageArgs<float>& a, const float* XT, int MT, 
                             cudaStream_t st);
 cudaError_t launch_tc_basis(const StageArgs<float>& a, const float* XT, int MT, int split, int nsub, int ncols,
                             cudaStream_t st);
+// one interface stage; cfg = nullptr: the default shape (4, 2 or 1 RHS per block, staged
+// when it fits, 3 CTAs per SM)
 template <typename R>
-cudaError_t launch_iface(const IfaceArgs<R>& a, int nactive, int max_rows, int max_Lb, cudaStream_t st);
+cudaError_t launch_iface(const IfaceArgs<R>& a, int nactive, int max_rows, int max_Lb, cudaStream_t st,
+                         const IfaceCfg* cfg = nullptr);
 // a whole sweep (nstages interface stages, in order) in one cooperative launch of `grid`
 // CTAs (sweep_grid: the co-resident count, 0 when unavailable); bar: two zeroed words
 template <typename R> int sweep_grid(int nrhs, int max_Lb);

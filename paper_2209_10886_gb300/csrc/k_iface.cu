@@ -151,7 +151,7 @@ __device__ void iface_item(const IfaceArgs<R>& a, int item_sub, int row_block, i
     }
     // the rows of this warp and their transmission coefficients (immutable: before the wait)
     constexpr int RPW = RB / (IT / 32);
-    constexpr int CU = (sizeof(R) == 8 && NR >= 4) ? 4 : 8;   // fits the 128-register bound
+    constexpr int CU = (NR >= 8 || (sizeof(R) == 8 && NR >= 4)) ? 4 : 8;   // fits the register bound
     int srow[RPW], krow[RPW];
     long long tofs[RPW];
     T cca[RPW], ccb[RPW];
@@ -399,9 +399,9 @@ cudaError_t launch_nr_s_m(const IfaceArgs<R>& a, int nactive, int max_rows, size
 }
 
 // RHS blocks: each CTA stages its K rows once and loops over the blocks z, z + gridDim.z,
-// ...; gridDim.z spreads them only as far as needed to fill the GPU about three times
+// ...; gridDim.z spreads them only as far as needed for `waves` CTAs per SM
 template <typename R, int NR, bool STAGED>
-cudaError_t launch_nr_s(const IfaceArgs<R>& a, int nactive, int max_rows, size_t smem, cudaStream_t st) {
+cudaError_t launch_nr_s(const IfaceArgs<R>& a, int nactive, int max_rows, size_t smem, int waves, cudaStream_t st) {
     static int sms = 0;
     if (sms == 0) {
         int dev = 0;
@@ -411,20 +411,23 @@ cudaError_t launch_nr_s(const IfaceArgs<R>& a, int nactive, int max_rows, size_t
     }
     const long long items = (long long)nactive * ((max_rows + RB - 1) / RB);
     const int nrb = (a.nrhs + NR - 1) / NR;
-    const int zb = (int)std::min<long long>(nrb, std::max<long long>(1, (3LL * sms + items - 1) / items));
+    const long long want = (long long)std::max(1, waves) * sms;
+    const int zb = (int)std::min<long long>(nrb, std::max<long long>(1, (want + items - 1) / items));
     if (zb == nrb) return launch_nr_s_m<R, NR, STAGED, false>(a, nactive, max_rows, smem, zb, st);
     return launch_nr_s_m<R, NR, STAGED, true>(a, nactive, max_rows, smem, zb, st);
 }
 
-// staged when the item's K rows and gather fit two CTAs per SM (K 16-byte aligned)
+// staged when allowed, when the item's K rows and gather fit two CTAs per SM and K is
+// 16-byte aligned
 template <typename R, int NR>
-cudaError_t launch_nr(const IfaceArgs<R>& a, int nactive, int max_rows, int max_Lb, cudaStream_t st) {
+cudaError_t launch_nr(const IfaceArgs<R>& a, int nactive, int max_rows, int max_Lb, int staged_ok, int waves,
+                      cudaStream_t st) {
     using T = Cx<R>;
     const size_t gather = 2 * (size_t)NR * max_Lb * sizeof(T);
     const size_t staged = (size_t)RB * staged_ld<T>(max_Lb) * sizeof(T) + gather;
-    if (staged <= 113 * 1024 && (reinterpret_cast<uintptr_t>(a.K) & 15) == 0)
-        return launch_nr_s<R, NR, true>(a, nactive, max_rows, staged, st);
-    return launch_nr_s<R, NR, false>(a, nactive, max_rows, gather, st);
+    if (staged_ok && staged <= 113 * 1024 && (reinterpret_cast<uintptr_t>(a.K) & 15) == 0)
+        return launch_nr_s<R, NR, true>(a, nactive, max_rows, staged, waves, st);
+    return launch_nr_s<R, NR, false>(a, nactive, max_rows, gather, waves, st);
 }
 
 template <typename R, int NR>
@@ -469,17 +472,24 @@ cudaError_t launch_sweep(const IfaceArgs<R>& a, const SweepStage* stages, int ns
 }
 
 template <typename R>
-cudaError_t launch_iface(const IfaceArgs<R>& a, int nactive, int max_rows, int max_Lb, cudaStream_t st) {
+cudaError_t launch_iface(const IfaceArgs<R>& a, int nactive, int max_rows, int max_Lb, cudaStream_t st,
+                         const IfaceCfg* cfg) {
     if (nactive == 0 || a.nrhs == 0) return cudaSuccess;
-    // blocks of 4 RHS: wider blocks (8, 16) re-read K less often but leave fewer CTAs
-    // and measured slower (16 RHS: 2x the time at 64 RHS on the 1023^2 workload)
-    if (a.nrhs >= 4) return launch_nr<R, 4>(a, nactive, max_rows, max_Lb, st);
-    if (a.nrhs >= 2) return launch_nr<R, 2>(a, nactive, max_rows, max_Lb, st);
-    return launch_nr<R, 1>(a, nactive, max_rows, max_Lb, st);
+    // default: blocks of 4 RHS (at 64 RHS on the 1023^2 workload, 16 measured 2x slower
+    // when every block had its own CTA); the autotuner may pick another shape
+    const int nr = cfg ? cfg->nr : (a.nrhs >= 4 ? 4 : a.nrhs >= 2 ? 2 : 1);
+    const int staged_ok = cfg ? cfg->staged : 1;
+    const int waves = cfg ? cfg->waves : 3;
+    if constexpr (sizeof(R) == 4)   // complex128 blocks of 16 would spill
+        if (nr >= 16) return launch_nr<R, 16>(a, nactive, max_rows, max_Lb, staged_ok, waves, st);
+    if (nr >= 8) return launch_nr<R, 8>(a, nactive, max_rows, max_Lb, staged_ok, waves, st);
+    if (nr >= 4) return launch_nr<R, 4>(a, nactive, max_rows, max_Lb, staged_ok, waves, st);
+    if (nr >= 2) return launch_nr<R, 2>(a, nactive, max_rows, max_Lb, staged_ok, waves, st);
+    return launch_nr<R, 1>(a, nactive, max_rows, max_Lb, staged_ok, waves, st);
 }
 
-template cudaError_t launch_iface<float>(const IfaceArgs<float>&, int, int, int, cudaStream_t);
-template cudaError_t launch_iface<double>(const IfaceArgs<double>&, int, int, int, cudaStream_t);
+template cudaError_t launch_iface<float>(const IfaceArgs<float>&, int, int, int, cudaStream_t, const IfaceCfg*);
+template cudaError_t launch_iface<double>(const IfaceArgs<double>&, int, int, int, cudaStream_t, const IfaceCfg*);
 template int sweep_grid<float>(int, int);
 template int sweep_grid<double>(int, int);
 template cudaError_t launch_sweep<float>(const IfaceArgs<float>&, const SweepStage*, int, int, int, unsigned*, int*,

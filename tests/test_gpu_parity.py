@@ -187,6 +187,26 @@ def test_fused_cgs2_matches_split(H, where):
     p.close()
 
 
+@pytest.mark.parametrize("prec", ["c64", "c128"])
+def test_autotuned_interface_shape(H, prec):
+    """The first application with several RHS times the interface-stage launch shapes
+    and keeps the fastest; the result equals the fixed-rule shape's up to the rounding
+    of the GEMV sums (their order depends on the RHS per block)."""
+    w = CASES["uneven_4x3"]()
+    mk = lambda tune: H.Problem(w.n, w.n, w.h, w.omega, cuda(w.m2, torch.float64), w.N1, w.N2, w.xcuts, w.ycuts,
+                                autotune=tune).factor(prec)
+    pa, pb = mk(True), mk(False)
+    r = cuda(W.random_complex((20, w.N), 51))
+    za = pa.precond_apply(r).cpu().numpy()
+    zb = pb.precond_apply(r).cpu().numpy()
+    sa, sb = H.iface_shape(pa, 20), H.iface_shape(pb, 20)
+    print(prec, "tuned", sa, "fixed", sb, "rel", rel(za, zb))
+    assert sa["tuned"] and not sb["tuned"] and sb["rhs_per_block"] == 4
+    assert not H.iface_shape(pa, 1)["tuned"]
+    assert rel(za, zb) <= (1e-5 if prec == "c64" else 1e-12)
+    pa.close(); pb.close()
+
+
 def test_impedance_transmission_matches_oracle(H):
     w = CASES["ragged_3x2"]()
     p, dec = make(H, w, "c128", transmission="impedance")
