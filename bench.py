@@ -172,12 +172,16 @@ def schedules(args):
     15, 20 rows.  Per schedule: Krylov steps to 1e-6 (ni: the interface FGMRES steps
     when the interface problem is solved iteratively, as in the paper, else the
     volume FGMRES steps), sweep steps per application of the sweep (ns: SP
-    2(N1+N2-2), BSP 2 N1, as in Table 1) and the solve time (t), with t / (ni ns).
+    2(N1+N2-2), BSP 2 N1, as in Table 1; BSP with non-overlapping bands 2(N1-1))
+    and the solve time (t), with t / (ni ns).  Per schedule also the residual
+    history of the interface FGMRES (unrestarted, to 1e-6) in one preconditioner
+    application (the paper's 'drop at the number of partial sweeps'): its first
+    values and the step of the largest one-step decrease.
     """
     import torch
 
     import workloads as W
-    from paper_2209_10886_gb300 import Problem, helm
+    from paper_2209_10886_gb300 import Problem, helm, schedule_info
     n = 639
     rows = []
     for N2 in (5, 10, 15, 20):
@@ -190,7 +194,7 @@ def schedules(args):
         p = Problem(w.n, w.n, w.h, w.omega, m2, w.N1, w.N2, w.xcuts, w.ycuts,
                     tensor_cores=TC_MODES[args.tensor_cores], tc_scale=args.tc_scale).factor(args.prec)
         row = {"N1xN2": f"5x{N2}"}
-        for sched in ("SP", "BSP"):
+        for sched in ("SP", "BSP", "BSP_NONOVERLAP"):
             kw = dict(restart=args.restart, maxit=2000, tol=args.tol, sched=sched, use_graph=args.graph,
                       raise_on_noconv=False, **inner_kw(args))
             p.solve(f, **kw)                                                    # warm-up
@@ -204,9 +208,24 @@ def schedules(args):
             t = e0.elapsed_time(e1) / 1e3
             outer = info[0][0]
             ni = helm.inner_steps(p) - s0 if args.inner_maxit > 0 else outer
-            ns = 2 * (5 + N2 - 2) if sched == "SP" else 2 * 5
+            ns = schedule_info(5, N2, sched)[0]          # SP 2(N1+N2-2), BSP 2 N1, non-overlapping 2(N1-1)
             row[sched] = {"ni": ni, "outer": outer, "ns": ns, "t_s": t, "relres": info[0][1],
                           "converged": info[0][1] <= args.tol, "t_per_ni_ns_ms": 1e3 * t / (max(ni, 1) * ns)}
+            # the paper's observation (Section 6, its Fig. 3): in GMRES on the interface
+            # problem the residual drops suddenly at the iteration equal to the number of
+            # partial sweeps (bands); here the interface FGMRES of the first preconditioner
+            # application, unrestarted, to 1e-6 (one outer step)
+            p.solve(f, restart=args.restart, maxit=1, tol=args.tol, sched=sched, raise_on_noconv=False,
+                    inner_maxit=300, inner_restart=300, inner_tol=1e-6, inner_history=True)
+            hist = p.last_inner_history[0]
+            ratios = [hist[k] / hist[k - 1] for k in range(1, len(hist)) if hist[k - 1] > 0]
+            k_drop = 1 + min(range(len(ratios)), key=lambda k: ratios[k]) if ratios else None
+            Ng = 5 + N2 - 1
+            nb = -(-(Ng - 1) // 5) if sched == "BSP" else (-(-Ng // 5) if sched == "BSP_NONOVERLAP" else 1)
+            row[sched]["interface_history"] = {
+                "relres_first_16": [float(f"{v:.3e}") for v in hist[:16]], "steps_to_1e-6": len(hist),
+                "largest_drop_at_step": (k_drop + 1) if k_drop is not None else None,
+                "largest_drop_ratio": min(ratios) if ratios else None, "bands": nb}
         p.close()
         rows.append(row)
     print(json.dumps({"mode": "schedules", "workload": f"{n}^2 layered+random 10 ppw, 5 x N2, 1 source",

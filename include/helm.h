@@ -82,8 +82,11 @@ typedef enum {
  *                 the top-right corner, all bands concurrently; 2 N1 sweep
  *                 steps (plus one residual stage) per application.
  * HELM_SCHED_SP:  symmetric Gauss-Seidel sweeping (Section 4,
- *                 Eq. sgs_preconditioner_forward_backward): 2 (N1+N2-2) steps. */
-typedef enum { HELM_SCHED_BSP = 0, HELM_SCHED_SP = 1 } helm_sched;
+ *                 Eq. sgs_preconditioner_forward_backward): 2 (N1+N2-2) steps.
+ * HELM_SCHED_BSP_NONOVERLAP: block Jacobi sweeping with bands of N1 diagonals that
+ *                 share none (the paper's band bounds read as half-open);
+ *                 2 (N1 - 1) sweep steps; for comparison with HELM_SCHED_BSP */
+typedef enum { HELM_SCHED_BSP = 0, HELM_SCHED_SP = 1, HELM_SCHED_BSP_NONOVERLAP = 2, HELM_NSCHED = 3 } helm_sched;
 
 /* Robin parameter T_e of the interface condition (d_n - T_e) u = g.
  * HELM_TC_OPTIMIZED: T_e = (i - 1) s sqrt(kappa_e pi / (2 h)) with s = tc_scale,
@@ -158,6 +161,11 @@ typedef struct {
                            operators); 0 (default): one launch per stage, replayed from a
                            CUDA graph inside the interface iterations (measured faster on
                            GB300: 48 vs 39 ms of interface stages per 1023^2 solve) */
+    double* inner_hist; /* optional host buffer of inner_maxit*nrhs doubles: the residual
+                           estimates ||b - (I - S) g_j|| / ||b|| of the interface iteration
+                           in the first preconditioner application of this call, RHS k
+                           after step j at inner_hist[k*inner_maxit+j] (that application
+                           runs the host-driven loop) */
     int inner_fp64;     /* interface iterations (inner_maxit > 0) with complex64 factors:
                            0 (default) keeps the interface Krylov vectors in complex64
                            (FP32 vector arithmetic; reductions, Gram-Schmidt coefficients

@@ -58,13 +58,16 @@ struct SubHost {
 };
 
 // Block Jacobi bands (Section 5): forward 2+(g-1)N1 <= d <= 2+g N1, backward
-// (1+Ng)-g N1 <= d <= (1+Ng)-(g-1)N1, clipped to [2, Ng+1].
-std::vector<std::pair<int, int>> bands(int N1, int Ng, bool forward) {
+// (1+Ng)-g N1 <= d <= (1+Ng)-(g-1)N1, clipped to [2, Ng+1] (consecutive bands share a
+// diagonal).  overlap = false: bands of N1 diagonals that share none (the paper's
+// bounds read as half-open), for comparison.
+std::vector<std::pair<int, int>> bands(int N1, int Ng, bool forward, bool overlap = true) {
     std::vector<std::pair<int, int>> out;
+    const int width = overlap ? N1 : N1 - 1;     // band g starts N1 diagonals after band g-1
     for (int g = 1;; ++g) {
         int lo, hi;
-        if (forward) { lo = 2 + (g - 1) * N1; hi = lo + N1; }
-        else { hi = (1 + Ng) - (g - 1) * N1; lo = hi - N1; }
+        if (forward) { lo = 2 + (g - 1) * N1; hi = lo + width; }
+        else { hi = (1 + Ng) - (g - 1) * N1; lo = hi - width; }
         lo = std::max(lo, 2);
         hi = std::min(hi, Ng + 1);
         if (lo > Ng + 1 || hi < 2) break;
@@ -73,6 +76,7 @@ std::vector<std::pair<int, int>> bands(int N1, int Ng, bool forward) {
     }
     return out;
 }
+static bool is_bsp(int sched) { return sched == HELM_SCHED_BSP || sched == HELM_SCHED_BSP_NONOVERLAP; }
 
 // Stage lists of one application of the volume preconditioner.  `ondiag[d]`
 // lists the subdomains of diagonal d; `all` every subdomain.
@@ -108,7 +112,8 @@ std::vector<StageDesc> build_schedule(int sched, int N1, int N2, const std::vect
     }
     // BSP: x' = B_L^{-1} b (bands run concurrently; a band's first diagonal
     // reads the unpropagated b, later ones the propagated x)
-    auto fb = bands(N1, Ng, true);
+    const bool overlap = sched != HELM_SCHED_BSP_NONOVERLAP;
+    auto fb = bands(N1, Ng, true, overlap);
     int fsteps = 0;
     for (auto& b : fb) fsteps = std::max(fsteps, b.second - b.first);
     for (int s = 1; s <= fsteps; ++s) {
@@ -122,7 +127,7 @@ std::vector<StageDesc> build_schedule(int sched, int N1, int N2, const std::vect
     // rho = b - (I - S) x': every subdomain, into B (in place) and Y
     st.push_back(mk_stage(all, 0, BUF_X, BUF_NONE, ALL, BUF_B, BUF_Y, BUF_B, BUF_X, 0));
     // y = B_U^{-1} rho
-    auto ub = bands(N1, Ng, false);
+    auto ub = bands(N1, Ng, false, overlap);
     int bsteps = 0;
     for (auto& b : ub) bsteps = std::max(bsteps, b.second - b.first);
     for (int s = 1; s <= bsteps; ++s) {
@@ -141,9 +146,10 @@ std::vector<StageDesc> build_schedule(int sched, int N1, int N2, const std::vect
 int sweep_steps(int sched, int N1, int N2) {
     const int Ng = N1 + N2 - 1;
     if (sched == HELM_SCHED_SP) return 2 * (Ng - 1);
+    const bool overlap = sched != HELM_SCHED_BSP_NONOVERLAP;
     int f = 0, b = 0;
-    for (auto& x : bands(N1, Ng, true)) f = std::max(f, x.second - x.first);
-    for (auto& x : bands(N1, Ng, false)) b = std::max(b, x.second - x.first);
+    for (auto& x : bands(N1, Ng, true, overlap)) f = std::max(f, x.second - x.first);
+    for (auto& x : bands(N1, Ng, false, overlap)) b = std::max(b, x.second - x.first);
     return f + b;
 }
 
@@ -192,7 +198,7 @@ struct helm_problem {
     int num_sms = 0;
     long long ntrace = 0;
     int nslots = 0;
-    std::vector<StageDesc> sched[2];
+    std::vector<StageDesc> sched[HELM_NSCHED];
 
     double* d_m2 = nullptr;
     double2* d_adiag = nullptr;
@@ -216,7 +222,7 @@ struct helm_problem {
     int tc_all_off[2] = {0, 0}, tc_all_n[2] = {0, 0};   // all subdomains by tile count, in d_stage_subs
     long long etot = 0;              // boundary slots 2 (mx + my) summed over the subdomains
     SweepStage* d_sweep = nullptr;   // interface stages of each schedule for the sweep kernel
-    int sweep_off[2] = {0, 0}, sweep_n[2] = {0, 0};
+    int sweep_off[HELM_NSCHED] = {}, sweep_n[HELM_NSCHED] = {};
     unsigned* d_sweep_bar = nullptr; // its grid-barrier words
 
     // preconditioner workspace
@@ -232,6 +238,7 @@ struct helm_problem {
     KrylovWS kw, kwi;
     long long inner_steps = 0;       // interface Krylov steps taken inside the preconditioner (all calls)
     int persistent = 0;              // gmres_solve option: sweeps in the persistent sweep kernel
+    bool inner_hist_taken = false;   // the interface history of this gmres_solve call is recorded
     struct TunedShape { int prec, nrhs; IfaceCfg cfg; };
     std::vector<TunedShape> iface_tuned;   // autotuned interface-stage launch shapes
 
@@ -391,6 +398,7 @@ extern "C" void helm_default_opts(helm_opts* o) {
     o->inner_restart = 100;
     o->inner_tol = 1e-4;
     o->persistent = 0;
+    o->inner_hist = nullptr;
     o->inner_fp64 = 0;
 }
 
@@ -408,7 +416,7 @@ extern "C" void helm_default_setup_opts(helm_setup_opts* o) {
 extern "C" const char* helm_last_error(void) { return g_err.c_str(); }
 
 extern "C" helm_status helm_schedule_info(int N1, int N2, int sched, int* steps, int* stages) {
-    if (N1 < 1 || N2 < 1 || (sched != HELM_SCHED_BSP && sched != HELM_SCHED_SP))
+    if (N1 < 1 || N2 < 1 || ((sched < 0 || sched >= HELM_NSCHED)))
         return arg_error("helm_schedule_info: N1, N2 >= 1 and a valid schedule are required");
     const int Ng = N1 + N2 - 1;
     std::vector<std::vector<int>> ondiag(Ng + 2);
@@ -567,7 +575,7 @@ extern "C" helm_status helm_setup(int n_x, int n_y, double h, double omega, cons
             n[c] = (int)all_stage_subs.size() - off[c];
         }
     };
-    for (int sc = 0; sc < 2; ++sc) {
+    for (int sc = 0; sc < HELM_NSCHED; ++sc) {
         p->sched[sc] = build_schedule(sc, N1, N2, p->ondiag, p->all, p->nslots > 0);
         for (auto& st : p->sched[sc]) {
             st.sub_off = (int)all_stage_subs.size();
@@ -583,7 +591,7 @@ extern "C" helm_status helm_setup(int n_x, int n_y, double h, double omega, cons
     // the interface stages of each schedule (between lifting and reconstruction) for the
     // persistent sweep kernel, when they are all boundary-operator stages
     std::vector<SweepStage> sweep_tab;
-    for (int sc = 0; sc < 2; ++sc) {
+    for (int sc = 0; sc < HELM_NSCHED; ++sc) {
         const auto& stg = p->sched[sc];
         p->sweep_off[sc] = (int)sweep_tab.size();
         p->sweep_n[sc] = 0;
@@ -1291,7 +1299,7 @@ extern "C" helm_status precond_apply(helm_problem* p, int sched, const helm_c128
                                      void* stream) {
     if (!p) return arg_error("precond_apply: NULL handle");
     if (!p->factored) { set_error("precond_apply: call precond_factor first"); return HELM_ERR_STATE; }
-    if (sched != HELM_SCHED_BSP && sched != HELM_SCHED_SP) return arg_error("precond_apply: unknown schedule");
+    if ((sched < 0 || sched >= HELM_NSCHED)) return arg_error("precond_apply: unknown schedule");
     if (nrhs < 0) return arg_error("precond_apply: nrhs < 0");
     if (nrhs == 0) return HELM_OK;
     if (!r || !z) return arg_error("precond_apply: NULL array");
@@ -1312,7 +1320,7 @@ extern "C" helm_status precond_apply_noalloc(helm_problem* p, int sched, const h
                                              void* stream) {
     if (!p) return arg_error("precond_apply_noalloc: NULL handle");
     if (!p->factored) { set_error("precond_apply_noalloc: call precond_factor first"); return HELM_ERR_STATE; }
-    if (sched != HELM_SCHED_BSP && sched != HELM_SCHED_SP) return arg_error("precond_apply_noalloc: unknown schedule");
+    if ((sched < 0 || sched >= HELM_NSCHED)) return arg_error("precond_apply_noalloc: unknown schedule");
     if (nrhs < 0) return arg_error("precond_apply_noalloc: nrhs < 0");
     if (nrhs == 0) return HELM_OK;
     if (!r || !z) return arg_error("precond_apply_noalloc: NULL array");
@@ -1843,7 +1851,7 @@ static helm_status run_precond_iface_t(helm_problem* p, int sched, const double2
         helm_status q = HELM_OK;
         if (run_sweep_persistent<R>(p, w, sched, nrhs, st, q)) {
             if (q != HELM_OK) return q;
-            launch_trace_to<T, VT>(tX, sched == HELM_SCHED_BSP ? tY : (T*)nullptr, 1, zv, tot, st);
+            launch_trace_to<T, VT>(tX, is_bsp(sched) ? tY : (T*)nullptr, 1, zv, tot, st);
             return HELM_OK;
         }
         q = run_captured(p, 2 * sched, nrhs, st, [&](cudaStream_t cs) {
@@ -1854,7 +1862,7 @@ static helm_status run_precond_iface_t(helm_problem* p, int sched, const double2
             return HELM_OK;
         });
         if (q != HELM_OK) return q;
-        launch_trace_to<T, VT>(tX, sched == HELM_SCHED_BSP ? tY : (T*)nullptr, 1, zv, tot, st);
+        launch_trace_to<T, VT>(tX, is_bsp(sched) ? tY : (T*)nullptr, 1, zv, tot, st);
         return HELM_OK;
     };
     // one Arnoldi step with the slot read on the device (*dj): the same kernels as
@@ -1874,7 +1882,7 @@ static helm_status run_precond_iface_t(helm_problem* p, int sched, const double2
                 if (q != HELM_OK) return q;
             }
             // z_j = X (+ Y) into Z slot j and into X, the input of S
-            launch_trace_to<T, VT>(tX, sched == HELM_SCHED_BSP ? tY : (T*)nullptr, 1, Z, tot, cs, dj, 0, vsk,
+            launch_trace_to<T, VT>(tX, is_bsp(sched) ? tY : (T*)nullptr, 1, Z, tot, cs, dj, 0, vsk,
                                    reinterpret_cast<VT*>(tX));
             return run_stage_t<R>(p, w, cx, sS, r, z, nrhs, cs);
         };
@@ -1890,7 +1898,7 @@ static helm_status run_precond_iface_t(helm_problem* p, int sched, const double2
                 helm_status q = run_stage_t<R>(p, w, cx, stg[i], r, z, nrhs, cs);
                 if (q != HELM_OK) return q;
             }
-            launch_trace_to<T, VT>(tX, sched == HELM_SCHED_BSP ? tY : (T*)nullptr, 1, Z, tot, cs, dj, 0, vsk);
+            launch_trace_to<T, VT>(tX, is_bsp(sched) ? tY : (T*)nullptr, 1, Z, tot, cs, dj, 0, vsk);
             launch_trace_from<VT, T>(Z, tX, (T*)nullptr, tot, cs, dj, 0, vsk);
             helm_status q = run_stage_t<R>(p, w, cx, sS, r, z, nrhs, cs);
             if (q != HELM_OK) return q;
@@ -1915,8 +1923,11 @@ static helm_status run_precond_iface_t(helm_problem* p, int sched, const double2
     HELM_CUDA_TRY(cudaStreamSynchronize(st));
     std::vector<int> it;
     std::vector<double> rr;
+    // the first application of a call may record the interface residual history
+    double* ihist = (o.inner_hist && !p->inner_hist_taken) ? o.inner_hist : nullptr;
+    if (ihist) p->inner_hist_taken = true;
     s = fgmres_core<VT>(p, p->kwi, nt, nrhs, o.inner_restart, o.inner_maxit, o.inner_tol, bnorm, kx, false,
-                    o.ortho == HELM_ORTHO_CGS2_SPLIT ? HELM_ORTHO_CGS2_SPLIT : HELM_ORTHO_CGS2, nullptr, ops, it, rr,
+                    o.ortho == HELM_ORTHO_CGS2_SPLIT ? HELM_ORTHO_CGS2_SPLIT : HELM_ORTHO_CGS2, ihist, ops, it, rr,
                     "gmres_solve (interface iterations)", st);
     if (s != HELM_OK) return s;
     p->inner_steps += it.empty() ? 0 : *std::max_element(it.begin(), it.end());
@@ -1971,6 +1982,7 @@ static helm_status gmres_impl(helm_problem* p, const double2* f, double2* u, int
     std::vector<int> iters;
     std::vector<double> relres;
     p->persistent = o.persistent != 0;
+    p->inner_hist_taken = false;
     s = fgmres_core(p, p->kw, N, nrhs, o.restart, o.maxit, o.tol, bnorm, u, o.x0_given != 0, o.ortho,
                     o.hist, ops, iters, relres, "gmres_solve", st);
     p->persistent = 0;
@@ -2000,7 +2012,7 @@ extern "C" helm_status gmres_solve(helm_problem* p, const helm_c128* f, helm_c12
     if (o.restart < 1 || o.restart > 500) return arg_error("gmres_solve: restart must be in 1..500");
     if (o.maxit < 1) return arg_error("gmres_solve: maxit must be >= 1");
     if (!(o.tol > 0)) return arg_error("gmres_solve: tol must be > 0");
-    if (o.sched != HELM_SCHED_BSP && o.sched != HELM_SCHED_SP) return arg_error("gmres_solve: unknown schedule");
+    if ((o.sched < 0 || o.sched >= HELM_NSCHED)) return arg_error("gmres_solve: unknown schedule");
     if (o.ortho != HELM_ORTHO_MGS && o.ortho != HELM_ORTHO_CGS2 && o.ortho != HELM_ORTHO_CGS2_SPLIT)
         return arg_error("gmres_solve: unknown ortho");
     if (o.inner_maxit < 0) return arg_error("gmres_solve: inner_maxit must be >= 0");

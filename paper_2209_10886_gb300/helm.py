@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libhelm.so")
 HEADER_PATH = os.path.join(os.path.dirname(_HERE), "include", "helm.h")
 
 PREC = {"c128": 0, "c64": 1}
-SCHED = {"BSP": 0, "SP": 1}
+SCHED = {"BSP": 0, "SP": 1, "BSP_NONOVERLAP": 2}
 TRANSMISSION = {"optimized": 0, "impedance": 1}
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_STATE", 5: "ERR_NO_CONVERGENCE",
           6: "ERR_TIMEOUT", 7: "ERR_UNSUPPORTED"}
@@ -35,7 +35,8 @@ class HelmOpts(ctypes.Structure):
                 ("x0_given", ctypes.c_int), ("sched", ctypes.c_int), ("use_graph", ctypes.c_int),
                 ("hist", ctypes.POINTER(ctypes.c_double)), ("ortho", ctypes.c_int),
                 ("inner_maxit", ctypes.c_int), ("inner_restart", ctypes.c_int), ("inner_tol", ctypes.c_double),
-                ("persistent", ctypes.c_int), ("inner_fp64", ctypes.c_int)]
+                ("persistent", ctypes.c_int), ("inner_hist", ctypes.POINTER(ctypes.c_double)),
+                ("inner_fp64", ctypes.c_int)]
 
 
 class HelmSetupOpts(ctypes.Structure):
@@ -187,10 +188,12 @@ class Problem:
 
     def solve(self, f, u=None, restart=50, maxit=1000, tol=1e-6, sched="BSP", x0=None, history=False,
               stream=None, raise_on_noconv=True, use_graph=False, inner_maxit=0, inner_restart=100, inner_tol=1e-4,
-              persistent=False, ortho="mgs", inner_fp64=False):
+              persistent=False, ortho="mgs", inner_fp64=False, inner_history=False):
         """Solve A u = h^2 f (FP64 FGMRES); returns (u, [(iters, relres)], history or None).
         ortho: "mgs" (volume default), "cgs2" or "cgs2_split" (see helm.h); inner_fp64: FP64
-        interface Krylov vectors with complex64 factors (default: complex64 vectors)."""
+        interface Krylov vectors with complex64 factors (default: complex64 vectors);
+        inner_history: keep the interface residual history of the first preconditioner
+        application in self.last_inner_history (one list per RHS)."""
         f = _as_fields(f, self.N, "f")
         nrhs = f.numel() // self.N
         u = torch.empty_like(f) if u is None else u
@@ -203,11 +206,19 @@ class Problem:
                          ortho=ORTHO[ortho], inner_fp64=int(bool(inner_fp64)))
         if hist is not None:
             o.hist = ctypes.cast(hist, ctypes.POINTER(ctypes.c_double))
+        ihist = (ctypes.c_double * (max(1, int(inner_maxit)) * nrhs))() if inner_history else None
+        if ihist is not None:
+            o.inner_hist = ctypes.cast(ihist, ctypes.POINTER(ctypes.c_double))
         info = (HelmInfo * nrhs)()
         st = lib().gmres_solve(self._h, _ptr(f), _ptr(u), nrhs, ctypes.byref(o), info, _stream(stream))
         if st != 0 and (raise_on_noconv or st != 5):
             _check(st)
         out = [(info[k].iters, info[k].relres) for k in range(nrhs)]
+        if ihist is not None:
+            m = max(1, int(inner_maxit))
+            rows = [list(ihist[k * m:(k + 1) * m]) for k in range(nrhs)]
+            # steps not taken keep the buffer's zeros
+            self.last_inner_history = [r[:max([i + 1 for i, v in enumerate(r) if v != 0.0] or [0])] for r in rows]
         hh = None
         if hist is not None:
             hh = [[hist[k * maxit + j] for j in range(out[k][0])] for k in range(nrhs)]

@@ -36,17 +36,21 @@ def test_scheduler_reproduces_table1(L, golden_dir):
 
 @pytest.mark.parametrize("N1,N2", [(1, 1), (2, 2), (8, 8), (12, 12), (16, 16), (5, 10), (3, 7), (7, 3), (1, 5)])
 def test_scheduler_matches_oracle_schedule(L, N1, N2):
-    """Step counts of the C++ scheduler equal the oracle's (Sections 4-5), and the
-    stage count is steps + lifting + reconstruction (+ residual for BSP)."""
+    """Step counts of the C++ scheduler equal the oracle's (Sections 4-5; BSP also with
+    non-overlapping bands), and the stage count is steps + lifting + reconstruction
+    (+ residual for BSP)."""
     from oracle import schedule_steps
     from paper_2209_10886_gb300 import schedule_info
-    for kind in ("SP", "BSP"):
+    for kind in ("SP", "BSP", "BSP_NONOVERLAP"):
         steps, stages = schedule_info(N1, N2, kind)
         if N1 * N2 == 1:
             assert (steps, stages) == (0, 1)
             continue
-        assert steps == schedule_steps(N1, N2, kind)
-        assert stages == steps + 2 + (kind == "BSP")
+        if kind == "BSP_NONOVERLAP":
+            assert steps == schedule_steps(N1, N2, "BSP", overlap=False) == 2 * (N1 - 1)
+        else:
+            assert steps == schedule_steps(N1, N2, kind)
+        assert stages == steps + 2 + (kind != "SP")
 
 
 def test_invalid_arguments_are_rejected_without_gpu(L):

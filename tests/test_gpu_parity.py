@@ -187,6 +187,24 @@ def test_fused_cgs2_matches_split(H, where):
     p.close()
 
 
+@pytest.mark.parametrize("case", ["ragged_3x2", "uneven_4x3"])
+def test_nonoverlapping_bands_match_oracle(H, case):
+    """BSP with bands of N1 diagonals that share none (the comparison variant of the
+    band rule) against the oracle's BSP with overlap=False, complex128."""
+    w = CASES[case]()
+    p, dec = make(H, w, "c128")
+    r = W.random_complex((2, w.N), 52)
+    z = p.precond_apply(cuda(r), sched="BSP_NONOVERLAP").cpu().numpy()
+    sw = Sweeper(dec)
+    for k in range(2):
+        ref = sw.precondition(r[k], "BSP", overlap=False)
+        other = sw.precondition(r[k], "BSP", overlap=True)
+        e = rel(z[k], ref)
+        print(f"{case} BSP non-overlapping rhs{k}: rel {e:.2e} (vs overlapping bands {rel(z[k], other):.2e})")
+        assert e <= 1e-10 and rel(z[k], other) > 1e-6
+    p.close()
+
+
 @pytest.mark.parametrize("prec", ["c64", "c128"])
 def test_autotuned_interface_shape(H, prec):
     """The first application with several RHS times the interface-stage launch shapes
