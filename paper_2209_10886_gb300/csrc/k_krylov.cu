@@ -416,9 +416,13 @@ template <> __device__ __forceinline__ float2 cvt<float2, double2>(double2 a) { 
 // out = sign * (a + b) for n * nrhs values, b optional; with dj, out is the Krylov slot
 // *dj + joff of an array of slots vsk apart (the slot index read on the device)
 // (and into out2, optional, unshifted: may be a, each element is read before it is written)
+// (launched with a programmatic dependency: waits for the previous kernel before any
+// access, lets the next one launch at once)
 template <typename T, typename VT>
 __global__ void trace_to_kernel(const T* a, const T* __restrict__ b, int sign, VT* __restrict__ out,
                                 long long total, const int* dj, int joff, long long vsk, VT* out2) {
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
     if (dj) out += (long long)(*dj + joff) * vsk;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x) {
@@ -451,11 +455,28 @@ __global__ void sub_kernel(const VT* __restrict__ b, const VT* __restrict__ w, V
 
 static int small_grid(long long total) { return (int)std::min<long long>(1216, (total + 255) / 256 + 1); }
 
+// launch of kernel `k` with a programmatic dependency on the previous kernel of the stream
+template <typename... P, typename... A>
+static cudaError_t launch_pdl(void (*k)(P...), dim3 grid, dim3 block, cudaStream_t st, A... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 template <typename T, typename VT>
 void launch_trace_to(const T* a, const T* b, int sign, VT* out, long long total, cudaStream_t st, const int* dj,
                      int joff, long long vsk, VT* out2) {
     count_launch();
-    trace_to_kernel<T, VT><<<small_grid(total), 256, 0, st>>>(a, b, sign, out, total, dj, joff, vsk, out2);
+    launch_pdl(trace_to_kernel<T, VT>, dim3(small_grid(total)), dim3(256), st, a, b, sign, out, total, dj, joff,
+               vsk, out2);
 }
 template <typename VT, typename T>
 void launch_trace_from(const VT* in, T* out, T* out2, long long total, cudaStream_t st, const int* dj, int joff,
@@ -486,6 +507,8 @@ template void launch_sub<double2>(const double2*, const double2*, double2*, long
 // is active, j + 1 < ctl[1] (the restart length) and no device wait expired.
 __global__ void arnoldi_ctl_kernel(int* ctl, const double* est, const double* thr, int* active, int* iters,
                                    int* jcount, int nrhs, const int* err, cudaGraphConditionalHandle h) {
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
     __shared__ int any;
     if (threadIdx.x == 0) any = 0;
     __syncthreads();
@@ -511,5 +534,5 @@ void launch_arnoldi_ctl(int* ctl, const double* est, const double* thr, int* act
                         int maxit, int nrhs, const int* err, cudaGraphConditionalHandle h, cudaStream_t st) {
     count_launch();
     (void)maxit;   // read on the device from ctl[2]: one graph serves every maxit
-    arnoldi_ctl_kernel<<<1, 256, 0, st>>>(ctl, est, thr, active, iters, jcount, nrhs, err, h);
+    launch_pdl(arnoldi_ctl_kernel, dim3(1), dim3(256), st, ctl, est, thr, active, iters, jcount, nrhs, err, h);
 }

@@ -397,6 +397,8 @@ template <typename VT> __device__ __forceinline__ VT warp_sumc(VT v) {
 
 template <typename VT>
 __global__ void __launch_bounds__(CT, 1) cgs2_step_kernel(Cgs2Args<VT> a) {
+    // the next kernel (the loop control) may launch now; it waits for this one to complete
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
     const int J = a.dj ? *a.dj : a.j;             // the new column
     using Re = decltype(VT::x);
     extern __shared__ __align__(16) double2 csm[];
