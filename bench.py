@@ -72,9 +72,9 @@ def parse():
                          "FGMRES with the sweep as preconditioner (at most this many steps); 0: one sweep")
     ap.add_argument("--inner-restart", type=int, default=30)
     ap.add_argument("--inner-tol", type=float, default=1e-2)
-    ap.add_argument("--persistent", action="store_true",
-                    help="run each sweep of the interface iterations as one cooperative launch (grid barriers "
-                         "between stages) instead of graph-replayed stage launches")
+    ap.add_argument("--sweep", default="stages", choices=["stages", "barrier", "dependency"],
+                    help="the sweeps of the interface iterations: stage launches (default), one cooperative launch "
+                         "with grid barriers between stages, or one dependency-driven cooperative launch")
     ap.add_argument("--inner-fp64", action="store_true",
                     help="FP64 interface Krylov vectors with complex64 factors (default: complex64 vectors)")
     ap.add_argument("--tc-scale", type=float, default=0.5,
@@ -97,7 +97,7 @@ ORACLE_RESTART = 150
 def inner_kw(args):
     """Interface-Krylov options of Problem.solve."""
     return dict(inner_maxit=args.inner_maxit, inner_restart=args.inner_restart, inner_tol=args.inner_tol,
-                inner_fp64=args.inner_fp64, persistent=args.persistent)
+                inner_fp64=args.inner_fp64, persistent={"stages": 0, "barrier": 1, "dependency": 2}[args.sweep])
 
 
 def precond_only(args):
@@ -568,7 +568,9 @@ def gpu_arm(args):
             "interface_krylov": ({"inner_maxit": args.inner_maxit, "inner_restart": args.inner_restart,
                                   "inner_tol": args.inner_tol, "inner_steps_per_solve": inner_per_solve,
                                   "vectors": "c128" if (args.inner_fp64 or args.prec == "c128") else "c64",
-                                  "sweep": "persistent kernel" if args.persistent else "graph-replayed stage launches"}
+                                  "sweep": {"stages": "stage launches (programmatic dependencies)",
+                                            "barrier": "one cooperative launch, grid barriers",
+                                            "dependency": "one cooperative launch, per-item dependencies"}[args.sweep]}
                                  if args.inner_maxit > 0 else None),
             "relres_host_check": check, "factor_ms": factor_ms, "factor_bytes": p.info()["factor_bytes"],
             "l2": (f"inputs larger than L2: every timed solve streams the {p.info()['factor_bytes'] / 1e9:.2f} GB "

@@ -156,11 +156,16 @@ typedef struct {
                            on the volume system */
     int inner_restart;  /* default 100 */
     double inner_tol;   /* default 1e-4 */
-    int persistent;     /* 1: the interface stages of every sweep run as one cooperative
-                           launch with a grid barrier between stages (needs the boundary
-                           operators); 0 (default): one launch per stage, replayed from a
-                           CUDA graph inside the interface iterations (measured faster on
-                           GB300: 48 vs 39 ms of interface stages per 1023^2 solve) */
+    int persistent;     /* 0 (default): the interface stages of every sweep are separate
+                           launches (graph-replayed inside the interface iterations, each
+                           starting its prologue while the previous stage runs);
+                           1: all of them in one cooperative launch with a grid barrier
+                           between stages (measured slower on GB300);
+                           2: all of them in one cooperative launch without barriers:
+                           each work item (stage, subdomain, row block) waits only for the
+                           earlier items that produce or read the trace slots it touches
+                           (counters in device memory, bounded waits).  1 and 2 need the
+                           boundary operators */
     double* inner_hist; /* optional host buffer of inner_maxit*nrhs doubles: the residual
                            estimates ||b - (I - S) g_j|| / ||b|| of the interface iteration
                            in the first preconditioner application of this call, RHS k

@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 #include <functional>
+#include <map>
 #include <new>
 #include <string>
 #include <vector>
@@ -222,6 +223,15 @@ struct helm_problem {
     int tc_all_off[2] = {0, 0}, tc_all_n[2] = {0, 0};   // all subdomains by tile count, in d_stage_subs
     long long etot = 0;              // boundary slots 2 (mx + my) summed over the subdomains
     SweepStage* d_sweep = nullptr;   // interface stages of each schedule for the sweep kernel
+    // dependency-driven sweep: work items, per-(stage, subdomain) counters (items needed,
+    // dependency list), per schedule offsets into the global arrays
+    int4* d_dep_items = nullptr;
+    int* d_dep_need = nullptr;
+    int2* d_dep_unit = nullptr;
+    int* d_dep_list = nullptr;
+    int* d_dep_cnt = nullptr;
+    int dep_item_off[HELM_NSCHED] = {}, dep_nitems[HELM_NSCHED] = {};
+    int dep_unit_off[HELM_NSCHED] = {}, dep_nunits[HELM_NSCHED] = {};
     int sweep_off[HELM_NSCHED] = {}, sweep_n[HELM_NSCHED] = {};
     unsigned* d_sweep_bar = nullptr; // its grid-barrier words
 
@@ -617,6 +627,78 @@ extern "C" helm_status helm_setup(int n_x, int n_y, double h, double omega, cons
         }
         p->sweep_n[sc] = (int)(sweep_tab.size() - p->sweep_off[sc]);
     }
+    // dependency-driven sweep tables: per schedule, the work items of its interface
+    // stages in order and, per (stage, subdomain), the earlier (stage, subdomain) pairs it
+    // must wait for: the last writers of the trace slots it reads and writes and the
+    // readers of the slots it overwrites, found by following every slot through the
+    // stages (a slot is keyed by its trace offset, per buffer)
+    std::vector<int4> dep_items;
+    std::vector<int> dep_need, dep_list;
+    std::vector<int2> dep_unit;
+    for (int sc = 0; sc < HELM_NSCHED; ++sc) {
+        p->dep_item_off[sc] = (int)dep_items.size();
+        p->dep_unit_off[sc] = (int)dep_need.size();
+        if (p->sweep_n[sc] == 0) continue;
+        const auto& stg = p->sched[sc];
+        std::map<long long, int> lastw[3];
+        std::map<long long, std::vector<int>> readers[3];
+        for (int si = 0; si < p->sweep_n[sc]; ++si) {
+            const StageDesc& sd = stg[si + 1];
+            struct Touch { int unit; std::vector<std::pair<int, long long>> reads, writes; };
+            std::vector<Touch> touched;
+            for (int q = 0; q < (int)sd.subs.size(); ++q) {
+                const SubDev& d = p->subs[sd.subs[q]].dev;
+                int rows = 0;
+                for (int sde = 0; sde < 4; ++sde)
+                    if ((sd.mask & (1 << sde)) && d.bo[sde] >= 0) rows += (sde == SW || sde == SE) ? d.my : d.mx;
+                const int nblk = (rows + IFACE_RB - 1) / IFACE_RB;
+                const int unit = (int)dep_need.size();
+                dep_need.push_back(nblk);
+                for (int rb = 0; rb < nblk; ++rb) dep_items.push_back(make_int4(si, q, rb, unit));
+                Touch t{unit, {}, {}};
+                if (nblk > 0) {
+                    for (int b : {sd.in0, sd.in1})
+                        if (b >= 0)
+                            for (int sde = 0; sde < 4; ++sde)
+                                if (d.bo[sde] >= 0) t.reads.push_back({b, (long long)d.tin[sde]});
+                    for (int sde = 0; sde < 4; ++sde) {
+                        if (!((sd.mask & (1 << sde)) && d.bo[sde] >= 0)) continue;
+                        for (int b : {sd.base, sd.sub})
+                            if (b >= 0) t.reads.push_back({b, (long long)d.tout[sde]});
+                        for (int b : {sd.dst, sd.dst2})
+                            if (b >= 0) t.writes.push_back({b, (long long)d.tout[sde]});
+                    }
+                }
+                std::vector<int> deps;
+                for (auto& r : t.reads) {
+                    auto it = lastw[r.first].find(r.second);
+                    if (it != lastw[r.first].end()) deps.push_back(it->second);
+                }
+                for (auto& wr : t.writes) {
+                    auto it = lastw[wr.first].find(wr.second);
+                    if (it != lastw[wr.first].end()) deps.push_back(it->second);
+                    auto jt = readers[wr.first].find(wr.second);
+                    if (jt != readers[wr.first].end()) deps.insert(deps.end(), jt->second.begin(), jt->second.end());
+                }
+                std::sort(deps.begin(), deps.end());
+                deps.erase(std::unique(deps.begin(), deps.end()), deps.end());
+                dep_unit.push_back(make_int2((int)dep_list.size(), (int)deps.size()));
+                dep_list.insert(dep_list.end(), deps.begin(), deps.end());
+                touched.push_back(std::move(t));
+            }
+            // the stage's reads and writes take effect after the whole stage (its items
+            // are independent of one another)
+            for (auto& t : touched)
+                for (auto& r : t.reads) readers[r.first][r.second].push_back(t.unit);
+            for (auto& t : touched)
+                for (auto& wr : t.writes) {
+                    lastw[wr.first][wr.second] = t.unit;
+                    readers[wr.first][wr.second].clear();
+                }
+        }
+        p->dep_nitems[sc] = (int)dep_items.size() - p->dep_item_off[sc];
+        p->dep_nunits[sc] = (int)dep_need.size() - p->dep_unit_off[sc];
+    }
 
     // device tables
     helm_status status = HELM_OK;
@@ -662,6 +744,18 @@ extern "C" helm_status helm_setup(int n_x, int n_y, double h, double omega, cons
             if ((e = dalloc(p->d_sweep, sweep_tab.size())) != cudaSuccess) { fail(e, "alloc sweep table"); break; }
             cudaMemcpy(p->d_sweep, sweep_tab.data(), sweep_tab.size() * sizeof(SweepStage), cudaMemcpyHostToDevice);
         }
+        if (!dep_items.empty()) {
+            if ((e = dalloc(p->d_dep_items, dep_items.size())) != cudaSuccess ||
+                (e = dalloc(p->d_dep_need, dep_need.size())) != cudaSuccess ||
+                (e = dalloc(p->d_dep_unit, dep_unit.size())) != cudaSuccess ||
+                (e = dalloc(p->d_dep_list, std::max<size_t>(1, dep_list.size()))) != cudaSuccess ||
+                (e = dalloc(p->d_dep_cnt, dep_need.size())) != cudaSuccess) { fail(e, "alloc sweep dependencies"); break; }
+            cudaMemcpy(p->d_dep_items, dep_items.data(), dep_items.size() * sizeof(int4), cudaMemcpyHostToDevice);
+            cudaMemcpy(p->d_dep_need, dep_need.data(), dep_need.size() * sizeof(int), cudaMemcpyHostToDevice);
+            cudaMemcpy(p->d_dep_unit, dep_unit.data(), dep_unit.size() * sizeof(int2), cudaMemcpyHostToDevice);
+            if (!dep_list.empty())
+                cudaMemcpy(p->d_dep_list, dep_list.data(), dep_list.size() * sizeof(int), cudaMemcpyHostToDevice);
+        }
         if ((e = dalloc(p->d_sweep_bar, 2)) != cudaSuccess) { fail(e, "alloc sweep barrier"); break; }
         if ((e = cudaMemset(p->d_sweep_bar, 0, 2 * sizeof(unsigned))) != cudaSuccess) { fail(e, "clear sweep barrier"); break; }
         if ((e = cudaDeviceSynchronize()) != cudaSuccess) { fail(e, "setup kernels"); break; }
@@ -682,6 +776,7 @@ extern "C" helm_status helm_destroy(helm_problem* p) {
     dfree(p->d_m2); dfree(p->d_adiag); dfree(p->d_dloc); dfree(p->d_subtab);
     dfree(p->d_tc128); dfree(p->d_tc64); dfree(p->d_stage_subs); dfree(p->d_err);
     dfree(p->d_sweep); dfree(p->d_sweep_bar);
+    dfree(p->d_dep_items); dfree(p->d_dep_need); dfree(p->d_dep_unit); dfree(p->d_dep_list); dfree(p->d_dep_cnt);
     for (auto& q : p->prof) {
         for (auto e : q.a) cudaEventDestroy(e);
         for (auto e : q.b) cudaEventDestroy(e);
@@ -923,8 +1018,9 @@ static bool run_sweep_persistent(helm_problem* p, const PcWork& w, int sched, in
                                  helm_status& status) {
     using T = Cx<R>;
     if (!p->persistent || !p->d_K || !p->d_sweep || p->sweep_n[sched] == 0) return false;
-    const int grid = sweep_grid<R>(nrhs, p->max_Lb);
+    const int grid = p->persistent == 1 ? sweep_grid<R>(nrhs, p->max_Lb) : 1;
     if (grid <= 0) return false;
+    if (p->persistent == 2 && p->dep_nitems[sched] == 0) return false;
     IfaceArgs<R> a{};
     a.subtab = p->d_subtab;
     a.subs = p->d_stage_subs;
@@ -940,8 +1036,18 @@ static bool run_sweep_persistent(helm_problem* p, const PcWork& w, int sched, in
         for (size_t i = 1; i + 1 < stg.size(); ++i) iface_accounting(p, stg[i], nrhs, sizeof(T), bytes, flops);
     }
     prof_begin(p, HELM_K_TRACE, st);
-    const cudaError_t e = launch_sweep<R>(a, p->d_sweep + p->sweep_off[sched], p->sweep_n[sched], p->max_Lb, grid,
-                                          p->d_sweep_bar, p->d_err, st);
+    cudaError_t e;
+    if (p->persistent == 2) {
+        // dependency-driven: the counters of this schedule start at zero
+        e = cudaMemsetAsync(p->d_dep_cnt + p->dep_unit_off[sched], 0, (size_t)p->dep_nunits[sched] * sizeof(int), st);
+        if (e == cudaSuccess)
+            e = launch_sweep_dep<R>(a, p->d_sweep + p->sweep_off[sched], p->d_dep_items + p->dep_item_off[sched],
+                                    p->dep_nitems[sched], p->d_dep_need, p->d_dep_unit, p->d_dep_list, p->d_dep_cnt,
+                                    p->max_Lb, st);
+    } else {
+        e = launch_sweep<R>(a, p->d_sweep + p->sweep_off[sched], p->sweep_n[sched], p->max_Lb, grid, p->d_sweep_bar,
+                            p->d_err, st);
+    }
     prof_end(p, HELM_K_TRACE, bytes, st, flops);
     if (p->prof_on && !p->prof_capture) p->prof[HELM_K_TRACE].kernels += p->sweep_n[sched] - 1;
     status = e == cudaSuccess ? HELM_OK : cuda_status(e, "sweep kernel launch");
@@ -1629,7 +1735,7 @@ static helm_status fgmres_core(helm_problem* p, KrylovWS& kw, long long n, int n
     // by a conditional (while) node until every RHS stopped or the cycle is full; the
     // host synchronises once per cycle instead of once per step.  Needs the fused
     // Gram-Schmidt step, no residual history and no per-launch profiling events.
-    const bool dev_loop = ops.dev_step && cgs2_grid_n > 0 && !hist && !p->prof_on && !p->persistent &&
+    const bool dev_loop = ops.dev_step && cgs2_grid_n > 0 && !hist && !p->prof_on && p->persistent != 1 &&
                           !p->dev_loop_broken && kw.ctl && kw.restart >= m;
     if (!x0_given) HELM_CUDA_TRY(cudaMemsetAsync(x, 0, (size_t)nrhs * N * sizeof(VT), st));
 
@@ -1867,7 +1973,17 @@ static helm_status run_precond_iface_t(helm_problem* p, int sched, const double2
     };
     // one Arnoldi step with the slot read on the device (*dj): the same kernels as
     // precond + matvec above, launched directly (this runs under a capture)
-    if (!p->persistent && std::is_same<T, VT>::value) {
+    // the sweep of one step: its stage launches, or the dependency-driven persistent sweep
+    auto sweep_stages = [&](cudaStream_t cs) -> helm_status {
+        helm_status q = HELM_OK;
+        if (p->persistent == 2 && run_sweep_persistent<R>(p, w, sched, nrhs, cs, q)) return q;
+        for (size_t i = 1; i + 1 < stg.size(); ++i) {
+            q = run_stage_t<R>(p, w, cx, stg[i], r, z, nrhs, cs);
+            if (q != HELM_OK) return q;
+        }
+        return HELM_OK;
+    };
+    if (p->persistent != 1 && std::is_same<T, VT>::value) {
         // vectors in the trace buffers' type: the step keeps its data in the trace
         // buffers (the Gram-Schmidt step reads S v - v from B and writes the next input
         // into B and X), one kernel between the sweep and S forms z_j
@@ -1877,10 +1993,8 @@ static helm_status run_precond_iface_t(helm_problem* p, int sched, const double2
         };
         ops.dev_step = [&](cudaStream_t cs, VT* V, VT* Z, long long vsk, const int* dj) -> helm_status {
             (void)V;
-            for (size_t i = 1; i + 1 < stg.size(); ++i) {
-                helm_status q = run_stage_t<R>(p, w, cx, stg[i], r, z, nrhs, cs);
-                if (q != HELM_OK) return q;
-            }
+            helm_status q0 = sweep_stages(cs);
+            if (q0 != HELM_OK) return q0;
             // z_j = X (+ Y) into Z slot j and into X, the input of S
             launch_trace_to<T, VT>(tX, is_bsp(sched) ? tY : (T*)nullptr, 1, Z, tot, cs, dj, 0, vsk,
                                    reinterpret_cast<VT*>(tX));
@@ -1889,15 +2003,13 @@ static helm_status run_precond_iface_t(helm_problem* p, int sched, const double2
         ops.dev_w_src = reinterpret_cast<VT*>(tB);
         ops.dev_v_out1 = reinterpret_cast<VT*>(tB);
         ops.dev_v_out2 = reinterpret_cast<VT*>(tX);
-        ops.dev_tag = 2 * sched + 1;
-    } else if (!p->persistent) {
-        ops.dev_tag = 2 * sched;
+        ops.dev_tag = 2 * sched + 1 + 16 * p->persistent;
+    } else if (p->persistent != 1) {
+        ops.dev_tag = 2 * sched + 16 * p->persistent;
         ops.dev_step = [&](cudaStream_t cs, VT* V, VT* Z, long long vsk, const int* dj) -> helm_status {
             launch_trace_from<VT, T>(V, tB, tX, tot, cs, dj, 0, vsk);
-            for (size_t i = 1; i + 1 < stg.size(); ++i) {
-                helm_status q = run_stage_t<R>(p, w, cx, stg[i], r, z, nrhs, cs);
-                if (q != HELM_OK) return q;
-            }
+            helm_status q0 = sweep_stages(cs);
+            if (q0 != HELM_OK) return q0;
             launch_trace_to<T, VT>(tX, is_bsp(sched) ? tY : (T*)nullptr, 1, Z, tot, cs, dj, 0, vsk);
             launch_trace_from<VT, T>(Z, tX, (T*)nullptr, tot, cs, dj, 0, vsk);
             helm_status q = run_stage_t<R>(p, w, cx, sS, r, z, nrhs, cs);
@@ -1981,7 +2093,7 @@ static helm_status gmres_impl(helm_problem* p, const double2* f, double2* u, int
     };
     std::vector<int> iters;
     std::vector<double> relres;
-    p->persistent = o.persistent != 0;
+    p->persistent = o.persistent;
     p->inner_hist_taken = false;
     s = fgmres_core(p, p->kw, N, nrhs, o.restart, o.maxit, o.tol, bnorm, u, o.x0_given != 0, o.ortho,
                     o.hist, ops, iters, relres, "gmres_solve", st);
@@ -2016,6 +2128,7 @@ extern "C" helm_status gmres_solve(helm_problem* p, const helm_c128* f, helm_c12
     if (o.ortho != HELM_ORTHO_MGS && o.ortho != HELM_ORTHO_CGS2 && o.ortho != HELM_ORTHO_CGS2_SPLIT)
         return arg_error("gmres_solve: unknown ortho");
     if (o.inner_maxit < 0) return arg_error("gmres_solve: inner_maxit must be >= 0");
+    if (o.persistent < 0 || o.persistent > 2) return arg_error("gmres_solve: persistent must be 0, 1 or 2");
     if (o.inner_fp64 != 0 && o.inner_fp64 != 1) return arg_error("gmres_solve: inner_fp64 must be 0 or 1");
     if (o.inner_maxit > 0 && (o.inner_restart < 1 || o.inner_restart > 500))
         return arg_error("gmres_solve: inner_restart must be in 1..500");

@@ -190,6 +190,9 @@ template <typename R> struct IfaceArgs {
     int* err;                  // HELM_ERR_TIMEOUT when a bounded wait expired
 };
 
+// output rows of one work item of an interface stage (host tables and kernels agree on it)
+constexpr int IFACE_RB = 16;
+
 // launch shape of the interface-stage kernel: right-hand sides per block (1, 2, 4, 8, 16),
 // K rows staged in shared memory when they fit (1) or read from global memory (0), and
 // the CTAs per SM the grid aims at when it spreads RHS blocks over CTAs
@@ -256,6 +259,14 @@ cudaError_t launch_tc_basis(const StageArgs<float>& a, const float* XT, int MT, 
 template <typename R>
 cudaError_t launch_iface(const IfaceArgs<R>& a, int nactive, int max_rows, int max_Lb, cudaStream_t st,
                          const IfaceCfg* cfg = nullptr);
+// the interface stages of a sweep as one dependency-driven cooperative launch: items
+// (stage, subdomain index in the stage, row block, counter id) in stage order; counter u
+// completes after need[u] items; unit_deps[u] = (offset, count) of its list in deps;
+// counters zero on entry
+template <typename R>
+cudaError_t launch_sweep_dep(const IfaceArgs<R>& a, const SweepStage* stages, const int4* items, int nitems,
+                             const int* need, const int2* unit_deps, const int* deps, int* counters, int max_Lb,
+                             cudaStream_t st);
 // a whole sweep (nstages interface stages, in order) in one cooperative launch of `grid`
 // CTAs (sweep_grid: the co-resident count, 0 when unavailable); bar: two zeroed words
 template <typename R> int sweep_grid(int nrhs, int max_Lb);

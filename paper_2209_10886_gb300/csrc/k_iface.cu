@@ -25,7 +25,7 @@
 namespace {
 
 constexpr int IT = 256;      // threads per CTA
-constexpr int RB = 16;       // output rows per work item
+constexpr int RB = IFACE_RB; // output rows per work item
 constexpr long long SWEEP_WAIT = 2000000000LL;   // cycles (~1 s) before a grid barrier gives up
 
 // LDCG: read through L2 only (data another SM wrote earlier in the same launch)
@@ -76,9 +76,23 @@ template <typename T> __host__ __device__ __forceinline__ int staged_ld(int Lb) 
 // gather.  Staged form (STAGED, one item per CTA): warp 0 first starts
 // one bulk copy per output row of K into shared memory (rows at smem_raw,
 // staged_ld apart; kofs[q] = where row q starts in its slot).
-template <typename R, int NR, bool LDCG, bool STAGED = false, bool MULTI = false>
-__device__ void iface_item(const IfaceArgs<R>& a, int item_sub, int row_block, int rb_first, int rb_step,
-                           unsigned char* smem_raw, unsigned long long* kbar = nullptr, int* kofs = nullptr) {
+// the dependency wait of a stage launched after the previous kernel (programmatic
+// dependency: griddepcontrol.wait, a no-op without one)
+struct GridDepWait {
+    __device__ bool operator()() const {
+        asm volatile("griddepcontrol.wait;\n" ::: "memory");
+        return true;
+    }
+};
+
+// Returns false when a bounded wait expired (the item was abandoned after its own bulk
+// copies completed).  kinit: initialise kbar here (else the caller did, once); kparity:
+// the phase of kbar this item's copies complete.  wait(): called by every thread after
+// the immutable prologue and before the first read of data earlier stages produce.
+template <typename R, int NR, bool LDCG, bool STAGED = false, bool MULTI = false, typename WaitF = GridDepWait>
+__device__ bool iface_item(const IfaceArgs<R>& a, int item_sub, int row_block, int rb_first, int rb_step,
+                           unsigned char* smem_raw, unsigned long long* kbar = nullptr, int* kofs = nullptr,
+                           WaitF wait = WaitF(), bool kinit = true, unsigned kparity = 0) {
     using T = Cx<R>;
     const SubDev sd = a.subtab[a.subs[item_sub]];
     const int Lb = sd.Lb;
@@ -94,7 +108,7 @@ __device__ void iface_item(const IfaceArgs<R>& a, int item_sub, int row_block, i
     for (int s = 0; s < 4; ++s)
         if (on(s)) rcount += len(s);
     const int row0 = row_block * RB;
-    if (row0 >= rcount) return;
+    if (row0 >= rcount) return true;
     // side s and point pt of output row `row` (s = -1 past the last row)
     auto locate = [&](int row, int& s, int& pt) {
         s = -1;
@@ -136,8 +150,10 @@ __device__ void iface_item(const IfaceArgs<R>& a, int item_sub, int row_block, i
         unsigned tot = nbytes;
         for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
         if (lane == 0) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(kbar)) : "memory");
-            asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+            if (kinit) {
+                asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(kbar)) : "memory");
+                asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+            }
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(kbar)), "r"(tot)
                          : "memory");
         }
@@ -171,7 +187,11 @@ __device__ void iface_item(const IfaceArgs<R>& a, int item_sub, int row_block, i
         }
     }
     // the incoming data, base and sub were written by earlier stages
-    asm volatile("griddepcontrol.wait;\n" ::: "memory");
+    if (!wait()) {
+        if (staged && warp == 0 && lane == 0) mb_wait(kbar, kparity);   // no copy outlives the item (bounded)
+        __syncthreads();
+        return false;
+    }
     // MULTI = false: exactly one block (straight-line code)
     for (int rb = rb_first; MULTI ? rb < nrb : rb == rb_first; rb += rb_step) {
     const int rhs0 = rb * NR;
@@ -231,14 +251,14 @@ __device__ void iface_item(const IfaceArgs<R>& a, int item_sub, int row_block, i
         __shared__ int kfail;
         if (threadIdx.x == 0) kfail = 0;
         __syncthreads();
-        if (!mb_wait(kbar, 0)) kfail = 1;
+        if (!mb_wait(kbar, kparity)) kfail = 1;
         __syncthreads();
         if (kfail) {
             if (threadIdx.x == 0) {
                 atomicExch(a.err, (int)HELM_ERR_TIMEOUT);
-                mb_wait(kbar, 0);                   // no copy outlives the CTA, bounded again
+                mb_wait(kbar, kparity);             // no copy outlives the CTA, bounded again
             }
-            return;
+            return false;
         }
     } else {
         __syncthreads();
@@ -302,11 +322,96 @@ __device__ void iface_item(const IfaceArgs<R>& a, int item_sub, int row_block, i
     }
     __syncthreads();                                // the shared gather is reused by the next block
     }
+    return true;
 }
 
 // One stage, one item per CTA, launched with a programmatic dependency on the
 // previous kernel of the stream: each CTA lets the next stage launch at once
 // (that stage waits for this one to complete before its gather).
+// ---------------------------------------------------------------------------
+// Dependency-driven persistent sweep: every interface stage of a sweep in one
+// cooperative launch, without grid barriers.  The work items (stage, subdomain of
+// the stage, block of RB output rows) are dealt to the CTAs in their global order
+// (stage-major); an item waits only for the items of earlier stages that write the
+// trace slots it reads or touch the slots it writes (a per-(stage, subdomain)
+// completion counter, `need` row blocks each), which the host derives from the
+// slots' read and write sets.  Meanwhile its K rows are already on their way into
+// shared memory.  Waits are bounded (HELM_ERR_TIMEOUT, then the CTA returns after
+// its own copies landed).  Deadlock-free with all CTAs resident: a wait points to a
+// strictly earlier stage, and each CTA runs its items in order.
+struct DepWait {
+    const int* deps;           // counter ids this item waits for
+    int ndep;
+    const int* need;           // per counter id: row-block items that complete it
+    const int* counters;
+    int* err;
+    volatile int* sflag;
+    __device__ bool operator()() const {
+        if (threadIdx.x == 0) {
+            const long long t0 = clock64();
+            for (int d = 0; d < ndep && !*sflag; ++d) {
+                const int u = deps[d], want = need[u];
+                for (;;) {
+                    int cur;
+                    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(cur) : "l"(counters + u) : "memory");
+                    if (cur >= want) break;
+                    if (clock64() - t0 > SWEEP_WAIT) {
+                        atomicExch(err, (int)HELM_ERR_TIMEOUT);
+                        *sflag = 1;
+                        break;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        return *sflag == 0;
+    }
+};
+
+template <typename R, int NR>
+__global__ void __launch_bounds__(IT) sweep_dep_kernel(IfaceArgs<R> base, const SweepStage* stages, const int4* items,
+                                                       int nitems, const int* need, const int2* unit_deps,
+                                                       const int* deps, int* counters) {
+    using T = Cx<R>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ __align__(8) unsigned long long kbar;
+    __shared__ int kofs[RB];
+    __shared__ int sflag;
+    if (threadIdx.x == 0) {
+        sflag = 0;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&kbar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+    T* const* bufs = reinterpret_cast<T* const*>(base.bufs);
+    unsigned parity = 0;
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const int4 d = items[it];                     // stage, subdomain in the stage, row block, counter id
+        const SweepStage& st = stages[d.x];
+        IfaceArgs<R> a = base;
+        a.subs = base.subs + st.sub_off;
+        a.gin0 = st.in0 >= 0 ? bufs[st.in0] : nullptr;
+        a.gin1 = st.in1 >= 0 ? bufs[st.in1] : nullptr;
+        a.mask = st.mask;
+        a.dst = st.dst >= 0 ? bufs[st.dst] : nullptr;
+        a.dst2 = st.dst2 >= 0 ? bufs[st.dst2] : nullptr;
+        a.base = st.base >= 0 ? bufs[st.base] : nullptr;
+        a.sub = st.sub >= 0 ? bufs[st.sub] : nullptr;
+        const int2 ud = unit_deps[d.w];
+        const DepWait w{deps + ud.x, ud.y, need, counters, base.err, &sflag};
+        const bool ok =
+            iface_item<R, NR, true, true, true, DepWait>(a, d.y, d.z, 0, 1, smem_raw, &kbar, kofs, w, false, parity);
+        parity ^= 1u;
+        if (!ok) return;
+        // publish: the item's stores (ordered before this point by the item's final
+        // __syncthreads) precede the count
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd(counters + d.w, 1);
+        }
+    }
+}
+
 template <typename R, int NR, bool STAGED, bool MULTI>
 __global__ void __launch_bounds__(IT) iface_kernel(IfaceArgs<R> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -443,6 +548,36 @@ cudaError_t launch_sweep_nr(const IfaceArgs<R>& a, const SweepStage* stages, int
     return cudaLaunchCooperativeKernel((const void*)sweep_kernel<R, NR>, dim3(grid), dim3(IT), args, smem, st);
 }
 
+template <typename R, int NR>
+cudaError_t launch_sweep_dep_nr(const IfaceArgs<R>& a, const SweepStage* stages, const int4* items, int nitems,
+                                const int* need, const int2* unit_deps, const int* deps, int* counters, int max_Lb,
+                                cudaStream_t st) {
+    using T = Cx<R>;
+    const size_t smem = (size_t)RB * staged_ld<T>(max_Lb) * sizeof(T) + 2 * (size_t)NR * max_Lb * sizeof(T);
+    if (smem > 227 * 1024 || (reinterpret_cast<uintptr_t>(a.K) & 15) != 0) return cudaErrorNotSupported;
+    cudaError_t e = cudaFuncSetAttribute(sweep_dep_kernel<R, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, sweep_dep_kernel<R, NR>, IT, smem)) != cudaSuccess)
+        return e;
+    if (per < 1) return cudaErrorNotSupported;
+    const int grid = (int)std::min<long long>((long long)std::min(per, 2) * sms, nitems);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(std::max(grid, 1));
+    cfg.blockDim = dim3(IT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    count_launch();
+    return cudaLaunchKernelEx(&cfg, sweep_dep_kernel<R, NR>, a, stages, items, nitems, need, unit_deps, deps, counters);
+}
+
 }  // namespace
 
 // CTAs of the sweep kernel that are co-resident on the device (0: cooperative launch unavailable)
@@ -471,6 +606,18 @@ cudaError_t launch_sweep(const IfaceArgs<R>& a, const SweepStage* stages, int ns
     return launch_sweep_nr<R, 1>(a, stages, nstages, max_Lb, grid, bar, err, st);
 }
 
+// the interface stages of a sweep as one dependency-driven cooperative launch (see
+// sweep_dep_kernel); counters must be zero on entry
+template <typename R>
+cudaError_t launch_sweep_dep(const IfaceArgs<R>& a, const SweepStage* stages, const int4* items, int nitems,
+                             const int* need, const int2* unit_deps, const int* deps, int* counters, int max_Lb,
+                             cudaStream_t st) {
+    if (nitems == 0 || a.nrhs == 0) return cudaSuccess;
+    if (a.nrhs >= 4) return launch_sweep_dep_nr<R, 4>(a, stages, items, nitems, need, unit_deps, deps, counters, max_Lb, st);
+    if (a.nrhs >= 2) return launch_sweep_dep_nr<R, 2>(a, stages, items, nitems, need, unit_deps, deps, counters, max_Lb, st);
+    return launch_sweep_dep_nr<R, 1>(a, stages, items, nitems, need, unit_deps, deps, counters, max_Lb, st);
+}
+
 template <typename R>
 cudaError_t launch_iface(const IfaceArgs<R>& a, int nactive, int max_rows, int max_Lb, cudaStream_t st,
                          const IfaceCfg* cfg) {
@@ -490,6 +637,10 @@ cudaError_t launch_iface(const IfaceArgs<R>& a, int nactive, int max_rows, int m
 
 template cudaError_t launch_iface<float>(const IfaceArgs<float>&, int, int, int, cudaStream_t, const IfaceCfg*);
 template cudaError_t launch_iface<double>(const IfaceArgs<double>&, int, int, int, cudaStream_t, const IfaceCfg*);
+template cudaError_t launch_sweep_dep<float>(const IfaceArgs<float>&, const SweepStage*, const int4*, int, const int*,
+                                             const int2*, const int*, int*, int, cudaStream_t);
+template cudaError_t launch_sweep_dep<double>(const IfaceArgs<double>&, const SweepStage*, const int4*, int, const int*,
+                                              const int2*, const int*, int*, int, cudaStream_t);
 template int sweep_grid<float>(int, int);
 template int sweep_grid<double>(int, int);
 template cudaError_t launch_sweep<float>(const IfaceArgs<float>&, const SweepStage*, int, int, int, unsigned*, int*,

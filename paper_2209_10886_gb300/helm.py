@@ -193,7 +193,9 @@ class Problem:
         ortho: "mgs" (volume default), "cgs2" or "cgs2_split" (see helm.h); inner_fp64: FP64
         interface Krylov vectors with complex64 factors (default: complex64 vectors);
         inner_history: keep the interface residual history of the first preconditioner
-        application in self.last_inner_history (one list per RHS)."""
+        application in self.last_inner_history (one list per RHS); persistent: False (stage
+        launches), True / "barrier" or "dependency" (one cooperative launch per sweep, see
+        helm.h)."""
         f = _as_fields(f, self.N, "f")
         nrhs = f.numel() // self.N
         u = torch.empty_like(f) if u is None else u
@@ -202,7 +204,8 @@ class Problem:
         hist = (ctypes.c_double * (maxit * nrhs))() if history else None
         o = default_opts(restart=restart, maxit=maxit, tol=tol, sched=sched, x0_given=int(x0 is not None),
                          use_graph=int(bool(use_graph)), inner_maxit=int(inner_maxit),
-                         inner_restart=int(inner_restart), inner_tol=float(inner_tol), persistent=int(bool(persistent)),
+                         inner_restart=int(inner_restart), inner_tol=float(inner_tol),
+                         persistent={False: 0, True: 1, "barrier": 1, "dependency": 2}.get(persistent, persistent),
                          ortho=ORTHO[ortho], inner_fp64=int(bool(inner_fp64)))
         if hist is not None:
             o.hist = ctypes.cast(hist, ctypes.POINTER(ctypes.c_double))

@@ -327,16 +327,20 @@ def test_device_driven_interface_loop_matches_host_loop(H, prec):
     p.close()
 
 
-@pytest.mark.parametrize("sched", ["BSP", "SP"])
-def test_persistent_sweep_gives_the_same_solve(H, sched):
-    """persistent: the interface stages of each sweep in one cooperative launch with grid
-    barriers; the same stages in the same order, so the same iterates."""
+@pytest.mark.parametrize("mode", ["barrier", "dependency"])
+@pytest.mark.parametrize("sched", ["BSP", "SP", "BSP_NONOVERLAP"])
+def test_persistent_sweep_gives_the_same_solve(H, sched, mode):
+    """persistent: the interface stages of each sweep in one cooperative launch, with grid
+    barriers between stages or with per-item dependencies; the same items with the same
+    arithmetic, so the same iterates (the dependency-driven form also inside the
+    device-driven loop)."""
     w = CASES["uneven_4x3"]()
     p, _ = make(H, w, "c64")
     f = cuda(W.random_complex((2, w.N), 24))
-    u0, i0, _ = p.solve(f, tol=1e-9, restart=30, maxit=200, sched=sched, inner_maxit=60, inner_tol=1e-3)
-    u1, i1, _ = p.solve(f, tol=1e-9, restart=30, maxit=200, sched=sched, inner_maxit=60, inner_tol=1e-3,
-                        persistent=True)
+    kw = dict(tol=1e-9, restart=30, maxit=200, sched=sched, inner_maxit=60, inner_tol=1e-3)
+    u0, i0, _ = p.solve(f, **kw)
+    u1, i1, _ = p.solve(f, persistent=mode, **kw)
+    print(f"{sched} {mode}: its {[i[0] for i in i0]} vs {[i[0] for i in i1]}, rel {rel(u1.cpu().numpy(), u0.cpu().numpy()):.1e}")
     assert [i[0] for i in i0] == [i[0] for i in i1]
     assert rel(u1.cpu().numpy(), u0.cpu().numpy()) <= 1e-9
     p.close()
