@@ -36,9 +36,12 @@ if ROOT not in sys.path:
 METRIC = "unknowns×RHS solved/s to rel. residual 1e-6 (mixed vs FP64, 1 GB300); % of roofline"
 UNIT = "unknowns*RHS/s"
 WORKLOAD = "plain_mixed"
-# DRAM traffic of one stage-kernel launch measured by ncu, keyed by the sha256 of
-# the kernel source it was measured on (None once the source changes).
-NCU_TRAFFIC = {}
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch measured by ncu,
+# keyed by (kernel source file, sha256 prefix of that file when it was measured): None
+# once the source changes.  k_iface.cu: mean over 36 consecutive iface_kernel launches
+# of the bench (sweep, residual and S stages), caches left warm (--cache-control none);
+# profiles/iface_kernel_plain_mixed_interface_krylov.md gives the command.
+NCU_TRAFFIC = {("k_iface.cu", "8a5e1404ccd329d2"): 8.392e6}
 FP64_PEAK_TFLOPS = 1.25
 
 
@@ -242,9 +245,9 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def kernel_hash():
-    src = os.path.join(ROOT, "paper_2209_10886_gb300", "csrc", "k_stage.cu")
-    return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+def kernel_hash(name="k_stage.cu"):
+    src = os.path.join(ROOT, "paper_2209_10886_gb300", "csrc", name)
+    return (name, hashlib.sha256(open(src, "rb").read()).hexdigest()[:16])
 
 
 # ------------------------------------------------------------------ clocks
@@ -539,7 +542,9 @@ def gpu_arm(args):
         bw = st_[2] / (st_[1] / 1e3) / 1e9
         names = {"trace": "iface_kernel (boundary-operator GEMV + transmission)", "matvec": "matvec_kernel"}
         roofline = {"bound": "hbm", "achieved": bw, "peak": peak, "unit": "GB/s", "frac": bw / peak,
-                    "traffic": None, "kernel": names.get(dom, dom), "launches": st_[0],
+                    "traffic": NCU_TRAFFIC.get(kernel_hash("k_iface.cu")) if dom == "trace" else None,
+                    "algorithmic_bytes_per_launch": st_[2] / max(st_[0], 1),
+                    "kernel": names.get(dom, dom), "launches": st_[0],
                     "peak_source": f"hbm_gbs of {peak_src}"}
     cpu = None
     if not args.no_cpu_baseline and world == 1 and wname == WORKLOAD and not args.nrhs:

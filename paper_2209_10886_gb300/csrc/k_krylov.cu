@@ -256,22 +256,40 @@ __global__ void hessenberg_step_kernel(double2* __restrict__ H, int ldh, long lo
 }
 
 // y = R^{-1} g (upper triangular R = rotated H, first jcount[k] columns)
+// one warp per RHS: the right-hand side (and, for up to HS_SMEM columns, the upper
+// triangle of R) in shared memory, then column-oriented back substitution: y_i from
+// row i, every lane subtracts R(r, i) y_i from its rows r < i
+constexpr int HS_SMEM = 48;
 __global__ void hessenberg_solve_kernel(const double2* __restrict__ H, int ldh, long long hs, const double2* __restrict__ g,
-                                        int ldg, const int* __restrict__ jcount, double2* __restrict__ y, int ldy, int nrhs) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+                                        int ldg, const int* __restrict__ jcount, double2* __restrict__ y, int ldy, int nrhs,
+                                        bool cache_ok) {
+    // rhs[m] | R[m][m] (column-major; allocated only when the restart length is at most HS_SMEM)
+    extern __shared__ double2 hsm2[];
+    const int k = blockIdx.x, lane = threadIdx.x;
     if (k >= nrhs) return;
     const int m = jcount[k];
     const double2* Hk = H + k * hs;
     double2* yk = y + (long long)k * ldy;
+    double2* rhs = hsm2;
+    double2* R = hsm2 + m;
+    const bool cached = cache_ok && m <= HS_SMEM;
+    for (int i = lane; i < m; i += 32) rhs[i] = g[(long long)k * ldg + i];
+    if (cached)
+        for (int c = 0; c < m; ++c)
+            for (int r = lane; r <= c; r += 32) R[c * m + r] = Hk[(long long)c * ldh + r];
+    __syncwarp();
     for (int i = m - 1; i >= 0; --i) {
-        double2 acc = g[(long long)k * ldg + i];
-        for (int jj = i + 1; jj < m; ++jj) {
-            const double2 h = Hk[(long long)jj * ldh + i];
-            const double2 yy = yk[jj];
-            acc.x -= h.x * yy.x - h.y * yy.y;
-            acc.y -= h.x * yy.y + h.y * yy.x;
+        const double2 d = cached ? R[i * m + i] : Hk[(long long)i * ldh + i];
+        const double2 yi = cdiv(rhs[i], d);
+        if (lane == 0) yk[i] = yi;
+        for (int r = lane; r < i; r += 32) {
+            const double2 h = cached ? R[i * m + r] : Hk[(long long)i * ldh + r];
+            double2 v = rhs[r];
+            v.x -= h.x * yi.x - h.y * yi.y;
+            v.y -= h.x * yi.y + h.y * yi.x;
+            rhs[r] = v;
         }
-        yk[i] = cdiv(acc, Hk[(long long)i * ldh + i]);
+        __syncwarp();
     }
 }
 
@@ -375,7 +393,10 @@ void launch_hessenberg_step(double2* H, int ldh, long long hs, double2* cs, doub
 void launch_hessenberg_solve(const double2* H, int ldh, long long hs, const double2* g, int ldg, const int* jcount,
                              double2* y, int ldy, int nrhs, cudaStream_t st) {
     count_launch();
-    hessenberg_solve_kernel<<<(nrhs + 31) / 32, 32, 0, st>>>(H, ldh, hs, g, ldg, jcount, y, ldy, nrhs);
+    // shared memory for the largest possible m (the restart length, at most ldh - 1)
+    const int mmax = ldh - 1;
+    const size_t smem = (size_t)(mmax + (mmax <= HS_SMEM ? mmax * mmax : 0)) * sizeof(double2);
+    hessenberg_solve_kernel<<<nrhs, 32, smem, st>>>(H, ldh, hs, g, ldg, jcount, y, ldy, nrhs, mmax <= HS_SMEM);
 }
 void launch_sqrt_inplace(double* v, int n, cudaStream_t st) {
     count_launch();
