@@ -1504,8 +1504,8 @@ static helm_status ensure_kw(KrylovWS& w, int nrhs, int m, long long n, bool wit
         const int g = mgs_grid();
         if (g > 0) {
             // two halves of per-CTA partials: one value (modified Gram-Schmidt) or j + 2
-            // values (the fused classical step) per CTA
-            chk(dalloc(w.mgs_part, (size_t)2 * g * (m + 2)));
+            // values per RHS of a group (the fused classical step) per CTA
+            chk(dalloc(w.mgs_part, (size_t)2 * g * (m + 2) * 16));   // groups of up to 16 RHS (k_mgs.cu)
             chk(dalloc(w.mgs_bar, (size_t)2));
             if (e == cudaSuccess) e = cudaMemset(w.mgs_bar, 0, 2 * sizeof(unsigned));
         }

@@ -637,6 +637,310 @@ __global__ void __launch_bounds__(CT, 1) cgs2_step_kernel(Cgs2Args<VT> a) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// The same step for several RHS at once (nrhs >= 2): groups of up to CG_MAX RHS go
+// through every phase together, so a group costs the grid barriers one RHS does (2, or
+// 4 when any of its RHS needs the second pass).  The dot products of all (RHS, basis
+// vector) pairs of the group and the squared norms (the dot of w with itself) share
+// one grid reduction; the second-pass test is per RHS; the Givens updates of the
+// group's RHS run on different CTAs.
+constexpr int CG_MAX = 16;
+
+template <typename VT>
+__global__ void __launch_bounds__(CT, 1) cgs2_group_kernel(Cgs2Args<VT> a, int G) {
+    using Re = decltype(VT::x);
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+    const int J = a.dj ? *a.dj : a.j;               // the new column
+    const int nvec = J + 1, PS = J + 2, CS = G * PS;
+    extern __shared__ __align__(16) double2 csm[];
+    double2* hv = csm;                              // [G * PS] reduced values of the current pass
+    double2* h1 = hv + (size_t)G * PS;              // [G * nvec] coefficients, both passes
+    double2* gv = h1 + (size_t)G * nvec;            // [3 (J + 2)] Givens scratch
+    VT* hc = reinterpret_cast<VT*>(gv + 3 * (J + 2));   // [G * nvec] -hv in the vectors' precision
+    VT* ws = hc + (size_t)G * nvec;                 // [G * L] slices of w
+    __shared__ double2 gsum[CT];
+    __shared__ int sflag;
+    __shared__ int gact[CG_MAX], gsec[CG_MAX];
+    __shared__ double gw2[CG_MAX], gn2[CG_MAX];
+    __shared__ Re ginv[CG_MAX];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int L = a.L;
+    const long long c0 = (long long)blockIdx.x * L;
+    const int len = (int)max(0LL, min((long long)L, a.n - c0));
+    if (threadIdx.x == 0) sflag = 0;
+    __syncthreads();
+    unsigned s = 0;
+    auto cur_part = [&]() { return a.partial + (size_t)(s & 1u) * gridDim.x * CS; };
+    // every CTA adds column k < cnt of all CTAs' partials (stride CS) in the same order
+    // into hv[k]: lane = column, warps over CTA groups, a butterfly, the warp sums in order
+    auto grid_reduce = [&](double2* part, int cnt) -> bool {
+        if (!grid_barrier(a.bar, a.err, &sflag)) return false;
+        const int Gd = (int)gridDim.x;
+        for (int kb = 0; kb < cnt; kb += 32) {
+            const int rem = min(32, cnt - kb);
+            int KP = 1;
+            while (KP < rem) KP <<= 1;
+            const int groups = CT / KP;
+            const int kq = threadIdx.x & (KP - 1), grp = threadIdx.x / KP;
+            double2 t = make_double2(0.0, 0.0);
+            if (kq < rem) {
+                for (int cb = grp; cb < Gd; cb += groups * 8) {
+                    double2 pv[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int c = cb + groups * u;
+                        pv[u] = c < Gd ? __ldcg(part + (long long)c * CS + kb + kq) : make_double2(0.0, 0.0);
+                    }
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) { t.x += pv[u].x; t.y += pv[u].y; }
+                }
+            }
+            for (int o = 16; o >= KP; o >>= 1) {
+                t.x += __shfl_xor_sync(0xffffffffu, t.x, o);
+                t.y += __shfl_xor_sync(0xffffffffu, t.y, o);
+            }
+            if (lane < KP) gsum[warp * KP + lane] = t;
+            __syncthreads();
+            if (threadIdx.x < rem) {
+                double2 v = gsum[threadIdx.x];
+                for (int q = 1; q < CT / 32; ++q) { v.x += gsum[q * KP + threadIdx.x].x; v.y += gsum[q * KP + threadIdx.x].y; }
+                hv[kb + threadIdx.x] = v;
+            }
+            __syncthreads();
+        }
+        ++s;
+        return true;
+    };
+
+    for (int g0 = 0; g0 < a.nrhs; g0 += G) {
+        const int gn = min(G, a.nrhs - g0);
+        if (threadIdx.x < CG_MAX) {
+            const int t = threadIdx.x;
+            gact[t] = t < gn && (!a.active || a.active[g0 + t]);
+            gsec[t] = 0;
+        }
+        __syncthreads();
+        int any = 0;
+        for (int g = 0; g < gn; ++g) any |= gact[g];
+        if (!any) continue;                          // every thread reads the same flags
+        // partial dots over the slices, one warp per (RHS, vector) pair, PP pairs of a warp
+        // with all their loads in flight: mode 0 every basis vector and w itself (the
+        // squared norm, k = nvec), mode 1 only w itself (partial at g), mode 2 the basis
+        // vectors of the RHS that need a second pass
+        constexpr int PP = 4;
+        auto dots = [&](int mode, double2* part) {
+            const int per = mode == 1 ? 1 : (mode == 0 ? nvec + 1 : nvec);
+            const int np = gn * per;
+            for (int pb = warp * PP; pb < np; pb += PP * (CT / 32)) {
+                const VT* vp[PP];
+                const VT* wp[PP];
+                bool onp[PP], selfp[PP];          // selfp: w with itself (shared memory, plain loads)
+#pragma unroll
+                for (int q = 0; q < PP; ++q) {
+                    const int pr = min(pb + q, np - 1);
+                    const int g = pr / per, kk = pr - g * per;
+                    const int k = mode == 1 ? nvec : kk;
+                    onp[q] = pb + q < np && gact[g] && (mode != 2 || gsec[g]);
+                    selfp[q] = k == nvec;
+                    wp[q] = ws + (size_t)g * L;
+                    vp[q] = k == nvec ? wp[q] : a.V + (long long)k * a.vsk + (long long)(g0 + g) * a.vsr + c0;
+                }
+                VT acc[PP];
+#pragma unroll
+                for (int q = 0; q < PP; ++q) acc[q] = czero<VT>();
+                for (int i0 = 0; i0 < len; i0 += 256) {
+                    VT x[PP][8];
+#pragma unroll
+                    for (int q = 0; q < PP; ++q)
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            const int i = i0 + lane + 32 * u;
+                            x[q][u] = (onp[q] && i < len) ? (selfp[q] ? wp[q][i] : __ldcg(vp[q] + i)) : czero<VT>();
+                        }
+#pragma unroll
+                    for (int q = 0; q < PP; ++q)
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            const int i = i0 + lane + 32 * u;
+                            if (i < len) acc[q] = cfmaconj(x[q][u], wp[q][i], acc[q]);
+                        }
+                }
+#pragma unroll
+                for (int q = 0; q < PP; ++q) {
+                    const VT t = warp_sumc(acc[q]);
+                    const int pr = pb + q;
+                    if (lane == 0 && pr < np) {
+                        const int g = pr / per, kk = pr - g * per;
+                        part[(long long)blockIdx.x * CS + (mode == 1 ? g : g * PS + (mode == 1 ? nvec : kk))] =
+                            make_double2((double)t.x, (double)t.y);
+                    }
+                }
+            }
+        };
+        // ws_g += sum_k hc_gk v_k over the slices (mode 0: active RHS, 2: second-pass ones),
+        // two elements per thread with all 2 x 16 loads in flight
+        auto update = [&](int mode) {
+            const int tot = gn * len;
+            for (int idx0 = threadIdx.x; idx0 < tot; idx0 += 2 * CT) {
+                int gq[2], iq[2];
+                bool onq[2];
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const int idx = min(idx0 + q * CT, tot - 1);
+                    gq[q] = idx / len;
+                    iq[q] = idx - gq[q] * len;
+                    onq[q] = idx0 + q * CT < tot && gact[gq[q]] && (mode != 2 || gsec[gq[q]]);
+                }
+                VT xq[2];
+#pragma unroll
+                for (int q = 0; q < 2; ++q) xq[q] = onq[q] ? ws[(size_t)gq[q] * L + iq[q]] : czero<VT>();
+                for (int k0 = 0; k0 < nvec; k0 += 16) {
+                    VT vv[2][16];
+#pragma unroll
+                    for (int q = 0; q < 2; ++q)
+#pragma unroll
+                        for (int u = 0; u < 16; ++u)
+                            vv[q][u] = (onq[q] && k0 + u < nvec)
+                                           ? __ldcg(a.V + (long long)(k0 + u) * a.vsk + (long long)(g0 + gq[q]) * a.vsr + c0 + iq[q])
+                                           : czero<VT>();
+#pragma unroll
+                    for (int q = 0; q < 2; ++q)
+#pragma unroll
+                        for (int u = 0; u < 16; ++u)
+                            if (k0 + u < nvec) xq[q] = cfma(hc[(size_t)gq[q] * nvec + k0 + u], vv[q][u], xq[q]);
+                }
+#pragma unroll
+                for (int q = 0; q < 2; ++q)
+                    if (onq[q]) ws[(size_t)gq[q] * L + iq[q]] = xq[q];
+            }
+        };
+        // the slices of w (the operator's output, negated, when it comes from wsrc)
+        for (int idx = threadIdx.x; idx < gn * len; idx += CT) {
+            const int g = idx / len, i = idx - g * len;
+            if (!gact[g]) continue;
+            const long long off = (long long)(g0 + g) * a.vsr + c0 + i;
+            VT x;
+            if (a.wsrc) {
+                x = a.wsrc[off];
+                x = mk(-x.x, -x.y);
+            } else {
+                x = a.V[off + (long long)nvec * a.vsk];
+            }
+            ws[(size_t)g * L + i] = x;
+        }
+        __syncthreads();
+        double2* part = cur_part();
+        dots(0, part);
+        if (!grid_reduce(part, gn * PS)) return;
+        if (threadIdx.x < gn) gw2[threadIdx.x] = hv[threadIdx.x * PS + nvec].x;
+        for (int idx = threadIdx.x; idx < gn * nvec; idx += CT) {
+            const int g = idx / nvec, k = idx - g * nvec;
+            const double2 h = hv[g * PS + k];
+            h1[idx] = h;
+            hc[idx] = mk((Re)-h.x, (Re)-h.y);
+        }
+        __syncthreads();
+        update(0);
+        __syncthreads();
+        part = cur_part();
+        dots(1, part);
+        if (!grid_reduce(part, gn)) return;
+        if (threadIdx.x < gn) {
+            const int g = threadIdx.x;
+            gn2[g] = hv[g].x;
+            gsec[g] = gact[g] && gn2[g] < 0.5 * gw2[g];
+        }
+        __syncthreads();
+        int anysec = 0;
+        for (int g = 0; g < gn; ++g) anysec |= gsec[g];
+        if (anysec) {
+            part = cur_part();
+            dots(2, part);
+            if (!grid_reduce(part, gn * PS)) return;
+            for (int idx = threadIdx.x; idx < gn * nvec; idx += CT) {
+                const int g = idx / nvec, k = idx - g * nvec;
+                if (!gsec[g]) continue;
+                const double2 h = hv[g * PS + k];
+                h1[idx] = cadd(h1[idx], h);
+                hc[idx] = mk((Re)-h.x, (Re)-h.y);
+            }
+            __syncthreads();
+            update(2);
+            __syncthreads();
+            part = cur_part();
+            dots(1, part);
+            if (!grid_reduce(part, gn)) return;
+            if (threadIdx.x < gn && gsec[threadIdx.x]) gn2[threadIdx.x] = hv[threadIdx.x].x;
+            __syncthreads();
+        }
+        if (threadIdx.x < gn) {
+            const double hn = sqrt(gn2[threadIdx.x]);
+            ginv[threadIdx.x] = (Re)(hn > 0.0 ? 1.0 / hn : 0.0);
+        }
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < gn * len; idx += CT) {
+            const int g = idx / len, i = idx - g * len;
+            if (!gact[g]) continue;
+            const VT x = ws[(size_t)g * L + i];
+            const VT v = mk(x.x * ginv[g], x.y * ginv[g]);
+            const long long off = (long long)(g0 + g) * a.vsr + c0 + i;
+            const_cast<VT*>(a.V)[off + (long long)nvec * a.vsk] = v;
+            if (a.vout1) a.vout1[off] = v;
+            if (a.vout2) a.vout2[off] = v;
+        }
+        // Givens: RHS g of the group on CTA g mod gridDim.x, in the vectors' precision
+        for (int g = blockIdx.x; g < gn; g += gridDim.x) {
+            if (!gact[g]) continue;                  // uniform over the CTA
+            const int r = g0 + g;
+            const double hn = sqrt(gn2[g]);
+            using C2 = VT;
+            C2* col = reinterpret_cast<C2*>(gv);
+            C2* csv = col + (J + 2);
+            C2* snv = csv + (J + 2);
+            double2* csr = a.cs + (long long)r * a.ldg;
+            double2* snr = a.sn + (long long)r * a.ldg;
+            double2* gr = a.g + (long long)r * a.ldg;
+            const double2* h1g = h1 + (size_t)g * nvec;
+            for (int k = threadIdx.x; k <= J + 1; k += CT) {
+                if (k <= J) a.hsum[(long long)r * a.ldh + k] = h1g[k];
+                const double2 hk = k <= J ? h1g[k] : make_double2(hn, 0.0);
+                col[k] = mk((Re)hk.x, (Re)hk.y);
+                if (k < J) {
+                    csv[k] = mk((Re)csr[k].x, (Re)0);
+                    snv[k] = mk((Re)snr[k].x, (Re)snr[k].y);
+                }
+            }
+            __shared__ C2 gpair[2];
+            if (threadIdx.x == 0) gpair[0] = mk((Re)gr[J].x, (Re)gr[J].y);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                a.hnorm[r] = hn;
+                a.need[r] = gsec[g] ? 1 : 0;
+                C2 gj = gpair[0], gj1;
+                givens_column<C2>(col, csv, snv, J, gj, gj1);
+                gpair[0] = gj;
+                gpair[1] = gj1;
+                a.invh[r] = hn > 0.0 ? 1.0 / hn : 0.0;
+            }
+            __syncthreads();
+            double2* colg = a.H + r * a.hs + (long long)J * a.ldH;
+            for (int k = threadIdx.x; k <= J + 1; k += CT) colg[k] = make_double2((double)col[k].x, (double)col[k].y);
+            if (threadIdx.x == 32) {
+                csr[J] = make_double2((double)csv[J].x, 0.0);
+                snr[J] = make_double2((double)snv[J].x, (double)snv[J].y);
+            }
+            if (threadIdx.x == 64) {
+                const C2 q0 = gpair[0], q1 = gpair[1];
+                gr[J] = make_double2((double)q0.x, (double)q0.y);
+                gr[J + 1] = make_double2((double)q1.x, (double)q1.y);
+                a.est[r] = sqrt((double)q1.x * (double)q1.x + (double)q1.y * (double)q1.y);
+            }
+            __syncthreads();
+        }
+        __syncthreads();                             // ws, hv, hc, h1 and the flags are reused by the next group
+    }
+}
+
 }  // namespace
 
 // Grid size (CTAs, all co-resident) for the persistent Gram-Schmidt kernel, or 0.
@@ -703,7 +1007,9 @@ int cgs2_grid(long long n, int max_j) {
 // kernel leaves them).  partial holds 2 * grid * (j + 2) values.  With dj, j is
 // read on the device (*dj, at most jmax) and shared memory is sized for jmax.
 // With wsrc, w = -wsrc (the interface operator's output, S v - v); with vout1/2,
-// v_{j+1} is also written there (the next step's preconditioner input).
+// v_{j+1} is also written there (the next step's preconditioner input).  Two or more
+// RHS go through cgs2_group_kernel in groups; partial then holds 2 * grid * G * (j + 2)
+// values for groups of G <= CG_MAX.
 // Launched through cudaLaunchKernelEx with the cooperative attribute, so it can
 // be captured into a graph.
 template <typename VT>
@@ -716,22 +1022,38 @@ cudaError_t launch_cgs2_step(const VT* V, long long vsk, long long vsr, int j, l
     const int L = (int)((n + grid - 1) / grid);
     Cgs2Args<VT> a{V, vsk, vsr, j, n, nrhs, active, hsum, ldh, hnorm, need, H, ldH, hs, cs, sn, g, ldg, est, invh,
                    partial, bar, err, L, dj, wsrc, vout1, vout2};
-    const size_t smem = cgs2_smem<VT>(L, dj ? jmax : j);
-    if (smem > 48 * 1024) {
-        cudaError_t e =
-            cudaFuncSetAttribute(cgs2_step_kernel<VT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(CT);
-    cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    const int J = dj ? jmax : j;
+    if (nrhs >= 2) {
+        // groups of RHS: as many as fit in ~200 KB of shared memory, at most CG_MAX
+        const size_t fixed = (size_t)3 * (J + 2) * sizeof(double2);
+        const size_t per = (size_t)((J + 2) + (J + 1)) * sizeof(double2) + (size_t)((J + 1) + L) * sizeof(VT);
+        const int G = (int)std::min<long long>(std::min(CG_MAX, nrhs), (long long)((200 * 1024 - fixed) / per));
+        if (G >= 2) {
+            const size_t smem = fixed + (size_t)G * per;
+            cudaError_t e =
+                cudaFuncSetAttribute(cgs2_group_kernel<VT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            cfg.dynamicSmemBytes = smem;
+            count_launch();
+            return cudaLaunchKernelEx(&cfg, cgs2_group_kernel<VT>, a, G);
+        }
+    }
+    const size_t smem = cgs2_smem<VT>(L, J);
+    if (smem > 48 * 1024) {
+        cudaError_t e =
+            cudaFuncSetAttribute(cgs2_step_kernel<VT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    cfg.dynamicSmemBytes = smem;
     count_launch();
     return cudaLaunchKernelEx(&cfg, cgs2_step_kernel<VT>, a);
 }
