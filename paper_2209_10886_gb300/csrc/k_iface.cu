@@ -213,6 +213,7 @@ __device__ bool iface_item(const IfaceArgs<R>& a, int item_sub, int row_block, i
 
     T* graw = staged ? Ks + (size_t)RB * Lbp : reinterpret_cast<T*>(smem_raw);   // [NR][Lb] incoming data
     T* g = graw + (size_t)NR * Lb;                 // [NR][Lb] cin * incoming data
+    if constexpr (NR == 1) {
     // every load of up to GU elements per thread is issued before the first is used
     constexpr int GU = 4;
     for (int i0 = threadIdx.x; i0 < NR * Lb; i0 += IT * GU) {
@@ -245,6 +246,33 @@ __device__ bool iface_item(const IfaceArgs<R>& a, int item_sub, int row_block, i
                 g[idx] = cmul(G[u], C[u]);
             }
         }
+    }
+    } else {
+    // several RHS: a thread takes boundary points, finds the point's trace index and
+    // coefficient once and issues the loads of all the block's RHS together
+    for (int e = threadIdx.x; e < Lb; e += IT) {
+        int s = 0;
+#pragma unroll
+        for (int q = 1; q < 4; ++q)
+            if (bo[q] >= 0 && e >= bo[q]) s = q;
+        const long long ti = sel4(tin, s) + (e - sel4(bo, s));
+        const T cin = a.tc[ti].cin;
+        T G[NR];
+#pragma unroll
+        for (int k = 0; k < NR; ++k) {
+            G[k] = czero<T>();
+            if (k < nr) {
+                const long long o = (long long)(rhs0 + k) * a.ntrace + ti;
+                if (a.gin0) G[k] = ldg_<T, LDCG>(a.gin0 + o);
+                if (a.gin1) G[k] = cadd(G[k], ldg_<T, LDCG>(a.gin1 + o));
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < NR; ++k) {
+            graw[k * Lb + e] = G[k];
+            g[k * Lb + e] = cmul(G[k], cin);
+        }
+    }
     }
     if (staged && rb == rb_first) {
         // every thread waits for the copies (bounded); a timeout anywhere ends the item
