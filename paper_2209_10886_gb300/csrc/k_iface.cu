@@ -196,20 +196,20 @@ __device__ bool iface_item(const IfaceArgs<R>& a, int item_sub, int row_block, i
     for (int rb = rb_first; MULTI ? rb < nrb : rb == rb_first; rb += rb_step) {
     const int rhs0 = rb * NR;
     const int nr = min(NR, a.nrhs - rhs0);
-    // base - sub of the warp's outputs (lane 0), loaded alongside the gather
-    T bsub[RPW][NR];
+    // base - sub of the warp's outputs, loaded alongside the gather: one RHS, lane 0;
+    // several, lane k for RHS k (the lane that forms that RHS's outputs)
+    T bsub[RPW];
 #pragma unroll
-    for (int q = 0; q < RPW; ++q)
-#pragma unroll
-        for (int k = 0; k < NR; ++k) {
-            T v = czero<T>();
-            if (lane == 0 && srow[q] >= 0 && k < nr) {
-                const long long o = (long long)(rhs0 + k) * a.ntrace + tofs[q];
-                if (a.base) v = ldg_<T, LDCG>(a.base + o);
-                if (a.sub) v = csub(v, ldg_<T, LDCG>(a.sub + o));
-            }
-            bsub[q][k] = v;
+    for (int q = 0; q < RPW; ++q) {
+        T v = czero<T>();
+        const int k = NR == 1 ? 0 : lane;
+        if ((NR == 1 ? lane == 0 : lane < nr) && srow[q] >= 0) {
+            const long long o = (long long)(rhs0 + k) * a.ntrace + tofs[q];
+            if (a.base) v = ldg_<T, LDCG>(a.base + o);
+            if (a.sub) v = csub(v, ldg_<T, LDCG>(a.sub + o));
         }
+        bsub[q] = v;
+    }
 
     T* graw = staged ? Ks + (size_t)RB * Lbp : reinterpret_cast<T*>(smem_raw);   // [NR][Lb] incoming data
     T* g = graw + (size_t)NR * Lb;                 // [NR][Lb] cin * incoming data
@@ -331,18 +331,31 @@ __device__ bool iface_item(const IfaceArgs<R>& a, int item_sub, int row_block, i
     }
 #pragma unroll
     for (int q = 0; q < RPW; ++q) {
-#pragma unroll
-        for (int k = 0; k < NR; ++k)
+        if constexpr (NR == 1) {
             for (int o = 16; o > 0; o >>= 1) {
-                acc[q][k].x += __shfl_down_sync(0xffffffffu, acc[q][k].x, o);
-                acc[q][k].y += __shfl_down_sync(0xffffffffu, acc[q][k].y, o);
+                acc[q][0].x += __shfl_down_sync(0xffffffffu, acc[q][0].x, o);
+                acc[q][0].y += __shfl_down_sync(0xffffffffu, acc[q][0].y, o);
             }
-        if (lane == 0 && srow[q] >= 0) {
+            if (lane == 0 && srow[q] >= 0) {
+                const T out = cadd(cfma(ccb[q], acc[q][0], cmul(cca[q], graw[krow[q]])), bsub[q]);
+                const long long o = (long long)rhs0 * a.ntrace + tofs[q];
+                a.dst[o] = out;
+                if (a.dst2) a.dst2[o] = out;
+            }
+        } else {
+            // butterfly: every lane ends with the row's sums; lane k forms RHS k's output
+            T mine = czero<T>();
 #pragma unroll
             for (int k = 0; k < NR; ++k) {
-                if (k >= nr) break;
-                const T out = cadd(cfma(ccb[q], acc[q][k], cmul(cca[q], graw[k * Lb + krow[q]])), bsub[q][k]);
-                const long long o = (long long)(rhs0 + k) * a.ntrace + tofs[q];
+                for (int o = 16; o > 0; o >>= 1) {
+                    acc[q][k].x += __shfl_xor_sync(0xffffffffu, acc[q][k].x, o);
+                    acc[q][k].y += __shfl_xor_sync(0xffffffffu, acc[q][k].y, o);
+                }
+                if (k == lane) mine = acc[q][k];
+            }
+            if (lane < nr && srow[q] >= 0) {
+                const T out = cadd(cfma(ccb[q], mine, cmul(cca[q], graw[lane * Lb + krow[q]])), bsub[q]);
+                const long long o = (long long)(rhs0 + lane) * a.ntrace + tofs[q];
                 a.dst[o] = out;
                 if (a.dst2) a.dst2[o] = out;
             }
