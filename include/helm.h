@@ -125,8 +125,14 @@ typedef struct {
                            RHS count (2 or more) times the candidate launch shapes of the
                            interface-stage kernel (RHS per block 2/4/8/16, K rows staged in
                            shared memory or not) on the all-subdomain stage S, on the
-                           caller's stream, and keeps the fastest for this problem;
+                           caller's stream, and keeps the fastest for this problem
+                           (with the tensor-core form among the candidates where
+                           tensor_cores allows it);
                            0: fixed rules (see helm_iface_shape) */
+    int tc_iface_min_ctas;  /* an interface stage runs in the tensor-core form (when that
+                           form is chosen) only if it makes at least this many CTAs (of
+                           128 output rows x 16 or 32 RHS); smaller stages take the
+                           CUDA-core shape.  -1 (default): two per SM */
 } helm_setup_opts;
 
 typedef struct {
@@ -321,11 +327,17 @@ typedef struct {
                               writes of the data they touch, counted once) */
 } helm_kstat;
 
-/* Launch shape of the interface-stage kernel for nrhs right-hand sides on p: RHS per
- * block (*nr), K rows staged in shared memory when they fit (*staged), target CTAs per SM
- * (*waves); *tuned = 1 when the autotuner chose it, 0 for the fixed rules (4, 2 or 1 RHS
- * per block, staged, 3).  Any output pointer may be NULL. */
-helm_status helm_iface_shape(const helm_problem* p, int nrhs, int* nr, int* staged, int* waves, int* tuned);
+/* Launch shape of the interface stages for nrhs right-hand sides on p.  CUDA-core form:
+ * RHS per block (*nr), K rows staged in shared memory when they fit (*staged), target
+ * CTAs per SM (*waves).  *tensor = 3 or 1 when the stages large enough to put two CTAs
+ * on every SM run as tensor-core MMAs (3xTF32 or TF32 operands; complex64 factors with
+ * tensor_cores on and nrhs >= tc_min_rhs) with *tensor_rhs = 16 or 32 RHS per CTA, the
+ * smaller stages in the CUDA-core form; 0 and 0 when every stage runs on the CUDA cores.
+ * *tuned = 1 when the autotuner chose it, 0 for the fixed rules (4, 2 or 1 RHS per block,
+ * staged, 3; the tensor cores where allowed, 32 RHS per CTA from 32 RHS, else 16).  Any
+ * output pointer may be NULL. */
+helm_status helm_iface_shape(const helm_problem* p, int nrhs, int* nr, int* staged, int* waves, int* tensor,
+                             int* tensor_rhs, int* tuned);
 
 /* Number of CUDA kernel launches issued by the library in this process. */
 long long helm_launch_count(void);

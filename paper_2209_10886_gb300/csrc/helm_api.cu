@@ -421,6 +421,7 @@ extern "C" void helm_default_setup_opts(helm_setup_opts* o) {
     o->tensor_cores = 1;
     o->tc_min_rhs = 16;
     o->autotune = 1;
+    o->tc_iface_min_ctas = -1;
 }
 
 extern "C" const char* helm_last_error(void) { return g_err.c_str(); }
@@ -474,6 +475,7 @@ extern "C" helm_status helm_setup(int n_x, int n_y, double h, double omega, cons
     if (so.tensor_cores < 0 || so.tensor_cores > 2) return arg_error("helm_setup: tensor_cores must be 0, 1 or 2");
     if (so.tc_min_rhs < 1) return arg_error("helm_setup: tc_min_rhs must be >= 1");
     if (so.autotune != 0 && so.autotune != 1) return arg_error("helm_setup: autotune must be 0 or 1");
+    if (so.tc_iface_min_ctas < -1) return arg_error("helm_setup: tc_iface_min_ctas must be >= -1");
 
     auto xc = make_cuts(n_x, N1, xcuts), yc = make_cuts(n_y, N2, ycuts);
     for (int k = 0; k < N1; ++k)
@@ -1085,6 +1087,23 @@ static const IfaceCfg* tuned_shape(const helm_problem* p, int nrhs) {
         if (t.prec == p->prec && t.nrhs == nrhs) return &t.cfg;
     return nullptr;
 }
+// the tensor-core form of the interface stages for nrhs RHS, where it is allowed
+static bool iface_tc_cfg(const helm_problem* p, int nrhs, IfaceCfg& c) {
+    if (p->prec != HELM_PREC_C64 || !tc_used(p, nrhs) || (p->tc_split != 1 && p->tc_split != 3)) return false;
+    c = IfaceCfg{};
+    c.nr = nrhs >= 4 ? 4 : nrhs >= 2 ? 2 : 1;
+    c.tc = p->tc_split;
+    c.tc_nb = nrhs >= 32 ? 32 : 16;
+    c.tc_min_ctas = p->sopts.tc_iface_min_ctas;
+    return true;
+}
+// the launch shape the interface stages use: the autotuned one, else the tensor cores
+// where allowed, else the kernel's fixed rules (nullptr)
+static const IfaceCfg* iface_shape_for(const helm_problem* p, int nrhs, IfaceCfg& tmp) {
+    if (const IfaceCfg* t = tuned_shape(p, nrhs)) return t;
+    if (iface_tc_cfg(p, nrhs, tmp)) return &tmp;
+    return nullptr;
+}
 
 // The autotuner of the interface-stage kernel: the first application with nrhs >= 2 RHS
 // times each candidate shape (RHS per block 2/4/8/16 up to nrhs, K staged or not) on
@@ -1122,6 +1141,9 @@ static helm_status tune_shape_t(helm_problem* p, int nrhs, cudaStream_t st) {
     const long long before = helm_launch_count();
     IfaceCfg best{};
     float best_ms = 1e30f;
+    // candidates: CUDA cores with 2..16 RHS per block, K staged or not; the tensor-core
+    // form with 16 or 32 RHS per CTA where it is allowed
+    std::vector<IfaceCfg> cands;
     for (int nr : {2, 4, 8, 16}) {
         if (nr > 2 * nrhs || (nr == 16 && sizeof(R) != 4)) continue;
         for (int staged : {1, 0}) {
@@ -1129,6 +1151,37 @@ static helm_status tune_shape_t(helm_problem* p, int nrhs, cudaStream_t st) {
             c.nr = nr;
             c.staged = staged;
             c.waves = 3;
+            cands.push_back(c);
+        }
+    }
+    IfaceCfg tcc;
+    const bool with_tc = sizeof(R) == 4 && iface_tc_cfg(p, nrhs, tcc);
+    for (const IfaceCfg& c : cands) {
+        if (launch_iface<R>(ia, (int)all.subs.size(), max_rows, p->max_Lb, st, &c) != cudaSuccess) {
+            (void)cudaGetLastError();
+            continue;
+        }
+        cudaEventRecord(e0, st);
+        for (int rep = 0; rep < 3; ++rep) launch_iface<R>(ia, (int)all.subs.size(), max_rows, p->max_Lb, st, &c);
+        cudaEventRecord(e1, st);
+        float ms = 0;
+        if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess &&
+            ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+    }
+    // the tensor-core form for the stages that fill the GPU (S, on which it is timed, is
+    // one of them), the best CUDA-core shape for the others
+    if (with_tc && best_ms < 1e30f)
+        for (int nb : {16, 32}) {
+            if (nb == 32 && nrhs < 32) continue;
+            const long long ctas = (long long)all.subs.size() * ((max_rows + 127) / 128) * ((nrhs + nb - 1) / nb);
+            if (ctas < (tcc.tc_min_ctas >= 0 ? (long long)tcc.tc_min_ctas : 2LL * p->num_sms)) continue;
+            IfaceCfg c = best;
+            c.tc = tcc.tc;
+            c.tc_nb = nb;
+            c.tc_min_ctas = tcc.tc_min_ctas;
             if (launch_iface<R>(ia, (int)all.subs.size(), max_rows, p->max_Lb, st, &c) != cudaSuccess) {
                 (void)cudaGetLastError();
                 continue;
@@ -1143,7 +1196,6 @@ static helm_status tune_shape_t(helm_problem* p, int nrhs, cudaStream_t st) {
                 best = c;
             }
         }
-    }
     uncount_launch(helm_launch_count() - before);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -1161,15 +1213,18 @@ static helm_status tune_shape(helm_problem* p, int nrhs, cudaStream_t st) {
 }
 
 extern "C" helm_status helm_iface_shape(const helm_problem* p, int nrhs, int* nr, int* staged, int* waves,
-                                        int* tuned) {
+                                        int* tensor, int* tensor_rhs, int* tuned) {
     if (!p) return arg_error("helm_iface_shape: NULL handle");
-    const IfaceCfg* c = tuned_shape(p, nrhs);
+    IfaceCfg tmp;
+    const IfaceCfg* c = iface_shape_for(p, nrhs, tmp);
     IfaceCfg d;
     d.nr = nrhs >= 4 ? 4 : nrhs >= 2 ? 2 : 1;
     if (!c) c = &d;
     if (nr) *nr = c->nr;
     if (staged) *staged = c->staged;
     if (waves) *waves = c->waves;
+    if (tensor) *tensor = c->tc;
+    if (tensor_rhs) *tensor_rhs = c->tc ? c->tc_nb : 0;
     if (tuned) *tuned = tuned_shape(p, nrhs) != nullptr;
     return HELM_OK;
 }
@@ -1207,7 +1262,8 @@ static helm_status run_stage_t(helm_problem* p, const PcWork& w, const PcCtx& cx
         double bytes = 0, flops = 0;
         if (p->prof_on) iface_accounting(p, sd, nrhs, sizeof(T), bytes, flops);
         prof_begin(p, HELM_K_TRACE, st);
-        cudaError_t e = launch_iface<R>(ia, (int)sd.subs.size(), max_rows, p->max_Lb, st, tuned_shape(p, nrhs));
+        IfaceCfg tmp;
+        cudaError_t e = launch_iface<R>(ia, (int)sd.subs.size(), max_rows, p->max_Lb, st, iface_shape_for(p, nrhs, tmp));
         prof_end(p, HELM_K_TRACE, bytes, st, flops);
         if (e != cudaSuccess) return cuda_status(e, "interface stage launch");
         return HELM_OK;

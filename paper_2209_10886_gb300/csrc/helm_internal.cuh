@@ -198,6 +198,10 @@ constexpr int IFACE_RB = 16;
 // the CTAs per SM the grid aims at when it spreads RHS blocks over CTAs
 struct IfaceCfg {
     int nr = 4, staged = 1, waves = 3;
+    // complex64 only: tc = 3 or 1 runs the stages of at least tc_min_ctas CTAs (-1: two per
+    // SM) as tensor-core MMAs (3xTF32 or TF32 operands, tc_iface_kernel) with tc_nb = 16 or
+    // 32 RHS per CTA, the smaller stages with the CUDA-core shape above; tc = 0: CUDA cores
+    int tc = 0, tc_nb = 16, tc_min_ctas = -1;
 };
 
 // one interface stage of a sweep run by the persistent sweep kernel (device table)
@@ -252,6 +256,7 @@ long long tc_layout_floats(int mx, int my, int MT, int split);   // floats of on
 cudaError_t launch_tc_layout(const SubDev* subtab, int nsub, int split, const float2* X, float* XT, cudaStream_t st);
 cudaError_t launch_tc_stage(const StageArgs<float>& a, const float* XT, int MT, int split, int nactive,
                             cudaStream_t st);
+cudaError_t launch_iface_tc(const IfaceArgs<float>& a, int nactive, int max_rows, int split, int nb, cudaStream_t st);
 cudaError_t launch_tc_basis(const StageArgs<float>& a, const float* XT, int MT, int split, int nsub, int ncols,
                             cudaStream_t st);
 // one interface stage; cfg = nullptr: the default shape (4, 2 or 1 RHS per block, staged

@@ -665,6 +665,22 @@ cudaError_t launch_iface(const IfaceArgs<R>& a, int nactive, int max_rows, int m
     if (nactive == 0 || a.nrhs == 0) return cudaSuccess;
     // default: blocks of 4 RHS (at 64 RHS on the 1023^2 workload, 16 measured 2x slower
     // when every block had its own CTA); the autotuner may pick another shape
+    if constexpr (sizeof(R) == 4)
+        if (cfg && cfg->tc) {
+            // the tensor-core form walks all boundary points of its rows in one CTA: only a
+            // stage with at least two of its CTAs per SM (by default) keeps every SM's tensor
+            // pipe busy
+            static int sms = 0;
+            if (sms == 0) {
+                int dev = 0;
+                if (cudaGetDevice(&dev) != cudaSuccess ||
+                    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+                    sms = 1;
+            }
+            const long long ctas = (long long)nactive * ((max_rows + 127) / 128) * ((a.nrhs + cfg->tc_nb - 1) / cfg->tc_nb);
+            if (ctas >= (cfg->tc_min_ctas >= 0 ? (long long)cfg->tc_min_ctas : 2LL * sms))
+                return launch_iface_tc(a, nactive, max_rows, cfg->tc, cfg->tc_nb, st);
+        }
     const int nr = cfg ? cfg->nr : (a.nrhs >= 4 ? 4 : a.nrhs >= 2 ? 2 : 1);
     const int staged_ok = cfg ? cfg->staged : 1;
     const int waves = cfg ? cfg->waves : 3;

@@ -631,6 +631,322 @@ cudaError_t tc_launch(const StageArgs<float>& a, const float* XT, int nunits, in
     return cudaGetLastError();
 }
 
+// ------------------------------------------------- interface stages, many RHS
+// One interface stage with NB right-hand sides per CTA as a complex GEMM on the tensor
+// cores: for the output rows (points of the masked sides) of one subdomain,
+//     D = K_rows (cin * G)       (K: Lb boundary points wide, G: incoming data, NB RHS)
+// then G_out = cb D + ca G_in + base - sub per row and RHS, as the CUDA-core form of the
+// stage computes it.  A CTA takes 128 rows (one M tile) and NB RHS, and walks the
+// boundary points in chunks of KC = 16: its four warps load the next chunk's K rows
+// (thread t: row t) and incoming data into registers, write the current one into a
+// double-buffered pair of operands (A: real and imaginary planes of K, B: [-Gi | Gr | Gi],
+// each split into TF32 hi and lo for SPLIT = 3, the same no-swizzle K-major core-matrix
+// layouts as the stage kernel) and one thread issues the chunk's MMAs, committed to the
+// buffer's mbarrier, while the warps move on.  The accumulator [Re D | Im D] (128 lanes
+// x 2 NB columns) is in tensor memory; warp w reads lanes 32w.. for the epilogue.  Waits
+// are bounded: on expiry the CTA records HELM_ERR_TIMEOUT, issues nothing more, waits
+// (bounded) for its MMAs and frees its tensor memory.
+template <int NB, int SPLIT>
+__global__ void __launch_bounds__(128, 1) tc_iface_kernel(IfaceArgs<float> a) {
+    using T = float2;
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ __align__(8) unsigned long long mma_bar[2], fin_bar;
+    __shared__ unsigned tmem_base;
+    __shared__ int abort_flag;
+
+    constexpr int KC = 16;                                  // boundary points per chunk
+    constexpr unsigned PLANE = 128u * KC * 4u;              // one plane of A (8 KB)
+    constexpr unsigned ABYTES = (SPLIT == 3 ? 4u : 2u) * PLANE;
+    constexpr unsigned KSA = 2048u;                         // K-adjacent core matrices of A
+    constexpr unsigned KSB = 48u * NB;                      // K-adjacent core matrices of B
+    constexpr unsigned BPART = (KC / 4) * KSB;              // B hi (and B lo after it)
+    constexpr unsigned BBYTES = (SPLIT == 3 ? 2u : 1u) * BPART;
+    constexpr int NCOLS = 2 * NB;                           // [Re D | Im D]
+    constexpr int TCOLS = NCOLS <= 32 ? 32 : NCOLS <= 64 ? 64 : 128;
+    constexpr unsigned IDESC = tf32_idesc(2 * NB);
+    constexpr int PPT = (4 * NB + 127) / 128;               // (point quad, RHS) pairs per thread
+
+    const int rhs0 = blockIdx.x * NB;
+    const int nr = min(NB, a.nrhs - rhs0);
+    const int row0 = blockIdx.y * 128;
+    const SubDev sd = a.subtab[a.subs[blockIdx.z]];
+    const int Lb = sd.Lb;
+    const int bo[4] = {sd.bo[0], sd.bo[1], sd.bo[2], sd.bo[3]};
+    const int tin[4] = {sd.tin[0], sd.tin[1], sd.tin[2], sd.tin[3]};
+    auto sel = [&](const int (&v)[4], int q) { return q == 0 ? v[0] : q == 1 ? v[1] : q == 2 ? v[2] : v[3]; };
+    auto len = [&](int q) { return q < 2 ? sd.my : sd.mx; };
+    auto on = [&](int q) { return ((a.mask >> q) & 1) && sel(bo, q) >= 0; };
+    int rcount = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        if (on(q)) rcount += len(q);
+    if (row0 >= rcount || nr <= 0) return;                  // uniform over the CTA
+    const int tid = threadIdx.x, warp = tid >> 5;
+
+    // this thread's output row: side srow, point pt (srow = -1 past the last row)
+    int srow = -1, pt = row0 + tid;
+    if (row0 + tid < rcount) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (srow < 0 && on(q)) {
+                if (pt < len(q)) srow = q;
+                else pt -= len(q);
+            }
+    }
+    const bool live = srow >= 0;
+    const T* Krow = a.K + sd.koff + (long long)(live ? sel(bo, srow) + pt : 0) * Lb;
+    const int nch = (Lb + KC - 1) / KC;
+
+    if (tid == 0) {
+        bar_init(&mma_bar[0], 1);
+        bar_init(&mma_bar[1], 1);
+        bar_init(&fin_bar, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(sm_addr(&tmem_base)),
+                     "r"(TCOLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    const unsigned sbase = sm_addr(smem_raw);
+    auto abuf = [&](int b) { return sbase + (unsigned)b * ABYTES; };
+    auto bbuf = [&](int b) { return sbase + 2u * ABYTES + (unsigned)b * BBYTES; };
+
+    // K of chunk c (row Krow, 16 points) and incoming data of the thread's (quad, RHS) pairs
+    auto load_k = [&](int c, T (&kv)[KC]) {
+#pragma unroll
+        for (int j = 0; j < KC; ++j) {
+            const int col = c * KC + j;
+            kv[j] = (live && col < Lb) ? Krow[col] : make_float2(0.f, 0.f);
+        }
+    };
+    auto load_g = [&](int c, T (&gv)[PPT][4], T (&cv)[PPT][4]) {
+#pragma unroll
+        for (int u = 0; u < PPT; ++u) {
+            const int pr = tid + 128 * u;
+            const int quad = pr / NB, k = pr - quad * NB;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int e = c * KC + 4 * quad + q;
+                T G = make_float2(0.f, 0.f), C = G;
+                if (pr < 4 * NB && k < nr && e < Lb) {
+                    int sd_ = 0;
+#pragma unroll
+                    for (int t = 1; t < 4; ++t)
+                        if (bo[t] >= 0 && e >= bo[t]) sd_ = t;
+                    const long long ti = sel(tin, sd_) + (e - sel(bo, sd_));
+                    const long long o = (long long)(rhs0 + k) * a.ntrace + ti;
+                    if (a.gin0) G = a.gin0[o];
+                    if (a.gin1) G = cadd(G, a.gin1[o]);
+                    C = a.tc[ti].cin;
+                }
+                gv[u][q] = G;
+                cv[u][q] = C;
+            }
+        }
+    };
+    // operands of one chunk into buffer b
+    auto store = [&](int b, const T (&kv)[KC], const T (&gv)[PPT][4], const T (&cv)[PPT][4]) {
+        const unsigned ar = abuf(b) + (unsigned)(tid >> 3) * 128u + (unsigned)(tid & 7) * 16u;
+#pragma unroll
+        for (int g4 = 0; g4 < KC / 4; ++g4) {
+            float xr[4], xi[4], hr[4], hi[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                xr[q] = kv[4 * g4 + q].x;
+                xi[q] = kv[4 * g4 + q].y;
+                hr[q] = tf32_round(xr[q]);
+                hi[q] = tf32_round(xi[q]);
+            }
+            const unsigned ad = ar + (unsigned)g4 * KSA;
+            st_shared_v4(ad, hr[0], hr[1], hr[2], hr[3]);
+            st_shared_v4(ad + PLANE, hi[0], hi[1], hi[2], hi[3]);
+            if (SPLIT == 3) {
+                st_shared_v4(ad + 2u * PLANE, tf32_round(xr[0] - hr[0]), tf32_round(xr[1] - hr[1]),
+                             tf32_round(xr[2] - hr[2]), tf32_round(xr[3] - hr[3]));
+                st_shared_v4(ad + 3u * PLANE, tf32_round(xi[0] - hi[0]), tf32_round(xi[1] - hi[1]),
+                             tf32_round(xi[2] - hi[2]), tf32_round(xi[3] - hi[3]));
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < PPT; ++u) {
+            const int pr = tid + 128 * u;
+            if (pr < 4 * NB) {
+                const int quad = pr / NB, k = pr - quad * NB;
+                float gr[4], gi[4], lr[4], li[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const T g = cmul(gv[u][q], cv[u][q]);
+                    gr[q] = tf32_round(g.x);
+                    gi[q] = tf32_round(g.y);
+                    lr[q] = tf32_round(g.x - gr[q]);
+                    li[q] = tf32_round(g.y - gi[q]);
+                }
+                auto row = [&](int n) {
+                    return bbuf(b) + (unsigned)quad * KSB + (unsigned)(n >> 3) * 128u + (unsigned)(n & 7) * 16u;
+                };
+                st_shared_v4(row(k), -gi[0], -gi[1], -gi[2], -gi[3]);
+                st_shared_v4(row(NB + k), gr[0], gr[1], gr[2], gr[3]);
+                st_shared_v4(row(2 * NB + k), gi[0], gi[1], gi[2], gi[3]);
+                if (SPLIT == 3) {
+                    st_shared_v4(BPART + row(k), -li[0], -li[1], -li[2], -li[3]);
+                    st_shared_v4(BPART + row(NB + k), lr[0], lr[1], lr[2], lr[3]);
+                    st_shared_v4(BPART + row(2 * NB + k), li[0], li[1], li[2], li[3]);
+                }
+            }
+        }
+    };
+    // the MMAs of chunk c from buffer b: per K step of 8 points, [Re D | Im D] +=
+    // Kr [Gr | Gi] + Ki [-Gi | Gr] (hi*hi, and hi*lo + lo*hi for SPLIT = 3)
+    auto issue = [&](int c, int b, unsigned tmem) {
+#pragma unroll
+        for (int ks = 0; ks < KC / 8; ++ks) {
+            const unsigned bb = bbuf(b) + (unsigned)ks * 2u * KSB;
+            const unsigned ar = abuf(b) + (unsigned)ks * 2u * KSA;
+            const unsigned long long b1 = smem_desc(bb + (unsigned)(NB / 8) * 128u, KSB, 128u);
+            const unsigned long long b2 = smem_desc(bb, KSB, 128u);
+            const unsigned long long dre = smem_desc(ar, KSA, 128u);
+            const unsigned long long dim = smem_desc(ar + PLANE, KSA, 128u);
+            mma_tf32(tmem, dre, b1, IDESC, (c > 0 || ks > 0) ? 1 : 0);
+            mma_tf32(tmem, dim, b2, IDESC, 1);
+            if (SPLIT == 3) {
+                const unsigned long long b1l = smem_desc(BPART + bb + (unsigned)(NB / 8) * 128u, KSB, 128u);
+                const unsigned long long b2l = smem_desc(BPART + bb, KSB, 128u);
+                mma_tf32(tmem, dre, b1l, IDESC, 1);
+                mma_tf32(tmem, dim, b2l, IDESC, 1);
+                mma_tf32(tmem, smem_desc(ar + 2u * PLANE, KSA, 128u), b1, IDESC, 1);
+                mma_tf32(tmem, smem_desc(ar + 3u * PLANE, KSA, 128u), b2, IDESC, 1);
+            }
+        }
+        mma_commit(&mma_bar[b]);
+    };
+
+    T k0[KC], k1[KC], g0[PPT][4], g1[PPT][4], c0[PPT][4], c1[PPT][4];
+    load_k(0, k0);                                          // K is immutable: before the wait
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const unsigned tmem = tmem_base;
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");    // incoming data, base and sub are ready
+    load_g(0, g0, c0);
+    bool issued = false;
+    // one chunk: prefetch chunk c + 1, wait until the MMAs of chunk c - 2 released the
+    // buffer, write chunk c, hand it to the MMA thread
+    auto step = [&](int c, T (&kc)[KC], T (&gc)[PPT][4], T (&cc)[PPT][4], T (&kn)[KC], T (&gn)[PPT][4],
+                    T (&cn)[PPT][4]) -> bool {
+        const int b = c & 1;
+        if (c + 1 < nch) {
+            load_k(c + 1, kn);
+            load_g(c + 1, gn, cn);
+        }
+        if (c >= 2 && !bar_wait(&mma_bar[b], (unsigned)(((c - 2) >> 1) & 1), TC_WAIT_LIMIT)) {
+            abort_flag = 1;
+            if (a.err) atomicExch(a.err, (int)HELM_ERR_TIMEOUT);
+        }
+        store(b, kc, gc, cc);
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        tc_fence_before();
+        __syncthreads();
+        if (abort_flag) return false;
+        if (tid == 0) {
+            tc_fence_after();
+            issue(c, b, tmem);
+            issued = true;
+        }
+        return true;
+    };
+    bool ok = true;
+    for (int c = 0; c < nch && ok; c += 2) {
+        ok = step(c, k0, g0, c0, k1, g1, c1);
+        if (ok && c + 1 < nch) ok = step(c + 1, k1, g1, c1, k0, g0, c0);
+    }
+    if (ok) {
+        // the last commit arrives when every MMA of the CTA has completed
+        if (!bar_wait(&mma_bar[(nch - 1) & 1], (unsigned)(((nch - 1) >> 1) & 1), TC_WAIT_LIMIT)) {
+            abort_flag = 1;
+            if (a.err) atomicExch(a.err, (int)HELM_ERR_TIMEOUT);
+        }
+    }
+    __syncthreads();
+    ok = abort_flag == 0;
+    if (!ok && tid == 0 && issued) {
+        mma_commit(&fin_bar);
+        bar_wait(&fin_bar, 0u, TC_WAIT_LIMIT);
+    }
+    tc_fence_after();
+    if (ok) {
+        // epilogue: row tid's accumulators for the block's RHS, then the outgoing data
+        float acc[NCOLS];
+        const unsigned trow = tmem + ((unsigned)(32 * warp) << 16);
+#pragma unroll
+        for (int cb = 0; cb < NCOLS; cb += 8) tmem_ld8(trow + (unsigned)cb, acc + cb);
+        tmem_wait_ld();
+        if (live) {
+            const long long ti = sel(tin, srow) + pt;
+            const TraceCoef<T> cf = a.tc[ti];
+            const long long to = (long long)(srow == 0 ? sd.tout[0] : srow == 1 ? sd.tout[1] : srow == 2 ? sd.tout[2]
+                                                                                                         : sd.tout[3]) + pt;
+#pragma unroll
+            for (int k0_ = 0; k0_ < NB; k0_ += 8) {
+                T gin[8], bs[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int k = k0_ + u;
+                    gin[u] = bs[u] = make_float2(0.f, 0.f);
+                    if (k < nr) {
+                        const long long oi = (long long)(rhs0 + k) * a.ntrace + ti;
+                        const long long o = (long long)(rhs0 + k) * a.ntrace + to;
+                        if (a.gin0) gin[u] = a.gin0[oi];
+                        if (a.gin1) gin[u] = cadd(gin[u], a.gin1[oi]);
+                        if (a.base) bs[u] = a.base[o];
+                        if (a.sub) bs[u] = csub(bs[u], a.sub[o]);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int k = k0_ + u;
+                    if (k < nr) {
+                        const T d = make_float2(acc[k], acc[NB + k]);
+                        const T out = cadd(cfma(cf.cb, d, cmul(cf.ca, gin[u])), bs[u]);
+                        const long long o = (long long)(rhs0 + k) * a.ntrace + to;
+                        a.dst[o] = out;
+                        if (a.dst2) a.dst2[o] = out;
+                    }
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TCOLS) : "memory");
+    }
+}
+
+template <int NB, int SPLIT>
+cudaError_t tc_iface_launch(const IfaceArgs<float>& a, int nactive, int max_rows, cudaStream_t st) {
+    constexpr size_t smem = 2 * ((SPLIT == 3 ? 4 : 2) * 8192 + (SPLIT == 3 ? 2 : 1) * 4 * 48 * NB);
+    cudaError_t e = cudaFuncSetAttribute(tc_iface_kernel<NB, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((a.nrhs + NB - 1) / NB, (max_rows + 127) / 128, nactive);
+    cfg.blockDim = dim3(128);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    count_launch();
+    return cudaLaunchKernelEx(&cfg, tc_iface_kernel<NB, SPLIT>, a);
+}
+
 }  // namespace
 
 int tc_tiles(int mx) { return mx <= 128 ? 1 : mx <= 256 ? 2 : 0; }
@@ -683,4 +999,14 @@ cudaError_t launch_tc_basis(const StageArgs<float>& a, const float* XT, int MT, 
     if (MT == 1) return tc_launch<1, 64, true, 1>(a, XT, nsub, (ncols + 63) / 64, st);
     if (MT == 2) return tc_launch<2, 32, true, 1>(a, XT, nsub, (ncols + 31) / 32, st);
     return cudaErrorInvalidValue;
+}
+
+// an interface stage with 16 or more RHS on the tensor cores (see tc_iface_kernel)
+cudaError_t launch_iface_tc(const IfaceArgs<float>& a, int nactive, int max_rows, int split, int nb,
+                            cudaStream_t st) {
+    if (nactive == 0 || a.nrhs == 0 || max_rows == 0) return cudaSuccess;
+    if (nactive > 65535) return cudaErrorInvalidValue;
+    if (split == 3) return nb >= 32 ? tc_iface_launch<32, 3>(a, nactive, max_rows, st)
+                                    : tc_iface_launch<16, 3>(a, nactive, max_rows, st);
+    return nb >= 32 ? tc_iface_launch<32, 1>(a, nactive, max_rows, st) : tc_iface_launch<16, 1>(a, nactive, max_rows, st);
 }

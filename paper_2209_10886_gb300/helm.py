@@ -42,7 +42,7 @@ class HelmOpts(ctypes.Structure):
 class HelmSetupOpts(ctypes.Structure):
     _fields_ = [("transmission", ctypes.c_int), ("tc_scale", ctypes.c_double),
                 ("boundary_operators", ctypes.c_int), ("tensor_cores", ctypes.c_int),
-                ("tc_min_rhs", ctypes.c_int), ("autotune", ctypes.c_int)]
+                ("tc_min_rhs", ctypes.c_int), ("autotune", ctypes.c_int), ("tc_iface_min_ctas", ctypes.c_int)]
 
 
 class HelmInfo(ctypes.Structure):
@@ -142,14 +142,14 @@ class Problem:
 
     def __init__(self, n_x, n_y, h, omega, m2, N1, N2, xcuts=None, ycuts=None,
                  transmission="optimized", tc_scale=1.0, boundary_operators=True, tensor_cores=True,
-                 tc_min_rhs=16, autotune=True):
+                 tc_min_rhs=16, autotune=True, tc_iface_min_ctas=-1):
         L = lib()
         if not (m2.is_cuda and m2.dtype == torch.float64 and m2.numel() == n_x * n_y):
             raise TypeError("m2 must be a float64 CUDA tensor with n_x*n_y values")
         m2 = m2.contiguous()
         tcm = {False: 0, True: 1, "3xtf32": 1, "tf32": 2}[tensor_cores]
         so = HelmSetupOpts(TRANSMISSION[transmission], float(tc_scale), int(bool(boundary_operators)), tcm,
-                           int(tc_min_rhs), int(bool(autotune)))
+                           int(tc_min_rhs), int(bool(autotune)), int(tc_iface_min_ctas))
         xc = (ctypes.c_int * (N1 + 1))(*[int(v) for v in xcuts]) if xcuts is not None else None
         yc = (ctypes.c_int * (N2 + 1))(*[int(v) for v in ycuts]) if ycuts is not None else None
         h_ = ctypes.c_void_p()
@@ -313,10 +313,11 @@ def iface_shape(problem: "Problem", nrhs: int) -> dict:
     """Launch shape of the interface-stage kernel for nrhs RHS (autotuned or the fixed rules)."""
     L = lib()
     L.helm_iface_shape.restype = ctypes.c_int
-    L.helm_iface_shape.argtypes = [_vp, ctypes.c_int] + [ctypes.POINTER(ctypes.c_int)] * 4
-    v = [ctypes.c_int() for _ in range(4)]
+    L.helm_iface_shape.argtypes = [_vp, ctypes.c_int] + [ctypes.POINTER(ctypes.c_int)] * 6
+    v = [ctypes.c_int() for _ in range(6)]
     _check(L.helm_iface_shape(problem._h, int(nrhs), *[ctypes.byref(x) for x in v]))
-    return {"rhs_per_block": v[0].value, "staged": v[1].value, "ctas_per_sm": v[2].value, "tuned": bool(v[3].value)}
+    return {"rhs_per_block": v[0].value, "staged": v[1].value, "ctas_per_sm": v[2].value,
+            "tensor_cores": v[3].value, "tensor_rhs_per_cta": v[4].value, "tuned": bool(v[5].value)}
 
 
 def profile(problem: "Problem", on: bool = True):

@@ -209,7 +209,8 @@ def test_nonoverlapping_bands_match_oracle(H, case):
 def test_autotuned_interface_shape(H, prec):
     """The first application with several RHS times the interface-stage launch shapes
     and keeps the fastest; the result equals the fixed-rule shape's up to the rounding
-    of the GEMV sums (their order depends on the RHS per block)."""
+    of the GEMV sums (their order depends on the RHS per block) or, with complex64
+    factors, that of the 3xTF32 tensor-core form the fixed rules pick at 20 RHS."""
     w = CASES["uneven_4x3"]()
     mk = lambda tune: H.Problem(w.n, w.n, w.h, w.omega, cuda(w.m2, torch.float64), w.N1, w.N2, w.xcuts, w.ycuts,
                                 autotune=tune).factor(prec)
@@ -219,7 +220,14 @@ def test_autotuned_interface_shape(H, prec):
     zb = pb.precond_apply(r).cpu().numpy()
     sa, sb = H.iface_shape(pa, 20), H.iface_shape(pb, 20)
     print(prec, "tuned", sa, "fixed", sb, "rel", rel(za, zb))
-    assert sa["tuned"] and not sb["tuned"] and sb["rhs_per_block"] == 4
+    assert sa["tuned"] and not sb["tuned"]
+    # fixed rules at 20 RHS: blocks of 4 RHS on the CUDA cores, and with complex64 factors
+    # the tensor-core form (16 RHS per CTA) for stages of at least two CTAs per SM (none
+    # on this small problem)
+    if prec == "c64":
+        assert sb["tensor_cores"] == 3 and sb["tensor_rhs_per_cta"] == 16 and sb["rhs_per_block"] == 4
+    else:
+        assert sb["tensor_cores"] == 0 and sb["rhs_per_block"] == 4
     assert not H.iface_shape(pa, 1)["tuned"]
     assert rel(za, zb) <= (1e-5 if prec == "c64" else 1e-12)
     pa.close(); pb.close()

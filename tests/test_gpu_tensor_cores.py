@@ -61,9 +61,10 @@ CASES = {
 }
 
 
-def make(H, w, tensor_cores=True, boundary_operators=True):
+def make(H, w, tensor_cores=True, boundary_operators=True, autotune=True, tc_iface_min_ctas=-1):
     p = H.Problem(w.n, w.n, w.h, w.omega, cuda(w.m2, torch.float64), w.N1, w.N2, w.xcuts, w.ycuts,
-                  boundary_operators=boundary_operators, tensor_cores=tensor_cores)
+                  boundary_operators=boundary_operators, tensor_cores=tensor_cores, autotune=autotune,
+                  tc_iface_min_ctas=tc_iface_min_ctas)
     return p.factor("c64")
 
 
@@ -155,5 +156,67 @@ def test_interface_krylov_with_tensor_core_stages(H):
     for k in (0, 19):
         ref = lu.solve(w.h ** 2 * f[k])
         print(f"uneven_4x3 TF32 interface Krylov rhs{k}: outer its {info[k][0]}, rel {rel(u[k], ref):.2e}")
+        assert info[k][1] <= 1e-9 and rel(u[k], ref) <= 1e-5
+    p.close()
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("nrhs", [16, 20, 40, 70])
+def test_tensor_core_interface_stages(H, case, nrhs):
+    """Interface stages as tcgen05 GEMMs (tc_iface_kernel: 128 output rows x 16 or 32 RHS
+    per CTA, boundary points in chunks of 16; ragged RHS blocks 20 = 16 + 4, 40 = 32 + 8,
+    70 = 32 + 32 + 6; 1..3 row tiles and ragged chunks) against the CUDA-core stages and
+    the oracle.  The fixed rules (no autotuner) pick the tensor cores from 16 RHS; every
+    stage takes them here (tc_iface_min_ctas = 1), however few CTAs it makes."""
+    w = CASES[case]()
+    a = make(H, w, autotune=False, tc_iface_min_ctas=1)
+    b = make(H, w, tensor_cores=False, autotune=False)
+    assert H.iface_shape(a, nrhs)["tensor_cores"] == 3
+    assert H.iface_shape(a, nrhs)["tensor_rhs_per_cta"] == (32 if nrhs >= 32 else 16)
+    assert H.iface_shape(b, nrhs)["tensor_cores"] == 0
+    assert H.iface_shape(a, 15)["tensor_cores"] == 0
+    sw = Sweeper(Decomposition(w.n, w.h, w.omega, w.m2, w.xcuts, w.ycuts))
+    r = W.random_complex((nrhs, w.N), 31)
+    for sched in ("BSP", "SP"):
+        za = a.precond_apply(cuda(r), sched=sched).cpu().numpy()
+        zb = b.precond_apply(cuda(r), sched=sched).cpu().numpy()
+        e_ab = rel(za, zb)
+        print(f"{case} nrhs {nrhs} {sched}: tensor-core vs CUDA-core interface stages rel {e_ab:.2e}")
+        assert e_ab <= TF32_PRECOND_TOL
+        for k in sorted({0, 15, 16, 31, 32, nrhs - 1} & set(range(nrhs))):
+            e = rel(za[k], sw.precondition(r[k], sched))
+            assert e <= TF32_PRECOND_TOL, (sched, k, e)
+    a.close(); b.close()
+
+
+def test_tensor_core_interface_stages_plain_tf32(H):
+    w = CASES["wide_2x2_131"]()
+    p = make(H, w, tensor_cores="tf32", autotune=False, tc_iface_min_ctas=1)
+    assert H.iface_shape(p, 40)["tensor_cores"] == 1
+    sw = Sweeper(Decomposition(w.n, w.h, w.omega, w.m2, w.xcuts, w.ycuts))
+    r = W.random_complex((40, w.N), 32)
+    z = p.precond_apply(cuda(r), sched="BSP").cpu().numpy()
+    for k in (0, 31, 32, 39):
+        e = rel(z[k], sw.precondition(r[k], "BSP"))
+        print(f"wide_2x2_131 plain TF32 interface stages rhs{k}: rel {e:.2e}")
+        assert e <= PLAIN_TF32_TOL
+    p.close()
+
+
+def test_interface_krylov_with_tensor_core_interface_stages(H):
+    """The interface FGMRES with every interface stage on the tensor cores (fixed rules,
+    20 RHS) still converges to the direct solution: the outer FGMRES keeps FP64."""
+    w = CASES["uneven_4x3"]()
+    p = make(H, w, autotune=False, tc_iface_min_ctas=1)
+    assert H.iface_shape(p, 20)["tensor_cores"] == 3
+    A = assemble_operator(w.n, w.h, w.omega, w.m2).tocsc()
+    f = W.random_complex((20, w.N), 33)
+    u, info, _ = p.solve(cuda(f), tol=1e-9, restart=30, maxit=300, inner_maxit=60, inner_tol=1e-3)
+    u = u.cpu().numpy()
+    lu = spla.splu(A)
+    for k in (0, 19):
+        ref = lu.solve(w.h ** 2 * f[k])
+        print(f"uneven_4x3 tensor-core interface stages, interface Krylov rhs{k}: outer its {info[k][0]}, "
+              f"rel {rel(u[k], ref):.2e}")
         assert info[k][1] <= 1e-9 and rel(u[k], ref) <= 1e-5
     p.close()
