@@ -84,6 +84,10 @@ def parse():
                     help="scale s of the optimized Robin parameter T_e = (i - 1) s sqrt(kappa_e pi / (2 h))")
     ap.add_argument("--graph", action="store_true",
                     help="replay every preconditioner application from a captured CUDA graph")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="fixed launch-shape rules for the interface stages (no autotuner)")
+    ap.add_argument("--tc-iface-min-ctas", type=int, default=-1,
+                    help="interface stages of fewer CTAs stay on the CUDA cores (-1: two per SM)")
     ap.add_argument("--tc-min-rhs", type=int, default=16,
                     help="stages with at least this many RHS run on the tensor cores (1: all)")
     return ap.parse_args()
@@ -113,7 +117,8 @@ def precond_only(args):
     w = W.workload(name, nrhs=args.nrhs) if args.nrhs else W.workload(name)
     m2 = torch.as_tensor(w.m2, dtype=torch.float64, device="cuda")
     p = Problem(w.n, w.n, w.h, w.omega, m2, w.N1, w.N2, w.xcuts, w.ycuts, tensor_cores=TC_MODES[args.tensor_cores],
-                tc_min_rhs=args.tc_min_rhs, tc_scale=args.tc_scale)
+                tc_min_rhs=args.tc_min_rhs, tc_scale=args.tc_scale, tc_iface_min_ctas=args.tc_iface_min_ctas,
+                autotune=not args.no_autotune)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     p.factor(args.prec)
@@ -405,7 +410,8 @@ def gpu_arm(args):
     m2 = torch.as_tensor(w.m2, dtype=torch.float64, device=dev)
     f = torch.as_tensor(w.f, dtype=torch.complex128, device=dev)
     p = Problem(w.n, w.n, w.h, w.omega, m2, w.N1, w.N2, w.xcuts, w.ycuts, tensor_cores=TC_MODES[args.tensor_cores],
-                tc_min_rhs=args.tc_min_rhs, tc_scale=args.tc_scale)
+                tc_min_rhs=args.tc_min_rhs, tc_scale=args.tc_scale, tc_iface_min_ctas=args.tc_iface_min_ctas,
+                autotune=not args.no_autotune)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     p.factor(args.prec)
@@ -569,7 +575,8 @@ def gpu_arm(args):
             "workload": w.description, "n": w.n, "N1": w.N1, "N2": w.N2, "nrhs": w.nrhs, "unknowns": w.N,
             "prec": args.prec, "sched": args.sched, "restart": args.restart, "tol": args.tol,
             "transmission": f"optimized, scale {args.tc_scale:g}", "iterations": iters[-1][0], "relres": relres,
-            "tensor_cores": args.tensor_cores, "tc_min_rhs": args.tc_min_rhs, "cuda_graph": args.graph,
+            "tensor_cores": args.tensor_cores, "tc_min_rhs": args.tc_min_rhs,
+            "tc_iface_min_ctas": args.tc_iface_min_ctas, "cuda_graph": args.graph,
             "interface_krylov": ({"inner_maxit": args.inner_maxit, "inner_restart": args.inner_restart,
                                   "inner_tol": args.inner_tol, "inner_steps_per_solve": inner_per_solve,
                                   "vectors": "c128" if (args.inner_fp64 or args.prec == "c128") else "c64",

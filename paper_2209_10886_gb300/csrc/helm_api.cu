@@ -217,6 +217,10 @@ struct helm_problem {
     size_t K_bytes = 0;
     size_t X_bytes = 0;
     float* d_XT = nullptr;           // complex64 factors in the tensor cores' operand layout (k_tc.cu)
+    float* d_tcpart = nullptr;       // partial sums of the tensor-core interface stages split over CTAs
+    long long tcpart_cap = 0;        // floats
+    int* d_tccnt = nullptr;          // their arrival counters (zero between launches)
+    int tccnt_cap = 0;
     size_t XT_bytes = 0;
     int tc_mt = 0;                   // largest tile count (128 nodes each) of that layout
     int tc_split = 0;                // 3: hi + lo TF32 pairs, 1: TF32 alone
@@ -786,6 +790,8 @@ extern "C" helm_status helm_destroy(helm_problem* p) {
     if (p->d_X) cudaFree(p->d_X);
     if (p->d_K) cudaFree(p->d_K);
     if (p->d_XT) cudaFree(p->d_XT);
+    if (p->d_tcpart) cudaFree(p->d_tcpart);
+    if (p->d_tccnt) cudaFree(p->d_tccnt);
     delete p;
     return HELM_OK;
 }
@@ -948,6 +954,17 @@ extern "C" helm_status precond_factor(helm_problem* p, helm_prec prec, void* str
         p->tc_split = split;
         e = launch_tc_layout(p->d_subtab, (int)p->subs.size(), split, (const float2*)p->d_X, p->d_XT, st);
         if (e != cudaSuccess) return cuda_status(e, "precond_factor: tensor-core layout");
+        if (!p->d_tcpart) {
+            // a split tensor-core interface stage makes fewer than 4 CTAs per SM, each with
+            // 128 rows x 2 x 32 partial sums; fewer than 2 tiles per SM are split
+            const long long cap = 4LL * p->num_sms * 128 * 64;
+            e = cudaMalloc(&p->d_tcpart, (size_t)cap * sizeof(float));
+            if (e == cudaSuccess) e = cudaMalloc(&p->d_tccnt, (size_t)4 * p->num_sms * sizeof(int));
+            if (e == cudaSuccess) e = cudaMemsetAsync(p->d_tccnt, 0, (size_t)4 * p->num_sms * sizeof(int), st);
+            if (e != cudaSuccess) return cuda_status(e, "precond_factor: allocating the interface-stage scratch");
+            p->tcpart_cap = cap;
+            p->tccnt_cap = 4 * p->num_sms;
+        }
     }
     {
         const helm_status ks = p->sopts.boundary_operators ? build_boundary_operators(p, st) : HELM_OK;
@@ -1126,6 +1143,8 @@ static helm_status tune_shape_t(helm_problem* p, int nrhs, cudaStream_t st) {
     ia.dst = (T*)p->d_trace[BUF_B];
     ia.sub = (const T*)p->d_trace[BUF_X];
     ia.err = p->d_err;
+    ia.part = p->d_tcpart; ia.part_cap = p->tcpart_cap;
+    ia.cnt = p->d_tccnt; ia.cnt_cap = p->tccnt_cap;
     int max_rows = 0;
     for (int id : all.subs) {
         const SubDev& d = p->subs[id].dev;
@@ -1250,6 +1269,8 @@ static helm_status run_stage_t(helm_problem* p, const PcWork& w, const PcCtx& cx
         ia.mask = sd.mask;
         ia.dst = B(sd.dst); ia.dst2 = B(sd.dst2); ia.base = B(sd.base); ia.sub = B(sd.sub);
         ia.err = p->d_err;
+        ia.part = p->d_tcpart; ia.part_cap = p->tcpart_cap;
+        ia.cnt = p->d_tccnt; ia.cnt_cap = p->tccnt_cap;
         // grid rows: the most output rows (points of the masked sides) of a subdomain
         int max_rows = 0;
         for (int id : sd.subs) {

@@ -188,6 +188,10 @@ template <typename R> struct IfaceArgs {
     T* dst; T* dst2; const T* base; const T* sub;
     void* bufs[3];             // sweep kernel: the interface buffers B, X, Y the stages name
     int* err;                  // HELM_ERR_TIMEOUT when a bounded wait expired
+    // tensor-core form split over the boundary points: partial accumulators (part_cap
+    // floats) and one arrival counter per output tile (cnt_cap, zero between launches)
+    float* part; long long part_cap;
+    int* cnt; int cnt_cap;
 };
 
 // output rows of one work item of an interface stage (host tables and kernels agree on it)
@@ -256,7 +260,8 @@ long long tc_layout_floats(int mx, int my, int MT, int split);   // floats of on
 cudaError_t launch_tc_layout(const SubDev* subtab, int nsub, int split, const float2* X, float* XT, cudaStream_t st);
 cudaError_t launch_tc_stage(const StageArgs<float>& a, const float* XT, int MT, int split, int nactive,
                             cudaStream_t st);
-cudaError_t launch_iface_tc(const IfaceArgs<float>& a, int nactive, int max_rows, int split, int nb, cudaStream_t st);
+cudaError_t launch_iface_tc(const IfaceArgs<float>& a, int nactive, int max_rows, int split, int nb, int min_ctas,
+                            int max_Lb, cudaStream_t st);
 cudaError_t launch_tc_basis(const StageArgs<float>& a, const float* XT, int MT, int split, int nsub, int ncols,
                             cudaStream_t st);
 // one interface stage; cfg = nullptr: the default shape (4, 2 or 1 RHS per block, staged

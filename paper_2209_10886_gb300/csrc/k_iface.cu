@@ -679,7 +679,7 @@ cudaError_t launch_iface(const IfaceArgs<R>& a, int nactive, int max_rows, int m
             }
             const long long ctas = (long long)nactive * ((max_rows + 127) / 128) * ((a.nrhs + cfg->tc_nb - 1) / cfg->tc_nb);
             if (ctas >= (cfg->tc_min_ctas >= 0 ? (long long)cfg->tc_min_ctas : 2LL * sms))
-                return launch_iface_tc(a, nactive, max_rows, cfg->tc, cfg->tc_nb, st);
+                return launch_iface_tc(a, nactive, max_rows, cfg->tc, cfg->tc_nb, 2 * sms, max_Lb, st);
         }
     const int nr = cfg ? cfg->nr : (a.nrhs >= 4 ? 4 : a.nrhs >= 2 ? 2 : 1);
     const int staged_ok = cfg ? cfg->staged : 1;

@@ -40,6 +40,8 @@
 // work, waits (bounded) for its own copies and MMAs and frees its tensor memory.
 #include "helm_internal.cuh"
 
+#include <algorithm>
+
 namespace {
 
 constexpr long long TC_WAIT_LIMIT = 2000000000LL;  // cycles (~1 s)
@@ -638,16 +640,17 @@ cudaError_t tc_launch(const StageArgs<float>& a, const float* XT, int nunits, in
 // then G_out = cb D + ca G_in + base - sub per row and RHS, as the CUDA-core form of the
 // stage computes it.  A CTA takes 128 rows (one M tile) and NB RHS, and walks the
 // boundary points in chunks of KC = 16: its four warps load the next chunk's K rows
-// (thread t: row t) and incoming data into registers, write the current one into a
-// double-buffered pair of operands (A: real and imaginary planes of K, B: [-Gi | Gr | Gi],
-// each split into TF32 hi and lo for SPLIT = 3, the same no-swizzle K-major core-matrix
-// layouts as the stage kernel) and one thread issues the chunk's MMAs, committed to the
-// buffer's mbarrier, while the warps move on.  The accumulator [Re D | Im D] (128 lanes
+// (coalesced: 16 lanes per row) and incoming data into registers, write the current one
+// into a double-buffered pair of operands (A: real and imaginary planes of K; B:
+// [-Gi | Gr | Gi]; each split into TF32 hi and lo for SPLIT = 3; no-swizzle K-major
+// core-matrix layouts as in the stage kernel, A's K groups padded by 16 bytes against
+// bank conflicts) and one thread issues the chunk's MMAs, committed to the buffer's
+// mbarrier, while the warps move on.  The accumulator [Re D | Im D] (128 lanes
 // x 2 NB columns) is in tensor memory; warp w reads lanes 32w.. for the epilogue.  Waits
 // are bounded: on expiry the CTA records HELM_ERR_TIMEOUT, issues nothing more, waits
 // (bounded) for its MMAs and frees its tensor memory.
 template <int NB, int SPLIT>
-__global__ void __launch_bounds__(128, 1) tc_iface_kernel(IfaceArgs<float> a) {
+__global__ void __launch_bounds__(128, 1) tc_iface_kernel(IfaceArgs<float> a, int S) {
     using T = float2;
     asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -656,9 +659,11 @@ __global__ void __launch_bounds__(128, 1) tc_iface_kernel(IfaceArgs<float> a) {
     __shared__ int abort_flag;
 
     constexpr int KC = 16;                                  // boundary points per chunk
-    constexpr unsigned PLANE = 128u * KC * 4u;              // one plane of A (8 KB)
+    // A: K-adjacent core matrices 2048 + 16 bytes apart, so that the 16 points of a row
+    // written by 16 lanes fall in 16 different banks
+    constexpr unsigned KSA = 2064u;
+    constexpr unsigned PLANE = (KC / 4) * KSA;              // one plane of A
     constexpr unsigned ABYTES = (SPLIT == 3 ? 4u : 2u) * PLANE;
-    constexpr unsigned KSA = 2048u;                         // K-adjacent core matrices of A
     constexpr unsigned KSB = 48u * NB;                      // K-adjacent core matrices of B
     constexpr unsigned BPART = (KC / 4) * KSB;              // B hi (and B lo after it)
     constexpr unsigned BBYTES = (SPLIT == 3 ? 2u : 1u) * BPART;
@@ -667,10 +672,12 @@ __global__ void __launch_bounds__(128, 1) tc_iface_kernel(IfaceArgs<float> a) {
     constexpr unsigned IDESC = tf32_idesc(2 * NB);
     constexpr int PPT = (4 * NB + 127) / 128;               // (point quad, RHS) pairs per thread
 
+
     const int rhs0 = blockIdx.x * NB;
     const int nr = min(NB, a.nrhs - rhs0);
     const int row0 = blockIdx.y * 128;
-    const SubDev sd = a.subtab[a.subs[blockIdx.z]];
+    const int slot = blockIdx.z / S, split = blockIdx.z - slot * S;   // S CTAs share one output tile
+    const SubDev sd = a.subtab[a.subs[slot]];
     const int Lb = sd.Lb;
     const int bo[4] = {sd.bo[0], sd.bo[1], sd.bo[2], sd.bo[3]};
     const int tin[4] = {sd.tin[0], sd.tin[1], sd.tin[2], sd.tin[3]};
@@ -695,8 +702,12 @@ __global__ void __launch_bounds__(128, 1) tc_iface_kernel(IfaceArgs<float> a) {
             }
     }
     const bool live = srow >= 0;
-    const T* Krow = a.K + sd.koff + (long long)(live ? sel(bo, srow) + pt : 0) * Lb;
-    const int nch = (Lb + KC - 1) / KC;
+    __shared__ long long rowoff[128];                       // element offset of each row of K (-1: none)
+    rowoff[tid] = live ? sd.koff + (long long)(sel(bo, srow) + pt) * Lb : -1LL;
+    // this CTA's chunks of boundary points: [cb0, cb1) of the tile's (Lb + KC - 1) / KC
+    const int nall = (Lb + KC - 1) / KC;
+    const int cb0 = (int)((long long)split * nall / S), cb1 = (int)((long long)(split + 1) * nall / S);
+    const int nch = cb1 - cb0;
 
     if (tid == 0) {
         bar_init(&mma_bar[0], 1);
@@ -714,23 +725,28 @@ __global__ void __launch_bounds__(128, 1) tc_iface_kernel(IfaceArgs<float> a) {
     const unsigned sbase = sm_addr(smem_raw);
     auto abuf = [&](int b) { return sbase + (unsigned)b * ABYTES; };
     auto bbuf = [&](int b) { return sbase + 2u * ABYTES + (unsigned)b * BBYTES; };
-
-    // K of chunk c (row Krow, 16 points) and incoming data of the thread's (quad, RHS) pairs
+    // K of chunk c for the warp's 32 rows, coalesced: load i takes row 32 w + r_i (lanes
+    // 0-15) and row 32 w + r_i + 4 (lanes 16-31), point lane % 16 of the chunk, with
+    // r_i = 8 (i / 4) + i % 4
+    const int lhalf = (tid & 31) >> 4, lcol = tid & 15;
+    auto krow_of = [&](int i) { return 32 * warp + 8 * (i >> 2) + (i & 3) + 4 * lhalf; };
     auto load_k = [&](int c, T (&kv)[KC]) {
+        const int col = (cb0 + c) * KC + lcol;
 #pragma unroll
-        for (int j = 0; j < KC; ++j) {
-            const int col = c * KC + j;
-            kv[j] = (live && col < Lb) ? Krow[col] : make_float2(0.f, 0.f);
+        for (int i = 0; i < KC; ++i) {
+            const long long ro = rowoff[krow_of(i)];
+            kv[i] = (ro >= 0 && col < Lb) ? a.K[ro + col] : make_float2(0.f, 0.f);
         }
     };
+    // incoming data of the thread's (quad, RHS) pairs: quad = pair % 4, RHS = pair / 4
     auto load_g = [&](int c, T (&gv)[PPT][4], T (&cv)[PPT][4]) {
 #pragma unroll
         for (int u = 0; u < PPT; ++u) {
             const int pr = tid + 128 * u;
-            const int quad = pr / NB, k = pr - quad * NB;
+            const int quad = pr & 3, k = pr >> 2;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const int e = c * KC + 4 * quad + q;
+                const int e = (cb0 + c) * KC + 4 * quad + q;
                 T G = make_float2(0.f, 0.f), C = G;
                 if (pr < 4 * NB && k < nr && e < Lb) {
                     int sd_ = 0;
@@ -748,34 +764,28 @@ __global__ void __launch_bounds__(128, 1) tc_iface_kernel(IfaceArgs<float> a) {
             }
         }
     };
-    // operands of one chunk into buffer b
+    // operands of chunk c into buffer b: A from the raw K rows (thread t: row t), B from
+    // the incoming data in registers
     auto store = [&](int b, const T (&kv)[KC], const T (&gv)[PPT][4], const T (&cv)[PPT][4]) {
-        const unsigned ar = abuf(b) + (unsigned)(tid >> 3) * 128u + (unsigned)(tid & 7) * 16u;
+        // element (row, point) of a plane at (point / 4) KSA + (row / 8) 128 + (row % 8) 16 + (point % 4) 4
+        const unsigned acol = abuf(b) + (unsigned)(lcol >> 2) * KSA + (unsigned)(lcol & 3) * 4u;
 #pragma unroll
-        for (int g4 = 0; g4 < KC / 4; ++g4) {
-            float xr[4], xi[4], hr[4], hi[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                xr[q] = kv[4 * g4 + q].x;
-                xi[q] = kv[4 * g4 + q].y;
-                hr[q] = tf32_round(xr[q]);
-                hi[q] = tf32_round(xi[q]);
-            }
-            const unsigned ad = ar + (unsigned)g4 * KSA;
-            st_shared_v4(ad, hr[0], hr[1], hr[2], hr[3]);
-            st_shared_v4(ad + PLANE, hi[0], hi[1], hi[2], hi[3]);
+        for (int i = 0; i < KC; ++i) {
+            const int row = krow_of(i);
+            const unsigned ad = acol + (unsigned)(row >> 3) * 128u + (unsigned)(row & 7) * 16u;
+            const float hr = tf32_round(kv[i].x), hi = tf32_round(kv[i].y);
+            asm volatile("st.shared.f32 [%0], %1;\n" ::"r"(ad), "f"(hr) : "memory");
+            asm volatile("st.shared.f32 [%0], %1;\n" ::"r"(ad + PLANE), "f"(hi) : "memory");
             if (SPLIT == 3) {
-                st_shared_v4(ad + 2u * PLANE, tf32_round(xr[0] - hr[0]), tf32_round(xr[1] - hr[1]),
-                             tf32_round(xr[2] - hr[2]), tf32_round(xr[3] - hr[3]));
-                st_shared_v4(ad + 3u * PLANE, tf32_round(xi[0] - hi[0]), tf32_round(xi[1] - hi[1]),
-                             tf32_round(xi[2] - hi[2]), tf32_round(xi[3] - hi[3]));
+                asm volatile("st.shared.f32 [%0], %1;\n" ::"r"(ad + 2u * PLANE), "f"(tf32_round(kv[i].x - hr)) : "memory");
+                asm volatile("st.shared.f32 [%0], %1;\n" ::"r"(ad + 3u * PLANE), "f"(tf32_round(kv[i].y - hi)) : "memory");
             }
         }
 #pragma unroll
         for (int u = 0; u < PPT; ++u) {
             const int pr = tid + 128 * u;
             if (pr < 4 * NB) {
-                const int quad = pr / NB, k = pr - quad * NB;
+                const int quad = pr & 3, k = pr >> 2;
                 float gr[4], gi[4], lr[4], li[4];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
@@ -825,16 +835,16 @@ __global__ void __launch_bounds__(128, 1) tc_iface_kernel(IfaceArgs<float> a) {
     };
 
     T k0[KC], k1[KC], g0[PPT][4], g1[PPT][4], c0[PPT][4], c1[PPT][4];
-    load_k(0, k0);                                          // K is immutable: before the wait
     tc_fence_before();
-    __syncthreads();
+    __syncthreads();                                        // row offsets, barriers, tensor memory
     tc_fence_after();
     const unsigned tmem = tmem_base;
+    if (nch > 0) load_k(0, k0);                             // K is immutable: before the wait
     asm volatile("griddepcontrol.wait;\n" ::: "memory");    // incoming data, base and sub are ready
-    load_g(0, g0, c0);
+    if (nch > 0) load_g(0, g0, c0);
     bool issued = false;
-    // one chunk: prefetch chunk c + 1, wait until the MMAs of chunk c - 2 released the
-    // buffer, write chunk c, hand it to the MMA thread
+    // one chunk: load chunk c + 1, wait until the MMAs of chunk c - 2 released buffer
+    // c % 2, write chunk c, hand it to the MMA thread
     auto step = [&](int c, T (&kc)[KC], T (&gc)[PPT][4], T (&cc)[PPT][4], T (&kn)[KC], T (&gn)[PPT][4],
                     T (&cn)[PPT][4]) -> bool {
         const int b = c & 1;
@@ -863,7 +873,7 @@ __global__ void __launch_bounds__(128, 1) tc_iface_kernel(IfaceArgs<float> a) {
         ok = step(c, k0, g0, c0, k1, g1, c1);
         if (ok && c + 1 < nch) ok = step(c + 1, k1, g1, c1, k0, g0, c0);
     }
-    if (ok) {
+    if (ok && nch > 0) {
         // the last commit arrives when every MMA of the CTA has completed
         if (!bar_wait(&mma_bar[(nch - 1) & 1], (unsigned)(((nch - 1) >> 1) & 1), TC_WAIT_LIMIT)) {
             abort_flag = 1;
@@ -877,14 +887,46 @@ __global__ void __launch_bounds__(128, 1) tc_iface_kernel(IfaceArgs<float> a) {
         bar_wait(&fin_bar, 0u, TC_WAIT_LIMIT);
     }
     tc_fence_after();
+    __shared__ int last_s;
     if (ok) {
-        // epilogue: row tid's accumulators for the block's RHS, then the outgoing data
+        // row tid's accumulators for the block's RHS (none: this CTA had no chunk)
         float acc[NCOLS];
         const unsigned trow = tmem + ((unsigned)(32 * warp) << 16);
+        if (nch > 0) {
 #pragma unroll
-        for (int cb = 0; cb < NCOLS; cb += 8) tmem_ld8(trow + (unsigned)cb, acc + cb);
-        tmem_wait_ld();
-        if (live) {
+            for (int cb = 0; cb < NCOLS; cb += 8) tmem_ld8(trow + (unsigned)cb, acc + cb);
+            tmem_wait_ld();
+        } else {
+#pragma unroll
+            for (int cc = 0; cc < NCOLS; ++cc) acc[cc] = 0.f;
+        }
+        bool fin = true;
+        if (S > 1) {
+            // split tile: every CTA stores its partial sums; the last to arrive adds the S
+            // partials in split order (the same sums whichever CTA is last) and finishes
+            const long long unit = ((long long)slot * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+            float* pp = a.part + unit * S * (128LL * NCOLS);
+#pragma unroll
+            for (int cc = 0; cc < NCOLS; ++cc) pp[((long long)split * NCOLS + cc) * 128 + tid] = acc[cc];
+            __threadfence();
+            __syncthreads();
+            if (tid == 0) {
+                const int old = atomicAdd(a.cnt + unit, 1);
+                last_s = old == S - 1;
+                if (old == S - 1) a.cnt[unit] = 0;          // ready for the next launch
+            }
+            __syncthreads();
+            fin = last_s != 0;
+            if (fin) {
+                __threadfence();
+#pragma unroll
+                for (int cc = 0; cc < NCOLS; ++cc) acc[cc] = 0.f;
+                for (int sp = 0; sp < S; ++sp)
+#pragma unroll
+                    for (int cc = 0; cc < NCOLS; ++cc) acc[cc] += __ldcg(pp + ((long long)sp * NCOLS + cc) * 128 + tid);
+            }
+        }
+        if (fin && live) {
             const long long ti = sel(tin, srow) + pt;
             const TraceCoef<T> cf = a.tc[ti];
             const long long to = (long long)(srow == 0 ? sd.tout[0] : srow == 1 ? sd.tout[1] : srow == 2 ? sd.tout[2]
@@ -928,13 +970,13 @@ __global__ void __launch_bounds__(128, 1) tc_iface_kernel(IfaceArgs<float> a) {
 }
 
 template <int NB, int SPLIT>
-cudaError_t tc_iface_launch(const IfaceArgs<float>& a, int nactive, int max_rows, cudaStream_t st) {
-    constexpr size_t smem = 2 * ((SPLIT == 3 ? 4 : 2) * 8192 + (SPLIT == 3 ? 2 : 1) * 4 * 48 * NB);
+cudaError_t tc_iface_launch(const IfaceArgs<float>& a, int nactive, int max_rows, int S, cudaStream_t st) {
+    constexpr size_t smem = 2 * ((SPLIT == 3 ? 4 : 2) * 4 * 2064 + (SPLIT == 3 ? 2 : 1) * 4 * 48 * NB);
     cudaError_t e = cudaFuncSetAttribute(tc_iface_kernel<NB, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((a.nrhs + NB - 1) / NB, (max_rows + 127) / 128, nactive);
+    cfg.gridDim = dim3((a.nrhs + NB - 1) / NB, (max_rows + 127) / 128, nactive * S);
     cfg.blockDim = dim3(128);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
@@ -944,7 +986,7 @@ cudaError_t tc_iface_launch(const IfaceArgs<float>& a, int nactive, int max_rows
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     count_launch();
-    return cudaLaunchKernelEx(&cfg, tc_iface_kernel<NB, SPLIT>, a);
+    return cudaLaunchKernelEx(&cfg, tc_iface_kernel<NB, SPLIT>, a, S);
 }
 
 }  // namespace
@@ -1001,12 +1043,22 @@ cudaError_t launch_tc_basis(const StageArgs<float>& a, const float* XT, int MT, 
     return cudaErrorInvalidValue;
 }
 
-// an interface stage with 16 or more RHS on the tensor cores (see tc_iface_kernel)
-cudaError_t launch_iface_tc(const IfaceArgs<float>& a, int nactive, int max_rows, int split, int nb,
-                            cudaStream_t st) {
+// an interface stage with 16 or more RHS on the tensor cores (see tc_iface_kernel); a
+// stage of fewer than 2 * min_ctas output tiles splits each tile's boundary points over
+// up to 8 CTAs (when the partial-sum scratch holds them) so that it makes about that many
+cudaError_t launch_iface_tc(const IfaceArgs<float>& a, int nactive, int max_rows, int split, int nb, int min_ctas,
+                            int max_Lb, cudaStream_t st) {
     if (nactive == 0 || a.nrhs == 0 || max_rows == 0) return cudaSuccess;
-    if (nactive > 65535) return cudaErrorInvalidValue;
-    if (split == 3) return nb >= 32 ? tc_iface_launch<32, 3>(a, nactive, max_rows, st)
-                                    : tc_iface_launch<16, 3>(a, nactive, max_rows, st);
-    return nb >= 32 ? tc_iface_launch<32, 1>(a, nactive, max_rows, st) : tc_iface_launch<16, 1>(a, nactive, max_rows, st);
+    const long long tiles = (long long)nactive * ((max_rows + 127) / 128) * ((a.nrhs + nb - 1) / nb);
+    int S = 1;
+    if (a.part && a.cnt && tiles < min_ctas) {
+        S = (int)std::min<long long>(8, (min_ctas + tiles - 1) / tiles);
+        S = std::min(S, std::max(1, (max_Lb + 15) / 16));
+        while (S > 1 && (tiles > a.cnt_cap || tiles * S * 128LL * 2 * (nb >= 32 ? 32 : 16) > a.part_cap)) --S;
+    }
+    if ((long long)nactive * S > 65535) return cudaErrorInvalidValue;
+    if (split == 3) return nb >= 32 ? tc_iface_launch<32, 3>(a, nactive, max_rows, S, st)
+                                    : tc_iface_launch<16, 3>(a, nactive, max_rows, S, st);
+    return nb >= 32 ? tc_iface_launch<32, 1>(a, nactive, max_rows, S, st)
+                    : tc_iface_launch<16, 1>(a, nactive, max_rows, S, st);
 }
