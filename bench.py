@@ -41,7 +41,7 @@ WORKLOAD = "plain_mixed"
 # once the source changes.  k_iface.cu: mean over 36 consecutive iface_kernel launches
 # of the bench (sweep, residual and S stages), caches left warm (--cache-control none);
 # profiles/iface_kernel_plain_mixed_interface_krylov.md gives the command.
-NCU_TRAFFIC = {("k_iface.cu", "72ffc2c2d53c76b6"): 9.380e6}
+NCU_TRAFFIC = {("k_iface.cu", "68a2ba5c6ef1dc72"): 9.380e6}
 FP64_PEAK_TFLOPS = 1.25
 
 
