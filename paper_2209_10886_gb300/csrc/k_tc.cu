@@ -646,8 +646,11 @@ cudaError_t tc_launch(const StageArgs<float>& a, const float* XT, int nunits, in
 // core-matrix layouts as in the stage kernel, A's K groups padded by 16 bytes against
 // bank conflicts) and one thread issues the chunk's MMAs, committed to the buffer's
 // mbarrier, while the warps move on.  The accumulator [Re D | Im D] (128 lanes
-// x 2 NB columns) is in tensor memory; warp w reads lanes 32w.. for the epilogue.  Waits
-// are bounded: on expiry the CTA records HELM_ERR_TIMEOUT, issues nothing more, waits
+// x 2 NB columns) is in tensor memory; warp w reads lanes 32w.. for the epilogue.  With
+// S > 1 a tile's chunks are split over S CTAs: each stores its partial sums, and the last
+// to arrive (one counter per tile, reset by that CTA) adds the S partials in split order
+// and finishes the tile, so the sums do not depend on which CTA ends last.  Waits are
+// bounded: on expiry the CTA records HELM_ERR_TIMEOUT, issues nothing more, waits
 // (bounded) for its MMAs and frees its tensor memory.
 template <int NB, int SPLIT>
 __global__ void __launch_bounds__(128, 1) tc_iface_kernel(IfaceArgs<float> a, int S) {
@@ -1044,8 +1047,8 @@ cudaError_t launch_tc_basis(const StageArgs<float>& a, const float* XT, int MT, 
 }
 
 // an interface stage with 16 or more RHS on the tensor cores (see tc_iface_kernel); a
-// stage of fewer than 2 * min_ctas output tiles splits each tile's boundary points over
-// up to 8 CTAs (when the partial-sum scratch holds them) so that it makes about that many
+// stage of fewer than min_ctas output tiles splits each tile's boundary points over up
+// to 8 CTAs (when the partial-sum scratch holds them) so that it makes about that many
 cudaError_t launch_iface_tc(const IfaceArgs<float>& a, int nactive, int max_rows, int split, int nb, int min_ctas,
                             int max_Lb, cudaStream_t st) {
     if (nactive == 0 || a.nrhs == 0 || max_rows == 0) return cudaSuccess;
