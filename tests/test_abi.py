@@ -60,3 +60,37 @@ def test_invalid_arguments_are_rejected_without_gpu(L):
     assert b"N1" in L.helm_last_error()
     assert L.helm_setup(0, 5, 0.1, 1.0, None, 1, 1, None, None, None, ctypes.byref(ctypes.c_void_p())) == 1
     assert L.helm_destroy(None) == 0
+
+
+def _header_struct_fields(name):
+    """Field names of the typedef struct `name` in include/helm.h, in order."""
+    import re
+    from paper_2209_10886_gb300 import helm
+    txt = re.sub(r"/\*.*?\*/", "", open(helm.HEADER_PATH).read(), flags=re.S)
+    body = re.search(r"typedef\s+struct\s*\{([^}]*)\}\s*" + name + r"\s*;", txt).group(1)
+    fields = []
+    for decl in filter(None, (d.strip() for d in body.split(";"))):
+        # "int a, b" / "double* hist" / "int x[4]": the identifier ending each declarator
+        fields += [re.findall(r"(\w+)\s*$", part.split("[")[0])[0] for part in decl.split(",")]
+    return fields
+
+
+@pytest.mark.parametrize("cname,pyname", [("helm_setup_opts", "HelmSetupOpts"), ("helm_opts", "HelmOpts")])
+def test_binding_structs_follow_the_header(L, cname, pyname):
+    """The ctypes structures the binding passes across the ABI have the header's fields
+    in the header's order."""
+    from paper_2209_10886_gb300 import helm
+    py = [f[0] for f in getattr(helm, pyname)._fields_]
+    assert py == _header_struct_fields(cname)
+
+
+def test_shape_query_rejects_a_null_handle_without_gpu(L):
+    """helm_iface_shape through the binding (all eight arguments) reports HELM_ERR_ARG
+    for a NULL handle."""
+    from paper_2209_10886_gb300 import helm
+
+    class NoProblem:
+        _h = None
+    with pytest.raises(helm.HelmError) as e:
+        helm.iface_shape(NoProblem(), 4)
+    assert e.value.status == 1 and "NULL" in str(e.value)
