@@ -547,8 +547,14 @@ def gpu_arm(args):
         st_ = classes[dom]
         bw = st_[2] / (st_[1] / 1e3) / 1e9
         names = {"trace": "iface_kernel (boundary-operator GEMV + transmission)", "matvec": "matvec_kernel"}
+        tc_form = helm.iface_shape(p, w.nrhs)["tensor_cores"] != 0
+        if tc_form:
+            names["trace"] = ("iface_kernel (CUDA-core GEMV, the smaller stages) + tc_iface_kernel "
+                              "(tcgen05 GEMM, the stages that fill the GPU)")
+        # the ncu traffic figure belongs to the 1-RHS default workload it was captured on
+        same_capture = dom == "trace" and wname == WORKLOAD and w.nrhs == 1 and not tc_form
         roofline = {"bound": "hbm", "achieved": bw, "peak": peak, "unit": "GB/s", "frac": bw / peak,
-                    "traffic": NCU_TRAFFIC.get(kernel_hash("k_iface.cu")) if dom == "trace" else None,
+                    "traffic": NCU_TRAFFIC.get(kernel_hash("k_iface.cu")) if same_capture else None,
                     "algorithmic_bytes_per_launch": st_[2] / max(st_[0], 1),
                     "kernel": names.get(dom, dom), "launches": st_[0],
                     "peak_source": f"hbm_gbs of {peak_src}"}
