@@ -137,7 +137,13 @@ class Problem:
 
     ``m2``: squared slowness (float64, n_x*n_y values, CUDA).  ``xcuts`` /
     ``ycuts``: node offsets of the subdomain columns / rows (length N1+1 /
-    N2+1) or None for an even split.
+    N2+1) or None for an even split.  The remaining keywords are the fields of
+    ``helm_setup_opts``: ``transmission`` ("optimized" or "impedance") and
+    ``tc_scale``; ``boundary_operators``; ``tensor_cores`` (True / "3xtf32",
+    "tf32", False) with ``tc_min_rhs``; ``autotune`` (time the interface-stage
+    shapes at the first application per RHS count); ``tc_iface_min_ctas``
+    (interface stages of fewer CTAs keep the CUDA-core form when the tensor-core
+    form is chosen; -1: two per SM).
     """
 
     def __init__(self, n_x, n_y, h, omega, m2, N1, N2, xcuts=None, ycuts=None,
