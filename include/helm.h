@@ -40,7 +40,8 @@
  *   returned and helm_last_error() describes it.  HELM_ERR_ARG for invalid
  *   arguments, HELM_ERR_STATE for calls in the wrong order, HELM_ERR_OOM when
  *   a device allocation fails, HELM_ERR_CUDA for any other CUDA error,
- *   HELM_ERR_TIMEOUT when a bounded device-side wait gave up.
+ *   HELM_ERR_TIMEOUT when a bounded device-side wait gave up (the work of that
+ *   call is incomplete; call precond_factor again before reusing the handle).
  * * Threads: a handle must not be used from two host threads at once.
  */
 #ifndef HELM_H

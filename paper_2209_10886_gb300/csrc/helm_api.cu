@@ -960,11 +960,14 @@ extern "C" helm_status precond_factor(helm_problem* p, helm_prec prec, void* str
             const long long cap = 4LL * p->num_sms * 128 * 64;
             e = cudaMalloc(&p->d_tcpart, (size_t)cap * sizeof(float));
             if (e == cudaSuccess) e = cudaMalloc(&p->d_tccnt, (size_t)4 * p->num_sms * sizeof(int));
-            if (e == cudaSuccess) e = cudaMemsetAsync(p->d_tccnt, 0, (size_t)4 * p->num_sms * sizeof(int), st);
             if (e != cudaSuccess) return cuda_status(e, "precond_factor: allocating the interface-stage scratch");
             p->tcpart_cap = cap;
             p->tccnt_cap = 4 * p->num_sms;
         }
+        // the arrival counters start at zero; each factorisation resets them (after a
+        // HELM_ERR_TIMEOUT a split tile may have left its counter short of S)
+        e = cudaMemsetAsync(p->d_tccnt, 0, (size_t)p->tccnt_cap * sizeof(int), st);
+        if (e != cudaSuccess) return cuda_status(e, "precond_factor: resetting the interface-stage counters");
     }
     {
         const helm_status ks = p->sopts.boundary_operators ? build_boundary_operators(p, st) : HELM_OK;
