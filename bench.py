@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--no-fp64-form", action="store_true", help="skip the all-FP64 comparison solve")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=2, help="oracle FGMRES iterations per CPU sample")
+    ap.add_argument("--cpu-pool", type=int, default=-1,
+                    help="worker processes of the all-cores oracle sample (-1: every host core, 0: skip it)")
     ap.add_argument("--mode", default="solve", choices=["solve", "precond", "schedules"],
                     help="precond: factor once, then time --steps preconditioner applications only "
                          "(a small, fixed launch sequence for profilers); schedules: SP vs BSP on 5 x N2 "
@@ -313,10 +315,15 @@ from oracle import Decomposition, Sweeper, assemble_operator, fgmres
 w = W.workload({workload!r})
 A = assemble_operator(w.n, w.h, w.omega, w.m2)
 dec = Decomposition(w.n, w.h, w.omega, w.m2, w.xcuts, w.ycuts)
-sw = Sweeper(dec)
+P = {pool}
 t0 = time.perf_counter()
-for i in dec.subdomains:
-    dec.local_solver(i)
+if P > 1:
+    from oracle.parallel import PoolSweeper
+    sw = PoolSweeper(dec, (w.n, w.h, w.omega, w.m2, w.xcuts, w.ycuts), processes=P)
+else:
+    sw = Sweeper(dec)
+    for i in dec.subdomains:
+        dec.local_solver(i)
 t_factor = time.perf_counter() - t0
 b = w.h ** 2 * w.f[0]
 times = []
@@ -326,6 +333,8 @@ for rep in range({reps}):
                        restart={restart}, maxit={iters})
     times.append((time.perf_counter() - t0) / it)
 print(json.dumps(dict(t_factor=t_factor, t_iter=times, iters=it)))
+if P > 1:
+    sw.close()
 """
 
 
@@ -340,14 +349,17 @@ def oracle_iterations(sched, restart):
         return None, None
 
 
-def run_oracle_sample(sched, restart, iters, reps):
+def run_oracle_sample(sched, restart, iters, reps, pool=1, timeout=1800):
+    """Time the oracle's FGMRES on the bench workload in a CPU-only child process:
+    one thread (pool = 1), or its local solves spread over `pool` worker processes
+    (oracle.parallel, one thread each)."""
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[k] = "1"
     env["CUDA_VISIBLE_DEVICES"] = ""
     code = ORACLE_SAMPLE.format(root=ROOT, workload=WORKLOAD, sched=sched, restart=max(restart, iters),
-                                iters=iters, reps=reps)
-    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=1800)
+                                iters=iters, reps=reps, pool=int(pool))
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=timeout)
     if r.returncode != 0:
         raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
     return json.loads(r.stdout.strip().splitlines()[-1])
@@ -573,6 +585,23 @@ def gpu_arm(args):
                              f"{t_iter:.3f} s per iteration x {ni} iterations ({src})"}
         except Exception as e:  # the baseline must not hide the GPU line
             cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {e}"[:300]}
+    cpu_pool = None
+    ncores = len(os.sched_getaffinity(0))
+    npool = ncores if args.cpu_pool < 0 else args.cpu_pool
+    if cpu is not None and cpu.get("value") and npool >= 2:
+        # the all-cores mode: the same oracle with its local solves over npool processes
+        try:
+            res = run_oracle_sample(args.sched, ORACLE_RESTART, args.cpu_iters, 1, pool=npool, timeout=300)
+            t_iter = res["t_iter"][-1]
+            ni, src = oracle_iterations(args.sched, ORACLE_RESTART)
+            ni = ni or iters[-1][0]
+            cpu_pool = {"value": w.N * w.nrhs / (t_iter * ni), "unit": UNIT, "cores": npool, "kind": "oracle",
+                        "sample": f"{args.cpu_iters} oracle FGMRES iterations, local solves over {npool} worker "
+                                  f"processes of one thread (oracle.parallel; subdomain i on worker i mod "
+                                  f"{npool}): {t_iter:.3f} s per iteration x {ni} iterations"}
+        except Exception as e:
+            cpu_pool = {"value": None, "unit": UNIT, "cores": npool, "kind": "oracle",
+                        "sample": f"failed: {e}"[:300]}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -612,6 +641,7 @@ def gpu_arm(args):
                 "d2h_bytes_per_step": int(f.numel() * 16)},
         "gpu_launches": launches,
         "cpu_baseline": cpu,
+        "cpu_baseline_all_cores": cpu_pool,
     }
     print(json.dumps(line), flush=True)
     p.close()
