@@ -20,6 +20,8 @@ Plain complex128 NumPy/SciPy code, written for readability, not speed:
 * :mod:`oracle.krylov` - restarted flexible GMRES (right preconditioning,
   modified Gram-Schmidt, dense least squares on the Hessenberg matrix).
 * :mod:`oracle.adjoint` - source-receiver misfit and its adjoint-state gradient.
+* :mod:`oracle.parallel` - the same sweeps with the local solves of a stage run
+  in worker processes (the all-cores CPU baseline).
 
 Every function states the passage it follows.  Readings of passages where the
 paper is silent or ambiguous are listed in the project's design notes and
