@@ -44,7 +44,16 @@ import numpy as np
 import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
+from . import habc
 from .discretization import ghost_factor
+
+
+def ghost_matrix(B):
+    """``(I - B)^{-1} (I + B)``: the ghost values ``u_g = C u_p`` of one side when its
+    condition ``(u_g - u_p)/h - T (u_g + u_p)/2 = 0`` has a matrix ``B = T h / 2``
+    (the scalar :func:`ghost_factor` along the side's points when B is diagonal)."""
+    Id = np.eye(B.shape[0], dtype=np.complex128)
+    return np.linalg.solve(Id - B, Id + B)
 
 # sides of a subdomain, named by the direction of the neighbour
 WEST, EAST, SOUTH, NORTH = "W", "E", "S", "N"
@@ -69,9 +78,11 @@ class Decomposition:
     owns 0-based x-nodes ``xcuts[i1-1] .. xcuts[i1]-1``.
     """
 
-    def __init__(self, n, h, omega, m2, xcuts, ycuts, transmission="optimized", tc_scale=1.0):
+    def __init__(self, n, h, omega, m2, xcuts, ycuts, transmission="optimized", tc_scale=1.0,
+                 n_pade=8, phi=np.pi / 3):
         self.n, self.h, self.omega = n, h, omega
         self.transmission, self.tc_scale = transmission, tc_scale
+        self.n_pade, self.phi = n_pade, phi         # transmission = "habc" (oracle.habc)
         self.m2 = np.asarray(m2, dtype=np.float64).reshape(n, n)   # [b, a]
         self.xcuts = [int(v) for v in xcuts]
         self.ycuts = [int(v) for v in ycuts]
@@ -140,6 +151,9 @@ class Decomposition:
             p_local = (bp - y0) * mx + (xs - x0)
             mp, mq = self.m2[bp, xs], self.m2[bq, xs]
         kappa_e = self.omega * np.sqrt(0.5 * (mp + mq))
+        if self.transmission == "habc":
+            # beta_e = T h / 2 as the side's dense matrix (oracle.habc)
+            return p_local, 0.5 * self.h * habc.side_operator(kappa_e, self.h, self.n_pade, self.phi)
         beta_e = 0.5 * self.h * self.transmission_operator(kappa_e)
         return p_local, beta_e
 
@@ -190,16 +204,25 @@ class Decomposition:
         if y1 == n:
             diag[-1, :] -= c_outer[-1, :]
         diag = diag.reshape(-1)
-        # interface sides: ghost factor with the edge's kappa_e
+        # interface sides: ghost factor with the edge's kappa_e (a dense block for the HABC)
+        blocks = []
         for j in self.neighbours(i):
             p_local, beta_e = self._edges[(i, j)]
-            np.add.at(diag, p_local, -ghost_factor(beta_e))
+            if np.ndim(beta_e) == 2:
+                blocks.append((p_local, ghost_matrix(beta_e)))
+            else:
+                np.add.at(diag, p_local, -ghost_factor(beta_e))
         M = mx * my
         la = np.tile(np.arange(mx), my)
         east = np.where(la[:-1] < mx - 1, -1.0, 0.0)
         north = -np.ones(M - mx)
         A = sp.diags([diag, east, east, north, north], [0, 1, -1, mx, -mx], shape=(M, M),
                      format="csc", dtype=np.complex128)
+        for p_local, C in blocks:
+            rows = np.repeat(p_local, len(p_local))
+            cols = np.tile(p_local, len(p_local))
+            A = A - sp.csc_matrix((C.reshape(-1), (rows, cols)), shape=(M, M))
+        A = A.tocsc()
         self._mat[i] = A
         return A
 
@@ -229,7 +252,10 @@ class Decomposition:
         rhs = np.zeros(M, dtype=np.complex128) if source is None else np.array(source, dtype=np.complex128)
         for j, G in incoming.items():
             p_local, beta_e = self._edges[(i, j)]
-            np.add.at(rhs, p_local, G / (1.0 - beta_e))
+            if np.ndim(beta_e) == 2:
+                np.add.at(rhs, p_local, np.linalg.solve(np.eye(len(p_local)) - beta_e, G))
+            else:
+                np.add.at(rhs, p_local, G / (1.0 - beta_e))
         return self.local_solver(i).solve(rhs)
 
     def outgoing(self, i, j, u_local, G_in):
@@ -237,6 +263,14 @@ class Decomposition:
         (Eq. subPbm right-hand side ``(-d_{n_{i,j}} - T) u_i``), scaled form:
         ``-((1 + beta_e) G_in + 4 beta_e u_p)/(1 - beta_e)``."""
         p_local, beta_e = self._edges[(i, j)]
+        if np.ndim(beta_e) == 2:
+            # the same relation with the side matrix B = T h / 2: the ghost values
+            # u_g = (I - B)^{-1} ((I + B) u_p + G_in), mid-edge mean m = (u_g + u_p)/2,
+            # G_out = -G_in - 4 B m (the scalar formula above when B = beta I)
+            B = beta_e
+            up = u_local[p_local]
+            ug = np.linalg.solve(np.eye(len(up)) - B, up + B @ up + G_in)
+            return -G_in - 2.0 * (B @ (ug + up))
         return -((1.0 + beta_e) * G_in + 4.0 * beta_e * u_local[p_local]) / (1.0 - beta_e)
 
     def insert(self, z, i, u_local):

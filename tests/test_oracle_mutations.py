@@ -129,3 +129,83 @@ def test_double_counted_shared_diagonal_is_caught():
     y = sw.block_jacobi_U(rho)
     bad = dec.flatten({ij: xh[ij] + y[ij] for ij in dec.slots})
     assert np.linalg.norm(bad - ref) > 1e-3 * np.linalg.norm(ref)
+
+
+# ------------------------------------------------ Pade HABC transmission (oracle.habc)
+import oracle.habc as ohabc  # noqa: E402
+
+
+def _habc_fixed_point_error():
+    w = W.workload("custom", n=30, N1=3, N2=2, medium="layered", seed=2,
+                   xcuts=[0, 11, 19, 30], ycuts=[0, 13, 30])
+    A = assemble_operator(w.n, w.h, w.omega, w.m2)
+    dec = Decomposition(w.n, w.h, w.omega, w.m2, w.xcuts, w.ycuts, transmission="habc")
+    r = W.random_complex(w.N, 11)
+    z = Sweeper(dec).precondition(r, "exact")
+    u = spla.spsolve(A.tocsc(), r)
+    return np.linalg.norm(z - u) / np.linalg.norm(u)
+
+
+def _neumann_symbol_error():
+    L, h, kappa = 21, 0.02, 40.0
+    T = ohabc.side_operator(np.full(L, kappa), h, 8, np.pi / 3)
+    j = np.arange(L)
+    worst = 0.0
+    for k in (0, 3, 11):
+        v = np.cos(np.pi * k * (j + 0.5) / L)
+        lam = -(2.0 - 2.0 * np.cos(np.pi * k / L)) / h ** 2
+        sym = 1j * kappa * ohabc.rotated_sqrt(lam / kappa ** 2, 8, np.pi / 3)
+        worst = max(worst, np.linalg.norm(T @ v - sym * v) / np.linalg.norm(sym * v))
+    return worst
+
+
+def test_habc_pins_hold_unpatched():
+    assert _habc_fixed_point_error() < 1e-12
+    assert _neumann_symbol_error() < 1e-10
+
+
+def test_habc_outgoing_without_the_incoming_term_is_caught(monkeypatch):
+    orig = odec.Decomposition.outgoing
+
+    def bad(self, i, j, u_local, G_in):
+        return orig(self, i, j, u_local, G_in) + G_in      # drops the -G_in term
+    monkeypatch.setattr(odec.Decomposition, "outgoing", bad)
+    assert _habc_fixed_point_error() > 1e-3
+
+
+def test_habc_one_sided_operator_is_caught(monkeypatch):
+    """Transposing the side matrix on one side of each interface only breaks the
+    fixed point (both sides must apply the same operator)."""
+    orig = odec.Decomposition._edge_geometry
+
+    def bad(self, i, j):
+        p, B = orig(self, i, j)
+        return (p, B.T.copy()) if (np.ndim(B) == 2 and i < j) else (p, B)
+    # the layered medium makes kappa_e vary along the side, so B is not symmetric
+    monkeypatch.setattr(odec.Decomposition, "_edge_geometry", bad)
+    assert _habc_fixed_point_error() > 1e-6
+
+
+def test_habc_dropped_neumann_ends_are_caught(monkeypatch):
+    orig = ohabc.tangential_laplacian
+
+    def bad(L, h):
+        D = orig(L, h)
+        D[0, 0] -= 1.0 / h ** 2          # Dirichlet instead of Neumann ends
+        D[-1, -1] -= 1.0 / h ** 2
+        return D
+    monkeypatch.setattr(ohabc, "tangential_laplacian", bad)
+    assert _neumann_symbol_error() > 1e-3
+
+
+def test_habc_swapped_pade_coefficients_are_caught(monkeypatch):
+    orig = ohabc.pade_coefficients
+
+    def bad(N):
+        a, b = orig(N)
+        M = 2 * N + 1
+        return 2.0 / M * b, a * M / 2.0                 # sin and cos exchanged
+    monkeypatch.setattr(ohabc, "pade_coefficients", bad)
+    w = 0.1
+    err = abs(ohabc.pade_sqrt(w, 3) - np.sqrt(1 + w))
+    assert err > 0.05 * w ** 7                          # the Taylor-order pin fails
