@@ -20,6 +20,8 @@ Plain complex128 NumPy/SciPy code, written for readability, not speed:
 * :mod:`oracle.krylov` - restarted flexible GMRES (right preconditioning,
   modified Gram-Schmidt, dense least squares on the Hessenberg matrix).
 * :mod:`oracle.adjoint` - source-receiver misfit and its adjoint-state gradient.
+* :mod:`oracle.habc` - the Pade-type high-order transmission operator
+  (``Decomposition(..., transmission="habc")``).
 * :mod:`oracle.parallel` - the same sweeps with the local solves of a stage run
   in worker processes (the all-cores CPU baseline).
 
@@ -30,6 +32,7 @@ repeated at the functions that take them.
 from .discretization import assemble_operator, ghost_factor, operator_diagonal_derivative
 from .decomposition import Decomposition
 from .sweeping import Sweeper, schedule_steps
+from . import habc
 from .krylov import fgmres
 from .adjoint import misfit_gradient_direct, misfit_gradient_iterative, misfit_value
 
