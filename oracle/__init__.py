@@ -25,9 +25,8 @@ Plain complex128 NumPy/SciPy code, written for readability, not speed:
 * :mod:`oracle.parallel` - the same sweeps with the local solves of a stage run
   in worker processes (the all-cores CPU baseline).
 
-Every function states the passage it follows.  Readings of passages where the
-paper is silent or ambiguous are listed in the project's design notes and
-repeated at the functions that take them.
+Every function states the passage it follows, and the reading it takes where
+the paper is silent or ambiguous.
 """
 from .discretization import assemble_operator, ghost_factor, operator_diagonal_derivative
 from .decomposition import Decomposition

@@ -20,7 +20,7 @@ modes (z < -1) are damped.  The auxiliary-field form of the references
 (phi_l = w / (1 + b_l w) u on the boundary) is the same operator; here each
 interface side carries it as the dense matrix it defines on the side's points.
 
-Readings (listed in the design notes): Delta_G is the 3-point second difference
+Readings taken where the paper is silent: Delta_G is the 3-point second difference
 along the side with spacing h and homogeneous Neumann ends (no corner
 treatment: the fields of one side do not see the other sides); k is the edge
 wavenumber kappa_e of each point; the HABC acts on interfaces only, the outer
