@@ -290,6 +290,40 @@ class MisfitFn(torch.autograd.Function):
         return grad_output * grad, None, None, None, None
 
 
+# ------------------------------------------------- sources over several ranks
+def source_shard(nsrc: int, rank: int, world: int) -> range:
+    """The sources of ``rank`` when ``nsrc`` sources are dealt to ``world`` ranks in
+    contiguous blocks (the first ``nsrc % world`` ranks take one more)."""
+    if world < 1 or not 0 <= rank < world:
+        raise ValueError("need 0 <= rank < world")
+    q, r = divmod(int(nsrc), int(world))
+    lo = rank * q + min(rank, r)
+    return range(lo, lo + q + (1 if rank < r else 0))
+
+
+def reduce_misfit(J: float, grad: "torch.Tensor", group=None):
+    """Sum a rank's misfit and gradient over the ranks of ``group`` (the default
+    process group when None; unchanged without torch.distributed): the misfit and
+    its gradient are sums over the sources, so source-parallel inversion needs this
+    one all-reduce of N + 1 doubles and nothing else."""
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return J, grad
+    buf = torch.cat([grad.reshape(-1).to(torch.float64),
+                     torch.tensor([J], dtype=torch.float64, device=grad.device)])
+    dist.all_reduce(buf, op=dist.ReduceOp.SUM, group=group)
+    return float(buf[-1]), buf[:-1].reshape(grad.shape)
+
+
+def misfit_grad_sharded(problem: "Problem", f, rec_idx, d, group=None, **kw):
+    """``(J, grad_m2, u)`` over the sources of all ranks: each rank passes its own
+    sources (``f``: its rows, ``d``: their data; see :func:`source_shard`) and gets
+    the total misfit and gradient; ``u`` stays the rank's own fields."""
+    J, grad, u = problem.misfit_grad(f, rec_idx, d, **kw)
+    J, grad = reduce_misfit(J, grad, group)
+    return J, grad, u
+
+
 # ------------------------------------------------------------------ profiling
 class HelmKStat(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_longlong), ("ms", ctypes.c_double), ("flops", ctypes.c_double),
