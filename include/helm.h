@@ -304,6 +304,20 @@ const char* helm_last_error(void);
  * reconstruction stages, plus the residual stage of BSP).  steps/stages host. */
 helm_status helm_schedule_info(int N1, int N2, int sched, int* steps, int* stages);
 
+/* Host only (no GPU): the Pade-type high-order transmission operator of one interface
+ * side (Sections 3 and 6: HABC transmission with n_pade auxiliary fields and rotation
+ * phi; the paper's runs use 8 and pi/3), as the dense L x L matrix
+ *   T = i diag(k) e^{i phi/2} R_N(W),  W = (I + diag(1/k^2) Lap) e^{-i phi} - I,
+ *   R_N(W) = I + sum_{l=1..N} a_l (I + b_l W)^{-1} W,
+ *   a_l = 2/M sin^2(l pi/M), b_l = cos^2(l pi/M), M = 2N + 1,
+ * the rotated-branch Pade approximation of i k sqrt(1 + Lap/k^2), where Lap is the
+ * 3-point second difference of spacing h along the side with Neumann ends.
+ * kappa: host, L wavenumbers (> 0) of the side's points; T: host, L*L values,
+ * row-major (T[r*L + c]), written by the call.  n_pade = 0 and phi = 0 give
+ * i diag(kappa), the impedance condition.  HELM_ERR_ARG for NULL pointers, L < 1,
+ * h <= 0, n_pade < 0, a non-positive kappa or a singular factor. */
+helm_status helm_habc_side_operator(const double* kappa, int L, double h, int n_pade, double phi, helm_c128* T);
+
 /* Problem sizes of a handle: N = n_x*n_y unknowns, number of subdomains,
  * 2 N_e interface unknowns (trace points), bytes of the current factors. */
 helm_status helm_problem_info(const helm_problem* p, long long* n_unknowns, int* n_subdomains,

@@ -8,9 +8,11 @@ missing or fails to load, every call raises.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import re
 
+import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -288,6 +290,18 @@ class MisfitFn(torch.autograd.Function):
     def backward(ctx, grad_output):
         (grad,) = ctx.saved_tensors
         return grad_output * grad, None, None, None, None
+
+
+def habc_side_operator(kappa, h: float, n_pade: int = 8, phi: float = math.pi / 3):
+    """The HABC transmission operator of one interface side as an L x L complex128
+    array (host only; see ``helm_habc_side_operator`` in include/helm.h)."""
+    k = np.ascontiguousarray(kappa, dtype=np.float64).reshape(-1)
+    L = k.size
+    T = np.empty((L, L), dtype=np.complex128)
+    fn = lib().helm_habc_side_operator
+    fn.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_void_p]
+    _check(fn(k.ctypes.data, L, float(h), int(n_pade), float(phi), T.ctypes.data))
+    return T
 
 
 # ------------------------------------------------- sources over several ranks

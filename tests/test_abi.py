@@ -94,3 +94,23 @@ def test_shape_query_rejects_a_null_handle_without_gpu(L):
     with pytest.raises(helm.HelmError) as e:
         helm.iface_shape(NoProblem(), 4)
     assert e.value.status == 1 and "NULL" in str(e.value)
+
+
+def test_habc_side_operator_matches_the_oracle_without_gpu(L):
+    """The library's host builder of the HABC side operator (C++, its own LU) equals
+    the oracle's NumPy one; N = 0 without rotation is i diag(kappa); bad arguments
+    give HELM_ERR_ARG."""
+    from oracle import habc
+    from paper_2209_10886_gb300 import helm
+    rng = np.random.default_rng(3)
+    for Lside, N, phi in ((37, 8, np.pi / 3), (5, 3, 0.4), (1, 8, np.pi / 3), (128, 8, np.pi / 3)):
+        kappa = 40.0 + 10.0 * rng.random(Lside)
+        T = helm.habc_side_operator(kappa, 0.01, N, phi)
+        ref = habc.side_operator(kappa, 0.01, N, phi)
+        assert np.linalg.norm(T - ref) <= 1e-12 * np.linalg.norm(ref), (Lside, N)
+    kappa = 30.0 + rng.random(9)
+    assert np.allclose(helm.habc_side_operator(kappa, 0.02, 0, 0.0), np.diag(1j * kappa), rtol=0, atol=1e-14)
+    with pytest.raises(helm.HelmError):
+        helm.habc_side_operator(np.array([1.0, -2.0]), 0.01)
+    with pytest.raises(helm.HelmError):
+        helm.habc_side_operator(np.array([1.0, 2.0]), 0.0)
