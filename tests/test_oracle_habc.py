@@ -93,3 +93,34 @@ def test_habc_needs_fewer_interface_iterations_than_robin():
         assert rr <= 1e-6
     print("BSP interface GMRES iterations:", its)
     assert its["habc"] < its["optimized"]
+
+
+def test_habc_local_problem_is_a_boundary_modification_of_the_robin_one():
+    """The HABC local matrix differs from a Robin one only by the side blocks on the
+    boundary points, A_habc = A_robin - P C P^T, so its boundary block follows from
+    the Robin one in the boundary space: K_habc = (I - K_robin C)^{-1} K_robin (the
+    push-through form of the Woodbury identity; P may repeat a corner node)."""
+    import oracle.decomposition as odec
+    w = W.workload("custom", **CASE)
+    args = (w.n, w.h, w.omega, w.m2, w.xcuts, w.ycuts)
+    dh = Decomposition(*args, transmission="habc")
+    db = Decomposition(*args, transmission="optimized", tc_scale=0.5)
+    i = max(dh.subdomains, key=lambda s: len(dh.neighbours(s)))       # the most interface sides
+    sides = list(dh.neighbours(i))
+    pts = np.concatenate([dh._edges[(i, j)][0] for j in sides])        # boundary points, side by side
+    Mi = dh.local_matrix(i).shape[0]
+    P = np.zeros((Mi, pts.size))
+    P[pts, np.arange(pts.size)] = 1.0
+    C = np.zeros((pts.size, pts.size), dtype=np.complex128)
+    o = 0
+    for j in sides:
+        L = len(dh._edges[(i, j)][0])
+        Ch = odec.ghost_matrix(dh._edges[(i, j)][1])
+        Cb = np.diag(odec.ghost_factor(db._edges[(i, j)][1]))
+        C[o:o + L, o:o + L] = Ch - Cb
+        o += L
+    Ah, Ab = dh.local_matrix(i).toarray(), db.local_matrix(i).toarray()
+    assert np.abs(Ah - (Ab - P @ C @ P.T)).max() < 1e-12
+    Kh = P.T @ np.linalg.solve(Ah, P)
+    Kb = P.T @ np.linalg.solve(Ab, P)
+    assert rel(np.linalg.solve(np.eye(pts.size) - Kb @ C, Kb), Kh) < 1e-10
