@@ -2,18 +2,21 @@
 the serial oracle's results bit for bit: same factors, same solves, only the
 process that runs them differs."""
 import numpy as np
+import pytest
 
 import workloads as W
 from oracle import Decomposition, Sweeper
 from oracle.parallel import PoolSweeper
 
 
-def test_pool_sweeper_equals_serial_sweeper():
+@pytest.mark.parametrize("transmission", ["optimized", "habc"])
+def test_pool_sweeper_equals_serial_sweeper(transmission):
     w = W.workload("custom", n=60, N1=3, N2=2, medium="layered", seed=3,
                    xcuts=[0, 21, 39, 60], ycuts=[0, 33, 60])
     args = (w.n, w.h, w.omega, w.m2, w.xcuts, w.ycuts)
-    serial = Sweeper(Decomposition(*args))
-    pool = PoolSweeper(Decomposition(*args), args, processes=2)
+    kw = dict(transmission=transmission)
+    serial = Sweeper(Decomposition(*args, **kw))
+    pool = PoolSweeper(Decomposition(*args, **kw), args, kw, processes=2)
     try:
         r = W.random_complex((1, w.N), 5)[0]
         for kind in ("BSP", "SP"):
