@@ -94,9 +94,20 @@ typedef enum { HELM_SCHED_BSP = 0, HELM_SCHED_SP = 1, HELM_SCHED_BSP_NONOVERLAP 
  *                    an optimized zeroth-order complex Robin parameter.
  * HELM_TC_IMPEDANCE: T_e = i kappa_e, the basic impedance operator the paper
  *                    uses for its algebra (Section 3).
+ * HELM_TC_HABC:      the Pade-type high-order absorbing condition of the paper's
+ *                    experiments (Sections 3 and 6: N_pade auxiliary fields and
+ *                    rotation phi, 8 and pi/3 there): on each interface side the
+ *                    dense operator T = i diag(k) e^{i phi/2} R_N(W) that
+ *                    helm_habc_side_operator returns (Neumann ends, no corner
+ *                    treatment), in place of the scalar T_e.  The library factors
+ *                    the local problems with the optimized Robin parameter (tc_scale)
+ *                    and folds the HABC side blocks in through the interface boundary
+ *                    points (needs boundary_operators = 1 and at most 1024 interface
+ *                    boundary points per subdomain); every sweep stage stays one GEMV
+ *                    (or GEMM) per subdomain.
  * kappa_e = omega sqrt((m2_p + m2_q)/2) on the edge between nodes p and q.
  * The converged solution does not depend on T_e; the iteration count does. */
-typedef enum { HELM_TC_OPTIMIZED = 0, HELM_TC_IMPEDANCE = 1 } helm_transmission;
+typedef enum { HELM_TC_OPTIMIZED = 0, HELM_TC_IMPEDANCE = 1, HELM_TC_HABC = 2 } helm_transmission;
 
 typedef struct {
     int transmission;   /* helm_transmission; default HELM_TC_OPTIMIZED */
@@ -134,6 +145,17 @@ typedef struct {
                            form is chosen) only if it makes at least this many CTAs (of
                            128 output rows x 16 or 32 RHS); smaller stages take the
                            CUDA-core shape.  -1 (default): two per SM */
+    size_t device_budget;  /* 0 (default): no limit.  Otherwise the most device memory, in
+                           bytes, that the handle's large arrays may take: precond_factor
+                           returns HELM_ERR_OOM (allocating nothing) when the factors, their
+                           tensor-core copy and the boundary operators would exceed it, and
+                           gmres_solve plans its right-hand-side chunks within what the
+                           factors leave of it (HELM_ERR_OOM when not even one right-hand
+                           side's Krylov workspace fits).  Tables of a few KB per subdomain
+                           and the preconditioner's interface buffers are not counted */
+    int n_pade;         /* HELM_TC_HABC: auxiliary fields of the Pade approximation (>= 0);
+                           default 8 */
+    double pade_phi;    /* HELM_TC_HABC: branch-cut rotation phi (radians); default pi/3 */
 } helm_setup_opts;
 
 typedef struct {
@@ -184,6 +206,12 @@ typedef struct {
                            and the least-squares problem stay FP64), which suits an
                            inner_tol well above the FP32 roundoff; 1 keeps them FP64.
                            With complex128 factors they are always FP64 */
+    long long wait_cycles; /* 0 (default): the grid barriers of the Gram-Schmidt kernels (the
+                           volume and interface Arnoldi steps) give up after ~2e9 SM clock
+                           cycles (~1 s).  > 0: after this many cycles instead; a barrier that
+                           gives up makes the call return HELM_ERR_TIMEOUT (a diagnostic
+                           knob for bounding a solve's stalls, and for exercising the
+                           timeout path: with a few cycles every barrier gives up) */
 } helm_opts;
 
 /* Orthogonalisation of the Arnoldi vectors.
@@ -227,7 +255,8 @@ helm_status helm_setup(int n_x, int n_y, double h, double omega, const double* m
 /* Factor every subdomain matrix (paper Eq. subPbm; the paper uses a sparse
  * direct solver, Section 6) as a block tridiagonal LU over its grid rows:
  * T_1 = D_1, X_r = T_r^{-1}, T_{r+1} = D_{r+1} - X_r, storing all X_r.
- * Replaces factors of another precision.  Stream-ordered. */
+ * Replaces factors of another precision.  Synchronises `stream` (it reads the
+ * pivot checks back and reports a zero pivot as HELM_ERR_ARG). */
 helm_status precond_factor(helm_problem* p, helm_prec prec, void* stream);
 
 /* z = M^{-1} r for nrhs right-hand sides (device r and z, nrhs*n_x*n_y each,
@@ -251,11 +280,20 @@ helm_status precond_apply(helm_problem* p, int sched, const helm_c128* r, helm_c
  * interface buffers, the solve workspace, norms) from one static array of
  * HELM_NOALLOC_SCRATCH_BYTES in device memory that belongs to the library
  * image: every GPU that loads the library holds it until the process exits.
- * Result: the same z = M^{-1} r as precond_apply (same kernels, same order).
+ * Result: z = M^{-1} r as precond_apply computes it, by the same kernels in the
+ * same order.  This call never runs the autotuner: its interface stages take the
+ * launch shape an earlier precond_apply or gmres_solve tuned for this nrhs on p,
+ * else the fixed rules (see helm_iface_shape), so the two can differ by the
+ * rounding of differently ordered sums (not bit for bit).
  * Arguments as for precond_apply; p must be factored (HELM_ERR_STATE if not).
- * Sizes: returns HELM_ERR_ARG, with a message naming the bytes needed, when
- * 3*ntrace*nrhs*e + N*nrhs*e (e = 8 for HELM_PREC_C64, 16 for C128) plus a
- * few KB exceed HELM_NOALLOC_SCRATCH_BYTES; nothing is launched then.
+ * Sizes: returns HELM_ERR_ARG, with a message naming the bytes needed, when the
+ * scratch exceeds HELM_NOALLOC_SCRATCH_BYTES; nothing is launched then.  The
+ * scratch is 3*ntrace*nrhs*e + N*nrhs*e bytes (e = 8 for HELM_PREC_C64, 16 for
+ * C128; 4*ntrace*nrhs*e with the HABC transmission, which keeps the liftings'
+ * boundary values) plus 8*nrhs*(3 + 1216) bytes of norms and partial sums, each part
+ * rounded up to 256 bytes; with HELM_PREC_C64, tensor_cores on and nrhs >=
+ * tc_min_rhs (the tensor-core stages) add 2*etot*nrhs*8 + N*nrhs*8 bytes, etot
+ * = 2 * sum over the subdomains of (mx + my).
  * Calls no cudaMalloc, cudaFree or other allocating routine.  The first call
  * on a device looks up the array's device address with that device current;
  * make that first call before any stream capture.  Every call on a device

@@ -91,6 +91,7 @@ class Sweeper:
     def __init__(self, dec):
         self.dec = dec
         self.steps = 0      # sequential steps taken by the last sweep
+        self.interface_steps = 0   # interface Krylov steps of precondition_interface_krylov, summed
 
     # ------------------------------------------------------------- S and E, F
     def scatter_from(self, i, x):
@@ -250,7 +251,8 @@ class Sweeper:
         def interface_precond(v):
             return dec.flatten(sweep(dec.unflatten(v)))
 
-        g, _, _ = fgmres(interface_operator, interface_precond, b, tol=tol, restart=restart, maxit=maxit)
+        g, it, _ = fgmres(interface_operator, interface_precond, b, tol=tol, restart=restart, maxit=maxit)
+        self.interface_steps += it          # running count of interface Krylov steps (bookkeeping only)
         return self.reconstruct(r, dec.unflatten(g))
 
     # ------------------------------------------------------------ dense (tiny)

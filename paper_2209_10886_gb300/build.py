@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhelm.so")
 SOURCES = ["helm_api.cu", "k_setup.cu", "k_factor.cu", "k_stage.cu", "k_iface.cu", "k_krylov.cu", "k_mgs.cu", "k_adjoint.cu", "k_tc.cu",
-           "habc_host.cu"]
+           "habc_host.cu", "k_habc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

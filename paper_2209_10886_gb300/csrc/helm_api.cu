@@ -17,9 +17,10 @@
 size_t factor_work_elems(int max_mx, size_t elem);
 int mgs_grid();
 long long mgs_max_n(int grid);
+// limit: cycles a grid barrier waits before it gives up (0: the default, ~1 s)
 cudaError_t launch_mgs(const double2* V, long long vsk, long long vsr, double2* w, int nvec, long long n, int nrhs,
                        const int* active, double2* hcol, int ldh, double* hnorm, double2* partial, unsigned* bar,
-                       int* err, int grid, cudaStream_t st);
+                       int* err, int grid, cudaStream_t st, long long limit);
 template <typename VT>
 int cgs2_grid(long long n, int max_j);
 template <typename VT>
@@ -28,7 +29,7 @@ cudaError_t launch_cgs2_step(const VT* V, long long vsk, long long vsr, int j, l
                              long long hs, double2* cs, double2* sn, double2* g, int ldg, double* est, double* invh,
                              double2* partial, unsigned* bar, int* err, int grid, cudaStream_t st,
                              const int* dj = nullptr, int jmax = 0, const VT* wsrc = nullptr,
-                             VT* vout1 = nullptr, VT* vout2 = nullptr);
+                             VT* vout1 = nullptr, VT* vout2 = nullptr, long long limit = 0);
 
 // ------------------------------------------------------------ launch count
 #include <atomic>
@@ -201,6 +202,20 @@ struct helm_problem {
     int nslots = 0;
     std::vector<StageDesc> sched[HELM_NSCHED];
 
+    // HABC transmission (setup option): the local problems are factored with the optimized
+    // Robin condition and the HABC side blocks enter through the boundary space (k_habc.cu)
+    int habc = 0;
+    double2* d_rin = nullptr;        // per interface slot: Rin = (I - h T / 2)^{-1}, L x L row-major, FP64
+    std::vector<long long> slot_moff;   // offset of each slot's matrix in d_rin
+    std::vector<int> slot_len;
+    std::map<long long, int> slot_of_toff;   // trace offset of a slot's first point -> the slot
+    int* d_swap = nullptr;           // trace point -> the same point of the neighbour's slot
+    TraceCoef<double2>* d_tcid128 = nullptr;   // stage coefficients with the HABC: cin = 1, ca = 0, cb = 1
+    TraceCoef<float2>* d_tcid64 = nullptr;
+    void* d_Lq = nullptr;            // lifting map, reconstruction maps (factor precision, K layout)
+    void* d_D1 = nullptr;
+    void* d_D2 = nullptr;
+
     double* d_m2 = nullptr;
     double2* d_adiag = nullptr;
     double2* d_dloc = nullptr;
@@ -241,7 +256,7 @@ struct helm_problem {
 
     // preconditioner workspace
     int ws_nrhs = 0;
-    void* d_trace[3] = {nullptr, nullptr, nullptr};
+    void* d_trace[4] = {nullptr, nullptr, nullptr, nullptr};   // B, X, Y (and U with the HABC transmission)
     void* d_yws = nullptr;
     void* d_escr = nullptr;          // tensor-core path: 2 nrhs etot complex64 (interface data, boundary values)
     void* d_r64 = nullptr;           // tensor-core path: the scaled source in complex64 (nrhs N)
@@ -252,6 +267,7 @@ struct helm_problem {
     KrylovWS kw, kwi;
     long long inner_steps = 0;       // interface Krylov steps taken inside the preconditioner (all calls)
     int persistent = 0;              // gmres_solve option: sweeps in the persistent sweep kernel
+    long long wait_cycles = 0;       // gmres_solve option: grid-barrier limit of the Gram-Schmidt kernels (0: default)
     bool inner_hist_taken = false;   // the interface history of this gmres_solve call is recorded
     struct TunedShape { int prec, nrhs; IfaceCfg cfg; };
     std::vector<TunedShape> iface_tuned;   // autotuned interface-stage launch shapes
@@ -290,6 +306,7 @@ struct helm_problem {
         cudaGraph_t tmpl = nullptr;  // device-loop graphs keep their template (conditional node)
         long long gen = 0;           // Krylov workspace generation a device-loop graph was built for
         int m = 0;                   // its restart length
+        long long limit = 0;         // the grid-barrier limit its Gram-Schmidt launch was captured with
     };
     bool dev_loop_broken = false;    // a device-loop graph failed to build: host-driven loop from then on
     std::vector<PcGraph> graphs;
@@ -298,6 +315,22 @@ struct helm_problem {
 
     long long N() const { return (long long)nx * ny; }
 };
+
+// trace coefficients of the stages: the Robin ones, or with the HABC transmission the
+// identity ones (cin = 1, ca = 0, cb = 1: the stage matrices carry the transmission)
+template <typename T> static const TraceCoef<T>* stage_tc(const helm_problem* p) {
+    if constexpr (sizeof(T) == 8) return p->habc ? p->d_tcid64 : p->d_tc64;
+    else return p->habc ? p->d_tcid128 : p->d_tc128;
+}
+// the matrix an interface stage applies (KMAT_*)
+static const void* stage_kmat(const helm_problem* p, int kmat) {
+    switch (kmat) {
+        case KMAT_LQ: return p->d_Lq;
+        case KMAT_D1: return p->d_D1;
+        case KMAT_D2: return p->d_D2;
+        default: return p->d_K;
+    }
+}
 
 // event pair around one launch of class k (no-op when profiling is off)
 static void prof_begin(helm_problem* p, int k, cudaStream_t st) {
@@ -414,6 +447,7 @@ extern "C" void helm_default_opts(helm_opts* o) {
     o->persistent = 0;
     o->inner_hist = nullptr;
     o->inner_fp64 = 0;
+    o->wait_cycles = 0;
 }
 
 extern "C" long long helm_inner_steps(const helm_problem* p) { return p ? p->inner_steps : 0; }
@@ -426,6 +460,9 @@ extern "C" void helm_default_setup_opts(helm_setup_opts* o) {
     o->tc_min_rhs = 16;
     o->autotune = 1;
     o->tc_iface_min_ctas = -1;
+    o->device_budget = 0;
+    o->n_pade = 8;
+    o->pade_phi = 3.14159265358979323846 / 3.0;
 }
 
 extern "C" const char* helm_last_error(void) { return g_err.c_str(); }
@@ -461,6 +498,94 @@ static std::vector<int> make_cuts(int n, int parts, const int* cuts) {
     return c;
 }
 
+// The HABC transmission's setup (k_habc.cu): per interface slot the side matrix
+// Rin = (I - h T / 2)^{-1} (FP64), the identity stage coefficients and the slot-swap
+// table.  d_ssub / d_sside / d_slen: the slots' subdomain, side and length on the device.
+static helm_status habc_setup(helm_problem* p, const int* d_ssub, const int* d_sside, const int* d_slen,
+                              const std::vector<int>& slot_len, const std::vector<int>& slot_off) {
+    const int nslots = p->nslots;
+    p->slot_len = slot_len;
+    for (int k = 0; k < nslots; ++k) p->slot_of_toff[slot_off[k]] = k;
+    p->slot_moff.assign(nslots, 0);
+    long long tot = 0;
+    int max_len = 0;
+    for (int k = 0; k < nslots; ++k) {
+        p->slot_moff[k] = tot;
+        tot += (long long)slot_len[k] * slot_len[k];
+        max_len = std::max(max_len, slot_len[k]);
+    }
+    if (gj_grid(max_len) <= 0 || gj_grid(p->max_Lb) <= 0) {
+        set_error("helm_setup: the HABC transmission takes at most 1024 interface boundary points per subdomain");
+        return HELM_ERR_UNSUPPORTED;
+    }
+    helm_status status = HELM_OK;
+    double2* Y = nullptr;
+    long long* d_moff = nullptr;
+    void* d_mats = nullptr;
+    double2* pub = nullptr;
+    unsigned* bar = nullptr;
+    int* info = nullptr;
+    do {
+        cudaError_t e;
+        if ((e = dalloc(p->d_rin, tot)) != cudaSuccess || (e = dalloc(Y, tot)) != cudaSuccess ||
+            (e = dalloc(d_moff, nslots)) != cudaSuccess) { status = cuda_status(e, "helm_setup: HABC side matrices"); break; }
+        cudaMemcpy(d_moff, p->slot_moff.data(), nslots * sizeof(long long), cudaMemcpyHostToDevice);
+        e = launch_habc_sides(p->d_m2, p->nx, p->h, p->omega, p->sopts.n_pade, p->sopts.pade_phi, d_ssub, d_sside,
+                              d_slen, d_moff, nslots, max_len, p->d_subtab, p->d_rin, Y, 0);
+        if (e != cudaSuccess) { status = cuda_status(e, "helm_setup: HABC side operators"); break; }
+        // Rin_s = (I - h T_s / 2)^{-1}, in place
+        std::vector<unsigned char> mats(gj_mat_bytes() * nslots);
+        for (int k = 0; k < nslots; ++k) gj_mat_fill(mats.data(), k, p->d_rin + p->slot_moff[k], slot_len[k], slot_len[k]);
+        if ((e = cudaMalloc(&d_mats, mats.size())) != cudaSuccess || (e = dalloc(pub, 2 * (size_t)(max_len + 2))) ||
+            (e = dalloc(bar, 2)) || (e = dalloc(info, nslots))) { status = cuda_status(e, "helm_setup: HABC inversion"); break; }
+        cudaMemcpy(d_mats, mats.data(), mats.size(), cudaMemcpyHostToDevice);
+        cudaMemset(bar, 0, 2 * sizeof(unsigned));
+        cudaMemset(info, 0, nslots * sizeof(int));
+        e = launch_gj_inverse(d_mats, nslots, max_len, pub, bar, p->d_err, info, 0);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) { status = cuda_status(e, "helm_setup: HABC side inversion"); break; }
+        std::vector<int> hinfo(nslots);
+        cudaMemcpy(hinfo.data(), info, nslots * sizeof(int), cudaMemcpyDeviceToHost);
+        for (int k = 0; k < nslots; ++k)
+            if (hinfo[k]) { set_error("helm_setup: singular HABC side factor I - h T / 2"); status = HELM_ERR_ARG; }
+        if (status != HELM_OK) break;
+        // stage coefficients: the HABC stages apply their maps in full (cin = 1, ca = 0, cb = 1)
+        std::vector<TraceCoef<double2>> id128(p->ntrace, TraceCoef<double2>{make_double2(1, 0), make_double2(0, 0),
+                                                                             make_double2(1, 0)});
+        std::vector<TraceCoef<float2>> id64(p->ntrace, TraceCoef<float2>{make_float2(1, 0), make_float2(0, 0),
+                                                                          make_float2(1, 0)});
+        // the point pt of slot (i, j) <-> the point pt of slot (j, i)
+        std::vector<int> swp(p->ntrace, 0);
+        for (auto& sh : p->subs)
+            for (int sd = 0; sd < 4; ++sd) {
+                if (sh.dev.tin[sd] < 0) continue;
+                const int len = (sd == SW || sd == SE) ? sh.dev.my : sh.dev.mx;
+                for (int pt = 0; pt < len; ++pt) swp[sh.dev.tin[sd] + pt] = sh.dev.tout[sd] + pt;
+            }
+        if ((e = dalloc(p->d_tcid128, p->ntrace)) || (e = dalloc(p->d_tcid64, p->ntrace)) ||
+            (e = dalloc(p->d_swap, p->ntrace))) { status = cuda_status(e, "helm_setup: HABC tables"); break; }
+        cudaMemcpy(p->d_tcid128, id128.data(), id128.size() * sizeof(id128[0]), cudaMemcpyHostToDevice);
+        cudaMemcpy(p->d_tcid64, id64.data(), id64.size() * sizeof(id64[0]), cudaMemcpyHostToDevice);
+        if ((e = cudaMemcpy(p->d_swap, swp.data(), swp.size() * sizeof(int), cudaMemcpyHostToDevice)) != cudaSuccess) {
+            status = cuda_status(e, "helm_setup: HABC tables");
+            break;
+        }
+    } while (0);
+    dfree(Y); dfree(d_moff); dfree(pub); dfree(bar); dfree(info);
+    if (d_mats) cudaFree(d_mats);
+    if (status == HELM_OK) {
+        int v = 0;
+        cudaMemcpy(&v, p->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+        if (v) {
+            cudaMemset(p->d_err, 0, sizeof(int));
+            set_error("helm_setup: a device wait timed out in the HABC setup");
+            status = HELM_ERR_TIMEOUT;
+        }
+    }
+    p->habc = status == HELM_OK;
+    return status;
+}
+
 extern "C" helm_status helm_setup(int n_x, int n_y, double h, double omega, const double* m2, int N1, int N2,
                                   const int* xcuts, const int* ycuts, const helm_setup_opts* opts,
                                   helm_problem** out) {
@@ -473,9 +598,15 @@ extern "C" helm_status helm_setup(int n_x, int n_y, double h, double omega, cons
     helm_setup_opts so;
     helm_default_setup_opts(&so);
     if (opts) so = *opts;
-    if (so.transmission != HELM_TC_OPTIMIZED && so.transmission != HELM_TC_IMPEDANCE)
+    if (so.transmission != HELM_TC_OPTIMIZED && so.transmission != HELM_TC_IMPEDANCE && so.transmission != HELM_TC_HABC)
         return arg_error("helm_setup: unknown transmission");
-    if (so.transmission == HELM_TC_OPTIMIZED && !(so.tc_scale > 0)) return arg_error("helm_setup: tc_scale must be > 0");
+    if (so.transmission != HELM_TC_IMPEDANCE && !(so.tc_scale > 0)) return arg_error("helm_setup: tc_scale must be > 0");
+    if (so.transmission == HELM_TC_HABC && (so.n_pade < 0 || so.n_pade > 64 || !std::isfinite(so.pade_phi)))
+        return arg_error("helm_setup: n_pade must be in 0..64 and pade_phi finite");
+    if (so.transmission == HELM_TC_HABC && !so.boundary_operators) {
+        set_error("helm_setup: the HABC transmission needs boundary_operators = 1");
+        return HELM_ERR_UNSUPPORTED;
+    }
     if (so.tensor_cores < 0 || so.tensor_cores > 2) return arg_error("helm_setup: tensor_cores must be 0, 1 or 2");
     if (so.tc_min_rhs < 1) return arg_error("helm_setup: tc_min_rhs must be >= 1");
     if (so.autotune != 0 && so.autotune != 1) return arg_error("helm_setup: autotune must be 0 or 1");
@@ -729,7 +860,9 @@ extern "C" helm_status helm_setup(int n_x, int n_y, double h, double omega, cons
         cudaMemcpy(d_xcut, xc.data(), xc.size() * sizeof(int), cudaMemcpyHostToDevice);
         cudaMemcpy(d_ycut, yc.data(), yc.size() * sizeof(int), cudaMemcpyHostToDevice);
         cudaMemcpy(d_subid, subid.data(), subid.size() * sizeof(int), cudaMemcpyHostToDevice);
-        launch_setup_coeffs(p->d_m2, n_x, n_y, h, omega, d_xcut, d_ycut, N1, N2, d_subid, so.transmission, so.tc_scale,
+        // with the HABC the factored base problem has the optimized Robin condition
+        const int base_tr = so.transmission == HELM_TC_HABC ? HELM_TC_OPTIMIZED : so.transmission;
+        launch_setup_coeffs(p->d_m2, n_x, n_y, h, omega, d_xcut, d_ycut, N1, N2, d_subid, base_tr, so.tc_scale,
                             p->d_adiag, p->d_dloc, p->d_subtab, 0);
         if (p->nslots > 0) {
             if ((e = dalloc(p->d_tc128, p->ntrace)) || (e = dalloc(p->d_tc64, p->ntrace))) { fail(e, "alloc trace coefficients"); break; }
@@ -739,8 +872,12 @@ extern "C" helm_status helm_setup(int n_x, int n_y, double h, double omega, cons
             cudaMemcpy(d_sside, slot_side.data(), p->nslots * sizeof(int), cudaMemcpyHostToDevice);
             cudaMemcpy(d_soff, slot_off.data(), p->nslots * sizeof(int), cudaMemcpyHostToDevice);
             cudaMemcpy(d_slen, slot_len.data(), p->nslots * sizeof(int), cudaMemcpyHostToDevice);
-            launch_trace_coeffs(p->d_m2, n_x, h, omega, so.transmission, so.tc_scale, d_ssub, d_sside, d_soff, d_slen,
+            launch_trace_coeffs(p->d_m2, n_x, h, omega, base_tr, so.tc_scale, d_ssub, d_sside, d_soff, d_slen,
                                 p->nslots, p->d_subtab, p->d_tc128, p->d_tc64, 0);
+            if (so.transmission == HELM_TC_HABC) {
+                const helm_status hs = habc_setup(p, d_ssub, d_sside, d_slen, slot_len, slot_off);
+                if (hs != HELM_OK) { status = hs; break; }
+            }
         }
         if ((e = dalloc(p->d_stage_subs, all_stage_subs.size())) != cudaSuccess) { fail(e, "alloc stage lists"); break; }
         if ((e = dalloc(p->d_err, 1)) != cudaSuccess) { fail(e, "alloc status word"); break; }
@@ -789,6 +926,10 @@ extern "C" helm_status helm_destroy(helm_problem* p) {
     }
     if (p->d_X) cudaFree(p->d_X);
     if (p->d_K) cudaFree(p->d_K);
+    if (p->d_Lq) cudaFree(p->d_Lq);
+    if (p->d_D1) cudaFree(p->d_D1);
+    if (p->d_D2) cudaFree(p->d_D2);
+    dfree(p->d_rin); dfree(p->d_swap); dfree(p->d_tcid128); dfree(p->d_tcid64);
     if (p->d_XT) cudaFree(p->d_XT);
     if (p->d_tcpart) cudaFree(p->d_tcpart);
     if (p->d_tccnt) cudaFree(p->d_tccnt);
@@ -875,6 +1016,154 @@ static helm_status build_boundary_operators(helm_problem* p, cudaStream_t st) {
                                     : build_boundary_operators_t<double>(p, st);
 }
 
+// The HABC stage matrices of every subdomain from its base boundary operator K (the
+// block comment of k_habc.cu has the algebra), in FP64, in batches of subdomains:
+//   KR = K Rin, W = (I - 2 KR + K + K diag(c0))^{-1} = (I - K C)^{-1}, P1 = W KR,
+//   RP = Rin P1, RW = Rin W, then Q (replaces K), Lq, D1, D2 in the factor precision.
+template <typename R>
+static helm_status habc_precompute_t(helm_problem* p, cudaStream_t st) {
+    using T = Cx<R>;
+    const int nsub = (int)p->subs.size();
+    const long long Lb2 = (long long)p->max_Lb * p->max_Lb;
+    long long kel = 0;
+    for (auto& sh : p->subs) kel += (long long)sh.dev.Lb * sh.dev.Lb;
+    // six FP64 temporaries per subdomain of a batch, at most ~2 GB
+    const int bsz = (int)std::max<long long>(1, std::min<long long>(nsub, (2LL << 30) / (6 * Lb2 * 16)));
+    helm_status status = HELM_OK;
+    double2* tmp = nullptr;
+    void *Q = nullptr, *Lq = nullptr, *D1 = nullptr, *D2 = nullptr;
+    void *d_subs = nullptr, *d_mats = nullptr, *d_gemm = nullptr;
+    double2* pub = nullptr;
+    unsigned* bar = nullptr;
+    int* info = nullptr;
+    const size_t mbytes = (size_t)kel * sizeof(T) + 16;     // as K: 16 bytes of padding
+    do {
+        cudaError_t e;
+        if ((e = cudaMalloc(&Q, mbytes)) || (e = cudaMalloc(&Lq, mbytes)) || (e = cudaMalloc(&D1, mbytes)) ||
+            (e = cudaMalloc(&D2, mbytes))) { status = cuda_status(e, "precond_factor: HABC stage matrices"); break; }
+        if ((e = dalloc(tmp, (size_t)6 * bsz * Lb2)) != cudaSuccess) {
+            status = cuda_status(e, "precond_factor: HABC workspace");
+            break;
+        }
+        const int maxprob = std::max(1, 4 * bsz);
+        if ((e = cudaMalloc(&d_subs, habc_sub_bytes() * bsz)) || (e = cudaMalloc(&d_mats, gj_mat_bytes() * bsz)) ||
+            (e = cudaMalloc(&d_gemm, gemm_prob_bytes() * maxprob)) || (e = dalloc(pub, 2 * (size_t)(p->max_Lb + 2))) ||
+            (e = dalloc(bar, 2)) || (e = dalloc(info, bsz))) {
+            status = cuda_status(e, "precond_factor: HABC tables");
+            break;
+        }
+        cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), st);
+        double2* K64 = tmp;
+        double2* KR = tmp + (size_t)bsz * Lb2;
+        double2* W = tmp + 2 * (size_t)bsz * Lb2;
+        double2* P1 = tmp + 3 * (size_t)bsz * Lb2;
+        double2* RP = tmp + 4 * (size_t)bsz * Lb2;
+        double2* RW = tmp + 5 * (size_t)bsz * Lb2;
+        std::vector<unsigned char> hs(habc_sub_bytes() * bsz), hm(gj_mat_bytes() * bsz), hg(gemm_prob_bytes() * maxprob);
+        const double2 one = make_double2(1.0, 0.0);
+        for (int b0 = 0; b0 < nsub && status == HELM_OK; b0 += bsz) {
+            const int nb = std::min(bsz, nsub - b0);
+            // per subdomain: boundary layout, the side matrices of its slots (slot_of_toff:
+            // the slot whose trace starts at a given offset), its matrix to invert
+            for (int q = 0; q < nb; ++q) {
+                const SubDev& d = p->subs[b0 + q].dev;
+                int len[4];
+                long long moff[4];
+                for (int sd = 0; sd < 4; ++sd) {
+                    len[sd] = d.bo[sd] >= 0 ? ((sd == SW || sd == SE) ? d.my : d.mx) : 0;
+                    moff[sd] = d.tin[sd] >= 0 ? p->slot_moff[p->slot_of_toff.at(d.tin[sd])] : 0;
+                }
+                habc_sub_fill(hs.data(), q, d.koff, (long long)q * Lb2, d.Lb, d.bo, len, moff, d.tin);
+                gj_mat_fill(hm.data(), q, W + (size_t)q * Lb2, d.Lb, d.Lb);
+            }
+            cudaMemcpyAsync(d_subs, hs.data(), habc_sub_bytes() * nb, cudaMemcpyHostToDevice, st);
+            cudaMemcpyAsync(d_mats, hm.data(), gj_mat_bytes() * nb, cudaMemcpyHostToDevice, st);
+            // K in FP64
+            e = launch_habc_form<T>(d_subs, nb, p->max_Lb, (const T*)p->d_K, p->d_tc128, K64, KR, W, 0, st);
+            // KR = K Rin: per side s, columns [bo_s, bo_s + L) of K times Rin_s
+            auto side_products = [&](bool left, const double2* X, double2* out) -> cudaError_t {
+                int np = 0, mm = 0, mn = 0;
+                for (int q = 0; q < nb; ++q) {
+                    const SubDev& d = p->subs[b0 + q].dev;
+                    for (int sd = 0; sd < 4; ++sd) {
+                        if (d.bo[sd] < 0) continue;
+                        const int L = (sd == SW || sd == SE) ? d.my : d.mx;
+                        const double2* rin = p->d_rin + p->slot_moff[p->slot_of_toff.at(d.tin[sd])];
+                        const size_t t = (size_t)q * Lb2;
+                        if (!left)   // out[:, bo + c] = X[:, bo + c'] Rin[c', c]
+                            gemm_prob_fill(hg.data(), np++, X + t + d.bo[sd], rin, out + t + d.bo[sd], d.Lb, L, L,
+                                           d.Lb, L, d.Lb, one, 0);
+                        else         // out[bo + r, :] = Rin[r, r'] X[bo + r', :]
+                            gemm_prob_fill(hg.data(), np++, rin, X + t + (size_t)d.bo[sd] * d.Lb,
+                                           out + t + (size_t)d.bo[sd] * d.Lb, L, d.Lb, L, L, d.Lb, d.Lb, one, 0);
+                        mm = std::max(mm, left ? L : d.Lb);
+                        mn = std::max(mn, left ? d.Lb : L);
+                    }
+                }
+                cudaError_t e2 = cudaMemcpyAsync(d_gemm, hg.data(), gemm_prob_bytes() * np, cudaMemcpyHostToDevice, st);
+                if (e2 == cudaSuccess) e2 = launch_zgemm_batched(d_gemm, np, mm, mn, st);
+                // the host table is reused by the next call: wait for the copy
+                if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(st);
+                return e2;
+            };
+            if (e == cudaSuccess) e = side_products(false, K64, KR);
+            // W = I - K C, then its inverse in place
+            if (e == cudaSuccess) e = launch_habc_form<T>(d_subs, nb, p->max_Lb, (const T*)p->d_K, p->d_tc128, K64, KR, W, 1, st);
+            if (e == cudaSuccess) e = cudaMemsetAsync(info, 0, nb * sizeof(int), st);
+            if (e == cudaSuccess) e = launch_gj_inverse(d_mats, nb, p->max_Lb, pub, bar, p->d_err, info, st);
+            // P1 = W KR
+            if (e == cudaSuccess) {
+                for (int q = 0; q < nb; ++q) {
+                    const SubDev& d = p->subs[b0 + q].dev;
+                    const size_t t = (size_t)q * Lb2;
+                    gemm_prob_fill(hg.data(), q, W + t, KR + t, P1 + t, d.Lb, d.Lb, d.Lb, d.Lb, d.Lb, d.Lb, one, 0);
+                }
+                e = cudaMemcpyAsync(d_gemm, hg.data(), gemm_prob_bytes() * nb, cudaMemcpyHostToDevice, st);
+                if (e == cudaSuccess) e = launch_zgemm_batched(d_gemm, nb, p->max_Lb, p->max_Lb, st);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            }
+            if (e == cudaSuccess) e = side_products(true, P1, RP);
+            if (e == cudaSuccess) e = side_products(true, W, RW);
+            if (e == cudaSuccess)
+                e = launch_habc_final<T>(d_subs, nb, p->max_Lb, p->d_rin, p->d_tc128, P1, RP, W, RW, (T*)Q, (T*)Lq,
+                                         (T*)D1, (T*)D2, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) { status = cuda_status(e, "precond_factor: HABC stage matrices"); break; }
+            std::vector<int> hinfo(nb);
+            cudaMemcpy(hinfo.data(), info, nb * sizeof(int), cudaMemcpyDeviceToHost);
+            for (int q = 0; q < nb; ++q)
+                if (hinfo[q]) {
+                    char buf[160];
+                    snprintf(buf, sizeof buf, "precond_factor: I - K C of subdomain %d is singular (pivot %d)", b0 + q,
+                             hinfo[q] - 1);
+                    set_error(buf);
+                    status = HELM_ERR_ARG;
+                }
+        }
+    } while (0);
+    dfree(tmp); dfree(pub); dfree(bar); dfree(info);
+    if (d_subs) cudaFree(d_subs);
+    if (d_mats) cudaFree(d_mats);
+    if (d_gemm) cudaFree(d_gemm);
+    if (status == HELM_OK) status = take_device_status(p, "precond_factor (HABC stage matrices)");
+    if (status != HELM_OK) {
+        for (void* q : {Q, Lq, D1, D2}) if (q) cudaFree(q);
+        return status;
+    }
+    // the interface stages apply Q in place of K
+    cudaFree(p->d_K);
+    p->d_K = Q;
+    p->K_bytes *= 4;                 // Q, Lq, D1, D2
+    p->d_Lq = Lq;
+    p->d_D1 = D1;
+    p->d_D2 = D2;
+    return HELM_OK;
+}
+static helm_status habc_precompute(helm_problem* p, cudaStream_t st) {
+    if (p->max_Lb == 0) return HELM_OK;
+    return p->prec == HELM_PREC_C64 ? habc_precompute_t<float>(p, st) : habc_precompute_t<double>(p, st);
+}
+
 // ----------------------------------------------------------------- factor
 extern "C" helm_status precond_factor(helm_problem* p, helm_prec prec, void* stream) {
     if (!p) return arg_error("precond_factor: NULL handle");
@@ -907,10 +1196,26 @@ extern "C" helm_status precond_factor(helm_problem* p, helm_prec prec, void* str
         tab.push_back(s.dev);
     }
     const size_t bytes = (size_t)xoff * elem;
+    if (p->sopts.device_budget > 0) {
+        // the arrays this factorisation keeps: factors, their tensor-core copy, boundary operators
+        long long kel = 0;
+        for (auto& s : p->subs) kel += (long long)s.dev.Lb * s.dev.Lb;
+        const size_t keep = bytes + (size_t)xtoff * sizeof(float) +
+                            (p->sopts.boundary_operators ? (size_t)kel * elem * (p->habc ? 4 : 1) : 0);
+        if (keep > p->sopts.device_budget) {
+            char buf[200];
+            snprintf(buf, sizeof buf, "precond_factor: the factors need %zu bytes, more than the device budget of %zu",
+                     keep, p->sopts.device_budget);
+            set_error(buf);
+            return HELM_ERR_OOM;
+        }
+    }
     HELM_CUDA_TRY(cudaStreamSynchronize(st));
     drop_graphs(p);
     if (p->d_X) { cudaFree(p->d_X); p->d_X = nullptr; p->X_bytes = 0; p->factored = 0; }
     if (p->d_K) { cudaFree(p->d_K); p->d_K = nullptr; p->K_bytes = 0; }
+    for (void** q : {&p->d_Lq, &p->d_D1, &p->d_D2})
+        if (*q) { cudaFree(*q); *q = nullptr; }
     if (p->d_XT) { cudaFree(p->d_XT); p->d_XT = nullptr; p->XT_bytes = 0; p->tc_mt = 0; p->tc_split = 0; }
     cudaError_t e = cudaMalloc(&p->d_X, bytes);
     if (e != cudaSuccess) { p->d_X = nullptr; return cuda_status(e, "precond_factor: allocating the factors"); }
@@ -970,7 +1275,8 @@ extern "C" helm_status precond_factor(helm_problem* p, helm_prec prec, void* str
         if (e != cudaSuccess) return cuda_status(e, "precond_factor: resetting the interface-stage counters");
     }
     {
-        const helm_status ks = p->sopts.boundary_operators ? build_boundary_operators(p, st) : HELM_OK;
+        helm_status ks = p->sopts.boundary_operators ? build_boundary_operators(p, st) : HELM_OK;
+        if (ks == HELM_OK && p->habc) ks = habc_precompute(p, st);
         if (ks != HELM_OK) return ks;
     }
     p->factored = 1;
@@ -990,7 +1296,7 @@ static helm_status ensure_pc_ws(helm_problem* p, int nrhs) {
     free_pc_ws(p);
     const size_t elem = p->prec == HELM_PREC_C64 ? sizeof(float2) : sizeof(double2);
     cudaError_t e = cudaSuccess;
-    for (int b = 0; b < 3 && e == cudaSuccess && p->ntrace > 0; ++b)
+    for (int b = 0; b < (p->habc ? 4 : 3) && e == cudaSuccess && p->ntrace > 0; ++b)
         e = cudaMalloc(&p->d_trace[b], (size_t)p->ntrace * nrhs * elem);
     if (e == cudaSuccess) e = cudaMalloc(&p->d_yws, (size_t)p->N() * nrhs * elem);
     if (e == cudaSuccess && tc_used(p, nrhs)) {
@@ -1008,7 +1314,7 @@ static helm_status ensure_pc_ws(helm_problem* p, int nrhs) {
 // ntrace*nrhs values, the solve workspace (N*nrhs), 3*nrhs norms and
 // kPartialBlocks*nrhs partial sums
 struct PcWork {
-    void* trace[3];
+    void* trace[4];                  // B, X, Y (and U with the HABC transmission)
     void* yws;
     double* norm;
     double* partial;
@@ -1049,7 +1355,7 @@ static bool run_sweep_persistent(helm_problem* p, const PcWork& w, int sched, in
     a.nrhs = nrhs;
     a.ntrace = p->ntrace;
     a.K = (const T*)p->d_K;
-    a.tc = sizeof(R) == 4 ? (const TraceCoef<T>*)p->d_tc64 : (const TraceCoef<T>*)p->d_tc128;
+    a.tc = stage_tc<T>(p);
     for (int b = 0; b < 3; ++b) a.bufs[b] = w.trace[b];
     a.err = p->d_err;
     double bytes = 0, flops = 0;
@@ -1140,7 +1446,7 @@ static helm_status tune_shape_t(helm_problem* p, int nrhs, cudaStream_t st) {
     ia.nrhs = nrhs;
     ia.ntrace = p->ntrace;
     ia.K = (const T*)p->d_K;
-    ia.tc = sizeof(R) == 4 ? (const TraceCoef<T>*)p->d_tc64 : (const TraceCoef<T>*)p->d_tc128;
+    ia.tc = stage_tc<T>(p);
     ia.gin0 = (const T*)p->d_trace[BUF_X];
     ia.mask = 15;
     ia.dst = (T*)p->d_trace[BUF_B];
@@ -1258,7 +1564,7 @@ static helm_status run_stage_t(helm_problem* p, const PcWork& w, const PcCtx& cx
     const double* rinv = cx.rinv;
     const double* rsc = cx.rsc;
     const bool tc = cx.tc;
-    T* buf[3] = {(T*)w.trace[0], (T*)w.trace[1], (T*)w.trace[2]};
+    T* buf[4] = {(T*)w.trace[0], (T*)w.trace[1], (T*)w.trace[2], (T*)w.trace[3]};
     auto B = [&](int id) -> T* { return id < 0 ? nullptr : buf[id]; };
     if (sd.iface && p->d_K) {
         IfaceArgs<R> ia{};
@@ -1266,8 +1572,8 @@ static helm_status run_stage_t(helm_problem* p, const PcWork& w, const PcCtx& cx
         ia.subs = p->d_stage_subs + sd.sub_off;
         ia.nrhs = nrhs;
         ia.ntrace = p->ntrace;
-        ia.K = (const T*)p->d_K;
-        ia.tc = sizeof(R) == 4 ? (const TraceCoef<T>*)p->d_tc64 : (const TraceCoef<T>*)p->d_tc128;
+        ia.K = (const T*)stage_kmat(p, sd.kmat);
+        ia.tc = stage_tc<T>(p);
         ia.gin0 = B(sd.in0); ia.gin1 = B(sd.in1);
         ia.mask = sd.mask;
         ia.dst = B(sd.dst); ia.dst2 = B(sd.dst2); ia.base = B(sd.base); ia.sub = B(sd.sub);
@@ -1299,7 +1605,7 @@ static helm_status run_stage_t(helm_problem* p, const PcWork& w, const PcCtx& cx
     a.ntrace = p->ntrace;
     a.wstride = p->N();
     a.X = (const T*)p->d_X;
-    a.tc = sizeof(R) == 4 ? (const TraceCoef<T>*)p->d_tc64 : (const TraceCoef<T>*)p->d_tc128;
+    a.tc = stage_tc<T>(p);
     a.src = sd.src;
     a.r = r;
     a.rscale = rinv;
@@ -1358,12 +1664,60 @@ static helm_status run_stage_t(helm_problem* p, const PcWork& w, const PcCtx& cx
     return HELM_OK;
 }
 
+// With the HABC transmission the lifting is a base solve of the source whose boundary
+// values u_f (written as outgoing data with the identity coefficients, i.e. into the
+// neighbours' slots) are swapped into U, then b = Lq u_f as an interface stage into
+// the lifting's outputs (k_habc.cu)
+template <typename R>
+static helm_status habc_lifting_t(helm_problem* p, const PcWork& w, const PcCtx& cx, const StageDesc& lift,
+                                  const double2* r, int nrhs, cudaStream_t st) {
+    using T = Cx<R>;
+    StageDesc a = lift;
+    a.dst = BUF_B; a.dst2 = BUF_NONE; a.base = a.sub = BUF_NONE; a.mask = 15; a.final_ = 0;
+    helm_status s = run_stage_t<R>(p, w, cx, a, r, nullptr, nrhs, st);
+    if (s != HELM_OK) return s;
+    launch_trace_swap<T>((const T*)w.trace[BUF_B], (T*)w.trace[BUF_U], p->d_swap, p->ntrace, nrhs, st);
+    StageDesc g = lift;
+    g.iface = 1; g.src = 0; g.in0 = BUF_U; g.in1 = BUF_NONE; g.mask = 15; g.final_ = 0; g.kmat = KMAT_LQ;
+    return run_stage_t<R>(p, w, cx, g, r, nullptr, nrhs, st);
+}
+// ... and the reconstruction a base solve with the source and the boundary datum
+// D1 g + D2 u_f (g = in0 (+ in1)): D2 u_f into t1, D1 g + t1 into t2 (both in the
+// neighbours' slots), swapped into t1, the incoming data of the base solves
+template <typename R>
+static helm_status habc_recon_t(helm_problem* p, const PcWork& w, const PcCtx& cx, const StageDesc& rec, int in0,
+                                int in1, int t1, int t2, const double2* r, double2* z, int nrhs, cudaStream_t st) {
+    using T = Cx<R>;
+    StageDesc g = rec;
+    g.iface = 1; g.src = 0; g.mask = 15; g.dst2 = BUF_NONE; g.sub = BUF_NONE; g.final_ = 0;
+    g.in0 = BUF_U; g.in1 = BUF_NONE; g.base = BUF_NONE; g.dst = t1; g.kmat = KMAT_D2;
+    helm_status s = run_stage_t<R>(p, w, cx, g, r, nullptr, nrhs, st);
+    if (s != HELM_OK) return s;
+    g.in0 = in0; g.in1 = in1; g.base = t1; g.dst = t2; g.kmat = KMAT_D1;
+    s = run_stage_t<R>(p, w, cx, g, r, nullptr, nrhs, st);
+    if (s != HELM_OK) return s;
+    launch_trace_swap<T>((const T*)w.trace[t2], (T*)w.trace[t1], p->d_swap, p->ntrace, nrhs, st);
+    StageDesc f = rec;
+    f.in0 = t1; f.in1 = BUF_NONE;
+    return run_stage_t<R>(p, w, cx, f, r, z, nrhs, st);
+}
+
 template <typename R>
 static helm_status run_precond_t(helm_problem* p, const PcWork& w, int sched, const double2* r, double2* z, int nrhs,
                                  cudaStream_t st) {
     const PcCtx cx = precond_prologue<R>(p, w, r, nrhs, st);
     const std::vector<StageDesc>& stg = p->sched[sched];
+    const bool habc = p->habc && stg.size() > 2;
     for (size_t i = 0; i < stg.size(); ++i) {
+        if (habc && i == 0) {
+            const helm_status s = habc_lifting_t<R>(p, w, cx, stg[0], r, nrhs, st);
+            if (s != HELM_OK) return s;
+            continue;
+        }
+        if (habc && i + 1 == stg.size()) {
+            // after the sweep B is free (and U once D2 has read it)
+            return habc_recon_t<R>(p, w, cx, stg[i], stg[i].in0, stg[i].in1, BUF_B, BUF_U, r, z, nrhs, st);
+        }
         if (i == 1 && stg.size() > 2) {
             helm_status s = HELM_OK;
             if (run_sweep_persistent<R>(p, w, sched, nrhs, st, s)) {
@@ -1383,8 +1737,8 @@ static helm_status run_precond(helm_problem* p, int sched, const double2* r, dou
     if (s != HELM_OK) return s;
     s = tune_shape(p, nrhs, st);
     if (s != HELM_OK) return s;
-    const PcWork w{{p->d_trace[0], p->d_trace[1], p->d_trace[2]}, p->d_yws, p->d_pc_norm, p->d_pc_partial,
-                   p->d_escr, p->d_r64};
+    const PcWork w{{p->d_trace[0], p->d_trace[1], p->d_trace[2], p->d_trace[3]}, p->d_yws, p->d_pc_norm,
+                   p->d_pc_partial, p->d_escr, p->d_r64};
     return p->prec == HELM_PREC_C64 ? run_precond_t<float>(p, w, sched, r, z, nrhs, st)
                                     : run_precond_t<double>(p, w, sched, r, z, nrhs, st);
 }
@@ -1520,7 +1874,8 @@ extern "C" helm_status precond_apply_noalloc(helm_problem* p, int sched, const h
     const bool tc = p->prec == HELM_PREC_C64 && tc_used(p, nrhs);
     const size_t ebytes = tc ? round256((size_t)2 * p->etot * nrhs * sizeof(float2)) : 0;
     const size_t rbytes = tc ? round256((size_t)p->N() * nrhs * sizeof(float2)) : 0;
-    const size_t need = 3 * tbytes + ybytes + nbytes + pbytes + ebytes + rbytes;
+    const int nbuf = p->habc ? 4 : 3;                 // the HABC keeps the liftings' boundary values
+    const size_t need = nbuf * tbytes + ybytes + nbytes + pbytes + ebytes + rbytes;
     if (need > (size_t)HELM_NOALLOC_SCRATCH_BYTES) {
         char buf[256];
         snprintf(buf, sizeof buf,
@@ -1540,9 +1895,10 @@ extern "C" helm_status precond_apply_noalloc(helm_problem* p, int sched, const h
         g_noalloc_ptr[dev].store(base);
     }
     unsigned char* b = (unsigned char*)base;
-    unsigned char* tail = b + 3 * tbytes + ybytes + nbytes + pbytes;
-    PcWork w{{b, b + tbytes, b + 2 * tbytes}, b + 3 * tbytes, (double*)(b + 3 * tbytes + ybytes),
-             (double*)(b + 3 * tbytes + ybytes + nbytes), tc ? tail : nullptr, tc ? tail + ebytes : nullptr};
+    unsigned char* v = b + nbuf * tbytes;             // after the interface buffers
+    unsigned char* tail = v + ybytes + nbytes + pbytes;
+    PcWork w{{b, b + tbytes, b + 2 * tbytes, nbuf == 4 ? b + 3 * tbytes : nullptr}, v, (double*)(v + ybytes),
+             (double*)(v + ybytes + nbytes), tc ? tail : nullptr, tc ? tail + ebytes : nullptr};
     cudaStream_t st = (cudaStream_t)stream;
     return p->prec == HELM_PREC_C64 ? run_precond_t<float>(p, w, sched, (const double2*)r, (double2*)z, nrhs, st)
                                     : run_precond_t<double>(p, w, sched, (const double2*)r, (double2*)z, nrhs, st);
@@ -1679,7 +2035,8 @@ static helm_status device_cycle(helm_problem* p, KrylovWS& kw, long long N, int 
     const void* key = reinterpret_cast<const void*>((intptr_t)(1000 + (int)sizeof(VT) + 64 * ops.dev_tag));
     helm_problem::PcGraph* gr = nullptr;
     for (auto& g : p->graphs)
-        if (g.sched == -2 && g.r == key && g.nrhs == nrhs && g.gen == kw.gen && g.m == m) gr = &g;
+        if (g.sched == -2 && g.r == key && g.nrhs == nrhs && g.gen == kw.gen && g.m == m && g.limit == p->wait_cycles)
+            gr = &g;
     if (!gr) {
         // graphs of earlier workspaces hold freed pointers: drop them
         for (size_t i = 0; i < p->graphs.size();) {
@@ -1723,7 +2080,7 @@ static helm_status device_cycle(helm_problem* p, KrylovWS& kw, long long N, int 
                 e = launch_cgs2_step<VT>(KV, vsk, N, 0, N, nrhs, kw.active, kw.hsum, ld, kw.rn + 3 * nrhs, kw.need,
                                          kw.H, ld, (long long)ld * m, kw.cs, kw.sn, kw.g, ld, kw.est, kw.invh,
                                          kw.mgs_part, kw.mgs_bar, p->d_err, grid, p->cap_stream, kw.ctl, m - 1,
-                                         ops.dev_w_src, ops.dev_v_out1, ops.dev_v_out2);
+                                         ops.dev_w_src, ops.dev_v_out1, ops.dev_v_out2, p->wait_cycles);
             if (q == HELM_OK && e == cudaSuccess)
                 launch_arnoldi_ctl(kw.ctl, kw.est, kw.thr, kw.active, kw.iters, kw.jcount, maxit, nrhs, p->d_err, h,
                                    p->cap_stream);
@@ -1746,6 +2103,7 @@ static helm_status device_cycle(helm_problem* p, KrylovWS& kw, long long N, int 
         g.tmpl = graph;
         g.gen = kw.gen;
         g.m = m;
+        g.limit = p->wait_cycles;
         p->graphs.push_back(g);
         gr = &p->graphs.back();
     }
@@ -1883,7 +2241,8 @@ static helm_status fgmres_core(helm_problem* p, KrylovWS& kw, long long n, int n
                 prof_begin(p, HELM_K_ORTHO, st);
                 // (FP64 vectors only: use_mgs is false for float2)
                 cudaError_t e = launch_mgs(kw.V, vsk, N, reinterpret_cast<double2*>(Vn), j + 1, N, nrhs, kw.active, kw.hsum, ld,
-                                           kw.rn + 3 * nrhs, kw.mgs_part, kw.mgs_bar, p->d_err, mgs_grid_n, st);
+                                           kw.rn + 3 * nrhs, kw.mgs_part, kw.mgs_bar, p->d_err, mgs_grid_n, st,
+                                           p->wait_cycles);
                 prof_end(p, HELM_K_ORTHO, (j + 3) * 16.0 * N * nact, st, (16.0 * (j + 1) + 4.0) * N * nact);
                 if (e != cudaSuccess) return cuda_status(e, "modified Gram-Schmidt launch");
                 launch_hessenberg_step(kw.H, ld, (long long)ld * m, kw.cs, kw.sn, kw.g, ld, kw.hsum, ld,
@@ -1898,7 +2257,8 @@ static helm_status fgmres_core(helm_problem* p, KrylovWS& kw, long long n, int n
                 prof_begin(p, HELM_K_ORTHO, st);
                 cudaError_t e = launch_cgs2_step<VT>(KV, vsk, N, j, N, nrhs, kw.active, kw.hsum, ld, kw.rn + 3 * nrhs,
                                                  kw.need, kw.H, ld, (long long)ld * m, kw.cs, kw.sn, kw.g, ld, kw.est,
-                                                 kw.invh, kw.mgs_part, kw.mgs_bar, p->d_err, cgs2_grid_n, st);
+                                                 kw.invh, kw.mgs_part, kw.mgs_bar, p->d_err, cgs2_grid_n, st,
+                                                 nullptr, 0, nullptr, nullptr, nullptr, p->wait_cycles);
                 prof_end(p, HELM_K_ORTHO, (2.0 * j + 5) * (double)sizeof(VT) * N * nact, st,
                          (16.0 * (j + 1) + 4.0) * N * nact);
                 if (e != cudaSuccess) return cuda_status(e, "Gram-Schmidt launch");
@@ -2003,15 +2363,15 @@ static helm_status run_precond_iface_t(helm_problem* p, int sched, const double2
     // typed views of the interface workspace (allocated by ensure_kw just above)
     VT* const kb = reinterpret_cast<VT*>(p->kwi.b);      // interface right-hand side
     VT* const kx = reinterpret_cast<VT*>(p->kwi.x);      // interface iterate
-    const PcWork w{{p->d_trace[0], p->d_trace[1], p->d_trace[2]}, p->d_yws, p->d_pc_norm, p->d_pc_partial,
-                   p->d_escr, p->d_r64};
+    const PcWork w{{p->d_trace[0], p->d_trace[1], p->d_trace[2], p->d_trace[3]}, p->d_yws, p->d_pc_norm,
+                   p->d_pc_partial, p->d_escr, p->d_r64};
     T* tB = (T*)w.trace[BUF_B];
     T* tX = (T*)w.trace[BUF_X];
     T* tY = (T*)w.trace[BUF_Y];
     const long long tot = nt * nrhs;
     const PcCtx cx = precond_prologue<R>(p, w, r, nrhs, st);
     // b: outgoing data of the liftings
-    s = run_stage_t<R>(p, w, cx, stg.front(), r, z, nrhs, st);
+    s = p->habc ? habc_lifting_t<R>(p, w, cx, stg.front(), r, nrhs, st) : run_stage_t<R>(p, w, cx, stg.front(), r, z, nrhs, st);
     if (s != HELM_OK) return s;
     launch_trace_to<T, VT>(tB, nullptr, 1, kb, tot, st);
     // (I - S) v: one interface stage over every subdomain writes S v - v into B
@@ -2127,6 +2487,7 @@ static helm_status run_precond_iface_t(helm_problem* p, int sched, const double2
     launch_trace_from<VT, T>(kx, tX, (T*)nullptr, tot, st);
     StageDesc sR = stg.back();
     sR.in0 = BUF_X; sR.in1 = BUF_NONE;
+    if (p->habc) return habc_recon_t<R>(p, w, cx, sR, BUF_X, BUF_NONE, BUF_B, BUF_Y, r, z, nrhs, st);
     return run_stage_t<R>(p, w, cx, sR, r, z, nrhs, st);
 }
 
@@ -2174,10 +2535,12 @@ static helm_status gmres_impl(helm_problem* p, const double2* f, double2* u, int
     std::vector<int> iters;
     std::vector<double> relres;
     p->persistent = o.persistent;
+    p->wait_cycles = o.wait_cycles;
     p->inner_hist_taken = false;
     s = fgmres_core(p, p->kw, N, nrhs, o.restart, o.maxit, o.tol, bnorm, u, o.x0_given != 0, o.ortho,
                     o.hist, ops, iters, relres, "gmres_solve", st);
     p->persistent = 0;
+    p->wait_cycles = 0;
     if (s != HELM_OK) return s;
     bool ok = true;
     for (int k = 0; k < nrhs; ++k) {
@@ -2210,6 +2573,7 @@ extern "C" helm_status gmres_solve(helm_problem* p, const helm_c128* f, helm_c12
     if (o.inner_maxit < 0) return arg_error("gmres_solve: inner_maxit must be >= 0");
     if (o.persistent < 0 || o.persistent > 2) return arg_error("gmres_solve: persistent must be 0, 1 or 2");
     if (o.inner_fp64 != 0 && o.inner_fp64 != 1) return arg_error("gmres_solve: inner_fp64 must be 0 or 1");
+    if (o.wait_cycles < 0) return arg_error("gmres_solve: wait_cycles must be >= 0");
     if (o.inner_maxit > 0 && (o.inner_restart < 1 || o.inner_restart > 500))
         return arg_error("gmres_solve: inner_restart must be in 1..500");
     if (o.inner_maxit > 0 && !(o.inner_tol > 0)) return arg_error("gmres_solve: inner_tol must be > 0");
@@ -2222,6 +2586,15 @@ extern "C" helm_status gmres_solve(helm_problem* p, const helm_c128* f, helm_c12
     const size_t held = (size_t)p->kw.nrhs * ((size_t)2 * p->kw.restart + 1) * N * sizeof(double2);
     const size_t per_rhs = ((size_t)2 * o.restart + 1) * N * sizeof(double2) + (size_t)N * 2 * sizeof(double2);
     long long fit = (long long)((0.6 * (double)(freeb + held)) / (double)per_rhs);
+    if (p->sopts.device_budget > 0) {
+        // within what the factors leave of the handle's budget
+        const double left = (double)p->sopts.device_budget - (double)(p->X_bytes + p->XT_bytes + p->K_bytes);
+        fit = std::min(fit, (long long)(std::max(0.0, left) / (double)per_rhs));
+        if (fit < 1) {
+            set_error("gmres_solve: the Krylov workspace of one right-hand side does not fit in the device budget");
+            return HELM_ERR_OOM;
+        }
+    }
     if (fit < 1) {
         set_error("gmres_solve: the Krylov workspace of one right-hand side does not fit in device memory; "
                   "lower the restart length");

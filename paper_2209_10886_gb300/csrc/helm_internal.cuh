@@ -126,7 +126,9 @@ struct SubDev {
 template <typename T> struct TraceCoef { T cin, ca, cb; };
 
 // Interface-buffer identifiers used by the stage lists.
-enum Buf { BUF_NONE = -1, BUF_B = 0, BUF_X = 1, BUF_Y = 2 };
+// BUF_U (HABC transmission only): the boundary values of the liftings' base solves,
+// kept from the lifting to the reconstruction
+enum Buf { BUF_NONE = -1, BUF_B = 0, BUF_X = 1, BUF_Y = 2, BUF_U = 3 };
 
 struct StageDesc {
     int iface;                 // 1: zero volume source and no volume output: boundary-operator GEMV
@@ -138,7 +140,12 @@ struct StageDesc {
     int final_;                // 1: write the volume solution into z
     int sub_off;               // offset of `subs` in the device stage-list array
     int tc_off[2], tc_n[2];    // the same subdomains split by tensor-core tile count (1, 2): offsets, counts
+    int kmat = 0;              // interface stages: the per-subdomain matrix they apply (KMAT_*)
 };
+// matrices of the interface stages: K (or, with the HABC transmission, Q), and the
+// HABC lifting (Lq) and reconstruction (D1 on the incoming data, D2 on the lifting's
+// boundary values) maps
+enum { KMAT_K = 0, KMAT_LQ = 1, KMAT_D1 = 2, KMAT_D2 = 3 };
 
 // launch parameters of the fused stage kernel (passed by value)
 template <typename R> struct StageArgs {
@@ -335,6 +342,34 @@ void launch_scale_from_norm(const double* norm2, double* inv, double* scale, int
 // device-driven Arnoldi loop: step bookkeeping and the loop condition (ctl[0] = j, ctl[1] = restart)
 void launch_arnoldi_ctl(int* ctl, const double* est, const double* thr, int* active, int* iters, int* jcount,
                         int maxit, int nrhs, const int* err, cudaGraphConditionalHandle h, cudaStream_t st);
+// HABC transmission (k_habc.cu): side operators M_s = I - (h/2) T_s per slot, batched
+// Gauss-Jordan inversion, batched complex GEMM, the precomputed stage matrices, and the
+// trace swap (slot (i, j) <-> (j, i))
+cudaError_t launch_habc_sides(const double* m2, int nx, double h, double omega, int n_pade, double phi,
+                              const int* slot_sub, const int* slot_side, const int* slot_len,
+                              const long long* slot_moff, int nslots, int max_len, const SubDev* subtab, double2* M,
+                              double2* Y, cudaStream_t st);
+int gj_grid(int maxn);
+size_t gj_mat_bytes();
+void gj_mat_fill(void* dst, int i, double2* A, int n, int lda);
+cudaError_t launch_gj_inverse(const void* mats, int nmat, int maxn, double2* pub, unsigned* bar, int* err, int* info,
+                              cudaStream_t st);
+size_t gemm_prob_bytes();
+void gemm_prob_fill(void* dst, int i, const double2* A, const double2* B, double2* C, int m, int n, int k, int lda,
+                    int ldb, int ldc, double2 alpha, int accumulate);
+cudaError_t launch_zgemm_batched(const void* probs, int nprob, int max_m, int max_n, cudaStream_t st);
+size_t habc_sub_bytes();
+void habc_sub_fill(void* dst, int i, long long koff, long long toff, int Lb, const int* bo, const int* len,
+                   const long long* moff, const int* tin);
+template <typename T>
+cudaError_t launch_habc_form(const void* subs, int nsub, int max_Lb, const T* K, const TraceCoef<double2>* tc,
+                             double2* K64, const double2* KR, double2* W, int phase, cudaStream_t st);
+template <typename T>
+cudaError_t launch_habc_final(const void* subs, int nsub, int max_Lb, const double2* Mside,
+                              const TraceCoef<double2>* tc, const double2* P1, const double2* RP, const double2* W,
+                              const double2* RW, T* Q, T* Lq, T* D1, T* D2, cudaStream_t st);
+template <typename T>
+void launch_trace_swap(const T* in, T* out, const int* swp, long long ntrace, int nrhs, cudaStream_t st);
 // adjoint
 void launch_receiver_residual(const double2* u, long long N, const int* rec, int nrec, const double2* d,
                               int nsrc, double2* res, double* partial, cudaStream_t st);

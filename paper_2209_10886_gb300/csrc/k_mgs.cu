@@ -20,7 +20,7 @@
 namespace {
 
 constexpr int MT = 256;                          // threads per CTA
-constexpr long long BAR_LIMIT = 2000000000LL;    // cycles (~1 s)
+constexpr long long BAR_LIMIT = 2000000000LL;    // cycles (~1 s): the default limit of a grid barrier
 
 struct MgsArgs {
     const double2* V;          // basis: v_k of RHS r at V + k*vsk + r*vsr
@@ -36,6 +36,7 @@ struct MgsArgs {
     double2* partial;          // [2 * gridDim.x] scratch of partial sums
     unsigned* bar;             // [0] arrival count, [1] generation (zero before the first launch)
     int* err;
+    long long limit;           // cycles a grid barrier waits before it gives up
 };
 
 __device__ __forceinline__ double2 warp_sum2(double2 v) {
@@ -47,7 +48,7 @@ __device__ __forceinline__ double2 warp_sum2(double2 v) {
 }
 
 // grid-wide barrier over co-resident CTAs; returns false when the wait expired
-__device__ bool grid_barrier(unsigned* bar, int* err, int* sflag) {
+__device__ bool grid_barrier(unsigned* bar, int* err, int* sflag, long long limit) {
     // bar[0] counts arrivals, bar[1] is the generation; the last arrival resets the count
     // and publishes the next generation with release semantics, the others poll it with
     // acquire loads (CTA writes before the barrier are ordered by __syncthreads and the
@@ -65,7 +66,7 @@ __device__ bool grid_barrier(unsigned* bar, int* err, int* sflag) {
             unsigned cur;
             do {
                 asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(bar + 1) : "memory");
-                if (cur == g && clock64() - t0 > BAR_LIMIT) {
+                if (cur == g && clock64() - t0 > limit) {
                     atomicExch(err, (int)HELM_ERR_TIMEOUT);
                     *sflag = 1;
                     break;
@@ -123,7 +124,7 @@ __global__ void __launch_bounds__(MT) mgs_kernel(MgsArgs a) {
     auto reduce = [&](double2 v, double2& out) -> bool {
         double2* part = a.partial + (s & 1u) * gridDim.x;
         block_partial(v, part, sh);
-        if (!grid_barrier(a.bar, a.err, &sflag)) return false;
+        if (!grid_barrier(a.bar, a.err, &sflag, a.limit)) return false;
         out = sum_partials(part, sh);
         ++s;
         return true;
@@ -240,7 +241,7 @@ __global__ void __launch_bounds__(NT) mgs_smem_kernel(MgsArgs a, int L) {
     auto reduce = [&](double2 v, double2& out) -> bool {
         double2* part = a.partial + (s & 1u) * gridDim.x;
         block_partial(v, part, sh);
-        if (!grid_barrier(a.bar, a.err, &sflag)) return false;
+        if (!grid_barrier(a.bar, a.err, &sflag, a.limit)) return false;
         out = sum_partials(part, sh);
         ++s;
         return true;
@@ -383,6 +384,7 @@ struct Cgs2Args {
     const VT* wsrc;            // when set, w = -wsrc (RHS r at wsrc + r*vsr) instead of the slot j + 1
     VT* vout1;                 // when set, v_{j+1} is also written here and to vout2 (RHS r at + r*vsr)
     VT* vout2;
+    long long limit;           // cycles a grid barrier waits before it gives up
 };
 
 constexpr int CT = 256;        // threads per CTA of the fused step
@@ -434,7 +436,7 @@ __global__ void __launch_bounds__(CT, 1) cgs2_step_kernel(Cgs2Args<VT> a) {
     // coalesced along k, few per thread); a butterfly over the lanes of equal column,
     // then the CT / 32 warp sums in order
     auto grid_reduce = [&](double2* part, int cnt) -> bool {
-        if (!grid_barrier(a.bar, a.err, &sflag)) return false;
+        if (!grid_barrier(a.bar, a.err, &sflag, a.limit)) return false;
         const int G = (int)gridDim.x;
         for (int kb = 0; kb < cnt; kb += 32) {
             const int rem = min(32, cnt - kb);
@@ -674,7 +676,7 @@ __global__ void __launch_bounds__(CT, 1) cgs2_group_kernel(Cgs2Args<VT> a, int G
     // every CTA adds column k < cnt of all CTAs' partials (stride CS) in the same order
     // into hv[k]: lane = column, warps over CTA groups, a butterfly, the warp sums in order
     auto grid_reduce = [&](double2* part, int cnt) -> bool {
-        if (!grid_barrier(a.bar, a.err, &sflag)) return false;
+        if (!grid_barrier(a.bar, a.err, &sflag, a.limit)) return false;
         const int Gd = (int)gridDim.x;
         for (int kb = 0; kb < cnt; kb += 32) {
             const int rem = min(32, cnt - kb);
@@ -958,8 +960,9 @@ long long mgs_max_n(int grid) { return (long long)grid * MT * 32; }
 // w <- (w - V V^H w) / ||.|| by modified Gram-Schmidt for every active RHS.
 cudaError_t launch_mgs(const double2* V, long long vsk, long long vsr, double2* w, int nvec, long long n, int nrhs,
                        const int* active, double2* hcol, int ldh, double* hnorm, double2* partial, unsigned* bar,
-                       int* err, int grid, cudaStream_t st) {
-    MgsArgs a{V, vsk, vsr, w, nvec, n, nrhs, active, hcol, ldh, hnorm, partial, bar, err};
+                       int* err, int grid, cudaStream_t st, long long limit) {
+    MgsArgs a{V, vsk, vsr, w, nvec, n, nrhs, active, hcol, ldh, hnorm, partial, bar, err,
+              limit > 0 ? limit : BAR_LIMIT};
     {
         // basis streamed through shared memory when two slices of every CTA fit; the
         // slice start must stay 16-byte aligned (double2 elements: always)
@@ -1017,11 +1020,11 @@ cudaError_t launch_cgs2_step(const VT* V, long long vsk, long long vsr, int j, l
                              const int* active, double2* hsum, int ldh, double* hnorm, int* need, double2* H, int ldH,
                              long long hs, double2* cs, double2* sn, double2* g, int ldg, double* est, double* invh,
                              double2* partial, unsigned* bar, int* err, int grid, cudaStream_t st, const int* dj,
-                             int jmax, const VT* wsrc, VT* vout1, VT* vout2) {
+                             int jmax, const VT* wsrc, VT* vout1, VT* vout2, long long limit) {
     if (grid <= 0) return cudaErrorInvalidValue;
     const int L = (int)((n + grid - 1) / grid);
     Cgs2Args<VT> a{V, vsk, vsr, j, n, nrhs, active, hsum, ldh, hnorm, need, H, ldH, hs, cs, sn, g, ldg, est, invh,
-                   partial, bar, err, L, dj, wsrc, vout1, vout2};
+                   partial, bar, err, L, dj, wsrc, vout1, vout2, limit > 0 ? limit : BAR_LIMIT};
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(CT);
@@ -1062,7 +1065,7 @@ cudaError_t launch_cgs2_step(const VT* V, long long vsk, long long vsr, int j, l
     template cudaError_t launch_cgs2_step<VT>(const VT*, long long, long long, int, long long, int, const int*,   \
                                               double2*, int, double*, int*, double2*, int, long long, double2*,   \
                                               double2*, double2*, int, double*, double*, double2*, unsigned*, int*, \
-                                              int, cudaStream_t, const int*, int, const VT*, VT*, VT*);
+                                              int, cudaStream_t, const int*, int, const VT*, VT*, VT*, long long);
 HELM_CGS2_INST(double2)
 HELM_CGS2_INST(float2)
 #undef HELM_CGS2_INST

@@ -21,7 +21,7 @@ HEADER_PATH = os.path.join(os.path.dirname(_HERE), "include", "helm.h")
 
 PREC = {"c128": 0, "c64": 1}
 SCHED = {"BSP": 0, "SP": 1, "BSP_NONOVERLAP": 2}
-TRANSMISSION = {"optimized": 0, "impedance": 1}
+TRANSMISSION = {"optimized": 0, "impedance": 1, "habc": 2}
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_STATE", 5: "ERR_NO_CONVERGENCE",
           6: "ERR_TIMEOUT", 7: "ERR_UNSUPPORTED"}
 
@@ -38,13 +38,14 @@ class HelmOpts(ctypes.Structure):
                 ("hist", ctypes.POINTER(ctypes.c_double)), ("ortho", ctypes.c_int),
                 ("inner_maxit", ctypes.c_int), ("inner_restart", ctypes.c_int), ("inner_tol", ctypes.c_double),
                 ("persistent", ctypes.c_int), ("inner_hist", ctypes.POINTER(ctypes.c_double)),
-                ("inner_fp64", ctypes.c_int)]
+                ("inner_fp64", ctypes.c_int), ("wait_cycles", ctypes.c_longlong)]
 
 
 class HelmSetupOpts(ctypes.Structure):
     _fields_ = [("transmission", ctypes.c_int), ("tc_scale", ctypes.c_double),
                 ("boundary_operators", ctypes.c_int), ("tensor_cores", ctypes.c_int),
-                ("tc_min_rhs", ctypes.c_int), ("autotune", ctypes.c_int), ("tc_iface_min_ctas", ctypes.c_int)]
+                ("tc_min_rhs", ctypes.c_int), ("autotune", ctypes.c_int), ("tc_iface_min_ctas", ctypes.c_int),
+                ("device_budget", ctypes.c_size_t), ("n_pade", ctypes.c_int), ("pade_phi", ctypes.c_double)]
 
 
 class HelmInfo(ctypes.Structure):
@@ -145,19 +146,24 @@ class Problem:
     "tf32", False) with ``tc_min_rhs``; ``autotune`` (time the interface-stage
     shapes at the first application per RHS count); ``tc_iface_min_ctas``
     (interface stages of fewer CTAs keep the CUDA-core form when the tensor-core
-    form is chosen; -1: two per SM).
+    form is chosen; -1: two per SM); ``device_budget`` (bytes the handle's large arrays
+    may take, 0: no limit); ``n_pade`` and ``pade_phi`` of the "habc" transmission (the
+    Pade HABC of the paper's experiments, with ``tc_scale`` the Robin parameter of the
+    factored base problem).
     """
 
     def __init__(self, n_x, n_y, h, omega, m2, N1, N2, xcuts=None, ycuts=None,
                  transmission="optimized", tc_scale=1.0, boundary_operators=True, tensor_cores=True,
-                 tc_min_rhs=16, autotune=True, tc_iface_min_ctas=-1):
+                 tc_min_rhs=16, autotune=True, tc_iface_min_ctas=-1, device_budget=0, n_pade=8,
+                 pade_phi=math.pi / 3):
         L = lib()
         if not (m2.is_cuda and m2.dtype == torch.float64 and m2.numel() == n_x * n_y):
             raise TypeError("m2 must be a float64 CUDA tensor with n_x*n_y values")
         m2 = m2.contiguous()
         tcm = {False: 0, True: 1, "3xtf32": 1, "tf32": 2}[tensor_cores]
         so = HelmSetupOpts(TRANSMISSION[transmission], float(tc_scale), int(bool(boundary_operators)), tcm,
-                           int(tc_min_rhs), int(bool(autotune)), int(tc_iface_min_ctas))
+                           int(tc_min_rhs), int(bool(autotune)), int(tc_iface_min_ctas), int(device_budget),
+                           int(n_pade), float(pade_phi))
         xc = (ctypes.c_int * (N1 + 1))(*[int(v) for v in xcuts]) if xcuts is not None else None
         yc = (ctypes.c_int * (N2 + 1))(*[int(v) for v in ycuts]) if ycuts is not None else None
         h_ = ctypes.c_void_p()
@@ -196,14 +202,14 @@ class Problem:
 
     def solve(self, f, u=None, restart=50, maxit=1000, tol=1e-6, sched="BSP", x0=None, history=False,
               stream=None, raise_on_noconv=True, use_graph=False, inner_maxit=0, inner_restart=100, inner_tol=1e-4,
-              persistent=False, ortho="mgs", inner_fp64=False, inner_history=False):
+              persistent=False, ortho="mgs", inner_fp64=False, inner_history=False, wait_cycles=0):
         """Solve A u = h^2 f (FP64 FGMRES); returns (u, [(iters, relres)], history or None).
         ortho: "mgs" (volume default), "cgs2" or "cgs2_split" (see helm.h); inner_fp64: FP64
         interface Krylov vectors with complex64 factors (default: complex64 vectors);
         inner_history: keep the interface residual history of the first preconditioner
         application in self.last_inner_history (one list per RHS); persistent: False (stage
         launches), True / "barrier" or "dependency" (one cooperative launch per sweep, see
-        helm.h)."""
+        helm.h); wait_cycles: grid-barrier limit of the Gram-Schmidt kernels (0: ~1 s)."""
         f = _as_fields(f, self.N, "f")
         nrhs = f.numel() // self.N
         u = torch.empty_like(f) if u is None else u
@@ -214,7 +220,7 @@ class Problem:
                          use_graph=int(bool(use_graph)), inner_maxit=int(inner_maxit),
                          inner_restart=int(inner_restart), inner_tol=float(inner_tol),
                          persistent={False: 0, True: 1, "barrier": 1, "dependency": 2}.get(persistent, persistent),
-                         ortho=ORTHO[ortho], inner_fp64=int(bool(inner_fp64)))
+                         ortho=ORTHO[ortho], inner_fp64=int(bool(inner_fp64)), wait_cycles=int(wait_cycles))
         if hist is not None:
             o.hist = ctypes.cast(hist, ctypes.POINTER(ctypes.c_double))
         ihist = (ctypes.c_double * (max(1, int(inner_maxit)) * nrhs))() if inner_history else None

@@ -5,8 +5,9 @@ Tolerances (written per test):
   different elimination orders (block-tridiagonal Gauss-Jordan vs sparse LU);
   the difference is roundoff times the local condition number, <= 1e-10.
 * complex64 preconditioner vs the complex128 oracle: unit roundoff 6e-8
-  amplified by the block recursion over ~128 grid rows; bound 5e-4 (measured
-  values are printed with -s).
+  amplified by the block recursion over the grid rows (measured 4e-6..7e-6 for
+  64-row subdomains, 2.9e-5 for 131-row ones: an amplification of 60..500;
+  printed with -s); bound 1e-4.
 * Solutions: both sides solve to a true relative residual of 1e-9, so they
   agree to cond(A) * 1e-9; the bar is rel. L2 <= 1e-5.
 """
@@ -20,6 +21,8 @@ pytestmark = pytest.mark.gpu
 import workloads as W
 from oracle import Decomposition, Sweeper, assemble_operator
 from oracle.adjoint import misfit_gradient_direct
+
+C64_TOL = 1e-4       # rel. L2 of one complex64 preconditioner application vs the oracle
 
 
 @pytest.fixture(scope="module")
@@ -73,7 +76,7 @@ def test_matvec_matches_sparse_matrix(H):
         p.close()
 
 
-@pytest.mark.parametrize("prec,tol", [("c128", 1e-11), ("c64", 5e-4)])
+@pytest.mark.parametrize("prec,tol", [("c128", 1e-11), ("c64", C64_TOL)])
 def test_single_subdomain_is_direct_solve(H, prec, tol):
     w = W.workload("custom", n=75, N1=1, N2=1, medium="layered", seed=2)
     p, _ = make(H, w, prec)
@@ -114,11 +117,11 @@ def test_precond_apply_c64_matches_oracle(H, case):
     for k in range(5):
         e = rel(z[k], sw.precondition(r[k], "BSP"))
         print(f"{case} BSP c64 rhs{k}: rel {e:.2e}")
-        assert e <= 5e-4
+        assert e <= C64_TOL
     p.close()
 
 
-@pytest.mark.parametrize("prec,tol", [("c128", 1e-10), ("c64", 5e-4)])
+@pytest.mark.parametrize("prec,tol", [("c128", 1e-10), ("c64", C64_TOL)])
 def test_without_boundary_operators_matches_oracle(H, prec, tol):
     """Sweep steps as full block-tridiagonal solves (no K): the same operator."""
     w = CASES["uneven_4x3"]()

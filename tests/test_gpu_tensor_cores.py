@@ -9,9 +9,9 @@ accumulation (k_tc.cu).  Tolerances, from the arithmetic:
   path measures 4e-6..1e-5 against the oracle, an amplification of 60..170 by
   the block recursion over the grid rows, so 3xTF32 should land near
   170 x 4.8e-7 = 8e-5 (measured up to 1.6e-4: the tensor cores' FP32 accumulation
-  adds its own rounding).  Bar: 2e-3.
+  adds its own rounding).  Bar: 5e-4.
 * plain TF32 (tensor_cores="tf32"): u = 2^-11 = 4.9e-4 per operand, expected up
-  to 170 x 4.9e-4 = 8e-2, measured ~1.7e-3.  Bar: 2e-2.
+  to 170 x 4.9e-4 = 8e-2, measured ~1.7e-3.  Bar: 6e-3.
 The FGMRES solution does not inherit this error: the residual, the Arnoldi
 basis and the update stay FP64, so a solve to 1e-9 matches the direct solve to
 the same 1e-5 as the complex128 path.
@@ -30,8 +30,8 @@ pytestmark = pytest.mark.gpu
 import workloads as W
 from oracle import Decomposition, Sweeper, assemble_operator
 
-TF32_PRECOND_TOL = 2e-3      # rel. L2 of one 3xTF32 preconditioner application vs the oracle
-PLAIN_TF32_TOL = 2e-2        # the same with plain TF32 operands
+TF32_PRECOND_TOL = 5e-4      # rel. L2 of one 3xTF32 preconditioner application vs the oracle
+PLAIN_TF32_TOL = 6e-3        # the same with plain TF32 operands
 
 
 @pytest.fixture(scope="module")

@@ -88,9 +88,12 @@ def test_differentiation_gradient_matches_central_differences(H, diff_case):
     assert worst <= 1e-4
 
 
-# complex64 on the CUDA cores: bar 5e-4; 3xTF32 on the tensor cores: bar 2e-3 (the
-# derivation is in test_gpu_tensor_cores.py)
-@pytest.mark.parametrize("tensor_cores,bar", [(False, 5e-4), ("3xtf32", 2e-3)])
+# complex64 on the CUDA cores: measured 1.5e-5..1.6e-5, bar 6e-5; 3xTF32 on the tensor
+# cores: measured 8.6e-4, bar 3e-3.  The tensor-core form drops the lo x lo products
+# (2^-22 per product against FP32's 2^-24) and accumulates in the tensor cores' FP32
+# adders; over the 12 x 12 sweep of 128-row block recursions that costs ~50x the
+# CUDA-core form's error.  Neither reaches the solution: FP64 FGMRES corrects it.
+@pytest.mark.parametrize("tensor_cores,bar", [(False, 6e-5), ("3xtf32", 3e-3)])
 def test_batching_preconditioner_matches_oracle_at_full_size(H, tensor_cores, bar):
     w = W.workload("batching", nrhs=64)
     p = H.Problem(w.n, w.n, w.h, w.omega, cuda(w.m2, torch.float64), w.N1, w.N2, w.xcuts, w.ycuts,

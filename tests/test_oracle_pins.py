@@ -63,6 +63,22 @@ def test_operator_is_complex_symmetric_and_five_point():
     assert A.nnz == 5 * n * n - 4 * n
 
 
+def test_nested_dissection_solver_is_the_direct_solve():
+    """The oracle's fast direct solver (sparse LU of the grid matrix in nested-dissection
+    order, plus refinement) is a permutation of the same system: it must return what
+    scipy's spsolve returns, on a ragged grid too, and its order must be a permutation."""
+    from oracle.discretization import GridDirectSolver, nested_dissection_order
+    for n in (1, 5, 17, 40):
+        p = nested_dissection_order(n, n)
+        assert np.array_equal(np.sort(p), np.arange(n * n))
+    w = W.workload("custom", n=45, N1=2, N2=2, medium="layered", seed=6)
+    A = assemble_operator(w.n, w.h, w.omega, w.m2)
+    b = W.random_complex((2, w.N), 12)
+    solver = GridDirectSolver(A, w.n)
+    for k in range(2):
+        assert _rel(solver.solve(b[k]), spla.spsolve(A.tocsc(), b[k])) <= 1e-12
+
+
 def test_discrete_plane_wave_is_exact():
     """A discrete plane wave solves the interior stencil exactly when
     (kappa h)^2 = 4 - 2 cos(xi h) - 2 cos(eta h); with boundary data built from
