@@ -721,6 +721,7 @@ def gpu_arm(args):
                    "solve the boundary operators are reused across the interface iterations)"),
             "parallelism": f"replicas x{world}",
             "iface_shape": helm.iface_shape(p, w.nrhs),
+            "stage_shape": helm.stage_shape(p, w.nrhs),
             "profiled_pass": {"ms_per_step": ms_prof,
                               "note": "the same solves again with CUDA events around every launch (host-driven "
                                       "interface loop); kernel_time_ms_per_step and the roofline come from it"},

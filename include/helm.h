@@ -134,13 +134,15 @@ typedef struct {
                            cores (when tensor_cores != 0); default 16, minimum 1.  Below
                            16 the MMA columns are padded (N = 32 per 16 RHS) */
     int autotune;       /* 1 (default): the first preconditioner application with a given
-                           RHS count (2 or more) times the candidate launch shapes of the
-                           interface-stage kernel (RHS per block 2/4/8/16, K rows staged in
-                           shared memory or not) on the all-subdomain stage S, on the
-                           caller's stream, and keeps the fastest for this problem
-                           (with the tensor-core form among the candidates where
-                           tensor_cores allows it);
-                           0: fixed rules (see helm_iface_shape) */
+                           RHS count times candidate launch shapes on the caller's stream
+                           and keeps the fastest for this problem: for 2 or more RHS, the
+                           interface-stage kernel's (RHS per block 2/4/8/16, K rows staged
+                           in shared memory or not; the tensor-core form among them where
+                           tensor_cores allows it) on the all-subdomain stage S; for any
+                           RHS count, the full-stage kernels' (CTAs per subdomain, factor
+                           chunk per ring slot; RHS per CTA of the tensor-core form) on
+                           the liftings;
+                           0: fixed rules (see helm_iface_shape, helm_stage_shape) */
     int tc_iface_min_ctas;  /* an interface stage runs in the tensor-core form (when that
                            form is chosen) only if it makes at least this many CTAs (of
                            128 output rows x 16 or 32 RHS); smaller stages take the
@@ -391,6 +393,14 @@ typedef struct {
  * output pointer may be NULL. */
 helm_status helm_iface_shape(const helm_problem* p, int nrhs, int* nr, int* staged, int* waves, int* tensor,
                              int* tensor_rhs, int* tuned);
+
+/* Launch shape of the full-stage kernels (the liftings and reconstructions, which stream
+ * the factors) for nrhs right-hand sides on p, as the autotuner chose it (setup option
+ * autotune; *tuned = 1) or 0 for each field when the kernels' rules apply (*tuned = 0):
+ * *csize CTAs per subdomain on the CUDA cores (1, or 2 = one per column half of the
+ * factors), *chunk_kb KB of factors per ring slot of the bulk-copy stream (64, 48, 32),
+ * *tensor_rhs RHS per CTA of the tensor-core form (16, 32, 64).  Any output may be NULL. */
+helm_status helm_stage_shape(const helm_problem* p, int nrhs, int* csize, int* chunk_kb, int* tensor_rhs, int* tuned);
 
 /* Number of CUDA kernel launches issued by the library in this process. */
 long long helm_launch_count(void);

@@ -271,6 +271,9 @@ struct helm_problem {
     bool inner_hist_taken = false;   // the interface history of this gmres_solve call is recorded
     struct TunedShape { int prec, nrhs; IfaceCfg cfg; };
     std::vector<TunedShape> iface_tuned;   // autotuned interface-stage launch shapes
+    struct TunedStage { int prec, nrhs; StageCfg cfg; };
+    std::vector<TunedStage> stage_tuned;   // autotuned full-stage launch shapes
+    const StageCfg* stage_try = nullptr;   // the candidate being timed by the autotuner
 
     // adjoint workspace
     double2 *d_res = nullptr, *d_fadj = nullptr, *d_U = nullptr, *d_L = nullptr;
@@ -1557,6 +1560,110 @@ extern "C" helm_status helm_iface_shape(const helm_problem* p, int nrhs, int* nr
     return HELM_OK;
 }
 
+// autotuned launch shape of the full stages for nrhs RHS (nullptr: the kernels' rules)
+static const StageCfg* stage_shape_for(const helm_problem* p, int nrhs) {
+    for (const auto& t : p->stage_tuned)
+        if (t.prec == p->prec && t.nrhs == nrhs) return &t.cfg;
+    return nullptr;
+}
+
+template <typename R>
+static helm_status run_stage_t(helm_problem* p, const PcWork& w, const PcCtx& cx, const StageDesc& sd,
+                               const double2* r, double2* z, int nrhs, cudaStream_t st);
+
+// The autotuner of the full-stage kernels (the liftings and reconstructions, which
+// stream the factors): the first application with a given RHS count times the lifting
+// stage (every subdomain; it reads r and writes B and X, so it may run any number of
+// times) for each candidate shape with CUDA events on the caller's stream, and keeps
+// the fastest: on the CUDA cores, one or two CTAs per subdomain (the second taking one
+// column half of the factors, halves of the next input exchanged through distributed
+// shared memory) and the factor chunk per ring slot (64, 48, 32 KB); in the tensor-core
+// form, 16, 32 or 64 RHS per CTA.  Not while a stream is being captured.
+template <typename R>
+static helm_status tune_stage_t(helm_problem* p, const double2* r, int nrhs, cudaStream_t st) {
+    const PcWork w{{p->d_trace[0], p->d_trace[1], p->d_trace[2], p->d_trace[3]}, p->d_yws, p->d_pc_norm,
+                   p->d_pc_partial, p->d_escr, p->d_r64};
+    const PcCtx cx = precond_prologue<R>(p, w, r, nrhs, st);
+    StageDesc lift = p->sched[HELM_SCHED_BSP].front();
+    lift.final_ = 0;
+    if (lift.mask == 0) lift.dst = lift.dst2 = BUF_NONE;     // one subdomain: no traces
+    std::vector<StageCfg> cands;
+    if (cx.tc) {
+        for (int nr : {16, 32, 64}) {
+            if (nr > nrhs && nr > 16) continue;
+            if (nr == 64 && (p->tc_split != 1 || p->tc_mt != 1)) continue;
+            if (nr == 32 && p->tc_split == 3 && p->tc_mt != 1) continue;
+            StageCfg c;
+            c.tc_nr = nr;
+            cands.push_back(c);
+        }
+    } else {
+        for (int cs : {1, 2})
+            for (int kb : {64, 48, 32}) {
+                StageCfg c;
+                c.csize = cs;
+                c.chunk_kb = kb;
+                cands.push_back(c);
+            }
+    }
+    if (cands.size() < 2) return HELM_OK;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    HELM_CUDA_TRY(cudaEventCreate(&e0));
+    HELM_CUDA_TRY(cudaEventCreate(&e1));
+    const long long before = helm_launch_count();
+    const int prof_was = p->prof_on;
+    p->prof_on = 0;
+    StageCfg best{};
+    float best_ms = 1e30f;
+    for (const StageCfg& c : cands) {
+        p->stage_try = &c;
+        if (run_stage_t<R>(p, w, cx, lift, r, nullptr, nrhs, st) != HELM_OK) {   // warm (and validity)
+            (void)cudaGetLastError();
+            continue;
+        }
+        cudaEventRecord(e0, st);
+        for (int rep = 0; rep < 3; ++rep) run_stage_t<R>(p, w, cx, lift, r, nullptr, nrhs, st);
+        cudaEventRecord(e1, st);
+        float ms = 0;
+        if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess &&
+            ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+    }
+    p->stage_try = nullptr;
+    p->prof_on = prof_was;
+    uncount_launch(helm_launch_count() - before);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    HELM_CUDA_TRY(cudaGetLastError());
+    int dev_status = 0;
+    HELM_CUDA_TRY(cudaMemcpyAsync(&dev_status, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    HELM_CUDA_TRY(cudaStreamSynchronize(st));
+    if (dev_status != 0) return take_device_status(p, "autotuning the stage kernels");
+    if (best_ms < 1e30f) p->stage_tuned.push_back({p->prec, nrhs, best});
+    return HELM_OK;
+}
+static helm_status tune_stage(helm_problem* p, const double2* r, int nrhs, cudaStream_t st) {
+    if (!p->sopts.autotune || p->prof_capture || stage_shape_for(p, nrhs)) return HELM_OK;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return HELM_OK;
+    return p->prec == HELM_PREC_C64 ? tune_stage_t<float>(p, r, nrhs, st) : tune_stage_t<double>(p, r, nrhs, st);
+}
+
+extern "C" helm_status helm_stage_shape(const helm_problem* p, int nrhs, int* csize, int* chunk_kb, int* tensor_rhs,
+                                        int* tuned) {
+    if (!p) return arg_error("helm_stage_shape: NULL handle");
+    const StageCfg* c = stage_shape_for(p, nrhs);
+    const StageCfg d{};
+    if (!c) c = &d;
+    if (csize) *csize = c->csize;
+    if (chunk_kb) *chunk_kb = c->chunk_kb;
+    if (tensor_rhs) *tensor_rhs = c->tc_nr;
+    if (tuned) *tuned = c != &d;
+    return HELM_OK;
+}
+
 template <typename R>
 static helm_status run_stage_t(helm_problem* p, const PcWork& w, const PcCtx& cx, const StageDesc& sd,
                                const double2* r, double2* z, int nrhs, cudaStream_t st) {
@@ -1639,6 +1746,7 @@ static helm_status run_stage_t(helm_problem* p, const PcWork& w, const PcCtx& cx
             flops += 8.0 * (2.0 * d.my - 1) * d.mx * (double)d.mx * nrhs;
         }
     }
+    const StageCfg* scfg = p->stage_try ? p->stage_try : stage_shape_for(p, nrhs);
     prof_begin(p, HELM_K_STAGE, st);
     cudaError_t e = cudaSuccess;
     bool done = false;
@@ -1652,13 +1760,13 @@ static helm_status run_stage_t(helm_problem* p, const PcWork& w, const PcCtx& cx
                 ac.estride = p->etot;
                 ac.r64 = (const T*)w.r64;
                 ac.subs = p->d_stage_subs + sd.tc_off[c];
-                e = launch_tc_stage(ac, p->d_XT, c + 1, p->tc_split, sd.tc_n[c], st);
+                e = launch_tc_stage(ac, p->d_XT, c + 1, p->tc_split, sd.tc_n[c], st, scfg ? scfg->tc_nr : 0);
             }
             done = true;
         }
     }
     if (!done)
-        e = launch_stage<R>(a, (int)sd.subs.size(), p->max_mx, p->max_my, p->max_w, p->max_ld, p->num_sms, st);
+        e = launch_stage<R>(a, (int)sd.subs.size(), p->max_mx, p->max_my, p->max_w, p->max_ld, p->num_sms, st, scfg);
     prof_end(p, HELM_K_STAGE, bytes, st, flops);
     if (e != cudaSuccess) return cuda_status(e, "stage launch");
     return HELM_OK;
@@ -1737,6 +1845,8 @@ static helm_status run_precond(helm_problem* p, int sched, const double2* r, dou
     if (s != HELM_OK) return s;
     s = tune_shape(p, nrhs, st);
     if (s != HELM_OK) return s;
+    s = tune_stage(p, r, nrhs, st);
+    if (s != HELM_OK) return s;
     const PcWork w{{p->d_trace[0], p->d_trace[1], p->d_trace[2], p->d_trace[3]}, p->d_yws, p->d_pc_norm,
                    p->d_pc_partial, p->d_escr, p->d_r64};
     return p->prec == HELM_PREC_C64 ? run_precond_t<float>(p, w, sched, r, z, nrhs, st)
@@ -1753,6 +1863,8 @@ static helm_status run_precond_graph(helm_problem* p, int sched, const double2* 
     helm_status s = ensure_pc_ws(p, nrhs);
     if (s != HELM_OK) return s;
     s = tune_shape(p, nrhs, st);
+    if (s != HELM_OK) return s;
+    s = tune_stage(p, r, nrhs, st);
     if (s != HELM_OK) return s;
     for (const auto& g : p->graphs)
         if (g.sched == sched && g.nrhs == nrhs && g.r == r && g.z == z) {
@@ -2356,6 +2468,8 @@ static helm_status run_precond_iface_t(helm_problem* p, int sched, const double2
     helm_status s = ensure_pc_ws(p, nrhs);
     if (s != HELM_OK) return s;
     s = tune_shape(p, nrhs, st);
+    if (s != HELM_OK) return s;
+    s = tune_stage(p, r, nrhs, st);
     if (s != HELM_OK) return s;
     const long long nt = p->ntrace;
     s = ensure_kw(p->kwi, nrhs, o.inner_restart, nt, true);

@@ -251,9 +251,13 @@ cudaError_t launch_factor(const SubDev* subtab, int nsub, int max_mx, const doub
                           Cx<R>* X, Cx<R>* work, size_t work_stride, int* info, cudaStream_t st);
 // stage
 // max_w: widest column half, max_ld: largest half leading dimension, num_sms: SMs of the device
+// launch shape of the full-stage kernels chosen by the autotuner (0: the kernel's rule):
+// csize CTAs per subdomain (1, 2), factor chunk of chunk_kb KB per ring slot (64, 48,
+// 32), tensor-core form tc_nr RHS per CTA (16, 32, 64)
+struct StageCfg { int csize = 0, chunk_kb = 0, tc_nr = 0; };
 template <typename R>
 cudaError_t launch_stage(const StageArgs<R>& a, int nactive, int max_mx, int max_my, int max_w, int max_ld,
-                         int num_sms, cudaStream_t st);
+                         int num_sms, cudaStream_t st, const StageCfg* cfg = nullptr);
 // boundary operators K of all subdomains, columns [col0, col0 + ncols) per launch
 template <typename R>
 cudaError_t launch_basis(const StageArgs<R>& a, int nsub, int ncols, int max_mx, int max_my, int max_w, int max_ld,
@@ -266,7 +270,7 @@ int tc_tiles(int mx);                                     // 128-node M tiles (1
 long long tc_layout_floats(int mx, int my, int MT, int split);   // floats of one subdomain's factors in that layout
 cudaError_t launch_tc_layout(const SubDev* subtab, int nsub, int split, const float2* X, float* XT, cudaStream_t st);
 cudaError_t launch_tc_stage(const StageArgs<float>& a, const float* XT, int MT, int split, int nactive,
-                            cudaStream_t st);
+                            cudaStream_t st, int nr = 0);   // nr: RHS per CTA (0: the rule)
 cudaError_t launch_iface_tc(const IfaceArgs<float>& a, int nactive, int max_rows, int split, int nb, int min_ctas,
                             int max_Lb, cudaStream_t st);
 cudaError_t launch_tc_basis(const StageArgs<float>& a, const float* XT, int MT, int split, int nsub, int ncols,

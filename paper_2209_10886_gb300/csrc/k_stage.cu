@@ -457,8 +457,9 @@ struct Geo {
     size_t smem;
 };
 
+// chunk_kb > 0: that chunk size only (the autotuner's choice), else the rule below
 template <typename R, int NR>
-static bool geometry(int max_mx, int max_my, int max_w, int max_ld, int csize, Geo& g) {
+static bool geometry(int max_mx, int max_my, int max_w, int max_ld, int csize, Geo& g, int chunk_kb = 0) {
     using T = Cx<R>;
     g.csize = csize;
     const int width = csize == 2 ? max_w : max_mx;       // columns of one CTA
@@ -472,7 +473,8 @@ static bool geometry(int max_mx, int max_my, int max_w, int max_ld, int csize, G
     // the largest chunk (64, 48 or 32 KB, a multiple of 4 rows) that leaves three ring
     // slots: the copy engine streams few large copies faster than many small ones
     int rows = 0, nslots = 0;
-    for (int kb : {64, 48, 32}) {
+    const int kbs[3] = {chunk_kb > 0 ? chunk_kb : 64, chunk_kb > 0 ? chunk_kb : 48, chunk_kb > 0 ? chunk_kb : 32};
+    for (int kb : kbs) {
         rows = (int)((size_t)kb * 1024 / ((size_t)max_ld * sizeof(T)));
         rows = std::min(std::max(4, rows & ~3), max_mx);
         nslots = std::min((int)((budget - fixed) / ((size_t)rows * max_ld * sizeof(T))), MAXNS);
@@ -510,25 +512,26 @@ cudaError_t launch_nr(const StageArgs<R>& a, int nunits, int ny_blocks, const Ge
 
 template <typename R>
 cudaError_t launch_stage(const StageArgs<R>& a, int nactive, int max_mx, int max_my, int max_w, int max_ld,
-                         int num_sms, cudaStream_t st) {
+                         int num_sms, cudaStream_t st, const StageCfg* cfg) {
     if (nactive == 0) return cudaSuccess;
     if (max_mx > 256) return cudaErrorInvalidValue;
-    // two CTAs per subdomain when the stage leaves enough SMs idle
     // two CTAs per subdomain when the stage leaves enough SMs idle and the arithmetic is
     // FP64 (complex128 solves are bound by the FP64 units of one SM; complex64 ones by the
-    // per-row exchange latency the split adds)
-    const int csize =
+    // per-row exchange latency the split adds); the autotuner may choose otherwise
+    int csize =
         (sizeof(R) == 8 && 2 * nactive * std::max(1, (a.nrhs + 15) / 16) <= num_sms && max_mx >= 64) ? 2 : 1;
+    if (cfg && cfg->csize > 0) csize = cfg->csize;
+    const int kb = cfg ? cfg->chunk_kb : 0;
     Geo g;
 #define HELM_TRY_NR(NRV)                                                                                    \
-    if (a.nrhs >= NRV && geometry<R, NRV>(max_mx, max_my, max_w, max_ld, csize, g))                        \
+    if (a.nrhs >= NRV && geometry<R, NRV>(max_mx, max_my, max_w, max_ld, csize, g, kb))                    \
         return launch_nr<R, NRV, false>(a, nactive, (a.nrhs + NRV - 1) / NRV, g, st);
     HELM_TRY_NR(16)
     HELM_TRY_NR(8)
     HELM_TRY_NR(4)
     HELM_TRY_NR(2)
 #undef HELM_TRY_NR
-    if (!geometry<R, 1>(max_mx, max_my, max_w, max_ld, csize, g)) return cudaErrorInvalidValue;
+    if (!geometry<R, 1>(max_mx, max_my, max_w, max_ld, csize, g, kb)) return cudaErrorInvalidValue;
     return launch_nr<R, 1, false>(a, nactive, a.nrhs, g, st);
 }
 
@@ -543,7 +546,9 @@ cudaError_t launch_basis(const StageArgs<R>& a, int nsub, int ncols, int max_mx,
     return cudaErrorInvalidValue;
 }
 
-template cudaError_t launch_stage<float>(const StageArgs<float>&, int, int, int, int, int, int, cudaStream_t);
-template cudaError_t launch_stage<double>(const StageArgs<double>&, int, int, int, int, int, int, cudaStream_t);
+template cudaError_t launch_stage<float>(const StageArgs<float>&, int, int, int, int, int, int, cudaStream_t,
+                                        const StageCfg*);
+template cudaError_t launch_stage<double>(const StageArgs<double>&, int, int, int, int, int, int, cudaStream_t,
+                                         const StageCfg*);
 template cudaError_t launch_basis<float>(const StageArgs<float>&, int, int, int, int, int, int, cudaStream_t);
 template cudaError_t launch_basis<double>(const StageArgs<double>&, int, int, int, int, int, int, cudaStream_t);

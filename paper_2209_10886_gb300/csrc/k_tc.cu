@@ -1010,24 +1010,26 @@ cudaError_t launch_tc_layout(const SubDev* subtab, int nsub, int split, const fl
 
 // RHS per CTA: the widest block whose operands fit next to a ring of chunk slots
 cudaError_t launch_tc_stage(const StageArgs<float>& a, const float* XT, int MT, int split, int nactive,
-                            cudaStream_t st) {
+                            cudaStream_t st, int nr) {
     if (nactive == 0) return cudaSuccess;
     const int n = a.nrhs;
+    // RHS per CTA: the largest variant that the RHS count fills (or the tuned one)
+    auto want = [&](int v) { return nr > 0 ? nr == v : n >= v; };
     if (split == 3) {
         if (MT == 1) {
-            if (n >= 32) return tc_launch<1, 32, false, 3>(a, XT, nactive, (n + 31) / 32, st);
+            if (want(32) && n >= 32) return tc_launch<1, 32, false, 3>(a, XT, nactive, (n + 31) / 32, st);
             return tc_launch<1, 16, false, 3>(a, XT, nactive, (n + 15) / 16, st);
         }
         if (MT == 2) return tc_launch<2, 16, false, 3>(a, XT, nactive, (n + 15) / 16, st);
         return cudaErrorInvalidValue;
     }
     if (MT == 1) {
-        if (n >= 64) return tc_launch<1, 64, false, 1>(a, XT, nactive, (n + 63) / 64, st);
-        if (n >= 32) return tc_launch<1, 32, false, 1>(a, XT, nactive, (n + 31) / 32, st);
+        if (want(64) && n >= 64) return tc_launch<1, 64, false, 1>(a, XT, nactive, (n + 63) / 64, st);
+        if (want(32) && n >= 32) return tc_launch<1, 32, false, 1>(a, XT, nactive, (n + 31) / 32, st);
         return tc_launch<1, 16, false, 1>(a, XT, nactive, (n + 15) / 16, st);
     }
     if (MT == 2) {
-        if (n >= 32) return tc_launch<2, 32, false, 1>(a, XT, nactive, (n + 31) / 32, st);
+        if (want(32) && n >= 32) return tc_launch<2, 32, false, 1>(a, XT, nactive, (n + 31) / 32, st);
         return tc_launch<2, 16, false, 1>(a, XT, nactive, (n + 15) / 16, st);
     }
     return cudaErrorInvalidValue;

@@ -380,6 +380,17 @@ def iface_shape(problem: "Problem", nrhs: int) -> dict:
             "tensor_cores": v[3].value, "tensor_rhs_per_cta": v[4].value, "tuned": bool(v[5].value)}
 
 
+def stage_shape(problem: "Problem", nrhs: int) -> dict:
+    """Launch shape of the full-stage kernels for nrhs RHS (autotuned, or 0s for the rules)."""
+    L = lib()
+    L.helm_stage_shape.restype = ctypes.c_int
+    L.helm_stage_shape.argtypes = [_vp, ctypes.c_int] + [ctypes.POINTER(ctypes.c_int)] * 4
+    v = [ctypes.c_int() for _ in range(4)]
+    _check(L.helm_stage_shape(problem._h, int(nrhs), *[ctypes.byref(x) for x in v]))
+    return {"ctas_per_subdomain": v[0].value, "chunk_kb": v[1].value, "tensor_rhs_per_cta": v[2].value,
+            "tuned": bool(v[3].value)}
+
+
 def profile(problem: "Problem", on: bool = True):
     _check(lib().helm_profile(problem._h, int(on)))
 

@@ -144,3 +144,18 @@ def test_habc_interface_krylov_solve(H, prec):
             assert info[k][1] <= 1e-9 and rel(u[k], ref) <= 1e-5
         p.close()
     assert steps["habc"] > 0 and steps["optimized"] > 0
+
+
+@pytest.mark.parametrize("mode", ["dependency", "barrier"])
+def test_habc_persistent_sweep_gives_the_same_solve(H, mode):
+    """The persistent sweep forms apply the HABC stage maps like the stage launches."""
+    w = CASES["uneven_4x3"]()
+    p = gpu_problem(H, w, "c64")
+    f = cuda(W.random_complex((2, w.N), 94))
+    kw = dict(tol=1e-9, restart=30, maxit=200, inner_maxit=60, inner_tol=1e-3)
+    u0, i0, _ = p.solve(f, **kw)
+    u1, i1, _ = p.solve(f, persistent=mode, **kw)
+    print(f"HABC {mode}: its {[i[0] for i in i0]} vs {[i[0] for i in i1]}, rel {rel(u1.cpu().numpy(), u0.cpu().numpy()):.1e}")
+    assert [i[0] for i in i0] == [i[0] for i in i1]
+    assert rel(u1.cpu().numpy(), u0.cpu().numpy()) <= 1e-9
+    p.close()

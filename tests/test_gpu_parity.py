@@ -236,6 +236,27 @@ def test_autotuned_interface_shape(H, prec):
     pa.close(); pb.close()
 
 
+@pytest.mark.parametrize("prec,nrhs", [("c64", 1), ("c128", 1), ("c64", 40), ("c128", 3)])
+def test_autotuned_stage_shape(H, prec, nrhs):
+    """The first application per RHS count also times the full-stage kernels' launch
+    shapes on the liftings (CTAs per subdomain and factor chunk on the CUDA cores; RHS
+    per CTA in the tensor-core form) and keeps the fastest: the same solves, so the same
+    z up to the rounding of the order of the sums."""
+    w = CASES["uneven_4x3"]()
+    mk = lambda tune: H.Problem(w.n, w.n, w.h, w.omega, cuda(w.m2, torch.float64), w.N1, w.N2, w.xcuts, w.ycuts,
+                                autotune=tune).factor(prec)
+    pa, pb = mk(True), mk(False)
+    r = cuda(W.random_complex((nrhs, w.N), 53))
+    za = pa.precond_apply(r).cpu().numpy()
+    zb = pb.precond_apply(r).cpu().numpy()
+    sa, sb = H.stage_shape(pa, nrhs), H.stage_shape(pb, nrhs)
+    print(prec, nrhs, "tuned", sa, "fixed", sb, "rel", rel(za, zb))
+    assert sa["tuned"] and not sb["tuned"]
+    assert (sa["tensor_rhs_per_cta"] > 0) == (prec == "c64" and nrhs >= 16)
+    assert rel(za, zb) <= (C64_TOL if prec == "c64" else 1e-12)
+    pa.close(); pb.close()
+
+
 def test_impedance_transmission_matches_oracle(H):
     w = CASES["ragged_3x2"]()
     p, dec = make(H, w, "c128", transmission="impedance")
