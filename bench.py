@@ -93,6 +93,8 @@ def parse():
                     help="fixed launch-shape rules for the interface stages (no autotuner)")
     ap.add_argument("--tc-iface-min-ctas", type=int, default=-1,
                     help="interface stages of fewer CTAs stay on the CUDA cores (-1: two per SM)")
+    ap.add_argument("--no-tc-factor", action="store_true",
+                    help="complex64 factorisation on the CUDA cores (default: trailing updates on the tensor cores)")
     ap.add_argument("--tc-min-rhs", type=int, default=16,
                     help="stages with at least this many RHS run on the tensor cores (1: all)")
     return ap.parse_args()
@@ -123,7 +125,7 @@ def precond_only(args):
     m2 = torch.as_tensor(w.m2, dtype=torch.float64, device="cuda")
     p = Problem(w.n, w.n, w.h, w.omega, m2, w.N1, w.N2, w.xcuts, w.ycuts, tensor_cores=TC_MODES[args.tensor_cores],
                 tc_min_rhs=args.tc_min_rhs, tc_scale=args.tc_scale, tc_iface_min_ctas=args.tc_iface_min_ctas,
-                autotune=not args.no_autotune, transmission=args.transmission)
+                autotune=not args.no_autotune, transmission=args.transmission, tc_factor=not args.no_tc_factor)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     p.factor(args.prec)
@@ -156,6 +158,7 @@ def precond_only(args):
     helm.profile(p, False)
     print(json.dumps({"mode": "precond", "workload": name, "nrhs": int(r.shape[0]), "prec": args.prec,
                       "sched": args.sched, "tensor_cores": args.tensor_cores, "factor_ms": factor_ms,
+                      "factor_on_tensor_cores": p.factor_on_tensor_cores(),
                       "ms_per_apply": ms, "unknowns_rhs_per_s": w.N * r.shape[0] / (ms / 1e3),
                       "kernels": kern}))
     p.close()
@@ -442,6 +445,42 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
+def habc_form(args, w, m2, f, ms, st, err_vs_oracle):
+    """The paper's transmission (Pade HABC, N_pade = 8, phi = pi/3, Sections 3 and 6) on the
+    same workload and method: factors with the optimized Robin condition plus the HABC
+    boundary maps; one warm solve, one timed.  Runs after the main problem is released."""
+    import torch
+    from paper_2209_10886_gb300 import Problem, helm
+    qh = Problem(w.n, w.n, w.h, w.omega, m2, w.N1, w.N2, w.xcuts, w.ycuts, transmission="habc",
+                 tc_scale=args.tc_scale, tensor_cores=TC_MODES[args.tensor_cores], tc_factor=not args.no_tc_factor)
+    try:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        qh.factor(args.prec)
+        torch.cuda.synchronize()
+        hfac = (time.perf_counter() - t0) * 1e3
+        hkw = dict(restart=args.restart, maxit=3000, tol=args.tol, sched=args.sched, use_graph=args.graph,
+                   **inner_kw(args))
+        qh.solve(f, **hkw)
+        torch.cuda.synchronize()
+        h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0 = helm.inner_steps(qh)
+        h0.record(st)
+        uh_, ih, _ = qh.solve(f, **hkw)
+        h1.record(st)
+        torch.cuda.synchronize()
+        msh = h0.elapsed_time(h1)
+        return {"value": w.N * w.nrhs / (msh / 1e3), "ms_per_step": msh, "iterations": ih[0][0],
+                "interface_steps": helm.inner_steps(qh) - s0, "relres": max(i[1] for i in ih),
+                "err_vs_oracle": err_vs_oracle(uh_.cpu().numpy()), "factor_ms": hfac,
+                "transmission": "Pade HABC, N_pade 8, phi pi/3 (base factors: optimized Robin, scale "
+                                f"{args.tc_scale:g})", "speedup_over_robin": ms / msh}
+    except helm.HelmError as e:
+        return {"error": str(e)[:300]}
+    finally:
+        qh.close()
+
+
 def gpu_arm(args):
     import numpy as np
     import torch
@@ -468,7 +507,7 @@ def gpu_arm(args):
     f = torch.as_tensor(w.f, dtype=torch.complex128, device=dev)
     p = Problem(w.n, w.n, w.h, w.omega, m2, w.N1, w.N2, w.xcuts, w.ycuts, tensor_cores=TC_MODES[args.tensor_cores],
                 tc_min_rhs=args.tc_min_rhs, tc_scale=args.tc_scale, tc_iface_min_ctas=args.tc_iface_min_ctas,
-                autotune=not args.no_autotune)
+                autotune=not args.no_autotune, tc_factor=not args.no_tc_factor)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     p.factor(args.prec)
@@ -590,36 +629,6 @@ def gpu_arm(args):
                 "speedup_mixed_over_fp64": ms64 / ms}
         q.close()
 
-    # the paper's transmission (Pade HABC, N_pade = 8, phi = pi/3, Sections 3 and 6) on the
-    # same workload and method: factors with the optimized Robin condition plus the HABC
-    # boundary maps; one warm solve, one timed
-    habc = None
-    if not args.no_habc_form:
-        qh = Problem(w.n, w.n, w.h, w.omega, m2, w.N1, w.N2, w.xcuts, w.ycuts, transmission="habc",
-                     tc_scale=args.tc_scale, tensor_cores=TC_MODES[args.tensor_cores])
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        qh.factor(args.prec)
-        torch.cuda.synchronize()
-        hfac = (time.perf_counter() - t0) * 1e3
-        hkw = dict(restart=args.restart, maxit=3000, tol=args.tol, sched=args.sched, use_graph=args.graph,
-                   **inner_kw(args))
-        qh.solve(f, **hkw)
-        torch.cuda.synchronize()
-        h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        s0 = helm.inner_steps(qh)
-        h0.record(st)
-        uh_, ih, _ = qh.solve(f, **hkw)
-        h1.record(st)
-        torch.cuda.synchronize()
-        msh = h0.elapsed_time(h1)
-        habc = {"value": w.N * w.nrhs / (msh / 1e3), "ms_per_step": msh, "iterations": ih[0][0],
-                "interface_steps": helm.inner_steps(qh) - s0, "relres": ih[0][1],
-                "err_vs_oracle": err_vs_oracle(uh_.cpu().numpy()), "factor_ms": hfac,
-                "transmission": "Pade HABC, N_pade 8, phi pi/3 (base factors: optimized Robin, scale "
-                                f"{args.tc_scale:g})", "speedup_over_robin": msh and ms / msh}
-        qh.close()
-
     if rank != 0:
         return
     total_units = w.N * w.nrhs * world
@@ -712,6 +721,7 @@ def gpu_arm(args):
                                             "dependency": "one cooperative launch, per-item dependencies"}[args.sweep]}
                                  if args.inner_maxit > 0 else None),
             "relres_host_check": check,
+            "factor_on_tensor_cores": p.factor_on_tensor_cores(),
             "err_vs_oracle": err_vs_oracle(u_main),
             "err_vs_oracle_note": ("rel. L2 of the first RHS's solution (tol above) against the oracle's sparse "
                                    "direct solution of the global system (nested-dissection LU + refinement)"),
@@ -730,7 +740,7 @@ def gpu_arm(args):
             "launches_per_step": {"stage": stage[0] / args.steps, "trace": trace[0] / args.steps},
             "fp64_form": fp64,
             "sp_schedule": sp_form,
-            "habc_form": habc,
+            "habc_form": None,
         },
         "roofline": roofline,
         "roofline_stage_kernel": stage_roof,
@@ -742,8 +752,10 @@ def gpu_arm(args):
         "cpu_baseline_all_cores": cpu_pool,
         "cpu_baseline_single_sweep": cpu_single,
     }
-    print(json.dumps(line), flush=True)
     p.close()
+    if not args.no_habc_form:
+        line["config"]["habc_form"] = habc_form(args, w, m2, f, ms, st, err_vs_oracle)
+    print(json.dumps(line), flush=True)
 
 
 def main():

@@ -158,6 +158,11 @@ typedef struct {
     int n_pade;         /* HELM_TC_HABC: auxiliary fields of the Pade approximation (>= 0);
                            default 8 */
     double pade_phi;    /* HELM_TC_HABC: branch-cut rotation phi (radians); default pi/3 */
+    int tc_factor;      /* 1 (default): with complex64 factors, tensor_cores != 0 and subdomains
+                           at most 128 nodes wide, precond_factor runs each inversion
+                           X_r = T_r^{-1} as a blocked Gauss-Jordan elimination (panels of 16
+                           columns, partial pivoting) whose rank-16 trailing updates are
+                           3xTF32 tensor-core GEMMs; 0: the CUDA-core elimination */
 } helm_setup_opts;
 
 typedef struct {
@@ -357,6 +362,10 @@ helm_status helm_schedule_info(int N1, int N2, int sched, int* steps, int* stage
  * i diag(kappa), the impedance condition.  HELM_ERR_ARG for NULL pointers, L < 1,
  * h <= 0, n_pade < 0, a non-positive kappa or a singular factor. */
 helm_status helm_habc_side_operator(const double* kappa, int L, double h, int n_pade, double phi, helm_c128* T);
+
+/* 1 when the last precond_factor of p ran its eliminations' trailing updates on the
+ * tensor cores (helm_setup_opts.tc_factor), else 0 (also for NULL or unfactored p). */
+int helm_factor_on_tensor_cores(const helm_problem* p);
 
 /* Problem sizes of a handle: N = n_x*n_y unknowns, number of subdomains,
  * 2 N_e interface unknowns (trace points), bytes of the current factors. */

@@ -227,6 +227,7 @@ struct helm_problem {
 
     int factored = 0;
     int prec = HELM_PREC_C128;
+    bool tc_factor_used = false;     // the last factorisation ran its trailing updates on the tensor cores
     void* d_X = nullptr;
     void* d_K = nullptr;             // boundary operators of all subdomains
     size_t K_bytes = 0;
@@ -466,6 +467,7 @@ extern "C" void helm_default_setup_opts(helm_setup_opts* o) {
     o->device_budget = 0;
     o->n_pade = 8;
     o->pade_phi = 3.14159265358979323846 / 3.0;
+    o->tc_factor = 1;
 }
 
 extern "C" const char* helm_last_error(void) { return g_err.c_str(); }
@@ -612,6 +614,7 @@ extern "C" helm_status helm_setup(int n_x, int n_y, double h, double omega, cons
     }
     if (so.tensor_cores < 0 || so.tensor_cores > 2) return arg_error("helm_setup: tensor_cores must be 0, 1 or 2");
     if (so.tc_min_rhs < 1) return arg_error("helm_setup: tc_min_rhs must be >= 1");
+    if (so.tc_factor != 0 && so.tc_factor != 1) return arg_error("helm_setup: tc_factor must be 0 or 1");
     if (so.autotune != 0 && so.autotune != 1) return arg_error("helm_setup: autotune must be 0 or 1");
     if (so.tc_iface_min_ctas < -1) return arg_error("helm_setup: tc_iface_min_ctas must be >= -1");
 
@@ -940,6 +943,8 @@ extern "C" helm_status helm_destroy(helm_problem* p) {
     return HELM_OK;
 }
 
+extern "C" int helm_factor_on_tensor_cores(const helm_problem* p) { return p && p->factored && p->tc_factor_used; }
+
 extern "C" helm_status helm_problem_info(const helm_problem* p, long long* n_unknowns, int* n_subdomains,
                                          long long* n_trace, long long* factor_bytes) {
     if (!p) return arg_error("helm_problem_info: NULL handle");
@@ -1233,7 +1238,12 @@ extern "C" helm_status precond_factor(helm_problem* p, helm_prec prec, void* str
     }
     e = cudaMalloc(&info, p->subs.size() * sizeof(int));
     if (e != cudaSuccess) { if (work) cudaFree(work); return cuda_status(e, "precond_factor: alloc info"); }
-    if (prec == HELM_PREC_C64)
+    // complex64 with subdomains at most 128 nodes wide: the Gauss-Jordan trailing updates on
+    // the tensor cores (k_tc.cu), else the CUDA-core kernel (k_factor.cu)
+    p->tc_factor_used = prec == HELM_PREC_C64 && p->sopts.tensor_cores && p->sopts.tc_factor && p->max_mx <= 128;
+    if (p->tc_factor_used)
+        e = launch_tc_factor(p->d_subtab, (int)p->subs.size(), p->d_dloc, (float2*)p->d_X, info, p->d_err, st);
+    else if (prec == HELM_PREC_C64)
         e = launch_factor<float>(p->d_subtab, (int)p->subs.size(), p->max_mx, p->d_dloc, (float2*)p->d_X, (float2*)work,
                                  wel, info, st);
     else
@@ -1245,6 +1255,10 @@ extern "C" helm_status precond_factor(helm_problem* p, helm_prec prec, void* str
     if (work) cudaFree(work);
     cudaFree(info);
     if (e != cudaSuccess) return cuda_status(e, "precond_factor: factor kernel");
+    {
+        const helm_status ds = take_device_status(p, "precond_factor");
+        if (ds != HELM_OK) return ds;
+    }
     for (size_t k = 0; k < hinfo.size(); ++k)
         if (hinfo[k]) {
             char buf[160];

@@ -269,6 +269,10 @@ cudaError_t launch_basis(const StageArgs<R>& a, int nsub, int ncols, int max_mx,
 int tc_tiles(int mx);                                     // 128-node M tiles (1 or 2), 0: unsupported width
 long long tc_layout_floats(int mx, int my, int MT, int split);   // floats of one subdomain's factors in that layout
 cudaError_t launch_tc_layout(const SubDev* subtab, int nsub, int split, const float2* X, float* XT, cudaStream_t st);
+// complex64 factorisation with the Gauss-Jordan trailing updates on the tensor cores
+// (3xTF32); every subdomain at most 128 nodes wide
+cudaError_t launch_tc_factor(const SubDev* subtab, int nsub, const double2* dloc, float2* X, int* info, int* err,
+                             cudaStream_t st);
 cudaError_t launch_tc_stage(const StageArgs<float>& a, const float* XT, int MT, int split, int nactive,
                             cudaStream_t st, int nr = 0);   // nr: RHS per CTA (0: the rule)
 cudaError_t launch_iface_tc(const IfaceArgs<float>& a, int nactive, int max_rows, int split, int nb, int min_ctas,

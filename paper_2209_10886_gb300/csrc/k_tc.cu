@@ -992,6 +992,295 @@ cudaError_t tc_iface_launch(const IfaceArgs<float>& a, int nactive, int max_rows
     return cudaLaunchKernelEx(&cfg, tc_iface_kernel<NB, SPLIT>, a, S);
 }
 
+// ------------------------------------------------------------- factorisation
+// The block-tridiagonal factorisation of a subdomain (T_1 = D_1, X_r = T_r^{-1},
+// T_{r+1} = D_{r+1} - X_r; see k_factor.cu) with the inversions as blocked
+// Gauss-Jordan eliminations whose trailing updates run on the tensor cores.
+//
+// Partial pivoting is virtual: rows stay where they are, the pivot of column k is the
+// largest remaining entry of that column, at row p_k.  Columns are taken in panels of
+// FB = 16.  A panel is eliminated on the CUDA cores on its own columns only (one row
+// per thread of the first four warps): afterwards its pivot rows hold M11^{-1} and the
+// other rows -M21 M11^{-1}, where M11 is the panel's block on its pivot rows.  Every
+// other column then takes the same row operations, for all rows at once, as the rank-FB
+// update
+//     W[:, q] += A B[:, q],   A[i, j] = W[i, c + j] - (i == p_{c+j}),   B[j, q] = W_old[p_{c+j}, q]
+// (for a pivot row this is M11^{-1} M12, for the others M22 - M21 M11^{-1} M12), with B
+// zero on the panel's own columns: a complex (128 x 16) x (16 x 128) product, the
+// [-Bi | Br | Bi] operand of the block solves (k_tc.cu above), split into TF32 hi + lo
+// (three MMAs per real product), accumulated in tensor memory and added to W by the
+// epilogue warps.  At the end X[k][l] = W[p_k][j(l)] with p_{j(l)} = l undoes the
+// virtual interchanges; the stored X_r is symmetrised as in k_factor.cu.  One CTA of
+// 512 threads per subdomain (at most 128 nodes wide), W in shared memory (row stride
+// 129 complex values: conflict-free row and column walks).
+constexpr int FB = 16;                                   // panel width (K of the update)
+constexpr int FT_TC = 512;                               // threads per CTA
+constexpr int LDW = 129;                                 // row stride of W (complex values)
+constexpr unsigned F_PLANE = 128u * FB * 4u;             // one plane of the A operand (bytes)
+constexpr unsigned F_KSA = 2048u;                        // A: K-adjacent core matrices
+constexpr unsigned F_KSB = 48u * 128u + 64u;             // B: K-adjacent core matrices (N = 3 x 128)
+constexpr unsigned F_BLO = (FB / 4) * F_KSB;             // offset of the lo B operand
+constexpr size_t F_W_BYTES = (size_t)128 * LDW * sizeof(float2);
+constexpr size_t F_A_OFF = (F_W_BYTES + 1023) & ~(size_t)1023;
+constexpr size_t F_B_OFF = F_A_OFF + 4 * F_PLANE;
+constexpr size_t F_SMEM = F_B_OFF + 2 * (size_t)F_BLO;
+
+__global__ void __launch_bounds__(FT_TC, 1) tc_factor_kernel(const SubDev* __restrict__ subtab,
+                                                             const double2* __restrict__ dloc, float2* __restrict__ X,
+                                                             int* __restrict__ info, int* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ __align__(8) unsigned long long mma_bar, fin_bar;
+    __shared__ unsigned tmem_base;
+    __shared__ int piv[128], ipiv[128], used[128];
+    __shared__ float2 prow[FB];
+    __shared__ float red_v[4];
+    __shared__ int red_i[4];
+    __shared__ int s_p, abort_flag;
+    __shared__ float2 s_inv;
+    float2* W = reinterpret_cast<float2*>(smem_raw);
+    unsigned char* aop = smem_raw + F_A_OFF;
+    unsigned char* bop = smem_raw + F_B_OFF;
+    const unsigned a_s = sm_addr(aop), b_s = sm_addr(bop);
+    const SubDev sd = subtab[blockIdx.x];
+    const int m = sd.mx, my = sd.my;
+    const int w0 = sd.w0, ld0 = sd.ld0, ld1 = sd.ld1;
+    const long long xr_elems = (long long)m * (ld0 + ld1);
+    auto xidx = [&](int i, int j) -> long long {
+        return j < w0 ? (long long)i * ld0 + j : (long long)m * ld0 + (long long)i * ld1 + (j - w0);
+    };
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    constexpr unsigned IDESC = tf32_idesc(256);
+    if (tid == 0) {
+        bar_init(&mma_bar, 1);
+        bar_init(&fin_bar, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(sm_addr(&tmem_base)),
+                     "r"(256)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const unsigned tmem = tmem_base;
+    int fail_at = 0;                                     // thread 0: first vanishing pivot (1-based)
+    unsigned ph = 0;
+    bool issued_any = false;
+
+    for (int r = 0; r < my && !abort_flag; ++r) {
+        // T_r = D_r - X_{r-1}
+        const double2* d = dloc + sd.loff + (long long)r * m;
+        const float2* Xp = X + sd.xoff + (long long)(r - 1) * xr_elems;
+        for (int idx = tid; idx < m * m; idx += FT_TC) {
+            const int i = idx / m, j = idx - i * m;
+            float2 v = make_float2(0.f, 0.f);
+            if (r > 0) {
+                const float2 xp = Xp[xidx(i, j)];
+                v = make_float2(-xp.x, -xp.y);
+            }
+            if (i == j) v = make_float2(v.x + (float)d[i].x, v.y + (float)d[i].y);
+            else if (i - j == 1 || j - i == 1) v.x -= 1.f;
+            W[i * LDW + j] = v;
+        }
+        if (tid < 128) used[tid] = 0;
+        __syncthreads();
+        for (int c = 0; c < m; c += FB) {
+            const int nb = min(FB, m - c);
+            // ---- the panel's own columns, rows on the first four warps
+            if (tid < 128) {
+                const int i = tid;
+                for (int k = c; k < c + nb; ++k) {
+                    float best = -1.f;
+                    if (i < m && !used[i]) {
+                        const float2 v = W[i * LDW + k];
+                        best = v.x * v.x + v.y * v.y;
+                    }
+                    int bi = i;
+                    for (int o = 16; o > 0; o >>= 1) {
+                        const float ob = __shfl_down_sync(0xffffffffu, best, o);
+                        const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+                        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+                    }
+                    if (lane == 0) { red_v[warp] = best; red_i[warp] = bi; }
+                    asm volatile("bar.sync 1, 128;\n" ::: "memory");
+                    if (tid == 0) {
+                        float b = red_v[0];
+                        int p = red_i[0];
+                        for (int q = 1; q < 4; ++q)
+                            if (red_v[q] > b || (red_v[q] == b && red_i[q] < p)) { b = red_v[q]; p = red_i[q]; }
+                        if (!(b > 0.f) && !fail_at) fail_at = r * m + k + 1;
+                        s_p = p;
+                        piv[k] = p;
+                        used[p] = 1;
+                        const float2 pv = W[p * LDW + k];
+                        const float dd = pv.x * pv.x + pv.y * pv.y;
+                        s_inv = dd > 0.f ? make_float2(pv.x / dd, -pv.y / dd) : make_float2(0.f, 0.f);
+                    }
+                    asm volatile("bar.sync 1, 128;\n" ::: "memory");
+                    const int p = s_p;
+                    const float2 inv = s_inv;
+                    if (tid < nb) {
+                        const int j = c + tid;
+                        prow[tid] = j == k ? inv : cmul(W[p * LDW + j], inv);
+                    }
+                    asm volatile("bar.sync 1, 128;\n" ::: "memory");
+                    if (i < m) {
+                        if (i == p) {
+                            for (int jj = 0; jj < nb; ++jj) W[i * LDW + c + jj] = prow[jj];
+                        } else {
+                            const float2 f = W[i * LDW + k];
+                            for (int jj = 0; jj < nb; ++jj) {
+                                const int j = c + jj;
+                                W[i * LDW + j] = j == k ? make_float2(-(f.x * inv.x - f.y * inv.y), -(f.x * inv.y + f.y * inv.x))
+                                                        : cfma(make_float2(-f.x, -f.y), prow[jj], W[i * LDW + j]);
+                            }
+                        }
+                    }
+                    asm volatile("bar.sync 1, 128;\n" ::: "memory");
+                }
+            }
+            __syncthreads();
+            // ---- operands of the rank-nb update
+            for (int e = tid; e < 128 * FB; e += FT_TC) {
+                const int i = e / FB, jj = e - i * FB;
+                float2 v = make_float2(0.f, 0.f);
+                if (i < m && jj < nb) {
+                    v = W[i * LDW + c + jj];
+                    if (i == piv[c + jj]) v.x -= 1.f;
+                }
+                const unsigned off = (unsigned)((((jj >> 2) * 16 + (i >> 3)) * 32 + (i & 7) * 4 + (jj & 3)) * 4);
+                const float hr = tf32_round(v.x), hi = tf32_round(v.y);
+                *reinterpret_cast<float*>(aop + off) = hr;
+                *reinterpret_cast<float*>(aop + F_PLANE + off) = hi;
+                *reinterpret_cast<float*>(aop + 2 * F_PLANE + off) = tf32_round(v.x - hr);
+                *reinterpret_cast<float*>(aop + 3 * F_PLANE + off) = tf32_round(v.y - hi);
+            }
+            for (int e = tid; e < FB * 128; e += FT_TC) {
+                const int jj = e >> 7, q = e & 127;
+                float2 v = make_float2(0.f, 0.f);
+                if (jj < nb && q < m && (q < c || q >= c + nb)) v = W[piv[c + jj] * LDW + q];
+                const float hr = tf32_round(v.x), hi = tf32_round(v.y);
+                const float lr = tf32_round(v.x - hr), li = tf32_round(v.y - hi);
+                auto row = [&](int n) {
+                    return (unsigned)(jj >> 2) * F_KSB + (unsigned)(n >> 3) * 128u + (unsigned)(n & 7) * 16u +
+                           (unsigned)(jj & 3) * 4u;
+                };
+                *reinterpret_cast<float*>(bop + row(q)) = -hi;
+                *reinterpret_cast<float*>(bop + row(128 + q)) = hr;
+                *reinterpret_cast<float*>(bop + row(256 + q)) = hi;
+                *reinterpret_cast<float*>(bop + F_BLO + row(q)) = -li;
+                *reinterpret_cast<float*>(bop + F_BLO + row(128 + q)) = lr;
+                *reinterpret_cast<float*>(bop + F_BLO + row(256 + q)) = li;
+            }
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            tc_fence_before();
+            __syncthreads();
+            // ---- [Re D | Im D] = Ar [Br | Bi] + Ai [-Bi | Br], 3xTF32
+            if (tid == 0) {
+                tc_fence_after();
+#pragma unroll
+                for (int kk = 0; kk < FB / 8; ++kk) {
+                    const unsigned ar = a_s + (unsigned)kk * 2u * F_KSA;
+                    const unsigned bb = b_s + (unsigned)kk * 2u * F_KSB;
+                    const unsigned long long dre = smem_desc(ar, F_KSA, 128u);
+                    const unsigned long long dim = smem_desc(ar + F_PLANE, F_KSA, 128u);
+                    const unsigned long long drel = smem_desc(ar + 2u * F_PLANE, F_KSA, 128u);
+                    const unsigned long long diml = smem_desc(ar + 3u * F_PLANE, F_KSA, 128u);
+                    const unsigned long long b1 = smem_desc(bb + 16u * 128u, F_KSB, 128u);
+                    const unsigned long long b2 = smem_desc(bb, F_KSB, 128u);
+                    const unsigned long long b1l = smem_desc(F_BLO + bb + 16u * 128u, F_KSB, 128u);
+                    const unsigned long long b2l = smem_desc(F_BLO + bb, F_KSB, 128u);
+                    mma_tf32(tmem, dre, b1, IDESC, kk > 0 ? 1 : 0);
+                    mma_tf32(tmem, dim, b2, IDESC, 1);
+                    mma_tf32(tmem, dre, b1l, IDESC, 1);
+                    mma_tf32(tmem, dim, b2l, IDESC, 1);
+                    mma_tf32(tmem, drel, b1, IDESC, 1);
+                    mma_tf32(tmem, diml, b2, IDESC, 1);
+                }
+                mma_commit(&mma_bar);
+                issued_any = true;
+            }
+            if (!bar_wait(&mma_bar, ph, TC_WAIT_LIMIT)) {
+                if (threadIdx.x == 0) {
+                    abort_flag = 1;
+                    if (err) atomicExch(err, (int)HELM_ERR_TIMEOUT);
+                }
+            }
+            ph ^= 1u;
+            tc_fence_after();
+            // ---- W += D: warp w reads TMEM lanes 32 (w & 3) .. (rows) and columns 32 (w >> 2) ..
+            {
+                const int qr = warp & 3, g = warp >> 2;
+                const int i = 32 * qr + lane;
+                const unsigned base = tmem + ((unsigned)(32 * qr) << 16) + (unsigned)(32 * g);
+                float dr[32], di[32];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    tmem_ld8(base + (unsigned)(8 * t), dr + 8 * t);
+                    tmem_ld8(base + 128u + (unsigned)(8 * t), di + 8 * t);
+                }
+                tmem_wait_ld();
+                if (i < m && !abort_flag) {
+#pragma unroll
+                    for (int t = 0; t < 32; ++t) {
+                        const int q = 32 * g + t;
+                        if (q < m) {
+                            float2 w = W[i * LDW + q];
+                            w.x += dr[t];
+                            w.y += di[t];
+                            W[i * LDW + q] = w;
+                        }
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncthreads();
+            if (abort_flag) break;
+        }
+        if (abort_flag) break;
+        // X_r: undo the virtual interchanges, symmetrise, two-half layout with zeroed padding
+        if (tid < m) ipiv[piv[tid]] = tid;
+        __syncthreads();
+        float2* Xr = X + sd.xoff + (long long)r * xr_elems;
+        for (long long idx = tid; idx < xr_elems; idx += FT_TC) {
+            int i, j;
+            bool pad;
+            if (idx < (long long)m * ld0) {
+                i = (int)(idx / ld0);
+                j = (int)(idx - (long long)i * ld0);
+                pad = j >= w0;
+            } else {
+                const long long t2 = idx - (long long)m * ld0;
+                i = (int)(t2 / ld1);
+                j = w0 + (int)(t2 - (long long)i * ld1);
+                pad = j >= m;
+            }
+            float2 v = make_float2(0.f, 0.f);
+            if (!pad) {
+                const float2 a = W[piv[i] * LDW + ipiv[j]], b = W[piv[j] * LDW + ipiv[i]];
+                v = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y + b.y));
+            }
+            Xr[idx] = v;
+        }
+        __syncthreads();
+    }
+    // no MMA of this CTA is in flight when tensor memory is freed (bounded)
+    if (tid == 0 && issued_any) {
+        mma_commit(&fin_bar);
+        bar_wait(&fin_bar, 0u, TC_WAIT_LIMIT);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(256) : "memory");
+    }
+    if (tid == 0) info[blockIdx.x] = fail_at;
+}
+
 }  // namespace
 
 int tc_tiles(int mx) { return mx <= 128 ? 1 : mx <= 256 ? 2 : 0; }
@@ -1066,4 +1355,16 @@ cudaError_t launch_iface_tc(const IfaceArgs<float>& a, int nactive, int max_rows
                                     : tc_iface_launch<16, 3>(a, nactive, max_rows, S, st);
     return nb >= 32 ? tc_iface_launch<32, 1>(a, nactive, max_rows, S, st)
                     : tc_iface_launch<16, 1>(a, nactive, max_rows, S, st);
+}
+
+// The complex64 factorisation with the tensor-core trailing updates (tc_factor_kernel);
+// every subdomain at most 128 nodes wide.
+cudaError_t launch_tc_factor(const SubDev* subtab, int nsub, const double2* dloc, float2* X, int* info, int* err,
+                             cudaStream_t st) {
+    if (nsub == 0) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(tc_factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)F_SMEM);
+    if (e != cudaSuccess) return e;
+    count_launch();
+    tc_factor_kernel<<<nsub, FT_TC, F_SMEM, st>>>(subtab, dloc, X, info, err);
+    return cudaGetLastError();
 }

@@ -45,7 +45,8 @@ class HelmSetupOpts(ctypes.Structure):
     _fields_ = [("transmission", ctypes.c_int), ("tc_scale", ctypes.c_double),
                 ("boundary_operators", ctypes.c_int), ("tensor_cores", ctypes.c_int),
                 ("tc_min_rhs", ctypes.c_int), ("autotune", ctypes.c_int), ("tc_iface_min_ctas", ctypes.c_int),
-                ("device_budget", ctypes.c_size_t), ("n_pade", ctypes.c_int), ("pade_phi", ctypes.c_double)]
+                ("device_budget", ctypes.c_size_t), ("n_pade", ctypes.c_int), ("pade_phi", ctypes.c_double),
+                ("tc_factor", ctypes.c_int)]
 
 
 class HelmInfo(ctypes.Structure):
@@ -149,13 +150,14 @@ class Problem:
     form is chosen; -1: two per SM); ``device_budget`` (bytes the handle's large arrays
     may take, 0: no limit); ``n_pade`` and ``pade_phi`` of the "habc" transmission (the
     Pade HABC of the paper's experiments, with ``tc_scale`` the Robin parameter of the
-    factored base problem).
+    factored base problem); ``tc_factor`` (complex64 factorisation with tensor-core
+    trailing updates, subdomains at most 128 nodes wide).
     """
 
     def __init__(self, n_x, n_y, h, omega, m2, N1, N2, xcuts=None, ycuts=None,
                  transmission="optimized", tc_scale=1.0, boundary_operators=True, tensor_cores=True,
                  tc_min_rhs=16, autotune=True, tc_iface_min_ctas=-1, device_budget=0, n_pade=8,
-                 pade_phi=math.pi / 3):
+                 pade_phi=math.pi / 3, tc_factor=True):
         L = lib()
         if not (m2.is_cuda and m2.dtype == torch.float64 and m2.numel() == n_x * n_y):
             raise TypeError("m2 must be a float64 CUDA tensor with n_x*n_y values")
@@ -163,7 +165,7 @@ class Problem:
         tcm = {False: 0, True: 1, "3xtf32": 1, "tf32": 2}[tensor_cores]
         so = HelmSetupOpts(TRANSMISSION[transmission], float(tc_scale), int(bool(boundary_operators)), tcm,
                            int(tc_min_rhs), int(bool(autotune)), int(tc_iface_min_ctas), int(device_budget),
-                           int(n_pade), float(pade_phi))
+                           int(n_pade), float(pade_phi), int(bool(tc_factor)))
         xc = (ctypes.c_int * (N1 + 1))(*[int(v) for v in xcuts]) if xcuts is not None else None
         yc = (ctypes.c_int * (N2 + 1))(*[int(v) for v in ycuts]) if ycuts is not None else None
         h_ = ctypes.c_void_p()
@@ -176,6 +178,13 @@ class Problem:
         self.m2 = m2
 
     # ----------------------------------------------------------------- info
+    def factor_on_tensor_cores(self) -> bool:
+        """True when the last factorisation ran its trailing updates on the tensor cores."""
+        L = lib()
+        L.helm_factor_on_tensor_cores.restype = ctypes.c_int
+        L.helm_factor_on_tensor_cores.argtypes = [_vp]
+        return bool(L.helm_factor_on_tensor_cores(self._h))
+
     def info(self):
         n, ns, nt, fb = _ll(), _i(), _ll(), _ll()
         _check(lib().helm_problem_info(self._h, ctypes.byref(n), ctypes.byref(ns), ctypes.byref(nt),

@@ -220,3 +220,43 @@ def test_interface_krylov_with_tensor_core_interface_stages(H):
               f"rel {rel(u[k], ref):.2e}")
         assert info[k][1] <= 1e-9 and rel(u[k], ref) <= 1e-5
     p.close()
+
+
+@pytest.mark.parametrize("case", ["tiny_2x2", "uneven_4x3"])
+def test_tensor_core_factorisation_matches_oracle(H, case):
+    """precond_factor with the Gauss-Jordan trailing updates on the tensor cores (blocked
+    elimination, panels of 16 columns, 3xTF32 updates; subdomains up to 128 nodes wide)
+    against the oracle and against the CUDA-core elimination: one BSP application with
+    1 and 3 RHS (the CUDA-core block solves, so only the factors differ).  The factors
+    carry the 3xTF32 products' 2^-21 instead of FP32's 2^-24: bar as for the tensor-core
+    solves."""
+    w = CASES[case]()
+    mk = lambda tcf: H.Problem(w.n, w.n, w.h, w.omega, cuda(w.m2, torch.float64), w.N1, w.N2, w.xcuts, w.ycuts,
+                               tc_factor=tcf).factor("c64")
+    pt, pc = mk(True), mk(False)
+    assert pt.factor_on_tensor_cores() and not pc.factor_on_tensor_cores()
+    sw = Sweeper(Decomposition(w.n, w.h, w.omega, w.m2, w.xcuts, w.ycuts))
+    r = W.random_complex((3, w.N), 17)
+    zt = pt.precond_apply(cuda(r)).cpu().numpy()
+    zc = pc.precond_apply(cuda(r)).cpu().numpy()
+    for k in range(3):
+        ref = sw.precondition(r[k], "BSP")
+        et, ec = rel(zt[k], ref), rel(zc[k], ref)
+        print(f"{case} rhs{k}: tensor-core factors rel {et:.2e}, CUDA-core factors rel {ec:.2e}")
+        assert et <= TF32_PRECOND_TOL
+    q = H.Problem(w.n, w.n, w.h, w.omega, cuda(w.m2, torch.float64), w.N1, w.N2, w.xcuts, w.ycuts).factor("c128")
+    assert not q.factor_on_tensor_cores()
+    pt.close(); pc.close(); q.close()
+
+
+def test_tensor_core_factorisation_solves_to_the_direct_solution(H):
+    w = CASES["uneven_4x3"]()
+    p = H.Problem(w.n, w.n, w.h, w.omega, cuda(w.m2, torch.float64), w.N1, w.N2, w.xcuts, w.ycuts).factor("c64")
+    assert p.factor_on_tensor_cores()
+    A = assemble_operator(w.n, w.h, w.omega, w.m2).tocsc()
+    u, info, _ = p.solve(cuda(w.f), tol=1e-9, restart=30, maxit=300, inner_maxit=60, inner_tol=1e-3)
+    ref = spla.spsolve(A, w.h ** 2 * w.f[0])
+    e = rel(u.cpu().numpy()[0], ref)
+    print(f"tensor-core factors, interface-Krylov solve: its {info[0][0]}, relres {info[0][1]:.2e}, rel {e:.2e}")
+    assert info[0][1] <= 1e-9 and e <= 1e-5
+    p.close()
