@@ -159,3 +159,34 @@ def test_habc_persistent_sweep_gives_the_same_solve(H, mode):
     assert [i[0] for i in i0] == [i[0] for i in i1]
     assert rel(u1.cpu().numpy(), u0.cpu().numpy()) <= 1e-9
     p.close()
+
+
+def test_habc_graph_replay_gives_the_same_solve(H):
+    """use_graph: the HABC preconditioner (liftings with Lq, slot swaps, reconstructions
+    with D1 and D2) replayed from captured CUDA graphs gives the same iterates."""
+    w = CASES["uneven_4x3"]()
+    p = gpu_problem(H, w, "c64")
+    f = cuda(W.random_complex((2, w.N), 95))
+    u0, i0, _ = p.solve(f, tol=1e-9, restart=30, maxit=400)
+    u1, i1, _ = p.solve(f, tol=1e-9, restart=30, maxit=400, use_graph=True)
+    assert i0 == i1 and rel(u1.cpu().numpy(), u0.cpu().numpy()) <= 1e-12
+    p.close()
+
+
+def test_habc_misfit_gradient_matches_direct_adjoint(H):
+    """The gradient does not depend on the transmission condition (the decomposition
+    leaves the discrete solution unchanged): with the HABC preconditioner it matches the
+    oracle's direct-solve adjoint."""
+    from oracle.adjoint import misfit_gradient_direct
+    n = 63
+    w = W.workload("custom", n=n, N1=2, N2=2, medium="layered", seed=3, nrhs=2)
+    rec = np.arange((n - 1) * n + 1, n * n, 4)
+    rng = np.random.default_rng(2)
+    d = (rng.normal(size=(2, len(rec))) + 1j * rng.normal(size=(2, len(rec)))) * 1e-4
+    J, g, _ = misfit_gradient_direct(w.n, w.h, w.omega, w.m2, w.f, rec, d)
+    p = gpu_problem(H, w, "c64")
+    Jg, gg, _ = p.misfit_grad(cuda(w.f), torch.as_tensor(rec), cuda(d), tol=1e-11, maxit=2000)
+    e = rel(gg.cpu().numpy(), g)
+    print(f"HABC misfit: J rel {abs(Jg - J) / J:.2e}, gradient rel {e:.2e}")
+    assert abs(Jg - J) <= 1e-7 * J and e <= 1e-6
+    p.close()

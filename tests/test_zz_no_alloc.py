@@ -129,3 +129,22 @@ def test_noalloc_allocates_no_device_memory(H):
         torch.cuda.synchronize()
         assert _rel(z, ref) <= 3e-5
     p.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("c128", 1e-10), ("c64", 3e-5)])
+def test_noalloc_with_the_habc_transmission(H, prec, tol):
+    """The HABC transmission keeps a fourth interface buffer (the liftings' boundary
+    values) in the fixed array; two calls in a row against precond_apply."""
+    w = W.workload("custom", n=60, N1=3, N2=2, medium="layered", seed=3, xcuts=[0, 21, 39, 60], ycuts=[0, 33, 60])
+    m2 = torch.as_tensor(w.m2, dtype=torch.float64, device="cuda")
+    p = H.Problem(w.n, w.n, w.h, w.omega, m2, w.N1, w.N2, w.xcuts, w.ycuts, transmission="habc",
+                  autotune=False).factor(prec)
+    for call, nrhs in enumerate((3, 1)):
+        r = torch.as_tensor(W.random_complex((nrhs, w.N), 90 + call), device="cuda")
+        st, z = _noalloc(H, p, r, "BSP")
+        assert st == 0, H.lib().helm_last_error()
+        ref = p.precond_apply(r)
+        torch.cuda.synchronize()
+        for k in range(nrhs):
+            assert _rel(z[k], ref[k]) <= tol
+    p.close()
