@@ -95,6 +95,8 @@ def parse():
                     help="interface stages of fewer CTAs stay on the CUDA cores (-1: two per SM)")
     ap.add_argument("--no-tc-factor", action="store_true",
                     help="complex64 factorisation on the CUDA cores (default: trailing updates on the tensor cores)")
+    ap.add_argument("--sym-k", action="store_true",
+                    help="one-RHS interface stages that apply all of K read the packed symmetric tiles")
     ap.add_argument("--tc-min-rhs", type=int, default=16,
                     help="stages with at least this many RHS run on the tensor cores (1: all)")
     return ap.parse_args()
@@ -125,7 +127,8 @@ def precond_only(args):
     m2 = torch.as_tensor(w.m2, dtype=torch.float64, device="cuda")
     p = Problem(w.n, w.n, w.h, w.omega, m2, w.N1, w.N2, w.xcuts, w.ycuts, tensor_cores=TC_MODES[args.tensor_cores],
                 tc_min_rhs=args.tc_min_rhs, tc_scale=args.tc_scale, tc_iface_min_ctas=args.tc_iface_min_ctas,
-                autotune=not args.no_autotune, transmission=args.transmission, tc_factor=not args.no_tc_factor)
+                autotune=not args.no_autotune, transmission=args.transmission, tc_factor=not args.no_tc_factor,
+                sym_k=args.sym_k)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     p.factor(args.prec)
@@ -159,6 +162,7 @@ def precond_only(args):
     print(json.dumps({"mode": "precond", "workload": name, "nrhs": int(r.shape[0]), "prec": args.prec,
                       "sched": args.sched, "tensor_cores": args.tensor_cores, "factor_ms": factor_ms,
                       "factor_on_tensor_cores": p.factor_on_tensor_cores(),
+                      "iface_symmetric": p.iface_symmetric(r.shape[0]),
                       "ms_per_apply": ms, "unknowns_rhs_per_s": w.N * r.shape[0] / (ms / 1e3),
                       "kernels": kern}))
     p.close()
@@ -507,7 +511,7 @@ def gpu_arm(args):
     f = torch.as_tensor(w.f, dtype=torch.complex128, device=dev)
     p = Problem(w.n, w.n, w.h, w.omega, m2, w.N1, w.N2, w.xcuts, w.ycuts, tensor_cores=TC_MODES[args.tensor_cores],
                 tc_min_rhs=args.tc_min_rhs, tc_scale=args.tc_scale, tc_iface_min_ctas=args.tc_iface_min_ctas,
-                autotune=not args.no_autotune, tc_factor=not args.no_tc_factor)
+                autotune=not args.no_autotune, tc_factor=not args.no_tc_factor, sym_k=args.sym_k)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     p.factor(args.prec)
@@ -660,10 +664,15 @@ def gpu_arm(args):
         if tc_form:
             names["trace"] = ("iface_kernel (CUDA-core GEMV, the smaller stages) + tc_iface_kernel "
                               "(tcgen05 GEMM, the stages that fill the GPU)")
+        sym_form = p.iface_symmetric(w.nrhs)
+        if sym_form:
+            names["trace"] = ("iface_sym_kernel (packed symmetric boundary operators, each stored tile read "
+                              "once for both of its blocks)")
         # the ncu traffic figure belongs to the 1-RHS default workload it was captured on
         same_capture = dom == "trace" and wname == WORKLOAD and w.nrhs == 1 and not tc_form
+        kfile = "k_iface_sym.cu" if sym_form else "k_iface.cu"
         roofline = {"bound": "hbm", "achieved": bw, "peak": peak, "unit": "GB/s", "frac": bw / peak,
-                    "traffic": NCU_TRAFFIC.get(kernel_hash("k_iface.cu")) if same_capture else None,
+                    "traffic": NCU_TRAFFIC.get(kernel_hash(kfile)) if same_capture else None,
                     "algorithmic_bytes_per_launch": st_[2] / max(st_[0], 1),
                     "kernel": names.get(dom, dom), "launches": st_[0],
                     "peak_source": f"hbm_gbs of {peak_src}"}
@@ -722,6 +731,7 @@ def gpu_arm(args):
                                  if args.inner_maxit > 0 else None),
             "relres_host_check": check,
             "factor_on_tensor_cores": p.factor_on_tensor_cores(),
+            "iface_symmetric": p.iface_symmetric(w.nrhs),
             "err_vs_oracle": err_vs_oracle(u_main),
             "err_vs_oracle_note": ("rel. L2 of the first RHS's solution (tol above) against the oracle's sparse "
                                    "direct solution of the global system (nested-dissection LU + refinement)"),

@@ -163,6 +163,16 @@ typedef struct {
                            X_r = T_r^{-1} as a blocked Gauss-Jordan elimination (panels of 16
                            columns, partial pivoting) whose rank-16 trailing updates are
                            3xTF32 tensor-core GEMMs; 0: the CUDA-core elimination */
+    int sym_k;          /* 1: with complex64 factors, boundary_operators = 1, the optimized
+                           or impedance transmission and at most 1024 interface boundary
+                           points per subdomain, precond_factor also stores the symmetric
+                           part (K + K^T)/2 of each K (K = P^T A_loc^{-1} P is complex
+                           symmetric, A_loc being so; the two differ by rounding) as its
+                           upper-triangle 32 x 32 tiles, half the bytes of K, and the
+                           interface stages of one right-hand side that apply all of K (the
+                           block Jacobi residual, the interface operator S) read it, each
+                           stored tile once for both of its blocks.  0 (default): every
+                           interface stage applies the full K */
 } helm_setup_opts;
 
 typedef struct {
@@ -366,6 +376,32 @@ helm_status helm_habc_side_operator(const double* kappa, int L, double h, int n_
 /* 1 when the last precond_factor of p ran its eliminations' trailing updates on the
  * tensor cores (helm_setup_opts.tc_factor), else 0 (also for NULL or unfactored p). */
 int helm_factor_on_tensor_cores(const helm_problem* p);
+
+/* 1 when the interface stages that apply all of K (block Jacobi residual, interface
+ * operator S) in preconditioner applications with nrhs right-hand sides read the packed
+ * symmetric boundary operators of the last precond_factor (helm_setup_opts.sym_k),
+ * else 0 (also for NULL or unfactored p). */
+int helm_iface_symmetric(const helm_problem* p, int nrhs);
+
+/* Bounds-checking build (the library compiled with -DHELM_CHECK_BOUNDS; the normal
+ * build returns 0 from both calls and touches nothing).  In that build the kernels
+ * check their global accesses (every bulk copy and the computed loads and stores of the
+ * stage, interface, Krylov and HABC kernels) against the live device ranges: the
+ * library's allocations and the caller's buffers of the current call.  A failed check
+ * skips the access and is counted.
+ * helm_check_bounds_report: the failed checks since the last reset summed over the
+ * kernels' translation units (*violations), and the first one found (address, bytes,
+ * source line, source file name into unit[unit_len]); reset != 0 clears the counts.
+ * Host pointers, any may be NULL.  Returns 1 (checking build), 0 (normal build) or -1
+ * (CUDA error).  Synchronises the device.
+ * helm_check_bounds_selftest: runs the check, without any access, on a 256-byte
+ * allocation: results[0] = the whole allocation passes, results[1] = the byte past
+ * its end passes, results[2] = a 2-byte range straddling its end passes (expected
+ * 1, 0, 0; the two failures are counted).  results: host, 3 ints.  Returns 1, 0 or
+ * -1 as above. */
+int helm_check_bounds_report(long long* violations, unsigned long long* first_addr, long long* first_bytes,
+                             int* first_line, char* unit, int unit_len, int reset);
+int helm_check_bounds_selftest(int* results);
 
 /* Problem sizes of a handle: N = n_x*n_y unknowns, number of subdomains,
  * 2 N_e interface unknowns (trace points), bytes of the current factors. */

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhelm.so")
-SOURCES = ["helm_api.cu", "k_setup.cu", "k_factor.cu", "k_stage.cu", "k_iface.cu", "k_krylov.cu", "k_mgs.cu", "k_adjoint.cu", "k_tc.cu",
+SOURCES = ["helm_api.cu", "k_setup.cu", "k_factor.cu", "k_stage.cu", "k_iface.cu", "k_iface_sym.cu", "k_krylov.cu", "k_mgs.cu", "k_adjoint.cu", "k_tc.cu",
            "habc_host.cu", "k_habc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -38,21 +38,30 @@ def _stale(obj, src):
     if not os.path.exists(obj):
         return True
     t = os.path.getmtime(obj)
-    deps = [src, os.path.join(CSRC, "helm_internal.cuh"), os.path.join(INCLUDE, "helm.h")]
+    deps = [src, os.path.join(CSRC, "helm_internal.cuh"), os.path.join(CSRC, "helm_check.cuh"),
+            os.path.join(INCLUDE, "helm.h")]
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(verbose: bool = False, extra=()) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+# variant "check": the bounds-checking build (every checked global access of the kernels
+# tested against the live device ranges, see csrc/helm_check.cuh) as libhelm_check.so
+VARIANTS = {"": [], "check": ["-DHELM_CHECK_BOUNDS"]}
+
+
+def build(verbose: bool = False, extra=(), variant: str = "") -> str:
+    vflags = VARIANTS[variant]
+    bdir = BUILD + ("_" + variant if variant else "")
+    lib = LIB if not variant else os.path.join(HERE, f"libhelm_{variant}.so")
+    os.makedirs(bdir, exist_ok=True)
     cc = nvcc()
     jobs = []
     objs = []
     for s in SOURCES:
         src = os.path.join(CSRC, s)
-        obj = os.path.join(BUILD, s.replace(".cu", ".o"))
+        obj = os.path.join(bdir, s.replace(".cu", ".o"))
         objs.append(obj)
         if _stale(obj, src) or extra:
-            jobs.append([cc, "-c", src, "-o", obj] + flags(extra))
+            jobs.append([cc, "-c", src, "-o", obj] + flags(list(extra) + vflags))
 
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -64,13 +73,13 @@ def build(verbose: bool = False, extra=()) -> str:
                 sys.stderr.write(r.stdout + r.stderr)
             if r.returncode != 0:
                 raise RuntimeError("nvcc failed: " + " ".join(cmd))
-    if jobs or not os.path.exists(LIB):
-        cmd = [cc, "-shared", "-o", LIB] + objs + ARCH + ["-lcudart_static" if False else "-cudart=static"]
+    if jobs or not os.path.exists(lib):
+        cmd = [cc, "-shared", "-o", lib] + objs + ARCH + ["-cudart=static"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             sys.stderr.write(r.stdout + r.stderr)
             raise RuntimeError("link failed")
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":

@@ -14,6 +14,189 @@
 
 #include "helm_internal.cuh"
 
+// NVTX ranges around the entry points and every stage (header-only NVTX v3: each call
+// is a no-op unless a profiler injects its library)
+#if __has_include(<nvtx3/nvToolsExt.h>)
+#include <nvtx3/nvToolsExt.h>
+#define HELM_HAVE_NVTX 1
+#endif
+namespace {
+struct NvtxRange {
+    explicit NvtxRange(const char* name) {
+#ifdef HELM_HAVE_NVTX
+        nvtxRangePushA(name);
+#else
+        (void)name;
+#endif
+    }
+    ~NvtxRange() {
+#ifdef HELM_HAVE_NVTX
+        nvtxRangePop();
+#endif
+    }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+}  // namespace
+
+// ------------------------------------------------------------ bounds-checking build
+// The live device ranges the kernels may touch: every allocation of the library (the
+// cudaMalloc / cudaFree calls of this file go through hc_malloc / hc_free) and the
+// caller's buffers of the call in progress (HcCall).  Every change is uploaded to the
+// range table of each translation unit before the next launch.
+#ifdef HELM_CHECK_BOUNDS
+#include <mutex>
+namespace {
+struct HcUnit {
+    HcUpload up;
+    HcRead rd;
+    HcReset rs;
+    const char* file;
+};
+struct HcState {
+    std::mutex mu;
+    std::vector<HcUnit> units;
+    std::map<unsigned long long, unsigned long long> allocs;        // start -> end
+    std::vector<std::pair<unsigned long long, unsigned long long>> call;
+};
+HcState& hc() {
+    static HcState s;
+    return s;
+}
+cudaError_t hc_upload_locked(HcState& s) {
+    static HcTable t;
+    t.n = 0;
+    auto add = [&](unsigned long long lo, unsigned long long hi) {
+        if (lo < hi && t.n < HC_MAX_RANGES) t.r[t.n++] = {lo, hi};
+    };
+    for (auto& a : s.allocs) add(a.first, a.second);
+    for (auto& c : s.call) add(c.first, c.second);
+    cudaError_t e = cudaSuccess;
+    for (auto& u : s.units)
+        if (e == cudaSuccess) e = u.up(t);
+    return e;
+}
+cudaError_t hc_malloc(void** p, size_t n) {
+    const cudaError_t e = cudaMalloc(p, n);
+    if (e != cudaSuccess || !*p) return e;
+    HcState& s = hc();
+    std::lock_guard<std::mutex> g(s.mu);
+    const unsigned long long lo = reinterpret_cast<unsigned long long>(*p);
+    s.allocs[lo] = lo + n;
+    return hc_upload_locked(s);
+}
+cudaError_t hc_free(void* p) {
+    {
+        HcState& s = hc();
+        std::lock_guard<std::mutex> g(s.mu);
+        s.allocs.erase(reinterpret_cast<unsigned long long>(p));
+        (void)hc_upload_locked(s);
+    }
+    return cudaFree(p);
+}
+}  // namespace
+void hc_register_unit(HcUpload up, HcRead rd, HcReset rs, const char* file) {
+    HcState& s = hc();
+    std::lock_guard<std::mutex> g(s.mu);
+    s.units.push_back({up, rd, rs, file});
+}
+namespace {
+// the caller's buffers of one entry point, for the duration of the call
+struct HcCall {
+    size_t keep;
+    HcCall(std::initializer_list<std::pair<const void*, size_t>> bufs) {
+        HcState& s = hc();
+        std::lock_guard<std::mutex> g(s.mu);
+        keep = s.call.size();
+        for (auto& b : bufs)
+            if (b.first && b.second) {
+                const unsigned long long lo = reinterpret_cast<unsigned long long>(b.first);
+                s.call.push_back({lo, lo + b.second});
+            }
+        (void)hc_upload_locked(s);
+    }
+    ~HcCall() {
+        HcState& s = hc();
+        std::lock_guard<std::mutex> g(s.mu);
+        s.call.resize(keep);
+    }
+    HcCall(const HcCall&) = delete;
+    HcCall& operator=(const HcCall&) = delete;
+};
+}  // namespace
+#define cudaMalloc(pp, n) hc_malloc((void**)(pp), (n))
+#define cudaFree(p) hc_free((void*)(p))
+#else
+namespace {
+struct HcCall {
+    HcCall(std::initializer_list<std::pair<const void*, size_t>>) {}
+};
+}  // namespace
+#endif
+
+extern "C" int helm_check_bounds_report(long long* violations, unsigned long long* first_addr,
+                                        long long* first_bytes, int* first_line, char* unit, int unit_len,
+                                        int reset) {
+#ifdef HELM_CHECK_BOUNDS
+    HcState& s = hc();
+    std::lock_guard<std::mutex> g(s.mu);
+    long long total = 0;
+    bool have = false;
+    for (auto& u : s.units) {
+        HcBad b{};
+        if (u.rd(b) != cudaSuccess) return -1;
+        total += (long long)b.count;
+        if (b.count && !have) {
+            have = true;
+            if (first_addr) *first_addr = b.addr;
+            if (first_bytes) *first_bytes = (long long)b.bytes;
+            if (first_line) *first_line = b.line;
+            if (unit && unit_len > 0) snprintf(unit, (size_t)unit_len, "%s", u.file);
+        }
+        if (reset && u.rs() != cudaSuccess) return -1;
+    }
+    if (violations) *violations = total;
+    if (!have) {
+        if (first_addr) *first_addr = 0;
+        if (first_bytes) *first_bytes = 0;
+        if (first_line) *first_line = 0;
+        if (unit && unit_len > 0) unit[0] = 0;
+    }
+    return 1;
+#else
+    (void)first_addr; (void)first_bytes; (void)first_line; (void)unit; (void)unit_len; (void)reset;
+    if (violations) *violations = 0;
+    return 0;
+#endif
+}
+
+#ifdef HELM_CHECK_BOUNDS
+namespace {
+__global__ void hc_selftest_kernel(const unsigned char* buf, int* out) {
+    out[0] = HELM_CHK(buf, 256);          // the whole allocation
+    out[1] = HELM_CHK(buf + 256, 1);      // the byte past its end
+    out[2] = HELM_CHK(buf + 255, 2);      // straddles its end
+}
+}  // namespace
+#endif
+
+extern "C" int helm_check_bounds_selftest(int* results) {
+#ifdef HELM_CHECK_BOUNDS
+    unsigned char* buf = nullptr;
+    int* out = nullptr;
+    if (cudaMalloc(&buf, 256) != cudaSuccess) return -1;
+    if (cudaMalloc(&out, 3 * sizeof(int)) != cudaSuccess) { cudaFree(buf); return -1; }
+    hc_selftest_kernel<<<1, 1>>>(buf, out);
+    cudaError_t e = cudaMemcpy(results, out, 3 * sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(out);
+    cudaFree(buf);
+    return e == cudaSuccess ? 1 : -1;
+#else
+    (void)results;
+    return 0;
+#endif
+}
+
 size_t factor_work_elems(int max_mx, size_t elem);
 int mgs_grid();
 long long mgs_max_n(int grid);
@@ -231,6 +414,13 @@ struct helm_problem {
     void* d_X = nullptr;
     void* d_K = nullptr;             // boundary operators of all subdomains
     size_t K_bytes = 0;
+    // packed symmetric boundary operators (complex64, k_iface_sym.cu): the tiles, the
+    // per-tile partial sums and arrival counters of one stage, tiles per row of the largest K
+    float2* d_Kp = nullptr;
+    float2* d_spart = nullptr;
+    int* d_scnt = nullptr;
+    long long kp_elems = 0;
+    int sym_ntmax = 0;
     size_t X_bytes = 0;
     float* d_XT = nullptr;           // complex64 factors in the tensor cores' operand layout (k_tc.cu)
     float* d_tcpart = nullptr;       // partial sums of the tensor-core interface stages split over CTAs
@@ -468,6 +658,7 @@ extern "C" void helm_default_setup_opts(helm_setup_opts* o) {
     o->n_pade = 8;
     o->pade_phi = 3.14159265358979323846 / 3.0;
     o->tc_factor = 1;
+    o->sym_k = 0;
 }
 
 extern "C" const char* helm_last_error(void) { return g_err.c_str(); }
@@ -594,11 +785,13 @@ static helm_status habc_setup(helm_problem* p, const int* d_ssub, const int* d_s
 extern "C" helm_status helm_setup(int n_x, int n_y, double h, double omega, const double* m2, int N1, int N2,
                                   const int* xcuts, const int* ycuts, const helm_setup_opts* opts,
                                   helm_problem** out) {
+    NvtxRange nvtx("helm_setup");
     if (!out) return arg_error("helm_setup: out is NULL");
     *out = nullptr;
     if (n_x < 1 || n_y < 1) return arg_error("helm_setup: n_x, n_y must be >= 1");
     if (!(h > 0) || !(omega > 0)) return arg_error("helm_setup: h and omega must be > 0");
     if (!m2) return arg_error("helm_setup: m2 is NULL");
+    HcCall hcc{{m2, (size_t)n_x * n_y * sizeof(double)}};
     if (N1 < 1 || N2 < 1 || N1 > n_x || N2 > n_y) return arg_error("helm_setup: need 1 <= N1 <= n_x, 1 <= N2 <= n_y");
     helm_setup_opts so;
     helm_default_setup_opts(&so);
@@ -714,8 +907,11 @@ extern "C" helm_status helm_setup(int n_x, int n_y, double h, double omega, cons
         s.dev.Lb = lb;
         s.dev.koff = koff;
         koff += (long long)lb * lb;
+        s.dev.kpoff = p->kp_elems;
+        p->kp_elems += sym_tiles(lb) * SYM_TB * SYM_TB;
         p->max_Lb = std::max(p->max_Lb, lb);
     }
+    p->sym_ntmax = (p->max_Lb + SYM_TB - 1) / SYM_TB;
 
     // stage lists and their subdomain arrays
     std::vector<int> all_stage_subs;
@@ -932,6 +1128,7 @@ extern "C" helm_status helm_destroy(helm_problem* p) {
     }
     if (p->d_X) cudaFree(p->d_X);
     if (p->d_K) cudaFree(p->d_K);
+    dfree(p->d_Kp); dfree(p->d_spart); dfree(p->d_scnt);
     if (p->d_Lq) cudaFree(p->d_Lq);
     if (p->d_D1) cudaFree(p->d_D1);
     if (p->d_D2) cudaFree(p->d_D2);
@@ -1020,6 +1217,7 @@ static helm_status build_boundary_operators_t(helm_problem* p, cudaStream_t st) 
 }
 
 static helm_status build_boundary_operators(helm_problem* p, cudaStream_t st) {
+    NvtxRange nvtx("boundary operators");
     return p->prec == HELM_PREC_C64 ? build_boundary_operators_t<float>(p, st)
                                     : build_boundary_operators_t<double>(p, st);
 }
@@ -1168,12 +1366,45 @@ static helm_status habc_precompute_t(helm_problem* p, cudaStream_t st) {
     return HELM_OK;
 }
 static helm_status habc_precompute(helm_problem* p, cudaStream_t st) {
+    NvtxRange nvtx("HABC stage matrices");
     if (p->max_Lb == 0) return HELM_OK;
     return p->prec == HELM_PREC_C64 ? habc_precompute_t<float>(p, st) : habc_precompute_t<double>(p, st);
 }
 
 // ----------------------------------------------------------------- factor
+// the packed symmetric operators: complex64, the scalar transmissions (the HABC stage
+// matrices are not symmetric), K built, at most SYM_MAXLB boundary points per subdomain
+static bool sym_wanted(const helm_problem* p, int prec) {
+    return p->sopts.sym_k && prec == HELM_PREC_C64 && p->sopts.boundary_operators && !p->habc &&
+           p->max_Lb > 0 && p->max_Lb <= SYM_MAXLB;
+}
+// their bytes: the tiles, the partial sums of one stage, the arrival counters
+static size_t sym_bytes(const helm_problem* p) {
+    const size_t ns = p->subs.size(), nt = (size_t)p->sym_ntmax;
+    return (size_t)p->kp_elems * sizeof(float2) + ns * nt * nt * SYM_TB * sizeof(float2) + ns * nt * sizeof(int);
+}
+static helm_status build_symmetric_operators(helm_problem* p, cudaStream_t st) {
+    const size_t ns = p->subs.size(), nt = (size_t)p->sym_ntmax;
+    cudaError_t e;
+    if ((e = dalloc(p->d_Kp, (size_t)p->kp_elems)) != cudaSuccess || (e = dalloc(p->d_spart, ns * nt * nt * SYM_TB)) ||
+        (e = dalloc(p->d_scnt, ns * nt))) {
+        dfree(p->d_Kp); dfree(p->d_spart); dfree(p->d_scnt);
+        return cuda_status(e, "precond_factor: allocating the packed symmetric boundary operators");
+    }
+    e = cudaMemsetAsync(p->d_scnt, 0, ns * nt * sizeof(int), st);
+    if (e == cudaSuccess)
+        e = launch_sym_pack(p->d_subtab, (int)ns, p->sym_ntmax, (const float2*)p->d_K, p->d_Kp, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_status(e, "precond_factor: packing the symmetric boundary operators");
+    return HELM_OK;
+}
+
+extern "C" int helm_iface_symmetric(const helm_problem* p, int nrhs) {
+    return p && p->factored && p->d_Kp && nrhs == 1;
+}
+
 extern "C" helm_status precond_factor(helm_problem* p, helm_prec prec, void* stream) {
+    NvtxRange nvtx("precond_factor");
     if (!p) return arg_error("precond_factor: NULL handle");
     if (prec != HELM_PREC_C128 && prec != HELM_PREC_C64) return arg_error("precond_factor: unknown precision");
     cudaStream_t st = (cudaStream_t)stream;
@@ -1209,7 +1440,8 @@ extern "C" helm_status precond_factor(helm_problem* p, helm_prec prec, void* str
         long long kel = 0;
         for (auto& s : p->subs) kel += (long long)s.dev.Lb * s.dev.Lb;
         const size_t keep = bytes + (size_t)xtoff * sizeof(float) +
-                            (p->sopts.boundary_operators ? (size_t)kel * elem * (p->habc ? 4 : 1) : 0);
+                            (p->sopts.boundary_operators ? (size_t)kel * elem * (p->habc ? 4 : 1) : 0) +
+                            (sym_wanted(p, prec) ? sym_bytes(p) : 0);
         if (keep > p->sopts.device_budget) {
             char buf[200];
             snprintf(buf, sizeof buf, "precond_factor: the factors need %zu bytes, more than the device budget of %zu",
@@ -1222,6 +1454,7 @@ extern "C" helm_status precond_factor(helm_problem* p, helm_prec prec, void* str
     drop_graphs(p);
     if (p->d_X) { cudaFree(p->d_X); p->d_X = nullptr; p->X_bytes = 0; p->factored = 0; }
     if (p->d_K) { cudaFree(p->d_K); p->d_K = nullptr; p->K_bytes = 0; }
+    dfree(p->d_Kp); dfree(p->d_spart); dfree(p->d_scnt);
     for (void** q : {&p->d_Lq, &p->d_D1, &p->d_D2})
         if (*q) { cudaFree(*q); *q = nullptr; }
     if (p->d_XT) { cudaFree(p->d_XT); p->d_XT = nullptr; p->XT_bytes = 0; p->tc_mt = 0; p->tc_split = 0; }
@@ -1294,6 +1527,7 @@ extern "C" helm_status precond_factor(helm_problem* p, helm_prec prec, void* str
     {
         helm_status ks = p->sopts.boundary_operators ? build_boundary_operators(p, st) : HELM_OK;
         if (ks == HELM_OK && p->habc) ks = habc_precompute(p, st);
+        if (ks == HELM_OK && sym_wanted(p, prec)) ks = build_symmetric_operators(p, st);
         if (ks != HELM_OK) return ks;
     }
     p->factored = 1;
@@ -1341,8 +1575,9 @@ struct PcWork {
 
 // algorithmic bytes and flops of one interface stage: the rows of K it applies,
 // the incoming data it reads, the outgoing data (and base / sub) it moves
+// (packed symmetric form: the stored tiles the stage reads, each once, instead of the rows)
 static void iface_accounting(const helm_problem* p, const StageDesc& sd, int nrhs, double sT, double& bytes,
-                             double& flops) {
+                             double& flops, bool sym = false) {
     for (int id : sd.subs) {
         const SubDev& d = p->subs[id].dev;
         double rows = 0;
@@ -1350,7 +1585,21 @@ static void iface_accounting(const helm_problem* p, const StageDesc& sd, int nrh
             if ((sd.mask & (1 << sde)) && d.bo[sde] >= 0) rows += (sde == SW || sde == SE) ? d.my : d.mx;
         const double io = d.Lb * sT * ((sd.in0 >= 0) + (sd.in1 >= 0)) +
                           rows * sT * (1 + (sd.dst2 >= 0) + (sd.base >= 0) + (sd.sub >= 0));
-        bytes += rows * d.Lb * sT + io * nrhs;
+        double kbytes = rows * d.Lb * sT;
+        if (sym) {
+            const int nt = (d.Lb + SYM_TB - 1) / SYM_TB;
+            unsigned long long M = 0;
+            for (int sde = 0; sde < 4; ++sde)
+                if ((sd.mask & (1 << sde)) && d.bo[sde] >= 0) {
+                    const int len = (sde == SW || sde == SE) ? d.my : d.mx;
+                    for (int t = d.bo[sde] / SYM_TB; t <= (d.bo[sde] + len - 1) / SYM_TB; ++t) M |= 1ull << t;
+                }
+            long long tiles = 0;
+            for (int I = 0; I < nt; ++I)
+                for (int J = I; J < nt; ++J) tiles += ((M >> I) & 1) || ((M >> J) & 1);
+            kbytes = (double)tiles * SYM_TB * SYM_TB * sT;
+        }
+        bytes += kbytes + io * nrhs;
         flops += 8.0 * rows * d.Lb * nrhs;
     }
 }
@@ -1687,6 +1936,8 @@ static helm_status run_stage_t(helm_problem* p, const PcWork& w, const PcCtx& cx
     const bool tc = cx.tc;
     T* buf[4] = {(T*)w.trace[0], (T*)w.trace[1], (T*)w.trace[2], (T*)w.trace[3]};
     auto B = [&](int id) -> T* { return id < 0 ? nullptr : buf[id]; };
+    NvtxRange nvtx(sd.iface ? "interface stage" : sd.final_ ? "reconstruction stage" : sd.src ? "lifting stage"
+                                                                                              : "full stage");
     if (sd.iface && p->d_K) {
         IfaceArgs<R> ia{};
         ia.subtab = p->d_subtab;
@@ -1710,11 +1961,26 @@ static helm_status run_stage_t(helm_problem* p, const PcWork& w, const PcCtx& cx
                 if ((sd.mask & (1 << sde)) && d.bo[sde] >= 0) rows += (sde == SW || sde == SE) ? d.my : d.mx;
             max_rows = std::max(max_rows, rows);
         }
+        // one complex64 RHS applying K itself: the packed symmetric tiles
+        const bool sym = sizeof(R) == 4 && nrhs == 1 && p->d_Kp && sd.kmat == KMAT_K && (sd.mask & 15) == 15;
         double bytes = 0, flops = 0;
-        if (p->prof_on) iface_accounting(p, sd, nrhs, sizeof(T), bytes, flops);
+        if (p->prof_on) iface_accounting(p, sd, nrhs, sizeof(T), bytes, flops, sym);
         prof_begin(p, HELM_K_TRACE, st);
         IfaceCfg tmp;
-        cudaError_t e = launch_iface<R>(ia, (int)sd.subs.size(), max_rows, p->max_Lb, st, iface_shape_for(p, nrhs, tmp));
+        cudaError_t e;
+        if constexpr (sizeof(R) == 4) {
+            if (sym) {
+                ia.Kp = p->d_Kp;
+                ia.spart = p->d_spart;
+                ia.scnt = p->d_scnt;
+                ia.ntmax = p->sym_ntmax;
+                e = launch_iface_sym(ia, (int)sd.subs.size(), st);
+            } else {
+                e = launch_iface<R>(ia, (int)sd.subs.size(), max_rows, p->max_Lb, st, iface_shape_for(p, nrhs, tmp));
+            }
+        } else {
+            e = launch_iface<R>(ia, (int)sd.subs.size(), max_rows, p->max_Lb, st, iface_shape_for(p, nrhs, tmp));
+        }
         prof_end(p, HELM_K_TRACE, bytes, st, flops);
         if (e != cudaSuccess) return cuda_status(e, "interface stage launch");
         return HELM_OK;
@@ -1963,12 +2229,15 @@ static helm_status run_captured(helm_problem* p, int tag, int nrhs, cudaStream_t
 
 extern "C" helm_status precond_apply(helm_problem* p, int sched, const helm_c128* r, helm_c128* z, int nrhs,
                                      void* stream) {
+    NvtxRange nvtx("precond_apply");
     if (!p) return arg_error("precond_apply: NULL handle");
     if (!p->factored) { set_error("precond_apply: call precond_factor first"); return HELM_ERR_STATE; }
     if ((sched < 0 || sched >= HELM_NSCHED)) return arg_error("precond_apply: unknown schedule");
     if (nrhs < 0) return arg_error("precond_apply: nrhs < 0");
     if (nrhs == 0) return HELM_OK;
     if (!r || !z) return arg_error("precond_apply: NULL array");
+    const size_t vb = (size_t)p->N() * nrhs * sizeof(double2);
+    HcCall hcc{{r, vb}, {z, vb}};
     return run_precond(p, sched, (const double2*)r, (double2*)z, nrhs, (cudaStream_t)stream);
 }
 
@@ -1984,6 +2253,7 @@ static std::atomic<void*> g_noalloc_ptr[128];
 
 extern "C" helm_status precond_apply_noalloc(helm_problem* p, int sched, const helm_c128* r, helm_c128* z, int nrhs,
                                              void* stream) {
+    NvtxRange nvtx("precond_apply_noalloc");
     if (!p) return arg_error("precond_apply_noalloc: NULL handle");
     if (!p->factored) { set_error("precond_apply_noalloc: call precond_factor first"); return HELM_ERR_STATE; }
     if ((sched < 0 || sched >= HELM_NSCHED)) return arg_error("precond_apply_noalloc: unknown schedule");
@@ -2020,6 +2290,8 @@ extern "C" helm_status precond_apply_noalloc(helm_problem* p, int sched, const h
         if (e != cudaSuccess || !base) return cuda_status(e, "precond_apply_noalloc: cudaGetSymbolAddress");
         g_noalloc_ptr[dev].store(base);
     }
+    const size_t vb = (size_t)p->N() * nrhs * sizeof(double2);
+    HcCall hcc{{r, vb}, {z, vb}, {base, (size_t)HELM_NOALLOC_SCRATCH_BYTES}};
     unsigned char* b = (unsigned char*)base;
     unsigned char* v = b + nbuf * tbytes;             // after the interface buffers
     unsigned char* tail = v + ybytes + nbytes + pbytes;
@@ -2031,10 +2303,13 @@ extern "C" helm_status precond_apply_noalloc(helm_problem* p, int sched, const h
 }
 
 extern "C" helm_status helm_matvec(helm_problem* p, const helm_c128* u, helm_c128* Au, int nrhs, void* stream) {
+    NvtxRange nvtx("helm_matvec");
     if (!p) return arg_error("helm_matvec: NULL handle");
     if (nrhs < 0) return arg_error("helm_matvec: nrhs < 0");
     if (nrhs == 0) return HELM_OK;
     if (!u || !Au) return arg_error("helm_matvec: NULL array");
+    const size_t vb = (size_t)p->N() * nrhs * sizeof(double2);
+    HcCall hcc{{u, vb}, {Au, vb}};
     launch_matvec(p->d_adiag, p->nx, p->ny, (const double2*)u, (double2*)Au, nrhs, (cudaStream_t)stream);
     HELM_CUDA_TRY(cudaGetLastError());
     return HELM_OK;
@@ -2476,6 +2751,7 @@ static helm_status fgmres_core(helm_problem* p, KrylovWS& kw, long long n, int n
 template <typename R, typename VT>
 static helm_status run_precond_iface_t(helm_problem* p, int sched, const double2* r, double2* z, int nrhs,
                                        const helm_opts& o, cudaStream_t st) {
+    NvtxRange nvtx("interface FGMRES");
     using T = Cx<R>;
     const std::vector<StageDesc>& stg = p->sched[sched];
     if (stg.size() < 2 || p->ntrace == 0) return run_precond(p, sched, r, z, nrhs, st);   // one subdomain
@@ -2684,11 +2960,14 @@ static helm_status gmres_impl(helm_problem* p, const double2* f, double2* u, int
 
 extern "C" helm_status gmres_solve(helm_problem* p, const helm_c128* f, helm_c128* u, int nrhs, const helm_opts* opts,
                                    helm_info* info, void* stream) {
+    NvtxRange nvtx("gmres_solve");
     if (!p) return arg_error("gmres_solve: NULL handle");
     if (!p->factored) { set_error("gmres_solve: call precond_factor first"); return HELM_ERR_STATE; }
     if (nrhs < 0) return arg_error("gmres_solve: nrhs < 0");
     if (nrhs == 0) return HELM_OK;
     if (!f || !u) return arg_error("gmres_solve: NULL array");
+    const size_t vb = (size_t)p->N() * nrhs * sizeof(double2);
+    HcCall hcc{{f, vb}, {u, vb}};
     helm_opts o;
     helm_default_opts(&o);
     if (opts) o = *opts;
@@ -2746,12 +3025,16 @@ extern "C" helm_status gmres_solve(helm_problem* p, const helm_c128* f, helm_c12
 extern "C" helm_status misfit_grad(helm_problem* p, const helm_c128* f, int nsrc, const int* rec_idx, int nrec,
                                    const helm_c128* d, const helm_opts* opts, double* misfit, double* grad_m2,
                                    helm_c128* u_out, void* stream) {
+    NvtxRange nvtx("misfit_grad");
     if (!p) return arg_error("misfit_grad: NULL handle");
     if (!p->factored) { set_error("misfit_grad: call precond_factor first"); return HELM_ERR_STATE; }
     if (nsrc < 1 || nrec < 1) return arg_error("misfit_grad: nsrc and nrec must be >= 1");
     if (!f || !rec_idx || !d || !misfit || !grad_m2) return arg_error("misfit_grad: NULL array");
     cudaStream_t st = (cudaStream_t)stream;
     const long long N = p->N();
+    HcCall hcc{{f, (size_t)nsrc * N * sizeof(double2)}, {rec_idx, (size_t)nrec * sizeof(int)},
+               {d, (size_t)nsrc * nrec * sizeof(double2)}, {grad_m2, (size_t)N * sizeof(double)},
+               {u_out, (size_t)nsrc * N * sizeof(double2)}};
     // receivers must be valid nodes
     {
         std::vector<int> r(nrec);

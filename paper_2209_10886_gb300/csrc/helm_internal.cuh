@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "helm.h"
+#include "helm_check.cuh"
 
 // ----------------------------------------------------------------- complex
 // float2 / double2 carry complex64 / complex128 values (re, im).
@@ -114,6 +115,7 @@ struct SubDev {
     int bo[4];
     int Lb;
     long long koff;            // element offset of the Lb x Lb boundary operator K in its array
+    long long kpoff;           // element offset of K's packed symmetric tiles (k_iface_sym.cu)
     long long xtoff;           // float offset of this subdomain's factors in the tensor-core layout (k_tc.cu)
     int tcmt;                  // 128-node tiles of that layout: 1 (mx <= 128), 2 (mx <= 256), 0 (wider)
     long long eoff;            // offset of this subdomain's 2 (mx + my) boundary slots in the edge scratch
@@ -199,6 +201,10 @@ template <typename R> struct IfaceArgs {
     // floats) and one arrival counter per output tile (cnt_cap, zero between launches)
     float* part; long long part_cap;
     int* cnt; int cnt_cap;
+    // packed symmetric form (complex64, one RHS, k_iface_sym.cu): the upper-triangle tiles
+    // of every K, the per-tile partial sums (ntmax^2 tiles of 32 values per subdomain id)
+    // and one arrival counter per (subdomain id, row tile), zero between launches
+    const T* Kp; T* spart; int* scnt; int ntmax;
 };
 
 // output rows of one work item of an interface stage (host tables and kernels agree on it)
@@ -292,6 +298,21 @@ template <typename R>
 cudaError_t launch_sweep_dep(const IfaceArgs<R>& a, const SweepStage* stages, const int4* items, int nitems,
                              const int* need, const int2* unit_deps, const int* deps, int* counters, int max_Lb,
                              cudaStream_t st);
+// Packed symmetric boundary operators (k_iface_sym.cu).  K = P^T A_loc^{-1} P is complex
+// symmetric (A_loc is); its upper triangle is stored in SYM_TB x SYM_TB tiles, tile row
+// by tile row, tile (I, J >= I) at kpoff + (I nt - I (I - 1) / 2 + J - I) SYM_TB^2, zero
+// past Lb (nt = ceil(Lb / SYM_TB) <= 32)
+constexpr int SYM_TB = 32;
+constexpr int SYM_MAXLB = 1024;
+__host__ __device__ __forceinline__ long long sym_tiles(int Lb) {
+    const long long nt = (Lb + SYM_TB - 1) / SYM_TB;
+    return nt * (nt + 1) / 2;
+}
+// Kp = the symmetric part (K + K^T) / 2 of every subdomain's K, packed as above
+cudaError_t launch_sym_pack(const SubDev* subtab, int nsub, int ntmax, const float2* K, float2* Kp, cudaStream_t st);
+// one complex64 interface stage with one RHS from the packed operators (a.Kp, a.spart,
+// a.scnt, a.ntmax set); the same outputs as launch_iface up to rounding
+cudaError_t launch_iface_sym(const IfaceArgs<float>& a, int nactive, cudaStream_t st);
 // a whole sweep (nstages interface stages, in order) in one cooperative launch of `grid`
 // CTAs (sweep_grid: the co-resident count, 0 when unavailable); bar: two zeroed words
 template <typename R> int sweep_grid(int nrhs, int max_Lb);

@@ -16,10 +16,10 @@ __global__ void receiver_residual_kernel(const double2* __restrict__ u, long lon
     const int s = blockIdx.x;
     double acc = 0.0;
     for (int k = threadIdx.x; k < nrec; k += blockDim.x) {
-        const double2 uv = u[(long long)s * N + rec[k]];
-        const double2 dv = d[(long long)s * nrec + k];
+        const double2 uv = HLD(u + (long long)s * N + HLD(rec + k));
+        const double2 dv = HLD(d + (long long)s * nrec + k);
         const double2 rv = make_double2(uv.x - dv.x, uv.y - dv.y);
-        res[(long long)s * nrec + k] = rv;
+        HST(res + (long long)s * nrec + k, rv);
         acc += rv.x * rv.x + rv.y * rv.y;
     }
     sh[threadIdx.x] = acc;
@@ -37,8 +37,9 @@ __global__ void adjoint_rhs_kernel(const double2* __restrict__ res, const int* _
     const int s = blockIdx.x;
     if (threadIdx.x != 0) return;     // serial per source: receivers may repeat
     for (int k = 0; k < nrec; ++k) {
-        const double2 rv = res[(long long)s * nrec + k];
-        double2* t = f_adj + (long long)s * N + rec[k];
+        const double2 rv = HLD(res + (long long)s * nrec + k);
+        double2* t = f_adj + (long long)s * N + HLD(rec + k);
+        if (!HELM_CHK(t, sizeof(double2))) continue;
         t->x += rv.x * inv_h2;
         t->y += -rv.y * inv_h2;
     }
@@ -50,7 +51,7 @@ __global__ void gradient_kernel(const double2* __restrict__ U, const double2* __
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
         const int a = (int)(p % nx), b = (int)(p / nx);
         const int nouter = (a == 0) + (a == nx - 1) + (b == 0) + (b == ny - 1);
-        const double m = m2[p];
+        const double m = HLD(m2 + p);
         const double wh = omega * h;
         double2 da = make_double2(-wh * wh, 0.0);
         if (nouter) {
@@ -63,11 +64,11 @@ __global__ void gradient_kernel(const double2* __restrict__ U, const double2* __
         }
         double g = 0.0;
         for (int s = 0; s < nsrc; ++s) {
-            const double2 l = Lt[(long long)s * N + p], u = U[(long long)s * N + p];
+            const double2 l = HLD(Lt + (long long)s * N + p), u = HLD(U + (long long)s * N + p);
             const double2 lu = make_double2(l.x * u.x - l.y * u.y, l.x * u.y + l.y * u.x);
             g -= lu.x * da.x - lu.y * da.y;
         }
-        grad[p] = g;
+        HST(grad + p, g);
     }
 }
 

@@ -419,17 +419,17 @@ __global__ void habc_form_kernel(const HabcSub* __restrict__ subs, const T* __re
     const long long LL = (long long)s.Lb * s.Lb;
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < LL; e += (long long)gridDim.x * blockDim.x) {
         if (phase == 0) {
-            const T v = K[s.koff + e];
-            K64[s.toff + e] = make_double2((double)v.x, (double)v.y);
+            const T v = HLD(K + s.koff + e);
+            HST(K64 + s.toff + e, make_double2((double)v.x, (double)v.y));
         } else {
             const int r = (int)(e / s.Lb), c = (int)(e % s.Lb);
             int pt;
             const int sd = side_of(s, c, pt);
-            const double2 ca = tc[s.tin[sd] + pt].ca;            // c0 = -ca of the base Robin condition
-            const double2 k = K64[s.toff + e], kr = KR[s.toff + e];
+            const double2 ca = HLD(tc + s.tin[sd] + pt).ca;      // c0 = -ca of the base Robin condition
+            const double2 k = HLD(K64 + s.toff + e), kr = HLD(KR + s.toff + e);
             // I - K C with C = 2 Rin - I - diag(c0):  I - 2 K Rin + K + K diag(c0)
             const double2 kc0 = cmul(k, make_double2(-ca.x, -ca.y));
-            W[s.toff + e] = make_double2((r == c ? 1.0 : 0.0) - 2.0 * kr.x + k.x + kc0.x, -2.0 * kr.y + k.y + kc0.y);
+            HST(W + s.toff + e, make_double2((r == c ? 1.0 : 0.0) - 2.0 * kr.x + k.x + kc0.x, -2.0 * kr.y + k.y + kc0.y));
         }
     }
 }
@@ -447,20 +447,21 @@ __global__ void habc_final_kernel(const HabcSub* __restrict__ subs, const double
         const int r = (int)(e / s.Lb), c = (int)(e % s.Lb);
         int pr, pc;
         const int sr = side_of(s, r, pr), sc = side_of(s, c, pc);
-        const double2 rin = sr == sc ? Mside[s.moff[sr] + (long long)pr * s.len[sr] + pc] : make_double2(0.0, 0.0);
-        const double2 ca = tc[s.tin[sr] + pr].ca;
+        const double2 rin = sr == sc ? HLD(Mside + s.moff[sr] + (long long)pr * s.len[sr] + pc) : make_double2(0.0, 0.0);
+        const double2 ca = HLD(tc + s.tin[sr] + pr).ca;
         const double2 c0 = make_double2(-ca.x, -ca.y);
-        const double2 p1 = P1[s.toff + e], rp = RP[s.toff + e], w = W[s.toff + e], rw = RW[s.toff + e];
+        const double2 p1 = HLD(P1 + s.toff + e), rp = HLD(RP + s.toff + e), w = HLD(W + s.toff + e),
+                      rw = HLD(RW + s.toff + e);
         const double id = r == c ? 1.0 : 0.0;
         const double2 q = make_double2(4.0 * (p1.x - rp.x) + id - 2.0 * rin.x, 4.0 * (p1.y - rp.y) - 2.0 * rin.y);
         const double2 lq = make_double2(4.0 * (w.x - rw.x), 4.0 * (w.y - rw.y));
         const double2 c0p = cmul(c0, p1), c0w = cmul(c0, w);
         const double2 d1 = make_double2(rin.x + 2.0 * rp.x - p1.x - c0p.x, rin.y + 2.0 * rp.y - p1.y - c0p.y);
         const double2 d2 = make_double2(2.0 * rw.x - w.x - c0w.x, 2.0 * rw.y - w.y - c0w.y);
-        Q[s.koff + e] = from_c128<T>(q);
-        Lq[s.koff + e] = from_c128<T>(lq);
-        D1[s.koff + e] = from_c128<T>(d1);
-        D2[s.koff + e] = from_c128<T>(d2);
+        HST(Q + s.koff + e, from_c128<T>(q));
+        HST(Lq + s.koff + e, from_c128<T>(lq));
+        HST(D1 + s.koff + e, from_c128<T>(d1));
+        HST(D2 + s.koff + e, from_c128<T>(d2));
     }
 }
 
@@ -471,7 +472,7 @@ __global__ void trace_swap_kernel(const T* __restrict__ in, T* __restrict__ out,
     const long long tot = ntrace * nrhs;
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
         const long long k = e / ntrace, t = e - k * ntrace;
-        out[e] = in[k * ntrace + swp[t]];
+        HST(out + e, HLD(in + k * ntrace + HLD(swp + t)));
     }
 }
 

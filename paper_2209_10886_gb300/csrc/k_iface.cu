@@ -31,6 +31,7 @@ constexpr long long SWEEP_WAIT = 2000000000LL;   // cycles (~1 s) before a grid 
 // LDCG: read through L2 only (data another SM wrote earlier in the same launch)
 template <typename T, bool LDCG>
 __device__ __forceinline__ T ldg_(const T* p) {
+    if (!HELM_CHK(p, sizeof(T))) return T{};
     if constexpr (LDCG) return __ldcg(p);
     else return *p;
 }
@@ -94,7 +95,7 @@ __device__ bool iface_item(const IfaceArgs<R>& a, int item_sub, int row_block, i
                            unsigned char* smem_raw, unsigned long long* kbar = nullptr, int* kofs = nullptr,
                            WaitF wait = WaitF(), bool kinit = true, unsigned kparity = 0) {
     using T = Cx<R>;
-    const SubDev sd = a.subtab[a.subs[item_sub]];
+    const SubDev sd = HLD(a.subtab + HLD(a.subs + item_sub));
     const int Lb = sd.Lb;
     const int nrb = (a.nrhs + NR - 1) / NR;        // RHS blocks: this item takes rb_first, + rb_step, ...
     // the per-side tables as scalars (a dynamically indexed array would live in local memory)
@@ -158,7 +159,7 @@ __device__ bool iface_item(const IfaceArgs<R>& a, int item_sub, int row_block, i
                          : "memory");
         }
         __syncwarp();
-        if (nbytes > 0)
+        if (nbytes > 0 && HELM_CHK(a.K + a0, nbytes))     // checking build: a failed check times out the wait
             asm volatile(
                 "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
                     smem_u32(Ks + (size_t)lane * Lbp)),
@@ -180,7 +181,7 @@ __device__ bool iface_item(const IfaceArgs<R>& a, int item_sub, int row_block, i
         tofs[q] = 0;
         cca[q] = ccb[q] = czero<T>();
         if (s >= 0) {
-            const TraceCoef<T> c = a.tc[sel4(tin, s) + pt];
+            const TraceCoef<T> c = HLD(a.tc + sel4(tin, s) + pt);
             cca[q] = c.ca;
             ccb[q] = c.cb;
             tofs[q] = (long long)(s == 0 ? sd.tout[0] : s == 1 ? sd.tout[1] : s == 2 ? sd.tout[2] : sd.tout[3]) + pt;
@@ -234,7 +235,7 @@ __device__ bool iface_item(const IfaceArgs<R>& a, int item_sub, int row_block, i
                     const long long o = (long long)(rhs0 + k) * a.ntrace + ti;
                     if (a.gin0) G[u] = ldg_<T, LDCG>(a.gin0 + o);
                     if (a.gin1) G[u] = cadd(G[u], ldg_<T, LDCG>(a.gin1 + o));
-                    C[u] = a.tc[ti].cin;
+                    C[u] = HLD(a.tc + ti).cin;
                 }
             }
         }
@@ -256,7 +257,7 @@ __device__ bool iface_item(const IfaceArgs<R>& a, int item_sub, int row_block, i
         for (int q = 1; q < 4; ++q)
             if (bo[q] >= 0 && e >= bo[q]) s = q;
         const long long ti = sel4(tin, s) + (e - sel4(bo, s));
-        const T cin = a.tc[ti].cin;
+        const T cin = HLD(a.tc + ti).cin;
         T G[NR];
 #pragma unroll
         for (int k = 0; k < NR; ++k) {
@@ -314,7 +315,7 @@ __device__ bool iface_item(const IfaceArgs<R>& a, int item_sub, int row_block, i
 #pragma unroll
             for (int u = 0; u < CU; ++u) {
                 const int c = c0 + 32 * u;
-                kv[q][u] = (srow[q] >= 0 && c < Lb) ? Kr[q][c] : czero<T>();
+                kv[q][u] = (srow[q] >= 0 && c < Lb) ? (STAGED ? Kr[q][c] : HLD(Kr[q] + c)) : czero<T>();
             }
 #pragma unroll
         for (int u = 0; u < CU; ++u) {
@@ -339,8 +340,8 @@ __device__ bool iface_item(const IfaceArgs<R>& a, int item_sub, int row_block, i
             if (lane == 0 && srow[q] >= 0) {
                 const T out = cadd(cfma(ccb[q], acc[q][0], cmul(cca[q], graw[krow[q]])), bsub[q]);
                 const long long o = (long long)rhs0 * a.ntrace + tofs[q];
-                a.dst[o] = out;
-                if (a.dst2) a.dst2[o] = out;
+                HST(a.dst + o, out);
+                if (a.dst2) HST(a.dst2 + o, out);
             }
         } else {
             // butterfly: every lane ends with the row's sums; lane k forms RHS k's output
@@ -356,8 +357,8 @@ __device__ bool iface_item(const IfaceArgs<R>& a, int item_sub, int row_block, i
             if (lane < nr && srow[q] >= 0) {
                 const T out = cadd(cfma(ccb[q], mine, cmul(cca[q], graw[lane * Lb + krow[q]])), bsub[q]);
                 const long long o = (long long)(rhs0 + lane) * a.ntrace + tofs[q];
-                a.dst[o] = out;
-                if (a.dst2) a.dst2[o] = out;
+                HST(a.dst + o, out);
+                if (a.dst2) HST(a.dst2 + o, out);
             }
         }
     }

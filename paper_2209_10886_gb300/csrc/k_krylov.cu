@@ -35,11 +35,11 @@ __device__ double block_sum(double v, double* sh) {
 __device__ __forceinline__ double2 apply_A(const double2* __restrict__ u, const double2 ad, long long p, int a, int b,
                                            int nx, int ny) {
     double sx = 0.0, sy = 0.0;
-    if (a > 0) { double2 q = u[p - 1]; sx += q.x; sy += q.y; }
-    if (a < nx - 1) { double2 q = u[p + 1]; sx += q.x; sy += q.y; }
-    if (b > 0) { double2 q = u[p - nx]; sx += q.x; sy += q.y; }
-    if (b < ny - 1) { double2 q = u[p + nx]; sx += q.x; sy += q.y; }
-    const double2 c = u[p];
+    if (a > 0) { double2 q = HLD(u + p - 1); sx += q.x; sy += q.y; }
+    if (a < nx - 1) { double2 q = HLD(u + p + 1); sx += q.x; sy += q.y; }
+    if (b > 0) { double2 q = HLD(u + p - nx); sx += q.x; sy += q.y; }
+    if (b < ny - 1) { double2 q = HLD(u + p + nx); sx += q.x; sy += q.y; }
+    const double2 c = HLD(u + p);
     return make_double2(fma(ad.x, c.x, fma(-ad.y, c.y, -sx)), fma(ad.x, c.y, fma(ad.y, c.x, -sy)));
 }
 
@@ -53,7 +53,7 @@ __global__ void matvec_kernel(const double2* __restrict__ adiag, int nx, int ny,
     const double2* uk = u + k * N;
     for (int b = blockIdx.y; b < ny; b += gridDim.y) {
         const long long p = (long long)b * nx + a;
-        Au[k * N + p] = apply_A(uk, adiag[p], p, a, b, nx, ny);
+        HST(Au + k * N + p, apply_A(uk, HLD(adiag + p), p, a, b, nx, ny));
     }
 }
 
@@ -75,15 +75,15 @@ __global__ void residual_kernel(const double2* __restrict__ adiag, int nx, int n
     if (a < nx) {
         for (int b = blockIdx.y; b < ny; b += gridDim.y) {
             const long long p = (long long)b * nx + a;
-            const double2 Av = apply_A(uk, adiag[p], p, a, b, nx, ny);
-            const double2 fv = f[k * N + p];
+            const double2 Av = apply_A(uk, HLD(adiag + p), p, a, b, nx, ny);
+            const double2 fv = HLD(f + k * N + p);
             const double2 rv = make_double2(fma(fscale, fv.x, -Av.x), fma(fscale, fv.y, -Av.y));
-            r[k * N + p] = rv;
+            HST(r + k * N + p, rv);
             acc = fma(rv.x, rv.x, fma(rv.y, rv.y, acc));
         }
     }
     acc = block_sum(acc, sh);
-    if (threadIdx.x == 0) partial[(long long)k * nb + bid] = acc;
+    if (threadIdx.x == 0) HST(partial + (long long)k * nb + bid, acc);
 }
 
 template <typename VT>
@@ -94,11 +94,11 @@ __global__ void norm2_partial_kernel(const VT* __restrict__ v, long long n, long
     const int k = blockIdx.y;
     Re acc = 0;
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
-        const VT x = v[k * stride + p];
+        const VT x = HLD(v + k * stride + p);
         acc = fma(x.x, x.x, fma(x.y, x.y, acc));
     }
     const double t = block_sum((double)acc, sh);
-    if (threadIdx.x == 0) partial[(long long)k * gridDim.x + blockIdx.x] = t;
+    if (threadIdx.x == 0) HST(partial + (long long)k * gridDim.x + blockIdx.x, t);
 }
 
 // out[row] = sum_b partial[row][b]   (mode 1: sqrt of the sum)
@@ -106,9 +106,9 @@ __global__ void reduce_rows_kernel(const double* __restrict__ partial, int nblk,
     __shared__ double sh[32];
     const int row = blockIdx.x;
     double acc = 0.0;
-    for (int b = threadIdx.x; b < nblk; b += blockDim.x) acc += partial[(long long)row * nblk + b];
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) acc += HLD(partial + (long long)row * nblk + b);
     acc = block_sum(acc, sh);
-    if (threadIdx.x == 0) out[row] = mode == 1 ? sqrt(acc) : acc;
+    if (threadIdx.x == 0) HST(out + row, mode == 1 ? sqrt(acc) : acc);
 }
 
 // partial[k][blk][j] = sum_{p in block range} conj(V_j[p]) w[p],  j < nvec (summed in the
@@ -134,17 +134,17 @@ __global__ void mdot_kernel(const VT* __restrict__ V, long long vsk, long long v
 #pragma unroll
         for (int q = 0; q < KB; ++q) acc[q] = czero<VT>();
         for (long long p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
-            const VT wv = wk[p];
+            const VT wv = HLD(wk + p);
 #pragma unroll
             for (int q = 0; q < KB; ++q)
-                if (j0 + q < nvec) acc[q] = cfmaconj(V[(long long)(j0 + q) * vsk + k * vsr + p], wv, acc[q]);
+                if (j0 + q < nvec) acc[q] = cfmaconj(HLD(V + (long long)(j0 + q) * vsk + k * vsr + p), wv, acc[q]);
         }
 #pragma unroll
         for (int q = 0; q < KB; ++q) {
             if (j0 + q >= nvec) break;
             const double re = block_sum((double)acc[q].x, sh);
             const double im = block_sum((double)acc[q].y, sh);
-            if (threadIdx.x == 0) out[j0 + q] = make_double2(re, im);
+            if (threadIdx.x == 0) HST(out + j0 + q, make_double2(re, im));
         }
     }
 }
@@ -155,13 +155,13 @@ __global__ void reduce_cpartials_kernel(const double2* __restrict__ partial, int
     const int k = blockIdx.y, j = blockIdx.x;
     double re = 0.0, im = 0.0;
     for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
-        const double2 v = partial[((long long)k * nblk + b) * nvec + j];
+        const double2 v = HLD(partial + ((long long)k * nblk + b) * nvec + j);
         re += v.x;
         im += v.y;
     }
     re = block_sum(re, sh);
     im = block_sum(im, sh);
-    if (threadIdx.x == 0) out[k * os + j] = make_double2(re, im);
+    if (threadIdx.x == 0) HST(out + k * os + j, make_double2(re, im));
 }
 
 // w += sign * sum_j coef[k][j] V_j, optional per-block ||w||^2 partials (the update in
@@ -186,9 +186,9 @@ __global__ void mupdate_kernel(const VT* __restrict__ V, long long vsk, long lon
     if (on) {
         VT* wk = w + k * ws;
         for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
-            VT x = wk[p];
-            for (int j = 0; j < nv; ++j) x = cfma(c[j], V[(long long)j * vsk + k * vsr + p], x);
-            wk[p] = x;
+            VT x = HLD(wk + p);
+            for (int j = 0; j < nv; ++j) x = cfma(c[j], HLD(V + (long long)j * vsk + k * vsr + p), x);
+            HST(wk + p, x);
             acc = fma(x.x, x.x, fma(x.y, x.y, acc));
         }
     }
@@ -208,8 +208,8 @@ __global__ void scale_vec_kernel(VT* __restrict__ dst, long long ds, const VT* _
     const bool on = !(active && !active[k]);
     const Re s = on ? (Re)inv[k] : (Re)0;
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
-        const VT x = on ? src[k * ss + p] : czero<VT>();
-        dst[k * ds + p] = mk(x.x * s, x.y * s);
+        const VT x = on ? HLD(src + k * ss + p) : czero<VT>();
+        HST(dst + k * ds + p, mk(x.x * s, x.y * s));
     }
 }
 
@@ -252,7 +252,7 @@ __global__ void hessenberg_step_kernel(double2* __restrict__ H, int ldh, long lo
     }
     __syncwarp();
     double2* colg = H + k * hs + (long long)j * ldh;       // column-major: H(i, jj) at H[jj*ldh + i]
-    for (int i = lane; i <= j + 1; i += 32) colg[i] = col[i];
+    for (int i = lane; i <= j + 1; i += 32) HST(colg + i, col[i]);
 }
 
 // y = R^{-1} g (upper triangular R = rotated H, first jcount[k] columns)
@@ -273,17 +273,17 @@ __global__ void hessenberg_solve_kernel(const double2* __restrict__ H, int ldh, 
     double2* rhs = hsm2;
     double2* R = hsm2 + m;
     const bool cached = cache_ok && m <= HS_SMEM;
-    for (int i = lane; i < m; i += 32) rhs[i] = g[(long long)k * ldg + i];
+    for (int i = lane; i < m; i += 32) rhs[i] = HLD(g + (long long)k * ldg + i);
     if (cached)
         for (int c = 0; c < m; ++c)
-            for (int r = lane; r <= c; r += 32) R[c * m + r] = Hk[(long long)c * ldh + r];
+            for (int r = lane; r <= c; r += 32) R[c * m + r] = HLD(Hk + (long long)c * ldh + r);
     __syncwarp();
     for (int i = m - 1; i >= 0; --i) {
-        const double2 d = cached ? R[i * m + i] : Hk[(long long)i * ldh + i];
+        const double2 d = cached ? R[i * m + i] : HLD(Hk + (long long)i * ldh + i);
         const double2 yi = cdiv(rhs[i], d);
-        if (lane == 0) yk[i] = yi;
+        if (lane == 0) HST(yk + i, yi);
         for (int r = lane; r < i; r += 32) {
-            const double2 h = cached ? R[i * m + r] : Hk[(long long)i * ldh + r];
+            const double2 h = cached ? R[i * m + r] : HLD(Hk + (long long)i * ldh + r);
             double2 v = rhs[r];
             v.x -= h.x * yi.x - h.y * yi.y;
             v.y -= h.x * yi.y + h.y * yi.x;
@@ -413,9 +413,9 @@ __global__ void to_c64_scaled_kernel(const double2* __restrict__ src, const doub
     const long long total = n * nrhs;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x) {
-        const double sc = scale[i / n];
-        const double2 v = src[i];
-        out[i] = make_float2((float)(v.x * sc), (float)(v.y * sc));
+        const double sc = HLD(scale + i / n);
+        const double2 v = HLD(src + i);
+        HST(out + i, make_float2((float)(v.x * sc), (float)(v.y * sc)));
     }
 }
 
@@ -447,11 +447,11 @@ __global__ void trace_to_kernel(const T* a, const T* __restrict__ b, int sign, V
     if (dj) out += (long long)(*dj + joff) * vsk;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x) {
-        VT v = cvt<VT>(a[i]);
-        if (b) v = cadd(v, cvt<VT>(b[i]));
+        VT v = cvt<VT>(HLD(a + i));
+        if (b) v = cadd(v, cvt<VT>(HLD(b + i)));
         if (sign < 0) v = mk(-v.x, -v.y);
-        out[i] = v;
-        if (out2) out2[i] = v;
+        HST(out + i, v);
+        if (out2) HST(out2 + i, v);
     }
 }
 // out (and out2, optional) = in rounded to T; with dj, in is the slot *dj + joff
@@ -461,9 +461,9 @@ __global__ void trace_from_kernel(const VT* __restrict__ in, T* __restrict__ out
     if (dj) in += (long long)(*dj + joff) * vsk;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x) {
-        const T f = cvt<T>(in[i]);
-        out[i] = f;
-        if (out2) out2[i] = f;
+        const T f = cvt<T>(HLD(in + i));
+        HST(out + i, f);
+        if (out2) HST(out2 + i, f);
     }
 }
 // r = b - w
@@ -471,7 +471,7 @@ template <typename VT>
 __global__ void sub_kernel(const VT* __restrict__ b, const VT* __restrict__ w, VT* __restrict__ r, long long total) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x)
-        r[i] = csub(b[i], w[i]);
+        HST(r + i, csub(HLD(b + i), HLD(w + i)));
 }
 
 static int small_grid(long long total) { return (int)std::min<long long>(1216, (total + 255) / 256 + 1); }

@@ -83,7 +83,7 @@ __device__ double2 sum_partials(const double2* partial, double2* sh) {
     double2 t = make_double2(0.0, 0.0);
     if (threadIdx.x < 32) {
         for (int c = threadIdx.x; c < (int)gridDim.x; c += 32) {
-            const double2 v = __ldcg(partial + c);
+            const double2 v = HLDCG(partial + c);
             t.x += v.x;
             t.y += v.y;
         }
@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(MT) mgs_kernel(MgsArgs a) {
 #pragma unroll
         for (int e = 0; e < EPT; ++e) {
             const long long p = base + e * stride;
-            wr[e] = p < a.n ? w[p] : make_double2(0.0, 0.0);
+            wr[e] = p < a.n ? HLD(w + p) : make_double2(0.0, 0.0);
         }
         // step k: finish the update with v_{k-1} (h_{k-1} known) and, in the same
         // pass over the elements, the dot product with v_k against the updated w
@@ -152,15 +152,15 @@ __global__ void __launch_bounds__(MT) mgs_kernel(MgsArgs a) {
             for (int e = 0; e < EPT; ++e) {
                 const long long p = base + e * stride;
                 if (p < a.n) {
-                    if (vprev) wr[e] = cfma(mh, vprev[p], wr[e]);
-                    acc[e & 3] = cfmaconj(v[p], wr[e], acc[e & 3]);
+                    if (vprev) wr[e] = cfma(mh, HLD(vprev + p), wr[e]);
+                    acc[e & 3] = cfmaconj(HLD(v + p), wr[e], acc[e & 3]);
                 }
             }
             const double2 accs = make_double2((acc[0].x + acc[1].x) + (acc[2].x + acc[3].x),
                                               (acc[0].y + acc[1].y) + (acc[2].y + acc[3].y));
             double2 h;
             if (!reduce(accs, h)) return;
-            if (blockIdx.x == 0 && threadIdx.x == 0) a.hcol[(long long)r * a.ldh + k] = h;
+            if (blockIdx.x == 0 && threadIdx.x == 0) HST(a.hcol + (long long)r * a.ldh + k, h);
             mh = make_double2(-h.x, -h.y);
             vprev = v;
         }
@@ -168,18 +168,18 @@ __global__ void __launch_bounds__(MT) mgs_kernel(MgsArgs a) {
 #pragma unroll
         for (int e = 0; e < EPT; ++e) {
             const long long p = base + e * stride;
-            if (vprev && p < a.n) wr[e] = cfma(mh, vprev[p], wr[e]);
+            if (vprev && p < a.n) wr[e] = cfma(mh, HLD(vprev + p), wr[e]);
             nrm = fma(wr[e].x, wr[e].x, fma(wr[e].y, wr[e].y, nrm));
         }
         double2 tot;
         if (!reduce(make_double2(nrm, 0.0), tot)) return;
         const double hn = sqrt(tot.x);
-        if (blockIdx.x == 0 && threadIdx.x == 0) a.hnorm[r] = hn;
+        if (blockIdx.x == 0 && threadIdx.x == 0) HST(a.hnorm + r, hn);
         const double inv = hn > 0.0 ? 1.0 / hn : 0.0;
 #pragma unroll
         for (int e = 0; e < EPT; ++e) {
             const long long p = base + e * stride;
-            if (p < a.n) w[p] = make_double2(wr[e].x * inv, wr[e].y * inv);
+            if (p < a.n) HST(w + p, make_double2(wr[e].x * inv, wr[e].y * inv));
         }
     }
 }
@@ -214,6 +214,7 @@ __device__ __forceinline__ bool mb_wait(unsigned long long* b, unsigned parity) 
 __device__ __forceinline__ void bulk_fetch(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
                  : "memory");
+    if (!HELM_CHK(src, bytes)) return;                  // checking build: the wait then gives up
     asm volatile(
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
             smem_u32(dst)),
@@ -266,7 +267,7 @@ __global__ void __launch_bounds__(NT) mgs_smem_kernel(MgsArgs a, int L) {
 #pragma unroll
         for (int e = 0; e < EPT; ++e) {
             const int i = e * NT + threadIdx.x;
-            wr[e] = i < len ? w[c0 + i] : make_double2(0.0, 0.0);
+            wr[e] = i < len ? HLD(w + c0 + i) : make_double2(0.0, 0.0);
         }
         const double2* V = a.V + r * a.vsr;
         __syncthreads();                                       // the buffers are free
@@ -297,7 +298,7 @@ __global__ void __launch_bounds__(NT) mgs_smem_kernel(MgsArgs a, int L) {
                 if (k + 1 < a.nvec) wait_buf(b ^ 1);          // no copy outlives the CTA
                 return;
             }
-            if (blockIdx.x == 0 && threadIdx.x == 0) a.hcol[(long long)r * a.ldh + k] = h;
+            if (blockIdx.x == 0 && threadIdx.x == 0) HST(a.hcol + (long long)r * a.ldh + k, h);
             mh = make_double2(-h.x, -h.y);
         }
         const double2* vl = vbuf + (size_t)((a.nvec - 1) & 1) * L;
@@ -314,12 +315,12 @@ __global__ void __launch_bounds__(NT) mgs_smem_kernel(MgsArgs a, int L) {
         double2 tot;
         if (!reduce(make_double2(nrm0 + nrm1, 0.0), tot)) return;
         const double hn = sqrt(tot.x);
-        if (blockIdx.x == 0 && threadIdx.x == 0) a.hnorm[r] = hn;
+        if (blockIdx.x == 0 && threadIdx.x == 0) HST(a.hnorm + r, hn);
         const double inv = hn > 0.0 ? 1.0 / hn : 0.0;
 #pragma unroll
         for (int e = 0; e < EPT; ++e) {
             const int i = e * NT + threadIdx.x;
-            if (i < len) w[c0 + i] = make_double2(wr[e].x * inv, wr[e].y * inv);
+            if (i < len) HST(w + c0 + i, make_double2(wr[e].x * inv, wr[e].y * inv));
         }
     }
 }
@@ -451,7 +452,7 @@ __global__ void __launch_bounds__(CT, 1) cgs2_step_kernel(Cgs2Args<VT> a) {
 #pragma unroll
                     for (int u = 0; u < 8; ++u) {
                         const int c = c0 + groups * u;
-                        pv[u] = c < G ? __ldcg(part + (long long)c * PS + kb + kq) : make_double2(0.0, 0.0);
+                        pv[u] = c < G ? HLDCG(part + (long long)c * PS + kb + kq) : make_double2(0.0, 0.0);
                     }
 #pragma unroll
                     for (int u = 0; u < 8; ++u) { t.x += pv[u].x; t.y += pv[u].y; }
@@ -489,8 +490,8 @@ __global__ void __launch_bounds__(CT, 1) cgs2_step_kernel(Cgs2Args<VT> a) {
                 for (int u = 0; u < 8; ++u) {
                     const int i = i0 + lane + 32 * u;
                     const bool in = i < len;
-                    xa[u] = in ? __ldcg(va + i) : czero<VT>();
-                    xb[u] = (in && hb) ? __ldcg(vb + i) : czero<VT>();
+                    xa[u] = in ? HLDCG(va + i) : czero<VT>();
+                    xb[u] = (in && hb) ? HLDCG(vb + i) : czero<VT>();
                 }
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
@@ -525,7 +526,7 @@ __global__ void __launch_bounds__(CT, 1) cgs2_step_kernel(Cgs2Args<VT> a) {
             for (int k0 = 0; k0 < nvec; k0 += 16) {
                 VT vv[16];
 #pragma unroll
-                for (int u = 0; u < 16; ++u) vv[u] = k0 + u < nvec ? __ldcg(v + (k0 + u) * a.vsk) : czero<VT>();
+                for (int u = 0; u < 16; ++u) vv[u] = k0 + u < nvec ? HLDCG(v + (k0 + u) * a.vsk) : czero<VT>();
 #pragma unroll
                 for (int u = 0; u < 16; ++u)
                     if (k0 + u < nvec) x = cfma(hc[k0 + u], vv[u], x);
@@ -545,10 +546,10 @@ __global__ void __launch_bounds__(CT, 1) cgs2_step_kernel(Cgs2Args<VT> a) {
         for (int i = threadIdx.x; i < len; i += CT) {
             VT x;
             if (wsrc) {
-                x = wsrc[c0 + i];
+                x = HLD(wsrc + c0 + i);
                 x = mk(-x.x, -x.y);
             } else {
-                x = w[c0 + i];
+                x = HLD(w + c0 + i);
             }
             ws[i] = x;
             n0 = fma(x.x, x.x, fma(x.y, x.y, n0));
@@ -585,9 +586,9 @@ __global__ void __launch_bounds__(CT, 1) cgs2_step_kernel(Cgs2Args<VT> a) {
         const Re invr = (Re)inv;
         for (int i = threadIdx.x; i < len; i += CT) {
             const VT v = mk(ws[i].x * invr, ws[i].y * invr);
-            w[c0 + i] = v;
-            if (a.vout1) a.vout1[r * a.vsr + c0 + i] = v;
-            if (a.vout2) a.vout2[r * a.vsr + c0 + i] = v;
+            HST(w + c0 + i, v);
+            if (a.vout1) HST(a.vout1 + r * a.vsr + c0 + i, v);
+            if (a.vout2) HST(a.vout2 + r * a.vsr + c0 + i, v);
         }
         if (blockIdx.x == 0) {
             // h column, then the Givens update of the least-squares problem in the
@@ -601,38 +602,39 @@ __global__ void __launch_bounds__(CT, 1) cgs2_step_kernel(Cgs2Args<VT> a) {
             double2* snr = a.sn + (long long)r * a.ldg;
             double2* gr = a.g + (long long)r * a.ldg;
             for (int k = threadIdx.x; k <= J + 1; k += CT) {
-                if (k <= J) a.hsum[(long long)r * a.ldh + k] = h1[k];
+                if (k <= J) HST(a.hsum + (long long)r * a.ldh + k, h1[k]);
                 const double2 hk = k <= J ? h1[k] : make_double2(hn, 0.0);
                 col[k] = mk((Re)hk.x, (Re)hk.y);
                 if (k < J) {
-                    csv[k] = mk((Re)csr[k].x, (Re)0);
-                    snv[k] = mk((Re)snr[k].x, (Re)snr[k].y);
+                    const double2 ck = HLD(csr + k), sk = HLD(snr + k);
+                    csv[k] = mk((Re)ck.x, (Re)0);
+                    snv[k] = mk((Re)sk.x, (Re)sk.y);
                 }
             }
             __shared__ C2 gpair[2];
-            if (threadIdx.x == 0) gpair[0] = mk((Re)gr[J].x, (Re)gr[J].y);
+            if (threadIdx.x == 0) gpair[0] = mk((Re)HLD(gr + J).x, (Re)HLD(gr + J).y);
             __syncthreads();
             if (threadIdx.x == 0) {
-                a.hnorm[r] = hn;
-                a.need[r] = second ? 1 : 0;
+                HST(a.hnorm + r, hn);
+                HST(a.need + r, second ? 1 : 0);
                 C2 gj = gpair[0], gj1;
                 givens_column<C2>(col, csv, snv, J, gj, gj1);
                 gpair[0] = gj;
                 gpair[1] = gj1;
-                a.invh[r] = inv;
+                HST(a.invh + r, inv);
             }
             __syncthreads();
             double2* colg = a.H + r * a.hs + (long long)J * a.ldH;
-            for (int k = threadIdx.x; k <= J + 1; k += CT) colg[k] = make_double2((double)col[k].x, (double)col[k].y);
+            for (int k = threadIdx.x; k <= J + 1; k += CT) HST(colg + k, make_double2((double)col[k].x, (double)col[k].y));
             if (threadIdx.x == 32) {
-                csr[J] = make_double2((double)csv[J].x, 0.0);
-                snr[J] = make_double2((double)snv[J].x, (double)snv[J].y);
+                HST(csr + J, make_double2((double)csv[J].x, 0.0));
+                HST(snr + J, make_double2((double)snv[J].x, (double)snv[J].y));
             }
             if (threadIdx.x == 64) {
                 const C2 g0 = gpair[0], g1 = gpair[1];
-                gr[J] = make_double2((double)g0.x, (double)g0.y);
-                gr[J + 1] = make_double2((double)g1.x, (double)g1.y);
-                a.est[r] = sqrt((double)g1.x * (double)g1.x + (double)g1.y * (double)g1.y);
+                HST(gr + J, make_double2((double)g0.x, (double)g0.y));
+                HST(gr + J + 1, make_double2((double)g1.x, (double)g1.y));
+                HST(a.est + r, sqrt((double)g1.x * (double)g1.x + (double)g1.y * (double)g1.y));
             }
         }
         __syncthreads();                              // ws, hv, hc and h1 are reused by the next RHS
@@ -691,7 +693,7 @@ __global__ void __launch_bounds__(CT, 1) cgs2_group_kernel(Cgs2Args<VT> a, int G
 #pragma unroll
                     for (int u = 0; u < 8; ++u) {
                         const int c = cb + groups * u;
-                        pv[u] = c < Gd ? __ldcg(part + (long long)c * CS + kb + kq) : make_double2(0.0, 0.0);
+                        pv[u] = c < Gd ? HLDCG(part + (long long)c * CS + kb + kq) : make_double2(0.0, 0.0);
                     }
 #pragma unroll
                     for (int u = 0; u < 8; ++u) { t.x += pv[u].x; t.y += pv[u].y; }
@@ -757,7 +759,7 @@ __global__ void __launch_bounds__(CT, 1) cgs2_group_kernel(Cgs2Args<VT> a, int G
 #pragma unroll
                         for (int u = 0; u < 8; ++u) {
                             const int i = i0 + lane + 32 * u;
-                            x[q][u] = (onp[q] && i < len) ? (selfp[q] ? wp[q][i] : __ldcg(vp[q] + i)) : czero<VT>();
+                            x[q][u] = (onp[q] && i < len) ? (selfp[q] ? wp[q][i] : HLDCG(vp[q] + i)) : czero<VT>();
                         }
 #pragma unroll
                     for (int q = 0; q < PP; ++q)
@@ -803,7 +805,7 @@ __global__ void __launch_bounds__(CT, 1) cgs2_group_kernel(Cgs2Args<VT> a, int G
 #pragma unroll
                         for (int u = 0; u < 16; ++u)
                             vv[q][u] = (onq[q] && k0 + u < nvec)
-                                           ? __ldcg(a.V + (long long)(k0 + u) * a.vsk + (long long)(g0 + gq[q]) * a.vsr + c0 + iq[q])
+                                           ? HLDCG(a.V + (long long)(k0 + u) * a.vsk + (long long)(g0 + gq[q]) * a.vsr + c0 + iq[q])
                                            : czero<VT>();
 #pragma unroll
                     for (int q = 0; q < 2; ++q)
@@ -908,12 +910,13 @@ __global__ void __launch_bounds__(CT, 1) cgs2_group_kernel(Cgs2Args<VT> a, int G
                 const double2 hk = k <= J ? h1g[k] : make_double2(hn, 0.0);
                 col[k] = mk((Re)hk.x, (Re)hk.y);
                 if (k < J) {
-                    csv[k] = mk((Re)csr[k].x, (Re)0);
-                    snv[k] = mk((Re)snr[k].x, (Re)snr[k].y);
+                    const double2 ck = HLD(csr + k), sk = HLD(snr + k);
+                    csv[k] = mk((Re)ck.x, (Re)0);
+                    snv[k] = mk((Re)sk.x, (Re)sk.y);
                 }
             }
             __shared__ C2 gpair[2];
-            if (threadIdx.x == 0) gpair[0] = mk((Re)gr[J].x, (Re)gr[J].y);
+            if (threadIdx.x == 0) gpair[0] = mk((Re)HLD(gr + J).x, (Re)HLD(gr + J).y);
             __syncthreads();
             if (threadIdx.x == 0) {
                 a.hnorm[r] = hn;
@@ -926,10 +929,10 @@ __global__ void __launch_bounds__(CT, 1) cgs2_group_kernel(Cgs2Args<VT> a, int G
             }
             __syncthreads();
             double2* colg = a.H + r * a.hs + (long long)J * a.ldH;
-            for (int k = threadIdx.x; k <= J + 1; k += CT) colg[k] = make_double2((double)col[k].x, (double)col[k].y);
+            for (int k = threadIdx.x; k <= J + 1; k += CT) HST(colg + k, make_double2((double)col[k].x, (double)col[k].y));
             if (threadIdx.x == 32) {
-                csr[J] = make_double2((double)csv[J].x, 0.0);
-                snr[J] = make_double2((double)snv[J].x, (double)snv[J].y);
+                HST(csr + J, make_double2((double)csv[J].x, 0.0));
+                HST(snr + J, make_double2((double)snv[J].x, (double)snv[J].y));
             }
             if (threadIdx.x == 64) {
                 const C2 q0 = gpair[0], q1 = gpair[1];

@@ -76,6 +76,7 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* b, unsigned parity
     return true;
 }
 __device__ __forceinline__ void bulk_copy(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+    if (!HELM_CHK(src, bytes)) return;                  // checking build: the wait then gives up
     asm volatile(
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
             smem_addr(dst)),
@@ -116,8 +117,8 @@ __global__ void __launch_bounds__(NR <= 4 ? 544 : 288) stage_kernel(StageArgs<R>
     __shared__ int abort_flag;
 
     const int rank = csize == 2 ? (int)(blockIdx.x & 1) : 0;
-    const int s = BASIS ? blockIdx.x / csize : a.subs[blockIdx.x / csize];
-    const SubDev sd = a.subtab[s];
+    const int s = BASIS ? blockIdx.x / csize : HLD(a.subs + blockIdx.x / csize);
+    const SubDev sd = HLD(a.subtab + s);
     const int mx = sd.mx, my = sd.my;
     const int rhs0 = blockIdx.y * NR;                    // first RHS (workspace slot) of this CTA
     const int e0 = BASIS ? a.col0 + rhs0 : 0;            // first boundary point (basis mode)
@@ -167,8 +168,8 @@ __global__ void __launch_bounds__(NR <= 4 ? 544 : 288) stage_kernel(StageArgs<R>
     const T* Xs = a.X + sd.xoff;
 
     auto gin = [&](int k, long long idx) -> T {
-        T g = a.gin0 ? a.gin0[(long long)(rhs0 + k) * a.ntrace + idx] : czero<T>();
-        if (a.gin1) g = cadd(g, a.gin1[(long long)(rhs0 + k) * a.ntrace + idx]);
+        T g = a.gin0 ? HLD(a.gin0 + (long long)(rhs0 + k) * a.ntrace + idx) : czero<T>();
+        if (a.gin1) g = cadd(g, HLD(a.gin1 + (long long)(rhs0 + k) * a.ntrace + idx));
         return g;
     };
     auto bterm = [&](int r, int c, int k) -> T {
@@ -181,13 +182,13 @@ __global__ void __launch_bounds__(NR <= 4 ? 544 : 288) stage_kernel(StageArgs<R>
         return b;
     };
     auto src_row = [&](int r, int c, int k) -> double2 {
-        return a.r[(long long)(rhs0 + k) * N + (long long)(sd.y0 + r) * a.nx + sd.x0 + c];
+        return HLD(a.r + (long long)(rhs0 + k) * N + (long long)(sd.y0 + r) * a.nx + sd.x0 + c);
     };
     double rsc[NR], zsc[NR];
 #pragma unroll
     for (int k = 0; k < NR; ++k) {
-        rsc[k] = (a.rscale && k < nr) ? a.rscale[rhs0 + k] : 1.0;
-        zsc[k] = (a.zscale && k < nr) ? a.zscale[rhs0 + k] : 1.0;
+        rsc[k] = (a.rscale && k < nr) ? HLD(a.rscale + rhs0 + k) : 1.0;
+        zsc[k] = (a.zscale && k < nr) ? HLD(a.zscale + rhs0 + k) : 1.0;
     }
     auto scaled = [&](double2 rv, int k) -> T { return from_c128<T>(make_double2(rv.x * rsc[k], rv.y * rsc[k])); };
     auto finish_row = [&](int r, int c, int k, T u) {
@@ -198,8 +199,8 @@ __global__ void __launch_bounds__(NR <= 4 ? 544 : 288) stage_kernel(StageArgs<R>
         if (r == my - 1) uk[boff(SN) + c] = u;
         if (!BASIS && a.z) {
             const double2 zu = to_c128(u);
-            a.z[(long long)(rhs0 + k) * N + (long long)(sd.y0 + r) * a.nx + sd.x0 + c] =
-                make_double2(zu.x * zsc[k], zu.y * zsc[k]);
+            HST(a.z + (long long)(rhs0 + k) * N + (long long)(sd.y0 + r) * a.nx + sd.x0 + c,
+                make_double2(zu.x * zsc[k], zu.y * zsc[k]));
         }
     };
     // is boundary point e (of side `side`, index pt along it) in this CTA's columns?
@@ -227,7 +228,7 @@ __global__ void __launch_bounds__(NR <= 4 ? 544 : 288) stage_kernel(StageArgs<R>
             if (k < nr && sd.bo[side] >= 0 && sd.bo[side] + pt == e0 + k) b = mk((R)1, (R)0);
         } else if (k < nr && sd.tin[side] >= 0 && (a.gin0 || a.gin1)) {
             const long long ti = sd.tin[side] + pt;
-            b = cmul(gin(k, ti), a.tc[ti].cin);
+            b = cmul(gin(k, ti), HLD(a.tc + ti).cin);
         }
         binc[idx] = b;
     }
@@ -376,7 +377,7 @@ __global__ void __launch_bounds__(NR <= 4 ? 544 : 288) stage_kernel(StageArgs<R>
                     T nv;
                     if (fwd) {
                         if (r < my - 1) {
-                            ywk[(long long)r * mx + col] = sum;                   // y_r
+                            HST(ywk + (long long)r * mx + col, sum);              // y_r
                             T b = bterm(r + 1, col, k);
                             if (!BASIS && a.src) b = cadd(b, scaled(rnext[k], k));
                             nv = cadd(b, sum);                                     // b_{r+1} + y_r
@@ -390,7 +391,7 @@ __global__ void __launch_bounds__(NR <= 4 ? 544 : 288) stage_kernel(StageArgs<R>
                         const T u = cadd(ynext[k], sum);                          // u_r = y_r + X_r u_{r+1}
                         finish_row(r, col, k, u);
                         nv = u;
-                        if (r >= 1) ynext[k] = ywk[(long long)(r - 1) * mx + col];
+                        if (r >= 1) ynext[k] = HLD(ywk + (long long)(r - 1) * mx + col);
                     }
                     vn[k * mxp + col] = nv;
                     if (csize == 2 && !last) st_peer(peer_addr(&vn[k * mxp + col], rank ^ 1), nv);
@@ -426,7 +427,7 @@ __global__ void __launch_bounds__(NR <= 4 ? 544 : 288) stage_kernel(StageArgs<R>
             if (sd.bo[side] < 0) continue;
             const int pt = e - boff(side);
             if (!owns_point(side, pt)) continue;
-            a.K[sd.koff + (long long)(e0 + k) * sd.Lb + sd.bo[side] + pt] = ub[idx];
+            HST(a.K + sd.koff + (long long)(e0 + k) * sd.Lb + sd.bo[side] + pt, ub[idx]);
         }
         return;
     }
@@ -440,13 +441,13 @@ __global__ void __launch_bounds__(NR <= 4 ? 544 : 288) stage_kernel(StageArgs<R>
             const int pt = e - boff(side);
             if (!owns_point(side, pt)) continue;
             const long long in = sd.tin[side] + pt, out = sd.tout[side] + pt;
-            const TraceCoef<T> c = a.tc[in];
+            const TraceCoef<T> c = HLD(a.tc + in);
             T g = cfma(c.cb, ub[idx], cmul(c.ca, gin(k, in)));
             const long long o = (long long)(rhs0 + k) * a.ntrace + out;
-            if (a.base) g = cadd(g, a.base[o]);
-            if (a.sub) g = csub(g, a.sub[o]);
-            a.dst[o] = g;
-            if (a.dst2) a.dst2[o] = g;
+            if (a.base) g = cadd(g, HLD(a.base + o));
+            if (a.sub) g = csub(g, HLD(a.sub + o));
+            HST(a.dst + o, g);
+            if (a.dst2) HST(a.dst2 + o, g);
         }
     }
 }

@@ -77,6 +77,7 @@ __device__ __forceinline__ bool bar_wait(unsigned long long* b, unsigned parity,
     return true;
 }
 __device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+    if (!HELM_CHK(src, bytes)) return;                  // checking build: the wait then gives up
     asm volatile(
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(sm_addr(dst)),
         "l"(src), "r"(bytes), "r"(sm_addr(bar))
@@ -185,12 +186,12 @@ __global__ void tc_layout_kernel(const SubDev* subtab, int nsub, int split, cons
         if (i < sd.mx && j < sd.mx) {
             const long long e = j < sd.w0 ? (long long)i * sd.ld0 + j
                                           : (long long)sd.mx * sd.ld0 + (long long)i * sd.ld1 + (j - sd.w0);
-            const float2 x = X[sd.xoff + (long long)r * sd.mx * (sd.ld0 + sd.ld1) + e];
+            const float2 x = HLD(X + sd.xoff + (long long)r * sd.mx * (sd.ld0 + sd.ld1) + e);
             const float xv = (p & 1) ? x.y : x.x;
             const float hi = tf32_round(xv);
             v = p < 2 ? hi : tf32_round(xv - hi);
         }
-        XT[sd.xtoff + f] = v;
+        HST(XT + sd.xtoff + f, v);
     }
 }
 
@@ -224,8 +225,8 @@ __global__ void __launch_bounds__(32 * (TC_EPI_WARPS + 2), 1)
     constexpr unsigned KSTRIDE_A = 2048u * MT;              // K-adjacent core matrices of A
     constexpr unsigned IDESC = tf32_idesc(2 * NR);
 
-    const int s = a.subs[blockIdx.x];
-    const SubDev sd = a.subtab[s];
+    const int s = HLD(a.subs + blockIdx.x);
+    const SubDev sd = HLD(a.subtab + s);
     const int mx = sd.mx, my = sd.my;
     const int rhs0 = blockIdx.y * NR;
     const int e0 = BASIS ? a.col0 + rhs0 : 0;
@@ -253,7 +254,7 @@ __global__ void __launch_bounds__(32 * (TC_EPI_WARPS + 2), 1)
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
-    for (int k = tid; k < NR; k += blockDim.x) zsc_s[k] = (!BASIS && a.zscale && k < nr) ? (float)a.zscale[rhs0 + k] : 1.f;
+    for (int k = tid; k < NR; k += blockDim.x) zsc_s[k] = (!BASIS && a.zscale && k < nr) ? (float)HLD(a.zscale + rhs0 + k) : 1.f;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(sm_addr(&tmem_base)),
                      "r"(TCOLS)
@@ -265,8 +266,8 @@ __global__ void __launch_bounds__(32 * (TC_EPI_WARPS + 2), 1)
     const int tinW = sd.tin[SW], tinE = sd.tin[SE], tinS = sd.tin[SS], tinN = sd.tin[SN];
     const int boW = sd.bo[SW], boE = sd.bo[SE], boS = sd.bo[SS], boN = sd.bo[SN];
     auto gin = [&](int k, long long idx) -> T {
-        T g = a.gin0 ? a.gin0[(long long)(rhs0 + k) * a.ntrace + idx] : czero<T>();
-        if (a.gin1) g = cadd(g, a.gin1[(long long)(rhs0 + k) * a.ntrace + idx]);
+        T g = a.gin0 ? HLD(a.gin0 + (long long)(rhs0 + k) * a.ntrace + idx) : czero<T>();
+        if (a.gin1) g = cadd(g, HLD(a.gin1 + (long long)(rhs0 + k) * a.ntrace + idx));
         return g;
     };
     // interface part of the right-hand side at boundary node (r, cc) for RHS k: the
@@ -276,7 +277,7 @@ __global__ void __launch_bounds__(32 * (TC_EPI_WARPS + 2), 1)
             if (bo >= 0 && bo + pt == e0 + k) b = cadd(b, mk(1.f, 0.f));
         } else if (tin >= 0 && has_gin) {
             const long long ti = tin + pt;
-            b = cadd(b, cmul(gin(k, ti), a.tc[ti].cin));
+            b = cadd(b, cmul(gin(k, ti), HLD(a.tc + ti).cin));
         }
         return b;
     };
@@ -301,7 +302,7 @@ __global__ void __launch_bounds__(32 * (TC_EPI_WARPS + 2), 1)
             const int r = e < my ? e : e < 2 * my ? e - my : e < 2 * my + mx ? 0 : my - 1;
             const int cc = e < my ? 0 : e < 2 * my ? mx - 1 : e < 2 * my + mx ? e - 2 * my : e - 2 * my - mx;
             if (node_slot(r, cc) != e) continue;            // a corner's S/N entry, or E when mx = 1
-            escr[(long long)k * a.estride + e] = bnode(r, cc, k);
+            HST(escr + (long long)k * a.estride + e, bnode(r, cc, k));
         }
     }
     tc_fence_before();
@@ -333,9 +334,9 @@ __global__ void __launch_bounds__(32 * (TC_EPI_WARPS + 2), 1)
         auto finish_edge = [&](int r, int k, T u) {
             auto one = [&](int tin, int bo, int e, int pt) {
                 if (BASIS) {
-                    if (bo >= 0) a.K[sd.koff + (long long)(e0 + k) * sd.Lb + bo + pt] = u;
+                    if (bo >= 0) HST(a.K + sd.koff + (long long)(e0 + k) * sd.Lb + bo + pt, u);
                 } else if (uscr && tin >= 0) {
-                    uscr[(long long)k * a.estride + e] = u;
+                    HST(uscr + (long long)k * a.estride + e, u);
                 }
             };
             if (c == 0) one(tinW, boW, r, r);
@@ -387,8 +388,8 @@ __global__ void __launch_bounds__(32 * (TC_EPI_WARPS + 2), 1)
                 T b = czero<T>();
                 if (live && k < nr) {
                     const int sl = node_slot(0, c);
-                    if (sl >= 0) b = has_gin ? escr[(long long)k * a.estride + sl] : bnode(0, c, k);
-                    if (!BASIS && a.src) b = cadd(b, a.r64[(long long)(rhs0 + k) * N + (long long)sd.y0 * a.nx + sd.x0 + c]);
+                    if (sl >= 0) b = has_gin ? HLD(escr + (long long)k * a.estride + sl) : bnode(0, c, k);
+                    if (!BASIS && a.src) b = cadd(b, HLD(a.r64 + (long long)(rhs0 + k) * N + (long long)sd.y0 * a.nx + sd.x0 + c));
                 }
                 v[j] = b;
             }
@@ -430,7 +431,7 @@ __global__ void __launch_bounds__(32 * (TC_EPI_WARPS + 2), 1)
                     if (k < nr) {
                         if (loady) pv[j] = yrow[(long long)k * ws];
                         else if (srow) pv[j] = srow[(long long)k * N];
-                        if (erow) ev[j] = erow[(long long)k * a.estride];
+                        if (erow) ev[j] = HLD(erow + (long long)k * a.estride);
                     }
                 }
             };
@@ -598,13 +599,13 @@ __global__ void __launch_bounds__(32 * (TC_EPI_WARPS + 2), 1)
             const int tout = side == SW ? toutW : side == SE ? toutE : side == SS ? toutS : toutN;
             if (!(a.mask & (1 << side)) || tin < 0) continue;
             const long long in = tin + pt, out = tout + pt;
-            const TraceCoef<T> cf = a.tc[in];
-            T g = cfma(cf.cb, uscr[(long long)k * a.estride + e], cmul(cf.ca, gin(k, in)));
+            const TraceCoef<T> cf = HLD(a.tc + in);
+            T g = cfma(cf.cb, HLD(uscr + (long long)k * a.estride + e), cmul(cf.ca, gin(k, in)));
             const long long o = (long long)(rhs0 + k) * a.ntrace + out;
-            if (a.base) g = cadd(g, a.base[o]);
-            if (a.sub) g = csub(g, a.sub[o]);
-            a.dst[o] = g;
-            if (a.dst2) a.dst2[o] = g;
+            if (a.base) g = cadd(g, HLD(a.base + o));
+            if (a.sub) g = csub(g, HLD(a.sub + o));
+            HST(a.dst + o, g);
+            if (a.dst2) HST(a.dst2 + o, g);
         }
     }
 }
@@ -680,7 +681,7 @@ __global__ void __launch_bounds__(128, 1) tc_iface_kernel(IfaceArgs<float> a, in
     const int nr = min(NB, a.nrhs - rhs0);
     const int row0 = blockIdx.y * 128;
     const int slot = blockIdx.z / S, split = blockIdx.z - slot * S;   // S CTAs share one output tile
-    const SubDev sd = a.subtab[a.subs[slot]];
+    const SubDev sd = HLD(a.subtab + HLD(a.subs + slot));
     const int Lb = sd.Lb;
     const int bo[4] = {sd.bo[0], sd.bo[1], sd.bo[2], sd.bo[3]};
     const int tin[4] = {sd.tin[0], sd.tin[1], sd.tin[2], sd.tin[3]};
@@ -738,7 +739,7 @@ __global__ void __launch_bounds__(128, 1) tc_iface_kernel(IfaceArgs<float> a, in
 #pragma unroll
         for (int i = 0; i < KC; ++i) {
             const long long ro = rowoff[krow_of(i)];
-            kv[i] = (ro >= 0 && col < Lb) ? a.K[ro + col] : make_float2(0.f, 0.f);
+            kv[i] = (ro >= 0 && col < Lb) ? HLD(a.K + ro + col) : make_float2(0.f, 0.f);
         }
     };
     // incoming data of the thread's (quad, RHS) pairs: quad = pair % 4, RHS = pair / 4
@@ -758,9 +759,9 @@ __global__ void __launch_bounds__(128, 1) tc_iface_kernel(IfaceArgs<float> a, in
                         if (bo[t] >= 0 && e >= bo[t]) sd_ = t;
                     const long long ti = sel(tin, sd_) + (e - sel(bo, sd_));
                     const long long o = (long long)(rhs0 + k) * a.ntrace + ti;
-                    if (a.gin0) G = a.gin0[o];
-                    if (a.gin1) G = cadd(G, a.gin1[o]);
-                    C = a.tc[ti].cin;
+                    if (a.gin0) G = HLD(a.gin0 + o);
+                    if (a.gin1) G = cadd(G, HLD(a.gin1 + o));
+                    C = HLD(a.tc + ti).cin;
                 }
                 gv[u][q] = G;
                 cv[u][q] = C;
@@ -910,13 +911,13 @@ __global__ void __launch_bounds__(128, 1) tc_iface_kernel(IfaceArgs<float> a, in
             const long long unit = ((long long)slot * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
             float* pp = a.part + unit * S * (128LL * NCOLS);
 #pragma unroll
-            for (int cc = 0; cc < NCOLS; ++cc) pp[((long long)split * NCOLS + cc) * 128 + tid] = acc[cc];
+            for (int cc = 0; cc < NCOLS; ++cc) HST(pp + ((long long)split * NCOLS + cc) * 128 + tid, acc[cc]);
             __threadfence();
             __syncthreads();
             if (tid == 0) {
-                const int old = atomicAdd(a.cnt + unit, 1);
+                const int old = HELM_CHK(a.cnt + unit, sizeof(int)) ? atomicAdd(a.cnt + unit, 1) : -1;
                 last_s = old == S - 1;
-                if (old == S - 1) a.cnt[unit] = 0;          // ready for the next launch
+                if (old == S - 1) HST(a.cnt + unit, 0);     // ready for the next launch
             }
             __syncthreads();
             fin = last_s != 0;
@@ -926,12 +927,12 @@ __global__ void __launch_bounds__(128, 1) tc_iface_kernel(IfaceArgs<float> a, in
                 for (int cc = 0; cc < NCOLS; ++cc) acc[cc] = 0.f;
                 for (int sp = 0; sp < S; ++sp)
 #pragma unroll
-                    for (int cc = 0; cc < NCOLS; ++cc) acc[cc] += __ldcg(pp + ((long long)sp * NCOLS + cc) * 128 + tid);
+                    for (int cc = 0; cc < NCOLS; ++cc) acc[cc] += HLDCG(pp + ((long long)sp * NCOLS + cc) * 128 + tid);
             }
         }
         if (fin && live) {
             const long long ti = sel(tin, srow) + pt;
-            const TraceCoef<T> cf = a.tc[ti];
+            const TraceCoef<T> cf = HLD(a.tc + ti);
             const long long to = (long long)(srow == 0 ? sd.tout[0] : srow == 1 ? sd.tout[1] : srow == 2 ? sd.tout[2]
                                                                                                          : sd.tout[3]) + pt;
 #pragma unroll
@@ -944,10 +945,10 @@ __global__ void __launch_bounds__(128, 1) tc_iface_kernel(IfaceArgs<float> a, in
                     if (k < nr) {
                         const long long oi = (long long)(rhs0 + k) * a.ntrace + ti;
                         const long long o = (long long)(rhs0 + k) * a.ntrace + to;
-                        if (a.gin0) gin[u] = a.gin0[oi];
-                        if (a.gin1) gin[u] = cadd(gin[u], a.gin1[oi]);
-                        if (a.base) bs[u] = a.base[o];
-                        if (a.sub) bs[u] = csub(bs[u], a.sub[o]);
+                        if (a.gin0) gin[u] = HLD(a.gin0 + oi);
+                        if (a.gin1) gin[u] = cadd(gin[u], HLD(a.gin1 + oi));
+                        if (a.base) bs[u] = HLD(a.base + o);
+                        if (a.sub) bs[u] = csub(bs[u], HLD(a.sub + o));
                     }
                 }
 #pragma unroll
@@ -957,8 +958,8 @@ __global__ void __launch_bounds__(128, 1) tc_iface_kernel(IfaceArgs<float> a, in
                         const T d = make_float2(acc[k], acc[NB + k]);
                         const T out = cadd(cfma(cf.cb, d, cmul(cf.ca, gin[u])), bs[u]);
                         const long long o = (long long)(rhs0 + k) * a.ntrace + to;
-                        a.dst[o] = out;
-                        if (a.dst2) a.dst2[o] = out;
+                        HST(a.dst + o, out);
+                        if (a.dst2) HST(a.dst2 + o, out);
                     }
                 }
             }

@@ -16,7 +16,8 @@ import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libhelm.so")
+# HELM_LIBRARY=check loads the bounds-checking build (build.build(variant="check"))
+LIB_PATH = os.path.join(_HERE, "libhelm_check.so" if os.environ.get("HELM_LIBRARY") == "check" else "libhelm.so")
 HEADER_PATH = os.path.join(os.path.dirname(_HERE), "include", "helm.h")
 
 PREC = {"c128": 0, "c64": 1}
@@ -46,7 +47,7 @@ class HelmSetupOpts(ctypes.Structure):
                 ("boundary_operators", ctypes.c_int), ("tensor_cores", ctypes.c_int),
                 ("tc_min_rhs", ctypes.c_int), ("autotune", ctypes.c_int), ("tc_iface_min_ctas", ctypes.c_int),
                 ("device_budget", ctypes.c_size_t), ("n_pade", ctypes.c_int), ("pade_phi", ctypes.c_double),
-                ("tc_factor", ctypes.c_int)]
+                ("tc_factor", ctypes.c_int), ("sym_k", ctypes.c_int)]
 
 
 class HelmInfo(ctypes.Structure):
@@ -63,7 +64,8 @@ def lib():
     if _lib is not None:
         return _lib
     if not os.path.exists(LIB_PATH):
-        raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2209_10886_gb300.build.build()")
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2209_10886_gb300.build.build()"
+                           + (' (variant="check")' if LIB_PATH.endswith("_check.so") else ""))
     L = ctypes.CDLL(LIB_PATH)
     L.helm_default_opts.argtypes = [ctypes.POINTER(HelmOpts)]
     L.helm_default_opts.restype = None
@@ -151,13 +153,14 @@ class Problem:
     may take, 0: no limit); ``n_pade`` and ``pade_phi`` of the "habc" transmission (the
     Pade HABC of the paper's experiments, with ``tc_scale`` the Robin parameter of the
     factored base problem); ``tc_factor`` (complex64 factorisation with tensor-core
-    trailing updates, subdomains at most 128 nodes wide).
+    trailing updates, subdomains at most 128 nodes wide); ``sym_k`` (complex64 interface
+    stages of one RHS that apply all of K read the packed symmetric operators).
     """
 
     def __init__(self, n_x, n_y, h, omega, m2, N1, N2, xcuts=None, ycuts=None,
                  transmission="optimized", tc_scale=1.0, boundary_operators=True, tensor_cores=True,
                  tc_min_rhs=16, autotune=True, tc_iface_min_ctas=-1, device_budget=0, n_pade=8,
-                 pade_phi=math.pi / 3, tc_factor=True):
+                 pade_phi=math.pi / 3, tc_factor=True, sym_k=False):
         L = lib()
         if not (m2.is_cuda and m2.dtype == torch.float64 and m2.numel() == n_x * n_y):
             raise TypeError("m2 must be a float64 CUDA tensor with n_x*n_y values")
@@ -165,7 +168,7 @@ class Problem:
         tcm = {False: 0, True: 1, "3xtf32": 1, "tf32": 2}[tensor_cores]
         so = HelmSetupOpts(TRANSMISSION[transmission], float(tc_scale), int(bool(boundary_operators)), tcm,
                            int(tc_min_rhs), int(bool(autotune)), int(tc_iface_min_ctas), int(device_budget),
-                           int(n_pade), float(pade_phi), int(bool(tc_factor)))
+                           int(n_pade), float(pade_phi), int(bool(tc_factor)), int(bool(sym_k)))
         xc = (ctypes.c_int * (N1 + 1))(*[int(v) for v in xcuts]) if xcuts is not None else None
         yc = (ctypes.c_int * (N2 + 1))(*[int(v) for v in ycuts]) if ycuts is not None else None
         h_ = ctypes.c_void_p()
@@ -184,6 +187,13 @@ class Problem:
         L.helm_factor_on_tensor_cores.restype = ctypes.c_int
         L.helm_factor_on_tensor_cores.argtypes = [_vp]
         return bool(L.helm_factor_on_tensor_cores(self._h))
+
+    def iface_symmetric(self, nrhs=1) -> bool:
+        """True when interface stages with nrhs RHS apply the packed symmetric operators."""
+        L = lib()
+        L.helm_iface_symmetric.restype = ctypes.c_int
+        L.helm_iface_symmetric.argtypes = [_vp, ctypes.c_int]
+        return bool(L.helm_iface_symmetric(self._h, int(nrhs)))
 
     def info(self):
         n, ns, nt, fb = _ll(), _i(), _ll(), _ll()
@@ -398,6 +408,37 @@ def stage_shape(problem: "Problem", nrhs: int) -> dict:
     _check(L.helm_stage_shape(problem._h, int(nrhs), *[ctypes.byref(x) for x in v]))
     return {"ctas_per_subdomain": v[0].value, "chunk_kb": v[1].value, "tensor_rhs_per_cta": v[2].value,
             "tuned": bool(v[3].value)}
+
+
+def check_bounds_report(reset: bool = False) -> dict:
+    """Failed bounds checks of the bounds-checking build (HELM_LIBRARY=check) since the last
+    reset: their count and the first one; checking_build is False for the normal build."""
+    L = lib()
+    L.helm_check_bounds_report.restype = ctypes.c_int
+    L.helm_check_bounds_report.argtypes = [ctypes.POINTER(_ll), ctypes.POINTER(ctypes.c_ulonglong),
+                                           ctypes.POINTER(_ll), ctypes.POINTER(_i), ctypes.c_char_p, _i, _i]
+    v, b, ln = _ll(), _ll(), _i()
+    a = ctypes.c_ulonglong()
+    unit = ctypes.create_string_buffer(256)
+    rc = L.helm_check_bounds_report(ctypes.byref(v), ctypes.byref(a), ctypes.byref(b), ctypes.byref(ln), unit, 256,
+                                    int(bool(reset)))
+    if rc < 0:
+        raise HelmError(2, "helm_check_bounds_report: CUDA error")
+    return {"checking_build": rc == 1, "violations": v.value, "first_addr": a.value, "first_bytes": b.value,
+            "first_line": ln.value, "unit": unit.value.decode()}
+
+
+def check_bounds_selftest():
+    """The checking build's check on a 256-byte allocation: (whole allocation passes, the
+    byte past its end passes, a range straddling its end passes); None for the normal build."""
+    L = lib()
+    L.helm_check_bounds_selftest.restype = ctypes.c_int
+    L.helm_check_bounds_selftest.argtypes = [ctypes.POINTER(_i)]
+    res = (_i * 3)()
+    rc = L.helm_check_bounds_selftest(res)
+    if rc < 0:
+        raise HelmError(2, "helm_check_bounds_selftest: CUDA error")
+    return tuple(bool(x) for x in res) if rc == 1 else None
 
 
 def profile(problem: "Problem", on: bool = True):

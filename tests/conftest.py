@@ -19,6 +19,20 @@ def pytest_collection_modifyitems(config, items):
     pass
 
 
+@pytest.fixture(autouse=True)
+def _no_failed_bounds_checks(request):
+    """Under HELM_LIBRARY=check (the bounds-checking build of the library) every GPU test
+    must end without a failed check of a kernel's global access."""
+    yield
+    if os.environ.get("HELM_LIBRARY") != "check" or "gpu" not in request.keywords:
+        return
+    from paper_2209_10886_gb300 import helm
+    if helm._lib is None:
+        return
+    rep = helm.check_bounds_report(reset=True)
+    assert rep["checking_build"] and rep["violations"] == 0, f"failed bounds checks: {rep}"
+
+
 @pytest.fixture(scope="session")
 def golden_dir():
     return os.path.join(ROOT, "tests", "golden")

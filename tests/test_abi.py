@@ -114,3 +114,20 @@ def test_habc_side_operator_matches_the_oracle_without_gpu(L):
         helm.habc_side_operator(np.array([1.0, -2.0]), 0.01)
     with pytest.raises(helm.HelmError):
         helm.habc_side_operator(np.array([1.0, 2.0]), 0.0)
+
+
+def test_normal_build_reports_no_bounds_checking_without_gpu(L):
+    """The diagnostics of the bounds-checking build exist in the normal build too, where
+    they report that no check is compiled in and touch no device."""
+    from paper_2209_10886_gb300 import helm
+    if os.environ.get("HELM_LIBRARY") == "check":
+        pytest.skip("the checking build is loaded")
+    r = helm.check_bounds_report()
+    assert r["checking_build"] is False and r["violations"] == 0
+    assert helm.check_bounds_selftest() is None
+
+
+def test_packed_operator_query_rejects_a_null_handle_without_gpu(L):
+    L.helm_iface_symmetric.restype = ctypes.c_int
+    L.helm_iface_symmetric.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    assert L.helm_iface_symmetric(None, 1) == 0
