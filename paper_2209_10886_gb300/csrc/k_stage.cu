@@ -18,7 +18,8 @@
 // A subdomain is solved either by one CTA (both halves) or by a cluster of
 // two CTAs, one per half: each computes its half of y, and after every grid
 // row the two exchange their halves of the next input vector through
-// distributed shared memory, signalled by a remote mbarrier arrival.  Every
+// distributed shared memory (st.async stores counted as bytes on the
+// receiver's mbarrier).  Every
 // wait is bounded in time; on expiry the kernel records HELM_ERR_TIMEOUT in a
 // device flag, finishes its (now meaningless) steps without waiting, drains
 // its own copies and skips the epilogue.
@@ -92,14 +93,17 @@ __device__ __forceinline__ unsigned peer_addr(const void* p, unsigned rank) {
     asm volatile("mapa.shared::cluster.u32 %0, %1, %2;\n" : "=r"(r) : "r"(smem_addr(p)), "r"(rank));
     return r;
 }
-__device__ __forceinline__ void st_peer(unsigned addr, float2 v) {
-    asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};\n" ::"r"(addr), "f"(v.x), "f"(v.y) : "memory");
+// store into the peer CTA's shared memory, counted as complete_tx bytes on the peer's
+// mbarrier `bar` (the completion releases the data at cluster scope)
+__device__ __forceinline__ void st_async_peer(unsigned addr, float2 v, unsigned bar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];\n" ::"r"(addr),
+                 "f"(v.x), "f"(v.y), "r"(bar)
+                 : "memory");
 }
-__device__ __forceinline__ void st_peer(unsigned addr, double2 v) {
-    asm volatile("st.shared::cluster.v2.f64 [%0], {%1, %2};\n" ::"r"(addr), "d"(v.x), "d"(v.y) : "memory");
-}
-__device__ __forceinline__ void arrive_peer(unsigned addr) {
-    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];\n" ::"r"(addr) : "memory");
+__device__ __forceinline__ void st_async_peer(unsigned addr, double2 v, unsigned bar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f64 [%0], {%1, %2}, [%3];\n" ::"r"(addr),
+                 "d"(v.x), "d"(v.y), "r"(bar)
+                 : "memory");
 }
 __device__ __forceinline__ void cluster_sync_all() {
     asm volatile("barrier.cluster.arrive.aligned;\nbarrier.cluster.wait.aligned;\n" ::: "memory");
@@ -113,7 +117,8 @@ __global__ void __launch_bounds__(NR <= 4 ? 544 : 288) stage_kernel(StageArgs<R>
                                                                   int cwarps, int ngroups, int csize) {
     using T = Cx<R>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ __align__(8) unsigned long long full_bar[MAXNS], empty_bar[MAXNS], xbar;
+    // xbar[b]: the peer's half of the next v of the steps with step & 1 == b (cluster form)
+    __shared__ __align__(8) unsigned long long full_bar[MAXNS], empty_bar[MAXNS], xbar[2];
     __shared__ int abort_flag;
 
     const int rank = csize == 2 ? (int)(blockIdx.x & 1) : 0;
@@ -130,6 +135,7 @@ __global__ void __launch_bounds__(NR <= 4 ? 544 : 288) stage_kernel(StageArgs<R>
     const int w0 = sd.w0;
     const int c_lo = csize == 2 ? (rank ? w0 : 0) : 0;
     const int c_hi = csize == 2 ? (rank ? mx : w0) : mx;
+    const int peer_cols = rank ? w0 : mx - w0;           // columns the peer CTA owns (cluster form)
     // consumers: ngroups groups of cwarps warps; thread (grp, c) sums the rows
     // grp, grp + ngroups, ... of every chunk for output column c_lo + c
     const int ncons = 32 * cwarps * ngroups;
@@ -215,7 +221,8 @@ __global__ void __launch_bounds__(NR <= 4 ? 544 : 288) stage_kernel(StageArgs<R>
             mbar_init(&full_bar[i], 1);
             mbar_init(&empty_bar[i], cwarps * ngroups);
         }
-        mbar_init(&xbar, 1);
+        mbar_init(&xbar[0], 1);
+        mbar_init(&xbar[1], 1);
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
@@ -394,18 +401,19 @@ __global__ void __launch_bounds__(NR <= 4 ? 544 : 288) stage_kernel(StageArgs<R>
                         if (r >= 1) ynext[k] = HLD(ywk + (long long)(r - 1) * mx + col);
                     }
                     vn[k * mxp + col] = nv;
-                    if (csize == 2 && !last) st_peer(peer_addr(&vn[k * mxp + col], rank ^ 1), nv);
+                    if (csize == 2 && !last)
+                        st_async_peer(peer_addr(&vn[k * mxp + col], rank ^ 1), nv, peer_addr(&xbar[step & 1], rank ^ 1));
                 }
             }
             consumer_sync(ncons);
             if (csize == 2 && !last) {
-                // exchange: my half of the next v is in the peer; wait for the peer's half
-                if (tid == 0) {
-                    asm volatile("fence.acq_rel.cluster;\n" ::: "memory");
-                    arrive_peer(peer_addr(&xbar, rank ^ 1));
-                }
+                // exchange: my half of the next v went to the peer by st.async; the peer's
+                // half arrives the same way, counted as bytes on xbar[step & 1] (each barrier
+                // completes every other step, so a half of step s + 2 cannot count towards
+                // step s)
+                if (tid == 0) mbar_expect_tx(&xbar[step & 1], (unsigned)(peer_cols * nr * sizeof(T)));
                 const bool ab = *((volatile int*)&abort_flag) != 0;
-                if (!mbar_wait<true>(&xbar, (unsigned)(step & 1), ab ? 1000 : WAIT_LIMIT)) {
+                if (!mbar_wait<true>(&xbar[step & 1], (unsigned)((step >> 1) & 1), ab ? 1000 : WAIT_LIMIT)) {
                     abort_flag = 1;
                     if (a.err) atomicExch(a.err, (int)HELM_ERR_TIMEOUT);
                 }
@@ -516,11 +524,10 @@ cudaError_t launch_stage(const StageArgs<R>& a, int nactive, int max_mx, int max
                          int num_sms, cudaStream_t st, const StageCfg* cfg) {
     if (nactive == 0) return cudaSuccess;
     if (max_mx > 256) return cudaErrorInvalidValue;
-    // two CTAs per subdomain when the stage leaves enough SMs idle and the arithmetic is
-    // FP64 (complex128 solves are bound by the FP64 units of one SM; complex64 ones by the
-    // per-row exchange latency the split adds); the autotuner may choose otherwise
-    int csize =
-        (sizeof(R) == 8 && 2 * nactive * std::max(1, (a.nrhs + 15) / 16) <= num_sms && max_mx >= 64) ? 2 : 1;
+    // two CTAs per subdomain when the stage leaves enough SMs idle: one SM alone streams a
+    // subdomain's factors well below its share of HBM (complex64) or is bound by its FP64
+    // units (complex128); the autotuner may choose otherwise
+    int csize = (2 * nactive * std::max(1, (a.nrhs + 15) / 16) <= num_sms && max_mx >= 64) ? 2 : 1;
     if (cfg && cfg->csize > 0) csize = cfg->csize;
     const int kb = cfg ? cfg->chunk_kb : 0;
     Geo g;
