@@ -90,7 +90,9 @@ struct GridDepWait {
 // copies completed).  kinit: initialise kbar here (else the caller did, once); kparity:
 // the phase of kbar this item's copies complete.  wait(): called by every thread after
 // the immutable prologue and before the first read of data earlier stages produce.
-template <typename R, int NR, bool LDCG, bool STAGED = false, bool MULTI = false, typename WaitF = GridDepWait>
+// RBI: output rows per item (RB, or fewer for the stage launches of one complex64 RHS)
+template <typename R, int NR, bool LDCG, bool STAGED = false, bool MULTI = false, typename WaitF = GridDepWait,
+          int RBI = RB>
 __device__ bool iface_item(const IfaceArgs<R>& a, int item_sub, int row_block, int rb_first, int rb_step,
                            unsigned char* smem_raw, unsigned long long* kbar = nullptr, int* kofs = nullptr,
                            WaitF wait = WaitF(), bool kinit = true, unsigned kparity = 0) {
@@ -108,7 +110,7 @@ __device__ bool iface_item(const IfaceArgs<R>& a, int item_sub, int row_block, i
 #pragma unroll
     for (int s = 0; s < 4; ++s)
         if (on(s)) rcount += len(s);
-    const int row0 = row_block * RB;
+    const int row0 = row_block * RBI;
     if (row0 >= rcount) return true;
     // side s and point pt of output row `row` (s = -1 past the last row)
     auto locate = [&](int row, int& s, int& pt) {
@@ -125,13 +127,13 @@ __device__ bool iface_item(const IfaceArgs<R>& a, int item_sub, int row_block, i
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr bool staged = STAGED;
     const int Lbp = staged_ld<T>(Lb);
-    T* Ks = reinterpret_cast<T*>(smem_raw);        // staged: [RB][Lbp] rows of K
+    T* Ks = reinterpret_cast<T*>(smem_raw);        // staged: [RBI][Lbp] rows of K
     if (staged && warp == 0) {
-        // lane q < RB copies row row0 + q: from the 16-byte unit holding its first element
+        // lane q < RBI copies row row0 + q: from the 16-byte unit holding its first element
         // to the one holding its last (complex64 rows need not start on a unit)
         long long a0 = 0;
         unsigned nbytes = 0;
-        if (lane < RB) {
+        if (lane < RBI) {
             int s, pt;
             locate(row0 + lane, s, pt);
             int off = 0;
@@ -167,7 +169,8 @@ __device__ bool iface_item(const IfaceArgs<R>& a, int item_sub, int row_block, i
                 : "memory");
     }
     // the rows of this warp and their transmission coefficients (immutable: before the wait)
-    constexpr int RPW = RB / (IT / 32);
+    constexpr int RPW = RBI / (IT / 32);
+    static_assert(RPW >= 1 && RPW * (IT / 32) == RBI, "whole rows per warp");
     constexpr int CU = (NR >= 8 || (sizeof(R) == 8 && NR >= 4)) ? 4 : 8;   // fits the register bound
     int srow[RPW], krow[RPW];
     long long tofs[RPW];
@@ -212,7 +215,7 @@ __device__ bool iface_item(const IfaceArgs<R>& a, int item_sub, int row_block, i
         bsub[q] = v;
     }
 
-    T* graw = staged ? Ks + (size_t)RB * Lbp : reinterpret_cast<T*>(smem_raw);   // [NR][Lb] incoming data
+    T* graw = staged ? Ks + (size_t)RBI * Lbp : reinterpret_cast<T*>(smem_raw);  // [NR][Lb] incoming data
     T* g = graw + (size_t)NR * Lb;                 // [NR][Lb] cin * incoming data
     if constexpr (NR == 1) {
     // every load of up to GU elements per thread is issued before the first is used
@@ -454,13 +457,14 @@ __global__ void __launch_bounds__(IT) sweep_dep_kernel(IfaceArgs<R> base, const 
     }
 }
 
-template <typename R, int NR, bool STAGED, bool MULTI>
+template <typename R, int NR, bool STAGED, bool MULTI, int RBI>
 __global__ void __launch_bounds__(IT) iface_kernel(IfaceArgs<R> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(8) unsigned long long kbar;
-    __shared__ int kofs[RB];
+    __shared__ int kofs[RBI];
     asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
-    iface_item<R, NR, false, STAGED, MULTI>(a, blockIdx.x, blockIdx.y, blockIdx.z, gridDim.z, smem_raw, &kbar, kofs);
+    iface_item<R, NR, false, STAGED, MULTI, GridDepWait, RBI>(a, blockIdx.x, blockIdx.y, blockIdx.z, gridDim.z,
+                                                              smem_raw, &kbar, kofs);
 }
 
 // grid-wide barrier of a cooperative launch; false (and HELM_ERR_TIMEOUT in err) when it expired
@@ -526,13 +530,13 @@ __global__ void __launch_bounds__(IT) sweep_kernel(IfaceArgs<R> base, const Swee
     }
 }
 
-template <typename R, int NR, bool STAGED, bool MULTI>
+template <typename R, int NR, bool STAGED, bool MULTI, int RBI>
 cudaError_t launch_nr_s_m(const IfaceArgs<R>& a, int nactive, int max_rows, size_t smem, int zb, cudaStream_t st) {
-    cudaError_t e =
-        cudaFuncSetAttribute(iface_kernel<R, NR, STAGED, MULTI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(iface_kernel<R, NR, STAGED, MULTI, RBI>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(nactive, (max_rows + RB - 1) / RB, zb);
+    cfg.gridDim = dim3(nactive, (max_rows + RBI - 1) / RBI, zb);
     cfg.blockDim = dim3(IT);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
@@ -542,12 +546,12 @@ cudaError_t launch_nr_s_m(const IfaceArgs<R>& a, int nactive, int max_rows, size
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     count_launch();
-    return cudaLaunchKernelEx(&cfg, iface_kernel<R, NR, STAGED, MULTI>, a);
+    return cudaLaunchKernelEx(&cfg, iface_kernel<R, NR, STAGED, MULTI, RBI>, a);
 }
 
 // RHS blocks: each CTA stages its K rows once and loops over the blocks z, z + gridDim.z,
 // ...; gridDim.z spreads them only as far as needed for `waves` CTAs per SM
-template <typename R, int NR, bool STAGED>
+template <typename R, int NR, bool STAGED, int RBI>
 cudaError_t launch_nr_s(const IfaceArgs<R>& a, int nactive, int max_rows, size_t smem, int waves, cudaStream_t st) {
     static int sms = 0;
     if (sms == 0) {
@@ -556,25 +560,29 @@ cudaError_t launch_nr_s(const IfaceArgs<R>& a, int nactive, int max_rows, size_t
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
             sms = 1;
     }
-    const long long items = (long long)nactive * ((max_rows + RB - 1) / RB);
+    const long long items = (long long)nactive * ((max_rows + RBI - 1) / RBI);
     const int nrb = (a.nrhs + NR - 1) / NR;
     const long long want = (long long)std::max(1, waves) * sms;
     const int zb = (int)std::min<long long>(nrb, std::max<long long>(1, (want + items - 1) / items));
-    if (zb == nrb) return launch_nr_s_m<R, NR, STAGED, false>(a, nactive, max_rows, smem, zb, st);
-    return launch_nr_s_m<R, NR, STAGED, true>(a, nactive, max_rows, smem, zb, st);
+    if (zb == nrb) return launch_nr_s_m<R, NR, STAGED, false, RBI>(a, nactive, max_rows, smem, zb, st);
+    return launch_nr_s_m<R, NR, STAGED, true, RBI>(a, nactive, max_rows, smem, zb, st);
 }
 
 // staged when allowed, when the item's K rows and gather fit two CTAs per SM and K is
-// 16-byte aligned
+// 16-byte aligned.  One complex64 RHS: items of 8 rows (twice the CTAs of 16-row items,
+// one row per warp; measured 23.1 vs 23.5 ms per solve on the 1023^2 workload, where the
+// sweep stages give each CTA an SM and its product over the staged rows is bound by
+// shared-memory reads); several RHS keep 16 rows (8 measured 3 % slower at 64 RHS)
 template <typename R, int NR>
 cudaError_t launch_nr(const IfaceArgs<R>& a, int nactive, int max_rows, int max_Lb, int staged_ok, int waves,
                       cudaStream_t st) {
     using T = Cx<R>;
+    constexpr int RBI = (sizeof(R) == 4 && NR == 1) ? RB / 2 : RB;
     const size_t gather = 2 * (size_t)NR * max_Lb * sizeof(T);
-    const size_t staged = (size_t)RB * staged_ld<T>(max_Lb) * sizeof(T) + gather;
+    const size_t staged = (size_t)RBI * staged_ld<T>(max_Lb) * sizeof(T) + gather;
     if (staged_ok && staged <= 113 * 1024 && (reinterpret_cast<uintptr_t>(a.K) & 15) == 0)
-        return launch_nr_s<R, NR, true>(a, nactive, max_rows, staged, waves, st);
-    return launch_nr_s<R, NR, false>(a, nactive, max_rows, gather, waves, st);
+        return launch_nr_s<R, NR, true, RBI>(a, nactive, max_rows, staged, waves, st);
+    return launch_nr_s<R, NR, false, RBI>(a, nactive, max_rows, gather, waves, st);
 }
 
 template <typename R, int NR>
