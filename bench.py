@@ -95,8 +95,9 @@ def parse():
                     help="interface stages of fewer CTAs stay on the CUDA cores (-1: two per SM)")
     ap.add_argument("--no-tc-factor", action="store_true",
                     help="complex64 factorisation on the CUDA cores (default: trailing updates on the tensor cores)")
-    ap.add_argument("--sym-k", action="store_true",
-                    help="one-RHS interface stages that apply all of K read the packed symmetric tiles")
+    ap.add_argument("--no-sym-k", action="store_true",
+                    help="one-RHS interface stages apply the full K (default: the stages that apply every "
+                         "subdomain's whole K stream its packed symmetric tiles)")
     ap.add_argument("--tc-min-rhs", type=int, default=16,
                     help="stages with at least this many RHS run on the tensor cores (1: all)")
     return ap.parse_args()
@@ -128,7 +129,7 @@ def precond_only(args):
     p = Problem(w.n, w.n, w.h, w.omega, m2, w.N1, w.N2, w.xcuts, w.ycuts, tensor_cores=TC_MODES[args.tensor_cores],
                 tc_min_rhs=args.tc_min_rhs, tc_scale=args.tc_scale, tc_iface_min_ctas=args.tc_iface_min_ctas,
                 autotune=not args.no_autotune, transmission=args.transmission, tc_factor=not args.no_tc_factor,
-                sym_k=args.sym_k)
+                sym_k=not args.no_sym_k)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     p.factor(args.prec)
@@ -511,7 +512,7 @@ def gpu_arm(args):
     f = torch.as_tensor(w.f, dtype=torch.complex128, device=dev)
     p = Problem(w.n, w.n, w.h, w.omega, m2, w.N1, w.N2, w.xcuts, w.ycuts, tensor_cores=TC_MODES[args.tensor_cores],
                 tc_min_rhs=args.tc_min_rhs, tc_scale=args.tc_scale, tc_iface_min_ctas=args.tc_iface_min_ctas,
-                autotune=not args.no_autotune, tc_factor=not args.no_tc_factor, sym_k=args.sym_k)
+                autotune=not args.no_autotune, tc_factor=not args.no_tc_factor, sym_k=not args.no_sym_k)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     p.factor(args.prec)
@@ -666,13 +667,14 @@ def gpu_arm(args):
                               "(tcgen05 GEMM, the stages that fill the GPU)")
         sym_form = p.iface_symmetric(w.nrhs)
         if sym_form:
-            names["trace"] = ("iface_sym_kernel (packed symmetric boundary operators, each stored tile read "
-                              "once for both of its blocks)")
-        # the ncu traffic figure belongs to the 1-RHS default workload it was captured on
-        same_capture = dom == "trace" and wname == WORKLOAD and w.nrhs == 1 and not tc_form
-        kfile = "k_iface_sym.cu" if sym_form else "k_iface.cu"
+            names["trace"] = ("iface_kernel (the sweep stages: boundary-operator GEMV + transmission) + "
+                              "iface_sym_kernel (the stages over every subdomain's whole K: packed symmetric "
+                              "tiles streamed by bulk copies, each counted once)")
+        # the ncu traffic figure belongs to the 1-RHS default workload it was captured on,
+        # with every interface stage in iface_kernel
+        same_capture = dom == "trace" and wname == WORKLOAD and w.nrhs == 1 and not tc_form and not sym_form
         roofline = {"bound": "hbm", "achieved": bw, "peak": peak, "unit": "GB/s", "frac": bw / peak,
-                    "traffic": NCU_TRAFFIC.get(kernel_hash(kfile)) if same_capture else None,
+                    "traffic": NCU_TRAFFIC.get(kernel_hash("k_iface.cu")) if same_capture else None,
                     "algorithmic_bytes_per_launch": st_[2] / max(st_[0], 1),
                     "kernel": names.get(dom, dom), "launches": st_[0],
                     "peak_source": f"hbm_gbs of {peak_src}"}

@@ -163,16 +163,16 @@ typedef struct {
                            X_r = T_r^{-1} as a blocked Gauss-Jordan elimination (panels of 16
                            columns, partial pivoting) whose rank-16 trailing updates are
                            3xTF32 tensor-core GEMMs; 0: the CUDA-core elimination */
-    int sym_k;          /* 1: with complex64 factors, boundary_operators = 1, the optimized
-                           or impedance transmission and at most 1024 interface boundary
-                           points per subdomain, precond_factor also stores the symmetric
-                           part (K + K^T)/2 of each K (K = P^T A_loc^{-1} P is complex
-                           symmetric, A_loc being so; the two differ by rounding) as its
-                           upper-triangle 32 x 32 tiles, half the bytes of K, and the
-                           interface stages of one right-hand side that apply all of K (the
-                           block Jacobi residual, the interface operator S) read it, each
-                           stored tile once for both of its blocks.  0 (default): every
-                           interface stage applies the full K */
+    int sym_k;          /* 1 (default): with complex64 factors, boundary_operators = 1, the
+                           optimized or impedance transmission and at most 1024 interface
+                           boundary points per subdomain, precond_factor also stores the
+                           symmetric part (K + K^T)/2 of each K (K = P^T A_loc^{-1} P is
+                           complex symmetric, A_loc being so; the two differ by rounding) as
+                           its upper-triangle 32 x 32 tiles, half the bytes of K, and the
+                           interface stages of one right-hand side that apply every
+                           subdomain's whole K (the block Jacobi residual, the interface
+                           operator S) stream them instead.  0: every interface stage
+                           applies the full K */
 } helm_setup_opts;
 
 typedef struct {

@@ -414,11 +414,12 @@ struct helm_problem {
     void* d_X = nullptr;
     void* d_K = nullptr;             // boundary operators of all subdomains
     size_t K_bytes = 0;
-    // packed symmetric boundary operators (complex64, k_iface_sym.cu): the tiles, the
-    // per-tile partial sums and arrival counters of one stage, tiles per row of the largest K
+    // packed symmetric boundary operators (complex64, k_iface_sym.cu): the tiles, the list
+    // of output row tiles (subdomain id, tile row) of all subdomains, tiles per row of the
+    // largest K
     float2* d_Kp = nullptr;
-    float2* d_spart = nullptr;
-    int* d_scnt = nullptr;
+    int2* d_symrt = nullptr;
+    int sym_nrt = 0;
     long long kp_elems = 0;
     int sym_ntmax = 0;
     size_t X_bytes = 0;
@@ -658,7 +659,7 @@ extern "C" void helm_default_setup_opts(helm_setup_opts* o) {
     o->n_pade = 8;
     o->pade_phi = 3.14159265358979323846 / 3.0;
     o->tc_factor = 1;
-    o->sym_k = 0;
+    o->sym_k = 1;
 }
 
 extern "C" const char* helm_last_error(void) { return g_err.c_str(); }
@@ -1128,7 +1129,7 @@ extern "C" helm_status helm_destroy(helm_problem* p) {
     }
     if (p->d_X) cudaFree(p->d_X);
     if (p->d_K) cudaFree(p->d_K);
-    dfree(p->d_Kp); dfree(p->d_spart); dfree(p->d_scnt);
+    dfree(p->d_Kp); dfree(p->d_symrt);
     if (p->d_Lq) cudaFree(p->d_Lq);
     if (p->d_D1) cudaFree(p->d_D1);
     if (p->d_D2) cudaFree(p->d_D2);
@@ -1378,20 +1379,22 @@ static bool sym_wanted(const helm_problem* p, int prec) {
     return p->sopts.sym_k && prec == HELM_PREC_C64 && p->sopts.boundary_operators && !p->habc &&
            p->max_Lb > 0 && p->max_Lb <= SYM_MAXLB;
 }
-// their bytes: the tiles, the partial sums of one stage, the arrival counters
+// their bytes: the tiles and the row-tile list
 static size_t sym_bytes(const helm_problem* p) {
-    const size_t ns = p->subs.size(), nt = (size_t)p->sym_ntmax;
-    return (size_t)p->kp_elems * sizeof(float2) + ns * nt * nt * SYM_TB * sizeof(float2) + ns * nt * sizeof(int);
+    return (size_t)p->kp_elems * sizeof(float2) + p->subs.size() * (size_t)p->sym_ntmax * sizeof(int2);
 }
 static helm_status build_symmetric_operators(helm_problem* p, cudaStream_t st) {
-    const size_t ns = p->subs.size(), nt = (size_t)p->sym_ntmax;
+    const size_t ns = p->subs.size();
+    std::vector<int2> rt;
+    for (size_t i = 0; i < ns; ++i)
+        for (int I = 0; I < (p->subs[i].dev.Lb + SYM_TB - 1) / SYM_TB; ++I) rt.push_back(make_int2((int)i, I));
     cudaError_t e;
-    if ((e = dalloc(p->d_Kp, (size_t)p->kp_elems)) != cudaSuccess || (e = dalloc(p->d_spart, ns * nt * nt * SYM_TB)) ||
-        (e = dalloc(p->d_scnt, ns * nt))) {
-        dfree(p->d_Kp); dfree(p->d_spart); dfree(p->d_scnt);
+    if ((e = dalloc(p->d_Kp, (size_t)p->kp_elems)) != cudaSuccess || (e = dalloc(p->d_symrt, rt.size()))) {
+        dfree(p->d_Kp); dfree(p->d_symrt);
         return cuda_status(e, "precond_factor: allocating the packed symmetric boundary operators");
     }
-    e = cudaMemsetAsync(p->d_scnt, 0, ns * nt * sizeof(int), st);
+    p->sym_nrt = (int)rt.size();
+    e = cudaMemcpyAsync(p->d_symrt, rt.data(), rt.size() * sizeof(int2), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
         e = launch_sym_pack(p->d_subtab, (int)ns, p->sym_ntmax, (const float2*)p->d_K, p->d_Kp, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -1454,7 +1457,7 @@ extern "C" helm_status precond_factor(helm_problem* p, helm_prec prec, void* str
     drop_graphs(p);
     if (p->d_X) { cudaFree(p->d_X); p->d_X = nullptr; p->X_bytes = 0; p->factored = 0; }
     if (p->d_K) { cudaFree(p->d_K); p->d_K = nullptr; p->K_bytes = 0; }
-    dfree(p->d_Kp); dfree(p->d_spart); dfree(p->d_scnt);
+    dfree(p->d_Kp); dfree(p->d_symrt);
     for (void** q : {&p->d_Lq, &p->d_D1, &p->d_D2})
         if (*q) { cudaFree(*q); *q = nullptr; }
     if (p->d_XT) { cudaFree(p->d_XT); p->d_XT = nullptr; p->XT_bytes = 0; p->tc_mt = 0; p->tc_split = 0; }
@@ -1962,7 +1965,8 @@ static helm_status run_stage_t(helm_problem* p, const PcWork& w, const PcCtx& cx
             max_rows = std::max(max_rows, rows);
         }
         // one complex64 RHS applying K itself: the packed symmetric tiles
-        const bool sym = sizeof(R) == 4 && nrhs == 1 && p->d_Kp && sd.kmat == KMAT_K && (sd.mask & 15) == 15;
+        const bool sym = sizeof(R) == 4 && nrhs == 1 && p->d_Kp && sd.kmat == KMAT_K && sd.mask == 15 &&
+                         sd.subs.size() == p->subs.size();
         double bytes = 0, flops = 0;
         if (p->prof_on) iface_accounting(p, sd, nrhs, sizeof(T), bytes, flops, sym);
         prof_begin(p, HELM_K_TRACE, st);
@@ -1971,10 +1975,7 @@ static helm_status run_stage_t(helm_problem* p, const PcWork& w, const PcCtx& cx
         if constexpr (sizeof(R) == 4) {
             if (sym) {
                 ia.Kp = p->d_Kp;
-                ia.spart = p->d_spart;
-                ia.scnt = p->d_scnt;
-                ia.ntmax = p->sym_ntmax;
-                e = launch_iface_sym(ia, (int)sd.subs.size(), st);
+                e = launch_iface_sym(ia, p->d_symrt, p->sym_nrt, p->max_Lb, p->num_sms, st);
             } else {
                 e = launch_iface<R>(ia, (int)sd.subs.size(), max_rows, p->max_Lb, st, iface_shape_for(p, nrhs, tmp));
             }

@@ -202,9 +202,8 @@ template <typename R> struct IfaceArgs {
     float* part; long long part_cap;
     int* cnt; int cnt_cap;
     // packed symmetric form (complex64, one RHS, k_iface_sym.cu): the upper-triangle tiles
-    // of every K, the per-tile partial sums (ntmax^2 tiles of 32 values per subdomain id)
-    // and one arrival counter per (subdomain id, row tile), zero between launches
-    const T* Kp; T* spart; int* scnt; int ntmax;
+    // of every K
+    const T* Kp;
 };
 
 // output rows of one work item of an interface stage (host tables and kernels agree on it)
@@ -310,9 +309,12 @@ __host__ __device__ __forceinline__ long long sym_tiles(int Lb) {
 }
 // Kp = the symmetric part (K + K^T) / 2 of every subdomain's K, packed as above
 cudaError_t launch_sym_pack(const SubDev* subtab, int nsub, int ntmax, const float2* K, float2* Kp, cudaStream_t st);
-// one complex64 interface stage with one RHS from the packed operators (a.Kp, a.spart,
-// a.scnt, a.ntmax set); the same outputs as launch_iface up to rounding
-cudaError_t launch_iface_sym(const IfaceArgs<float>& a, int nactive, cudaStream_t st);
+// one complex64 interface stage with one RHS over every subdomain and all four sides
+// (a.mask = 15) from the packed operators (a.Kp set); rt: the nrt output row tiles
+// (subdomain id, tile row), subdomain by subdomain; the same outputs as launch_iface up to
+// rounding
+cudaError_t launch_iface_sym(const IfaceArgs<float>& a, const int2* rt, int nrt, int max_Lb, int num_sms,
+                             cudaStream_t st);
 // a whole sweep (nstages interface stages, in order) in one cooperative launch of `grid`
 // CTAs (sweep_grid: the co-resident count, 0 when unavailable); bar: two zeroed words
 template <typename R> int sweep_grid(int nrhs, int max_Lb);

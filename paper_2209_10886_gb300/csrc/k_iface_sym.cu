@@ -1,4 +1,6 @@
-// Interface stages from the packed symmetric boundary operators (complex64, one RHS).
+// The stages that apply every subdomain's whole boundary operator (the block Jacobi
+// residual and the interface operator S), one complex64 RHS, from packed symmetric
+// boundary operators.
 //
 // The boundary operator of a subdomain, K = P^T A_loc^{-1} P (the local solve
 // restricted to the interface boundary points, before the transmission
@@ -6,28 +8,29 @@
 // symmetric because the local matrix is: the five-point rows and their Robin
 // diagonal terms are symmetric.  Its upper triangle, stored as 32 x 32 tiles,
 // takes half the bytes of the full operator: on the 1023^2, 8 x 8 workload 67
-// instead of 134 MB, which stays resident in the 129 MB L2 across the interface
-// iterations, while the full operator does not fit and streams from HBM at
-// every stage that applies all of it.
+// instead of 134 MB, which the 129 MB L2 can hold across the interface
+// iterations, while the full operator does not fit.
 //
-// One CTA per (subdomain, row tile I) reads each stored tile (I, J >= I) that
-// the stage needs once and uses it twice: K_IJ g_J adds to the outputs of row
-// tile I (a per-lane partial over the tile's columns, summed over the warp by a
-// butterfly reduce-scatter) and, for J > I, K_IJ^T g_I adds to those of row tile
-// J (one output per lane, no reduction).  The contributions to row tile J come
-// from the CTAs I <= J; each writes its partial vector into its own slot and
-// counts its arrival, and the CTA that arrives last for J adds the J + 1
-// partials in the order of I and forms the outgoing data
-//     G_out = ca G_in + cb u_b + (base - sub)
-// for the points of J that lie on masked sides.  No CTA waits for another, and
-// the sums do not depend on the order of arrival.
+// Persistent streaming form: each CTA owns a contiguous range of output row tiles
+// (subdomain, tile row I of 32 boundary points) and computes them completely, so no
+// CTA waits for another.  Row tile I needs the stored tiles (I, J) for J >= I and
+// (J, I) for J < I; one producer thread streams them, in J order, by bulk copies into
+// shared memory, starting before the dependency wait (K does not change during a
+// solve).  Consumer warp w takes the tiles J = w, w + 8, ..., through a slot of its own
+// (each slot is filled and emptied in one warp's order, so a parity wait never looks
+// more than one phase ahead):
+// lane l accumulates output row l, from a stored (I, J) tile along its row l (read
+// diagonally skewed, so that the 32 lanes hit distinct banks) and from a stored
+// (J, I) tile down its column l.  The warps' sums are added in warp order and the
+// outgoing data formed from per-point terms prepared with the gather:
+//     G_out = cb u_b + (ca G_in + base - sub).
 #include "helm_internal.cuh"
+
+#include <algorithm>
 
 namespace {
 
 constexpr int TB = SYM_TB;
-constexpr int NW = 8;              // warps per CTA
-constexpr int NT = 32 * NW;
 
 __device__ __forceinline__ int pick4(const int (&v)[4], int s) {
     return s == 0 ? v[0] : s == 1 ? v[1] : s == 2 ? v[2] : v[3];
@@ -63,162 +66,191 @@ __global__ void __launch_bounds__(256) sym_pack_kernel(const SubDev* subtab, con
     }
 }
 
-__global__ void __launch_bounds__(NT, 2) iface_sym_kernel(IfaceArgs<float> a) {
-    using T = float2;
-    __shared__ T gs[SYM_MAXLB];        // cin * incoming data of every boundary point, zero past Lb
-    __shared__ T ys[NW][TB];           // the warps' partial outputs of row tile I
-    __shared__ int jobs[32];           // row tiles this CTA completes
-    __shared__ int njobs;
-    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
-    const int sid = HLD(a.subs + blockIdx.x);
-    const SubDev sd = HLD(a.subtab + sid);
-    const int Lb = sd.Lb, nt = (Lb + TB - 1) / TB;
-    const int I = blockIdx.y;
-    if (I >= nt) return;
-    const int bo[4] = {sd.bo[0], sd.bo[1], sd.bo[2], sd.bo[3]};
-    const int tin[4] = {sd.tin[0], sd.tin[1], sd.tin[2], sd.tin[3]};
-    const int tout[4] = {sd.tout[0], sd.tout[1], sd.tout[2], sd.tout[3]};
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // row tiles holding points of masked sides
-    unsigned M = 0;
-#pragma unroll
-    for (int s = 0; s < 4; ++s)
-        if (((a.mask >> s) & 1) && bo[s] >= 0) {
-            const int len = s < 2 ? sd.my : sd.mx;
-            for (int t = bo[s] / TB; t <= (bo[s] + len - 1) / TB; ++t) M |= 1u << t;
-        }
-    const bool rowI = (M >> I) & 1u;
-    // the stored tiles (I, J) this CTA applies: all of tile row I when I is masked, else
-    // the ones whose transposed product feeds a masked row tile
-    unsigned need = 0;
-    for (int J = I; J < nt; ++J)
-        if (rowI || ((M >> J) & 1u)) need |= 1u << J;
-    if (need == 0) return;
-    const int ntile = __popc(need);
-    auto nth = [&](int k) {            // the k-th set bit of need
-        unsigned m = need;
-        for (int q = 0; q < k; ++q) m &= m - 1;
-        return __ffs(m) - 1;
-    };
-    const T* Kb = a.Kp + sd.kpoff;
-    // K does not change during the solve: start the first tile of each warp on its way
-    // into L1 while the previous stage may still run
-    if (warp < ntile) {
-        const char* t0 = reinterpret_cast<const char*>(Kb + tile_off(nt, I, nth(warp))) + lane * 256;
-        asm volatile("prefetch.global.L1 [%0];\n" ::"l"(t0));
-        asm volatile("prefetch.global.L1 [%0];\n" ::"l"(t0 + 128));
-    }
-    asm volatile("griddepcontrol.wait;\n" ::: "memory");
-    // cin * (G_in0 + G_in1) of every boundary point
-    for (int e = threadIdx.x; e < nt * TB; e += NT) {
-        T g = czero<T>();
-        if (e < Lb) {
-            const int s = side_of(bo, e);
-            const long long ti = pick4(tin, s) + (e - pick4(bo, s));
-            T G = czero<T>();
-            if (a.gin0) G = HLD(a.gin0 + ti);
-            if (a.gin1) G = cadd(G, HLD(a.gin1 + ti));
-            g = cmul(G, HLD(a.tc + ti).cin);
-        }
-        gs[e] = g;
-    }
-    __syncthreads();
+constexpr int CW = 8;                         // consumer warps
+constexpr int SLOTS = CW;                     // one tile slot (8 KB) per consumer warp
+constexpr int ST = 32 * (CW + 1);             // + one producer warp
+constexpr long long SYM_WAIT = 2000000000LL;  // cycles (~1 s) before a wait gives up
 
-    const long long slot0 = (long long)sid * a.ntmax;          // this subdomain's row tiles
-    T p[TB];                                                    // direct partials of row tile I
-#pragma unroll
-    for (int r = 0; r < TB; ++r) p[r] = czero<T>();
-    const T* gI = gs + I * TB;
-    for (int k = warp; k < ntile; k += NW) {
-        const int J = nth(k);
-        const T* tile = Kb + tile_off(nt, I, J) + lane;
-        const bool trn = J > I && ((M >> J) & 1u);
-        const T gJ = gs[J * TB + lane];
-        T q = czero<T>();
-#pragma unroll
-        for (int r0 = 0; r0 < TB; r0 += 16) {
-            T kv[16];
-#pragma unroll
-            for (int u = 0; u < 16; ++u) {
-                const T* kp = tile + (r0 + u) * TB;
-                kv[u] = HELM_CHK(kp, sizeof(T)) ? __ldg(kp) : czero<T>();
-            }
-#pragma unroll
-            for (int u = 0; u < 16; ++u) {
-                if (rowI) p[r0 + u] = cfma(kv[u], gJ, p[r0 + u]);
-                if (trn) q = cfma(kv[u], gI[r0 + u], q);
-            }
+__device__ __forceinline__ unsigned sm32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mb_init(unsigned long long* b) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(sm32(b)) : "memory");
+}
+__device__ __forceinline__ void mb_arrive(unsigned long long* b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(sm32(b)) : "memory");
+}
+__device__ __forceinline__ bool mb_try(unsigned long long* b, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(sm32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait for the phase with this parity (limit 0: one look)
+__device__ __forceinline__ bool mb_wait(unsigned long long* b, unsigned parity, long long limit) {
+    if (mb_try(b, parity)) return true;
+    const long long t0 = clock64();
+    while (!mb_try(b, parity))
+        if (clock64() - t0 > limit) return false;
+    return true;
+}
+__device__ __forceinline__ void consumers_sync() { asm volatile("bar.sync 1, %0;\n" ::"r"(32 * CW) : "memory"); }
+
+// rt[t] = (subdomain id, tile row I) of output row tile t, subdomain by subdomain;
+// dynamic shared memory: slot[CW][1024] | gc[gcap] (cin * G_in) | cb[gcap] | cterm[gcap]
+__global__ void __launch_bounds__(ST, 2) iface_sym_kernel(IfaceArgs<float> a, const int2* rt, int nrt, int gcap) {
+    using T = float2;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) unsigned long long full[SLOTS], empty[SLOTS];
+    __shared__ T ys[CW][TB];
+    __shared__ int abort_flag;
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+    T* ring = reinterpret_cast<T*>(smem);
+    T* gc = ring + (size_t)SLOTS * TB * TB;
+    T* cbv = gc + gcap;
+    T* ctv = cbv + gcap;
+    const int t0 = (int)((long long)blockIdx.x * nrt / gridDim.x);
+    const int t1 = (int)((long long)(blockIdx.x + 1) * nrt / gridDim.x);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < SLOTS; ++i) {
+            mb_init(&full[i]);
+            mb_init(&empty[i]);
         }
-        if (trn) HST(a.spart + ((slot0 + J) * a.ntmax + I) * TB + lane, q);
-    }
-    if (rowI) {
-        // reduce-scatter over the lanes: lane l ends with the warp's sum of p[l]
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const bool up = (lane & o) != 0;
-#pragma unroll
-            for (int i = 0; i < o; ++i) {
-                const T send = up ? p[i] : p[i + o];
-                const T keep = up ? p[i + o] : p[i];
-                p[i] = make_float2(keep.x + __shfl_xor_sync(0xffffffffu, send.x, o),
-                                   keep.y + __shfl_xor_sync(0xffffffffu, send.y, o));
-            }
-        }
-        ys[warp][lane] = p[0];
-    }
-    __syncthreads();
-    if (rowI && warp == 0) {
-        T y = ys[0][lane];
-#pragma unroll
-        for (int w = 1; w < NW; ++w) y = cadd(y, ys[w][lane]);
-        HST(a.spart + ((slot0 + I) * a.ntmax + I) * TB + lane, y);
-    }
-    // count this CTA's contributions (row tiles J >= I that are masked); the CTA that
-    // brings the (J + 1)-th one completes row tile J
-    __threadfence();
-    if (threadIdx.x == 0) njobs = 0;
-    __syncthreads();
-    if (threadIdx.x < nt) {
-        const int J = threadIdx.x;
-        if (J >= I && ((M >> J) & 1u)) {
-            const int old = HELM_CHK(a.scnt + slot0 + J, sizeof(int)) ? atomicAdd(a.scnt + slot0 + J, 1) : -1;
-            if (old == J) jobs[atomicAdd(&njobs, 1)] = J;
-        }
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     __syncthreads();
-    const int nj = njobs;
-    if (nj == 0) return;
-    __threadfence();
-    for (int jb = warp; jb < nj; jb += NW) {
-        const int J = jobs[jb];
-        const T* pj = a.spart + (slot0 + J) * a.ntmax * TB + lane;
-        T y = czero<T>();
-        for (int i = 0; i <= J; ++i) {
-            const T* pi = pj + (long long)i * TB;
-            y = cadd(y, HELM_CHK(pi, sizeof(T)) ? __ldcg(pi) : czero<T>());
+    if (t0 >= t1) return;
+
+    if (warp == CW) {
+        // producer: the tiles of every row tile of the range, in order
+        if (lane != 0) return;
+        int fills[CW];                    // tiles sent through each warp's slot so far
+#pragma unroll
+        for (int v = 0; v < CW; ++v) fills[v] = 0;
+        for (int t = t0; t < t1 && !*((volatile int*)&abort_flag); ++t) {
+            const int2 w = HLD(rt + t);
+            const SubDev sd = HLD(a.subtab + w.x);
+            const int nt = (sd.Lb + TB - 1) / TB, I = w.y;
+            const T* Kb = a.Kp + sd.kpoff;
+            for (int J = 0; J < nt; ++J) {
+                const int slot = J % CW;
+                int n = 0;
+#pragma unroll
+                for (int v = 0; v < CW; ++v)
+                    if (v == slot) n = fills[v];
+                // the warp has emptied the slot's previous tile (fill n - 1)
+                if (n >= 1 && !mb_wait(&empty[slot], (unsigned)((n - 1) & 1), SYM_WAIT)) {
+                    abort_flag = 1;
+                    if (a.err) atomicExch(a.err, (int)HELM_ERR_TIMEOUT);
+                    break;
+                }
+#pragma unroll
+                for (int v = 0; v < CW; ++v)
+                    if (v == slot) fills[v] = n + 1;
+                const T* src = Kb + (J >= I ? tile_off(nt, I, J) : tile_off(nt, J, I));
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(sm32(&full[slot])),
+                             "r"(TB * TB * 8)
+                             : "memory");
+                if (HELM_CHK(src, TB * TB * sizeof(T)))   // checking build: the wait then gives up
+                    asm volatile(
+                        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                            sm32(ring + (size_t)slot * TB * TB)),
+                        "l"(src), "r"(TB * TB * 8), "r"(sm32(&full[slot]))
+                        : "memory");
+            }
         }
-        const int e = J * TB + lane;
-        if (e < Lb) {
-            const int s = side_of(bo, e);
-            if ((a.mask >> s) & 1) {
-                const int pt = e - pick4(bo, s);
-                const long long ti = pick4(tin, s) + pt, to = pick4(tout, s) + pt;
-                const TraceCoef<T> c = HLD(a.tc + ti);
-                T G = czero<T>();
-                if (a.gin0) G = HLD(a.gin0 + ti);
-                if (a.gin1) G = cadd(G, HLD(a.gin1 + ti));
-                T bsub = czero<T>();
-                if (a.base) bsub = HLD(a.base + to);
-                if (a.sub) bsub = csub(bsub, HLD(a.sub + to));
-                const T out = cadd(cfma(c.cb, y, cmul(c.ca, G)), bsub);
+        // no copy outlives the CTA: on abort, wait (bounded) for the last fill of each slot
+        if (*((volatile int*)&abort_flag))
+#pragma unroll
+            for (int v = 0; v < CW; ++v)
+                if (fills[v] > 0) mb_wait(&full[v], (unsigned)((fills[v] - 1) & 1), SYM_WAIT);
+        return;
+    }
+
+    // consumers
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
+    int n = 0, cur = -1;                  // tiles this warp has taken from its slot
+    for (int t = t0; t < t1; ++t) {
+        const int2 w = HLD(rt + t);
+        const SubDev sd = HLD(a.subtab + w.x);
+        const int Lb = sd.Lb, nt = (Lb + TB - 1) / TB, I = w.y;
+        const int bo[4] = {sd.bo[0], sd.bo[1], sd.bo[2], sd.bo[3]};
+        const int tin[4] = {sd.tin[0], sd.tin[1], sd.tin[2], sd.tin[3]};
+        const int tout[4] = {sd.tout[0], sd.tout[1], sd.tout[2], sd.tout[3]};
+        if (w.x != cur) {
+            // a new subdomain: cin * G_in, cb and the constant term of every boundary point
+            for (int e = threadIdx.x; e < nt * TB; e += 32 * CW) {
+                T g = czero<T>(), cb = czero<T>(), ct = czero<T>();
+                if (e < Lb) {
+                    const int s = side_of(bo, e);
+                    const int pt = e - pick4(bo, s);
+                    const long long ti = pick4(tin, s) + pt, to = pick4(tout, s) + pt;
+                    const TraceCoef<T> c = HLD(a.tc + ti);
+                    T G = czero<T>();
+                    if (a.gin0) G = HLD(a.gin0 + ti);
+                    if (a.gin1) G = cadd(G, HLD(a.gin1 + ti));
+                    T bsub = czero<T>();
+                    if (a.base) bsub = HLD(a.base + to);
+                    if (a.sub) bsub = csub(bsub, HLD(a.sub + to));
+                    g = cmul(G, c.cin);
+                    cb = c.cb;
+                    ct = cadd(cmul(c.ca, G), bsub);
+                }
+                gc[e] = g;
+                cbv[e] = cb;
+                ctv[e] = ct;
+            }
+            consumers_sync();
+            cur = w.x;
+        }
+        T acc = czero<T>();
+        for (int J = warp; J < nt; J += CW, ++n) {
+            const int slot = warp;
+            const bool ab = *((volatile int*)&abort_flag) != 0;
+            if (!mb_wait(&full[slot], (unsigned)(n & 1), ab ? 0 : SYM_WAIT)) {
+                abort_flag = 1;
+                if (a.err) atomicExch(a.err, (int)HELM_ERR_TIMEOUT);
+            }
+            if (!*((volatile int*)&abort_flag)) {
+                const T* tile = ring + (size_t)slot * TB * TB;
+                const T* gJ = gc + J * TB;
+                if (J >= I) {
+                    // stored (I, J): row `lane` of the tile, diagonally
+#pragma unroll 8
+                    for (int cc = 0; cc < TB; ++cc) {
+                        const int c = (cc + lane) & (TB - 1);
+                        acc = cfma(tile[lane * TB + c], gJ[c], acc);
+                    }
+                } else {
+                    // stored (J, I): column `lane` of the tile
+#pragma unroll 8
+                    for (int r = 0; r < TB; ++r) acc = cfma(tile[r * TB + lane], gJ[r], acc);
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mb_arrive(&empty[slot]);
+        }
+        ys[warp][lane] = acc;
+        consumers_sync();
+        if (warp == 0 && !*((volatile int*)&abort_flag)) {
+            T y = ys[0][lane];
+#pragma unroll
+            for (int v = 1; v < CW; ++v) y = cadd(y, ys[v][lane]);
+            const int e = I * TB + lane;
+            if (e < Lb) {
+                const int s = side_of(bo, e);
+                const long long to = pick4(tout, s) + (e - pick4(bo, s));
+                const T out = cadd(cmul(cbv[e], y), ctv[e]);
                 HST(a.dst + to, out);
                 if (a.dst2) HST(a.dst2 + to, out);
             }
         }
-        if (lane == 0) HST(a.scnt + slot0 + J, 0);              // ready for the next stage
+        consumers_sync();                 // ys, and at a new subdomain the point terms, are reused
     }
 }
-
 }  // namespace
 
 cudaError_t launch_sym_pack(const SubDev* subtab, int nsub, int ntmax, const float2* K, float2* Kp, cudaStream_t st) {
@@ -229,14 +261,18 @@ cudaError_t launch_sym_pack(const SubDev* subtab, int nsub, int ntmax, const flo
     return cudaGetLastError();
 }
 
-cudaError_t launch_iface_sym(const IfaceArgs<float>& a, int nactive, cudaStream_t st) {
-    if (nactive == 0 || a.nrhs == 0) return cudaSuccess;
-    if (a.nrhs != 1 || !a.Kp || !a.spart || !a.scnt || a.ntmax < 1 || a.ntmax > SYM_MAXLB / SYM_TB)
-        return cudaErrorInvalidValue;
+cudaError_t launch_iface_sym(const IfaceArgs<float>& a, const int2* rt, int nrt, int max_Lb, int num_sms,
+                             cudaStream_t st) {
+    if (nrt == 0 || a.nrhs == 0) return cudaSuccess;
+    if (a.nrhs != 1 || !a.Kp || !rt || a.mask != 15 || max_Lb < 1 || max_Lb > SYM_MAXLB) return cudaErrorInvalidValue;
+    const int gcap = (max_Lb + TB - 1) / TB * TB;
+    const size_t smem = (size_t)SLOTS * TB * TB * sizeof(float2) + 3 * (size_t)gcap * sizeof(float2);
+    cudaError_t e = cudaFuncSetAttribute(iface_sym_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(nactive, a.ntmax);
-    cfg.blockDim = dim3(NT);
-    cfg.dynamicSmemBytes = 0;
+    cfg.gridDim = dim3(std::min(nrt, 2 * std::max(1, num_sms)));
+    cfg.blockDim = dim3(ST);
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -244,5 +280,5 @@ cudaError_t launch_iface_sym(const IfaceArgs<float>& a, int nactive, cudaStream_
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     count_launch();
-    return cudaLaunchKernelEx(&cfg, iface_sym_kernel, a);
+    return cudaLaunchKernelEx(&cfg, iface_sym_kernel, a, rt, nrt, gcap);
 }

@@ -154,13 +154,14 @@ class Problem:
     Pade HABC of the paper's experiments, with ``tc_scale`` the Robin parameter of the
     factored base problem); ``tc_factor`` (complex64 factorisation with tensor-core
     trailing updates, subdomains at most 128 nodes wide); ``sym_k`` (complex64 interface
-    stages of one RHS that apply all of K read the packed symmetric operators).
+    stages of one RHS that apply every subdomain's whole K stream the packed symmetric
+    operators).
     """
 
     def __init__(self, n_x, n_y, h, omega, m2, N1, N2, xcuts=None, ycuts=None,
                  transmission="optimized", tc_scale=1.0, boundary_operators=True, tensor_cores=True,
                  tc_min_rhs=16, autotune=True, tc_iface_min_ctas=-1, device_budget=0, n_pade=8,
-                 pade_phi=math.pi / 3, tc_factor=True, sym_k=False):
+                 pade_phi=math.pi / 3, tc_factor=True, sym_k=True):
         L = lib()
         if not (m2.is_cuda and m2.dtype == torch.float64 and m2.numel() == n_x * n_y):
             raise TypeError("m2 must be a float64 CUDA tensor with n_x*n_y values")

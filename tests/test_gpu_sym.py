@@ -8,8 +8,9 @@ from K^T by rounding, so the packed form and the full form agree to the complex6
 level, and both match the oracle's complex128 sweep (which never forms K) within
 the complex64 bar of test_gpu_parity.py.  Cases: even, ragged and uneven
 checkerboards (tile rows that straddle two sides, a last tile past Lb), 131-node
-sides, 256-node subdomains (1024 boundary points, the largest packed form), the
-impedance transmission, every stage mask of BSP, SP and the non-overlapping bands.
+sides, 256-node subdomains (1024 boundary points, the largest packed form), an 8 x 8
+checkerboard whose ~450 output row tiles make every CTA stream several in turn, the
+impedance transmission, every schedule (BSP, SP, the non-overlapping bands).
 """
 import numpy as np
 import pytest
@@ -22,9 +23,11 @@ import workloads as W
 from oracle import Decomposition, Sweeper, assemble_operator
 
 C64_BAR = 1e-4          # against the oracle (complex64 factors, as test_gpu_parity.py)
-# 256-node subdomains: the complex64 block recursion runs over 256 grid rows instead of
-# at most 131, measured 3.9e-4 with the full and with the packed operators alike
-C64_BAR_256 = 2e-3
+# cases whose complex64 error is larger with the full and the packed operators alike:
+# 256-node subdomains (the block recursion runs over 256 grid rows instead of at most
+# 131; measured 3.9e-4) and the 8 x 8 checkerboard (the rounding of 30 sweep stages
+# accumulates; measured 1.07e-4)
+CASE_BAR = {"side256_3x3": 2e-3, "many_8x8_64": 5e-4}
 FORMS_BAR = 5e-5        # packed against full operators, both complex64
 
 
@@ -55,6 +58,8 @@ CASES = {
                                        xcuts=[0, 131, 262], ycuts=[0, 129, 262]),
     "side256_3x3": lambda: W.workload("custom", n=768, N1=3, N2=3, medium="layered", seed=8,
                                       xcuts=[0, 256, 512, 768], ycuts=[0, 256, 512, 768]),
+    # ~450 output row tiles: more than one CTA per SM pair, so each CTA streams several
+    "many_8x8_64": lambda: W.workload("custom", n=512, N1=8, N2=8, medium="layered", seed=9),
 }
 
 
@@ -80,7 +85,7 @@ def test_packed_operators_match_full_and_oracle(H, case, transmission):
                else sw.precondition(r, sched))
         ea, eb, ef = rel(a, ref), rel(b, ref), rel(a, b)
         print(f"{case} {transmission} {sched}: packed {ea:.2e}, full {eb:.2e}, packed vs full {ef:.2e}")
-        bar = C64_BAR_256 if case == "side256_3x3" else C64_BAR
+        bar = CASE_BAR.get(case, C64_BAR)
         assert ea <= bar and eb <= bar and ef <= FORMS_BAR
     p.close(); q.close()
 
