@@ -66,8 +66,13 @@ __global__ void __launch_bounds__(256) sym_pack_kernel(const SubDev* subtab, con
     }
 }
 
+// measured on the 1023^2, 8 x 8 workload: 8 consumer warps with one slot each at two
+// CTAs per SM (22.0 ms per solve); 4 warps at 3 or 4 CTAs per SM, or two slots per warp,
+// within 1 %; one CTA per SM (16 slots) 24.4-24.9 ms
 constexpr int CW = 8;                         // consumer warps
-constexpr int SLOTS = CW;                     // one tile slot (8 KB) per consumer warp
+constexpr int D = 1;                          // tile slots (8 KB) per consumer warp
+constexpr int CTAS = 2;                       // CTAs per SM
+constexpr int SLOTS = CW * D;
 constexpr int ST = 32 * (CW + 1);             // + one producer warp
 constexpr long long SYM_WAIT = 2000000000LL;  // cycles (~1 s) before a wait gives up
 
@@ -99,7 +104,7 @@ __device__ __forceinline__ void consumers_sync() { asm volatile("bar.sync 1, %0;
 
 // rt[t] = (subdomain id, tile row I) of output row tile t, subdomain by subdomain;
 // dynamic shared memory: slot[CW][1024] | gc[gcap] (cin * G_in) | cb[gcap] | cterm[gcap]
-__global__ void __launch_bounds__(ST, 2) iface_sym_kernel(IfaceArgs<float> a, const int2* rt, int nrt, int gcap) {
+__global__ void __launch_bounds__(ST, CTAS) iface_sym_kernel(IfaceArgs<float> a, const int2* rt, int nrt, int gcap) {
     using T = float2;
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) unsigned long long full[SLOTS], empty[SLOTS];
@@ -136,20 +141,21 @@ __global__ void __launch_bounds__(ST, 2) iface_sym_kernel(IfaceArgs<float> a, co
             const int nt = (sd.Lb + TB - 1) / TB, I = w.y;
             const T* Kb = a.Kp + sd.kpoff;
             for (int J = 0; J < nt; ++J) {
-                const int slot = J % CW;
+                const int cw = J % CW;
                 int n = 0;
 #pragma unroll
                 for (int v = 0; v < CW; ++v)
-                    if (v == slot) n = fills[v];
-                // the warp has emptied the slot's previous tile (fill n - 1)
-                if (n >= 1 && !mb_wait(&empty[slot], (unsigned)((n - 1) & 1), SYM_WAIT)) {
+                    if (v == cw) n = fills[v];
+                const int slot = cw * D + n % D;
+                // the warp has emptied the slot's previous tile (its fill n / D - 1)
+                if (n >= D && !mb_wait(&empty[slot], (unsigned)((n / D - 1) & 1), SYM_WAIT)) {
                     abort_flag = 1;
                     if (a.err) atomicExch(a.err, (int)HELM_ERR_TIMEOUT);
                     break;
                 }
 #pragma unroll
                 for (int v = 0; v < CW; ++v)
-                    if (v == slot) fills[v] = n + 1;
+                    if (v == cw) fills[v] = n + 1;
                 const T* src = Kb + (J >= I ? tile_off(nt, I, J) : tile_off(nt, J, I));
                 asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(sm32(&full[slot])),
                              "r"(TB * TB * 8)
@@ -166,7 +172,8 @@ __global__ void __launch_bounds__(ST, 2) iface_sym_kernel(IfaceArgs<float> a, co
         if (*((volatile int*)&abort_flag))
 #pragma unroll
             for (int v = 0; v < CW; ++v)
-                if (fills[v] > 0) mb_wait(&full[v], (unsigned)((fills[v] - 1) & 1), SYM_WAIT);
+                for (int q = fills[v] - 1; q >= 0 && q >= fills[v] - D; --q)
+                    mb_wait(&full[v * D + q % D], (unsigned)((q / D) & 1), SYM_WAIT);
         return;
     }
 
@@ -208,9 +215,9 @@ __global__ void __launch_bounds__(ST, 2) iface_sym_kernel(IfaceArgs<float> a, co
         }
         T acc = czero<T>();
         for (int J = warp; J < nt; J += CW, ++n) {
-            const int slot = warp;
+            const int slot = warp * D + n % D;
             const bool ab = *((volatile int*)&abort_flag) != 0;
-            if (!mb_wait(&full[slot], (unsigned)(n & 1), ab ? 0 : SYM_WAIT)) {
+            if (!mb_wait(&full[slot], (unsigned)((n / D) & 1), ab ? 0 : SYM_WAIT)) {
                 abort_flag = 1;
                 if (a.err) atomicExch(a.err, (int)HELM_ERR_TIMEOUT);
             }
@@ -270,7 +277,7 @@ cudaError_t launch_iface_sym(const IfaceArgs<float>& a, const int2* rt, int nrt,
     cudaError_t e = cudaFuncSetAttribute(iface_sym_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(std::min(nrt, 2 * std::max(1, num_sms)));
+    cfg.gridDim = dim3(std::min(nrt, CTAS * std::max(1, num_sms)));
     cfg.blockDim = dim3(ST);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
