@@ -37,10 +37,11 @@ METRIC = "unknowns×RHS solved/s to rel. residual 1e-6 (mixed vs FP64, 1 GB300);
 UNIT = "unknowns*RHS/s"
 WORKLOAD = "plain_mixed"
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch measured by ncu,
-# keyed by (kernel source file, sha256 prefix of that file when it was measured): None
-# once the source changes.  k_iface.cu: mean over 36 consecutive iface_kernel launches
-# of the bench (sweep, residual and S stages), caches left warm (--cache-control none).
-NCU_TRAFFIC = {("k_iface.cu", "68a2ba5c6ef1dc72"): 9.380e6}
+# keyed by the kernel source files and the sha256 prefixes they had when it was measured:
+# None once a source changes.  The interface stages of one RHS: mean over 36 consecutive
+# interface-stage launches of the bench (32 sweep stages in iface_kernel, the residual and
+# S stages in iface_sym_kernel), caches left warm (--cache-control none).
+NCU_TRAFFIC = {(("k_iface.cu", "4eb8ed015935f074"), ("k_iface_sym.cu", "630bbaa666058470")): 9.716e6}
 FP64_PEAK_TFLOPS = 1.25
 
 
@@ -670,11 +671,11 @@ def gpu_arm(args):
             names["trace"] = ("iface_kernel (the sweep stages: boundary-operator GEMV + transmission) + "
                               "iface_sym_kernel (the stages over every subdomain's whole K: packed symmetric "
                               "tiles streamed by bulk copies, each counted once)")
-        # the ncu traffic figure belongs to the 1-RHS default workload it was captured on,
-        # with every interface stage in iface_kernel
-        same_capture = dom == "trace" and wname == WORKLOAD and w.nrhs == 1 and not tc_form and not sym_form
+        # the ncu traffic figure belongs to the 1-RHS default workload it was captured on
+        same_capture = dom == "trace" and wname == WORKLOAD and w.nrhs == 1 and not tc_form and sym_form
+        key = (kernel_hash("k_iface.cu"), kernel_hash("k_iface_sym.cu"))
         roofline = {"bound": "hbm", "achieved": bw, "peak": peak, "unit": "GB/s", "frac": bw / peak,
-                    "traffic": NCU_TRAFFIC.get(kernel_hash("k_iface.cu")) if same_capture else None,
+                    "traffic": NCU_TRAFFIC.get(key) if same_capture else None,
                     "algorithmic_bytes_per_launch": st_[2] / max(st_[0], 1),
                     "kernel": names.get(dom, dom), "launches": st_[0],
                     "peak_source": f"hbm_gbs of {peak_src}"}
