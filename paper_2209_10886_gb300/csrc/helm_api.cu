@@ -2985,18 +2985,32 @@ extern "C" helm_status gmres_solve(helm_problem* p, const helm_c128* f, helm_c12
     if (o.inner_maxit > 0 && (o.inner_restart < 1 || o.inner_restart > 500))
         return arg_error("gmres_solve: inner_restart must be in 1..500");
     if (o.inner_maxit > 0 && !(o.inner_tol > 0)) return arg_error("gmres_solve: inner_tol must be > 0");
-    // Right-hand sides are solved in chunks whose Krylov workspace, (2 restart + 1)
-    // complex128 fields per RHS plus the preconditioner workspace, fits in 60% of
-    // the device memory that is free now (already-allocated workspace counts as free).
+    // Right-hand sides are solved in chunks of equal size whose workspace fits in 80 % of
+    // the device memory that is free now (the workspace already allocated counts as free):
+    // per RHS the volume Krylov fields ((2 restart + 1) complex128 vectors, and two more),
+    // the interface Krylov fields of the nested solve ((2 inner_restart + 1) trace
+    // vectors), and the preconditioner's interface buffers, solve workspace and scaled
+    // source.
     const long long N = p->N();
     size_t freeb = 0, totalb = 0;
     HELM_CUDA_TRY(cudaMemGetInfo(&freeb, &totalb));
-    const size_t held = (size_t)p->kw.nrhs * ((size_t)2 * p->kw.restart + 1) * N * sizeof(double2);
-    const size_t per_rhs = ((size_t)2 * o.restart + 1) * N * sizeof(double2) + (size_t)N * 2 * sizeof(double2);
-    long long fit = (long long)((0.6 * (double)(freeb + held)) / (double)per_rhs);
+    const size_t pelem = p->prec == HELM_PREC_C64 ? sizeof(float2) : sizeof(double2);
+    const size_t nt = (size_t)std::max<long long>(p->ntrace, 0);
+    auto pc_per_rhs = [&]() {
+        return (size_t)(p->habc ? 4 : 3) * nt * pelem + (size_t)N * pelem + (size_t)N * sizeof(float2) +
+               (size_t)2 * p->etot * sizeof(float2);
+    };
+    const size_t held = (size_t)p->kw.nrhs * ((size_t)2 * p->kw.restart + 1) * N * sizeof(double2) +
+                        (size_t)p->kwi.nrhs * ((size_t)2 * p->kwi.restart + 1) * nt * sizeof(double2) +
+                        (size_t)p->ws_nrhs * pc_per_rhs();
+    const size_t per_rhs = ((size_t)2 * o.restart + 1) * N * sizeof(double2) + (size_t)N * 2 * sizeof(double2) +
+                           (o.inner_maxit > 0 ? ((size_t)2 * o.inner_restart + 1) * nt * sizeof(double2) : 0) +
+                           pc_per_rhs();
+    long long fit = (long long)((0.8 * (double)(freeb + held)) / (double)per_rhs);
     if (p->sopts.device_budget > 0) {
         // within what the factors leave of the handle's budget
-        const double left = (double)p->sopts.device_budget - (double)(p->X_bytes + p->XT_bytes + p->K_bytes);
+        const double left = (double)p->sopts.device_budget -
+                            (double)(p->X_bytes + p->XT_bytes + p->K_bytes + (p->d_Kp ? sym_bytes(p) : 0));
         fit = std::min(fit, (long long)(std::max(0.0, left) / (double)per_rhs));
         if (fit < 1) {
             set_error("gmres_solve: the Krylov workspace of one right-hand side does not fit in the device budget");
@@ -3008,7 +3022,10 @@ extern "C" helm_status gmres_solve(helm_problem* p, const helm_c128* f, helm_c12
                   "lower the restart length");
         return HELM_ERR_OOM;
     }
-    const int chunk = (int)std::min<long long>(fit, nrhs);
+    // as many chunks as needed, all of (nearly) the same size: a small last chunk would
+    // fall below the tensor-core threshold and repeat the nested iterations for few RHS
+    const long long nchunks = (nrhs + std::min<long long>(fit, nrhs) - 1) / std::min<long long>(fit, nrhs);
+    const int chunk = (int)((nrhs + nchunks - 1) / nchunks);
     helm_status worst = HELM_OK;
     for (int k0 = 0; k0 < nrhs; k0 += chunk) {
         const int nk = std::min(chunk, nrhs - k0);
