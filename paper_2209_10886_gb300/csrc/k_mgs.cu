@@ -345,7 +345,7 @@ cudaError_t launch_ept(MgsArgs& a, int grid, cudaStream_t st) {
 
 // ---------------------------------------------------------------------------
 // Classical Gram-Schmidt with selective reorthogonalisation (the DGKS test: a
-// second pass when ||w'||^2 < ||w||^2 / 2) for short vectors, one cooperative
+// second pass when ||w'||^2 < eta2 ||w||^2, eta2 = 1/2 by default) for short vectors, one cooperative
 // launch per Arnoldi step: CTA b keeps the contiguous slice [b*L, b*L + L) of w
 // in shared memory; a pass computes all j+1 dot products (warp q takes the basis
 // vectors q + 16 t and q + 8 + 16 t), reduces them over the grid (one barrier),
@@ -386,6 +386,7 @@ struct Cgs2Args {
     VT* vout1;                 // when set, v_{j+1} is also written here and to vout2 (RHS r at + r*vsr)
     VT* vout2;
     long long limit;           // cycles a grid barrier waits before it gives up
+    double eta2;               // second pass when ||w'||^2 < eta2 ||w||^2
 };
 
 constexpr int CT = 256;        // threads per CTA of the fused step
@@ -568,7 +569,7 @@ __global__ void __launch_bounds__(CT, 1) cgs2_step_kernel(Cgs2Args<VT> a) {
         if (threadIdx.x == 0) part[(long long)blockIdx.x * PS] = make_double2(n1, 0.0);
         if (!grid_reduce(part, 1)) return;
         double hn2 = hv[0].x;                        // ||w'||^2
-        const bool second = hn2 < 0.5 * w2;
+        const bool second = hn2 < a.eta2 * w2;
         if (second) {
             part = cur_part();
             dots(V, part);
@@ -852,7 +853,7 @@ __global__ void __launch_bounds__(CT, 1) cgs2_group_kernel(Cgs2Args<VT> a, int G
         if (threadIdx.x < gn) {
             const int g = threadIdx.x;
             gn2[g] = hv[g].x;
-            gsec[g] = gact[g] && gn2[g] < 0.5 * gw2[g];
+            gsec[g] = gact[g] && gn2[g] < a.eta2 * gw2[g];
         }
         __syncthreads();
         int anysec = 0;
@@ -1026,11 +1027,11 @@ cudaError_t launch_cgs2_step(const VT* V, long long vsk, long long vsr, int j, l
                              const int* active, double2* hsum, int ldh, double* hnorm, int* need, double2* H, int ldH,
                              long long hs, double2* cs, double2* sn, double2* g, int ldg, double* est, double* invh,
                              double2* partial, unsigned* bar, int* err, int grid, cudaStream_t st, const int* dj,
-                             int jmax, const VT* wsrc, VT* vout1, VT* vout2, long long limit) {
+                             int jmax, const VT* wsrc, VT* vout1, VT* vout2, long long limit, double eta2) {
     if (grid <= 0) return cudaErrorInvalidValue;
     const int L = (int)((n + grid - 1) / grid);
     Cgs2Args<VT> a{V, vsk, vsr, j, n, nrhs, active, hsum, ldh, hnorm, need, H, ldH, hs, cs, sn, g, ldg, est, invh,
-                   partial, bar, err, L, dj, wsrc, vout1, vout2, limit > 0 ? limit : BAR_LIMIT};
+                   partial, bar, err, L, dj, wsrc, vout1, vout2, limit > 0 ? limit : BAR_LIMIT, eta2};
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(CT);
@@ -1071,7 +1072,8 @@ cudaError_t launch_cgs2_step(const VT* V, long long vsk, long long vsr, int j, l
     template cudaError_t launch_cgs2_step<VT>(const VT*, long long, long long, int, long long, int, const int*,   \
                                               double2*, int, double*, int*, double2*, int, long long, double2*,   \
                                               double2*, double2*, int, double*, double*, double2*, unsigned*, int*, \
-                                              int, cudaStream_t, const int*, int, const VT*, VT*, VT*, long long);
+                                              int, cudaStream_t, const int*, int, const VT*, VT*, VT*, long long, \
+                                              double);
 HELM_CGS2_INST(double2)
 HELM_CGS2_INST(float2)
 #undef HELM_CGS2_INST
