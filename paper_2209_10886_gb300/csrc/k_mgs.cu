@@ -355,8 +355,10 @@ cudaError_t launch_ept(MgsArgs& a, int grid, cudaStream_t st) {
 // and the Givens arithmetic in the vectors' precision; sums across CTAs, the
 // coefficients and the stored least-squares problem in FP64 (the serial chain of
 // rotations in FP64 costs ~0.6 us per rotation on GB300's narrow FP64 pipe).  Reductions are deterministic: every CTA adds
-// the partials of all CTAs in the same order.  2 grid barriers per RHS, 4 when
-// the second pass runs, each bounded in time (HELM_ERR_TIMEOUT, then return).
+// the partials of all CTAs in the same order, so every CTA takes the same branches.
+// ||w'||^2 comes from ||w||^2 - ||h||^2 (no reduction of its own) when that keeps at
+// least 2 eta2 of ||w||^2.  1 grid barrier per RHS then, 2 when ||w'||^2 is reduced,
+// 4 when the second pass runs, each bounded in time (HELM_ERR_TIMEOUT, then return).
 template <typename VT>
 struct Cgs2Args {
     const VT* V;               // basis: v_k of RHS r at V + k*vsk + r*vsr; w = v_{j+1} in place
@@ -562,13 +564,24 @@ __global__ void __launch_bounds__(CT, 1) cgs2_step_kernel(Cgs2Args<VT> a) {
         if (threadIdx.x == 0) part[(long long)blockIdx.x * PS + nvec] = make_double2(w2l, 0.0);
         if (!grid_reduce(part, nvec + 1)) return;
         const double w2 = hv[nvec].x;
+        // ||h||^2: the same sum, in the same order, in every thread of every CTA
+        double hh = 0.0;
+        for (int k = 0; k < nvec; ++k) hh = fma(hv[k].x, hv[k].x, fma(hv[k].y, hv[k].y, hh));
         for (int k = threadIdx.x; k < nvec; k += CT) h1[k] = hv[k];
         set_coef();
         const double n1 = block_sum(update(V));
-        part = cur_part();
-        if (threadIdx.x == 0) part[(long long)blockIdx.x * PS] = make_double2(n1, 0.0);
-        if (!grid_reduce(part, 1)) return;
-        double hn2 = hv[0].x;                        // ||w'||^2
+        double hn2;                                  // ||w'||^2
+        if (w2 - hh >= 2.0 * a.eta2 * w2) {
+            // the projection removed at most 1 - 2 eta2 of ||w||^2: ||w'||^2 = ||w||^2 - ||h||^2
+            // loses at most a factor 1 / (2 eta2) of the sums' relative accuracy, and no
+            // second pass follows, so the grid reduction of ||w'||^2 is not needed
+            hn2 = w2 - hh;
+        } else {
+            part = cur_part();
+            if (threadIdx.x == 0) part[(long long)blockIdx.x * PS] = make_double2(n1, 0.0);
+            if (!grid_reduce(part, 1)) return;
+            hn2 = hv[0].x;
+        }
         const bool second = hn2 < a.eta2 * w2;
         if (second) {
             part = cur_part();
@@ -644,8 +657,8 @@ __global__ void __launch_bounds__(CT, 1) cgs2_step_kernel(Cgs2Args<VT> a) {
 
 // ---------------------------------------------------------------------------
 // The same step for several RHS at once (nrhs >= 2): groups of up to CG_MAX RHS go
-// through every phase together, so a group costs the grid barriers one RHS does (2, or
-// 4 when any of its RHS needs the second pass).  The dot products of all (RHS, basis
+// through every phase together, so a group costs the grid barriers one RHS does (1, 2
+// when any of its RHS needs ||w'||^2 reduced, 4 when any needs the second pass).  The dot products of all (RHS, basis
 // vector) pairs of the group and the squared norms (the dot of w with itself) share
 // one grid reduction; the second-pass test is per RHS; the Givens updates of the
 // group's RHS run on different CTAs.
@@ -846,13 +859,30 @@ __global__ void __launch_bounds__(CT, 1) cgs2_group_kernel(Cgs2Args<VT> a, int G
         }
         __syncthreads();
         update(0);
-        __syncthreads();
-        part = cur_part();
-        dots(1, part);
-        if (!grid_reduce(part, gn)) return;
+        // ||w'||^2 = ||w||^2 - ||h||^2 per RHS where the difference keeps at least 2 eta2
+        // of ||w||^2 (as in the one-RHS step); a grid reduction of ||w'||^2 otherwise
         if (threadIdx.x < gn) {
             const int g = threadIdx.x;
-            gn2[g] = hv[g].x;
+            double hh = 0.0;
+            for (int k = 0; k < nvec; ++k) {
+                const double2 h = h1[g * nvec + k];
+                hh = fma(h.x, h.x, fma(h.y, h.y, hh));
+            }
+            gn2[g] = gw2[g] - hh;
+            gsec[g] = gact[g] && !(gn2[g] >= 2.0 * a.eta2 * gw2[g]);    // 1: exact norm wanted
+        }
+        __syncthreads();
+        int exact = 0;
+        for (int g = 0; g < gn; ++g) exact |= gsec[g];
+        if (exact) {
+            part = cur_part();
+            dots(1, part);
+            if (!grid_reduce(part, gn)) return;
+            if (threadIdx.x < gn) gn2[threadIdx.x] = hv[threadIdx.x].x;
+        }
+        __syncthreads();
+        if (threadIdx.x < gn) {
+            const int g = threadIdx.x;
             gsec[g] = gact[g] && gn2[g] < a.eta2 * gw2[g];
         }
         __syncthreads();
