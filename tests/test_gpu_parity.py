@@ -3,11 +3,16 @@
 Tolerances (written per test):
 * complex128 path vs oracle: both compute the same operator in FP64 with
   different elimination orders (block-tridiagonal Gauss-Jordan vs sparse LU);
-  the difference is roundoff times the local condition number, <= 1e-10.
+  the difference is roundoff times the local condition number (measured
+  2e-15..2e-14 on the field and on the interface nodes); one application <= 1e-12.
 * complex64 preconditioner vs the complex128 oracle: unit roundoff 6e-8
-  amplified by the block recursion over the grid rows (measured 4e-6..7e-6 for
-  64-row subdomains, 2.9e-5 for 131-row ones: an amplification of 60..500;
-  printed with -s); bound 1e-4.
+  amplified by the block recursion over the grid rows (measured 2e-6..7e-6 on the
+  field and up to 1.4e-5 on the interface nodes for subdomains of at most 64 rows,
+  2.9e-5 / 3.2e-5 for 131-row ones: an amplification of 30..500; printed with -s).
+  Bars per case (C64_BARS) about 3x the measurement; 1e-4 where a test combines
+  other paths.
+* Every preconditioner comparison also takes the largest error on the interface
+  boundary nodes (iface_err) relative to the largest value there.
 * Solutions: both sides solve to a true relative residual of 1e-9, so they
   agree to cond(A) * 1e-9; the bar is rel. L2 <= 1e-5.
 """
@@ -23,6 +28,10 @@ from oracle import Decomposition, Sweeper, assemble_operator
 from oracle.adjoint import misfit_gradient_direct
 
 C64_TOL = 1e-4       # rel. L2 of one complex64 preconditioner application vs the oracle
+# (field, interface nodes) bars of one complex64 BSP application per case: subdomains of
+# at most 64 rows / 131 rows (the block recursion's amplification grows with the rows)
+C64_BARS = {"tiny_2x2": (2e-5, 5e-5), "uneven_4x3": (2e-5, 5e-5), "wide_2x2_131": (1e-4, 1e-4)}
+C128_BAR = 1e-12
 
 
 @pytest.fixture(scope="module")
@@ -64,6 +73,23 @@ CASES = {
 }
 
 
+def iface_mask(w):
+    """The subdomains' interface boundary nodes (every node next to a cut): the values
+    the transmission epilogues form, checked on their own so that an error confined to
+    them cannot hide in the norm over the whole field."""
+    mask = np.zeros((w.n, w.n), dtype=bool)
+    for c in w.xcuts[1:-1]:
+        mask[:, c - 1] = mask[:, c] = True
+    for c in w.ycuts[1:-1]:
+        mask[c - 1, :] = mask[c, :] = True
+    return mask.reshape(-1)
+
+
+def iface_err(z, ref, mask):
+    """Largest error on the interface nodes relative to the largest value there."""
+    return float(np.abs(z[mask] - ref[mask]).max() / np.abs(ref[mask]).max())
+
+
 def test_matvec_matches_sparse_matrix(H):
     for name in ("tiny_2x2", "uneven_4x3"):
         w = CASES[name]()
@@ -76,8 +102,10 @@ def test_matvec_matches_sparse_matrix(H):
         p.close()
 
 
-@pytest.mark.parametrize("prec,tol", [("c128", 1e-11), ("c64", C64_TOL)])
+@pytest.mark.parametrize("prec,tol", [("c128", 1e-12), ("c64", 1e-5)])
 def test_single_subdomain_is_direct_solve(H, prec, tol):
+    """One subdomain: the preconditioner is the direct solve (measured c128 8e-15,
+    c64 2.5e-6 on 75 rows)."""
     w = W.workload("custom", n=75, N1=1, N2=1, medium="layered", seed=2)
     p, _ = make(H, w, prec)
     A = assemble_operator(w.n, w.h, w.omega, w.m2).tocsc()
@@ -99,11 +127,13 @@ def test_precond_apply_c128_matches_oracle(H, case, sched):
     nrhs = 3 if case in ("tiny_2x2", "uneven_4x3") else 1
     r = W.random_complex((nrhs, w.N), 5)
     z = p.precond_apply(cuda(r), sched=sched).cpu().numpy()
+    mask = iface_mask(w)
     for k in range(nrhs):
         ref = sw.precondition(r[k], sched)
         e = rel(z[k], ref)
-        print(f"{case} {sched} c128 rhs{k}: rel {e:.2e}")
-        assert e <= 1e-10
+        ei = iface_err(z[k], ref, mask) if mask.any() else 0.0
+        print(f"{case} {sched} c128 rhs{k}: rel {e:.2e}, interface nodes max {ei:.2e}")
+        assert e <= C128_BAR and ei <= C128_BAR
     p.close()
 
 
@@ -114,10 +144,13 @@ def test_precond_apply_c64_matches_oracle(H, case):
     sw = Sweeper(dec)
     r = W.random_complex((5, w.N), 6)      # 5 RHS: one CTA of 4 and a ragged CTA of 1
     z = p.precond_apply(cuda(r), sched="BSP").cpu().numpy()
+    mask = iface_mask(w)
     for k in range(5):
-        e = rel(z[k], sw.precondition(r[k], "BSP"))
-        print(f"{case} BSP c64 rhs{k}: rel {e:.2e}")
-        assert e <= C64_TOL
+        ref = sw.precondition(r[k], "BSP")
+        e, ei = rel(z[k], ref), iface_err(z[k], ref, mask)
+        print(f"{case} BSP c64 rhs{k}: rel {e:.2e}, interface nodes max {ei:.2e}")
+        bar_field, bar_iface = C64_BARS[case]
+        assert e <= bar_field and ei <= bar_iface
     p.close()
 
 
