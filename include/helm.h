@@ -197,9 +197,10 @@ typedef struct {
                            FP64 FGMRES preconditioned by the sweep, at most inner_maxit
                            steps per application, inner_restart per cycle, stopping at
                            ||b - (I - S) g|| <= inner_tol ||b|| (classical Gram-Schmidt
-                           with reorthogonalisation on the ntrace-long vectors, their
-                           precision as inner_fp64 says); the outer FGMRES stays FP64
-                           on the volume system */
+                           on the ntrace-long vectors, a second pass only when the first
+                           removed more than 90 % of ||w||^2; their precision as
+                           inner_fp64 says); the outer FGMRES stays FP64 on the volume
+                           system */
     int inner_restart;  /* default 100 */
     double inner_tol;   /* default 1e-4 */
     int persistent;     /* 0 (default): the interface stages of every sweep are separate
@@ -235,7 +236,8 @@ typedef struct {
  * HELM_ORTHO_MGS:  modified Gram-Schmidt in one persistent kernel per step
  *                  (8 FP64 FMA per element per basis vector).
  * HELM_ORTHO_CGS2: classical Gram-Schmidt, a second pass when the first
- *                  cancelled more than half of the norm (16 FMA per element).
+ *                  removed more than half of the squared norm (16 FMA per
+ *                  element; more than 90 % in the interface iteration).
  *                  When a slice of the vector per SM fits in shared memory
  *                  (up to ~6000 values per SM), the passes, the norm and the
  *                  Givens update run as one cooperative launch per step.
