@@ -131,6 +131,41 @@ def test_double_counted_shared_diagonal_is_caught():
     assert np.linalg.norm(bad - ref) > 1e-3 * np.linalg.norm(ref)
 
 
+def _leading_band_error():
+    """The first check of the leading-band pin: B_L^{-1} b against S_L^{-1} b on the
+    first forward band, for b supported there (2 x 4 checkerboard, three bands)."""
+    w = W.workload("custom", n=24, N1=2, N2=4, medium="layered", seed=14)
+    dec = Decomposition(w.n, w.h, w.omega, w.m2, w.xcuts, w.ycuts)
+    sw = Sweeper(dec)
+    lo, hi = oswp.bands(dec.N1, dec.Ng, "L")[0]
+    full = dec.unflatten(W.random_complex(sum(dec.side_length(*ij) for ij in dec.slots), 12))
+    b = {ij: (v.copy() if lo <= dec.diagonal(ij[0]) <= hi else np.zeros_like(v)) for ij, v in full.items()}
+    x, ex = sw.block_jacobi_L(b), sw.inv_SL(b)
+    sel = [ij for ij in dec.slots if dec.diagonal(ij[0]) <= hi]
+    a, e = np.concatenate([x[ij] for ij in sel]), np.concatenate([ex[ij] for ij in sel])
+    return np.linalg.norm(a - e) / np.linalg.norm(e)
+
+
+def test_additive_band_sum_is_caught_by_the_leading_band_pin(monkeypatch):
+    """Summing every band's substitution over its whole band (the literal additive
+    reading) counts the shared diagonal twice: the leading-band pin fails."""
+    assert _leading_band_error() < 1e-13
+
+    def additive_L(self, b, overlap=True):
+        dec = self.dec
+        out = dec.zero_trace()
+        for lo, hi in oswp.bands(dec.N1, dec.Ng, "L", overlap):
+            band = set(range(lo, hi + 1))
+            xg = self.inv_SL(self._restrict_vec(b, band), restrict=band, diags=range(lo + 1, hi + 1))
+            for ij in dec.slots:
+                if dec.diagonal(ij[0]) in band:
+                    out[ij] = out[ij] + xg[ij]
+        return out
+
+    monkeypatch.setattr(oswp.Sweeper, "block_jacobi_L", additive_L)
+    assert _leading_band_error() > 1e-3
+
+
 # ------------------------------------------------ Pade HABC transmission (oracle.habc)
 import oracle.habc as ohabc  # noqa: E402
 

@@ -249,6 +249,46 @@ def test_block_jacobi_bands_against_dense():
     assert _rel(dec.flatten(sw.bsp(b)), xh + y) < 1e-12
 
 
+@pytest.mark.parametrize("N1,N2", [(2, 4), (2, 6), (3, 5)])
+def test_leading_band_is_an_exact_substitution(N1, N2):
+    """Section 5 without the dense restatement: S_L is block lower triangular by
+    diagonals, so S_L^{-1} b on the diagonals of the first forward band depends only on
+    b there and on that band's own blocks.  For b supported on the first band (its
+    shared last diagonal included), B_L^{-1} b must equal S_L^{-1} b (the product of
+    Proposition 1's factors) on those diagonals; with b zero on the shared diagonal as
+    well, the other bands start from zero and B_L^{-1} b vanishes beyond the band (no
+    propagation between bands in one block Jacobi half-step).  The same for the first
+    backward band (top-right corner) and S_U.  The literal additive sum counts the
+    shared diagonal twice and fails the first check."""
+    w, A, dec, sw = _problem(6 * max(N1, N2), N1, N2, medium="layered", seed=10 + N2)
+    n = sum(dec.side_length(*ij) for ij in dec.slots)
+    full = dec.unflatten(W.random_complex(n, 12))
+
+    def on(diags):
+        return {ij: (v.copy() if dec.diagonal(ij[0]) in diags else np.zeros_like(v)) for ij, v in full.items()}
+
+    def vec(x, pred):
+        return np.concatenate([x[ij] for ij in dec.slots if pred(dec.diagonal(ij[0]))])
+
+    (lo, hi) = bands(dec.N1, dec.Ng, "L")[0]
+    assert len(bands(dec.N1, dec.Ng, "L")) >= 2 and lo == 2
+    b = on(set(range(lo, hi + 1)))
+    assert _rel(vec(sw.block_jacobi_L(b), lambda d: d <= hi), vec(sw.inv_SL(b), lambda d: d <= hi)) < 1e-13
+    b = on(set(range(lo, hi)))
+    x, ex = sw.block_jacobi_L(b), sw.inv_SL(b)
+    assert _rel(vec(x, lambda d: d <= hi), vec(ex, lambda d: d <= hi)) < 1e-13
+    assert np.abs(vec(x, lambda d: d > hi)).max() == 0.0 and np.abs(vec(ex, lambda d: d > hi)).max() > 0.0
+
+    (lo, hi) = bands(dec.N1, dec.Ng, "U")[0]
+    assert hi == dec.Ng + 1
+    r = on(set(range(lo, hi + 1)))
+    assert _rel(vec(sw.block_jacobi_U(r), lambda d: d >= lo), vec(sw.inv_SU(r), lambda d: d >= lo)) < 1e-13
+    r = on(set(range(lo + 1, hi + 1)))
+    y, ey = sw.block_jacobi_U(r), sw.inv_SU(r)
+    assert _rel(vec(y, lambda d: d >= lo), vec(ey, lambda d: d >= lo)) < 1e-13
+    assert np.abs(vec(y, lambda d: d < lo)).max() == 0.0 and np.abs(vec(ey, lambda d: d < lo)).max() > 0.0
+
+
 @pytest.mark.parametrize("N1,N2", [(2, 2), (4, 2), (3, 2), (2, 1)])
 def test_bsp_with_one_band_equals_sgs(N1, N2):
     """One band (Ng - 1 <= N1): B_L = S_L and the two half-steps give exactly S_U^{-1} S_L^{-1}."""
