@@ -11,6 +11,9 @@
   .device_budget gets HELM_ERR_OOM from precond_factor (nothing allocated); one
   whose factors fit but whose Krylov workspace does not gets HELM_ERR_OOM from
   gmres_solve.
+* Non-convergence: maxit = 1 at a tolerance one step cannot reach gives
+  HELM_ERR_NO_CONVERGENCE with a message, the last iterate in u and the info
+  entries filled (one step, the true relative residual of that iterate).
 """
 import numpy as np
 import pytest
@@ -94,3 +97,33 @@ def test_device_budget_gives_oom(H):
     u, info, _ = tight.solve(cuda(w.f), restart=2, maxit=4, raise_on_noconv=False)   # a small workspace fits
     assert info[0][0] == 4
     tight.close()
+
+
+@pytest.mark.parametrize("inner_maxit", [0, 60])
+def test_non_convergence_reports_status_and_fills_info(H, inner_maxit):
+    w = uneven()
+    A = assemble_operator(w.n, w.h, w.omega, w.m2)
+    p = H.Problem(w.n, w.n, w.h, w.omega, cuda(w.m2, torch.float64), w.N1, w.N2, w.xcuts, w.ycuts).factor("c64")
+    fh = W.random_complex((2, w.N), 90)
+    f = cuda(fh)
+    kw = dict(tol=1e-12, restart=30, maxit=1, inner_maxit=inner_maxit, inner_tol=1e-2)
+    with pytest.raises(H.HelmError) as e:
+        p.solve(f, **kw)
+    assert e.value.status == 5 and "maxit" in str(e.value)
+    u, info, _ = p.solve(f, raise_on_noconv=False, **kw)
+    u = u.cpu().numpy()
+    for k in range(2):
+        b = w.h ** 2 * fh[k]
+        rr = float(np.linalg.norm(b - A @ u[k]) / np.linalg.norm(b))
+        print(f"inner_maxit {inner_maxit} rhs{k}: its {info[k][0]}, relres {info[k][1]:.3e}, host {rr:.3e}")
+        assert info[k][0] == 1
+        assert 1e-12 < info[k][1] < 1.0          # one minimal-residual step from u = 0
+        assert abs(info[k][1] - rr) <= 1e-6 * rr  # the reported residual is that of u
+    # the handle is unaffected: the same solve to a reachable tolerance converges
+    u2, info2, _ = p.solve(f, tol=1e-9, restart=30, maxit=200, inner_maxit=inner_maxit, inner_tol=1e-2)
+    u2 = u2.cpu().numpy()
+    for k in range(2):
+        b = w.h ** 2 * fh[k]
+        assert info2[k][1] <= 1e-9
+        assert np.linalg.norm(b - A @ u2[k]) <= 2e-9 * np.linalg.norm(b)
+    p.close()
