@@ -328,8 +328,10 @@ helm_status precond_apply_noalloc(helm_problem* p, int sched, const helm_c128* r
 helm_status helm_matvec(helm_problem* p, const helm_c128* u, helm_c128* Au, int nrhs, void* stream);
 
 /* Solve A u = h^2 f for nrhs sources by right-preconditioned flexible GMRES
- * in FP64 (residual, Gram-Schmidt, Hessenberg least squares and update in
- * FP64; the preconditioner in the factor precision).  f, u device; opts host
+ * in FP64 (the paper's outer Krylov solver, Section 6; residual, Gram-Schmidt,
+ * Hessenberg least squares and update in FP64; the preconditioner, precond_apply's
+ * M^{-1} or with opts->inner_maxit > 0 the interface FGMRES of Sections 3-5, in
+ * the factor precision).  f, u device; opts host
  * (NULL: defaults); info host array of nrhs entries (or NULL).
  * Returns HELM_ERR_NO_CONVERGENCE (u holds the last iterate, info filled)
  * when some RHS did not reach tol within maxit.  Synchronises `stream`. */
